@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the spectral-element elastic hot path on GB300.
+
+Workload: the three-layer jittered cube (vp 5000/3500/2000 m/s, side 4 km, interior vertex
+jitter up to 10 % of the element size, 256 GLL intervals per side: 64^3 elements at
+NGLL=5), Ricker point source at the centre, 256 surface receivers. One step = one explicit
+Newmark time step of the whole hot path (Newmark update, matrix-free forces over all
+colours with the coloured assembly, source, receivers). Metric: local GLL-point updates
+per second = nspec * NGLL^3 * steps / time, summed over ranks (replicas, weak scaling).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--ngll 5] [--impl ours|reference]
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle (the only
+reference this method has) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLL-pt updates/s & %HBM roofline; shots/s batched vs plain at 2e-5 rel L2"
+UNIT = "local GLL-pt updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--ngll", type=int, default=5)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--stiffness-reps", type=int, default=40)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return p.parse_args()
+
+
+def algorithmic_bytes(nspec: int, ngll: int, nglob: int):
+    """Bytes a perfect-reuse implementation moves (FP32 data, int32 ibool):
+    per local point 52 B (ibool, 9 inverse-Jacobian terms, J, kappa, mu), per global node
+    76 B per step (read u, v, a, 1/M; write u, v, a); the force kernel alone: 52 B per
+    local point plus u read once and f written once per node (24 B)."""
+    nloc = nspec * ngll ** 3
+    return dict(step=52 * nloc + 76 * nglob, forces=52 * nloc + 24 * nglob, nloc=nloc)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_12850_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(ngll: int):
+    """DRAM bytes per force-kernel launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"forces_kernel_ngll{ngll}_layered.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_sweep:\s*([0-9.eE+]+)\s+kernel_sources:\s*([0-9a-f]+)", text)
+    if not m or m.group(2) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.proc = None
+        target = str(device)
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(device)
+            target = "%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        except Exception:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            if vis:
+                target = vis.split(",")[device]
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", target, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+                for name, val in zip(names, r[4:8]):
+                    if val.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample_rate(ngll: int, seconds: float, steps_hint: int | None = None):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: a smaller
+    cube of the same recipe (same NGLL, layering, jitter, receivers), enough steps for about
+    ``seconds`` of CPU time. Returns (local-pt updates/s, sample description, steps, time)."""
+    from oracle import sem_oracle
+    from paper_2606_12850_gb300 import inputs
+
+    probe = inputs.layered_cube(ngll, n=6, nsteps=2)
+    m = sem_oracle.build_model(probe)
+    t = time.perf_counter()
+    sem_oracle.newmark_run(m, 1e-4, 2)
+    per_elem_step = (time.perf_counter() - t) / (2 * probe.mesh.nspec)
+    n = 16
+    nsteps = max(2, int(seconds / (per_elem_step * n ** 3)))
+    if steps_hint is not None:
+        nsteps = steps_hint
+    w = inputs.layered_cube(ngll, n=n, nsteps=nsteps)
+    m = sem_oracle.build_model(w)
+    dt = m.cfl_dt(w.courant)
+    src, rec = sem_oracle.locate_workload(m, w)
+    t = time.perf_counter()
+    sem_oracle.newmark_run(m, dt, nsteps, src_nodes=src, src_force=w.source_force, f0=w.f0, t0=w.t0,
+                           rec_nodes=rec)
+    el = time.perf_counter() - t
+    rate = w.mesh.nlocal * nsteps / el
+    desc = (f"FP64 numpy oracle, {n}^3-element three-layer jittered cube at NGLL={ngll} "
+            f"(1/{(inputs.LAYERED_ELEMS.get(ngll, 64) / n) ** 3:.0f} of the benchmark mesh), {nsteps} steps, "
+            f"{el:.1f} s, single thread")
+    return rate, desc, nsteps, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import sem_oracle
+    from paper_2606_12850_gb300 import inputs
+
+    # each step: one oracle time step on a sub-cube sized so that the run takes ~2 minutes
+    budget = 120.0
+    probe = inputs.layered_cube(args.ngll, n=6, nsteps=2)
+    m = sem_oracle.build_model(probe)
+    t = time.perf_counter()
+    sem_oracle.newmark_run(m, 1e-4, 2)
+    per_elem_step = (time.perf_counter() - t) / (2 * probe.mesh.nspec)
+    per_step = budget / max(1, args.steps + args.warmup)
+    n = int(max(2, min(16, round((per_step / per_elem_step) ** (1 / 3)))))
+    w = inputs.layered_cube(args.ngll, n=n, nsteps=args.steps)
+    m = sem_oracle.build_model(w)
+    dt = m.cfl_dt(w.courant)
+    src, rec = sem_oracle.locate_workload(m, w)
+    kw = dict(src_nodes=src, src_force=w.source_force, f0=w.f0, t0=w.t0, rec_nodes=rec)
+    _, u, v, a = sem_oracle.newmark_run(m, dt, args.warmup, **kw)
+    t = time.perf_counter()
+    sem_oracle.newmark_run(m, dt, args.steps, u0=u, v0=v, a0=a, **kw)
+    el = time.perf_counter() - t
+    value = w.mesh.nlocal * args.steps / el
+    sample = (f"FP64 numpy oracle, each step on a {n}^3-element cube of the same recipe "
+              f"(three-layer, jittered, NGLL={args.ngll}), single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"three-layer jittered cube, NGLL={args.ngll} (bounded {n}^3 sample per step)",
+                   "ngll": args.ngll, "nspec": w.mesh.nspec, "parallelism": "single host thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2606_12850_gb300 import build, inputs, sem
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+
+    K, W = args.steps, args.warmup
+    w = inputs.layered_cube(args.ngll, nsteps=K)
+    mesh = w.mesh
+    stream = torch.cuda.Stream(device=local)
+    s = sem.setup_workload(w, device=local, stream=stream)
+    ctx = s.ctx
+    info = sem.sem_info(ctx)
+    ncolors = info["ncolors"]
+    alg = algorithmic_bytes(mesh.nspec, mesh.ngll, mesh.nglob)
+    nrec = len(s.rec_nodes)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        seis_w = torch.empty(max(1, nrec * 3 * W), device="cuda")
+        seis = torch.empty(max(1, nrec * 3 * K), device="cuda")
+    sem.sem_run_dev(ctx, W, seis_w)
+    barrier()
+    clocks = ClockSampler(local)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    sem.sem_run_dev(ctx, K, seis)
+    end.record(stream)
+    end.synchronize()
+    clock_info = clocks.stop()
+    ms = start.elapsed_time(end)
+    barrier()
+    t_max = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t_max.item())
+    value = world * alg["nloc"] * K / (ms / 1e3)
+    launches = K * (ncolors + 2) + 1
+
+    # the dominant kernel (force kernel over all colours) timed alone on the same stream
+    with torch.cuda.stream(stream):
+        ud = (torch.rand(3 * mesh.nglob, device="cuda") - 0.5) * 2e-3
+        fd = torch.empty_like(ud)
+    stream.synchronize()
+    for _ in range(3):
+        sem.sem_apply_stiffness(ctx, ud, fd)
+    reps = max(1, args.stiffness_reps)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in evs:
+        a.record(stream)
+        sem.sem_apply_stiffness(ctx, ud, fd)
+        b.record(stream)
+    stream.synchronize()
+    sweep_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    peak, peak_src = measured_peaks()
+    achieved = alg["forces"] / (sweep_ms / 1e3) / 1e9
+    traffic = profiled_traffic(args.ngll)
+    step_gbs = alg["step"] * K / (ms / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers: initial state up, K steps, seismograms
+    # and final displacement down (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda shape: torch.zeros(shape, dtype=torch.float32, pin_memory=True).numpy()
+        u0, v0, a0 = pin((mesh.nglob, 3)), pin((mesh.nglob, 3)), pin((mesh.nglob, 3))
+        seis_h = pin((nrec, 3, K))
+        u_out = pin((mesh.nglob, 3))
+        barrier()
+        t = time.perf_counter()
+        sem.sem_set_state(ctx, u0, v0, a0)
+        sem.sem_run(ctx, K, out=seis_h)
+        lib = sem.lib()
+        rc = lib.sem_get_state(ctx.handle, u_out.ctypes.data_as(sem._P), None, None)
+        if rc != 0:
+            raise RuntimeError(sem.sem_last_error(ctx))
+        el = time.perf_counter() - t
+        el_t = torch.tensor([el], device="cuda", dtype=torch.float64)
+        if world > 1:
+            torch.distributed.all_reduce(el_t, op=torch.distributed.ReduceOp.MAX)
+        h2d = 3 * mesh.nglob * 3 * 4
+        d2h = nrec * 3 * K * 4 + mesh.nglob * 3 * 4
+        e2e = {"value": world * alg["nloc"] * K / float(el_t.item()), "unit": UNIT,
+               "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+               "what": "sem_set_state (u,v,a from pinned host) + sem_run (K steps, seismograms to host) + "
+                       "sem_get_state (u to host), wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, desc, _, _ = oracle_sample_rate(args.ngll, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"three-layer jittered cube {mesh.nx}^3 hex, NGLL={mesh.ngll}, 4 km "
+                                   "(plain SEM scaling / (h,p) sweep configuration)",
+                       "ngll": mesh.ngll, "nspec": mesh.nspec, "nglob": mesh.nglob, "nlocal": alg["nloc"],
+                       "ncolors": ncolors, "nrec": nrec, "dt": s.dt,
+                       "l2": "inputs larger than L2: 1.7 GB of element records stream every step",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": f"forces_kernel<{mesh.ngll}> (all {ncolors} colour launches of one stiffness "
+                                   "application)",
+                         "sweep_ms": sweep_ms, "peak_source": peak_src},
+            "hbm_roofline_step": {"achieved": step_gbs, "frac": step_gbs / peak, "unit": "GB/s",
+                                  "bytes_per_step": alg["step"]},
+            "global_pt_updates_per_s": world * mesh.nglob * K / (ms / 1e3),
+            "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clock_info,
+            "kernel_sources": kernel_source_hash(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

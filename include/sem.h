@@ -1,0 +1,166 @@
+/*
+ * sem.h -- C ABI of libsemgb, a GB300 (sm_103a) spectral-element solver for the 3D
+ * isotropic elastic wave equation (arXiv 2606.12850, "High-Order Spectral Element Methods
+ * for Wave Propagation on ARM Multicore CPU with SME").
+ *
+ * The library evaluates the hot path of Sec. II-B and IV-C on one GPU:
+ *   - matrix-free internal forces  f = -K u  (Sec. II-B: reference derivatives along
+ *     xi/eta/zeta as small products with the 1D GLL derivative matrix, Jacobian map,
+ *     isotropic Hooke stress, weighted transposed products);
+ *   - deterministic assembly through ibool, colour by colour with no atomics (Sec. IV-C:
+ *     elements sharing a node never share a colour);
+ *   - explicit second-order Newmark stepping with the diagonal GLL mass (Sec. I, II-B,
+ *     V-C), a Ricker point force and receiver recording (Sec. V-C).
+ *
+ * Conventions used by every call:
+ *   ngll     points per direction, NGLL = N + 1, 2 <= ngll <= 10.
+ *   local point index p = i + ngll*j + ngll*ngll*k (i along xi, j along eta, k along zeta).
+ *   ibool    int32 [nspec][ngll^3], 0-based global node of every local point.
+ *   ctrl     float64 [nspec][8][3] corner vertices of each (trilinear) hexahedron; corner
+ *            c = a + 2b + 4d sits at reference (xi, eta, zeta) = (2a-1, 2b-1, 2d-1).
+ *   fields   float32 [nglob][3] (x, y, z per node), metres, m/s, m/s^2.
+ *   seis     float32 [nrec][3][nsteps].
+ *   Step n (0-based since the last sem_set_state) advances u^n -> u^{n+1}; the source acts
+ *   at t_{n+1} = (n+1) dt and the record of step n is u^{n+1}.
+ *
+ * Ownership: host pointers are read (or written) during the call only. Pointers named
+ * *_dev are device pointers on the context's GPU, borrowed for the call (asynchronous
+ * calls: until the context's stream reaches that point). The library owns all the other
+ * device memory it allocates and frees it in sem_destroy.
+ *
+ * Errors: every int-returning call returns SEM_OK (0) or a negative code below and leaves a
+ * message for sem_last_error. No call aborts the process. A sem_ctx is not thread-safe.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEM_OK 0
+#define SEM_EINVAL (-1)    /* bad argument: size, index out of range, J <= 0, NaN ...     */
+#define SEM_ENOMEM (-2)    /* device or host allocation failed                             */
+#define SEM_ECUDA (-3)     /* a CUDA runtime call failed (message holds cudaGetErrorString) */
+#define SEM_ESTATE (-4)    /* call order: mesh, then material, then dt, before stepping     */
+#define SEM_ETIMEOUT (-5)  /* a bounded device wait gave up                                 */
+#define SEM_EDIVERGED (-6) /* NaN or Inf found in the wavefield                             */
+
+typedef struct sem_ctx sem_ctx;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int sem_version(void);
+
+/* GLL nodes, weights and derivative matrix for ngll points (Sec. II-B: tensor-product GLL
+ * interpolation; the 1D differentiation matrix of the small products).
+ * xi[ngll] ascending on [-1, 1]; w[ngll]; hprime[ngll*ngll] row-major with
+ * hprime[i*ngll + l] = l_l'(xi_i). Host only, no GPU needed. Any output may be NULL. */
+int sem_gll(int ngll, double* xi, double* w, double* hprime);
+
+/* Greedy colouring of elements (Sec. IV-C): corner vertices taken from ibool give an
+ * element-to-vertex incidence; elements sharing a vertex are adjacent (the sparsity of the
+ * incidence times its transpose); colours are assigned greedily in element order. On
+ * return color[e] in [0, *ncolors) and no two elements of one colour share any ibool
+ * entry (checked; SEM_EINVAL otherwise, e.g. for a non-conforming mesh or an element that
+ * repeats a node). Host only, no GPU needed. */
+int sem_color_elements(int nspec, int ngll, int nglob, const int32_t* ibool,
+                       int32_t* color, int* ncolors);
+
+/* Create a solver context on CUDA device `device` for polynomial degree ngll-1.
+ * `cuda_stream` is a cudaStream_t to issue all work on, or NULL for a stream the context
+ * creates and owns. */
+int sem_create(sem_ctx** out, int ngll, int device, void* cuda_stream);
+
+/* Free every device and host resource of the context. NULL is allowed. */
+int sem_destroy(sem_ctx* ctx);
+
+/* Set the mesh (Sec. II-B hexahedral mesh, Sec. IV-C global-to-local map).
+ * Computes GLL point positions from the trilinear corners, the inverse Jacobian terms by
+ * differentiating positions with hprime, the colouring, the colour-sorted element order
+ * and the device copies. SEM_EINVAL if nspec < 1, an ibool entry is outside [0, nglob),
+ * an element repeats a node, some node in [0, nglob) is never referenced, or J <= 0. */
+int sem_set_mesh(sem_ctx* ctx, int nspec, int nglob, const int32_t* ibool, const double* ctrl);
+
+/* Set the isotropic material per local point, float32 [nspec][ngll^3] each
+ * (Sec. II-B: density rho and stiffness C; here C from the wave speeds with
+ * mu = rho vs^2, lambda = rho (vp^2 - 2 vs^2), kappa = lambda + 2/3 mu). Assembles the
+ * diagonal mass M_I = sum rho J w_i w_j w_k. SEM_EINVAL for rho <= 0, vs < 0, vp <= vs,
+ * or non-finite values. Requires sem_set_mesh. */
+int sem_set_material(sem_ctx* ctx, const float* rho, const float* vp, const float* vs);
+
+/* dt = courant * min over elements of (smallest distance between neighbouring GLL points
+ * along a grid line / largest vp of the element) (Sec. IV-B, V-C). Requires material. */
+int sem_suggest_dt(sem_ctx* ctx, double courant, double* dt_out);
+
+/* Time step in seconds (> 0, finite). Requires material. */
+int sem_set_dt(sem_ctx* ctx, double dt);
+
+/* Nearest global GLL node to each of npts points xyz[npts][3] (ties: lowest index).
+ * With surface_z non-NULL only nodes whose z is within 1e-9 * max(1, |*surface_z|) of
+ * *surface_z are candidates. Requires sem_set_mesh. Host computation. */
+int sem_locate_nodes(sem_ctx* ctx, int npts, const double* xyz, const double* surface_z,
+                     int32_t* node_out);
+
+/* Point forces (Sec. V-C): at step n, accel_raw[node[s]] += force[s][0..2] * R(t_{n+1} - t0)
+ * with the Ricker wavelet R(tau) = (1 - 2 a) exp(-a), a = (pi f0 tau)^2, evaluated in
+ * float64. nsrc may be 0. */
+int sem_set_sources(sem_ctx* ctx, int nsrc, const int32_t* node, const double* force,
+                    double f0, double t0);
+
+/* Receivers: the displacement at node[r] is recorded after every step of sem_run /
+ * sem_run_dev. nrec may be 0. */
+int sem_set_receivers(sem_ctx* ctx, int nrec, const int32_t* node);
+
+/* Set (u, v, a) at t = 0 from host arrays [nglob][3] (NULL = zero) and reset the step
+ * counter. Requires sem_set_mesh. Synchronous. */
+int sem_set_state(sem_ctx* ctx, const float* u, const float* v, const float* a);
+/* Same from device arrays (NULL = zero). Asynchronous on the context's stream. */
+int sem_set_state_dev(sem_ctx* ctx, const float* u_dev, const float* v_dev, const float* a_dev);
+
+/* Copy the current state (u^n, v^n, a^n) to host arrays [nglob][3] (NULL = skip).
+ * Synchronous. */
+int sem_get_state(sem_ctx* ctx, float* u, float* v, float* a);
+/* Same into device arrays. Asynchronous on the context's stream. */
+int sem_get_state_dev(sem_ctx* ctx, float* u_dev, float* v_dev, float* a_dev);
+
+/* Advance nsteps >= 0 time steps without recording. Asynchronous on the stream. */
+int sem_step(sem_ctx* ctx, int nsteps);
+
+/* Advance nsteps time steps and record seismograms into host seis[nrec][3][nsteps]
+ * (may be NULL). Synchronous. */
+int sem_run(sem_ctx* ctx, int nsteps, float* seis);
+/* Same, recording into a device buffer seis_dev[nrec][3][nsteps] (may be NULL).
+ * Asynchronous on the context's stream. */
+int sem_run_dev(sem_ctx* ctx, int nsteps, float* seis_dev);
+
+/* One matrix-free stiffness application on the device: f_dev = -K u_dev, both
+ * [nglob][3] float32 (Sec. II-B). Every node of f_dev is written. u_dev and f_dev must not
+ * overlap. Asynchronous on the context's stream. Does not touch the solver state. */
+int sem_apply_stiffness(sem_ctx* ctx, const float* u_dev, float* f_dev);
+
+/* Kinetic and potential energy of the current state in float64:
+ * out[0] = 1/2 sum_I M_I |v_I|^2, out[1] = 1/2 u^T K u. Synchronous. */
+int sem_energy(sem_ctx* ctx, double* out);
+
+/* Wait for all work issued on the context's stream. */
+int sem_sync(sem_ctx* ctx);
+
+/* Sizes of the set-up problem: out[0] nspec, out[1] nglob, out[2] ngll, out[3] ncolors,
+ * out[4] steps taken since sem_set_state, out[5] bytes of device memory held.
+ * Any entry not yet defined is 0. */
+int sem_info(sem_ctx* ctx, int64_t* out);
+
+/* Element count of each colour, counts[ncolors] (see sem_info for ncolors). */
+int sem_color_counts(sem_ctx* ctx, int32_t* counts);
+
+/* Message of the last failed call on ctx, or of the last failed context-free call when
+ * ctx is NULL. Owned by the library; valid until the next call on the same ctx. */
+const char* sem_last_error(const sem_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

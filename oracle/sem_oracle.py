@@ -302,11 +302,13 @@ class Model:
 
     def nearest_nodes(self, points, surface_z: float | None = None) -> np.ndarray:
         """Index of the global node nearest to each point (ties: lowest index). With
-        ``surface_z`` only nodes with z == surface_z are candidates."""
+        ``surface_z`` only nodes whose z lies within 1e-9 * max(1, |surface_z|) of it are
+        candidates (nodes on a flat face, up to the rounding of their positions)."""
         pts = np.atleast_2d(np.asarray(points, dtype=np.float64))
         cand = np.arange(self.nglob)
         if surface_z is not None:
-            cand = cand[self.node_xyz[:, 2] == surface_z]
+            tol = 1e-9 * max(1.0, abs(surface_z))
+            cand = cand[np.abs(self.node_xyz[:, 2] - surface_z) <= tol]
         out = np.empty(len(pts), dtype=np.int64)
         for r, p in enumerate(pts):
             d2 = np.sum((self.node_xyz[cand] - p) ** 2, axis=1)

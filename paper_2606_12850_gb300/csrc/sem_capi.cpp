@@ -1,0 +1,737 @@
+// C ABI of libsemgb (declared in include/sem.h): context, set-up, device buffers, the
+// time-step sequence and its CUDA-graph capture.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sem.h"
+#include "sem_internal.h"
+
+using namespace semgb;
+
+namespace {
+
+constexpr int kStepsPerGraph = 10;
+thread_local std::string g_err;  // message of the last failed context-free call
+
+}  // namespace
+
+struct sem_ctx {
+  int ngll = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  std::vector<double> xi, w, hprime;
+
+  // mesh (host)
+  bool have_mesh = false, have_mat = false, have_dt = false;
+  int nspec = 0, nglob = 0, nglob_pad = 0, ncolors = 0;
+  std::vector<int32_t> ibool;       // caller order
+  std::vector<int> order;           // colour-sorted position -> caller element
+  std::vector<int> pos_of;          // caller element -> colour-sorted position
+  std::vector<int> color_off;       // ncolors + 1
+  std::vector<float> rec;           // colour-sorted element records (host copy)
+  std::vector<double> jac;          // caller order, per local point (for the mass)
+  std::vector<double> dxmin;        // per caller element
+  std::vector<double> node_xyz;     // [nglob][3]
+  std::vector<double> vpmax;        // per caller element
+  double dt = 0.0;
+
+  // device
+  float* d_rec = nullptr;
+  float *d_u = nullptr, *d_v = nullptr, *d_a = nullptr, *d_minv = nullptr;
+  float* d_f = nullptr;           // scratch force buffer for sem_energy
+  double* d_partials = nullptr;   // scratch partial sums for sem_energy
+  DevCtl* d_ctl = nullptr;
+  int* d_src_node = nullptr;
+  double* d_src_force = nullptr;
+  int nsrc = 0;
+  double f0 = 0.0, t0 = 0.0;
+  int* d_rec_node = nullptr;
+  int nrec = 0;
+  size_t dev_bytes = 0;
+
+  // time stepping
+  bool pending = false;  // a_raw holds forces and v the half-step velocity
+  long long steps = 0;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
+};
+
+namespace {
+
+int fail(sem_ctx* c, int code, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_err = msg;
+  return code;
+}
+
+int cuda_fail(sem_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, SEM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SEM_CUDA(c, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
+  } while (0)
+
+#define SEM_LAUNCH(c, call)                                                                    \
+  do {                                                                                         \
+    int r_ = (call);                                                                           \
+    if (r_ != 0) return cuda_fail((c), static_cast<cudaError_t>(r_), #call);                   \
+  } while (0)
+
+template <typename T>
+int dev_alloc(sem_ctx* c, T** p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (count == 0) return SEM_OK;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return fail(c, SEM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  *p = static_cast<T*>(q);
+  c->dev_bytes += count * sizeof(T);
+  return SEM_OK;
+}
+
+void free_device(sem_ctx* c) {
+  void* ptrs[] = {c->d_rec, c->d_u, c->d_v, c->d_a, c->d_minv, c->d_f, c->d_partials,
+                  c->d_ctl, c->d_src_node, c->d_src_force, c->d_rec_node};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  c->d_rec = nullptr;
+  c->d_u = c->d_v = c->d_a = c->d_minv = c->d_f = nullptr;
+  c->d_partials = nullptr;
+  c->d_ctl = nullptr;
+  c->d_src_node = nullptr;
+  c->d_src_force = nullptr;
+  c->d_rec_node = nullptr;
+  c->dev_bytes = 0;
+}
+
+void drop_graph(sem_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_valid = false;
+}
+
+DevProblem problem(const sem_ctx* c) {
+  DevProblem p{};
+  p.ngll = c->ngll;
+  p.nspec = c->nspec;
+  p.nglob = c->nglob;
+  p.nglob_pad = c->nglob_pad;
+  p.rec = c->d_rec;
+  p.u = c->d_u;
+  p.v = c->d_v;
+  p.a = c->d_a;
+  p.minv = c->d_minv;
+  p.ctl = c->d_ctl;
+  p.nsrc = c->nsrc;
+  p.src_node = c->d_src_node;
+  p.src_force = c->d_src_force;
+  p.f0 = c->f0;
+  p.t0 = c->t0;
+  p.nrec = c->nrec;
+  p.rec_node = c->d_rec_node;
+  p.dt = c->dt;
+  return p;
+}
+
+int set_device(sem_ctx* c) {
+  SEM_CUDA(c, cudaSetDevice(c->device));
+  return SEM_OK;
+}
+
+// f = -K u over all colours in order (Sec. IV-C: colour by colour, no atomics).
+int forces_all_colors(sem_ctx* c, const float* u, float* f) {
+  for (int col = 0; col < c->ncolors; ++col)
+    SEM_LAUNCH(c, launch_forces(c->ngll, c->d_rec, u, f, c->color_off[col], c->color_off[col + 1], c->stream));
+  return SEM_OK;
+}
+
+// One time step in the "pending" representation: corrector(n-1)+predictor(n), forces,
+// sources and records.
+int enqueue_pending_step(sem_ctx* c) {
+  const DevProblem p = problem(c);
+  SEM_LAUNCH(c, launch_fused_newmark(p, c->stream));
+  int r = forces_all_colors(c, c->d_u, c->d_a);
+  if (r) return r;
+  SEM_LAUNCH(c, launch_sources_record(p, c->stream));
+  return SEM_OK;
+}
+
+int enqueue_first_step(sem_ctx* c) {
+  const DevProblem p = problem(c);
+  SEM_LAUNCH(c, launch_predictor(p, c->stream));
+  int r = forces_all_colors(c, c->d_u, c->d_a);
+  if (r) return r;
+  SEM_LAUNCH(c, launch_sources_record(p, c->stream));
+  return SEM_OK;
+}
+
+int build_graph(sem_ctx* c) {
+  drop_graph(c);
+  cudaGraph_t g = nullptr;
+  SEM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int r = SEM_OK;
+  for (int s = 0; s < kStepsPerGraph && r == SEM_OK; ++s) r = enqueue_pending_step(c);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (r != SEM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  c->graph_valid = true;
+  return SEM_OK;
+}
+
+int check_ready(sem_ctx* c) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (!c->have_mat) return fail(c, SEM_ESTATE, "sem_set_material has not been called");
+  if (!c->have_dt) return fail(c, SEM_ESTATE, "sem_set_dt has not been called");
+  return SEM_OK;
+}
+
+int advance(sem_ctx* c, int nsteps, float* seis_dev) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (nsteps < 0) return fail(c, SEM_EINVAL, "nsteps must be >= 0");
+  if ((r = set_device(c))) return r;
+  SEM_LAUNCH(c, launch_set_ctl(c->d_ctl, c->steps, seis_dev ? nsteps : 0, seis_dev, c->stream));
+  int left = nsteps;
+  if (left > 0 && !c->pending) {
+    if ((r = enqueue_first_step(c))) return r;
+    c->pending = true;
+    --left;
+  }
+  if (left >= kStepsPerGraph && !c->graph_valid)
+    if ((r = build_graph(c))) return r;
+  while (left >= kStepsPerGraph) {
+    SEM_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+    left -= kStepsPerGraph;
+  }
+  while (left > 0) {
+    if ((r = enqueue_pending_step(c))) return r;
+    --left;
+  }
+  c->steps += nsteps;
+  return SEM_OK;
+}
+
+// Completes a pending state: a = M^-1 a_raw, v = v_half + dt/2 a.
+int finish_state(sem_ctx* c) {
+  if (!c->pending) return SEM_OK;
+  SEM_LAUNCH(c, launch_corrector(problem(c), c->stream));
+  c->pending = false;
+  return SEM_OK;
+}
+
+bool finite_all(const float* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sem_version(void) { return 100; }
+
+int sem_gll(int ngll, double* xi, double* w, double* hprime) {
+  std::string err;
+  if (gll_basis(ngll, xi, w, hprime, &err)) return fail(nullptr, SEM_EINVAL, err);
+  return SEM_OK;
+}
+
+int sem_color_elements(int nspec, int ngll, int nglob, const int32_t* ibool, int32_t* color, int* ncolors) {
+  if (nspec < 1 || nglob < 1 || !ibool || !color || !ncolors || ngll < kMinNgll || ngll > kMaxNgll)
+    return fail(nullptr, SEM_EINVAL, "sem_color_elements: bad arguments");
+  const size_t nloc = static_cast<size_t>(nspec) * ngll * ngll * ngll;
+  for (size_t q = 0; q < nloc; ++q)
+    if (ibool[q] < 0 || ibool[q] >= nglob) return fail(nullptr, SEM_EINVAL, "ibool entry out of range");
+  std::vector<int32_t> col;
+  std::string err;
+  if (color_elements(nspec, ngll, nglob, ibool, &col, ncolors, &err)) return fail(nullptr, SEM_EINVAL, err);
+  std::memcpy(color, col.data(), sizeof(int32_t) * nspec);
+  return SEM_OK;
+}
+
+int sem_create(sem_ctx** out, int ngll, int device, void* cuda_stream) {
+  if (!out) return fail(nullptr, SEM_EINVAL, "sem_create: out is NULL");
+  *out = nullptr;
+  if (ngll < kMinNgll || ngll > kMaxNgll) return fail(nullptr, SEM_EINVAL, "ngll must be in [2, 10]");
+  sem_ctx* c = new (std::nothrow) sem_ctx();
+  if (!c) return fail(nullptr, SEM_ENOMEM, "out of host memory");
+  c->ngll = ngll;
+  c->device = device;
+  c->xi.resize(ngll);
+  c->w.resize(ngll);
+  c->hprime.resize(ngll * ngll);
+  std::string err;
+  gll_basis(ngll, c->xi.data(), c->w.data(), c->hprime.data(), &err);
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      c->own_stream = (e == cudaSuccess);
+    }
+  }
+  if (e == cudaSuccess) {
+    int r = upload_basis(ngll, c->w.data(), c->hprime.data(), c->stream);
+    if (r) e = static_cast<cudaError_t>(r);
+  }
+  if (e == cudaSuccess) {
+    void* q = nullptr;
+    e = cudaMalloc(&q, sizeof(DevCtl));
+    c->d_ctl = static_cast<DevCtl*>(q);
+    if (e == cudaSuccess) e = cudaMemset(c->d_ctl, 0, sizeof(DevCtl));
+  }
+  if (e != cudaSuccess) {
+    g_err = std::string("sem_create: ") + cudaGetErrorString(e);
+    sem_destroy(c);
+    return SEM_ECUDA;
+  }
+  *out = c;
+  return SEM_OK;
+}
+
+int sem_destroy(sem_ctx* c) {
+  if (!c) return SEM_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  free_device(c);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return SEM_OK;
+}
+
+int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const double* ctrl) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (nspec < 1 || nglob < 1 || !ibool || !ctrl) return fail(c, SEM_EINVAL, "sem_set_mesh: bad arguments");
+  const int n = c->ngll, np = n * n * n;
+  const size_t nloc = static_cast<size_t>(nspec) * np;
+  if (nloc > (1ull << 31) - 1 || nglob > (1 << 30)) return fail(c, SEM_EINVAL, "mesh too large for int32 indexing");
+  std::vector<char> seen(nglob, 0);
+  for (size_t q = 0; q < nloc; ++q) {
+    if (ibool[q] < 0 || ibool[q] >= nglob)
+      return fail(c, SEM_EINVAL, "ibool entry " + std::to_string(q) + " out of range");
+    seen[ibool[q]] = 1;
+  }
+  for (int g = 0; g < nglob; ++g)
+    if (!seen[g]) return fail(c, SEM_EINVAL, "global node " + std::to_string(g) + " is not referenced by ibool");
+  for (size_t q = 0; q < static_cast<size_t>(nspec) * 24; ++q)
+    if (!std::isfinite(ctrl[q])) return fail(c, SEM_EINVAL, "non-finite corner coordinate");
+
+  std::vector<int32_t> color;
+  int ncolors = 0;
+  std::string err;
+  if (color_elements(nspec, n, nglob, ibool, &color, &ncolors, &err)) return fail(c, SEM_EINVAL, err);
+
+  // geometry per element (caller order)
+  std::vector<double> xyz(3 * np), G(9 * np), J(np);
+  c->jac.assign(nloc, 0.0);
+  c->dxmin.assign(nspec, 0.0);
+  c->node_xyz.assign(3 * static_cast<size_t>(nglob), 0.0);
+  std::vector<float> geom(static_cast<size_t>(nspec) * 10 * np);  // [e][10][p] in caller p order
+  for (int e = 0; e < nspec; ++e) {
+    if (!element_geometry(n, c->xi.data(), c->hprime.data(), ctrl + 24 * static_cast<size_t>(e), xyz.data(),
+                          G.data(), J.data()))
+      return fail(c, SEM_EINVAL, "element " + std::to_string(e) + " has a Jacobian determinant <= 0");
+    double dmin = 1e300;
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          const int p = i + n * (j + n * k);
+          const int nb[3] = {i + 1 < n ? p + 1 : -1, j + 1 < n ? p + n : -1, k + 1 < n ? p + n * n : -1};
+          for (int d = 0; d < 3; ++d) {
+            if (nb[d] < 0) continue;
+            const double dx = xyz[3 * nb[d]] - xyz[3 * p], dy = xyz[3 * nb[d] + 1] - xyz[3 * p + 1],
+                         dz = xyz[3 * nb[d] + 2] - xyz[3 * p + 2];
+            dmin = std::min(dmin, std::sqrt(dx * dx + dy * dy + dz * dz));
+          }
+        }
+    c->dxmin[e] = dmin;
+    for (int p = 0; p < np; ++p) {
+      const size_t q = static_cast<size_t>(e) * np + p;
+      c->jac[q] = J[p];
+      for (int d = 0; d < 3; ++d) c->node_xyz[3 * static_cast<size_t>(ibool[q]) + d] = xyz[3 * p + d];
+      float* gq = geom.data() + static_cast<size_t>(e) * 10 * np;
+      for (int a = 0; a < 9; ++a) gq[a * np + p] = static_cast<float>(G[9 * p + a]);
+      gq[9 * np + p] = static_cast<float>(J[p]);
+    }
+  }
+
+  // colour-sorted element order (stable within a colour)
+  c->color_off.assign(ncolors + 1, 0);
+  for (int e = 0; e < nspec; ++e) c->color_off[color[e] + 1]++;
+  for (int k = 0; k < ncolors; ++k) c->color_off[k + 1] += c->color_off[k];
+  c->order.assign(nspec, 0);
+  c->pos_of.assign(nspec, 0);
+  {
+    std::vector<int> fillp(c->color_off.begin(), c->color_off.end() - 1);
+    for (int e = 0; e < nspec; ++e) {
+      const int s = fillp[color[e]]++;
+      c->order[s] = e;
+      c->pos_of[e] = s;
+    }
+  }
+
+  // element records, colour-sorted, with the first-touch flag on ibool
+  const int RW = rec_words(n);
+  c->rec.assign(static_cast<size_t>(nspec) * RW, 0.f);
+  std::vector<char> touched(nglob, 0);
+  for (int s = 0; s < nspec; ++s) {
+    const int e = c->order[s];
+    float* r = c->rec.data() + static_cast<size_t>(s) * RW;
+    const float* gq = geom.data() + static_cast<size_t>(e) * 10 * np;
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          const int p = i + n * (j + n * k);
+          const int q = rec_pos(n, i, j, k);
+          uint32_t g = static_cast<uint32_t>(ibool[static_cast<size_t>(e) * np + p]);
+          if (!touched[g]) {
+            touched[g] = 1;
+            g |= kFirstTouchBit;
+          }
+          std::memcpy(&r[kIbool * np + q], &g, sizeof(uint32_t));
+          for (int a = 0; a < 10; ++a) r[(kG + a) * np + q] = gq[a * np + p];
+        }
+  }
+
+  c->ibool.assign(ibool, ibool + nloc);
+  c->nspec = nspec;
+  c->nglob = nglob;
+  c->nglob_pad = (nglob + 3) / 4 * 4;
+  c->ncolors = ncolors;
+  c->have_mesh = true;
+  c->have_mat = false;
+  c->have_dt = false;
+  c->pending = false;
+  c->steps = 0;
+  drop_graph(c);
+
+  int r = set_device(c);
+  if (r) return r;
+  cudaStreamSynchronize(c->stream);
+  DevCtl* keep_ctl = c->d_ctl;
+  c->d_ctl = nullptr;
+  free_device(c);
+  c->d_ctl = keep_ctl;
+  c->dev_bytes = sizeof(DevCtl);
+  const size_t nf = 3 * static_cast<size_t>(c->nglob_pad);
+  if ((r = dev_alloc(c, &c->d_rec, c->rec.size())) || (r = dev_alloc(c, &c->d_u, nf)) ||
+      (r = dev_alloc(c, &c->d_v, nf)) || (r = dev_alloc(c, &c->d_a, nf)) ||
+      (r = dev_alloc(c, &c->d_minv, static_cast<size_t>(c->nglob_pad))))
+    return r;
+  SEM_CUDA(c, cudaMemsetAsync(c->d_u, 0, nf * sizeof(float), c->stream));
+  SEM_CUDA(c, cudaMemsetAsync(c->d_v, 0, nf * sizeof(float), c->stream));
+  SEM_CUDA(c, cudaMemsetAsync(c->d_a, 0, nf * sizeof(float), c->stream));
+  SEM_CUDA(c, cudaMemsetAsync(c->d_minv, 0, c->nglob_pad * sizeof(float), c->stream));
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->nsrc = 0;
+  c->nrec = 0;
+  return SEM_OK;
+}
+
+int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float* vs) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (!rho || !vp || !vs) return fail(c, SEM_EINVAL, "sem_set_material: NULL array");
+  const int n = c->ngll, np = n * n * n, RW = rec_words(n);
+  const size_t nloc = static_cast<size_t>(c->nspec) * np;
+  for (size_t q = 0; q < nloc; ++q) {
+    if (!std::isfinite(rho[q]) || !std::isfinite(vp[q]) || !std::isfinite(vs[q]))
+      return fail(c, SEM_EINVAL, "non-finite material value");
+    if (!(rho[q] > 0.f) || vs[q] < 0.f || !(vp[q] > vs[q]))
+      return fail(c, SEM_EINVAL, "material needs rho > 0, vs >= 0, vp > vs (local point " + std::to_string(q) + ")");
+  }
+  std::vector<double> mass(c->nglob, 0.0);
+  c->vpmax.assign(c->nspec, 0.0);
+  for (int e = 0; e < c->nspec; ++e) {
+    float* r = c->rec.data() + static_cast<size_t>(c->pos_of[e]) * RW;
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          const int p = i + n * (j + n * k);
+          const size_t q = static_cast<size_t>(e) * np + p;
+          const double rh = rho[q], a = vp[q], b = vs[q];
+          const double mu = rh * b * b;
+          const double lam = rh * (a * a - 2.0 * b * b);
+          const double kappa = lam + 2.0 * mu / 3.0;
+          const int qq = rec_pos(n, i, j, k);
+          r[kKappa * np + qq] = static_cast<float>(kappa);
+          r[kMu * np + qq] = static_cast<float>(mu);
+          mass[c->ibool[q]] += rh * c->jac[q] * c->w[i] * c->w[j] * c->w[k];
+          c->vpmax[e] = std::max(c->vpmax[e], a);
+        }
+  }
+  std::vector<float> minv(c->nglob_pad, 0.f);
+  for (int g = 0; g < c->nglob; ++g) minv[g] = static_cast<float>(1.0 / mass[g]);
+  int r = set_device(c);
+  if (r) return r;
+  SEM_CUDA(c, cudaMemcpyAsync(c->d_rec, c->rec.data(), c->rec.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  SEM_CUDA(c, cudaMemcpyAsync(c->d_minv, minv.data(), minv.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->have_mat = true;
+  drop_graph(c);
+  return SEM_OK;
+}
+
+int sem_suggest_dt(sem_ctx* c, double courant, double* dt_out) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mat) return fail(c, SEM_ESTATE, "sem_set_material has not been called");
+  if (!dt_out || !(courant > 0.0)) return fail(c, SEM_EINVAL, "sem_suggest_dt: bad arguments");
+  double best = 1e300;
+  for (int e = 0; e < c->nspec; ++e) best = std::min(best, c->dxmin[e] / c->vpmax[e]);
+  *dt_out = courant * best;
+  return SEM_OK;
+}
+
+int sem_set_dt(sem_ctx* c, double dt) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mat) return fail(c, SEM_ESTATE, "sem_set_material has not been called");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SEM_EINVAL, "dt must be positive and finite");
+  if (c->pending) {  // complete the state with the old dt before switching
+    int r = set_device(c);
+    if (r || (r = finish_state(c))) return r;
+  }
+  c->dt = dt;
+  c->have_dt = true;
+  drop_graph(c);
+  return SEM_OK;
+}
+
+int sem_locate_nodes(sem_ctx* c, int npts, const double* xyz, const double* surface_z, int32_t* node_out) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (npts < 0 || (npts > 0 && (!xyz || !node_out))) return fail(c, SEM_EINVAL, "sem_locate_nodes: bad arguments");
+  if (locate_nodes(c->nglob, c->node_xyz.data(), npts, xyz, surface_z, node_out))
+    return fail(c, SEM_EINVAL, "no node lies on the requested surface");
+  return SEM_OK;
+}
+
+int sem_set_sources(sem_ctx* c, int nsrc, const int32_t* node, const double* force, double f0, double t0) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (nsrc < 0 || (nsrc > 0 && (!node || !force)) || !std::isfinite(f0) || !std::isfinite(t0))
+    return fail(c, SEM_EINVAL, "sem_set_sources: bad arguments");
+  // merge sources that share a node (same time function, forces add)
+  std::vector<int> nodes;
+  std::vector<double> forces;
+  for (int s = 0; s < nsrc; ++s) {
+    if (node[s] < 0 || node[s] >= c->nglob) return fail(c, SEM_EINVAL, "source node out of range");
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(force[3 * s + d])) return fail(c, SEM_EINVAL, "non-finite source force");
+    auto it = std::find(nodes.begin(), nodes.end(), node[s]);
+    if (it == nodes.end()) {
+      nodes.push_back(node[s]);
+      forces.insert(forces.end(), force + 3 * s, force + 3 * s + 3);
+    } else {
+      const size_t m = it - nodes.begin();
+      for (int d = 0; d < 3; ++d) forces[3 * m + d] += force[3 * s + d];
+    }
+  }
+  int r = set_device(c);
+  if (r) return r;
+  cudaStreamSynchronize(c->stream);
+  c->dev_bytes -= c->nsrc * (sizeof(int) + 3 * sizeof(double));
+  c->nsrc = static_cast<int>(nodes.size());
+  if ((r = dev_alloc(c, &c->d_src_node, nodes.size())) || (r = dev_alloc(c, &c->d_src_force, forces.size())))
+    return r;
+  if (!nodes.empty()) {
+    SEM_CUDA(c, cudaMemcpy(c->d_src_node, nodes.data(), nodes.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA(c, cudaMemcpy(c->d_src_force, forces.data(), forces.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  c->f0 = f0;
+  c->t0 = t0;
+  drop_graph(c);
+  return SEM_OK;
+}
+
+int sem_set_receivers(sem_ctx* c, int nrec, const int32_t* node) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (nrec < 0 || (nrec > 0 && !node)) return fail(c, SEM_EINVAL, "sem_set_receivers: bad arguments");
+  for (int r = 0; r < nrec; ++r)
+    if (node[r] < 0 || node[r] >= c->nglob) return fail(c, SEM_EINVAL, "receiver node out of range");
+  int r = set_device(c);
+  if (r) return r;
+  cudaStreamSynchronize(c->stream);
+  c->dev_bytes -= c->nrec * sizeof(int);
+  c->nrec = nrec;
+  if ((r = dev_alloc(c, &c->d_rec_node, static_cast<size_t>(nrec)))) return r;
+  if (nrec > 0) SEM_CUDA(c, cudaMemcpy(c->d_rec_node, node, nrec * sizeof(int), cudaMemcpyHostToDevice));
+  drop_graph(c);
+  return SEM_OK;
+}
+
+static int set_state_impl(sem_ctx* c, const float* u, const float* v, const float* a, cudaMemcpyKind kind) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  int r = set_device(c);
+  if (r) return r;
+  const size_t n3 = 3 * static_cast<size_t>(c->nglob);
+  if (kind == cudaMemcpyHostToDevice) {
+    if ((u && !finite_all(u, n3)) || (v && !finite_all(v, n3)) || (a && !finite_all(a, n3)))
+      return fail(c, SEM_EINVAL, "non-finite state value");
+  }
+  const float* src[3] = {u, v, a};
+  float* dst[3] = {c->d_u, c->d_v, c->d_a};
+  for (int q = 0; q < 3; ++q) {
+    SEM_CUDA(c, cudaMemsetAsync(dst[q], 0, 3 * static_cast<size_t>(c->nglob_pad) * sizeof(float), c->stream));
+    if (src[q]) SEM_CUDA(c, cudaMemcpyAsync(dst[q], src[q], n3 * sizeof(float), kind, c->stream));
+  }
+  if (kind == cudaMemcpyHostToDevice) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->pending = false;
+  c->steps = 0;
+  return SEM_OK;
+}
+
+int sem_set_state(sem_ctx* c, const float* u, const float* v, const float* a) {
+  return set_state_impl(c, u, v, a, cudaMemcpyHostToDevice);
+}
+
+int sem_set_state_dev(sem_ctx* c, const float* u, const float* v, const float* a) {
+  return set_state_impl(c, u, v, a, cudaMemcpyDeviceToDevice);
+}
+
+static int get_state_impl(sem_ctx* c, float* u, float* v, float* a, cudaMemcpyKind kind) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  int r = set_device(c);
+  if (r || (r = finish_state(c))) return r;
+  const size_t n3 = 3 * static_cast<size_t>(c->nglob);
+  float* dst[3] = {u, v, a};
+  const float* src[3] = {c->d_u, c->d_v, c->d_a};
+  for (int q = 0; q < 3; ++q)
+    if (dst[q]) SEM_CUDA(c, cudaMemcpyAsync(dst[q], src[q], n3 * sizeof(float), kind, c->stream));
+  if (kind == cudaMemcpyDeviceToHost) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SEM_OK;
+}
+
+int sem_get_state(sem_ctx* c, float* u, float* v, float* a) { return get_state_impl(c, u, v, a, cudaMemcpyDeviceToHost); }
+
+int sem_get_state_dev(sem_ctx* c, float* u, float* v, float* a) {
+  return get_state_impl(c, u, v, a, cudaMemcpyDeviceToDevice);
+}
+
+int sem_step(sem_ctx* c, int nsteps) { return advance(c, nsteps, nullptr); }
+
+int sem_run_dev(sem_ctx* c, int nsteps, float* seis_dev) { return advance(c, nsteps, seis_dev); }
+
+int sem_run(sem_ctx* c, int nsteps, float* seis) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (nsteps < 0) return fail(c, SEM_EINVAL, "nsteps must be >= 0");
+  if ((r = set_device(c))) return r;
+  float* d_seis = nullptr;
+  const size_t count = static_cast<size_t>(c->nrec) * 3 * nsteps;
+  if (seis && count) {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_seis), count * sizeof(float), c->stream);
+    if (e != cudaSuccess) return fail(c, SEM_ENOMEM, std::string("seismogram buffer: ") + cudaGetErrorString(e));
+  }
+  r = advance(c, nsteps, d_seis);
+  if (r == SEM_OK && d_seis) {
+    cudaError_t e = cudaMemcpyAsync(seis, d_seis, count * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) r = cuda_fail(c, e, "seismogram copy");
+  }
+  if (d_seis) cudaFreeAsync(d_seis, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (r == SEM_OK && e != cudaSuccess) r = cuda_fail(c, e, "sem_run");
+  return r;
+}
+
+int sem_apply_stiffness(sem_ctx* c, const float* u_dev, float* f_dev) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mat) return fail(c, SEM_ESTATE, "sem_set_material has not been called");
+  if (!u_dev || !f_dev) return fail(c, SEM_EINVAL, "sem_apply_stiffness: NULL pointer");
+  const size_t bytes = 3 * static_cast<size_t>(c->nglob) * sizeof(float);
+  const char* a = reinterpret_cast<const char*>(u_dev);
+  const char* b = reinterpret_cast<const char*>(f_dev);
+  if (a < b + bytes && b < a + bytes) return fail(c, SEM_EINVAL, "u_dev and f_dev overlap");
+  int r = set_device(c);
+  if (r) return r;
+  return forces_all_colors(c, u_dev, f_dev);
+}
+
+int sem_energy(sem_ctx* c, double* out) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mat) return fail(c, SEM_ESTATE, "sem_set_material has not been called");
+  if (!out) return fail(c, SEM_EINVAL, "sem_energy: NULL output");
+  int r = set_device(c);
+  if (r || (r = finish_state(c))) return r;
+  const size_t nf = 3 * static_cast<size_t>(c->nglob_pad);
+  if (!c->d_f) {
+    if ((r = dev_alloc(c, &c->d_f, nf)) || (r = dev_alloc(c, &c->d_partials, 2 * static_cast<size_t>(kEnergyBlocks))))
+      return r;
+    SEM_CUDA(c, cudaMemsetAsync(c->d_f, 0, nf * sizeof(float), c->stream));
+  }
+  if ((r = forces_all_colors(c, c->d_u, c->d_f))) return r;
+  SEM_LAUNCH(c, launch_energy_partials(c->d_u, c->d_v, c->d_f, c->d_minv, c->nglob_pad, c->d_partials, kEnergyBlocks,
+                                       c->stream));
+  std::vector<double> part(2 * kEnergyBlocks);
+  SEM_CUDA(c, cudaMemcpyAsync(part.data(), c->d_partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  double kin = 0.0, pot = 0.0;
+  for (int b = 0; b < kEnergyBlocks; ++b) {
+    kin += part[2 * b];
+    pot += part[2 * b + 1];
+  }
+  out[0] = 0.5 * kin;
+  out[1] = -0.5 * pot;  // f = -K u
+  return SEM_OK;
+}
+
+int sem_sync(sem_ctx* c) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  int r = set_device(c);
+  if (r) return r;
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SEM_OK;
+}
+
+int sem_info(sem_ctx* c, int64_t* out) {
+  if (!c || !out) return fail(c, SEM_EINVAL, "sem_info: bad arguments");
+  out[0] = c->nspec;
+  out[1] = c->nglob;
+  out[2] = c->ngll;
+  out[3] = c->ncolors;
+  out[4] = c->steps;
+  out[5] = static_cast<int64_t>(c->dev_bytes);
+  return SEM_OK;
+}
+
+int sem_color_counts(sem_ctx* c, int32_t* counts) {
+  if (!c || !counts) return fail(c, SEM_EINVAL, "sem_color_counts: bad arguments");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  for (int k = 0; k < c->ncolors; ++k) counts[k] = c->color_off[k + 1] - c->color_off[k];
+  return SEM_OK;
+}
+
+const char* sem_last_error(const sem_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// Internal declarations shared by the host set-up (sem_setup.cpp), the C ABI
+// (sem_capi.cpp) and the CUDA kernels (sem_kernels.cu) of libsemgb.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace semgb {
+
+constexpr int kMaxNgll = 10;
+constexpr int kMinNgll = 2;
+
+// Words per local point in the element record: ibool, nine inverse-Jacobian terms
+// dxi_r/dx_d (r-major: xix xiy xiz etax etay etaz gammax gammay gammaz), J, kappa, mu.
+constexpr int kRecFields = 13;
+enum RecField { kIbool = 0, kG = 1, kJac = 10, kKappa = 11, kMu = 12 };
+
+// Bit 31 of a record's ibool word marks the first contribution to that node in the
+// colour-by-colour processing order: the force kernel stores instead of adding there,
+// so the assembled array needs no zeroing pass.
+constexpr uint32_t kFirstTouchBit = 0x80000000u;
+
+inline int rec_words(int ngll) {
+  const int np = ngll * ngll * ngll;
+  return (kRecFields * np + 3) / 4 * 4;  // 16-byte aligned element records
+}
+
+// Position of local point (i, j, k) inside one field of an element record: points are
+// stored i-major so that the NGLL^2 threads owning the xi-lines (j, k) of an element read
+// consecutive words for a fixed i.
+inline int rec_pos(int ngll, int i, int j, int k) { return i * ngll * ngll + j + ngll * k; }
+
+// ---- host set-up (sem_setup.cpp) -------------------------------------------------------
+int gll_basis(int ngll, double* xi, double* w, double* hprime, std::string* err);
+
+// Positions, inverse Jacobian and determinant at every GLL point of one trilinear element;
+// xyz[np][3], G[np][9] (dxi_r/dx_d at 3r+d), J[np]; returns false if some J <= 0.
+bool element_geometry(int ngll, const double* xi, const double* hprime, const double* ctrl,
+                      double* xyz, double* G, double* J);
+
+int color_elements(int nspec, int ngll, int nglob, const int32_t* ibool,
+                   std::vector<int32_t>* color, int* ncolors, std::string* err);
+
+int locate_nodes(int nglob, const double* node_xyz, int npts, const double* xyz,
+                 const double* surface_z, int32_t* out);
+
+// ---- device side (sem_kernels.cu) ------------------------------------------------------
+struct DevCtl {
+  long long step;  // steps taken since the state was set
+  int col;         // next seismogram column
+  int ncols;       // columns in the seismogram buffer (0: no recording)
+  float* seis;     // [nrec][3][ncols] or null
+  int err;
+  int pad;
+};
+
+struct DevProblem {
+  int ngll;
+  int nspec;
+  int nglob;
+  int nglob_pad;  // multiple of 4
+  const float* rec;
+  float* u;
+  float* v;
+  float* a;
+  const float* minv;
+  DevCtl* ctl;
+  int nsrc;
+  const int* src_node;
+  const double* src_force;
+  double f0, t0;
+  int nrec;
+  const int* rec_node;
+  double dt;
+};
+
+// Copies hprime, hprime*w and w for this ngll into the kernels' constant banks.
+int upload_basis(int ngll, const double* w, const double* hprime, void* stream);
+
+// One colour's worth of elements [e0, e1) of the colour-sorted order: f (=|+=) -K u.
+int launch_forces(int ngll, const float* rec, const float* u, float* f, int e0, int e1, void* stream);
+int forces_kernel_smem_bytes(int ngll);
+int forces_elements_per_cta(int ngll);
+
+int launch_set_ctl(DevCtl* ctl, long long step, int ncols, float* seis, void* stream);
+int launch_predictor(const DevProblem& p, void* stream);
+int launch_fused_newmark(const DevProblem& p, void* stream);
+int launch_corrector(const DevProblem& p, void* stream);
+int launch_sources_record(const DevProblem& p, void* stream);
+int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv,
+                           int nglob_pad, double* partials, int nblocks, void* stream);
+constexpr int kEnergyBlocks = 608;  // 4 CTAs per SM on 152 SMs
+
+}  // namespace semgb

@@ -1,0 +1,328 @@
+"""ctypes binding of ``libsemgb.so`` (the C ABI in ``include/sem.h``).
+
+Every function here has the name of the C entry point it calls and only marshals
+arguments: numpy arrays for host pointers, CUDA tensors (or raw integer addresses) for
+``*_dev`` pointers. All arithmetic runs in the library. The library is loaded on first use;
+if it has not been built, or cannot be loaded, the call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+SEM_OK = 0
+ERRORS = {-1: "SEM_EINVAL", -2: "SEM_ENOMEM", -3: "SEM_ECUDA", -4: "SEM_ESTATE", -5: "SEM_ETIMEOUT",
+          -6: "SEM_EDIVERGED"}
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+# name: (restype, argtypes) for every symbol declared in include/sem.h
+SIGNATURES = {
+    "sem_version": (_I, []),
+    "sem_gll": (_I, [_I, _P, _P, _P]),
+    "sem_color_elements": (_I, [_I, _I, _I, _P, _P, _P]),
+    "sem_create": (_I, [_P, _I, _I, _P]),
+    "sem_destroy": (_I, [_P]),
+    "sem_set_mesh": (_I, [_P, _I, _I, _P, _P]),
+    "sem_set_material": (_I, [_P, _P, _P, _P]),
+    "sem_suggest_dt": (_I, [_P, _D, _P]),
+    "sem_set_dt": (_I, [_P, _D]),
+    "sem_locate_nodes": (_I, [_P, _I, _P, _P, _P]),
+    "sem_set_sources": (_I, [_P, _I, _P, _P, _D, _D]),
+    "sem_set_receivers": (_I, [_P, _I, _P]),
+    "sem_set_state": (_I, [_P, _P, _P, _P]),
+    "sem_set_state_dev": (_I, [_P, _P, _P, _P]),
+    "sem_get_state": (_I, [_P, _P, _P, _P]),
+    "sem_get_state_dev": (_I, [_P, _P, _P, _P]),
+    "sem_step": (_I, [_P, _I]),
+    "sem_run": (_I, [_P, _I, _P]),
+    "sem_run_dev": (_I, [_P, _I, _P]),
+    "sem_apply_stiffness": (_I, [_P, _P, _P]),
+    "sem_energy": (_I, [_P, _P]),
+    "sem_sync": (_I, [_P]),
+    "sem_info": (_I, [_P, _P]),
+    "sem_color_counts": (_I, [_P, _P]),
+    "sem_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+class SemError(RuntimeError):
+    def __init__(self, code: int, where: str, message: str):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {message}")
+        self.code = code
+
+
+def lib(build_if_missing: bool = False) -> ctypes.CDLL:
+    """The loaded library (raises if it is missing and ``build_if_missing`` is False)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libsemgb is not built ({path} missing); call "
+                                   "paper_2606_12850_gb300.build.build() first")
+            _build.build()
+        handle = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(code: int, where: str, ctx=None):
+    if code != SEM_OK:
+        msg = lib().sem_last_error(ctx.handle if ctx is not None else None)
+        raise SemError(code, where, (msg or b"").decode(errors="replace"))
+
+
+def _host(a, dtype, shape=None):
+    """Contiguous numpy array of ``dtype`` (copied only when needed) and its pointer."""
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if shape is not None and arr.size != int(np.prod(shape)):
+        raise ValueError(f"expected {int(np.prod(shape))} values, got {arr.size}")
+    return arr, arr.ctypes.data_as(_P)
+
+
+def _dev(t, nvalues=None):
+    """Device address of a contiguous float32 CUDA tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return _P(t)
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("device tensor must be contiguous")
+    if nvalues is not None and t.numel() < nvalues:
+        raise ValueError(f"device tensor holds {t.numel()} values, needs {nvalues}")
+    return _P(t.data_ptr())
+
+
+class Ctx:
+    """Owner of a ``sem_ctx*``; destroyed with the object."""
+
+    def __init__(self, handle: int, ngll: int):
+        self.handle = _P(handle)
+        self.ngll = ngll
+        self.nglob = 0
+        self.nspec = 0
+        self.nrec = 0
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.sem_destroy(self.handle)
+            self.handle = None
+
+
+def sem_version() -> int:
+    return lib().sem_version()
+
+
+def sem_gll(ngll: int):
+    m = max(int(ngll), 1)
+    xi, w, h = np.empty(m), np.empty(m), np.empty((m, m))
+    _check(lib().sem_gll(ngll, xi.ctypes.data_as(_P), w.ctypes.data_as(_P), h.ctypes.data_as(_P)), "sem_gll")
+    return xi, w, h
+
+
+def sem_color_elements(ibool, ngll: int, nglob: int):
+    ib, p = _host(ibool, np.int32)
+    nspec = ib.size // ngll ** 3
+    color = np.empty(nspec, dtype=np.int32)
+    nc = ctypes.c_int(0)
+    _check(lib().sem_color_elements(nspec, ngll, nglob, p, color.ctypes.data_as(_P), ctypes.byref(nc)),
+           "sem_color_elements")
+    return color, nc.value
+
+
+def sem_create(ngll: int, device: int = 0, stream=None) -> Ctx:
+    out = _P()
+    s = None
+    if stream is not None:
+        s = _P(stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().sem_create(ctypes.byref(out), ngll, device, s), "sem_create")
+    return Ctx(out.value, ngll)
+
+
+def sem_destroy(ctx: Ctx):
+    if ctx.handle is not None:
+        _check(lib().sem_destroy(ctx.handle), "sem_destroy")
+        ctx.handle = None
+
+
+def sem_set_mesh(ctx: Ctx, ibool, ctrl, nglob: int):
+    n3 = ctx.ngll ** 3
+    ib, pi = _host(ibool, np.int32)
+    nspec = ib.size // n3
+    ct, pc = _host(ctrl, np.float64, (nspec, 8, 3))
+    _check(lib().sem_set_mesh(ctx.handle, nspec, int(nglob), pi, pc), "sem_set_mesh", ctx)
+    ctx.nspec, ctx.nglob = nspec, int(nglob)
+
+
+def sem_set_material(ctx: Ctx, rho, vp, vs):
+    shape = (ctx.nspec, ctx.ngll ** 3)
+    r, pr = _host(rho, np.float32, shape)
+    a, pa = _host(vp, np.float32, shape)
+    b, pb = _host(vs, np.float32, shape)
+    _check(lib().sem_set_material(ctx.handle, pr, pa, pb), "sem_set_material", ctx)
+
+
+def sem_suggest_dt(ctx: Ctx, courant: float) -> float:
+    out = ctypes.c_double(0.0)
+    _check(lib().sem_suggest_dt(ctx.handle, float(courant), ctypes.byref(out)), "sem_suggest_dt", ctx)
+    return out.value
+
+
+def sem_set_dt(ctx: Ctx, dt: float):
+    _check(lib().sem_set_dt(ctx.handle, float(dt)), "sem_set_dt", ctx)
+
+
+def sem_locate_nodes(ctx: Ctx, xyz, surface_z=None) -> np.ndarray:
+    pts, pp = _host(np.atleast_2d(xyz), np.float64)
+    n = pts.size // 3
+    out = np.empty(n, dtype=np.int32)
+    z = ctypes.byref(ctypes.c_double(surface_z)) if surface_z is not None else None
+    _check(lib().sem_locate_nodes(ctx.handle, n, pp, z, out.ctypes.data_as(_P)), "sem_locate_nodes", ctx)
+    return out
+
+
+def sem_set_sources(ctx: Ctx, node, force, f0: float, t0: float):
+    nd, pn = _host(np.atleast_1d(node), np.int32)
+    fo, pf = _host(np.atleast_2d(force), np.float64, (nd.size, 3))
+    _check(lib().sem_set_sources(ctx.handle, nd.size, pn, pf, float(f0), float(t0)), "sem_set_sources", ctx)
+
+
+def sem_set_receivers(ctx: Ctx, node):
+    nd, pn = _host(np.atleast_1d(node), np.int32)
+    _check(lib().sem_set_receivers(ctx.handle, nd.size, pn), "sem_set_receivers", ctx)
+    ctx.nrec = nd.size
+
+
+def _state_ptrs(ctx, arrays):
+    keep, ptrs = [], []
+    for a in arrays:
+        if a is None:
+            ptrs.append(None)
+        else:
+            arr, p = _host(a, np.float32, (ctx.nglob, 3))
+            keep.append(arr)
+            ptrs.append(p)
+    return keep, ptrs
+
+
+def sem_set_state(ctx: Ctx, u=None, v=None, a=None):
+    keep, (pu, pv, pa) = _state_ptrs(ctx, (u, v, a))
+    _check(lib().sem_set_state(ctx.handle, pu, pv, pa), "sem_set_state", ctx)
+
+
+def sem_set_state_dev(ctx: Ctx, u=None, v=None, a=None):
+    n = 3 * ctx.nglob
+    _check(lib().sem_set_state_dev(ctx.handle, _dev(u, n), _dev(v, n), _dev(a, n)), "sem_set_state_dev", ctx)
+
+
+def sem_get_state(ctx: Ctx, want=(True, True, True)):
+    outs = [np.empty((ctx.nglob, 3), dtype=np.float32) if w else None for w in want]
+    ptrs = [o.ctypes.data_as(_P) if o is not None else None for o in outs]
+    _check(lib().sem_get_state(ctx.handle, *ptrs), "sem_get_state", ctx)
+    return tuple(outs)
+
+
+def sem_get_state_dev(ctx: Ctx, u=None, v=None, a=None):
+    n = 3 * ctx.nglob
+    _check(lib().sem_get_state_dev(ctx.handle, _dev(u, n), _dev(v, n), _dev(a, n)), "sem_get_state_dev", ctx)
+
+
+def sem_step(ctx: Ctx, nsteps: int):
+    _check(lib().sem_step(ctx.handle, int(nsteps)), "sem_step", ctx)
+
+
+def sem_run(ctx: Ctx, nsteps: int, record: bool = True, out=None):
+    seis = None
+    if record and ctx.nrec:
+        seis = out if out is not None else np.empty((ctx.nrec, 3, nsteps), dtype=np.float32)
+        if seis.dtype != np.float32 or not seis.flags.c_contiguous or seis.size != ctx.nrec * 3 * nsteps:
+            raise ValueError("out must be a contiguous float32 [nrec][3][nsteps] array")
+    _check(lib().sem_run(ctx.handle, int(nsteps), seis.ctypes.data_as(_P) if seis is not None else None),
+           "sem_run", ctx)
+    return seis
+
+
+def sem_run_dev(ctx: Ctx, nsteps: int, seis_dev=None):
+    _check(lib().sem_run_dev(ctx.handle, int(nsteps), _dev(seis_dev, ctx.nrec * 3 * nsteps)), "sem_run_dev", ctx)
+
+
+def sem_apply_stiffness(ctx: Ctx, u_dev, f_dev):
+    n = 3 * ctx.nglob
+    _check(lib().sem_apply_stiffness(ctx.handle, _dev(u_dev, n), _dev(f_dev, n)), "sem_apply_stiffness", ctx)
+
+
+def sem_energy(ctx: Ctx):
+    out = np.zeros(2)
+    _check(lib().sem_energy(ctx.handle, out.ctypes.data_as(_P)), "sem_energy", ctx)
+    return float(out[0]), float(out[1])
+
+
+def sem_sync(ctx: Ctx):
+    _check(lib().sem_sync(ctx.handle), "sem_sync", ctx)
+
+
+def sem_info(ctx: Ctx) -> dict:
+    out = np.zeros(6, dtype=np.int64)
+    _check(lib().sem_info(ctx.handle, out.ctypes.data_as(_P)), "sem_info", ctx)
+    keys = ("nspec", "nglob", "ngll", "ncolors", "steps", "device_bytes")
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
+def sem_color_counts(ctx: Ctx) -> np.ndarray:
+    nc = sem_info(ctx)["ncolors"]
+    out = np.zeros(nc, dtype=np.int32)
+    _check(lib().sem_color_counts(ctx.handle, out.ctypes.data_as(_P)), "sem_color_counts", ctx)
+    return out
+
+
+def sem_last_error(ctx: Ctx | None = None) -> str:
+    return (lib().sem_last_error(ctx.handle if ctx is not None else None) or b"").decode(errors="replace")
+
+
+@dataclass
+class Setup:
+    """A context set up for a workload: located sources/receivers and the time step."""
+
+    ctx: Ctx
+    dt: float
+    src_nodes: np.ndarray
+    rec_nodes: np.ndarray
+
+
+def setup_workload(workload, device: int = 0, stream=None, dt: float | None = None,
+                   src_nodes=None, rec_nodes=None) -> Setup:
+    """Create a context and issue the set-up calls for a ``inputs.Workload`` in order:
+    mesh, material, dt (the library's CFL suggestion unless given), node location
+    (unless given), sources, receivers, zero state."""
+    m = workload.mesh
+    ctx = sem_create(m.ngll, device, stream)
+    sem_set_mesh(ctx, m.ibool, m.ctrl, m.nglob)
+    sem_set_material(ctx, workload.rho, workload.vp, workload.vs)
+    if dt is None:
+        dt = sem_suggest_dt(ctx, workload.courant)
+    sem_set_dt(ctx, dt)
+    if src_nodes is None:
+        src_nodes = sem_locate_nodes(ctx, workload.source_xyz)
+    if rec_nodes is None:
+        surf = m.lengths[2] if workload.receiver_surface_only else None
+        rec_nodes = sem_locate_nodes(ctx, workload.receiver_xyz, surf)
+    sem_set_sources(ctx, src_nodes, workload.source_force, workload.f0, workload.t0)
+    sem_set_receivers(ctx, rec_nodes)
+    sem_set_state(ctx)
+    return Setup(ctx, dt, np.asarray(src_nodes), np.asarray(rec_nodes))

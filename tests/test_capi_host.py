@@ -1,0 +1,129 @@
+"""CPU-side checks of the C ABI library: it builds and loads without a GPU, exports every
+symbol ``include/sem.h`` declares, and its host-only set-up (GLL basis, colouring,
+argument validation) agrees with the oracle and with the colouring invariant of Sec. IV-C.
+No call here launches GPU work."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2606_12850_gb300 import build, inputs, sem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    build.build()
+    return sem.lib()
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "sem.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sem_[a-z_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported_and_bound():
+    declared = _declared_symbols()
+    assert len(declared) >= 20
+    lib = sem.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(sem.SIGNATURES) == declared
+
+
+def test_version():
+    assert sem.sem_version() >= 100
+
+
+@pytest.mark.parametrize("ngll", range(2, 11))
+def test_gll_matches_oracle(oracle, ngll):
+    """Library GLL basis (Newton on (1-x^2) P_N', closed-form derivative matrix) equals the
+    oracle's (Newton on P_N', product-formula derivative matrix)."""
+    xi, w, h = sem.sem_gll(ngll)
+    b = oracle.Basis(ngll)
+    np.testing.assert_allclose(xi, b.xi, atol=2e-16)
+    np.testing.assert_allclose(w, b.w, rtol=1e-14)
+    np.testing.assert_allclose(h, b.hprime, atol=1e-12 * ngll ** 2)
+
+
+def test_gll_rejects_bad_order():
+    for n in (1, 11, 0, -3):
+        with pytest.raises(sem.SemError) as ei:
+            sem.sem_gll(n)
+        assert ei.value.code == -1
+
+
+def _check_coloring(ibool, color, ncolors):
+    assert color.min() == 0 and color.max() == ncolors - 1
+    for c in range(ncolors):
+        nodes = ibool[color == c].reshape(-1)
+        assert len(np.unique(nodes)) == nodes.size, f"colour {c} shares a node"
+
+
+@pytest.mark.parametrize("n,ngll,jitter,periodic,expect", [
+    (8, 5, 0.0, False, 8),
+    (5, 3, 0.1, False, 8),
+    ((3, 4, 5), 4, 0.0, False, 8),
+    (4, 2, 0.0, True, 8),
+    (1, 5, 0.0, False, 1),
+    ((7, 1, 1), 6, 0.0, False, 2),
+])
+def test_coloring_valid(n, ngll, jitter, periodic, expect):
+    """Sec. IV-C: within a colour no two elements share a node; a structured lattice gets
+    the 8-colour parity pattern (2 for a line of elements, 1 for a single element)."""
+    mesh = inputs.structured_hex_mesh(n, ngll, 1000.0, jitter=jitter, periodic=periodic)
+    color, nc = sem.sem_color_elements(mesh.ibool, ngll, mesh.nglob)
+    _check_coloring(mesh.ibool, color, nc)
+    assert nc == expect
+
+
+def test_coloring_periodic_odd():
+    """A periodic lattice with an odd element count cannot use the parity pattern; the
+    greedy colouring still yields a valid colouring."""
+    mesh = inputs.structured_hex_mesh(3, 3, 1.0, periodic=True)
+    color, nc = sem.sem_color_elements(mesh.ibool, 3, mesh.nglob)
+    _check_coloring(mesh.ibool, color, nc)
+    assert nc == 27  # every pair of the 27 elements shares a node
+
+
+def test_coloring_rejects_repeated_node():
+    """A periodic line of a single element repeats its own nodes: rejected (its own
+    scatter would race)."""
+    mesh = inputs.structured_hex_mesh((1, 2, 2), 3, 1.0, periodic=True)
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_color_elements(mesh.ibool, 3, mesh.nglob)
+    assert ei.value.code == -1 and "repeats node" in str(ei.value)
+
+
+def test_coloring_rejects_out_of_range():
+    mesh = inputs.structured_hex_mesh(2, 3, 1.0)
+    bad = mesh.ibool.copy()
+    bad[1, 4] = mesh.nglob
+    with pytest.raises(sem.SemError):
+        sem.sem_color_elements(bad, 3, mesh.nglob)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: with the library absent, the binding raises."""
+    monkeypatch.setattr(sem, "_lib", None)
+    monkeypatch.setattr(build, "LIB", "/nonexistent/libsemgb.so")
+    with pytest.raises(RuntimeError, match="not built"):
+        sem.lib()
+
+
+def test_create_without_gpu_reports_cuda_error():
+    """On a machine without a GPU, creating a context returns SEM_ECUDA, it does not
+    crash or fall back to the CPU."""
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:  # pragma: no cover
+        has_gpu = False
+    if has_gpu:
+        pytest.skip("a GPU is present")
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_create(5)
+    assert ei.value.code == -3
