@@ -41,6 +41,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--ngll", type=int, default=5)
+    p.add_argument("--elems", type=int, default=None,
+                   help="elements per side (default: 256 GLL intervals per side); smaller cases for profiling")
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--stiffness-reps", type=int, default=40)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -240,7 +242,7 @@ def run_ours(args):
     build.build()
 
     K, W = args.steps, args.warmup
-    w = inputs.layered_cube(args.ngll, nsteps=K)
+    w = inputs.layered_cube(args.ngll, n=args.elems, nsteps=K)
     mesh = w.mesh
     stream = torch.cuda.Stream(device=local)
     s = sem.setup_workload(w, device=local, stream=stream)

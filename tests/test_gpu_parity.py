@@ -222,9 +222,10 @@ def test_duplicate_sources_merge(oracle):
 def test_argument_errors():
     mesh = inputs.structured_hex_mesh(2, 3, 100.0)
     ctx = sem.sem_create(3, 0)
-    with pytest.raises(sem.SemError) as ei:
-        sem.sem_set_material(ctx, *random_material(mesh, 1))
-    assert ei.value.code == -4
+    rho, vp, vs = random_material(mesh, 1)
+    ptr = lambda a: a.ctypes.data_as(sem._P)
+    assert sem.lib().sem_set_material(ctx.handle, ptr(rho), ptr(vp), ptr(vs)) == -4  # before the mesh
+    assert "sem_set_mesh" in sem.sem_last_error(ctx)
     bad = mesh.ibool.copy()
     bad[0, 0] = -1
     with pytest.raises(sem.SemError) as ei:
