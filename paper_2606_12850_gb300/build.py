@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
         objs.append(o)
         jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", cuda_inc, "-I", INCLUDE,
                      "-c", os.path.join(CSRC, f), "-o", o])
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4, len(jobs))) as ex:
         outs = list(ex.map(_compile, jobs))
     if verbose:
         for o in outs:

@@ -1,0 +1,305 @@
+// Force kernel template of libsemgb, compiled once per NGLL: each sem_forces_<N>.cu
+// defines SEM_NGLL and includes this file, so the orders build in parallel and every
+// translation unit owns the constant-memory copy of its 1D basis.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sem_internal.h"
+
+#define SEM_CAT2(a, b) a##b
+#define SEM_CAT(a, b) SEM_CAT2(a, b)
+
+#ifndef SEM_NGLL
+#error "define SEM_NGLL before including sem_forces.cuh"
+#endif
+
+namespace semgb {
+namespace {
+
+__constant__ float c_h[SEM_NGLL * SEM_NGLL];   // hprime[i*n + l] = l_l'(xi_i)
+__constant__ float c_hw[SEM_NGLL * SEM_NGLL];  // [l*n + i] = w_l * hprime[l][i]
+__constant__ float c_w[SEM_NGLL];
+
+// ---------------------------------------------------------------------------------------
+// Force kernel (Sec. II-B matrix-free stiffness action + Sec. IV-C coloured assembly),
+// optionally fused with the Newmark node update.
+//
+// A CTA holds E = T / NGLL^2 elements of one colour. Five phases, separated by barriers:
+//  0. the element's ibool words go to shared memory (coalesced record reads);
+//  1. cooperative gather: consecutive threads take consecutive (point, component) slots of
+//     the CTA's elements, so a warp reads whole xi-rows of the global arrays (coalesced
+//     along the lattice rows) instead of one scattered node per thread. At a node's first
+//     touch in the colour order the same thread applies the Newmark update of that node
+//     (MODE 1: predictor from a complete state; MODE 2: corrector of the previous step
+//     then predictor), so no separate pass over the global arrays is needed;
+//  2. one thread per xi-line (j, k): xi-derivative and xi-transposed product in registers,
+//     eta and zeta derivatives from the shared cube, Jacobian map, Hooke stress, fluxes;
+//  3. eta and zeta transposed products from the shared fluxes; element forces back to
+//     shared memory;
+//  4. cooperative scatter through ibool in the gather's coalesced order: a store at the
+//     node's first touch, a read-modify-write otherwise (elements of one launch share no
+//     node, so there are no atomics and the summation order is fixed).
+// Shared memory per element: u or F as [p][3], fluxes as [p][6], ibool as [p]; the element
+// stride is padded so that the two elements a warp spans fall in disjoint banks.
+// ---------------------------------------------------------------------------------------
+template <int N>
+struct ForceCfg {
+  static constexpr int NP = N * N * N;
+  static constexpr int NL = N * N;
+  static constexpr int T = (N <= 5) ? 128 : 256;
+  static constexpr int E = T / NL;
+  static constexpr int REC = (kRecFields * NP + 3) / 4 * 4;
+  // bank offset of the per-element stride (chosen by simulating the warp access patterns)
+  static constexpr int RES = N == 2 ? 7 : N == 3 ? 17 : N == 5 ? 23 : N == 7 ? 5 : N == 9 ? 11 : N == 8 ? 0 : 1;
+  static constexpr int S = 10 * NP + ((RES - 10 * NP) % 32 + 32) % 32;
+  static constexpr int SMEM_FLOATS = E * S;
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(ForceCfg<N>::T)
+    forces_kernel(const float* __restrict__ rec, float* u, float* __restrict__ f, float* __restrict__ v,
+                  const float* __restrict__ minv, int e0, int e1, float dt, float hdt, float hdt2) {
+  using C = ForceCfg<N>;
+  constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, T = C::T, S = C::S;
+  extern __shared__ float smem[];
+  const float* __restrict__ H = c_h;
+  const float* __restrict__ HW = c_hw;
+  const float* __restrict__ W = c_w;
+  const int t = threadIdx.x;
+  const int ebase = e0 + blockIdx.x * E;
+  const int ne = min(E, e1 - ebase);  // elements of this CTA (>= 1)
+
+  // phase 0: ibool words, record order q = i*NL + line -> shared order p = i + N*line
+  for (int idx = t; idx < ne * NP; idx += T) {
+    const int le = idx / NP;
+    const int q = idx - le * NP;
+    const int i = q / NL;
+    const int p = i + N * (q - i * NL);
+    const uint32_t w = __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + q));
+    reinterpret_cast<uint32_t*>(smem + le * S + 9 * NP)[p] = w;
+  }
+  __syncthreads();
+
+  // phase 1: coalesced gather of u (with the Newmark update at first touch)
+  for (int idx = t; idx < ne * 3 * NP; idx += T) {
+    const int le = idx / (3 * NP);
+    const int rem = idx - le * 3 * NP;
+    const int p = rem / 3;
+    const int c = rem - 3 * p;
+    const uint32_t w = reinterpret_cast<const uint32_t*>(smem + le * S + 9 * NP)[p];
+    const size_t g = w & ~kFirstTouchBit;
+    const size_t gi = 3 * g + c;
+    float uu = u[gi];
+    if (MODE != 0 && (w & kFirstTouchBit)) {
+      float acc = f[gi];
+      if (MODE == 2) acc *= minv[g];
+      float vv = v[gi];
+      if (MODE == 2) vv += hdt * acc;  // corrector of the previous step
+      uu += dt * vv + hdt2 * acc;      // predictor
+      vv += hdt * acc;
+      u[gi] = uu;
+      v[gi] = vv;
+    }
+    smem[le * S + rem] = uu;
+  }
+  __syncthreads();
+
+  // phase 2: per xi-line derivatives, stress and fluxes
+  const int le = t / NL;
+  const int line = t - le * NL;  // = j + N k
+  const int j = line % N;
+  const int k = line / N;
+  const bool active = le < ne;
+  const float* su = smem + (active ? le : 0) * S;
+  float* st = smem + (active ? le : 0) * S + 3 * NP;
+  const float* __restrict__ r = rec + static_cast<size_t>(ebase + (active ? le : 0)) * REC;
+
+  float ux[N], uy[N], uz[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int p = i + N * line;
+    ux[i] = su[3 * p];
+    uy[i] = su[3 * p + 1];
+    uz[i] = su[3 * p + 2];
+  }
+  float hj[N], hk[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    hj[l] = H[j * N + l];
+    hk[l] = H[k * N + l];
+  }
+  float fx[N], fy[N], fz[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) fx[i] = fy[i] = fz[i] = 0.f;
+
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
+    float det_x = 0.f, det_y = 0.f, det_z = 0.f;
+    float dze_x = 0.f, dze_y = 0.f, dze_z = 0.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const float h = H[i * N + l];
+      dxi_x += h * ux[l];
+      dxi_y += h * uy[l];
+      dxi_z += h * uz[l];
+      const int pe = 3 * (i + N * (l + N * k));
+      det_x += hj[l] * su[pe];
+      det_y += hj[l] * su[pe + 1];
+      det_z += hj[l] * su[pe + 2];
+      const int pz = 3 * (i + N * (j + N * l));
+      dze_x += hk[l] * su[pz];
+      dze_y += hk[l] * su[pz + 1];
+      dze_z += hk[l] * su[pz + 2];
+    }
+    const int q = i * NL + line;
+    float G[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) G[a] = active ? __ldg(r + (kG + a) * NP + q) : 0.f;
+    const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
+    const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
+    const float mu = active ? __ldg(r + kMu * NP + q) : 0.f;
+
+    const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
+    const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
+    const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
+    const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
+    const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
+    const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
+    const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
+    const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
+    const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
+
+    const float lam = kappa - (2.f / 3.f) * mu;
+    const float tr = uxx + uyy + uzz;
+    const float sxx = lam * tr + 2.f * mu * uxx;
+    const float syy = lam * tr + 2.f * mu * uyy;
+    const float szz = lam * tr + 2.f * mu * uzz;
+    const float sxy = mu * (uxy + uyx);
+    const float sxz = mu * (uxz + uzx);
+    const float syz = mu * (uyz + uzy);
+
+    const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
+    const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
+    const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
+#pragma unroll
+    for (int ip = 0; ip < N; ++ip) {
+      const float hw = HW[i * N + ip];
+      fx[ip] += hw * txi_x;
+      fy[ip] += hw * txi_y;
+      fz[ip] += hw * txi_z;
+    }
+    if (active) {
+      const int p6 = 6 * (i + N * line);
+      st[p6 + 0] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
+      st[p6 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
+      st[p6 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
+      st[p6 + 3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
+      st[p6 + 4] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
+      st[p6 + 5] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
+    }
+  }
+  __syncthreads();
+
+  // phase 3: eta and zeta transposed products; forces into the (now free) u slots
+  float hwj[N], hwk[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    hwj[l] = HW[l * N + j];
+    hwk[l] = HW[l * N + k];
+  }
+  const float wj = W[j], wk = W[k];
+  float* sf = smem + (active ? le : 0) * S;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float ex = 0.f, ey = 0.f, ez = 0.f, zx = 0.f, zy = 0.f, zz = 0.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const int pe = 6 * (i + N * (l + N * k));
+      ex += hwj[l] * st[pe];
+      ey += hwj[l] * st[pe + 1];
+      ez += hwj[l] * st[pe + 2];
+      const int pz = 6 * (i + N * (j + N * l)) + 3;
+      zx += hwk[l] * st[pz];
+      zy += hwk[l] * st[pz + 1];
+      zz += hwk[l] * st[pz + 2];
+    }
+    const float wi = W[i];
+    if (active) {
+      const int p = 3 * (i + N * line);
+      sf[p] = -(wj * wk * fx[i] + wi * wk * ex + wi * wj * zx);
+      sf[p + 1] = -(wj * wk * fy[i] + wi * wk * ey + wi * wj * zy);
+      sf[p + 2] = -(wj * wk * fz[i] + wi * wk * ez + wi * wj * zz);
+    }
+  }
+  __syncthreads();
+
+  // phase 4: coalesced scatter (store at first touch, read-modify-write otherwise)
+  for (int idx = t; idx < ne * 3 * NP; idx += T) {
+    const int e = idx / (3 * NP);
+    const int rem = idx - e * 3 * NP;
+    const int p = rem / 3;
+    const uint32_t w = reinterpret_cast<const uint32_t*>(smem + e * S + 9 * NP)[p];
+    const size_t gi = 3 * static_cast<size_t>(w & ~kFirstTouchBit) + (rem - 3 * p);
+    const float val = smem[e * S + rem];
+    if (w & kFirstTouchBit)
+      f[gi] = val;
+    else
+      f[gi] += val;
+  }
+}
+
+template <int N, int MODE>
+int launch_forces_nm(const ForceLaunch& L, cudaStream_t s) {
+  using C = ForceCfg<N>;
+  if (L.e1 <= L.e0) return 0;
+  static unsigned long long attr_done = 0;  // one bit per device ordinal
+  const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_done & bit)) {
+    cudaError_t e = cudaFuncSetAttribute(forces_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    attr_done |= bit;
+  }
+  const int grid = (L.e1 - L.e0 + C::E - 1) / C::E;
+  forces_kernel<N, MODE><<<grid, C::T, smem, s>>>(L.rec, L.u, L.f, L.v, L.minv, L.e0, L.e1, L.dt, L.hdt, L.hdt2);
+  return static_cast<int>(cudaGetLastError());
+}
+
+
+}  // namespace
+
+int SEM_CAT(upload_basis_, SEM_NGLL)(const double* w, const double* h, void* stream, int n) {
+  constexpr int N = SEM_NGLL;
+  if (n != N) return static_cast<int>(cudaErrorInvalidValue);
+  float hf[N * N], hwf[N * N], wf[N];
+  for (int i = 0; i < N; ++i) {
+    wf[i] = static_cast<float>(w[i]);
+    for (int l = 0; l < N; ++l) {
+      hf[i * N + l] = static_cast<float>(h[i * N + l]);
+      hwf[l * N + i] = static_cast<float>(w[l] * h[l * N + i]);
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_h, hf, sizeof(hf), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_hw, hwf, sizeof(hwf), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_w, wf, sizeof(wf), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return static_cast<int>(e);
+}
+
+int SEM_CAT(launch_forces_, SEM_NGLL)(const ForceLaunch& L, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (L.mode) {
+    case 0: return launch_forces_nm<SEM_NGLL, 0>(L, s);
+    case 1: return launch_forces_nm<SEM_NGLL, 1>(L, s);
+    case 2: return launch_forces_nm<SEM_NGLL, 2>(L, s);
+    default: return static_cast<int>(cudaErrorInvalidValue);
+  }
+}
+
+int SEM_CAT(forces_smem_bytes_, SEM_NGLL)() { return ForceCfg<SEM_NGLL>::SMEM_FLOATS * 4; }
+
+}  // namespace semgb

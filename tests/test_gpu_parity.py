@@ -1,12 +1,12 @@
 """GPU parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances:
-* one stiffness application f = -K u on random u: relative L2 <= 1e-5 and every entry
-  within 1e-4 * max|f|. FP32 unit roundoff is 6e-8; an entry of f is a sum of about
+* one stiffness application f = -K u on random u: relative L2 <= 2e-6 and every entry
+  within 1e-5 * max|f|. FP32 unit roundoff is 6e-8; an entry of f is a sum of about
   2N + 25 rounded products per quadrature point (derivative, chain rule, stress, flux,
-  transposed product) and up to 8 element contributions, and random u cancels a factor
-  of ~10 between the terms and the result, which gives a few 1e-6 (random-walk) to
-  2e-5 (worst case) relative error; 1e-5 in L2 sits between the two.
+  transposed product) and up to 8 element contributions; rounding errors that add like a
+  random walk give sqrt(40) * 6e-8 ~ 4e-7 relative to the magnitude of the terms, and
+  random u cancels up to a factor of ~5 between the terms and the result: 2e-6.
 * wavefield after 200 steps: relative L2 <= 2e-5; seismograms: relative L2 <= 1e-4
   (the solver's stated accuracy targets for the homogeneous 8^3 cube).
 """
@@ -19,8 +19,8 @@ from paper_2606_12850_gb300 import build, inputs, sem  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL_KU_L2 = 1e-5
-TOL_KU_MAX = 1e-4
+TOL_KU_L2 = 2e-6
+TOL_KU_MAX = 1e-5
 TOL_WAVEFIELD = 2e-5
 TOL_SEIS = 1e-4
 
