@@ -423,7 +423,7 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
             touched[g] = 1;
             g |= kFirstTouchBit;
           }
-          std::memcpy(&r[kIbool * np + q], &g, sizeof(uint32_t));
+          std::memcpy(&r[kIbool * np + p], &g, sizeof(uint32_t));
           for (int a = 0; a < 10; ++a) r[(kG + a) * np + q] = gq[a * np + p];
         }
   }

@@ -24,228 +24,301 @@ __constant__ float c_w[SEM_NGLL];
 // Force kernel (Sec. II-B matrix-free stiffness action + Sec. IV-C coloured assembly),
 // optionally fused with the Newmark node update.
 //
-// A CTA holds E = T / NGLL^2 elements of one colour. Five phases, separated by barriers:
-//  0. the element's ibool words go to shared memory (coalesced record reads);
-//  1. cooperative gather: consecutive threads take consecutive (point, component) slots of
-//     the CTA's elements, so a warp reads whole xi-rows of the global arrays (coalesced
-//     along the lattice rows) instead of one scattered node per thread. At a node's first
-//     touch in the colour order the same thread applies the Newmark update of that node
-//     (MODE 1: predictor from a complete state; MODE 2: corrector of the previous step
-//     then predictor), so no separate pass over the global arrays is needed;
-//  2. one thread per xi-line (j, k): xi-derivative and xi-transposed product in registers,
-//     eta and zeta derivatives from the shared cube, Jacobian map, Hooke stress, fluxes;
-//  3. eta and zeta transposed products from the shared fluxes; element forces back to
-//     shared memory;
-//  4. cooperative scatter through ibool in the gather's coalesced order: a store at the
-//     node's first touch, a read-modify-write otherwise (elements of one launch share no
-//     node, so there are no atomics and the summation order is fixed).
-// Shared memory per element: u or F as [p][3], fluxes as [p][6], ibool as [p]; the element
-// stride is padded so that the two elements a warp spans fall in disjoint banks.
+// Threads work in teams: one warp per team for NGLL <= 5 (then a team only ever needs
+// __syncwarp, so warps of a CTA drift freely and hide each other's memory latency), the
+// whole CTA for NGLL >= 6. A team holds E = TEAM / NGLL^2 elements of one colour.
+//  1. gather, one thread per local point: consecutive threads take consecutive points p,
+//     so a warp reads whole xi-rows of the global arrays. At a node's first touch in the
+//     colour order the same thread applies the Newmark update of the node (MODE 1:
+//     predictor from a complete state; MODE 2: corrector of the previous step, then the
+//     predictor), so the step needs no separate pass over the global arrays;
+//  2. one thread per xi-line (j, k): the xi-derivative and xi-transposed product stay in
+//     registers; eta and zeta derivatives accumulate whole xi-rows of the shared cube,
+//     read with 128-bit loads (rows are padded to a multiple of 4 floats); Jacobian map,
+//     Hooke stress and fluxes per point;
+//  3. eta and zeta transposed products from the shared flux rows, element forces back
+//     into the thread's own row;
+//  4. scatter in the gather's order: a store at the node's first touch, a
+//     read-modify-write otherwise (elements of one launch share no node: no atomics,
+//     fixed summation order).
+// Shared memory per element: u (then F), eta-flux and zeta-flux as [NGLL^2 rows][RS]
+// (row = xi-line, [i][3] inside), ibool as [NP].
 // ---------------------------------------------------------------------------------------
 template <int N>
 struct ForceCfg {
   static constexpr int NP = N * N * N;
   static constexpr int NL = N * N;
-  static constexpr int T = (N <= 5) ? 128 : 256;
-  static constexpr int E = T / NL;
+  static constexpr bool WARP_TEAM = NL <= 32;
+  static constexpr int T = WARP_TEAM ? 128 : 256;     // threads per CTA
+  static constexpr int TEAM = WARP_TEAM ? 32 : T;     // threads per team
+  static constexpr int TEAMS = T / TEAM;              // teams per CTA
+  static constexpr int E = TEAM / NL;                 // elements per team
+  static constexpr int EPC = TEAMS * E;               // elements per CTA
+  static constexpr int RS = (3 * N + 3) / 4 * 4;      // floats per padded xi-row
+  static constexpr int RV = RS / 4;                   // float4 per row
+  static constexpr int NPA = (NP + 3) / 4 * 4;
+  static constexpr int ES = 3 * NL * RS + NPA + (E > 1 ? 4 : 0);  // floats per element
+  static constexpr int TS = E * ES;                   // floats per team
+  static constexpr int SMEM_FLOATS = TEAMS * TS;
   static constexpr int REC = (kRecFields * NP + 3) / 4 * 4;
-  // bank offset of the per-element stride (chosen by simulating the warp access patterns)
-  static constexpr int RES = N == 2 ? 7 : N == 3 ? 17 : N == 5 ? 23 : N == 7 ? 5 : N == 9 ? 11 : N == 8 ? 0 : 1;
-  static constexpr int S = 10 * NP + ((RES - 10 * NP) % 32 + 32) % 32;
-  static constexpr int SMEM_FLOATS = E * S;
+  static constexpr bool LINE_VEC = N <= 7;            // whole-row register accumulation
 };
 
+template <bool WARP>
+__device__ __forceinline__ void team_sync() {
+  if (WARP)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
+template <int N>
+__device__ __forceinline__ void load_row(const float* rowp, float (&row)[ForceCfg<N>::RS]) {
+  const float4* r4 = reinterpret_cast<const float4*>(rowp);
+#pragma unroll
+  for (int m = 0; m < ForceCfg<N>::RV; ++m) {
+    const float4 q = r4[m];
+    row[4 * m] = q.x;
+    row[4 * m + 1] = q.y;
+    row[4 * m + 2] = q.z;
+    row[4 * m + 3] = q.w;
+  }
+}
+
+#ifndef SEM_FORCES_MIN_BLOCKS
+#define SEM_FORCES_MIN_BLOCKS 1
+#endif
+
 template <int N, int MODE>
-__global__ void __launch_bounds__(ForceCfg<N>::T)
+__global__ void __launch_bounds__(ForceCfg<N>::T, SEM_FORCES_MIN_BLOCKS)
     forces_kernel(const float* __restrict__ rec, float* u, float* __restrict__ f, float* __restrict__ v,
                   const float* __restrict__ minv, int e0, int e1, float dt, float hdt, float hdt2) {
   using C = ForceCfg<N>;
-  constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, T = C::T, S = C::S;
-  extern __shared__ float smem[];
+  constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES, RS = C::RS;
+  constexpr bool WT = C::WARP_TEAM;
+  extern __shared__ float4 smem4[];
   const float* __restrict__ H = c_h;
   const float* __restrict__ HW = c_hw;
   const float* __restrict__ W = c_w;
-  const int t = threadIdx.x;
-  const int ebase = e0 + blockIdx.x * E;
-  const int ne = min(E, e1 - ebase);  // elements of this CTA (>= 1)
 
-  // phase 0: ibool words, record order q = i*NL + line -> shared order p = i + N*line
-  for (int idx = t; idx < ne * NP; idx += T) {
+  const int team = threadIdx.x / TEAM;
+  const int tl = threadIdx.x - team * TEAM;
+  const int ebase = e0 + (blockIdx.x * C::TEAMS + team) * E;
+  const int ne = min(E, e1 - ebase);
+  if (WT && ne <= 0) return;  // a warp team with no element (never a CTA team)
+  float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
+
+  // 1. gather (+ Newmark at first touch), one thread per local point
+  for (int idx = tl; idx < ne * NP; idx += TEAM) {
     const int le = idx / NP;
-    const int q = idx - le * NP;
-    const int i = q / NL;
-    const int p = i + N * (q - i * NL);
-    const uint32_t w = __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + q));
-    reinterpret_cast<uint32_t*>(smem + le * S + 9 * NP)[p] = w;
-  }
-  __syncthreads();
-
-  // phase 1: coalesced gather of u (with the Newmark update at first touch)
-  for (int idx = t; idx < ne * 3 * NP; idx += T) {
-    const int le = idx / (3 * NP);
-    const int rem = idx - le * 3 * NP;
-    const int p = rem / 3;
-    const int c = rem - 3 * p;
-    const uint32_t w = reinterpret_cast<const uint32_t*>(smem + le * S + 9 * NP)[p];
+    const int p = idx - le * NP;
+    const int line = p / N;
+    const int i = p - line * N;
+    float* eb = ts + le * ES;
+    const uint32_t w = __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + p));
+    reinterpret_cast<uint32_t*>(eb + 3 * NL * RS)[p] = w;
     const size_t g = w & ~kFirstTouchBit;
-    const size_t gi = 3 * g + c;
-    float uu = u[gi];
-    if (MODE != 0 && (w & kFirstTouchBit)) {
-      float acc = f[gi];
-      if (MODE == 2) acc *= minv[g];
-      float vv = v[gi];
-      if (MODE == 2) vv += hdt * acc;  // corrector of the previous step
-      uu += dt * vv + hdt2 * acc;      // predictor
-      vv += hdt * acc;
-      u[gi] = uu;
-      v[gi] = vv;
+    float* dst = eb + line * RS + 3 * i;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t gi = 3 * g + c;
+      float uu = u[gi];
+      if (MODE != 0 && (w & kFirstTouchBit)) {
+        float acc = f[gi];
+        if (MODE == 2) acc *= minv[g];
+        float vv = v[gi];
+        if (MODE == 2) vv += hdt * acc;  // corrector of the previous step
+        uu += dt * vv + hdt2 * acc;      // predictor
+        vv += hdt * acc;
+        u[gi] = uu;
+        v[gi] = vv;
+      }
+      dst[c] = uu;
     }
-    smem[le * S + rem] = uu;
   }
-  __syncthreads();
+  team_sync<WT>();
 
-  // phase 2: per xi-line derivatives, stress and fluxes
-  const int le = t / NL;
-  const int line = t - le * NL;  // = j + N k
+  // 2. per xi-line derivatives, stress and fluxes
+  const int le = tl / NL;
+  const int line = tl - le * NL;  // = j + N k
   const int j = line % N;
   const int k = line / N;
   const bool active = le < ne;
-  const float* su = smem + (active ? le : 0) * S;
-  float* st = smem + (active ? le : 0) * S + 3 * NP;
+  float* eb = ts + (active ? le : 0) * ES;
+  float* rows_u = eb;
+  float* rows_te = eb + NL * RS;
+  float* rows_tz = eb + 2 * NL * RS;
   const float* __restrict__ r = rec + static_cast<size_t>(ebase + (active ? le : 0)) * REC;
 
-  float ux[N], uy[N], uz[N];
+  float fxi[3 * N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const int p = i + N * line;
-    ux[i] = su[3 * p];
-    uy[i] = su[3 * p + 1];
-    uz[i] = su[3 * p + 2];
-  }
-  float hj[N], hk[N];
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    hj[l] = H[j * N + l];
-    hk[l] = H[k * N + l];
-  }
-  float fx[N], fy[N], fz[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) fx[i] = fy[i] = fz[i] = 0.f;
-
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
-    float det_x = 0.f, det_y = 0.f, det_z = 0.f;
-    float dze_x = 0.f, dze_y = 0.f, dze_z = 0.f;
+  for (int q = 0; q < 3 * N; ++q) fxi[q] = 0.f;
+  {
+    float uo[RS];
+    load_row<N>(rows_u + line * RS, uo);
+    float hj[N], hk[N];
 #pragma unroll
     for (int l = 0; l < N; ++l) {
-      const float h = H[i * N + l];
-      dxi_x += h * ux[l];
-      dxi_y += h * uy[l];
-      dxi_z += h * uz[l];
-      const int pe = 3 * (i + N * (l + N * k));
-      det_x += hj[l] * su[pe];
-      det_y += hj[l] * su[pe + 1];
-      det_z += hj[l] * su[pe + 2];
-      const int pz = 3 * (i + N * (j + N * l));
-      dze_x += hk[l] * su[pz];
-      dze_y += hk[l] * su[pz + 1];
-      dze_z += hk[l] * su[pz + 2];
+      hj[l] = H[j * N + l];
+      hk[l] = H[k * N + l];
     }
-    const int q = i * NL + line;
-    float G[9];
+    float deta[C::LINE_VEC ? 3 * N : 1], dzet[C::LINE_VEC ? 3 * N : 1];
+    if (C::LINE_VEC) {
 #pragma unroll
-    for (int a = 0; a < 9; ++a) G[a] = active ? __ldg(r + (kG + a) * NP + q) : 0.f;
-    const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
-    const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
-    const float mu = active ? __ldg(r + kMu * NP + q) : 0.f;
-
-    const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
-    const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
-    const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
-    const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
-    const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
-    const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
-    const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
-    const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
-    const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
-
-    const float lam = kappa - (2.f / 3.f) * mu;
-    const float tr = uxx + uyy + uzz;
-    const float sxx = lam * tr + 2.f * mu * uxx;
-    const float syy = lam * tr + 2.f * mu * uyy;
-    const float szz = lam * tr + 2.f * mu * uzz;
-    const float sxy = mu * (uxy + uyx);
-    const float sxz = mu * (uxz + uzx);
-    const float syz = mu * (uyz + uzy);
-
-    const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
-    const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
-    const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
+      for (int q = 0; q < 3 * N; ++q) deta[q] = dzet[q] = 0.f;
 #pragma unroll
-    for (int ip = 0; ip < N; ++ip) {
-      const float hw = HW[i * N + ip];
-      fx[ip] += hw * txi_x;
-      fy[ip] += hw * txi_y;
-      fz[ip] += hw * txi_z;
+      for (int l = 0; l < N; ++l) {
+        float row[RS];
+        load_row<N>(rows_u + (l + N * k) * RS, row);
+#pragma unroll
+        for (int q = 0; q < 3 * N; ++q) deta[q] += hj[l] * row[q];
+        load_row<N>(rows_u + (j + N * l) * RS, row);
+#pragma unroll
+        for (int q = 0; q < 3 * N; ++q) dzet[q] += hk[l] * row[q];
+      }
     }
-    if (active) {
-      const int p6 = 6 * (i + N * line);
-      st[p6 + 0] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
-      st[p6 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
-      st[p6 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
-      st[p6 + 3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
-      st[p6 + 4] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
-      st[p6 + 5] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const float h = H[i * N + l];
+        dxi_x += h * uo[3 * l];
+        dxi_y += h * uo[3 * l + 1];
+        dxi_z += h * uo[3 * l + 2];
+      }
+      float det_x, det_y, det_z, dze_x, dze_y, dze_z;
+      if (C::LINE_VEC) {
+        det_x = deta[3 * i];
+        det_y = deta[3 * i + 1];
+        det_z = deta[3 * i + 2];
+        dze_x = dzet[3 * i];
+        dze_y = dzet[3 * i + 1];
+        dze_z = dzet[3 * i + 2];
+      } else {
+        det_x = det_y = det_z = dze_x = dze_y = dze_z = 0.f;
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          const float* pe = rows_u + (l + N * k) * RS + 3 * i;
+          det_x += hj[l] * pe[0];
+          det_y += hj[l] * pe[1];
+          det_z += hj[l] * pe[2];
+          const float* pz = rows_u + (j + N * l) * RS + 3 * i;
+          dze_x += hk[l] * pz[0];
+          dze_y += hk[l] * pz[1];
+          dze_z += hk[l] * pz[2];
+        }
+      }
+      const int q = i * NL + line;
+      float G[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) G[a] = active ? __ldg(r + (kG + a) * NP + q) : 0.f;
+      const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
+      const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
+      const float mu = active ? __ldg(r + kMu * NP + q) : 0.f;
+
+      const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
+      const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
+      const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
+      const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
+      const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
+      const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
+      const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
+      const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
+      const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
+
+      const float lam = kappa - (2.f / 3.f) * mu;
+      const float tr = uxx + uyy + uzz;
+      const float sxx = lam * tr + 2.f * mu * uxx;
+      const float syy = lam * tr + 2.f * mu * uyy;
+      const float szz = lam * tr + 2.f * mu * uzz;
+      const float sxy = mu * (uxy + uyx);
+      const float sxz = mu * (uxz + uzx);
+      const float syz = mu * (uyz + uzy);
+
+      const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
+      const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
+      const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
+#pragma unroll
+      for (int ip = 0; ip < N; ++ip) {
+        const float hw = HW[i * N + ip];
+        fxi[3 * ip] += hw * txi_x;
+        fxi[3 * ip + 1] += hw * txi_y;
+        fxi[3 * ip + 2] += hw * txi_z;
+      }
+      if (active) {
+        float* te = rows_te + line * RS + 3 * i;
+        te[0] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
+        te[1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
+        te[2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
+        float* tz = rows_tz + line * RS + 3 * i;
+        tz[0] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
+        tz[1] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
+        tz[2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
+      }
     }
   }
-  __syncthreads();
+  team_sync<WT>();
 
-  // phase 3: eta and zeta transposed products; forces into the (now free) u slots
-  float hwj[N], hwk[N];
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    hwj[l] = HW[l * N + j];
-    hwk[l] = HW[l * N + k];
-  }
-  const float wj = W[j], wk = W[k];
-  float* sf = smem + (active ? le : 0) * S;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float ex = 0.f, ey = 0.f, ez = 0.f, zx = 0.f, zy = 0.f, zz = 0.f;
+  // 3. eta and zeta transposed products; forces into the thread's own u row
+  {
+    float hwj[N], hwk[N];
 #pragma unroll
     for (int l = 0; l < N; ++l) {
-      const int pe = 6 * (i + N * (l + N * k));
-      ex += hwj[l] * st[pe];
-      ey += hwj[l] * st[pe + 1];
-      ez += hwj[l] * st[pe + 2];
-      const int pz = 6 * (i + N * (j + N * l)) + 3;
-      zx += hwk[l] * st[pz];
-      zy += hwk[l] * st[pz + 1];
-      zz += hwk[l] * st[pz + 2];
+      hwj[l] = HW[l * N + j];
+      hwk[l] = HW[l * N + k];
     }
-    const float wi = W[i];
+    float eacc[3 * N], zacc[3 * N];
+#pragma unroll
+    for (int q = 0; q < 3 * N; ++q) eacc[q] = zacc[q] = 0.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      float row[RS];
+      load_row<N>(rows_te + (l + N * k) * RS, row);
+#pragma unroll
+      for (int q = 0; q < 3 * N; ++q) eacc[q] += hwj[l] * row[q];
+      load_row<N>(rows_tz + (j + N * l) * RS, row);
+#pragma unroll
+      for (int q = 0; q < 3 * N; ++q) zacc[q] += hwk[l] * row[q];
+    }
+    const float wj = W[j], wk = W[k];
     if (active) {
-      const int p = 3 * (i + N * line);
-      sf[p] = -(wj * wk * fx[i] + wi * wk * ex + wi * wj * zx);
-      sf[p + 1] = -(wj * wk * fy[i] + wi * wk * ey + wi * wj * zy);
-      sf[p + 2] = -(wj * wk * fz[i] + wi * wk * ez + wi * wj * zz);
+      float out[RS];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const float wi = W[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          out[3 * i + c] = -(wj * wk * fxi[3 * i + c] + wi * wk * eacc[3 * i + c] + wi * wj * zacc[3 * i + c]);
+      }
+#pragma unroll
+      for (int q = 3 * N; q < RS; ++q) out[q] = 0.f;
+      float4* o4 = reinterpret_cast<float4*>(rows_u + line * RS);
+#pragma unroll
+      for (int m = 0; m < C::RV; ++m) o4[m] = make_float4(out[4 * m], out[4 * m + 1], out[4 * m + 2], out[4 * m + 3]);
     }
   }
-  __syncthreads();
+  team_sync<WT>();
 
-  // phase 4: coalesced scatter (store at first touch, read-modify-write otherwise)
-  for (int idx = t; idx < ne * 3 * NP; idx += T) {
-    const int e = idx / (3 * NP);
-    const int rem = idx - e * 3 * NP;
-    const int p = rem / 3;
-    const uint32_t w = reinterpret_cast<const uint32_t*>(smem + e * S + 9 * NP)[p];
-    const size_t gi = 3 * static_cast<size_t>(w & ~kFirstTouchBit) + (rem - 3 * p);
-    const float val = smem[e * S + rem];
-    if (w & kFirstTouchBit)
-      f[gi] = val;
-    else
-      f[gi] += val;
+  // 4. scatter in the gather's coalesced order
+  for (int idx = tl; idx < ne * NP; idx += TEAM) {
+    const int e = idx / NP;
+    const int p = idx - e * NP;
+    const int ln = p / N;
+    const int i = p - ln * N;
+    const float* sb = ts + e * ES;
+    const uint32_t w = reinterpret_cast<const uint32_t*>(sb + 3 * NL * RS)[p];
+    const size_t g3 = 3 * static_cast<size_t>(w & ~kFirstTouchBit);
+    const float* src = sb + ln * RS + 3 * i;
+    if (w & kFirstTouchBit) {
+      f[g3] = src[0];
+      f[g3 + 1] = src[1];
+      f[g3 + 2] = src[2];
+    } else {
+      f[g3] += src[0];
+      f[g3 + 1] += src[1];
+      f[g3 + 2] += src[2];
+    }
   }
 }
 
@@ -263,7 +336,7 @@ int launch_forces_nm(const ForceLaunch& L, cudaStream_t s) {
     if (e != cudaSuccess) return static_cast<int>(e);
     attr_done |= bit;
   }
-  const int grid = (L.e1 - L.e0 + C::E - 1) / C::E;
+  const int grid = (L.e1 - L.e0 + C::EPC - 1) / C::EPC;
   forces_kernel<N, MODE><<<grid, C::T, smem, s>>>(L.rec, L.u, L.f, L.v, L.minv, L.e0, L.e1, L.dt, L.hdt, L.hdt2);
   return static_cast<int>(cudaGetLastError());
 }

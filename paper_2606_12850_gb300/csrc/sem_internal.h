@@ -27,9 +27,10 @@ inline int rec_words(int ngll) {
   return (kRecFields * np + 3) / 4 * 4;  // 16-byte aligned element records
 }
 
-// Position of local point (i, j, k) inside one field of an element record: points are
-// stored i-major so that the NGLL^2 threads owning the xi-lines (j, k) of an element read
-// consecutive words for a fixed i.
+// Position of local point (i, j, k) inside a geometry or material field of an element
+// record: points are stored i-major so that the NGLL^2 threads owning the xi-lines (j, k)
+// of an element read consecutive words for a fixed i. The ibool field keeps the natural
+// order p = i + NGLL*j + NGLL^2*k, which the gather and scatter threads walk.
 inline int rec_pos(int ngll, int i, int j, int k) { return i * ngll * ngll + j + ngll * k; }
 
 // ---- host set-up (sem_setup.cpp) -------------------------------------------------------

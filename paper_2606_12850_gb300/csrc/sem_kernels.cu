@@ -60,7 +60,10 @@ int forces_kernel_smem_bytes(int n) {
   return 0;
 }
 
-int forces_elements_per_cta(int n) { return n >= 2 && n <= 10 ? ((n <= 5 ? 128 : 256) / (n * n)) : 0; }
+int forces_elements_per_cta(int n) {
+  if (n < 2 || n > 10) return 0;
+  return n * n <= 32 ? 4 * (32 / (n * n)) : 256 / (n * n);
+}
 
 // ---------------------------------------------------------------------------------------
 // Newmark corrector pass (Sec. I / V-C explicit second-order Newmark, diagonal mass), used

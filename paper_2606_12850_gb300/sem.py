@@ -65,7 +65,7 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
     """The loaded library (raises if it is missing and ``build_if_missing`` is False)."""
     global _lib
     if _lib is None:
-        path = _build.LIB
+        path = os.environ.get("SEMGB_LIBRARY", _build.LIB)  # alternate build of the same sources
         if not os.path.exists(path):
             if not build_if_missing:
                 raise RuntimeError(f"libsemgb is not built ({path} missing); call "
