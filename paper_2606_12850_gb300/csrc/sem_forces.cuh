@@ -24,25 +24,25 @@ __constant__ float c_w[SEM_NGLL];
 // Force kernel (Sec. II-B matrix-free stiffness action + Sec. IV-C coloured assembly),
 // optionally fused with the Newmark node update.
 //
-// Threads work in teams: one warp per team for NGLL <= 5 (then a team only ever needs
-// __syncwarp, so warps of a CTA drift freely and hide each other's memory latency), the
-// whole CTA for NGLL >= 6. A team holds E = TEAM / NGLL^2 elements of one colour.
+// Threads work in teams: one warp per team for NGLL <= 5 (a team then only needs
+// __syncwarp, so the warps of a CTA drift freely and hide each other's memory latency),
+// the whole CTA for NGLL >= 6. A team holds E = TEAM / NGLL^2 elements of one colour.
 //  1. gather, one thread per local point: consecutive threads take consecutive points p,
 //     so a warp reads whole xi-rows of the global arrays. At a node's first touch in the
 //     colour order the same thread applies the Newmark update of the node (MODE 1:
 //     predictor from a complete state; MODE 2: corrector of the previous step, then the
 //     predictor), so the step needs no separate pass over the global arrays;
-//  2. one thread per xi-line (j, k): the xi-derivative and xi-transposed product stay in
-//     registers; eta and zeta derivatives accumulate whole xi-rows of the shared cube,
-//     read with 128-bit loads (rows are padded to a multiple of 4 floats); Jacobian map,
-//     Hooke stress and fluxes per point;
-//  3. eta and zeta transposed products from the shared flux rows, element forces back
-//     into the thread's own row;
+//  2. one thread per xi-line (j, k): the xi-derivative and the xi-transposed product stay
+//     in registers; eta and zeta derivatives read the shared element cube; Jacobian map,
+//     Hooke stress and fluxes per point, eta/zeta fluxes to shared memory;
+//  3. eta and zeta transposed products from the shared fluxes; element forces back into
+//     the cube slots;
 //  4. scatter in the gather's order: a store at the node's first touch, a
 //     read-modify-write otherwise (elements of one launch share no node: no atomics,
 //     fixed summation order).
-// Shared memory per element: u (then F), eta-flux and zeta-flux as [NGLL^2 rows][RS]
-// (row = xi-line, [i][3] inside), ibool as [NP].
+// Shared memory per element: u (then F) as [NP][3], eta/zeta fluxes as [NP][6], ibool as
+// [NP]; with several elements per warp the element stride is padded so that they fall in
+// disjoint banks (offsets chosen by simulating the warp's access patterns).
 // ---------------------------------------------------------------------------------------
 template <int N>
 struct ForceCfg {
@@ -54,14 +54,11 @@ struct ForceCfg {
   static constexpr int TEAMS = T / TEAM;              // teams per CTA
   static constexpr int E = TEAM / NL;                 // elements per team
   static constexpr int EPC = TEAMS * E;               // elements per CTA
-  static constexpr int RS = (3 * N + 3) / 4 * 4;      // floats per padded xi-row
-  static constexpr int RV = RS / 4;                   // float4 per row
-  static constexpr int NPA = (NP + 3) / 4 * 4;
-  static constexpr int ES = 3 * NL * RS + NPA + (E > 1 ? 4 : 0);  // floats per element
+  static constexpr int RES = N == 2 ? 7 : N == 3 ? 17 : N == 5 ? 23 : N == 7 ? 5 : N == 9 ? 11 : N == 8 ? 0 : 1;
+  static constexpr int ES = 10 * NP + ((RES - 10 * NP) % 32 + 32) % 32;  // floats per element
   static constexpr int TS = E * ES;                   // floats per team
   static constexpr int SMEM_FLOATS = TEAMS * TS;
   static constexpr int REC = (kRecFields * NP + 3) / 4 * 4;
-  static constexpr bool LINE_VEC = N <= 7;            // whole-row register accumulation
 };
 
 template <bool WARP>
@@ -70,19 +67,6 @@ __device__ __forceinline__ void team_sync() {
     __syncwarp();
   else
     __syncthreads();
-}
-
-template <int N>
-__device__ __forceinline__ void load_row(const float* rowp, float (&row)[ForceCfg<N>::RS]) {
-  const float4* r4 = reinterpret_cast<const float4*>(rowp);
-#pragma unroll
-  for (int m = 0; m < ForceCfg<N>::RV; ++m) {
-    const float4 q = r4[m];
-    row[4 * m] = q.x;
-    row[4 * m + 1] = q.y;
-    row[4 * m + 2] = q.z;
-    row[4 * m + 3] = q.w;
-  }
 }
 
 #ifndef SEM_FORCES_MIN_BLOCKS
@@ -94,7 +78,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, SEM_FORCES_MIN_BLOCKS)
     forces_kernel(const float* __restrict__ rec, float* u, float* __restrict__ f, float* __restrict__ v,
                   const float* __restrict__ minv, int e0, int e1, float dt, float hdt, float hdt2) {
   using C = ForceCfg<N>;
-  constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES, RS = C::RS;
+  constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
   constexpr bool WT = C::WARP_TEAM;
   extern __shared__ float4 smem4[];
   const float* __restrict__ H = c_h;
@@ -105,20 +89,17 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, SEM_FORCES_MIN_BLOCKS)
   const int tl = threadIdx.x - team * TEAM;
   const int ebase = e0 + (blockIdx.x * C::TEAMS + team) * E;
   const int ne = min(E, e1 - ebase);
-  if (WT && ne <= 0) return;  // a warp team with no element (never a CTA team)
+  if (WT && ne <= 0) return;  // a warp team without elements (never a CTA team)
   float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
 
   // 1. gather (+ Newmark at first touch), one thread per local point
   for (int idx = tl; idx < ne * NP; idx += TEAM) {
     const int le = idx / NP;
     const int p = idx - le * NP;
-    const int line = p / N;
-    const int i = p - line * N;
     float* eb = ts + le * ES;
     const uint32_t w = __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + p));
-    reinterpret_cast<uint32_t*>(eb + 3 * NL * RS)[p] = w;
+    reinterpret_cast<uint32_t*>(eb + 9 * NP)[p] = w;
     const size_t g = w & ~kFirstTouchBit;
-    float* dst = eb + line * RS + 3 * i;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t gi = 3 * g + c;
@@ -133,7 +114,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, SEM_FORCES_MIN_BLOCKS)
         u[gi] = uu;
         v[gi] = vv;
       }
-      dst[c] = uu;
+      eb[3 * p + c] = uu;
     }
   }
   team_sync<WT>();
@@ -144,123 +125,98 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, SEM_FORCES_MIN_BLOCKS)
   const int j = line % N;
   const int k = line / N;
   const bool active = le < ne;
-  float* eb = ts + (active ? le : 0) * ES;
-  float* rows_u = eb;
-  float* rows_te = eb + NL * RS;
-  float* rows_tz = eb + 2 * NL * RS;
+  float* su = ts + (active ? le : 0) * ES;  // [NP][3]
+  float* st = su + 3 * NP;                   // [NP][6]
   const float* __restrict__ r = rec + static_cast<size_t>(ebase + (active ? le : 0)) * REC;
 
-  float fxi[3 * N];
+  float ux[N], uy[N], uz[N];
 #pragma unroll
-  for (int q = 0; q < 3 * N; ++q) fxi[q] = 0.f;
-  {
-    float uo[RS];
-    load_row<N>(rows_u + line * RS, uo);
-    float hj[N], hk[N];
+  for (int i = 0; i < N; ++i) {
+    const int p = i + N * line;
+    ux[i] = su[3 * p];
+    uy[i] = su[3 * p + 1];
+    uz[i] = su[3 * p + 2];
+  }
+  float hj[N], hk[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    hj[l] = H[j * N + l];
+    hk[l] = H[k * N + l];
+  }
+  float fx[N], fy[N], fz[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) fx[i] = fy[i] = fz[i] = 0.f;
+
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
+    float det_x = 0.f, det_y = 0.f, det_z = 0.f;
+    float dze_x = 0.f, dze_y = 0.f, dze_z = 0.f;
 #pragma unroll
     for (int l = 0; l < N; ++l) {
-      hj[l] = H[j * N + l];
-      hk[l] = H[k * N + l];
+      const float h = H[i * N + l];
+      dxi_x += h * ux[l];
+      dxi_y += h * uy[l];
+      dxi_z += h * uz[l];
+      const int pe = 3 * (i + N * (l + N * k));
+      det_x += hj[l] * su[pe];
+      det_y += hj[l] * su[pe + 1];
+      det_z += hj[l] * su[pe + 2];
+      const int pz = 3 * (i + N * (j + N * l));
+      dze_x += hk[l] * su[pz];
+      dze_y += hk[l] * su[pz + 1];
+      dze_z += hk[l] * su[pz + 2];
     }
-    float deta[C::LINE_VEC ? 3 * N : 1], dzet[C::LINE_VEC ? 3 * N : 1];
-    if (C::LINE_VEC) {
+    const int q = i * NL + line;
+    float G[9];
 #pragma unroll
-      for (int q = 0; q < 3 * N; ++q) deta[q] = dzet[q] = 0.f;
+    for (int a = 0; a < 9; ++a) G[a] = active ? __ldg(r + (kG + a) * NP + q) : 0.f;
+    const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
+    const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
+    const float mu = active ? __ldg(r + kMu * NP + q) : 0.f;
+
+    const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
+    const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
+    const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
+    const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
+    const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
+    const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
+    const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
+    const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
+    const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
+
+    const float lam = kappa - (2.f / 3.f) * mu;
+    const float tr = uxx + uyy + uzz;
+    const float sxx = lam * tr + 2.f * mu * uxx;
+    const float syy = lam * tr + 2.f * mu * uyy;
+    const float szz = lam * tr + 2.f * mu * uzz;
+    const float sxy = mu * (uxy + uyx);
+    const float sxz = mu * (uxz + uzx);
+    const float syz = mu * (uyz + uzy);
+
+    const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
+    const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
+    const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
 #pragma unroll
-      for (int l = 0; l < N; ++l) {
-        float row[RS];
-        load_row<N>(rows_u + (l + N * k) * RS, row);
-#pragma unroll
-        for (int q = 0; q < 3 * N; ++q) deta[q] += hj[l] * row[q];
-        load_row<N>(rows_u + (j + N * l) * RS, row);
-#pragma unroll
-        for (int q = 0; q < 3 * N; ++q) dzet[q] += hk[l] * row[q];
-      }
+    for (int ip = 0; ip < N; ++ip) {
+      const float hw = HW[i * N + ip];
+      fx[ip] += hw * txi_x;
+      fy[ip] += hw * txi_y;
+      fz[ip] += hw * txi_z;
     }
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        const float h = H[i * N + l];
-        dxi_x += h * uo[3 * l];
-        dxi_y += h * uo[3 * l + 1];
-        dxi_z += h * uo[3 * l + 2];
-      }
-      float det_x, det_y, det_z, dze_x, dze_y, dze_z;
-      if (C::LINE_VEC) {
-        det_x = deta[3 * i];
-        det_y = deta[3 * i + 1];
-        det_z = deta[3 * i + 2];
-        dze_x = dzet[3 * i];
-        dze_y = dzet[3 * i + 1];
-        dze_z = dzet[3 * i + 2];
-      } else {
-        det_x = det_y = det_z = dze_x = dze_y = dze_z = 0.f;
-#pragma unroll
-        for (int l = 0; l < N; ++l) {
-          const float* pe = rows_u + (l + N * k) * RS + 3 * i;
-          det_x += hj[l] * pe[0];
-          det_y += hj[l] * pe[1];
-          det_z += hj[l] * pe[2];
-          const float* pz = rows_u + (j + N * l) * RS + 3 * i;
-          dze_x += hk[l] * pz[0];
-          dze_y += hk[l] * pz[1];
-          dze_z += hk[l] * pz[2];
-        }
-      }
-      const int q = i * NL + line;
-      float G[9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) G[a] = active ? __ldg(r + (kG + a) * NP + q) : 0.f;
-      const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
-      const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
-      const float mu = active ? __ldg(r + kMu * NP + q) : 0.f;
-
-      const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
-      const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
-      const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
-      const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
-      const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
-      const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
-      const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
-      const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
-      const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
-
-      const float lam = kappa - (2.f / 3.f) * mu;
-      const float tr = uxx + uyy + uzz;
-      const float sxx = lam * tr + 2.f * mu * uxx;
-      const float syy = lam * tr + 2.f * mu * uyy;
-      const float szz = lam * tr + 2.f * mu * uzz;
-      const float sxy = mu * (uxy + uyx);
-      const float sxz = mu * (uxz + uzx);
-      const float syz = mu * (uyz + uzy);
-
-      const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
-      const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
-      const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
-#pragma unroll
-      for (int ip = 0; ip < N; ++ip) {
-        const float hw = HW[i * N + ip];
-        fxi[3 * ip] += hw * txi_x;
-        fxi[3 * ip + 1] += hw * txi_y;
-        fxi[3 * ip + 2] += hw * txi_z;
-      }
-      if (active) {
-        float* te = rows_te + line * RS + 3 * i;
-        te[0] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
-        te[1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
-        te[2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
-        float* tz = rows_tz + line * RS + 3 * i;
-        tz[0] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
-        tz[1] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
-        tz[2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
-      }
+    if (active) {
+      const int p6 = 6 * (i + N * line);
+      st[p6 + 0] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
+      st[p6 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
+      st[p6 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
+      st[p6 + 3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
+      st[p6 + 4] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
+      st[p6 + 5] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
     }
   }
   team_sync<WT>();
 
-  // 3. eta and zeta transposed products; forces into the thread's own u row
+  // 3. eta and zeta transposed products; forces into the (now free) u slots
   {
     float hwj[N], hwk[N];
 #pragma unroll
@@ -268,34 +224,28 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, SEM_FORCES_MIN_BLOCKS)
       hwj[l] = HW[l * N + j];
       hwk[l] = HW[l * N + k];
     }
-    float eacc[3 * N], zacc[3 * N];
-#pragma unroll
-    for (int q = 0; q < 3 * N; ++q) eacc[q] = zacc[q] = 0.f;
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      float row[RS];
-      load_row<N>(rows_te + (l + N * k) * RS, row);
-#pragma unroll
-      for (int q = 0; q < 3 * N; ++q) eacc[q] += hwj[l] * row[q];
-      load_row<N>(rows_tz + (j + N * l) * RS, row);
-#pragma unroll
-      for (int q = 0; q < 3 * N; ++q) zacc[q] += hwk[l] * row[q];
-    }
     const float wj = W[j], wk = W[k];
-    if (active) {
-      float out[RS];
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const float wi = W[i];
+    for (int i = 0; i < N; ++i) {
+      float ex = 0.f, ey = 0.f, ez = 0.f, zx = 0.f, zy = 0.f, zz = 0.f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-          out[3 * i + c] = -(wj * wk * fxi[3 * i + c] + wi * wk * eacc[3 * i + c] + wi * wj * zacc[3 * i + c]);
+      for (int l = 0; l < N; ++l) {
+        const int pe = 6 * (i + N * (l + N * k));
+        ex += hwj[l] * st[pe];
+        ey += hwj[l] * st[pe + 1];
+        ez += hwj[l] * st[pe + 2];
+        const int pz = 6 * (i + N * (j + N * l)) + 3;
+        zx += hwk[l] * st[pz];
+        zy += hwk[l] * st[pz + 1];
+        zz += hwk[l] * st[pz + 2];
       }
-#pragma unroll
-      for (int q = 3 * N; q < RS; ++q) out[q] = 0.f;
-      float4* o4 = reinterpret_cast<float4*>(rows_u + line * RS);
-#pragma unroll
-      for (int m = 0; m < C::RV; ++m) o4[m] = make_float4(out[4 * m], out[4 * m + 1], out[4 * m + 2], out[4 * m + 3]);
+      const float wi = W[i];
+      if (active) {
+        const int p = 3 * (i + N * line);
+        su[p] = -(wj * wk * fx[i] + wi * wk * ex + wi * wj * zx);
+        su[p + 1] = -(wj * wk * fy[i] + wi * wk * ey + wi * wj * zy);
+        su[p + 2] = -(wj * wk * fz[i] + wi * wk * ez + wi * wj * zz);
+      }
     }
   }
   team_sync<WT>();
@@ -304,12 +254,10 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, SEM_FORCES_MIN_BLOCKS)
   for (int idx = tl; idx < ne * NP; idx += TEAM) {
     const int e = idx / NP;
     const int p = idx - e * NP;
-    const int ln = p / N;
-    const int i = p - ln * N;
     const float* sb = ts + e * ES;
-    const uint32_t w = reinterpret_cast<const uint32_t*>(sb + 3 * NL * RS)[p];
+    const uint32_t w = reinterpret_cast<const uint32_t*>(sb + 9 * NP)[p];
     const size_t g3 = 3 * static_cast<size_t>(w & ~kFirstTouchBit);
-    const float* src = sb + ln * RS + 3 * i;
+    const float* src = sb + 3 * p;
     if (w & kFirstTouchBit) {
       f[g3] = src[0];
       f[g3 + 1] = src[1];
