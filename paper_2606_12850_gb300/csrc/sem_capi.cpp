@@ -156,20 +156,12 @@ int set_device(sem_ctx* c) {
   return SEM_OK;
 }
 
-// f = -K u over all colours in order (Sec. IV-C: colour by colour, no atomics). With
-// mode 1 or 2 the force kernel also applies the Newmark update of each node at its first
-// touch (see launch_forces); u and f are then the context's own state arrays.
-int forces_all_colors(sem_ctx* c, const float* u, float* f, int mode) {
+// f = -K u over all colours in order (Sec. IV-C: colour by colour, no atomics).
+int forces_all_colors(sem_ctx* c, const float* u, float* f) {
   ForceLaunch L{};
   L.rec = c->d_rec;
-  L.u = const_cast<float*>(u);  // written only in modes 1 and 2 (the context's own array)
+  L.u = u;
   L.f = f;
-  L.v = c->d_v;
-  L.minv = c->d_minv;
-  L.mode = mode;
-  L.dt = static_cast<float>(c->dt);
-  L.hdt = static_cast<float>(0.5 * c->dt);
-  L.hdt2 = static_cast<float>(0.5 * c->dt * c->dt);
   for (int col = 0; col < c->ncolors; ++col) {
     L.e0 = c->color_off[col];
     L.e1 = c->color_off[col + 1];
@@ -178,17 +170,22 @@ int forces_all_colors(sem_ctx* c, const float* u, float* f, int mode) {
   return SEM_OK;
 }
 
-// One time step: the force sweep with the Newmark update fused at first touch (mode 2:
-// corrector of step n-1 then predictor of step n; mode 1 for the first step from a
-// complete state), then sources and receivers.
-int enqueue_step(sem_ctx* c, int mode) {
-  int r = forces_all_colors(c, c->d_u, c->d_a, mode);
+// One time step in the "pending" representation (a holds M a_raw of the previous step, v
+// the half-step velocity): corrector(n-1) fused with predictor(n), forces, sources,
+// receivers. The first step from a complete state uses the predictor alone.
+int enqueue_step(sem_ctx* c, bool first) {
+  const DevProblem p = problem(c);
+  if (first)
+    SEM_LAUNCH(c, launch_predictor(p, c->stream));
+  else
+    SEM_LAUNCH(c, launch_fused_newmark(p, c->stream));
+  int r = forces_all_colors(c, c->d_u, c->d_a);
   if (r) return r;
-  SEM_LAUNCH(c, launch_sources_record(problem(c), c->stream));
+  SEM_LAUNCH(c, launch_sources_record(p, c->stream));
   return SEM_OK;
 }
-int enqueue_pending_step(sem_ctx* c) { return enqueue_step(c, 2); }
-int enqueue_first_step(sem_ctx* c) { return enqueue_step(c, 1); }
+int enqueue_pending_step(sem_ctx* c) { return enqueue_step(c, false); }
+int enqueue_first_step(sem_ctx* c) { return enqueue_step(c, true); }
 
 int build_graph(sem_ctx* c) {
   drop_graph(c);
@@ -681,7 +678,7 @@ int sem_apply_stiffness(sem_ctx* c, const float* u_dev, float* f_dev) {
   if (a < b + bytes && b < a + bytes) return fail(c, SEM_EINVAL, "u_dev and f_dev overlap");
   int r = set_device(c);
   if (r) return r;
-  return forces_all_colors(c, u_dev, f_dev, 0);
+  return forces_all_colors(c, u_dev, f_dev);
 }
 
 int sem_energy(sem_ctx* c, double* out) {
@@ -696,7 +693,7 @@ int sem_energy(sem_ctx* c, double* out) {
       return r;
     SEM_CUDA(c, cudaMemsetAsync(c->d_f, 0, nf * sizeof(float), c->stream));
   }
-  if ((r = forces_all_colors(c, c->d_u, c->d_f, 0))) return r;
+  if ((r = forces_all_colors(c, c->d_u, c->d_f))) return r;
   SEM_LAUNCH(c, launch_energy_partials(c->d_u, c->d_v, c->d_f, c->d_minv, c->nglob_pad, c->d_partials, kEnergyBlocks,
                                        c->stream));
   std::vector<double> part(2 * kEnergyBlocks);

@@ -21,17 +21,14 @@ __constant__ float c_hw[SEM_NGLL * SEM_NGLL];  // [l*n + i] = w_l * hprime[l][i]
 __constant__ float c_w[SEM_NGLL];
 
 // ---------------------------------------------------------------------------------------
-// Force kernel (Sec. II-B matrix-free stiffness action + Sec. IV-C coloured assembly),
-// optionally fused with the Newmark node update.
+// Force kernel (Sec. II-B matrix-free stiffness action + Sec. IV-C coloured assembly).
 //
 // Threads work in teams: one warp per team for NGLL <= 5 (a team then only needs
 // __syncwarp, so the warps of a CTA drift freely and hide each other's memory latency),
 // the whole CTA for NGLL >= 6. A team holds E = TEAM / NGLL^2 elements of one colour.
 //  1. gather, one thread per local point: consecutive threads take consecutive points p,
-//     so a warp reads whole xi-rows of the global arrays. At a node's first touch in the
-//     colour order the same thread applies the Newmark update of the node (MODE 1:
-//     predictor from a complete state; MODE 2: corrector of the previous step, then the
-//     predictor), so the step needs no separate pass over the global arrays;
+//     so a warp reads whole xi-rows of the global arrays (instead of one scattered row
+//     per thread);
 //  2. one thread per xi-line (j, k): the xi-derivative and the xi-transposed product stay
 //     in registers; eta and zeta derivatives read the shared element cube; Jacobian map,
 //     Hooke stress and fluxes per point, eta/zeta fluxes to shared memory;
@@ -59,6 +56,14 @@ struct ForceCfg {
   static constexpr int TS = E * ES;                   // floats per team
   static constexpr int SMEM_FLOATS = TEAMS * TS;
   static constexpr int REC = (kRecFields * NP + 3) / 4 * 4;
+  // CTAs per SM the register allocation must allow, from a GB300 sweep of force-sweep time
+  // against the register cap: 64 registers for NGLL <= 5, 85 for NGLL = 6-7, 128 for
+  // NGLL = 8, no cap above (the larger live set of the NGLL = 9-10 contractions wins).
+#ifdef SEM_FORCES_MIN_BLOCKS
+  static constexpr int MIN_BLOCKS = SEM_FORCES_MIN_BLOCKS;
+#else
+  static constexpr int MIN_BLOCKS = WARP_TEAM ? 8 : (N <= 7 ? 3 : (N == 8 ? 2 : 1));
+#endif
 };
 
 template <bool WARP>
@@ -69,14 +74,10 @@ __device__ __forceinline__ void team_sync() {
     __syncthreads();
 }
 
-#ifndef SEM_FORCES_MIN_BLOCKS
-#define SEM_FORCES_MIN_BLOCKS 1
-#endif
-
-template <int N, int MODE>
-__global__ void __launch_bounds__(ForceCfg<N>::T, SEM_FORCES_MIN_BLOCKS)
-    forces_kernel(const float* __restrict__ rec, float* u, float* __restrict__ f, float* __restrict__ v,
-                  const float* __restrict__ minv, int e0, int e1, float dt, float hdt, float hdt2) {
+template <int N>
+__global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
+    forces_kernel(const float* __restrict__ rec, const float* __restrict__ u, float* __restrict__ f, int e0,
+                  int e1) {
   using C = ForceCfg<N>;
   constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
   constexpr bool WT = C::WARP_TEAM;
@@ -92,30 +93,17 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, SEM_FORCES_MIN_BLOCKS)
   if (WT && ne <= 0) return;  // a warp team without elements (never a CTA team)
   float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
 
-  // 1. gather (+ Newmark at first touch), one thread per local point
+  // 1. gather, one thread per local point
   for (int idx = tl; idx < ne * NP; idx += TEAM) {
     const int le = idx / NP;
     const int p = idx - le * NP;
     float* eb = ts + le * ES;
     const uint32_t w = __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + p));
     reinterpret_cast<uint32_t*>(eb + 9 * NP)[p] = w;
-    const size_t g = w & ~kFirstTouchBit;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const size_t gi = 3 * g + c;
-      float uu = u[gi];
-      if (MODE != 0 && (w & kFirstTouchBit)) {
-        float acc = f[gi];
-        if (MODE == 2) acc *= minv[g];
-        float vv = v[gi];
-        if (MODE == 2) vv += hdt * acc;  // corrector of the previous step
-        uu += dt * vv + hdt2 * acc;      // predictor
-        vv += hdt * acc;
-        u[gi] = uu;
-        v[gi] = vv;
-      }
-      eb[3 * p + c] = uu;
-    }
+    const size_t g3 = 3 * static_cast<size_t>(w & ~kFirstTouchBit);
+    eb[3 * p] = __ldg(u + g3);
+    eb[3 * p + 1] = __ldg(u + g3 + 1);
+    eb[3 * p + 2] = __ldg(u + g3 + 2);
   }
   team_sync<WT>();
 
@@ -270,9 +258,8 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, SEM_FORCES_MIN_BLOCKS)
   }
 }
 
-template <int N, int MODE>
-int launch_forces_nm(const ForceLaunch& L, cudaStream_t s) {
-  using C = ForceCfg<N>;
+int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
+  using C = ForceCfg<SEM_NGLL>;
   if (L.e1 <= L.e0) return 0;
   static unsigned long long attr_done = 0;  // one bit per device ordinal
   const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
@@ -280,15 +267,14 @@ int launch_forces_nm(const ForceLaunch& L, cudaStream_t s) {
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_done & bit)) {
-    cudaError_t e = cudaFuncSetAttribute(forces_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(forces_kernel<SEM_NGLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return static_cast<int>(e);
     attr_done |= bit;
   }
   const int grid = (L.e1 - L.e0 + C::EPC - 1) / C::EPC;
-  forces_kernel<N, MODE><<<grid, C::T, smem, s>>>(L.rec, L.u, L.f, L.v, L.minv, L.e0, L.e1, L.dt, L.hdt, L.hdt2);
+  forces_kernel<SEM_NGLL><<<grid, C::T, smem, s>>>(L.rec, L.u, L.f, L.e0, L.e1);
   return static_cast<int>(cudaGetLastError());
 }
-
 
 }  // namespace
 
@@ -312,13 +298,7 @@ int SEM_CAT(upload_basis_, SEM_NGLL)(const double* w, const double* h, void* str
 }
 
 int SEM_CAT(launch_forces_, SEM_NGLL)(const ForceLaunch& L, void* stream) {
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  switch (L.mode) {
-    case 0: return launch_forces_nm<SEM_NGLL, 0>(L, s);
-    case 1: return launch_forces_nm<SEM_NGLL, 1>(L, s);
-    case 2: return launch_forces_nm<SEM_NGLL, 2>(L, s);
-    default: return static_cast<int>(cudaErrorInvalidValue);
-  }
+  return launch_forces_n(L, static_cast<cudaStream_t>(stream));
 }
 
 int SEM_CAT(forces_smem_bytes_, SEM_NGLL)() { return ForceCfg<SEM_NGLL>::SMEM_FLOATS * 4; }

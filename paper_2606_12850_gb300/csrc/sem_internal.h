@@ -80,25 +80,21 @@ struct DevProblem {
 // Copies hprime, hprime*w and w for this ngll into the kernels' constant banks.
 int upload_basis(int ngll, const double* w, const double* hprime, void* stream);
 
-// One colour's worth of elements [e0, e1) of the colour-sorted order: f (=|+=) -K u.
-// mode 0: forces only (u read-only); mode 1: at each node's first touch apply the Newmark
-// predictor from a complete state (f holds the acceleration); mode 2: at first touch apply
-// the corrector of the previous step (f holds M a_raw) then the predictor.
+// One colour's worth of elements [e0, e1) of the colour-sorted order: f (=|+=) -K u; a node
+// is stored at its first touch in colour order and accumulated afterwards.
 struct ForceLaunch {
   const float* rec;
-  float* u;
+  const float* u;
   float* f;
-  float* v;
-  const float* minv;
   int e0, e1;
-  int mode;
-  float dt, hdt, hdt2;
 };
 int launch_forces(int ngll, const ForceLaunch& launch, void* stream);
 int forces_kernel_smem_bytes(int ngll);
 int forces_elements_per_cta(int ngll);
 
 int launch_set_ctl(DevCtl* ctl, long long step, int ncols, float* seis, void* stream);
+int launch_predictor(const DevProblem& p, void* stream);
+int launch_fused_newmark(const DevProblem& p, void* stream);
 int launch_corrector(const DevProblem& p, void* stream);
 int launch_sources_record(const DevProblem& p, void* stream);
 int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv,

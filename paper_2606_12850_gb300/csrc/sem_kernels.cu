@@ -66,8 +66,7 @@ int forces_elements_per_cta(int n) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Newmark corrector pass (Sec. I / V-C explicit second-order Newmark, diagonal mass), used
-// to complete the state when it is read; the per-step updates run inside the force kernel.
+// Newmark streaming passes (Sec. I / V-C explicit second-order Newmark, diagonal mass).
 // Fields are [nglob_pad][3] float32 with nglob_pad % 4 == 0: a thread owns four nodes,
 // i.e. three float4 of each field and one float4 of the inverse mass.
 // ---------------------------------------------------------------------------------------
@@ -75,6 +74,74 @@ __device__ __forceinline__ float4 mass_lanes(const float4 m, int part) {
   // the three float4 words of 4 nodes (x0 y0 z0 x1 | y1 z1 x2 y2 | z2 x3 y3 z3)
   return part == 0 ? make_float4(m.x, m.x, m.x, m.y)
                    : (part == 1 ? make_float4(m.y, m.y, m.z, m.z) : make_float4(m.z, m.w, m.w, m.w));
+}
+
+// Predictor from a complete state (first step): u += dt v + dt^2/2 a ; v += dt/2 a.
+// All loads of a thread are issued before its arithmetic so that each thread keeps nine
+// 16-byte requests in flight.
+__global__ void predictor_kernel(float4* __restrict__ u, float4* __restrict__ v, const float4* __restrict__ a,
+                                 int n4, float dt, float hdt, float hdt2) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
+    float4 av[3], vv[3], uv[3];
+#pragma unroll
+    for (int part = 0; part < 3; ++part) {
+      av[part] = a[3 * t + part];
+      vv[part] = v[3 * t + part];
+      uv[part] = u[3 * t + part];
+    }
+#pragma unroll
+    for (int part = 0; part < 3; ++part) {
+      uv[part].x += dt * vv[part].x + hdt2 * av[part].x;
+      uv[part].y += dt * vv[part].y + hdt2 * av[part].y;
+      uv[part].z += dt * vv[part].z + hdt2 * av[part].z;
+      uv[part].w += dt * vv[part].w + hdt2 * av[part].w;
+      vv[part].x += hdt * av[part].x;
+      vv[part].y += hdt * av[part].y;
+      vv[part].z += hdt * av[part].z;
+      vv[part].w += hdt * av[part].w;
+      u[3 * t + part] = uv[part];
+      v[3 * t + part] = vv[part];
+    }
+  }
+}
+
+// Corrector of step n-1 fused with the predictor of step n:
+//   a = M^-1 a_raw ; v = v_half + dt/2 a ; u += dt v + dt^2/2 a ; v_half = v + dt/2 a
+// a_raw stays in place: the next force sweep overwrites it at each node's first touch.
+__global__ void fused_newmark_kernel(float4* __restrict__ u, float4* __restrict__ v,
+                                     const float4* __restrict__ a, const float4* __restrict__ minv, int n4,
+                                     float dt, float hdt, float hdt2) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
+    const float4 m = minv[t];
+    float4 ar[3], vv[3], uv[3];
+#pragma unroll
+    for (int part = 0; part < 3; ++part) {
+      ar[part] = a[3 * t + part];
+      vv[part] = v[3 * t + part];
+      uv[part] = u[3 * t + part];
+    }
+#pragma unroll
+    for (int part = 0; part < 3; ++part) {
+      const float4 mm = mass_lanes(m, part);
+      const float ax = ar[part].x * mm.x, ay = ar[part].y * mm.y, az = ar[part].z * mm.z, aw = ar[part].w * mm.w;
+      float4 w = vv[part];
+      w.x += hdt * ax;
+      w.y += hdt * ay;
+      w.z += hdt * az;
+      w.w += hdt * aw;
+      float4 x = uv[part];
+      x.x += dt * w.x + hdt2 * ax;
+      x.y += dt * w.y + hdt2 * ay;
+      x.z += dt * w.z + hdt2 * az;
+      x.w += dt * w.w + hdt2 * aw;
+      w.x += hdt * ax;
+      w.y += hdt * ay;
+      w.z += hdt * az;
+      w.w += hdt * aw;
+      u[3 * t + part] = x;
+      v[3 * t + part] = w;
+    }
+  }
 }
 
 // Corrector alone (completes the state): a = M^-1 a_raw ; v = v_half + dt/2 a
@@ -106,6 +173,23 @@ static int stream_grid(int n4) {
   const int per = 256;
   int g = (n4 + per - 1) / per;
   return g < 1 ? 1 : g;
+}
+
+int launch_predictor(const DevProblem& p, void* stream) {
+  const int n4 = p.nglob_pad / 4;
+  predictor_kernel<<<stream_grid(n4), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<float4*>(p.u), reinterpret_cast<float4*>(p.v), reinterpret_cast<const float4*>(p.a), n4,
+      static_cast<float>(p.dt), static_cast<float>(0.5 * p.dt), static_cast<float>(0.5 * p.dt * p.dt));
+  return static_cast<int>(cudaGetLastError());
+}
+
+int launch_fused_newmark(const DevProblem& p, void* stream) {
+  const int n4 = p.nglob_pad / 4;
+  fused_newmark_kernel<<<stream_grid(n4), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<float4*>(p.u), reinterpret_cast<float4*>(p.v), reinterpret_cast<const float4*>(p.a),
+      reinterpret_cast<const float4*>(p.minv), n4, static_cast<float>(p.dt), static_cast<float>(0.5 * p.dt),
+      static_cast<float>(0.5 * p.dt * p.dt));
+  return static_cast<int>(cudaGetLastError());
 }
 
 int launch_corrector(const DevProblem& p, void* stream) {
