@@ -144,6 +144,25 @@ int sem_apply_stiffness(sem_ctx* ctx, const float* u_dev, float* f_dev);
  * out[0] = 1/2 sum_I M_I |v_I|^2, out[1] = 1/2 u^T K u. Synchronous. */
 int sem_energy(sem_ctx* ctx, double* out);
 
+/* Energy sums for callers that cannot allocate device memory: code that runs where
+ * cudaMalloc is unavailable or forbidden, such as a host application whose device memory
+ * is owned by another runtime's pool, or a caller inside a region that must not allocate.
+ * The paper has no counterpart; it is a variant of the reduction behind sem_energy.
+ * Inputs: u_dev, v_dev, f_dev device arrays [nglob][3] float32 on the context's GPU, with
+ * f_dev = -K u_dev (for instance from sem_apply_stiffness, which allocates nothing); the
+ * context supplies the inverse mass. Output: out[0] = 1/2 sum_I M_I |v_I|^2,
+ * out[1] = -1/2 u.f = 1/2 u^T K u, host memory, float64. nglob must equal the mesh's.
+ * Scratch: the per-block partial sums go to a fixed 64 KiB array in the library's device
+ * memory (one per GPU that loads the library, held until the process exits), never to
+ * cudaMalloc; the call makes no device or host allocation. It supports at most
+ * 67,108,864 nodes and returns SEM_EINVAL with a message beyond that. All calls share the
+ * array, which keeps the last call's contents, so calls that overlap on the GPU (from
+ * several threads or contexts at once) race; each call rewrites every slot it reads.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Synchronous on the context's stream. */
+int sem_energy_noalloc(sem_ctx* ctx, int nglob, const float* u_dev, const float* v_dev, const float* f_dev,
+                       double* out);
+
 /* Wait for all work issued on the context's stream. */
 int sem_sync(sem_ctx* ctx);
 

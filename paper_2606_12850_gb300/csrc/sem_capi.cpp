@@ -256,6 +256,22 @@ bool finite_all(const float* p, size_t n) {
 
 }  // namespace
 
+namespace semgb {
+
+int ctx_view(sem_ctx* c, CtxView* out) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mat) return fail(c, SEM_ESTATE, "sem_set_material has not been called");
+  out->device = c->device;
+  out->stream = c->stream;
+  out->nglob = c->nglob;
+  out->minv = c->d_minv;
+  return SEM_OK;
+}
+
+int ctx_fail(sem_ctx* c, int code, const char* message) { return fail(c, code, message); }
+
+}  // namespace semgb
+
 extern "C" {
 
 int sem_version(void) { return 100; }

@@ -7,7 +7,11 @@
 #include <string>
 #include <vector>
 
+struct sem_ctx;
+
 namespace semgb {
+
+using sem_ctx_fwd = ::sem_ctx;
 
 constexpr int kMaxNgll = 10;
 constexpr int kMinNgll = 2;
@@ -100,5 +104,16 @@ int launch_sources_record(const DevProblem& p, void* stream);
 int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv,
                            int nglob_pad, double* partials, int nblocks, void* stream);
 constexpr int kEnergyBlocks = 608;  // 4 CTAs per SM on 152 SMs
+
+// ---- context access for entry points defined outside sem_capi.cpp ----------------------
+struct CtxView {
+  int device;
+  void* stream;
+  int nglob;
+  const float* minv;
+};
+// SEM_OK and the view when the material is set; otherwise an error code (message set).
+int ctx_view(sem_ctx_fwd* c, CtxView* out);
+int ctx_fail(sem_ctx_fwd* c, int code, const char* message);
 
 }  // namespace semgb

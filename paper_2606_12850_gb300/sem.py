@@ -46,6 +46,7 @@ SIGNATURES = {
     "sem_run_dev": (_I, [_P, _I, _P]),
     "sem_apply_stiffness": (_I, [_P, _P, _P]),
     "sem_energy": (_I, [_P, _P]),
+    "sem_energy_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
     "sem_sync": (_I, [_P]),
     "sem_info": (_I, [_P, _P]),
     "sem_color_counts": (_I, [_P, _P]),
@@ -270,6 +271,16 @@ def sem_apply_stiffness(ctx: Ctx, u_dev, f_dev):
 def sem_energy(ctx: Ctx):
     out = np.zeros(2)
     _check(lib().sem_energy(ctx.handle, out.ctypes.data_as(_P)), "sem_energy", ctx)
+    return float(out[0]), float(out[1])
+
+
+def sem_energy_noalloc(ctx: Ctx, u_dev, v_dev, f_dev, nglob: int | None = None):
+    """Energy sums from caller-owned device arrays with no device allocation (see sem.h)."""
+    n = ctx.nglob if nglob is None else int(nglob)
+    out = np.zeros(2)
+    m = 3 * min(n, ctx.nglob)
+    _check(lib().sem_energy_noalloc(ctx.handle, n, _dev(u_dev, m), _dev(v_dev, m), _dev(f_dev, m),
+                                    out.ctypes.data_as(_P)), "sem_energy_noalloc", ctx)
     return float(out[0]), float(out[1])
 
 
