@@ -37,8 +37,9 @@ __constant__ float c_w[SEM_NGLL];
 //  4. scatter in the gather's order: a store at the node's first touch, a
 //     read-modify-write otherwise (elements of one launch share no node: no atomics,
 //     fixed summation order).
-// Shared memory per element: u (then F) as [NP][3], eta/zeta fluxes as [NP][6], ibool as
-// [NP]; with several elements per warp the element stride is padded so that they fall in
+// Shared memory per element: u (then F), eta fluxes and zeta fluxes as [NP][3] each (the
+// odd per-line stride 3N keeps the per-line accesses conflict-free), ibool as [NP]; with
+// several elements per warp the element stride is padded so that they fall in
 // disjoint banks (offsets chosen by simulating the warp's access patterns).
 // ---------------------------------------------------------------------------------------
 template <int N>
@@ -51,7 +52,7 @@ struct ForceCfg {
   static constexpr int TEAMS = T / TEAM;              // teams per CTA
   static constexpr int E = TEAM / NL;                 // elements per team
   static constexpr int EPC = TEAMS * E;               // elements per CTA
-  static constexpr int RES = N == 2 ? 7 : N == 3 ? 17 : N == 5 ? 23 : N == 7 ? 5 : N == 9 ? 11 : N == 8 ? 0 : 1;
+  static constexpr int RES = N == 2 ? 7 : N == 3 ? 3 : N == 6 ? 5 : N == 7 ? 4 : N == 9 ? 9 : N == 4 || N == 10 ? 1 : 0;
   static constexpr int ES = 10 * NP + ((RES - 10 * NP) % 32 + 32) % 32;  // floats per element
   static constexpr int TS = E * ES;                   // floats per team
   static constexpr int SMEM_FLOATS = TEAMS * TS;
@@ -113,8 +114,9 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
   const int j = line % N;
   const int k = line / N;
   const bool active = le < ne;
-  float* su = ts + (active ? le : 0) * ES;  // [NP][3]
-  float* st = su + 3 * NP;                   // [NP][6]
+  float* su = ts + (active ? le : 0) * ES;  // u, then F: [NP][3]
+  float* se = su + 3 * NP;                   // eta fluxes [NP][3]
+  float* sz = su + 6 * NP;                   // zeta fluxes [NP][3]
   const float* __restrict__ r = rec + static_cast<size_t>(ebase + (active ? le : 0)) * REC;
 
   float ux[N], uy[N], uz[N];
@@ -193,13 +195,13 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       fz[ip] += hw * txi_z;
     }
     if (active) {
-      const int p6 = 6 * (i + N * line);
-      st[p6 + 0] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
-      st[p6 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
-      st[p6 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
-      st[p6 + 3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
-      st[p6 + 4] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
-      st[p6 + 5] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
+      const int p3 = 3 * (i + N * line);
+      se[p3] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
+      se[p3 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
+      se[p3 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
+      sz[p3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
+      sz[p3 + 1] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
+      sz[p3 + 2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
     }
   }
   team_sync<WT>();
@@ -218,14 +220,14 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       float ex = 0.f, ey = 0.f, ez = 0.f, zx = 0.f, zy = 0.f, zz = 0.f;
 #pragma unroll
       for (int l = 0; l < N; ++l) {
-        const int pe = 6 * (i + N * (l + N * k));
-        ex += hwj[l] * st[pe];
-        ey += hwj[l] * st[pe + 1];
-        ez += hwj[l] * st[pe + 2];
-        const int pz = 6 * (i + N * (j + N * l)) + 3;
-        zx += hwk[l] * st[pz];
-        zy += hwk[l] * st[pz + 1];
-        zz += hwk[l] * st[pz + 2];
+        const int pe = 3 * (i + N * (l + N * k));
+        ex += hwj[l] * se[pe];
+        ey += hwj[l] * se[pe + 1];
+        ez += hwj[l] * se[pe + 2];
+        const int pz = 3 * (i + N * (j + N * l));
+        zx += hwk[l] * sz[pz];
+        zy += hwk[l] * sz[pz + 1];
+        zz += hwk[l] * sz[pz + 2];
       }
       const float wi = W[i];
       if (active) {
