@@ -37,9 +37,7 @@ struct sem_ctx {
   std::vector<int32_t> ibool;       // caller order
   std::vector<int> order;           // colour-sorted position -> caller element
   std::vector<int> pos_of;          // caller element -> colour-sorted position
-  std::vector<int> color_off;       // ncolors + 1, in elements
-  std::vector<int> unit_off;        // ncolors + 1, in record units (elements or groups)
-  std::vector<int> unit_of, le_of;  // colour-sorted position -> record unit, slot in unit
+  std::vector<int> color_off;       // ncolors + 1
   std::vector<float> rec;           // colour-sorted element records (host copy)
   std::vector<double> jac;          // caller order, per local point (for the mass)
   std::vector<double> dxmin;        // per caller element
@@ -165,8 +163,8 @@ int forces_all_colors(sem_ctx* c, const float* u, float* f) {
   L.u = u;
   L.f = f;
   for (int col = 0; col < c->ncolors; ++col) {
-    L.e0 = c->unit_off[col];
-    L.e1 = c->unit_off[col + 1];
+    L.e0 = c->color_off[col];
+    L.e1 = c->color_off[col + 1];
     SEM_LAUNCH(c, launch_forces(c->ngll, L, c->stream));
   }
   return SEM_OK;
@@ -420,47 +418,26 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
     }
   }
 
-  // record units per colour: one element each, or groups of group_elems() elements
-  const int EPW = group_elems(n);
-  c->unit_off.assign(ncolors + 1, 0);
-  for (int k = 0; k < ncolors; ++k)
-    c->unit_off[k + 1] = c->unit_off[k] + (c->color_off[k + 1] - c->color_off[k] + EPW - 1) / EPW;
-  c->unit_of.assign(nspec, 0);
-  c->le_of.assign(nspec, 0);
-  for (int k = 0; k < ncolors; ++k)
-    for (int s = c->color_off[k]; s < c->color_off[k + 1]; ++s) {
-      c->unit_of[s] = c->unit_off[k] + (s - c->color_off[k]) / EPW;
-      c->le_of[s] = (s - c->color_off[k]) % EPW;
-    }
-
   // element records, colour-sorted, with the first-touch flag on ibool
-  const size_t UW = static_cast<size_t>(unit_words(n));
-  const size_t nunits = static_cast<size_t>(c->unit_off[ncolors]);
-  c->rec.assign(nunits * UW, 0.f);
-  if (EPW > 1) {  // padding slots of partial groups carry an invalid node index
-    for (size_t u = 0; u < nunits; ++u)
-      for (int le = 0; le < EPW; ++le)
-        for (int p = 0; p < np; ++p)
-          std::memcpy(&c->rec[u * UW + unit_word(n, le, kIbool, p % n, (p / n) % n, p / (n * n))], &kInvalidNode,
-                      sizeof(uint32_t));
-  }
+  const int RW = rec_words(n);
+  c->rec.assign(static_cast<size_t>(nspec) * RW, 0.f);
   std::vector<char> touched(nglob, 0);
   for (int s = 0; s < nspec; ++s) {
     const int e = c->order[s];
-    float* r = c->rec.data() + static_cast<size_t>(c->unit_of[s]) * UW;
-    const int le = c->le_of[s];
+    float* r = c->rec.data() + static_cast<size_t>(s) * RW;
     const float* gq = geom.data() + static_cast<size_t>(e) * 10 * np;
     for (int k = 0; k < n; ++k)
       for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
           const int p = i + n * (j + n * k);
+          const int q = rec_pos(n, i, j, k);
           uint32_t g = static_cast<uint32_t>(ibool[static_cast<size_t>(e) * np + p]);
           if (!touched[g]) {
             touched[g] = 1;
             g |= kFirstTouchBit;
           }
-          std::memcpy(&r[unit_word(n, le, kIbool, i, j, k)], &g, sizeof(uint32_t));
-          for (int a = 0; a < 10; ++a) r[unit_word(n, le, kG + a, i, j, k)] = gq[a * np + p];
+          std::memcpy(&r[kIbool * np + p], &g, sizeof(uint32_t));
+          for (int a = 0; a < 10; ++a) r[(kG + a) * np + q] = gq[a * np + p];
         }
   }
 
@@ -503,8 +480,7 @@ int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float*
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
   if (!rho || !vp || !vs) return fail(c, SEM_EINVAL, "sem_set_material: NULL array");
-  const int n = c->ngll, np = n * n * n;
-  const size_t UW = static_cast<size_t>(unit_words(n));
+  const int n = c->ngll, np = n * n * n, RW = rec_words(n);
   const size_t nloc = static_cast<size_t>(c->nspec) * np;
   for (size_t q = 0; q < nloc; ++q) {
     if (!std::isfinite(rho[q]) || !std::isfinite(vp[q]) || !std::isfinite(vs[q]))
@@ -515,9 +491,7 @@ int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float*
   std::vector<double> mass(c->nglob, 0.0);
   c->vpmax.assign(c->nspec, 0.0);
   for (int e = 0; e < c->nspec; ++e) {
-    const int s = c->pos_of[e];
-    float* r = c->rec.data() + static_cast<size_t>(c->unit_of[s]) * UW;
-    const int le = c->le_of[s];
+    float* r = c->rec.data() + static_cast<size_t>(c->pos_of[e]) * RW;
     for (int k = 0; k < n; ++k)
       for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
@@ -527,8 +501,9 @@ int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float*
           const double mu = rh * b * b;
           const double lam = rh * (a * a - 2.0 * b * b);
           const double kappa = lam + 2.0 * mu / 3.0;
-          r[unit_word(n, le, kKappa, i, j, k)] = static_cast<float>(kappa);
-          r[unit_word(n, le, kMu, i, j, k)] = static_cast<float>(mu);
+          const int qq = rec_pos(n, i, j, k);
+          r[kKappa * np + qq] = static_cast<float>(kappa);
+          r[kMu * np + qq] = static_cast<float>(mu);
           mass[c->ibool[q]] += rh * c->jac[q] * c->w[i] * c->w[j] * c->w[k];
           c->vpmax[e] = std::max(c->vpmax[e], a);
         }

@@ -260,251 +260,21 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// Force kernel for NGLL <= 5 (group record layout): one warp per group of EPW = 32/NGLL
-// elements, one thread per (element, zeta-plane k). The thread keeps its whole xi-eta plane
-// of u in registers, so the xi and eta derivatives and the xi- and eta-transposed products
-// need no exchange; only the zeta direction goes through shared memory. Per local point
-// that is 2 x 3 NGLL shared loads instead of 4 x 3 NGLL with one thread per xi-line.
-//  1. gather, one thread per (point, element) slot: u at consecutive slots to shared memory;
-//  2. each thread loads its plane, then per point (i, j): derivatives, Jacobian map, Hooke
-//     stress, fluxes; xi/eta fluxes (weights folded in) accumulate into the thread's
-//     force plane in registers, zeta fluxes go to shared memory;
-//  3. zeta-transposed product from shared memory, forces into the u slots;
-//  4. scatter in the gather's order: store at first touch, read-modify-write otherwise.
-// ---------------------------------------------------------------------------------------
-template <int N>
-struct PlaneCfg {
-  static constexpr int NP = N * N * N;
-  static constexpr int NL = N * N;
-  static constexpr int EPW = 32 / N;        // elements per warp (group)
-  static constexpr int LANES = EPW * N;     // working lanes
-  static constexpr int WARPS = 2;           // warps (groups) per CTA
-  static constexpr int T = 32 * WARPS;
-  // per-element stride of the shared cubes, chosen by simulating the warp's bank accesses
-  static constexpr int S = N == 5 ? 375 : N == 3 ? 81 : N == 4 ? 193 : 33;
-  static constexpr int WS = 2 * EPW * S + EPW * NP;  // floats per warp: u/F cube, zeta fluxes, ibool
-  static constexpr int SMEM_FLOATS = WARPS * WS;
-  static constexpr int GW = (kRecFields * NP * EPW + 3) / 4 * 4;  // words per group record
-#ifdef SEM_FORCES_MIN_BLOCKS
-  static constexpr int MIN_BLOCKS = SEM_FORCES_MIN_BLOCKS;
-#else
-  static constexpr int MIN_BLOCKS = 5;
-#endif
-};
-
-template <int N>
-__global__ void __launch_bounds__(PlaneCfg<N>::T, PlaneCfg<N>::MIN_BLOCKS)
-    forces_plane_kernel(const float* __restrict__ rec, const float* __restrict__ u, float* __restrict__ f, int g0,
-                        int g1) {
-  using C = PlaneCfg<N>;
-  constexpr int NP = C::NP, NL = C::NL, EPW = C::EPW, S = C::S;
-  extern __shared__ float4 smem4[];
-  const float* __restrict__ H = c_h;
-  const float* __restrict__ HW = c_hw;
-  const float* __restrict__ W = c_w;
-
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  const int grp = g0 + blockIdx.x * C::WARPS + warp;
-  if (grp >= g1) return;  // whole warp
-  const float* __restrict__ gr = rec + static_cast<size_t>(grp) * C::GW;
-  float* cu = reinterpret_cast<float*>(smem4) + warp * C::WS;  // [EPW][S]: u, then F
-  float* ct = cu + EPW * S;                                      // [EPW][S]: zeta fluxes
-  uint32_t* cib = reinterpret_cast<uint32_t*>(ct + EPW * S);    // [EPW][NP]
-
-  // 1. gather; slot s = p * EPW + le matches the ibool layout [p][le]
-  for (int s = lane; s < NP * EPW; s += 32) {
-    const int p = s / EPW;
-    const int le = s - p * EPW;
-    const uint32_t w = __float_as_uint(__ldg(gr + s));
-    cib[le * NP + p] = w;
-    if (w != kInvalidNode) {
-      const size_t g3 = 3 * static_cast<size_t>(w & ~kFirstTouchBit);
-      float* d = cu + le * S + 3 * p;
-      d[0] = __ldg(u + g3);
-      d[1] = __ldg(u + g3 + 1);
-      d[2] = __ldg(u + g3 + 2);
-    }
-  }
-  __syncwarp();
-
-  // 2. per-plane work: thread (le, k), le fastest across lanes
-  const int k = lane / EPW;
-  const int le = lane - k * EPW;
-  const bool active = lane < C::LANES && cib[(lane < C::LANES ? le : 0) * NP] != kInvalidNode;
-  const int lek = (lane < C::LANES) ? le : 0;
-  const int kk = (lane < C::LANES) ? k : 0;
-  const float* ce = cu + lek * S;  // this element's cube
-  float ux[NL], uy[NL], uz[NL];   // the plane: index i + N j
-#pragma unroll
-  for (int q = 0; q < NL; ++q) {
-    const int p = q + NL * kk;
-    ux[q] = ce[3 * p];
-    uy[q] = ce[3 * p + 1];
-    uz[q] = ce[3 * p + 2];
-  }
-  float Fx[NL], Fy[NL], Fz[NL];
-#pragma unroll
-  for (int q = 0; q < NL; ++q) Fx[q] = Fy[q] = Fz[q] = 0.f;
-  float hk[N], hwk[N];
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    hk[l] = H[kk * N + l];
-    hwk[l] = HW[l * N + kk];
-  }
-  const float wk = W[kk];
-  const float* __restrict__ gg = gr + NP * EPW + kk * EPW + lek;  // geometry of (point, field) at + ((pt*12+f)*N)*EPW
-  float* cz = ct + lek * S;
-
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int pt = i + N * j;
-      float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
-      float det_x = 0.f, det_y = 0.f, det_z = 0.f;
-      float dze_x = 0.f, dze_y = 0.f, dze_z = 0.f;
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        const float hi = H[i * N + l], hj = H[j * N + l];
-        dxi_x += hi * ux[l + N * j];
-        dxi_y += hi * uy[l + N * j];
-        dxi_z += hi * uz[l + N * j];
-        det_x += hj * ux[i + N * l];
-        det_y += hj * uy[i + N * l];
-        det_z += hj * uz[i + N * l];
-        const float* pz = ce + 3 * (pt + NL * l);
-        dze_x += hk[l] * pz[0];
-        dze_y += hk[l] * pz[1];
-        dze_z += hk[l] * pz[2];
-      }
-      const float* gp = gg + static_cast<size_t>(pt) * (kRecFields - 1) * N * EPW;
-      float G[9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) G[a] = active ? __ldg(gp + a * N * EPW) : 0.f;
-      const float jac = active ? __ldg(gp + 9 * N * EPW) : 0.f;
-      const float kappa = active ? __ldg(gp + 10 * N * EPW) : 0.f;
-      const float mu = active ? __ldg(gp + 11 * N * EPW) : 0.f;
-
-      const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
-      const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
-      const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
-      const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
-      const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
-      const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
-      const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
-      const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
-      const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
-
-      const float lam = kappa - (2.f / 3.f) * mu;
-      const float tr = uxx + uyy + uzz;
-      const float sxx = lam * tr + 2.f * mu * uxx;
-      const float syy = lam * tr + 2.f * mu * uyy;
-      const float szz = lam * tr + 2.f * mu * uzz;
-      const float sxy = mu * (uxy + uyx);
-      const float sxz = mu * (uxz + uzx);
-      const float syz = mu * (uyz + uzy);
-
-      // fluxes with the quadrature weights of the other two directions folded in
-      const float wxi = W[j] * wk, wet = W[i] * wk, wze = W[i] * W[j];
-      const float jx = jac * wxi, je = jac * wet, jz = jac * wze;
-      const float txi_x = jx * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
-      const float txi_y = jx * (sxy * G[0] + syy * G[1] + syz * G[2]);
-      const float txi_z = jx * (sxz * G[0] + syz * G[1] + szz * G[2]);
-      const float tet_x = je * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
-      const float tet_y = je * (sxy * G[3] + syy * G[4] + syz * G[5]);
-      const float tet_z = je * (sxz * G[3] + syz * G[4] + szz * G[5]);
-#pragma unroll
-      for (int m = 0; m < N; ++m) {
-        const float ax = HW[i * N + m], ae = HW[j * N + m];
-        Fx[m + N * j] += ax * txi_x;  // xi-transposed product along the row
-        Fy[m + N * j] += ax * txi_y;
-        Fz[m + N * j] += ax * txi_z;
-        Fx[i + N * m] += ae * tet_x;  // eta-transposed product along the column
-        Fy[i + N * m] += ae * tet_y;
-        Fz[i + N * m] += ae * tet_z;
-      }
-      if (active) {
-        float* zo = cz + 3 * (pt + NL * kk);
-        zo[0] = jz * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
-        zo[1] = jz * (sxy * G[6] + syy * G[7] + syz * G[8]);
-        zo[2] = jz * (sxz * G[6] + syz * G[7] + szz * G[8]);
-      }
-    }
-  }
-  __syncwarp();
-
-  // 3. zeta-transposed product; forces into this element's u slots (all u reads are done)
-#pragma unroll
-  for (int q = 0; q < NL; ++q) {
-    float zx = 0.f, zy = 0.f, zz = 0.f;
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      const float* pz = cz + 3 * (q + NL * l);
-      zx += hwk[l] * pz[0];
-      zy += hwk[l] * pz[1];
-      zz += hwk[l] * pz[2];
-    }
-    if (active) {
-      float* o = cu + lek * S + 3 * (q + NL * kk);
-      o[0] = -(Fx[q] + zx);
-      o[1] = -(Fy[q] + zy);
-      o[2] = -(Fz[q] + zz);
-    }
-  }
-  __syncwarp();
-
-  // 4. scatter in the gather's order
-  for (int s = lane; s < NP * EPW; s += 32) {
-    const int p = s / EPW;
-    const int e = s - p * EPW;
-    const uint32_t w = cib[e * NP + p];
-    if (w == kInvalidNode) continue;
-    const size_t g3 = 3 * static_cast<size_t>(w & ~kFirstTouchBit);
-    const float* src = cu + e * S + 3 * p;
-    if (w & kFirstTouchBit) {
-      f[g3] = src[0];
-      f[g3 + 1] = src[1];
-      f[g3 + 2] = src[2];
-    } else {
-      f[g3] += src[0];
-      f[g3 + 1] += src[1];
-      f[g3 + 2] += src[2];
-    }
-  }
-}
-
-template <typename KernelT>
-int ensure_smem_attr(KernelT kernel, int smem, unsigned long long* done) {
+int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
+  using C = ForceCfg<SEM_NGLL>;
+  if (L.e1 <= L.e0) return 0;
+  static unsigned long long attr_done = 0;  // one bit per device ordinal
+  const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
   int dev = 0;
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
-  if (!(*done & bit)) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (!(attr_done & bit)) {
+    cudaError_t e = cudaFuncSetAttribute(forces_kernel<SEM_NGLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return static_cast<int>(e);
-    *done |= bit;
+    attr_done |= bit;
   }
-  return 0;
-}
-
-template <int NG>
-int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
-  if (L.e1 <= L.e0) return 0;
-  static unsigned long long attr_done = 0;  // one bit per device ordinal
-  if constexpr (NG <= 5) {
-    using C = PlaneCfg<NG>;
-    const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
-    if (int r = ensure_smem_attr(forces_plane_kernel<NG>, smem, &attr_done)) return r;
-    const int grid = (L.e1 - L.e0 + C::WARPS - 1) / C::WARPS;
-    forces_plane_kernel<NG><<<grid, C::T, smem, s>>>(L.rec, L.u, L.f, L.e0, L.e1);
-  } else {
-    using C = ForceCfg<NG>;
-    const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
-    if (int r = ensure_smem_attr(forces_kernel<NG>, smem, &attr_done)) return r;
-    const int grid = (L.e1 - L.e0 + C::EPC - 1) / C::EPC;
-    forces_kernel<NG><<<grid, C::T, smem, s>>>(L.rec, L.u, L.f, L.e0, L.e1);
-  }
+  const int grid = (L.e1 - L.e0 + C::EPC - 1) / C::EPC;
+  forces_kernel<SEM_NGLL><<<grid, C::T, smem, s>>>(L.rec, L.u, L.f, L.e0, L.e1);
   return static_cast<int>(cudaGetLastError());
 }
 
@@ -530,17 +300,9 @@ int SEM_CAT(upload_basis_, SEM_NGLL)(const double* w, const double* h, void* str
 }
 
 int SEM_CAT(launch_forces_, SEM_NGLL)(const ForceLaunch& L, void* stream) {
-  return launch_forces_n<SEM_NGLL>(L, static_cast<cudaStream_t>(stream));
+  return launch_forces_n(L, static_cast<cudaStream_t>(stream));
 }
 
-template <int NG>
-int forces_smem_bytes_t() {
-  if constexpr (NG <= 5)
-    return PlaneCfg<NG>::SMEM_FLOATS * 4;
-  else
-    return ForceCfg<NG>::SMEM_FLOATS * 4;
-}
-
-int SEM_CAT(forces_smem_bytes_, SEM_NGLL)() { return forces_smem_bytes_t<SEM_NGLL>(); }
+int SEM_CAT(forces_smem_bytes_, SEM_NGLL)() { return ForceCfg<SEM_NGLL>::SMEM_FLOATS * 4; }
 
 }  // namespace semgb

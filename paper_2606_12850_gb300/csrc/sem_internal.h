@@ -26,37 +26,16 @@ enum RecField { kIbool = 0, kG = 1, kJac = 10, kKappa = 11, kMu = 12 };
 // so the assembled array needs no zeroing pass.
 constexpr uint32_t kFirstTouchBit = 0x80000000u;
 
-// Element records come in two layouts, both colour-sorted and 16-byte aligned:
-//  * element layout (NGLL >= 6): one record of unit_words() words per element; field 0
-//    (ibool) in natural point order p = i + N j + N^2 k, fields 1..12 in the order
-//    q = i N^2 + j + N k so that the N^2 xi-line threads of an element read consecutive
-//    words for a fixed i;
-//  * group layout (NGLL <= 5): group_elems() = 32/N consecutive elements of one colour form
-//    a group of unit_words() words read by one warp: ibool as [p][element], then the
-//    twelve other fields as [i + N j][field][k][element], so that the warp's (element,
-//    zeta-plane k) threads read consecutive words for a fixed point (i, j). A colour's last
-//    group is padded with elements whose ibool words are kInvalidNode.
-constexpr uint32_t kInvalidNode = 0xFFFFFFFFu;
-
-inline bool grouped_layout(int ngll) { return ngll <= 5; }
-inline int group_elems(int ngll) { return grouped_layout(ngll) ? 32 / ngll : 1; }
-
-inline int unit_words(int ngll) {
+inline int rec_words(int ngll) {
   const int np = ngll * ngll * ngll;
-  return (kRecFields * np * group_elems(ngll) + 3) / 4 * 4;
+  return (kRecFields * np + 3) / 4 * 4;  // 16-byte aligned element records
 }
 
-// Word of field f at point (i, j, k) of element le (0 in the element layout) of a unit.
-inline size_t unit_word(int n, int le, int f, int i, int j, int k) {
-  const size_t np = static_cast<size_t>(n) * n * n;
-  if (grouped_layout(n)) {
-    const size_t epw = group_elems(n);
-    if (f == kIbool) return static_cast<size_t>(i + n * j + n * n * k) * epw + le;
-    return np * epw + ((static_cast<size_t>(i + n * j) * (kRecFields - 1) + (f - 1)) * n + k) * epw + le;
-  }
-  if (f == kIbool) return static_cast<size_t>(i + n * j + n * n * k);
-  return f * np + static_cast<size_t>(i) * n * n + j + n * k;
-}
+// Position of local point (i, j, k) inside a geometry or material field of an element
+// record: points are stored i-major so that the NGLL^2 threads owning the xi-lines (j, k)
+// of an element read consecutive words for a fixed i. The ibool field keeps the natural
+// order p = i + NGLL*j + NGLL^2*k, which the gather and scatter threads walk.
+inline int rec_pos(int ngll, int i, int j, int k) { return i * ngll * ngll + j + ngll * k; }
 
 // ---- host set-up (sem_setup.cpp) -------------------------------------------------------
 int gll_basis(int ngll, double* xi, double* w, double* hprime, std::string* err);
@@ -105,9 +84,8 @@ struct DevProblem {
 // Copies hprime, hprime*w and w for this ngll into the kernels' constant banks.
 int upload_basis(int ngll, const double* w, const double* hprime, void* stream);
 
-// One colour's worth of record units [e0, e1) (elements, or groups of elements in the
-// group layout): f (=|+=) -K u; a node is stored at its first touch in colour order and
-// accumulated afterwards.
+// One colour's worth of elements [e0, e1) of the colour-sorted order: f (=|+=) -K u; a node
+// is stored at its first touch in colour order and accumulated afterwards.
 struct ForceLaunch {
   const float* rec;
   const float* u;
