@@ -129,11 +129,17 @@ int sem_get_state_dev(sem_ctx* ctx, float* u_dev, float* v_dev, float* a_dev);
 int sem_step(sem_ctx* ctx, int nsteps);
 
 /* Advance nsteps time steps and record seismograms into host seis[nrec][3][nsteps]
- * (may be NULL). Synchronous. */
+ * (may be NULL). Synchronous. Ends with sem_check_finite: SEM_EDIVERGED (seismograms
+ * still copied) when the run blew up. */
 int sem_run(sem_ctx* ctx, int nsteps, float* seis);
 /* Same, recording into a device buffer seis_dev[nrec][3][nsteps] (may be NULL).
  * Asynchronous on the context's stream. */
 int sem_run_dev(sem_ctx* ctx, int nsteps, float* seis_dev);
+
+/* Divergence watchdog: SEM_OK if every value of u, v and a is finite, SEM_EDIVERGED
+ * otherwise (an explicit scheme run above its stability limit grows until it overflows).
+ * Synchronous. */
+int sem_check_finite(sem_ctx* ctx);
 
 /* One matrix-free stiffness application on the device: f_dev = -K u_dev, both
  * [nglob][3] float32 (Sec. II-B). Every node of f_dev is written. u_dev and f_dev must not

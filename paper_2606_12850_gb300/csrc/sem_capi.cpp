@@ -662,6 +662,23 @@ int sem_step(sem_ctx* c, int nsteps) { return advance(c, nsteps, nullptr); }
 
 int sem_run_dev(sem_ctx* c, int nsteps, float* seis_dev) { return advance(c, nsteps, seis_dev); }
 
+int sem_check_finite(sem_ctx* c) {
+  int r = check_ready(c);
+  if (r) return r;
+  if ((r = set_device(c))) return r;
+  int* flag = &c->d_ctl->err;
+  SEM_CUDA(c, cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  SEM_LAUNCH(c, launch_nonfinite_check(problem(c), flag, c->stream));
+  int bad = 0;
+  SEM_CUDA(c, cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (bad)
+    return fail(c, SEM_EDIVERGED,
+                "non-finite displacement, velocity or acceleration after " + std::to_string(c->steps) +
+                    " steps (is dt above the stability limit?)");
+  return SEM_OK;
+}
+
 int sem_run(sem_ctx* c, int nsteps, float* seis) {
   int r = check_ready(c);
   if (r) return r;
@@ -681,6 +698,7 @@ int sem_run(sem_ctx* c, int nsteps, float* seis) {
   if (d_seis) cudaFreeAsync(d_seis, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (r == SEM_OK && e != cudaSuccess) r = cuda_fail(c, e, "sem_run");
+  if (r == SEM_OK) r = sem_check_finite(c);
   return r;
 }
 

@@ -101,6 +101,7 @@ int launch_predictor(const DevProblem& p, void* stream);
 int launch_fused_newmark(const DevProblem& p, void* stream);
 int launch_corrector(const DevProblem& p, void* stream);
 int launch_sources_record(const DevProblem& p, void* stream);
+int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream);
 int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv,
                            int nglob_pad, double* partials, int nblocks, void* stream);
 constexpr int kEnergyBlocks = 608;  // 4 CTAs per SM on 152 SMs

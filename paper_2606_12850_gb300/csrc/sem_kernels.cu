@@ -257,6 +257,30 @@ int launch_sources_record(const DevProblem& p, void* stream) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Divergence watchdog: flags any non-finite value of u, v or a (the fields hold 3*nglob_pad
+// floats). Threads that find one write 1 into the flag word; the host clears it first.
+// ---------------------------------------------------------------------------------------
+__global__ void nonfinite_kernel(const float4* __restrict__ u, const float4* __restrict__ v,
+                                 const float4* __restrict__ a, int n4x3, int* flag) {
+  bool bad = false;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4x3; t += gridDim.x * blockDim.x) {
+    const float4 x = u[t], y = v[t], z = a[t];
+    bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(x.w));
+    bad |= !(isfinite(y.x) && isfinite(y.y) && isfinite(y.z) && isfinite(y.w));
+    bad |= !(isfinite(z.x) && isfinite(z.y) && isfinite(z.z) && isfinite(z.w));
+  }
+  if (bad) *flag = 1;
+}
+
+int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream) {
+  const int n = 3 * (p.nglob_pad / 4);
+  nonfinite_kernel<<<kEnergyBlocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const float4*>(p.u), reinterpret_cast<const float4*>(p.v),
+      reinterpret_cast<const float4*>(p.a), n, flag);
+  return static_cast<int>(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------------------
 // Energy partial sums: per block, sum_I |v_I|^2 / minv_I and sum_I u_I . f_I in float64.
 // ---------------------------------------------------------------------------------------
 __global__ void energy_partials_kernel(const float* __restrict__ u, const float* __restrict__ v,

@@ -44,6 +44,7 @@ SIGNATURES = {
     "sem_step": (_I, [_P, _I]),
     "sem_run": (_I, [_P, _I, _P]),
     "sem_run_dev": (_I, [_P, _I, _P]),
+    "sem_check_finite": (_I, [_P]),
     "sem_apply_stiffness": (_I, [_P, _P, _P]),
     "sem_energy": (_I, [_P, _P]),
     "sem_energy_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
@@ -261,6 +262,10 @@ def sem_run(ctx: Ctx, nsteps: int, record: bool = True, out=None):
 
 def sem_run_dev(ctx: Ctx, nsteps: int, seis_dev=None):
     _check(lib().sem_run_dev(ctx.handle, int(nsteps), _dev(seis_dev, ctx.nrec * 3 * nsteps)), "sem_run_dev", ctx)
+
+
+def sem_check_finite(ctx: Ctx):
+    _check(lib().sem_check_finite(ctx.handle), "sem_check_finite", ctx)
 
 
 def sem_apply_stiffness(ctx: Ctx, u_dev, f_dev):

@@ -279,3 +279,21 @@ def test_plane_wave_periodic(oracle):
     assert rel_l2(seis, seis_ref) <= TOL_SEIS
     u, _, _ = sem.sem_get_state(ctx)
     assert rel_l2(u, u_ref) <= TOL_WAVEFIELD
+
+
+def test_divergence_watchdog():
+    """Failure detection without a GPU fault: a time step 3x above the CFL limit makes the
+    explicit scheme blow up to Inf; sem_run reports SEM_EDIVERGED and the context stays
+    usable (a fresh state with a stable dt runs again)."""
+    w = inputs.homogeneous_cube(n=4, side=500.0, nsteps=400)
+    s = sem.setup_workload(w)
+    dt_cfl = sem.sem_suggest_dt(s.ctx, 1.0)
+    sem.sem_set_dt(s.ctx, 3.0 * dt_cfl)
+    sem.sem_set_state(s.ctx, inputs.random_field(s.ctx.nglob, 3, scale=1e-6))
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_run(s.ctx, 400)
+    assert ei.value.code == -6 and "non-finite" in str(ei.value)
+    sem.sem_set_dt(s.ctx, s.dt)
+    sem.sem_set_state(s.ctx)
+    sem.sem_run(s.ctx, 20)
+    sem.sem_check_finite(s.ctx)
