@@ -33,7 +33,7 @@ struct sem_ctx {
 
   // mesh (host)
   bool have_mesh = false, have_mat = false, have_dt = false;
-  int nspec = 0, nglob = 0, nglob_pad = 0, ncolors = 0;
+  int nspec = 0, nglob = 0, ncolors = 0;
   std::vector<int32_t> ibool;       // caller order
   std::vector<int> order;           // colour-sorted position -> caller element
   std::vector<int> pos_of;          // caller element -> colour-sorted position
@@ -133,7 +133,6 @@ DevProblem problem(const sem_ctx* c) {
   p.ngll = c->ngll;
   p.nspec = c->nspec;
   p.nglob = c->nglob;
-  p.nglob_pad = c->nglob_pad;
   p.rec = c->d_rec;
   p.u = c->d_u;
   p.v = c->d_v;
@@ -157,11 +156,12 @@ int set_device(sem_ctx* c) {
 }
 
 // f = -K u over all colours in order (Sec. IV-C: colour by colour, no atomics).
-int forces_all_colors(sem_ctx* c, const float* u, float* f) {
+int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride = kNodeStride) {
   ForceLaunch L{};
   L.rec = c->d_rec;
   L.u = u;
   L.f = f;
+  L.node_stride = node_stride;
   for (int col = 0; col < c->ncolors; ++col) {
     L.e0 = c->color_off[col];
     L.e1 = c->color_off[col + 1];
@@ -444,7 +444,6 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   c->ibool.assign(ibool, ibool + nloc);
   c->nspec = nspec;
   c->nglob = nglob;
-  c->nglob_pad = (nglob + 3) / 4 * 4;
   c->ncolors = ncolors;
   c->have_mesh = true;
   c->have_mat = false;
@@ -461,15 +460,15 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   free_device(c);
   c->d_ctl = keep_ctl;
   c->dev_bytes = sizeof(DevCtl);
-  const size_t nf = 3 * static_cast<size_t>(c->nglob_pad);
+  const size_t nf = kNodeStride * static_cast<size_t>(nglob);
   if ((r = dev_alloc(c, &c->d_rec, c->rec.size())) || (r = dev_alloc(c, &c->d_u, nf)) ||
       (r = dev_alloc(c, &c->d_v, nf)) || (r = dev_alloc(c, &c->d_a, nf)) ||
-      (r = dev_alloc(c, &c->d_minv, static_cast<size_t>(c->nglob_pad))))
+      (r = dev_alloc(c, &c->d_minv, static_cast<size_t>(nglob))))
     return r;
   SEM_CUDA(c, cudaMemsetAsync(c->d_u, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_v, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_a, 0, nf * sizeof(float), c->stream));
-  SEM_CUDA(c, cudaMemsetAsync(c->d_minv, 0, c->nglob_pad * sizeof(float), c->stream));
+  SEM_CUDA(c, cudaMemsetAsync(c->d_minv, 0, nglob * sizeof(float), c->stream));
   SEM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->nsrc = 0;
   c->nrec = 0;
@@ -508,7 +507,7 @@ int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float*
           c->vpmax[e] = std::max(c->vpmax[e], a);
         }
   }
-  std::vector<float> minv(c->nglob_pad, 0.f);
+  std::vector<float> minv(c->nglob, 0.f);
   for (int g = 0; g < c->nglob; ++g) minv[g] = static_cast<float>(1.0 / mass[g]);
   int r = set_device(c);
   if (r) return r;
@@ -621,8 +620,10 @@ static int set_state_impl(sem_ctx* c, const float* u, const float* v, const floa
   const float* src[3] = {u, v, a};
   float* dst[3] = {c->d_u, c->d_v, c->d_a};
   for (int q = 0; q < 3; ++q) {
-    SEM_CUDA(c, cudaMemsetAsync(dst[q], 0, 3 * static_cast<size_t>(c->nglob_pad) * sizeof(float), c->stream));
-    if (src[q]) SEM_CUDA(c, cudaMemcpyAsync(dst[q], src[q], n3 * sizeof(float), kind, c->stream));
+    SEM_CUDA(c, cudaMemsetAsync(dst[q], 0, kNodeStride * static_cast<size_t>(c->nglob) * sizeof(float), c->stream));
+    if (src[q])  // [nglob][3] -> [nglob][kNodeStride]
+      SEM_CUDA(c, cudaMemcpy2DAsync(dst[q], kNodeStride * sizeof(float), src[q], 3 * sizeof(float),
+                                    3 * sizeof(float), c->nglob, kind, c->stream));
   }
   if (kind == cudaMemcpyHostToDevice) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->pending = false;
@@ -643,11 +644,12 @@ static int get_state_impl(sem_ctx* c, float* u, float* v, float* a, cudaMemcpyKi
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
   int r = set_device(c);
   if (r || (r = finish_state(c))) return r;
-  const size_t n3 = 3 * static_cast<size_t>(c->nglob);
   float* dst[3] = {u, v, a};
   const float* src[3] = {c->d_u, c->d_v, c->d_a};
   for (int q = 0; q < 3; ++q)
-    if (dst[q]) SEM_CUDA(c, cudaMemcpyAsync(dst[q], src[q], n3 * sizeof(float), kind, c->stream));
+    if (dst[q])  // [nglob][kNodeStride] -> [nglob][3]
+      SEM_CUDA(c, cudaMemcpy2DAsync(dst[q], 3 * sizeof(float), src[q], kNodeStride * sizeof(float),
+                                    3 * sizeof(float), c->nglob, kind, c->stream));
   if (kind == cudaMemcpyDeviceToHost) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
   return SEM_OK;
 }
@@ -712,7 +714,7 @@ int sem_apply_stiffness(sem_ctx* c, const float* u_dev, float* f_dev) {
   if (a < b + bytes && b < a + bytes) return fail(c, SEM_EINVAL, "u_dev and f_dev overlap");
   int r = set_device(c);
   if (r) return r;
-  return forces_all_colors(c, u_dev, f_dev);
+  return forces_all_colors(c, u_dev, f_dev, 3);
 }
 
 int sem_energy(sem_ctx* c, double* out) {
@@ -721,14 +723,14 @@ int sem_energy(sem_ctx* c, double* out) {
   if (!out) return fail(c, SEM_EINVAL, "sem_energy: NULL output");
   int r = set_device(c);
   if (r || (r = finish_state(c))) return r;
-  const size_t nf = 3 * static_cast<size_t>(c->nglob_pad);
+  const size_t nf = kNodeStride * static_cast<size_t>(c->nglob);
   if (!c->d_f) {
     if ((r = dev_alloc(c, &c->d_f, nf)) || (r = dev_alloc(c, &c->d_partials, 2 * static_cast<size_t>(kEnergyBlocks))))
       return r;
     SEM_CUDA(c, cudaMemsetAsync(c->d_f, 0, nf * sizeof(float), c->stream));
   }
   if ((r = forces_all_colors(c, c->d_u, c->d_f))) return r;
-  SEM_LAUNCH(c, launch_energy_partials(c->d_u, c->d_v, c->d_f, c->d_minv, c->nglob_pad, c->d_partials, kEnergyBlocks,
+  SEM_LAUNCH(c, launch_energy_partials(c->d_u, c->d_v, c->d_f, c->d_minv, c->nglob, c->d_partials, kEnergyBlocks,
                                        c->stream));
   std::vector<double> part(2 * kEnergyBlocks);
   SEM_CUDA(c, cudaMemcpyAsync(part.data(), c->d_partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost,

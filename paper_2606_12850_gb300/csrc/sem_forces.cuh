@@ -75,7 +75,8 @@ __device__ __forceinline__ void team_sync() {
     __syncthreads();
 }
 
-template <int N>
+// VS: floats per node in u and f (4 for the context's own padded fields, 3 for caller arrays).
+template <int N, int VS>
 __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     forces_kernel(const float* __restrict__ rec, const float* __restrict__ u, float* __restrict__ f, int e0,
                   int e1) {
@@ -101,10 +102,17 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     float* eb = ts + le * ES;
     const uint32_t w = __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + p));
     reinterpret_cast<uint32_t*>(eb + 9 * NP)[p] = w;
-    const size_t g3 = 3 * static_cast<size_t>(w & ~kFirstTouchBit);
-    eb[3 * p] = __ldg(u + g3);
-    eb[3 * p + 1] = __ldg(u + g3 + 1);
-    eb[3 * p + 2] = __ldg(u + g3 + 2);
+    const size_t g = w & ~kFirstTouchBit;
+    if (VS == 4) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(u) + g);
+      eb[3 * p] = q.x;
+      eb[3 * p + 1] = q.y;
+      eb[3 * p + 2] = q.z;
+    } else {
+      eb[3 * p] = __ldg(u + 3 * g);
+      eb[3 * p + 1] = __ldg(u + 3 * g + 1);
+      eb[3 * p + 2] = __ldg(u + 3 * g + 2);
+    }
   }
   team_sync<WT>();
 
@@ -246,36 +254,54 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     const int p = idx - e * NP;
     const float* sb = ts + e * ES;
     const uint32_t w = reinterpret_cast<const uint32_t*>(sb + 9 * NP)[p];
-    const size_t g3 = 3 * static_cast<size_t>(w & ~kFirstTouchBit);
+    const size_t g = w & ~kFirstTouchBit;
     const float* src = sb + 3 * p;
-    if (w & kFirstTouchBit) {
-      f[g3] = src[0];
-      f[g3 + 1] = src[1];
-      f[g3 + 2] = src[2];
+    if (VS == 4) {
+      float4* f4 = reinterpret_cast<float4*>(f) + g;
+      float4 o = make_float4(src[0], src[1], src[2], 0.f);
+      if (!(w & kFirstTouchBit)) {
+        const float4 prev = *f4;
+        o.x += prev.x;
+        o.y += prev.y;
+        o.z += prev.z;
+      }
+      *f4 = o;
+    } else if (w & kFirstTouchBit) {
+      f[3 * g] = src[0];
+      f[3 * g + 1] = src[1];
+      f[3 * g + 2] = src[2];
     } else {
-      f[g3] += src[0];
-      f[g3 + 1] += src[1];
-      f[g3 + 2] += src[2];
+      f[3 * g] += src[0];
+      f[3 * g + 1] += src[1];
+      f[3 * g + 2] += src[2];
     }
   }
 }
 
-int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
+template <int VS>
+int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   using C = ForceCfg<SEM_NGLL>;
-  if (L.e1 <= L.e0) return 0;
   static unsigned long long attr_done = 0;  // one bit per device ordinal
   const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
   int dev = 0;
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_done & bit)) {
-    cudaError_t e = cudaFuncSetAttribute(forces_kernel<SEM_NGLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(forces_kernel<SEM_NGLL, VS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return static_cast<int>(e);
     attr_done |= bit;
   }
   const int grid = (L.e1 - L.e0 + C::EPC - 1) / C::EPC;
-  forces_kernel<SEM_NGLL><<<grid, C::T, smem, s>>>(L.rec, L.u, L.f, L.e0, L.e1);
+  forces_kernel<SEM_NGLL, VS><<<grid, C::T, smem, s>>>(L.rec, L.u, L.f, L.e0, L.e1);
   return static_cast<int>(cudaGetLastError());
+}
+
+int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
+  if (L.e1 <= L.e0) return 0;
+  if (L.node_stride == 4) return launch_forces_vs<4>(L, s);
+  if (L.node_stride == 3) return launch_forces_vs<3>(L, s);
+  return static_cast<int>(cudaErrorInvalidValue);
 }
 
 }  // namespace

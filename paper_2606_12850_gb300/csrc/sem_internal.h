@@ -21,6 +21,11 @@ constexpr int kMinNgll = 2;
 constexpr int kRecFields = 13;
 enum RecField { kIbool = 0, kG = 1, kJac = 10, kKappa = 11, kMu = 12 };
 
+// The context's own wavefields u, v, a are float32 [nglob][kNodeStride]: x, y, z and a zero
+// pad, so that every node is one aligned 16-byte access in the gather, the scatter and the
+// Newmark passes. Caller-facing arrays stay [nglob][3]; copies at the boundary are strided.
+constexpr int kNodeStride = 4;
+
 // Bit 31 of a record's ibool word marks the first contribution to that node in the
 // colour-by-colour processing order: the force kernel stores instead of adding there,
 // so the assembled array needs no zeroing pass.
@@ -65,7 +70,6 @@ struct DevProblem {
   int ngll;
   int nspec;
   int nglob;
-  int nglob_pad;  // multiple of 4
   const float* rec;
   float* u;
   float* v;
@@ -91,6 +95,7 @@ struct ForceLaunch {
   const float* u;
   float* f;
   int e0, e1;
+  int node_stride;  // floats per node in u and f: kNodeStride, or 3 for caller arrays
 };
 int launch_forces(int ngll, const ForceLaunch& launch, void* stream);
 int forces_kernel_smem_bytes(int ngll);
@@ -103,7 +108,7 @@ int launch_corrector(const DevProblem& p, void* stream);
 int launch_sources_record(const DevProblem& p, void* stream);
 int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream);
 int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv,
-                           int nglob_pad, double* partials, int nblocks, void* stream);
+                           int nglob, double* partials, int nblocks, void* stream);
 constexpr int kEnergyBlocks = 608;  // 4 CTAs per SM on 152 SMs
 
 // ---- context access for entry points defined outside sem_capi.cpp ----------------------

@@ -67,41 +67,20 @@ int forces_elements_per_cta(int n) {
 
 // ---------------------------------------------------------------------------------------
 // Newmark streaming passes (Sec. I / V-C explicit second-order Newmark, diagonal mass).
-// Fields are [nglob_pad][3] float32 with nglob_pad % 4 == 0: a thread owns four nodes,
-// i.e. three float4 of each field and one float4 of the inverse mass.
+// Fields are [nglob][kNodeStride] float32: one thread per node reads one float4 of each
+// field (the 4th lane stays zero) and the node's inverse mass.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ float4 mass_lanes(const float4 m, int part) {
-  // the three float4 words of 4 nodes (x0 y0 z0 x1 | y1 z1 x2 y2 | z2 x3 y3 z3)
-  return part == 0 ? make_float4(m.x, m.x, m.x, m.y)
-                   : (part == 1 ? make_float4(m.y, m.y, m.z, m.z) : make_float4(m.z, m.w, m.w, m.w));
+__device__ __forceinline__ float4 axpy3(float4 y, float s, float4 x) {
+  return make_float4(y.x + s * x.x, y.y + s * x.y, y.z + s * x.z, 0.f);
 }
 
 // Predictor from a complete state (first step): u += dt v + dt^2/2 a ; v += dt/2 a.
-// All loads of a thread are issued before its arithmetic so that each thread keeps nine
-// 16-byte requests in flight.
 __global__ void predictor_kernel(float4* __restrict__ u, float4* __restrict__ v, const float4* __restrict__ a,
-                                 int n4, float dt, float hdt, float hdt2) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
-    float4 av[3], vv[3], uv[3];
-#pragma unroll
-    for (int part = 0; part < 3; ++part) {
-      av[part] = a[3 * t + part];
-      vv[part] = v[3 * t + part];
-      uv[part] = u[3 * t + part];
-    }
-#pragma unroll
-    for (int part = 0; part < 3; ++part) {
-      uv[part].x += dt * vv[part].x + hdt2 * av[part].x;
-      uv[part].y += dt * vv[part].y + hdt2 * av[part].y;
-      uv[part].z += dt * vv[part].z + hdt2 * av[part].z;
-      uv[part].w += dt * vv[part].w + hdt2 * av[part].w;
-      vv[part].x += hdt * av[part].x;
-      vv[part].y += hdt * av[part].y;
-      vv[part].z += hdt * av[part].z;
-      vv[part].w += hdt * av[part].w;
-      u[3 * t + part] = uv[part];
-      v[3 * t + part] = vv[part];
-    }
+                                 int nglob, float dt, float hdt, float hdt2) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob; g += gridDim.x * blockDim.x) {
+    const float4 ag = a[g], vg = v[g], ug = u[g];
+    u[g] = axpy3(axpy3(ug, dt, vg), hdt2, ag);
+    v[g] = axpy3(vg, hdt, ag);
   }
 }
 
@@ -109,93 +88,52 @@ __global__ void predictor_kernel(float4* __restrict__ u, float4* __restrict__ v,
 //   a = M^-1 a_raw ; v = v_half + dt/2 a ; u += dt v + dt^2/2 a ; v_half = v + dt/2 a
 // a_raw stays in place: the next force sweep overwrites it at each node's first touch.
 __global__ void fused_newmark_kernel(float4* __restrict__ u, float4* __restrict__ v,
-                                     const float4* __restrict__ a, const float4* __restrict__ minv, int n4,
+                                     const float4* __restrict__ a, const float* __restrict__ minv, int nglob,
                                      float dt, float hdt, float hdt2) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
-    const float4 m = minv[t];
-    float4 ar[3], vv[3], uv[3];
-#pragma unroll
-    for (int part = 0; part < 3; ++part) {
-      ar[part] = a[3 * t + part];
-      vv[part] = v[3 * t + part];
-      uv[part] = u[3 * t + part];
-    }
-#pragma unroll
-    for (int part = 0; part < 3; ++part) {
-      const float4 mm = mass_lanes(m, part);
-      const float ax = ar[part].x * mm.x, ay = ar[part].y * mm.y, az = ar[part].z * mm.z, aw = ar[part].w * mm.w;
-      float4 w = vv[part];
-      w.x += hdt * ax;
-      w.y += hdt * ay;
-      w.z += hdt * az;
-      w.w += hdt * aw;
-      float4 x = uv[part];
-      x.x += dt * w.x + hdt2 * ax;
-      x.y += dt * w.y + hdt2 * ay;
-      x.z += dt * w.z + hdt2 * az;
-      x.w += dt * w.w + hdt2 * aw;
-      w.x += hdt * ax;
-      w.y += hdt * ay;
-      w.z += hdt * az;
-      w.w += hdt * aw;
-      u[3 * t + part] = x;
-      v[3 * t + part] = w;
-    }
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob; g += gridDim.x * blockDim.x) {
+    const float m = minv[g];
+    const float4 ar = a[g], vh = v[g], ug = u[g];
+    const float4 acc = make_float4(ar.x * m, ar.y * m, ar.z * m, 0.f);
+    const float4 vf = axpy3(vh, hdt, acc);
+    u[g] = axpy3(axpy3(ug, dt, vf), hdt2, acc);
+    v[g] = axpy3(vf, hdt, acc);
   }
 }
 
 // Corrector alone (completes the state): a = M^-1 a_raw ; v = v_half + dt/2 a
-__global__ void corrector_kernel(float4* __restrict__ v, float4* __restrict__ a, const float4* __restrict__ minv,
-                                 int n4, float hdt) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
-    const float4 m = minv[t];
-#pragma unroll
-    for (int part = 0; part < 3; ++part) {
-      const int w = 3 * t + part;
-      const float4 mm = mass_lanes(m, part);
-      float4 ar = a[w];
-      float4 vv = v[w];
-      ar.x *= mm.x;
-      ar.y *= mm.y;
-      ar.z *= mm.z;
-      ar.w *= mm.w;
-      vv.x += hdt * ar.x;
-      vv.y += hdt * ar.y;
-      vv.z += hdt * ar.z;
-      vv.w += hdt * ar.w;
-      a[w] = ar;
-      v[w] = vv;
-    }
+__global__ void corrector_kernel(float4* __restrict__ v, float4* __restrict__ a, const float* __restrict__ minv,
+                                 int nglob, float hdt) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob; g += gridDim.x * blockDim.x) {
+    const float m = minv[g];
+    const float4 ar = a[g];
+    const float4 acc = make_float4(ar.x * m, ar.y * m, ar.z * m, 0.f);
+    a[g] = acc;
+    v[g] = axpy3(v[g], hdt, acc);
   }
 }
 
-static int stream_grid(int n4) {
-  const int per = 256;
-  int g = (n4 + per - 1) / per;
+static int stream_grid(int n) {
+  const int g = (n + 255) / 256;
   return g < 1 ? 1 : g;
 }
 
 int launch_predictor(const DevProblem& p, void* stream) {
-  const int n4 = p.nglob_pad / 4;
-  predictor_kernel<<<stream_grid(n4), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      reinterpret_cast<float4*>(p.u), reinterpret_cast<float4*>(p.v), reinterpret_cast<const float4*>(p.a), n4,
+  predictor_kernel<<<stream_grid(p.nglob), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<float4*>(p.u), reinterpret_cast<float4*>(p.v), reinterpret_cast<const float4*>(p.a), p.nglob,
       static_cast<float>(p.dt), static_cast<float>(0.5 * p.dt), static_cast<float>(0.5 * p.dt * p.dt));
   return static_cast<int>(cudaGetLastError());
 }
 
 int launch_fused_newmark(const DevProblem& p, void* stream) {
-  const int n4 = p.nglob_pad / 4;
-  fused_newmark_kernel<<<stream_grid(n4), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      reinterpret_cast<float4*>(p.u), reinterpret_cast<float4*>(p.v), reinterpret_cast<const float4*>(p.a),
-      reinterpret_cast<const float4*>(p.minv), n4, static_cast<float>(p.dt), static_cast<float>(0.5 * p.dt),
-      static_cast<float>(0.5 * p.dt * p.dt));
+  fused_newmark_kernel<<<stream_grid(p.nglob), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<float4*>(p.u), reinterpret_cast<float4*>(p.v), reinterpret_cast<const float4*>(p.a), p.minv,
+      p.nglob, static_cast<float>(p.dt), static_cast<float>(0.5 * p.dt), static_cast<float>(0.5 * p.dt * p.dt));
   return static_cast<int>(cudaGetLastError());
 }
 
 int launch_corrector(const DevProblem& p, void* stream) {
-  const int n4 = p.nglob_pad / 4;
-  corrector_kernel<<<stream_grid(n4), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      reinterpret_cast<float4*>(p.v), reinterpret_cast<float4*>(p.a), reinterpret_cast<const float4*>(p.minv), n4,
+  corrector_kernel<<<stream_grid(p.nglob), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<float4*>(p.v), reinterpret_cast<float4*>(p.a), p.minv, p.nglob,
       static_cast<float>(0.5 * p.dt));
   return static_cast<int>(cudaGetLastError());
 }
@@ -219,7 +157,7 @@ __global__ void sources_record_kernel(float* __restrict__ a, const float* __rest
   const double aa = x * x;
   const double R = (1.0 - 2.0 * aa) * exp(-aa);
   for (int s = threadIdx.x; s < nsrc; s += blockDim.x) {
-    const size_t g = 3 * static_cast<size_t>(src_node[s]);
+    const size_t g = kNodeStride * static_cast<size_t>(src_node[s]);
     a[g] += static_cast<float>(src_force[3 * s] * R);
     a[g + 1] += static_cast<float>(src_force[3 * s + 1] * R);
     a[g + 2] += static_cast<float>(src_force[3 * s + 2] * R);
@@ -227,7 +165,7 @@ __global__ void sources_record_kernel(float* __restrict__ a, const float* __rest
   if (seis != nullptr && col < ncols) {
     for (int q = threadIdx.x; q < 3 * nrec; q += blockDim.x) {
       const int r = q / 3, c = q - 3 * r;
-      seis[static_cast<size_t>(q) * ncols + col] = u[3 * static_cast<size_t>(rec_node[r]) + c];
+      seis[static_cast<size_t>(q) * ncols + col] = u[kNodeStride * static_cast<size_t>(rec_node[r]) + c];
     }
   }
   __syncthreads();
@@ -257,13 +195,13 @@ int launch_sources_record(const DevProblem& p, void* stream) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Divergence watchdog: flags any non-finite value of u, v or a (the fields hold 3*nglob_pad
-// floats). Threads that find one write 1 into the flag word; the host clears it first.
+// Divergence watchdog: flags any non-finite value of u, v or a ([nglob][kNodeStride]).
+// Threads that find one write 1 into the flag word; the host clears it first.
 // ---------------------------------------------------------------------------------------
 __global__ void nonfinite_kernel(const float4* __restrict__ u, const float4* __restrict__ v,
-                                 const float4* __restrict__ a, int n4x3, int* flag) {
+                                 const float4* __restrict__ a, int nglob, int* flag) {
   bool bad = false;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4x3; t += gridDim.x * blockDim.x) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nglob; t += gridDim.x * blockDim.x) {
     const float4 x = u[t], y = v[t], z = a[t];
     bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(x.w));
     bad |= !(isfinite(y.x) && isfinite(y.y) && isfinite(y.z) && isfinite(y.w));
@@ -273,7 +211,7 @@ __global__ void nonfinite_kernel(const float4* __restrict__ u, const float4* __r
 }
 
 int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream) {
-  const int n = 3 * (p.nglob_pad / 4);
+  const int n = p.nglob;
   nonfinite_kernel<<<kEnergyBlocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const float4*>(p.u), reinterpret_cast<const float4*>(p.v),
       reinterpret_cast<const float4*>(p.a), n, flag);
@@ -283,19 +221,17 @@ int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream) {
 // ---------------------------------------------------------------------------------------
 // Energy partial sums: per block, sum_I |v_I|^2 / minv_I and sum_I u_I . f_I in float64.
 // ---------------------------------------------------------------------------------------
-__global__ void energy_partials_kernel(const float* __restrict__ u, const float* __restrict__ v,
-                                       const float* __restrict__ f, const float* __restrict__ minv, int nglob_pad,
+__global__ void energy_partials_kernel(const float4* __restrict__ u, const float4* __restrict__ v,
+                                       const float4* __restrict__ f, const float* __restrict__ minv, int nglob,
                                        double* __restrict__ partials) {
   __shared__ double sk[256], sp[256];
   double kin = 0.0, pot = 0.0;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob_pad; g += gridDim.x * blockDim.x) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob; g += gridDim.x * blockDim.x) {
     const float m = minv[g];
-    if (m > 0.f) {
-      const double vx = v[3 * g], vy = v[3 * g + 1], vz = v[3 * g + 2];
-      kin += (vx * vx + vy * vy + vz * vz) / static_cast<double>(m);
-    }
-    pot += static_cast<double>(u[3 * g]) * f[3 * g] + static_cast<double>(u[3 * g + 1]) * f[3 * g + 1] +
-           static_cast<double>(u[3 * g + 2]) * f[3 * g + 2];
+    const float4 vg = v[g], ug = u[g], fg = f[g];
+    const double vx = vg.x, vy = vg.y, vz = vg.z;
+    kin += (vx * vx + vy * vy + vz * vz) / static_cast<double>(m);
+    pot += static_cast<double>(ug.x) * fg.x + static_cast<double>(ug.y) * fg.y + static_cast<double>(ug.z) * fg.z;
   }
   sk[threadIdx.x] = kin;
   sp[threadIdx.x] = pot;
@@ -313,10 +249,11 @@ __global__ void energy_partials_kernel(const float* __restrict__ u, const float*
   }
 }
 
-int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv, int nglob_pad,
+int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv, int nglob,
                            double* partials, int nblocks, void* stream) {
-  energy_partials_kernel<<<nblocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(u, v, f, minv, nglob_pad,
-                                                                                   partials);
+  energy_partials_kernel<<<nblocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const float4*>(u), reinterpret_cast<const float4*>(v), reinterpret_cast<const float4*>(f),
+      minv, nglob, partials);
   return static_cast<int>(cudaGetLastError());
 }
 
