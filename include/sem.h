@@ -146,6 +146,11 @@ int sem_check_finite(sem_ctx* ctx);
  * overlap. Asynchronous on the context's stream. Does not touch the solver state. */
 int sem_apply_stiffness(sem_ctx* ctx, const float* u_dev, float* f_dev);
 
+/* Same with node_stride floats per node (3 or 4; with 4, x y z and an ignored 4th value,
+ * arrays 16-byte aligned): [nglob][node_stride]. Stride 4 is the layout the solver keeps
+ * its own fields in, so this times the force kernel exactly as a time step runs it. */
+int sem_apply_stiffness_strided(sem_ctx* ctx, const float* u_dev, float* f_dev, int node_stride);
+
 /* Kinetic and potential energy of the current state in float64:
  * out[0] = 1/2 sum_I M_I |v_I|^2, out[1] = 1/2 u^T K u. Synchronous. */
 int sem_energy(sem_ctx* ctx, double* out);

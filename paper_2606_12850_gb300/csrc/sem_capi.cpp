@@ -704,17 +704,24 @@ int sem_run(sem_ctx* c, int nsteps, float* seis) {
   return r;
 }
 
-int sem_apply_stiffness(sem_ctx* c, const float* u_dev, float* f_dev) {
+int sem_apply_stiffness_strided(sem_ctx* c, const float* u_dev, float* f_dev, int node_stride) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->have_mat) return fail(c, SEM_ESTATE, "sem_set_material has not been called");
   if (!u_dev || !f_dev) return fail(c, SEM_EINVAL, "sem_apply_stiffness: NULL pointer");
-  const size_t bytes = 3 * static_cast<size_t>(c->nglob) * sizeof(float);
+  if (node_stride != 3 && node_stride != 4) return fail(c, SEM_EINVAL, "node_stride must be 3 or 4");
+  if (node_stride == 4 && ((reinterpret_cast<uintptr_t>(u_dev) | reinterpret_cast<uintptr_t>(f_dev)) & 15))
+    return fail(c, SEM_EINVAL, "node_stride 4 needs 16-byte aligned arrays");
+  const size_t bytes = node_stride * static_cast<size_t>(c->nglob) * sizeof(float);
   const char* a = reinterpret_cast<const char*>(u_dev);
   const char* b = reinterpret_cast<const char*>(f_dev);
   if (a < b + bytes && b < a + bytes) return fail(c, SEM_EINVAL, "u_dev and f_dev overlap");
   int r = set_device(c);
   if (r) return r;
-  return forces_all_colors(c, u_dev, f_dev, 3);
+  return forces_all_colors(c, u_dev, f_dev, node_stride);
+}
+
+int sem_apply_stiffness(sem_ctx* c, const float* u_dev, float* f_dev) {
+  return sem_apply_stiffness_strided(c, u_dev, f_dev, 3);
 }
 
 int sem_energy(sem_ctx* c, double* out) {

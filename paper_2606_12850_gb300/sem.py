@@ -46,6 +46,7 @@ SIGNATURES = {
     "sem_run_dev": (_I, [_P, _I, _P]),
     "sem_check_finite": (_I, [_P]),
     "sem_apply_stiffness": (_I, [_P, _P, _P]),
+    "sem_apply_stiffness_strided": (_I, [_P, _P, _P, _I]),
     "sem_energy": (_I, [_P, _P]),
     "sem_energy_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
     "sem_sync": (_I, [_P]),
@@ -271,6 +272,12 @@ def sem_check_finite(ctx: Ctx):
 def sem_apply_stiffness(ctx: Ctx, u_dev, f_dev):
     n = 3 * ctx.nglob
     _check(lib().sem_apply_stiffness(ctx.handle, _dev(u_dev, n), _dev(f_dev, n)), "sem_apply_stiffness", ctx)
+
+
+def sem_apply_stiffness_strided(ctx: Ctx, u_dev, f_dev, node_stride: int):
+    n = node_stride * ctx.nglob
+    _check(lib().sem_apply_stiffness_strided(ctx.handle, _dev(u_dev, n), _dev(f_dev, n), int(node_stride)),
+           "sem_apply_stiffness_strided", ctx)
 
 
 def sem_energy(ctx: Ctx):
