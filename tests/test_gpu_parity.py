@@ -111,7 +111,8 @@ def test_stiffness_strided_matches(oracle):
     f_ref = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, *mat, 5).forces(u.astype(np.float64))
     check_forces(f4[:, :3], f_ref)
     assert np.all(f4[:, 3] == 0.0)
-    np.testing.assert_array_equal(f4[:, :3], gpu_forces(ctx, u))
+    f3 = gpu_forces(ctx, u)  # same arithmetic; the compiler may contract differently
+    assert rel_l2(f4[:, :3], f3.astype(np.float64)) <= 1e-6
     with pytest.raises(sem.SemError):
         sem.sem_apply_stiffness_strided(ctx, ud, fd, 5)
 
