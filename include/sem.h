@@ -18,8 +18,9 @@
  *   ibool    int32 [nspec][ngll^3], 0-based global node of every local point.
  *   ctrl     float64 [nspec][8][3] corner vertices of each (trilinear) hexahedron; corner
  *            c = a + 2b + 4d sits at reference (xi, eta, zeta) = (2a-1, 2b-1, 2d-1).
- *   fields   float32 [nglob][3] (x, y, z per node), metres, m/s, m/s^2.
- *   seis     float32 [nrec][3][nsteps].
+ *   fields   float32 [shots][nglob][3] (x, y, z per node), metres, m/s, m/s^2; shots = 1
+ *            unless sem_set_shots chose more.
+ *   seis     float32 [shots][nrec][3][nsteps].
  *   Step n (0-based since the last sem_set_state) advances u^n -> u^{n+1}; the source acts
  *   at t_{n+1} = (n+1) dt and the record of step n is u^{n+1}.
  *
@@ -109,8 +110,21 @@ int sem_locate_nodes(sem_ctx* ctx, int npts, const double* xyz, const double* su
 int sem_set_sources(sem_ctx* ctx, int nsrc, const int32_t* node, const double* force,
                     double f0, double t0);
 
+/* Several shots on one model (same mesh, material, dt and receivers; each shot its own
+ * sources and wavefield): the shots advance together and every element's geometry and
+ * moduli are read once per step for all of them. Reallocates the wavefields, zeroes the
+ * state and the step counter and clears the sources (set them again). nshots >= 1; the
+ * wavefields take 3 * 16 * nglob * nshots bytes. Requires sem_set_mesh. */
+int sem_set_shots(sem_ctx* ctx, int nshots);
+
+/* Point forces per shot: source s acts only in shot shot[s] (0 <= shot[s] < nshots), with
+ * the Ricker time function of sem_set_sources (which instead applies each source in every
+ * shot). */
+int sem_set_shot_sources(sem_ctx* ctx, int nsrc, const int32_t* shot, const int32_t* node,
+                         const double* force, double f0, double t0);
+
 /* Receivers: the displacement at node[r] is recorded after every step of sem_run /
- * sem_run_dev. nrec may be 0. */
+ * sem_run_dev, for every shot. nrec may be 0. */
 int sem_set_receivers(sem_ctx* ctx, int nrec, const int32_t* node);
 
 /* Set (u, v, a) at t = 0 from host arrays [nglob][3] (NULL = zero) and reset the step
@@ -178,8 +192,8 @@ int sem_energy_noalloc(sem_ctx* ctx, int nglob, const float* u_dev, const float*
 int sem_sync(sem_ctx* ctx);
 
 /* Sizes of the set-up problem: out[0] nspec, out[1] nglob, out[2] ngll, out[3] ncolors,
- * out[4] steps taken since sem_set_state, out[5] bytes of device memory held.
- * Any entry not yet defined is 0. */
+ * out[4] steps taken since sem_set_state, out[5] bytes of device memory held,
+ * out[6] shots. out has room for 7 values; an entry not yet defined is 0. */
 int sem_info(sem_ctx* ctx, int64_t* out);
 
 /* Element count of each colour, counts[ncolors] (see sem_info for ncolors). */

@@ -52,8 +52,10 @@ struct sem_ctx {
   double* d_partials = nullptr;   // scratch partial sums for sem_energy
   DevCtl* d_ctl = nullptr;
   int* d_src_node = nullptr;
+  int* d_src_shot = nullptr;
   double* d_src_force = nullptr;
   int nsrc = 0;
+  int shots = 1;  // wavefields [nglob][shots][kNodeStride]
   double f0 = 0.0, t0 = 0.0;
   int* d_rec_node = nullptr;
   int nrec = 0;
@@ -109,7 +111,7 @@ int dev_alloc(sem_ctx* c, T** p, size_t count) {
 
 void free_device(sem_ctx* c) {
   void* ptrs[] = {c->d_rec, c->d_u, c->d_v, c->d_a, c->d_minv, c->d_f, c->d_partials,
-                  c->d_ctl, c->d_src_node, c->d_src_force, c->d_rec_node};
+                  c->d_ctl, c->d_src_node, c->d_src_shot, c->d_src_force, c->d_rec_node};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->d_rec = nullptr;
@@ -117,6 +119,7 @@ void free_device(sem_ctx* c) {
   c->d_partials = nullptr;
   c->d_ctl = nullptr;
   c->d_src_node = nullptr;
+  c->d_src_shot = nullptr;
   c->d_src_force = nullptr;
   c->d_rec_node = nullptr;
   c->dev_bytes = 0;
@@ -141,6 +144,8 @@ DevProblem problem(const sem_ctx* c) {
   p.ctl = c->d_ctl;
   p.nsrc = c->nsrc;
   p.src_node = c->d_src_node;
+  p.src_shot = c->d_src_shot;
+  p.shots = c->shots;
   p.src_force = c->d_src_force;
   p.f0 = c->f0;
   p.t0 = c->t0;
@@ -156,12 +161,13 @@ int set_device(sem_ctx* c) {
 }
 
 // f = -K u over all colours in order (Sec. IV-C: colour by colour, no atomics).
-int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride = kNodeStride) {
+int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride = kNodeStride, int shots = 1) {
   ForceLaunch L{};
   L.rec = c->d_rec;
   L.u = u;
   L.f = f;
   L.node_stride = node_stride;
+  L.shots = shots;
   for (int col = 0; col < c->ncolors; ++col) {
     L.e0 = c->color_off[col];
     L.e1 = c->color_off[col + 1];
@@ -460,7 +466,7 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   free_device(c);
   c->d_ctl = keep_ctl;
   c->dev_bytes = sizeof(DevCtl);
-  const size_t nf = kNodeStride * static_cast<size_t>(nglob);
+  const size_t nf = kNodeStride * static_cast<size_t>(nglob) * c->shots;
   if ((r = dev_alloc(c, &c->d_rec, c->rec.size())) || (r = dev_alloc(c, &c->d_u, nf)) ||
       (r = dev_alloc(c, &c->d_v, nf)) || (r = dev_alloc(c, &c->d_a, nf)) ||
       (r = dev_alloc(c, &c->d_minv, static_cast<size_t>(nglob))))
@@ -552,40 +558,88 @@ int sem_locate_nodes(sem_ctx* c, int npts, const double* xyz, const double* surf
   return SEM_OK;
 }
 
-int sem_set_sources(sem_ctx* c, int nsrc, const int32_t* node, const double* force, double f0, double t0) {
+static int set_sources_impl(sem_ctx* c, int nsrc, const int32_t* shot, const int32_t* node, const double* force,
+                            double f0, double t0) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
   if (nsrc < 0 || (nsrc > 0 && (!node || !force)) || !std::isfinite(f0) || !std::isfinite(t0))
     return fail(c, SEM_EINVAL, "sem_set_sources: bad arguments");
-  // merge sources that share a node (same time function, forces add)
-  std::vector<int> nodes;
+  // one entry per (shot, node); sources sharing both merge (same time function, forces add);
+  // without a shot index a source acts in every shot
+  std::vector<int> nodes, shots;
   std::vector<double> forces;
   for (int s = 0; s < nsrc; ++s) {
     if (node[s] < 0 || node[s] >= c->nglob) return fail(c, SEM_EINVAL, "source node out of range");
+    if (shot && (shot[s] < 0 || shot[s] >= c->shots)) return fail(c, SEM_EINVAL, "source shot out of range");
     for (int d = 0; d < 3; ++d)
       if (!std::isfinite(force[3 * s + d])) return fail(c, SEM_EINVAL, "non-finite source force");
-    auto it = std::find(nodes.begin(), nodes.end(), node[s]);
-    if (it == nodes.end()) {
-      nodes.push_back(node[s]);
-      forces.insert(forces.end(), force + 3 * s, force + 3 * s + 3);
-    } else {
-      const size_t m = it - nodes.begin();
-      for (int d = 0; d < 3; ++d) forces[3 * m + d] += force[3 * s + d];
+    const int first = shot ? shot[s] : 0, last = shot ? shot[s] : c->shots - 1;
+    for (int sh = first; sh <= last; ++sh) {
+      size_t m = 0;
+      while (m < nodes.size() && !(nodes[m] == node[s] && shots[m] == sh)) ++m;
+      if (m == nodes.size()) {
+        nodes.push_back(node[s]);
+        shots.push_back(sh);
+        forces.insert(forces.end(), force + 3 * s, force + 3 * s + 3);
+      } else {
+        for (int d = 0; d < 3; ++d) forces[3 * m + d] += force[3 * s + d];
+      }
     }
   }
   int r = set_device(c);
   if (r) return r;
   cudaStreamSynchronize(c->stream);
-  c->dev_bytes -= c->nsrc * (sizeof(int) + 3 * sizeof(double));
+  c->dev_bytes -= c->nsrc * (2 * sizeof(int) + 3 * sizeof(double));
   c->nsrc = static_cast<int>(nodes.size());
-  if ((r = dev_alloc(c, &c->d_src_node, nodes.size())) || (r = dev_alloc(c, &c->d_src_force, forces.size())))
+  if ((r = dev_alloc(c, &c->d_src_node, nodes.size())) || (r = dev_alloc(c, &c->d_src_shot, shots.size())) ||
+      (r = dev_alloc(c, &c->d_src_force, forces.size())))
     return r;
   if (!nodes.empty()) {
     SEM_CUDA(c, cudaMemcpy(c->d_src_node, nodes.data(), nodes.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA(c, cudaMemcpy(c->d_src_shot, shots.data(), shots.size() * sizeof(int), cudaMemcpyHostToDevice));
     SEM_CUDA(c, cudaMemcpy(c->d_src_force, forces.data(), forces.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
   c->f0 = f0;
   c->t0 = t0;
+  drop_graph(c);
+  return SEM_OK;
+}
+
+int sem_set_sources(sem_ctx* c, int nsrc, const int32_t* node, const double* force, double f0, double t0) {
+  return set_sources_impl(c, nsrc, nullptr, node, force, f0, t0);
+}
+
+int sem_set_shot_sources(sem_ctx* c, int nsrc, const int32_t* shot, const int32_t* node, const double* force,
+                         double f0, double t0) {
+  if (nsrc > 0 && !shot) return fail(c, SEM_EINVAL, "sem_set_shot_sources: NULL shot array");
+  return set_sources_impl(c, nsrc, shot, node, force, f0, t0);
+}
+
+int sem_set_shots(sem_ctx* c, int nshots) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (nshots < 1 || static_cast<long long>(nshots) * c->nglob > (1ll << 31) - 1)
+    return fail(c, SEM_EINVAL, "sem_set_shots: nshots must be >= 1 and nglob * nshots < 2^31");
+  int r = set_device(c);
+  if (r) return r;
+  cudaStreamSynchronize(c->stream);
+  const size_t old = kNodeStride * static_cast<size_t>(c->nglob) * c->shots * sizeof(float);
+  c->dev_bytes -= 3 * old;
+  if (c->d_f) {
+    c->dev_bytes -= old;
+    cudaFree(c->d_f);
+    c->d_f = nullptr;
+  }
+  c->shots = nshots;
+  const size_t nf = kNodeStride * static_cast<size_t>(c->nglob) * nshots;
+  if ((r = dev_alloc(c, &c->d_u, nf)) || (r = dev_alloc(c, &c->d_v, nf)) || (r = dev_alloc(c, &c->d_a, nf))) return r;
+  SEM_CUDA(c, cudaMemsetAsync(c->d_u, 0, nf * sizeof(float), c->stream));
+  SEM_CUDA(c, cudaMemsetAsync(c->d_v, 0, nf * sizeof(float), c->stream));
+  SEM_CUDA(c, cudaMemsetAsync(c->d_a, 0, nf * sizeof(float), c->stream));
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->pending = false;
+  c->steps = 0;
+  c->nsrc = 0;  // sources name shots: set them again
   drop_graph(c);
   return SEM_OK;
 }
@@ -612,18 +666,22 @@ static int set_state_impl(sem_ctx* c, const float* u, const float* v, const floa
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
   int r = set_device(c);
   if (r) return r;
-  const size_t n3 = 3 * static_cast<size_t>(c->nglob);
+  const size_t n3 = 3 * static_cast<size_t>(c->nglob) * c->shots;
   if (kind == cudaMemcpyHostToDevice) {
     if ((u && !finite_all(u, n3)) || (v && !finite_all(v, n3)) || (a && !finite_all(a, n3)))
       return fail(c, SEM_EINVAL, "non-finite state value");
   }
   const float* src[3] = {u, v, a};
   float* dst[3] = {c->d_u, c->d_v, c->d_a};
+  const size_t S = c->shots;
   for (int q = 0; q < 3; ++q) {
-    SEM_CUDA(c, cudaMemsetAsync(dst[q], 0, kNodeStride * static_cast<size_t>(c->nglob) * sizeof(float), c->stream));
-    if (src[q])  // [nglob][3] -> [nglob][kNodeStride]
-      SEM_CUDA(c, cudaMemcpy2DAsync(dst[q], kNodeStride * sizeof(float), src[q], 3 * sizeof(float),
-                                    3 * sizeof(float), c->nglob, kind, c->stream));
+    SEM_CUDA(c, cudaMemsetAsync(dst[q], 0, kNodeStride * static_cast<size_t>(c->nglob) * S * sizeof(float),
+                                c->stream));
+    if (src[q])  // [shots][nglob][3] -> [nglob][shots][kNodeStride]
+      for (size_t sh = 0; sh < S; ++sh)
+        SEM_CUDA(c, cudaMemcpy2DAsync(dst[q] + kNodeStride * sh, kNodeStride * S * sizeof(float),
+                                      src[q] + 3 * static_cast<size_t>(c->nglob) * sh, 3 * sizeof(float),
+                                      3 * sizeof(float), c->nglob, kind, c->stream));
   }
   if (kind == cudaMemcpyHostToDevice) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->pending = false;
@@ -646,10 +704,13 @@ static int get_state_impl(sem_ctx* c, float* u, float* v, float* a, cudaMemcpyKi
   if (r || (r = finish_state(c))) return r;
   float* dst[3] = {u, v, a};
   const float* src[3] = {c->d_u, c->d_v, c->d_a};
+  const size_t S = c->shots;
   for (int q = 0; q < 3; ++q)
-    if (dst[q])  // [nglob][kNodeStride] -> [nglob][3]
-      SEM_CUDA(c, cudaMemcpy2DAsync(dst[q], 3 * sizeof(float), src[q], kNodeStride * sizeof(float),
-                                    3 * sizeof(float), c->nglob, kind, c->stream));
+    if (dst[q])  // [nglob][shots][kNodeStride] -> [shots][nglob][3]
+      for (size_t sh = 0; sh < S; ++sh)
+        SEM_CUDA(c, cudaMemcpy2DAsync(dst[q] + 3 * static_cast<size_t>(c->nglob) * sh, 3 * sizeof(float),
+                                      src[q] + kNodeStride * sh, kNodeStride * S * sizeof(float), 3 * sizeof(float),
+                                      c->nglob, kind, c->stream));
   if (kind == cudaMemcpyDeviceToHost) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
   return SEM_OK;
 }
@@ -687,7 +748,7 @@ int sem_run(sem_ctx* c, int nsteps, float* seis) {
   if (nsteps < 0) return fail(c, SEM_EINVAL, "nsteps must be >= 0");
   if ((r = set_device(c))) return r;
   float* d_seis = nullptr;
-  const size_t count = static_cast<size_t>(c->nrec) * 3 * nsteps;
+  const size_t count = static_cast<size_t>(c->shots) * c->nrec * 3 * nsteps;
   if (seis && count) {
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_seis), count * sizeof(float), c->stream);
     if (e != cudaSuccess) return fail(c, SEM_ENOMEM, std::string("seismogram buffer: ") + cudaGetErrorString(e));
@@ -730,14 +791,15 @@ int sem_energy(sem_ctx* c, double* out) {
   if (!out) return fail(c, SEM_EINVAL, "sem_energy: NULL output");
   int r = set_device(c);
   if (r || (r = finish_state(c))) return r;
-  const size_t nf = kNodeStride * static_cast<size_t>(c->nglob);
+  const size_t nf = kNodeStride * static_cast<size_t>(c->nglob) * c->shots;
   if (!c->d_f) {
     if ((r = dev_alloc(c, &c->d_f, nf)) || (r = dev_alloc(c, &c->d_partials, 2 * static_cast<size_t>(kEnergyBlocks))))
       return r;
     SEM_CUDA(c, cudaMemsetAsync(c->d_f, 0, nf * sizeof(float), c->stream));
   }
-  if ((r = forces_all_colors(c, c->d_u, c->d_f))) return r;
-  SEM_LAUNCH(c, launch_energy_partials(c->d_u, c->d_v, c->d_f, c->d_minv, c->nglob, c->d_partials, kEnergyBlocks,
+  if ((r = forces_all_colors(c, c->d_u, c->d_f, kNodeStride, c->shots))) return r;
+  SEM_LAUNCH(c, launch_energy_partials(c->d_u, c->d_v, c->d_f, c->d_minv, c->nglob, c->shots, c->d_partials,
+                                       kEnergyBlocks,
                                        c->stream));
   std::vector<double> part(2 * kEnergyBlocks);
   SEM_CUDA(c, cudaMemcpyAsync(part.data(), c->d_partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
@@ -769,6 +831,7 @@ int sem_info(sem_ctx* c, int64_t* out) {
   out[3] = c->ncolors;
   out[4] = c->steps;
   out[5] = static_cast<int64_t>(c->dev_bytes);
+  out[6] = c->shots;
   return SEM_OK;
 }
 

@@ -278,6 +278,202 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Batched force kernel: S shots on one mesh (same model, different sources), wavefields
+// [nglob][S][4] with the shot index innermost. One CTA per element: the element record is
+// staged in shared memory once and serves every shot, so the 52 bytes per local point of
+// geometry and moduli are read once per S shot-points instead of once per shot-point. The
+// CTA works on SB shots at a time, one team of NGLL^2 xi-line threads per shot, with the
+// same per-team arithmetic as forces_kernel; gather and scatter walk (point, shot) slots
+// with the shot fastest, so a warp moves whole 16-byte nodes of consecutive shots.
+// ---------------------------------------------------------------------------------------
+template <int N>
+struct BatchCfg {
+  static constexpr int NP = N * N * N;
+  static constexpr int NL = N * N;
+  static constexpr int SB = NL <= 32 ? 8 : (N <= 7 ? 4 : 2);  // shots in flight per CTA
+  static constexpr int T = SB * NL;
+  static constexpr int REC = (kRecFields * NP + 3) / 4 * 4;
+  static constexpr int CS = ForceCfg<N>::ES;  // per-shot cube stride (bank-padded)
+  static constexpr int SMEM_FLOATS = REC + SB * CS;
+};
+
+template <int N>
+__global__ void __launch_bounds__(BatchCfg<N>::T)
+    forces_batched_kernel(const float* __restrict__ rec, const float* __restrict__ u, float* __restrict__ f,
+                          int e0, int shots) {
+  using C = BatchCfg<N>;
+  constexpr int NP = C::NP, NL = C::NL, SB = C::SB, T = C::T, CS = C::CS, REC = C::REC;
+  extern __shared__ float4 smem4[];
+  const float* __restrict__ H = c_h;
+  const float* __restrict__ HW = c_hw;
+  const float* __restrict__ W = c_w;
+  float* sr = reinterpret_cast<float*>(smem4);  // the element record
+  float* cubes = sr + REC;                       // [SB][CS]
+  const uint32_t* sib = reinterpret_cast<const uint32_t*>(sr);  // ibool field, p order
+  const int t = threadIdx.x;
+  const int e = e0 + blockIdx.x;
+
+  const float4* r4 = reinterpret_cast<const float4*>(rec + static_cast<size_t>(e) * REC);
+  for (int q = t; q < REC / 4; q += T) smem4[q] = __ldg(r4 + q);
+  __syncthreads();
+
+  const int team = t / NL;
+  const int line = t - team * NL;
+  const int j = line % N;
+  const int k = line / N;
+  float hj[N], hk[N], hwj[N], hwk[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    hj[l] = H[j * N + l];
+    hk[l] = H[k * N + l];
+    hwj[l] = HW[l * N + j];
+    hwk[l] = HW[l * N + k];
+  }
+  const float wj = W[j], wk = W[k];
+  const float4* u4 = reinterpret_cast<const float4*>(u);
+  float4* f4 = reinterpret_cast<float4*>(f);
+
+  for (int s0 = 0; s0 < shots; s0 += SB) {
+    const int ns = min(SB, shots - s0);
+    for (int idx = t; idx < NP * ns; idx += T) {
+      const int p = idx / ns;
+      const int sh = idx - p * ns;
+      const size_t g = sib[p] & ~kFirstTouchBit;
+      const float4 q4 = __ldg(u4 + g * shots + s0 + sh);
+      float* cb = cubes + sh * CS + 3 * p;
+      cb[0] = q4.x;
+      cb[1] = q4.y;
+      cb[2] = q4.z;
+    }
+    __syncthreads();
+
+    const bool active = team < ns;
+    float* su = cubes + (active ? team : 0) * CS;
+    float* se = su + 3 * NP;
+    float* sz = su + 6 * NP;
+    float ux[N], uy[N], uz[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int p = i + N * line;
+      ux[i] = su[3 * p];
+      uy[i] = su[3 * p + 1];
+      uz[i] = su[3 * p + 2];
+    }
+    float fx[N], fy[N], fz[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) fx[i] = fy[i] = fz[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
+      float det_x = 0.f, det_y = 0.f, det_z = 0.f;
+      float dze_x = 0.f, dze_y = 0.f, dze_z = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const float h = H[i * N + l];
+        dxi_x += h * ux[l];
+        dxi_y += h * uy[l];
+        dxi_z += h * uz[l];
+        const int pe = 3 * (i + N * (l + N * k));
+        det_x += hj[l] * su[pe];
+        det_y += hj[l] * su[pe + 1];
+        det_z += hj[l] * su[pe + 2];
+        const int pz = 3 * (i + N * (j + N * l));
+        dze_x += hk[l] * su[pz];
+        dze_y += hk[l] * su[pz + 1];
+        dze_z += hk[l] * su[pz + 2];
+      }
+      const int q = i * NL + line;
+      float G[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) G[a] = sr[(kG + a) * NP + q];
+      const float jac = sr[kJac * NP + q];
+      const float kappa = sr[kKappa * NP + q];
+      const float mu = sr[kMu * NP + q];
+
+      const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
+      const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
+      const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
+      const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
+      const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
+      const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
+      const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
+      const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
+      const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
+
+      const float lam = kappa - (2.f / 3.f) * mu;
+      const float tr = uxx + uyy + uzz;
+      const float sxx = lam * tr + 2.f * mu * uxx;
+      const float syy = lam * tr + 2.f * mu * uyy;
+      const float szz = lam * tr + 2.f * mu * uzz;
+      const float sxy = mu * (uxy + uyx);
+      const float sxz = mu * (uxz + uzx);
+      const float syz = mu * (uyz + uzy);
+
+      const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
+      const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
+      const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
+#pragma unroll
+      for (int ip = 0; ip < N; ++ip) {
+        const float hw = HW[i * N + ip];
+        fx[ip] += hw * txi_x;
+        fy[ip] += hw * txi_y;
+        fz[ip] += hw * txi_z;
+      }
+      if (active) {
+        const int p3 = 3 * (i + N * line);
+        se[p3] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
+        se[p3 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
+        se[p3 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
+        sz[p3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
+        sz[p3 + 1] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
+        sz[p3 + 2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float ex = 0.f, ey = 0.f, ez = 0.f, zx = 0.f, zy = 0.f, zz = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const int pe = 3 * (i + N * (l + N * k));
+        ex += hwj[l] * se[pe];
+        ey += hwj[l] * se[pe + 1];
+        ez += hwj[l] * se[pe + 2];
+        const int pz = 3 * (i + N * (j + N * l));
+        zx += hwk[l] * sz[pz];
+        zy += hwk[l] * sz[pz + 1];
+        zz += hwk[l] * sz[pz + 2];
+      }
+      const float wi = W[i];
+      if (active) {
+        const int p = 3 * (i + N * line);
+        su[p] = -(wj * wk * fx[i] + wi * wk * ex + wi * wj * zx);
+        su[p + 1] = -(wj * wk * fy[i] + wi * wk * ey + wi * wj * zy);
+        su[p + 2] = -(wj * wk * fz[i] + wi * wk * ez + wi * wj * zz);
+      }
+    }
+    __syncthreads();
+    for (int idx = t; idx < NP * ns; idx += T) {
+      const int p = idx / ns;
+      const int sh = idx - p * ns;
+      const uint32_t w = sib[p];
+      const size_t g = w & ~kFirstTouchBit;
+      const float* src = cubes + sh * CS + 3 * p;
+      float4* dst = f4 + g * shots + s0 + sh;
+      float4 o = make_float4(src[0], src[1], src[2], 0.f);
+      if (!(w & kFirstTouchBit)) {
+        const float4 prev = *dst;
+        o.x += prev.x;
+        o.y += prev.y;
+        o.z += prev.z;
+      }
+      *dst = o;
+    }
+    __syncthreads();
+  }
+}
+
 template <int VS>
 int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   using C = ForceCfg<SEM_NGLL>;
@@ -297,8 +493,26 @@ int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   return static_cast<int>(cudaGetLastError());
 }
 
+int launch_forces_batched(const ForceLaunch& L, cudaStream_t s) {
+  using C = BatchCfg<SEM_NGLL>;
+  static unsigned long long attr_done = 0;
+  const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_done & bit)) {
+    cudaError_t e =
+        cudaFuncSetAttribute(forces_batched_kernel<SEM_NGLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    attr_done |= bit;
+  }
+  forces_batched_kernel<SEM_NGLL><<<L.e1 - L.e0, C::T, smem, s>>>(L.rec, L.u, L.f, L.e0, L.shots);
+  return static_cast<int>(cudaGetLastError());
+}
+
 int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
   if (L.e1 <= L.e0) return 0;
+  if (L.shots > 1) return L.node_stride == 4 ? launch_forces_batched(L, s) : static_cast<int>(cudaErrorInvalidValue);
   if (L.node_stride == 4) return launch_forces_vs<4>(L, s);
   if (L.node_stride == 3) return launch_forces_vs<3>(L, s);
   return static_cast<int>(cudaErrorInvalidValue);

@@ -70,6 +70,7 @@ struct DevProblem {
   int ngll;
   int nspec;
   int nglob;
+  int shots;  // wavefields are [nglob][shots][kNodeStride]
   const float* rec;
   float* u;
   float* v;
@@ -77,7 +78,8 @@ struct DevProblem {
   const float* minv;
   DevCtl* ctl;
   int nsrc;
-  const int* src_node;
+  const int* src_node;   // per source: global node
+  const int* src_shot;   // per source: shot it acts in
   const double* src_force;
   double f0, t0;
   int nrec;
@@ -96,6 +98,7 @@ struct ForceLaunch {
   float* f;
   int e0, e1;
   int node_stride;  // floats per node in u and f: kNodeStride, or 3 for caller arrays
+  int shots;        // > 1: u and f are [nglob][shots][kNodeStride] (batched kernel)
 };
 int launch_forces(int ngll, const ForceLaunch& launch, void* stream);
 int forces_kernel_smem_bytes(int ngll);
@@ -108,7 +111,7 @@ int launch_corrector(const DevProblem& p, void* stream);
 int launch_sources_record(const DevProblem& p, void* stream);
 int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream);
 int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv,
-                           int nglob, double* partials, int nblocks, void* stream);
+                           int nglob, int shots, double* partials, int nblocks, void* stream);
 constexpr int kEnergyBlocks = 608;  // 4 CTAs per SM on 152 SMs
 
 // ---- context access for entry points defined outside sem_capi.cpp ----------------------

@@ -67,8 +67,8 @@ int forces_elements_per_cta(int n) {
 
 // ---------------------------------------------------------------------------------------
 // Newmark streaming passes (Sec. I / V-C explicit second-order Newmark, diagonal mass).
-// Fields are [nglob][kNodeStride] float32: one thread per node reads one float4 of each
-// field (the 4th lane stays zero) and the node's inverse mass.
+// Fields are [nglob][shots][kNodeStride] float32: one thread per (node, shot) reads one
+// float4 of each field (the 4th lane stays zero) and the node's inverse mass.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ float4 axpy3(float4 y, float s, float4 x) {
   return make_float4(y.x + s * x.x, y.y + s * x.y, y.z + s * x.z, 0.f);
@@ -76,8 +76,9 @@ __device__ __forceinline__ float4 axpy3(float4 y, float s, float4 x) {
 
 // Predictor from a complete state (first step): u += dt v + dt^2/2 a ; v += dt/2 a.
 __global__ void predictor_kernel(float4* __restrict__ u, float4* __restrict__ v, const float4* __restrict__ a,
-                                 int nglob, float dt, float hdt, float hdt2) {
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob; g += gridDim.x * blockDim.x) {
+                                 long long n, float dt, float hdt, float hdt2) {
+  for (long long g = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; g < n;
+       g += static_cast<long long>(gridDim.x) * blockDim.x) {
     const float4 ag = a[g], vg = v[g], ug = u[g];
     u[g] = axpy3(axpy3(ug, dt, vg), hdt2, ag);
     v[g] = axpy3(vg, hdt, ag);
@@ -88,10 +89,11 @@ __global__ void predictor_kernel(float4* __restrict__ u, float4* __restrict__ v,
 //   a = M^-1 a_raw ; v = v_half + dt/2 a ; u += dt v + dt^2/2 a ; v_half = v + dt/2 a
 // a_raw stays in place: the next force sweep overwrites it at each node's first touch.
 __global__ void fused_newmark_kernel(float4* __restrict__ u, float4* __restrict__ v,
-                                     const float4* __restrict__ a, const float* __restrict__ minv, int nglob,
-                                     float dt, float hdt, float hdt2) {
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob; g += gridDim.x * blockDim.x) {
-    const float m = minv[g];
+                                     const float4* __restrict__ a, const float* __restrict__ minv, long long n,
+                                     int shots, float dt, float hdt, float hdt2) {
+  for (long long g = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; g < n;
+       g += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float m = minv[g / shots];
     const float4 ar = a[g], vh = v[g], ug = u[g];
     const float4 acc = make_float4(ar.x * m, ar.y * m, ar.z * m, 0.f);
     const float4 vf = axpy3(vh, hdt, acc);
@@ -102,9 +104,10 @@ __global__ void fused_newmark_kernel(float4* __restrict__ u, float4* __restrict_
 
 // Corrector alone (completes the state): a = M^-1 a_raw ; v = v_half + dt/2 a
 __global__ void corrector_kernel(float4* __restrict__ v, float4* __restrict__ a, const float* __restrict__ minv,
-                                 int nglob, float hdt) {
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob; g += gridDim.x * blockDim.x) {
-    const float m = minv[g];
+                                 long long n, int shots, float hdt) {
+  for (long long g = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; g < n;
+       g += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float m = minv[g / shots];
     const float4 ar = a[g];
     const float4 acc = make_float4(ar.x * m, ar.y * m, ar.z * m, 0.f);
     a[g] = acc;
@@ -112,28 +115,31 @@ __global__ void corrector_kernel(float4* __restrict__ v, float4* __restrict__ a,
   }
 }
 
-static int stream_grid(int n) {
-  const int g = (n + 255) / 256;
-  return g < 1 ? 1 : g;
+static int stream_grid(long long n) {
+  const long long g = (n + 255) / 256;
+  return g < 1 ? 1 : static_cast<int>(g < (1ll << 30) ? g : (1ll << 30));
 }
 
 int launch_predictor(const DevProblem& p, void* stream) {
-  predictor_kernel<<<stream_grid(p.nglob), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      reinterpret_cast<float4*>(p.u), reinterpret_cast<float4*>(p.v), reinterpret_cast<const float4*>(p.a), p.nglob,
+  const long long n = static_cast<long long>(p.nglob) * p.shots;
+  predictor_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<float4*>(p.u), reinterpret_cast<float4*>(p.v), reinterpret_cast<const float4*>(p.a), n,
       static_cast<float>(p.dt), static_cast<float>(0.5 * p.dt), static_cast<float>(0.5 * p.dt * p.dt));
   return static_cast<int>(cudaGetLastError());
 }
 
 int launch_fused_newmark(const DevProblem& p, void* stream) {
-  fused_newmark_kernel<<<stream_grid(p.nglob), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+  const long long n = static_cast<long long>(p.nglob) * p.shots;
+  fused_newmark_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<float4*>(p.u), reinterpret_cast<float4*>(p.v), reinterpret_cast<const float4*>(p.a), p.minv,
-      p.nglob, static_cast<float>(p.dt), static_cast<float>(0.5 * p.dt), static_cast<float>(0.5 * p.dt * p.dt));
+      n, p.shots, static_cast<float>(p.dt), static_cast<float>(0.5 * p.dt), static_cast<float>(0.5 * p.dt * p.dt));
   return static_cast<int>(cudaGetLastError());
 }
 
 int launch_corrector(const DevProblem& p, void* stream) {
-  corrector_kernel<<<stream_grid(p.nglob), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      reinterpret_cast<float4*>(p.v), reinterpret_cast<float4*>(p.a), p.minv, p.nglob,
+  const long long n = static_cast<long long>(p.nglob) * p.shots;
+  corrector_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<float4*>(p.v), reinterpret_cast<float4*>(p.a), p.minv, n, p.shots,
       static_cast<float>(0.5 * p.dt));
   return static_cast<int>(cudaGetLastError());
 }
@@ -143,8 +149,8 @@ int launch_corrector(const DevProblem& p, void* stream) {
 // displacement u^{n+1} sampled at the receiver nodes; advances the device step counter.
 // Source nodes are distinct (the host merges duplicates), so the adds do not race.
 // ---------------------------------------------------------------------------------------
-__global__ void sources_record_kernel(float* __restrict__ a, const float* __restrict__ u, DevCtl* ctl,
-                                      int nsrc, const int* __restrict__ src_node,
+__global__ void sources_record_kernel(float* __restrict__ a, const float* __restrict__ u, DevCtl* ctl, int shots,
+                                      int nsrc, const int* __restrict__ src_node, const int* __restrict__ src_shot,
                                       const double* __restrict__ src_force, double f0, double t0, double dt,
                                       int nrec, const int* __restrict__ rec_node) {
   const long long n = ctl->step;
@@ -157,15 +163,18 @@ __global__ void sources_record_kernel(float* __restrict__ a, const float* __rest
   const double aa = x * x;
   const double R = (1.0 - 2.0 * aa) * exp(-aa);
   for (int s = threadIdx.x; s < nsrc; s += blockDim.x) {
-    const size_t g = kNodeStride * static_cast<size_t>(src_node[s]);
+    const size_t g = kNodeStride * (static_cast<size_t>(src_node[s]) * shots + src_shot[s]);
     a[g] += static_cast<float>(src_force[3 * s] * R);
     a[g + 1] += static_cast<float>(src_force[3 * s + 1] * R);
     a[g + 2] += static_cast<float>(src_force[3 * s + 2] * R);
   }
-  if (seis != nullptr && col < ncols) {
-    for (int q = threadIdx.x; q < 3 * nrec; q += blockDim.x) {
-      const int r = q / 3, c = q - 3 * r;
-      seis[static_cast<size_t>(q) * ncols + col] = u[kNodeStride * static_cast<size_t>(rec_node[r]) + c];
+  if (seis != nullptr && col < ncols) {  // seis [shots][nrec][3][ncols]
+    for (int q = threadIdx.x; q < 3 * nrec * shots; q += blockDim.x) {
+      const int sh = q / (3 * nrec);
+      const int rq = q - sh * 3 * nrec;
+      const int r = rq / 3, c = rq - 3 * r;
+      seis[static_cast<size_t>(q) * ncols + col] =
+          u[kNodeStride * (static_cast<size_t>(rec_node[r]) * shots + sh) + c];
     }
   }
   __syncthreads();
@@ -190,7 +199,7 @@ int launch_set_ctl(DevCtl* ctl, long long step, int ncols, float* seis, void* st
 
 int launch_sources_record(const DevProblem& p, void* stream) {
   sources_record_kernel<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      p.a, p.u, p.ctl, p.nsrc, p.src_node, p.src_force, p.f0, p.t0, p.dt, p.nrec, p.rec_node);
+      p.a, p.u, p.ctl, p.shots, p.nsrc, p.src_node, p.src_shot, p.src_force, p.f0, p.t0, p.dt, p.nrec, p.rec_node);
   return static_cast<int>(cudaGetLastError());
 }
 
@@ -211,7 +220,7 @@ __global__ void nonfinite_kernel(const float4* __restrict__ u, const float4* __r
 }
 
 int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream) {
-  const int n = p.nglob;
+  const int n = p.nglob * p.shots;
   nonfinite_kernel<<<kEnergyBlocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const float4*>(p.u), reinterpret_cast<const float4*>(p.v),
       reinterpret_cast<const float4*>(p.a), n, flag);
@@ -223,11 +232,13 @@ int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream) {
 // ---------------------------------------------------------------------------------------
 __global__ void energy_partials_kernel(const float4* __restrict__ u, const float4* __restrict__ v,
                                        const float4* __restrict__ f, const float* __restrict__ minv, int nglob,
-                                       double* __restrict__ partials) {
+                                       int shots, double* __restrict__ partials) {
   __shared__ double sk[256], sp[256];
   double kin = 0.0, pot = 0.0;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob; g += gridDim.x * blockDim.x) {
-    const float m = minv[g];
+  const long long n = static_cast<long long>(nglob) * shots;
+  for (long long g = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; g < n;
+       g += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float m = minv[g / shots];
     const float4 vg = v[g], ug = u[g], fg = f[g];
     const double vx = vg.x, vy = vg.y, vz = vg.z;
     kin += (vx * vx + vy * vy + vz * vz) / static_cast<double>(m);
@@ -250,10 +261,10 @@ __global__ void energy_partials_kernel(const float4* __restrict__ u, const float
 }
 
 int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv, int nglob,
-                           double* partials, int nblocks, void* stream) {
+                           int shots, double* partials, int nblocks, void* stream) {
   energy_partials_kernel<<<nblocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const float4*>(u), reinterpret_cast<const float4*>(v), reinterpret_cast<const float4*>(f),
-      minv, nglob, partials);
+      minv, nglob, shots, partials);
   return static_cast<int>(cudaGetLastError());
 }
 

@@ -221,3 +221,20 @@ def layered_cube(ngll: int = 5, n: int | None = None, side: float = 4000.0, jitt
 def random_field(nglob: int, seed: int, scale: float = 1.0, stream: int = 7) -> np.ndarray:
     """Seeded U(-scale, scale) wavefield, float32 [nglob][3]."""
     return uniform(seed, (nglob, 3), -scale, scale, stream=stream).astype(np.float32)
+
+
+def shot_positions(nshots: int, side: float, seed: int = 3, margin: float = 0.1) -> np.ndarray:
+    """Seeded source positions, i.i.d. uniform in [margin, 1 - margin]^3 * side, [nshots][3]."""
+    return uniform(seed, (nshots, 3), margin * side, (1.0 - margin) * side, stream=11)
+
+
+def batched_layered_cube(n: int = 48, ngll: int = 5, nshots: int = 32, seed: int = 2606,
+                         shot_seed: int = 3, nsteps: int = 1000) -> tuple:
+    """Many shots on one model: the three-layer jittered cube (side 4 km) with ``n`` elements
+    per side and ``nshots`` Ricker +z point forces at seeded random positions (one per shot),
+    sharing the 16 x 16 surface receivers. Returns (workload, source positions [nshots][3])."""
+    w = layered_cube(ngll, n=n, seed=seed, nsteps=nsteps)
+    pos = shot_positions(nshots, w.mesh.lengths[0], shot_seed)
+    w.name = f"{w.name}, {nshots} shots"
+    w.extra["shot_xyz"] = pos
+    return w, pos

@@ -37,6 +37,8 @@ SIGNATURES = {
     "sem_locate_nodes": (_I, [_P, _I, _P, _P, _P]),
     "sem_set_sources": (_I, [_P, _I, _P, _P, _D, _D]),
     "sem_set_receivers": (_I, [_P, _I, _P]),
+    "sem_set_shots": (_I, [_P, _I]),
+    "sem_set_shot_sources": (_I, [_P, _I, _P, _P, _P, _D, _D]),
     "sem_set_state": (_I, [_P, _P, _P, _P]),
     "sem_set_state_dev": (_I, [_P, _P, _P, _P]),
     "sem_get_state": (_I, [_P, _P, _P, _P]),
@@ -121,6 +123,7 @@ class Ctx:
         self.nglob = 0
         self.nspec = 0
         self.nrec = 0
+        self.shots = 1
 
     def __del__(self):
         if getattr(self, "handle", None) is not None and _lib is not None:
@@ -206,6 +209,19 @@ def sem_set_sources(ctx: Ctx, node, force, f0: float, t0: float):
     _check(lib().sem_set_sources(ctx.handle, nd.size, pn, pf, float(f0), float(t0)), "sem_set_sources", ctx)
 
 
+def sem_set_shots(ctx: Ctx, nshots: int):
+    _check(lib().sem_set_shots(ctx.handle, int(nshots)), "sem_set_shots", ctx)
+    ctx.shots = int(nshots)
+
+
+def sem_set_shot_sources(ctx: Ctx, shot, node, force, f0: float, t0: float):
+    sh, ps = _host(np.atleast_1d(shot), np.int32)
+    nd, pn = _host(np.atleast_1d(node), np.int32, (sh.size,))
+    fo, pf = _host(np.atleast_2d(force), np.float64, (sh.size, 3))
+    _check(lib().sem_set_shot_sources(ctx.handle, sh.size, ps, pn, pf, float(f0), float(t0)),
+           "sem_set_shot_sources", ctx)
+
+
 def sem_set_receivers(ctx: Ctx, node):
     nd, pn = _host(np.atleast_1d(node), np.int32)
     _check(lib().sem_set_receivers(ctx.handle, nd.size, pn), "sem_set_receivers", ctx)
@@ -218,7 +234,7 @@ def _state_ptrs(ctx, arrays):
         if a is None:
             ptrs.append(None)
         else:
-            arr, p = _host(a, np.float32, (ctx.nglob, 3))
+            arr, p = _host(a, np.float32, (ctx.shots, ctx.nglob, 3))
             keep.append(arr)
             ptrs.append(p)
     return keep, ptrs
@@ -230,19 +246,20 @@ def sem_set_state(ctx: Ctx, u=None, v=None, a=None):
 
 
 def sem_set_state_dev(ctx: Ctx, u=None, v=None, a=None):
-    n = 3 * ctx.nglob
+    n = 3 * ctx.nglob * ctx.shots
     _check(lib().sem_set_state_dev(ctx.handle, _dev(u, n), _dev(v, n), _dev(a, n)), "sem_set_state_dev", ctx)
 
 
 def sem_get_state(ctx: Ctx, want=(True, True, True)):
-    outs = [np.empty((ctx.nglob, 3), dtype=np.float32) if w else None for w in want]
+    shape = (ctx.nglob, 3) if ctx.shots == 1 else (ctx.shots, ctx.nglob, 3)
+    outs = [np.empty(shape, dtype=np.float32) if w else None for w in want]
     ptrs = [o.ctypes.data_as(_P) if o is not None else None for o in outs]
     _check(lib().sem_get_state(ctx.handle, *ptrs), "sem_get_state", ctx)
     return tuple(outs)
 
 
 def sem_get_state_dev(ctx: Ctx, u=None, v=None, a=None):
-    n = 3 * ctx.nglob
+    n = 3 * ctx.nglob * ctx.shots
     _check(lib().sem_get_state_dev(ctx.handle, _dev(u, n), _dev(v, n), _dev(a, n)), "sem_get_state_dev", ctx)
 
 
@@ -253,16 +270,18 @@ def sem_step(ctx: Ctx, nsteps: int):
 def sem_run(ctx: Ctx, nsteps: int, record: bool = True, out=None):
     seis = None
     if record and ctx.nrec:
-        seis = out if out is not None else np.empty((ctx.nrec, 3, nsteps), dtype=np.float32)
-        if seis.dtype != np.float32 or not seis.flags.c_contiguous or seis.size != ctx.nrec * 3 * nsteps:
-            raise ValueError("out must be a contiguous float32 [nrec][3][nsteps] array")
+        shape = (ctx.nrec, 3, nsteps) if ctx.shots == 1 else (ctx.shots, ctx.nrec, 3, nsteps)
+        seis = out if out is not None else np.empty(shape, dtype=np.float32)
+        if seis.dtype != np.float32 or not seis.flags.c_contiguous or seis.size != int(np.prod(shape)):
+            raise ValueError("out must be a contiguous float32 [shots][nrec][3][nsteps] array")
     _check(lib().sem_run(ctx.handle, int(nsteps), seis.ctypes.data_as(_P) if seis is not None else None),
            "sem_run", ctx)
     return seis
 
 
 def sem_run_dev(ctx: Ctx, nsteps: int, seis_dev=None):
-    _check(lib().sem_run_dev(ctx.handle, int(nsteps), _dev(seis_dev, ctx.nrec * 3 * nsteps)), "sem_run_dev", ctx)
+    _check(lib().sem_run_dev(ctx.handle, int(nsteps), _dev(seis_dev, ctx.shots * ctx.nrec * 3 * nsteps)),
+           "sem_run_dev", ctx)
 
 
 def sem_check_finite(ctx: Ctx):
@@ -301,9 +320,9 @@ def sem_sync(ctx: Ctx):
 
 
 def sem_info(ctx: Ctx) -> dict:
-    out = np.zeros(6, dtype=np.int64)
+    out = np.zeros(7, dtype=np.int64)
     _check(lib().sem_info(ctx.handle, out.ctypes.data_as(_P)), "sem_info", ctx)
-    keys = ("nspec", "nglob", "ngll", "ncolors", "steps", "device_bytes")
+    keys = ("nspec", "nglob", "ngll", "ncolors", "steps", "device_bytes", "shots")
     return {k: int(v) for k, v in zip(keys, out)}
 
 
