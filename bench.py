@@ -48,6 +48,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    p.add_argument("--shots", type=int, default=32, help="batched-shot measurement (0 = skip)")
+    p.add_argument("--shot-steps", type=int, default=100)
     return p.parse_args()
 
 
@@ -242,6 +244,56 @@ def run_reference(args):
     return 0
 
 
+def measure_batched(args, device: int):
+    """Many shots on one model vs one shot at a time: the three-layer jittered cube with 48^3
+    elements at NGLL=5 and S Ricker sources at seeded random positions. Shots/s are quoted
+    for a 1000-step shot; rel_l2 compares the batched seismograms of two shots with their
+    plain single-shot runs after the timed steps' worth of steps."""
+    import torch
+
+    from paper_2606_12850_gb300 import inputs, sem
+
+    S, K = args.shots, args.shot_steps
+    w, pos = inputs.batched_layered_cube(n=48, ngll=5, nshots=S)
+    stream = torch.cuda.Stream(device=device)
+    plain = sem.setup_workload(w, device=device, stream=stream)
+    nodes = sem.sem_locate_nodes(plain.ctx, pos)
+    force = np.tile([0.0, 0.0, 1.0e10], (S, 1))
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(ctx, steps):
+        a, b = ev(), ev()
+        sem.sem_run_dev(ctx, 5, None)
+        a.record(stream)
+        sem.sem_run_dev(ctx, steps, None)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / steps
+
+    sem.sem_set_sources(plain.ctx, nodes[:1], force[:1], w.f0, w.t0)
+    ms_plain = timed(plain.ctx, K)
+    batch = sem.setup_workload(w, device=device, stream=stream, src_nodes=nodes[:1], rec_nodes=plain.rec_nodes)
+    sem.sem_set_shots(batch.ctx, S)
+    sem.sem_set_shot_sources(batch.ctx, np.arange(S), nodes, force, w.f0, w.t0)
+    sem.sem_set_state(batch.ctx)
+    ms_batch = timed(batch.ctx, K)
+    # accuracy: batched vs plain seismograms of shots 0 and S-1 over 200 steps
+    sem.sem_set_state(batch.ctx)
+    seis_b = sem.sem_run(batch.ctx, 200)
+    errs = []
+    for sh in (0, S - 1):
+        sem.sem_set_sources(plain.ctx, nodes[sh:sh + 1], force[sh:sh + 1], w.f0, w.t0)
+        sem.sem_set_state(plain.ctx)
+        seis_p = sem.sem_run(plain.ctx, 200)
+        errs.append(float(np.linalg.norm(seis_b[sh] - seis_p) / np.linalg.norm(seis_p)))
+    nloc = w.mesh.nlocal
+    return {"model": f"three-layer jittered cube 48^3 hex, NGLL=5, {S} shots at seeded random positions",
+            "shots": S, "steps_timed": K, "ms_per_step_batched": ms_batch, "ms_per_step_plain_one_shot": ms_plain,
+            "shots_per_s_batched": S / (ms_batch * 1e-3 * 1000), "shots_per_s_plain": 1.0 / (ms_plain * 1e-3 * 1000),
+            "speedup": S * ms_plain / ms_batch, "shot_pt_updates_per_s_batched": S * nloc / (ms_batch * 1e-3),
+            "rel_l2_vs_plain": max(errs), "shot_steps_for_shots_per_s": 1000}
+
+
 def run_ours(args):
     import torch
 
@@ -335,6 +387,11 @@ def run_ours(args):
                "what": "sem_set_state (u,v,a from pinned host) + sem_run (K steps, seismograms to host) + "
                        "sem_get_state (u to host), wall clock"}
 
+    batched = None
+    if args.shots > 1:
+        del s, ctx
+        batched = measure_batched(args, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, _, _ = oracle_sample_rate(args.ngll, args.cpu_seconds)
@@ -360,6 +417,7 @@ def run_ours(args):
                                   "bytes_per_step": alg["step"]},
             "global_pt_updates_per_s": world * mesh.nglob * K / (ms / 1e3),
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clock_info,
+            "batched_shots": batched,
             "kernel_sources": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)
