@@ -277,21 +277,24 @@ def measure_batched(args, device: int):
     sem.sem_set_shot_sources(batch.ctx, np.arange(S), nodes, force, w.f0, w.t0)
     sem.sem_set_state(batch.ctx)
     ms_batch = timed(batch.ctx, K)
-    # accuracy: batched vs plain seismograms of shots 0 and S-1 over 200 steps
+    # accuracy: batched vs plain displacement fields of shots 0 and S-1 after 200 steps
     sem.sem_set_state(batch.ctx)
-    seis_b = sem.sem_run(batch.ctx, 200)
+    sem.sem_run(batch.ctx, 200)
+    u_b, _, _ = sem.sem_get_state(batch.ctx, want=(True, False, False))
     errs = []
     for sh in (0, S - 1):
         sem.sem_set_sources(plain.ctx, nodes[sh:sh + 1], force[sh:sh + 1], w.f0, w.t0)
         sem.sem_set_state(plain.ctx)
-        seis_p = sem.sem_run(plain.ctx, 200)
-        errs.append(float(np.linalg.norm(seis_b[sh] - seis_p) / np.linalg.norm(seis_p)))
+        sem.sem_run(plain.ctx, 200)
+        u_p, _, _ = sem.sem_get_state(plain.ctx, want=(True, False, False))
+        errs.append(float(np.linalg.norm(u_b[sh] - u_p) / np.linalg.norm(u_p)))
     nloc = w.mesh.nlocal
     return {"model": f"three-layer jittered cube 48^3 hex, NGLL=5, {S} shots at seeded random positions",
             "shots": S, "steps_timed": K, "ms_per_step_batched": ms_batch, "ms_per_step_plain_one_shot": ms_plain,
             "shots_per_s_batched": S / (ms_batch * 1e-3 * 1000), "shots_per_s_plain": 1.0 / (ms_plain * 1e-3 * 1000),
             "speedup": S * ms_plain / ms_batch, "shot_pt_updates_per_s_batched": S * nloc / (ms_batch * 1e-3),
-            "rel_l2_vs_plain": max(errs), "shot_steps_for_shots_per_s": 1000}
+            "rel_l2_vs_plain": max(errs), "rel_l2_what": "displacement of shots 0 and S-1 after 200 steps",
+            "shot_steps_for_shots_per_s": 1000}
 
 
 def run_ours(args):
@@ -389,8 +392,11 @@ def run_ours(args):
 
     batched = None
     if args.shots > 1:
+        dt_main = s.dt
         del s, ctx
         batched = measure_batched(args, local)
+    else:
+        dt_main = s.dt
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -405,7 +411,7 @@ def run_ours(args):
             "config": {"workload": f"three-layer jittered cube {mesh.nx}^3 hex, NGLL={mesh.ngll}, 4 km "
                                    "(plain SEM scaling / (h,p) sweep configuration)",
                        "ngll": mesh.ngll, "nspec": mesh.nspec, "nglob": mesh.nglob, "nlocal": alg["nloc"],
-                       "ncolors": ncolors, "nrec": nrec, "dt": s.dt,
+                       "ncolors": ncolors, "nrec": nrec, "dt": dt_main,
                        "l2": "inputs larger than L2: 1.7 GB of element records stream every step",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -161,7 +161,7 @@ int set_device(sem_ctx* c) {
 }
 
 // f = -K u over all colours in order (Sec. IV-C: colour by colour, no atomics).
-int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride = kNodeStride, int shots = 1) {
+int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int shots) {
   ForceLaunch L{};
   L.rec = c->d_rec;
   L.u = u;
@@ -185,7 +185,7 @@ int enqueue_step(sem_ctx* c, bool first) {
     SEM_LAUNCH(c, launch_predictor(p, c->stream));
   else
     SEM_LAUNCH(c, launch_fused_newmark(p, c->stream));
-  int r = forces_all_colors(c, c->d_u, c->d_a);
+  int r = forces_all_colors(c, c->d_u, c->d_a, kNodeStride, c->shots);
   if (r) return r;
   SEM_LAUNCH(c, launch_sources_record(p, c->stream));
   return SEM_OK;
@@ -778,7 +778,7 @@ int sem_apply_stiffness_strided(sem_ctx* c, const float* u_dev, float* f_dev, in
   if (a < b + bytes && b < a + bytes) return fail(c, SEM_EINVAL, "u_dev and f_dev overlap");
   int r = set_device(c);
   if (r) return r;
-  return forces_all_colors(c, u_dev, f_dev, node_stride);
+  return forces_all_colors(c, u_dev, f_dev, node_stride, 1);
 }
 
 int sem_apply_stiffness(sem_ctx* c, const float* u_dev, float* f_dev) {
