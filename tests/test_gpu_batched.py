@@ -27,14 +27,6 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-def _setup(w, nodes, shots):
-    s = sem.setup_workload(w)
-    if shots > 1:
-        sem.sem_set_shots(s.ctx, shots)
-        sem.sem_set_state(s.ctx)
-    return s
-
-
 def _batched_and_plain(ngll, n, nshots, nsteps):
     w, pos = inputs.batched_layered_cube(n=n, ngll=ngll, nshots=nshots, nsteps=nsteps)
     ref = sem.setup_workload(w)

@@ -113,8 +113,7 @@ def test_stiffness_strided_matches(oracle):
     assert np.all(f4[:, 3] == 0.0)
     f3 = gpu_forces(ctx, u)  # same arithmetic; the compiler may contract differently
     assert rel_l2(f4[:, :3], f3.astype(np.float64)) <= 1e-6
-    with pytest.raises(sem.SemError):
-        sem.sem_apply_stiffness_strided(ctx, ud, fd, 5)
+    assert sem.lib().sem_apply_stiffness_strided(ctx.handle, sem._P(ud.data_ptr()), sem._P(fd.data_ptr()), 5) == -1
 
 
 def test_stiffness_periodic(oracle):
