@@ -50,6 +50,7 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     p.add_argument("--shots", type=int, default=32, help="batched-shot measurement (0 = skip)")
     p.add_argument("--shot-steps", type=int, default=100)
+    p.add_argument("--no-sweep", action="store_true", help="skip the NGLL 3/5/7/9 (h,p) sweep")
     return p.parse_args()
 
 
@@ -297,6 +298,35 @@ def measure_batched(args, device: int):
             "shot_steps_for_shots_per_s": 1000}
 
 
+def measure_hp_sweep(device: int, steps: int = 50):
+    """(h,p) cost on GB300 at a fixed number of GLL intervals per side (256, i.e. fixed
+    points per wavelength): for NGLL = 3, 5, 7, 9 the throughput, the CFL step, device
+    memory and the device time to simulate one second (steps = 1 s / dt)."""
+    import torch
+
+    from paper_2606_12850_gb300 import inputs, sem
+
+    out = []
+    for ngll in (3, 5, 7, 9):
+        w = inputs.layered_cube(ngll)
+        stream = torch.cuda.Stream(device=device)
+        s = sem.setup_workload(w, device=device, stream=stream)
+        info = sem.sem_info(s.ctx)
+        sem.sem_run_dev(s.ctx, 5, None)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sem.sem_run_dev(s.ctx, steps, None)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        nloc = w.mesh.nlocal
+        out.append({"ngll": ngll, "elements": f"{w.mesh.nx}^3", "nlocal": nloc, "nglob": w.mesh.nglob,
+                    "ms_per_step": ms, "updates_per_s": nloc / (ms * 1e-3), "dt": s.dt,
+                    "device_mb": info["device_bytes"] / 1e6, "seconds_per_simulated_second": ms * 1e-3 / s.dt})
+        del s
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -398,6 +428,10 @@ def run_ours(args):
     else:
         dt_main = s.dt
 
+    sweep = None
+    if not args.no_sweep:
+        sweep = measure_hp_sweep(local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, _, _ = oracle_sample_rate(args.ngll, args.cpu_seconds)
@@ -423,7 +457,7 @@ def run_ours(args):
                                   "bytes_per_step": alg["step"]},
             "global_pt_updates_per_s": world * mesh.nglob * K / (ms / 1e3),
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clock_info,
-            "batched_shots": batched,
+            "batched_shots": batched, "hp_sweep": sweep,
             "kernel_sources": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)
