@@ -421,3 +421,110 @@ def run_workload(workload, nsteps: int | None = None, model: Model | None = None
     seis, u, v, a = newmark_run(model, dt, n, src_nodes=src, src_force=workload.source_force,
                                 f0=workload.f0, t0=workload.t0, rec_nodes=rec)
     return dict(seis=seis, u=u, v=v, a=a, dt=dt, src=src, rec=rec, model=model)
+
+
+# --------------------------------------------------------------------------------------
+# Discrete adjoint and material sensitivities (the gradient of a seismogram loss)
+# --------------------------------------------------------------------------------------
+#
+# From a zero state the explicit Newmark scheme above is the leapfrog recursion
+#     M (u^{n+1} - 2 u^n + u^{n-1}) + dt^2 (K u^n - f^n) = 0,   n = 1 .. N-1,
+# with u^0 = u^1 = 0 and records s^n = R u^n (n = 1 .. N). For a loss L(s) with
+# G^n = dL/ds^n, the Lagrangian L - sum_n (lam^n)^T R^n gives the adjoint recursion
+#     M (lam^{m-1} - 2 lam^m + lam^{m+1}) + dt^2 K lam^m = R^T G^m,  m = N .. 2,
+# with lam^N = lam^{N+1} = 0 (the same symmetric operator run backward in time with the
+# receiver residuals as sources), and the gradient
+#     dL/dp = - sum_{n=1}^{N-1} (lam^n)^T [ dM/dp (u^{n+1} - 2 u^n + u^{n-1}) + dt^2 dK/dp u^n ].
+# Per local point q (weights w_q J_q): dM/drho_q puts w_q J_q on node I(q);
+# lam^T dK/dkappa_q u = w_q J_q tr e(lam) tr e(u);
+# lam^T dK/dmu_q u = w_q J_q 2 (e(lam) : e(u) - tr e(lam) tr e(u) / 3),
+# with e the discrete strain of Sec. II-B at the quadrature point.
+
+
+def element_strain(u_e, dxi_dx, basis: Basis) -> np.ndarray:
+    """Symmetric gradient (strain) of an element-local field at every GLL point, by the same
+    reference derivatives and chain rule as element_forces: [nspec, 3, 3, k, j, i]."""
+    H = basis.hprime
+    du = np.empty(u_e.shape[:2] + (3,) + u_e.shape[2:])
+    du[:, :, 0] = np.einsum("il,eckjl->eckji", H, u_e)
+    du[:, :, 1] = np.einsum("jl,eckli->eckji", H, u_e)
+    du[:, :, 2] = np.einsum("kl,eclji->eckji", H, u_e)
+    grad = np.einsum("ecrkji,erdkji->ecdkji", du, dxi_dx)
+    return 0.5 * (grad + grad.transpose(0, 2, 1, 3, 4, 5))
+
+
+def set_moduli(model: Model, rho=None, kappa=None, mu=None) -> Model:
+    """A copy of ``model`` with per-point rho, kappa, mu replaced (float64 [nspec, k, j, i]);
+    the mass is re-assembled when rho changes."""
+    import copy
+    m = copy.copy(model)
+    if rho is not None:
+        m.rho = np.asarray(rho, dtype=np.float64).reshape(model.rho.shape)
+        m.mass = mass_matrix(m.rho, m.jac, m.ibool, m.nglob, m.basis)
+    if kappa is not None:
+        m.kappa = np.asarray(kappa, dtype=np.float64).reshape(model.kappa.shape)
+    if mu is not None:
+        m.mu = np.asarray(mu, dtype=np.float64).reshape(model.mu.shape)
+    return m
+
+
+def forward_history(model: Model, dt: float, nsteps: int, src_nodes, src_force, f0, t0, rec_nodes):
+    """Forward run from rest keeping every displacement: returns (u [nsteps+1, nglob, 3] with
+    u[n] = u^n, seis [nrec, 3, nsteps] with seis[..., n-1] = s^n)."""
+    ng = model.nglob
+    u = np.zeros((ng, 3))
+    v = np.zeros((ng, 3))
+    a = np.zeros((ng, 3))
+    Minv = 1.0 / model.mass
+    src_nodes = np.asarray(src_nodes, dtype=np.int64).reshape(-1)
+    src_force = np.asarray(src_force, dtype=np.float64).reshape(-1, 3)
+    rec_nodes = np.asarray(rec_nodes, dtype=np.int64).reshape(-1)
+    hist = np.zeros((nsteps + 1, ng, 3))
+    seis = np.zeros((len(rec_nodes), 3, nsteps))
+    for n in range(nsteps):
+        u_new = u + dt * v + 0.5 * dt * dt * a
+        f = model.forces(u_new)
+        for s, g in enumerate(src_nodes):
+            f[g] += src_force[s] * ricker((n + 1) * dt, f0, t0)
+        a_new = Minv[:, None] * f
+        v = v + 0.5 * dt * (a + a_new)
+        u, a = u_new, a_new
+        hist[n + 1] = u
+        seis[:, :, n] = u[rec_nodes]
+    return hist, seis
+
+
+def adjoint_gradient(model: Model, dt: float, u_hist: np.ndarray, rec_nodes, G: np.ndarray):
+    """Gradient of a loss with dL/ds^n = G[..., n-1] (G [nrec, 3, nsteps]) with respect to
+    rho, kappa and mu at every local point, by the discrete adjoint above.
+    Returns (g_rho, g_kappa, g_mu), each float64 [nspec, k, j, i]."""
+    N = u_hist.shape[0] - 1
+    ng = model.nglob
+    n = model.ngll
+    rec_nodes = np.asarray(rec_nodes, dtype=np.int64).reshape(-1)
+    Minv = 1.0 / model.mass
+    wJ = model.jac * quadrature_weights_3d(model.basis)[None]
+    g_rho = np.zeros_like(model.rho)
+    g_kappa = np.zeros_like(model.kappa)
+    g_mu = np.zeros_like(model.mu)
+    lam_next = np.zeros((ng, 3))  # lam^{m+1}
+    lam = np.zeros((ng, 3))       # lam^m
+    for m in range(N, 1, -1):
+        inj = np.zeros((ng, 3))
+        np.add.at(inj, rec_nodes, G[:, :, m - 1])
+        lam_prev = 2.0 * lam - lam_next + Minv[:, None] * (dt * dt * model.forces(lam) + inj)
+        # gradient term n = m - 1 with lam^{m-1}
+        k = m - 1
+        lam_e = gather(lam_prev, model.ibool, n)
+        u_e = gather(u_hist[k], model.ibool, n)
+        acc_e = gather(u_hist[k + 1] - 2.0 * u_hist[k] + u_hist[k - 1], model.ibool, n)
+        el = element_strain(lam_e, model.dxi_dx, model.basis)
+        eu = element_strain(u_e, model.dxi_dx, model.basis)
+        tr_l = el[:, 0, 0] + el[:, 1, 1] + el[:, 2, 2]
+        tr_u = eu[:, 0, 0] + eu[:, 1, 1] + eu[:, 2, 2]
+        ee = np.einsum("ecdkji,ecdkji->ekji", el, eu)
+        g_kappa -= dt * dt * wJ * tr_l * tr_u
+        g_mu -= dt * dt * wJ * 2.0 * (ee - tr_l * tr_u / 3.0)
+        g_rho -= wJ * np.einsum("eckji,eckji->ekji", lam_e, acc_e)
+        lam_next, lam = lam, lam_prev
+    return g_rho, g_kappa, g_mu
