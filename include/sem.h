@@ -91,6 +91,10 @@ int sem_set_mesh(sem_ctx* ctx, int nspec, int nglob, const int32_t* ibool, const
  * or non-finite values. Requires sem_set_mesh. */
 int sem_set_material(sem_ctx* ctx, const float* rho, const float* vp, const float* vs);
 
+/* Same with the moduli given directly: kappa (bulk) and mu (shear) per local point, float32
+ * [nspec][ngll^3] each; SEM_EINVAL unless rho > 0, kappa > 0, mu >= 0. */
+int sem_set_moduli(sem_ctx* ctx, const float* rho, const float* kappa, const float* mu);
+
 /* dt = courant * min over elements of (smallest distance between neighbouring GLL points
  * along a grid line / largest vp of the element) (Sec. IV-B, V-C). Requires material. */
 int sem_suggest_dt(sem_ctx* ctx, double courant, double* dt_out);
@@ -133,8 +137,14 @@ int sem_set_state(sem_ctx* ctx, const float* u, const float* v, const float* a);
 /* Same from device arrays (NULL = zero). Asynchronous on the context's stream. */
 int sem_set_state_dev(sem_ctx* ctx, const float* u_dev, const float* v_dev, const float* a_dev);
 
+/* Declare the current state to be u^n, v^n, a^n of step n = step >= 0 (sem_set_state sets
+ * n = 0): the next step applies the sources at t_{n+1}. Used to restart a run from a state
+ * saved at step n. Host-only, no device work. */
+int sem_set_step(sem_ctx* ctx, long long step);
+
 /* Copy the current state (u^n, v^n, a^n) to host arrays [nglob][3] (NULL = skip).
- * Synchronous. */
+ * Reading v or a completes the pending half step (the trajectory is unchanged up to
+ * rounding); reading u alone does not touch the state. Synchronous. */
 int sem_get_state(sem_ctx* ctx, float* u, float* v, float* a);
 /* Same into device arrays. Asynchronous on the context's stream. */
 int sem_get_state_dev(sem_ctx* ctx, float* u_dev, float* v_dev, float* a_dev);
@@ -164,6 +174,23 @@ int sem_apply_stiffness(sem_ctx* ctx, const float* u_dev, float* f_dev);
  * arrays 16-byte aligned): [nglob][node_stride]. Stride 4 is the layout the solver keeps
  * its own fields in, so this times the force kernel exactly as a time step runs it. */
 int sem_apply_stiffness_strided(sem_ctx* ctx, const float* u_dev, float* f_dev, int node_stride);
+
+/* Discrete adjoint and material sensitivities of a seismogram loss L (one shot). From a
+ * zero state the scheme is the leapfrog M(u^{n+1} - 2u^n + u^{n-1}) + dt^2 (K u^n - f^n) = 0
+ * with u^0 = u^1 = 0; with G^m = dL/ds^m (s^m = u^m at the receivers, m = 1..N) the adjoint
+ * runs backward, M(lam^{m-1} - 2 lam^m + lam^{m+1}) + dt^2 K lam^m = R^T G^m from
+ * lam^N = lam^{N+1} = 0, and
+ *   dL/dp = - sum_{n=1}^{N-1} (lam^n)^T [dM/dp (u^{n+1} - 2u^n + u^{n-1}) + dt^2 dK/dp u^n]
+ * for p = rho, kappa, mu at every local point (Sec. II-B operator; the adjoint is not in the
+ * paper). Usage: sem_adjoint_begin; for m = N down to 2: sem_adjoint_step(G^m) (lam becomes
+ * lam^{m-1}), sem_adjoint_accumulate(u^{m-2}, u^{m-1}, u^m); then sem_adjoint_gradients.
+ * Requires dt and one shot. G_dev: float32 [nrec][3] on the device, or NULL (zero);
+ * u_*: displacement snapshots float32 [nglob][3] on the device. Gradients: float64 host
+ * arrays [nspec][ngll^3] in the caller's element and point order (NULL = skip). */
+int sem_adjoint_begin(sem_ctx* ctx);
+int sem_adjoint_step(sem_ctx* ctx, const float* G_dev);
+int sem_adjoint_accumulate(sem_ctx* ctx, const float* u_lo_dev, const float* u_mid_dev, const float* u_hi_dev);
+int sem_adjoint_gradients(sem_ctx* ctx, double* g_rho, double* g_kappa, double* g_mu);
 
 /* Kinetic and potential energy of the current state in float64:
  * out[0] = 1/2 sum_I M_I |v_I|^2, out[1] = 1/2 u^T K u. Synchronous. */

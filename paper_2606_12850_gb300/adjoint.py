@@ -1,0 +1,120 @@
+"""Seismograms as a differentiable function of the material (rho, kappa, mu per local point).
+
+The forward pass runs the solver from rest and keeps a checkpoint of the complete state every
+``checkpoint_every`` steps; the backward pass walks the checkpoints in reverse, recomputes the
+displacements of one segment from its checkpoint, and runs the discrete adjoint of the
+explicit scheme backward through it (see ``sem_adjoint_begin`` in include/sem.h). All
+arithmetic runs in the CUDA library; this module only orders the calls and holds the device
+buffers (PyTorch tensors).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import sem
+
+
+class Simulation:
+    """One model, one shot: forward seismograms and their material gradients.
+
+    ``ctx`` is a context with its mesh, sources and receivers set; ``dt`` the time step. The
+    material is given per call as float tensors/arrays [nspec][ngll^3] (rho, kappa, mu).
+    """
+
+    def __init__(self, ctx: sem.Ctx, dt: float, nsteps: int, checkpoint_every: int = 50, device: int = 0):
+        if ctx.shots != 1:
+            raise ValueError("one shot per simulation")
+        self.ctx = ctx
+        self.dt = float(dt)
+        self.nsteps = int(nsteps)
+        self.every = max(1, int(checkpoint_every))
+        self.device = torch.device("cuda", device)
+        self.nglob = self.ctx.nglob
+        self.nrec = self.ctx.nrec
+        self.checkpoints = []  # (step, u, v, a) device tensors [nglob*3]
+
+    def _state(self):
+        n3 = 3 * self.nglob
+        u, v, a = (torch.empty(n3, device=self.device) for _ in range(3))
+        sem.sem_sync(self.ctx)
+        torch.cuda.synchronize(self.device)
+        sem.sem_get_state_dev(self.ctx, u, v, a)
+        sem.sem_sync(self.ctx)
+        return u, v, a
+
+    def set_material(self, rho, kappa, mu):
+        to_np = lambda x: x.detach().cpu().numpy() if torch.is_tensor(x) else np.asarray(x)
+        sem.sem_set_moduli(self.ctx, to_np(rho), to_np(kappa), to_np(mu))
+        sem.sem_set_dt(self.ctx, self.dt)
+
+    def forward(self, rho, kappa, mu) -> torch.Tensor:
+        """Seismograms [nrec][3][nsteps] (s^1 .. s^N) on the device."""
+        self.set_material(rho, kappa, mu)
+        sem.sem_set_state(self.ctx)
+        N = self.nsteps
+        seis = torch.empty((self.nrec, 3, N), device=self.device)
+        self.checkpoints = []
+        n = 0
+        while n < N:
+            self.checkpoints.append((n,) + self._state())
+            k = min(self.every, N - n)
+            chunk = torch.empty((self.nrec, 3, k), device=self.device)
+            sem.sem_run_dev(self.ctx, k, chunk)
+            sem.sem_sync(self.ctx)
+            seis[:, :, n:n + k] = chunk
+            n += k
+        return seis
+
+    def _segment_displacements(self, n0: int, n1: int) -> torch.Tensor:
+        """u^{n0} .. u^{n1} recomputed from the checkpoint at n0: [n1 - n0 + 1][nglob*3]."""
+        ck = [c for c in self.checkpoints if c[0] == n0][0]
+        _, u0, v0, a0 = ck
+        sem.sem_sync(self.ctx)
+        torch.cuda.synchronize(self.device)
+        sem.sem_set_state_dev(self.ctx, u0, v0, a0)
+        sem.sem_set_step(self.ctx, n0)
+        out = torch.empty((n1 - n0 + 1, 3 * self.nglob), device=self.device)
+        out[0] = u0
+        for m in range(1, n1 - n0 + 1):
+            sem.sem_step(self.ctx, 1)
+            sem.sem_get_state_dev(self.ctx, out[m], None, None)
+        sem.sem_sync(self.ctx)
+        return out
+
+    def gradient(self, G: torch.Tensor):
+        """dL/d(rho, kappa, mu) for dL/ds = G [nrec][3][nsteps]; float64 numpy [nspec][ngll^3]."""
+        N = self.nsteps
+        # Gt[m - 1] = G^m as a contiguous [nrec][3] block
+        Gt = G.detach().to(self.device, torch.float32).permute(2, 0, 1).contiguous()
+        sem.sem_adjoint_begin(self.ctx)
+        m = N  # the next adjoint step makes lam^{m-1} from lam^m and lam^{m+1}
+        for n0 in reversed([c[0] for c in self.checkpoints]):
+            # this segment accumulates the terms n = m - 1 in [n0 + 1, min(n0 + every, N - 1)],
+            # which read u^{n-1}, u^n, u^{n+1}: u^{n0} .. u^{hi}
+            hi = min(n0 + self.every + 1, N)
+            U = self._segment_displacements(n0, hi)
+            while m - 1 >= n0 + 1:
+                sem.sem_adjoint_step(self.ctx, Gt[m - 1])
+                n = m - 1
+                sem.sem_adjoint_accumulate(self.ctx, U[n - 1 - n0], U[n - n0], U[n + 1 - n0])
+                m -= 1
+        sem.sem_sync(self.ctx)
+        return sem.sem_adjoint_gradients(self.ctx)
+
+
+class Seismograms(torch.autograd.Function):
+    """seis = Seismograms.apply(rho, kappa, mu, simulation): differentiable in the three
+    per-point material tensors (gradients through the discrete adjoint)."""
+
+    @staticmethod
+    def forward(ctx, rho, kappa, mu, sim: Simulation):
+        ctx.sim = sim
+        ctx.device = rho.device
+        return sim.forward(rho, kappa, mu)
+
+    @staticmethod
+    def backward(ctx, grad_seis):
+        g_rho, g_kappa, g_mu = ctx.sim.gradient(grad_seis)
+        as_t = lambda g: torch.from_numpy(g.astype(np.float32)).to(ctx.device)  # noqa: E731
+        return as_t(g_rho), as_t(g_kappa), as_t(g_mu), None

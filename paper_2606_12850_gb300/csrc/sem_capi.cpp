@@ -49,6 +49,9 @@ struct sem_ctx {
   float* d_rec = nullptr;
   float *d_u = nullptr, *d_v = nullptr, *d_a = nullptr, *d_minv = nullptr;
   float* d_f = nullptr;           // scratch force buffer for sem_energy
+  float *d_lam = nullptr, *d_lam_old = nullptr, *d_lamF = nullptr;  // adjoint fields [nglob][4]
+  double* d_grad = nullptr;       // [3][nlocal] sensitivities (rho, kappa, mu), record order
+  bool adjoint = false;
   double* d_partials = nullptr;   // scratch partial sums for sem_energy
   DevCtl* d_ctl = nullptr;
   int* d_src_node = nullptr;
@@ -110,12 +113,16 @@ int dev_alloc(sem_ctx* c, T** p, size_t count) {
 }
 
 void free_device(sem_ctx* c) {
-  void* ptrs[] = {c->d_rec, c->d_u, c->d_v, c->d_a, c->d_minv, c->d_f, c->d_partials,
+  void* ptrs[] = {c->d_rec, c->d_u, c->d_v, c->d_a, c->d_minv, c->d_f, c->d_partials, c->d_lam, c->d_lam_old,
+                  c->d_lamF, c->d_grad,
                   c->d_ctl, c->d_src_node, c->d_src_shot, c->d_src_force, c->d_rec_node};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->d_rec = nullptr;
   c->d_u = c->d_v = c->d_a = c->d_minv = c->d_f = nullptr;
+  c->d_lam = c->d_lam_old = c->d_lamF = nullptr;
+  c->d_grad = nullptr;
+  c->adjoint = false;
   c->d_partials = nullptr;
   c->d_ctl = nullptr;
   c->d_src_node = nullptr;
@@ -481,17 +488,22 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   return SEM_OK;
 }
 
-int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float* vs) {
+// Shared by sem_set_material and sem_set_moduli: per local point rho and (kappa, mu), either
+// given or derived from (vp, vs).
+static int set_material_impl(sem_ctx* c, const float* rho, const float* p1, const float* p2, bool moduli) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
-  if (!rho || !vp || !vs) return fail(c, SEM_EINVAL, "sem_set_material: NULL array");
+  if (!rho || !p1 || !p2) return fail(c, SEM_EINVAL, "material: NULL array");
   const int n = c->ngll, np = n * n * n, RW = rec_words(n);
   const size_t nloc = static_cast<size_t>(c->nspec) * np;
   for (size_t q = 0; q < nloc; ++q) {
-    if (!std::isfinite(rho[q]) || !std::isfinite(vp[q]) || !std::isfinite(vs[q]))
+    if (!std::isfinite(rho[q]) || !std::isfinite(p1[q]) || !std::isfinite(p2[q]))
       return fail(c, SEM_EINVAL, "non-finite material value");
-    if (!(rho[q] > 0.f) || vs[q] < 0.f || !(vp[q] > vs[q]))
-      return fail(c, SEM_EINVAL, "material needs rho > 0, vs >= 0, vp > vs (local point " + std::to_string(q) + ")");
+    const bool ok = moduli ? (rho[q] > 0.f && p2[q] >= 0.f && p1[q] > 0.f) : (rho[q] > 0.f && p2[q] >= 0.f && p1[q] > p2[q]);
+    if (!ok)
+      return fail(c, SEM_EINVAL,
+                  std::string(moduli ? "moduli need rho > 0, kappa > 0, mu >= 0" : "material needs rho > 0, vs >= 0, vp > vs") +
+                      " (local point " + std::to_string(q) + ")");
   }
   std::vector<double> mass(c->nglob, 0.0);
   c->vpmax.assign(c->nspec, 0.0);
@@ -502,15 +514,23 @@ int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float*
         for (int i = 0; i < n; ++i) {
           const int p = i + n * (j + n * k);
           const size_t q = static_cast<size_t>(e) * np + p;
-          const double rh = rho[q], a = vp[q], b = vs[q];
-          const double mu = rh * b * b;
-          const double lam = rh * (a * a - 2.0 * b * b);
-          const double kappa = lam + 2.0 * mu / 3.0;
+          const double rh = rho[q];
+          double kappa, mu, vp;
+          if (moduli) {
+            kappa = p1[q];
+            mu = p2[q];
+            vp = std::sqrt((kappa + 4.0 * mu / 3.0) / rh);
+          } else {
+            const double a = p1[q], b = p2[q];
+            mu = rh * b * b;
+            kappa = rh * (a * a - 2.0 * b * b) + 2.0 * mu / 3.0;
+            vp = a;
+          }
           const int qq = rec_pos(n, i, j, k);
           r[kKappa * np + qq] = static_cast<float>(kappa);
           r[kMu * np + qq] = static_cast<float>(mu);
           mass[c->ibool[q]] += rh * c->jac[q] * c->w[i] * c->w[j] * c->w[k];
-          c->vpmax[e] = std::max(c->vpmax[e], a);
+          c->vpmax[e] = std::max(c->vpmax[e], vp);
         }
   }
   std::vector<float> minv(c->nglob, 0.f);
@@ -523,6 +543,14 @@ int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float*
   c->have_mat = true;
   drop_graph(c);
   return SEM_OK;
+}
+
+int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float* vs) {
+  return set_material_impl(c, rho, vp, vs, false);
+}
+
+int sem_set_moduli(sem_ctx* c, const float* rho, const float* kappa, const float* mu) {
+  return set_material_impl(c, rho, kappa, mu, true);
 }
 
 int sem_suggest_dt(sem_ctx* c, double courant, double* dt_out) {
@@ -701,7 +729,7 @@ static int get_state_impl(sem_ctx* c, float* u, float* v, float* a, cudaMemcpyKi
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
   int r = set_device(c);
-  if (r || (r = finish_state(c))) return r;
+  if (r || ((v || a) && (r = finish_state(c)))) return r;  // u is complete at any step
   float* dst[3] = {u, v, a};
   const float* src[3] = {c->d_u, c->d_v, c->d_a};
   const size_t S = c->shots;
@@ -712,6 +740,13 @@ static int get_state_impl(sem_ctx* c, float* u, float* v, float* a, cudaMemcpyKi
                                       src[q] + kNodeStride * sh, kNodeStride * S * sizeof(float), 3 * sizeof(float),
                                       c->nglob, kind, c->stream));
   if (kind == cudaMemcpyDeviceToHost) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SEM_OK;
+}
+
+int sem_set_step(sem_ctx* c, long long step) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (step < 0) return fail(c, SEM_EINVAL, "step must be >= 0");
+  c->steps = step;
   return SEM_OK;
 }
 
@@ -839,6 +874,76 @@ int sem_color_counts(sem_ctx* c, int32_t* counts) {
   if (!c || !counts) return fail(c, SEM_EINVAL, "sem_color_counts: bad arguments");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
   for (int k = 0; k < c->ncolors; ++k) counts[k] = c->color_off[k + 1] - c->color_off[k];
+  return SEM_OK;
+}
+
+int sem_adjoint_begin(sem_ctx* c) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (c->shots != 1) return fail(c, SEM_EINVAL, "the adjoint runs one shot at a time (sem_set_shots(ctx, 1))");
+  if ((r = set_device(c))) return r;
+  const size_t nf = kNodeStride * static_cast<size_t>(c->nglob);
+  const size_t nloc = static_cast<size_t>(c->nspec) * c->ngll * c->ngll * c->ngll;
+  if (!c->d_lam) {
+    if ((r = dev_alloc(c, &c->d_lam, nf)) || (r = dev_alloc(c, &c->d_lam_old, nf)) ||
+        (r = dev_alloc(c, &c->d_lamF, nf)) || (r = dev_alloc(c, &c->d_grad, 3 * nloc)))
+      return r;
+  }
+  SEM_CUDA(c, cudaMemsetAsync(c->d_lam, 0, nf * sizeof(float), c->stream));
+  SEM_CUDA(c, cudaMemsetAsync(c->d_lam_old, 0, nf * sizeof(float), c->stream));
+  SEM_CUDA(c, cudaMemsetAsync(c->d_grad, 0, 3 * nloc * sizeof(double), c->stream));
+  c->adjoint = true;
+  return SEM_OK;
+}
+
+int sem_adjoint_step(sem_ctx* c, const float* G_dev) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->adjoint) return fail(c, SEM_ESTATE, "sem_adjoint_begin has not been called");
+  int r = set_device(c);
+  if (r) return r;
+  if ((r = forces_all_colors(c, c->d_lam, c->d_lamF, kNodeStride, 1))) return r;
+  SEM_LAUNCH(c, launch_adjoint_update(c->d_lamF, G_dev, c->d_rec_node, c->nrec, c->d_lam, c->d_lam_old, c->d_minv,
+                                      c->nglob, c->dt, c->stream));
+  std::swap(c->d_lam, c->d_lam_old);  // lam <- lam^{m-1}, lam_old <- lam^m
+  return SEM_OK;
+}
+
+int sem_adjoint_accumulate(sem_ctx* c, const float* u_lo, const float* u_mid, const float* u_hi) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->adjoint) return fail(c, SEM_ESTATE, "sem_adjoint_begin has not been called");
+  if (!u_lo || !u_mid || !u_hi) return fail(c, SEM_EINVAL, "sem_adjoint_accumulate: NULL snapshot");
+  int r = set_device(c);
+  if (r) return r;
+  const size_t nloc = static_cast<size_t>(c->nspec) * c->ngll * c->ngll * c->ngll;
+  SEM_LAUNCH(c, launch_strain_products(c->ngll, c->d_rec, c->d_lam, u_mid, c->d_grad + nloc, c->d_grad + 2 * nloc,
+                                       c->nspec, -c->dt * c->dt, c->stream));
+  SEM_LAUNCH(c, launch_rho_products(c->ngll, c->d_rec, c->d_lam, u_lo, u_mid, u_hi, c->d_grad, c->nspec, -1.0,
+                                    c->stream));
+  return SEM_OK;
+}
+
+int sem_adjoint_gradients(sem_ctx* c, double* g_rho, double* g_kappa, double* g_mu) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->adjoint) return fail(c, SEM_ESTATE, "sem_adjoint_begin has not been called");
+  int r = set_device(c);
+  if (r) return r;
+  const int n = c->ngll, np = n * n * n, nl = n * n;
+  const size_t nloc = static_cast<size_t>(c->nspec) * np;
+  std::vector<double> h(3 * nloc);
+  SEM_CUDA(c, cudaMemcpyAsync(h.data(), c->d_grad, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  double* outs[3] = {g_rho, g_kappa, g_mu};
+  for (int f = 0; f < 3; ++f) {
+    if (!outs[f]) continue;
+    for (int s = 0; s < c->nspec; ++s) {
+      const size_t caller = static_cast<size_t>(c->order[s]) * np;
+      const double* src = h.data() + f * nloc + static_cast<size_t>(s) * np;
+      for (int q = 0; q < np; ++q) {
+        const int i = q / nl, line = q - i * nl;
+        outs[f][caller + i + n * line] = src[q];
+      }
+    }
+  }
   return SEM_OK;
 }
 

@@ -474,6 +474,136 @@ __global__ void __launch_bounds__(BatchCfg<N>::T)
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Material sensitivities (the discrete adjoint of the explicit scheme): at one adjoint step,
+// for every local point q of every element
+//   g_kappa[q] += c * w_q J_q tr e(lam) tr e(u)
+//   g_mu[q]    += c * w_q J_q 2 (e(lam) : e(u) - tr e(lam) tr e(u) / 3)
+// with e the discrete strain (the same derivatives and chain rule as the force kernel) and
+// c = -dt^2. lam is the adjoint field in the solver layout [nglob][4], u a displacement
+// snapshot [nglob][3]. Outputs are per local point in record order (element, q = i N^2 +
+// line), float64; no two threads write the same point, so there are no colours here.
+// ---------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(ForceCfg<N>::T)
+    strain_products_kernel(const float* __restrict__ rec, const float* __restrict__ lam, const float* __restrict__ u,
+                           double* __restrict__ g_kappa, double* __restrict__ g_mu, int nspec, double c) {
+  using C = ForceCfg<N>;
+  constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
+  constexpr bool WT = C::WARP_TEAM;
+  extern __shared__ float4 smem4[];
+  const float* __restrict__ H = c_h;
+  const float* __restrict__ W = c_w;
+  const int team = threadIdx.x / TEAM;
+  const int tl = threadIdx.x - team * TEAM;
+  const int ebase = (blockIdx.x * C::TEAMS + team) * E;
+  const int ne = min(E, nspec - ebase);
+  if (WT && ne <= 0) return;
+  float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
+  for (int idx = tl; idx < ne * NP; idx += TEAM) {
+    const int le = idx / NP;
+    const int p = idx - le * NP;
+    float* eb = ts + le * ES;
+    const size_t g = __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + p)) & ~kFirstTouchBit;
+    const float4 l4 = __ldg(reinterpret_cast<const float4*>(lam) + g);
+    eb[3 * p] = l4.x;
+    eb[3 * p + 1] = l4.y;
+    eb[3 * p + 2] = l4.z;
+    eb[3 * NP + 3 * p] = __ldg(u + 3 * g);
+    eb[3 * NP + 3 * p + 1] = __ldg(u + 3 * g + 1);
+    eb[3 * NP + 3 * p + 2] = __ldg(u + 3 * g + 2);
+  }
+  team_sync<WT>();
+  const int le = tl / NL;
+  const int line = tl - le * NL;
+  const int j = line % N;
+  const int k = line / N;
+  if (le >= ne) return;  // no barrier follows
+  const float* fl = ts + le * ES;
+  const float* fu = fl + 3 * NP;
+  const float* __restrict__ r = rec + static_cast<size_t>(ebase + le) * REC;
+  const size_t out = static_cast<size_t>(ebase + le) * NP;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float dl[3][3], du[3][3];  // [component][reference direction]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) dl[a][b] = du[a][b] = 0.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const float hi = H[i * N + l], hj = H[j * N + l], hk = H[k * N + l];
+      const int px = 3 * (l + N * line), pe = 3 * (i + N * (l + N * k)), pz = 3 * (i + N * (j + N * l));
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        dl[a][0] += hi * fl[px + a];
+        dl[a][1] += hj * fl[pe + a];
+        dl[a][2] += hk * fl[pz + a];
+        du[a][0] += hi * fu[px + a];
+        du[a][1] += hj * fu[pe + a];
+        du[a][2] += hk * fu[pz + a];
+      }
+    }
+    const int q = i * NL + line;
+    float G[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) G[a] = __ldg(r + (kG + a) * NP + q);
+    const float jac = __ldg(r + kJac * NP + q);
+    float gl[3][3], gu[3][3];  // physical gradients [component][x_d]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        gl[a][d] = dl[a][0] * G[d] + dl[a][1] * G[3 + d] + dl[a][2] * G[6 + d];
+        gu[a][d] = du[a][0] * G[d] + du[a][1] * G[3 + d] + du[a][2] * G[6 + d];
+      }
+    double ee = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double el = 0.5 * (static_cast<double>(gl[a][d]) + gl[d][a]);
+        const double eu = 0.5 * (static_cast<double>(gu[a][d]) + gu[d][a]);
+        ee += el * eu;
+      }
+    const double trl = static_cast<double>(gl[0][0]) + gl[1][1] + gl[2][2];
+    const double tru = static_cast<double>(gu[0][0]) + gu[1][1] + gu[2][2];
+    const double wJ = static_cast<double>(W[i]) * W[j] * W[k] * jac;
+    g_kappa[out + q] += c * wJ * trl * tru;
+    g_mu[out + q] += c * wJ * 2.0 * (ee - trl * tru / 3.0);
+  }
+}
+
+// g_rho[q] += c * w_q J_q lam_I . (u_hi - 2 u_mid + u_lo)_I at every local point (record
+// order), with c = -1; one thread per local point.
+template <int N>
+__global__ void rho_products_kernel(const float* __restrict__ rec, const float* __restrict__ lam,
+                                    const float* __restrict__ u_lo, const float* __restrict__ u_mid,
+                                    const float* __restrict__ u_hi, double* __restrict__ g_rho, int nspec, double c) {
+  using C = ForceCfg<N>;
+  constexpr int NP = C::NP, NL = C::NL, REC = C::REC;
+  const float* __restrict__ W = c_w;
+  const long long total = static_cast<long long>(nspec) * NP;
+  for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long e = t / NP;
+    const int q = static_cast<int>(t - e * NP);  // record order q = i N^2 + j + N k
+    const int i = q / NL, line = q - i * NL, j = line % N, k = line / N;
+    const int p = i + N * line;
+    const float* __restrict__ r = rec + static_cast<size_t>(e) * REC;
+    const size_t g = __float_as_uint(__ldg(r + p)) & ~kFirstTouchBit;
+    const float4 l4 = __ldg(reinterpret_cast<const float4*>(lam) + g);
+    double dot = 0.0;
+    const float lv[3] = {l4.x, l4.y, l4.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      dot += static_cast<double>(lv[a]) *
+             (static_cast<double>(u_hi[3 * g + a]) - 2.0 * u_mid[3 * g + a] + static_cast<double>(u_lo[3 * g + a]));
+    const double wJ = static_cast<double>(W[i]) * W[j] * W[k] * __ldg(r + kJac * NP + q);
+    g_rho[static_cast<size_t>(e) * NP + q] += c * wJ * dot;
+  }
+}
+
 template <int VS>
 int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   using C = ForceCfg<SEM_NGLL>;
@@ -541,6 +671,35 @@ int SEM_CAT(upload_basis_, SEM_NGLL)(const double* w, const double* h, void* str
 
 int SEM_CAT(launch_forces_, SEM_NGLL)(const ForceLaunch& L, void* stream) {
   return launch_forces_n(L, static_cast<cudaStream_t>(stream));
+}
+
+int SEM_CAT(launch_strain_products_, SEM_NGLL)(const float* rec, const float* lam, const float* u, double* g_kappa,
+                                              double* g_mu, int nspec, double c, void* stream) {
+  using C = ForceCfg<SEM_NGLL>;
+  static unsigned long long attr_done = 0;
+  const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_done & bit)) {
+    cudaError_t e =
+        cudaFuncSetAttribute(strain_products_kernel<SEM_NGLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    attr_done |= bit;
+  }
+  const int grid = (nspec + C::EPC - 1) / C::EPC;
+  strain_products_kernel<SEM_NGLL><<<grid, C::T, smem, static_cast<cudaStream_t>(stream)>>>(rec, lam, u, g_kappa, g_mu,
+                                                                                           nspec, c);
+  return static_cast<int>(cudaGetLastError());
+}
+
+int SEM_CAT(launch_rho_products_, SEM_NGLL)(const float* rec, const float* lam, const float* u_lo, const float* u_mid,
+                                           const float* u_hi, double* g_rho, int nspec, double c, void* stream) {
+  const long long total = static_cast<long long>(nspec) * SEM_NGLL * SEM_NGLL * SEM_NGLL;
+  const int grid = static_cast<int>(min((total + 255) / 256, 1ll << 20));
+  rho_products_kernel<SEM_NGLL><<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(rec, lam, u_lo, u_mid, u_hi,
+                                                                                     g_rho, nspec, c);
+  return static_cast<int>(cudaGetLastError());
 }
 
 int SEM_CAT(forces_smem_bytes_, SEM_NGLL)() { return ForceCfg<SEM_NGLL>::SMEM_FLOATS * 4; }

@@ -109,6 +109,12 @@ int launch_predictor(const DevProblem& p, void* stream);
 int launch_fused_newmark(const DevProblem& p, void* stream);
 int launch_corrector(const DevProblem& p, void* stream);
 int launch_sources_record(const DevProblem& p, void* stream);
+int launch_strain_products(int ngll, const float* rec, const float* lam, const float* u, double* g_kappa,
+                           double* g_mu, int nspec, double c, void* stream);
+int launch_rho_products(int ngll, const float* rec, const float* lam, const float* u_lo, const float* u_mid,
+                        const float* u_hi, double* g_rho, int nspec, double c, void* stream);
+int launch_adjoint_update(float* F, const float* G_dev, const int* rec_node, int nrec, const float* lam,
+                          float* lam_old, const float* minv, int nglob, double dt, void* stream);
 int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream);
 int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv,
                            int nglob, int shots, double* partials, int nblocks, void* stream);

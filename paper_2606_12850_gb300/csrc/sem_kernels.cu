@@ -11,10 +11,14 @@ namespace semgb {
 // ---------------------------------------------------------------------------------------
 // Dispatch to the per-order translation units (sem_forces_<N>.cu).
 // ---------------------------------------------------------------------------------------
-#define SEM_DECLARE_ORDER(n)                                                        \
-  int upload_basis_##n(const double* w, const double* h, void* stream, int ngll); \
-  int launch_forces_##n(const ForceLaunch& L, void* stream);                      \
-  int forces_smem_bytes_##n();
+#define SEM_DECLARE_ORDER(n)                                                                                \
+  int upload_basis_##n(const double* w, const double* h, void* stream, int ngll);                         \
+  int launch_forces_##n(const ForceLaunch& L, void* stream);                                              \
+  int forces_smem_bytes_##n();                                                                            \
+  int launch_strain_products_##n(const float* rec, const float* lam, const float* u, double* g_kappa,     \
+                                 double* g_mu, int nspec, double c, void* stream);                        \
+  int launch_rho_products_##n(const float* rec, const float* lam, const float* u_lo, const float* u_mid, \
+                              const float* u_hi, double* g_rho, int nspec, double c, void* stream);
 SEM_DECLARE_ORDER(2)
 SEM_DECLARE_ORDER(3)
 SEM_DECLARE_ORDER(4)
@@ -48,6 +52,22 @@ int upload_basis(int n, const double* w, const double* h, void* stream) {
 
 int launch_forces(int n, const ForceLaunch& L, void* stream) {
 #define SEM_CALL(k) launch_forces_##k(L, stream)
+  SEM_ORDER_SWITCH(n, SEM_CALL)
+#undef SEM_CALL
+  return static_cast<int>(cudaErrorInvalidValue);
+}
+
+int launch_strain_products(int n, const float* rec, const float* lam, const float* u, double* g_kappa, double* g_mu,
+                           int nspec, double c, void* stream) {
+#define SEM_CALL(k) launch_strain_products_##k(rec, lam, u, g_kappa, g_mu, nspec, c, stream)
+  SEM_ORDER_SWITCH(n, SEM_CALL)
+#undef SEM_CALL
+  return static_cast<int>(cudaErrorInvalidValue);
+}
+
+int launch_rho_products(int n, const float* rec, const float* lam, const float* u_lo, const float* u_mid,
+                        const float* u_hi, double* g_rho, int nspec, double c, void* stream) {
+#define SEM_CALL(k) launch_rho_products_##k(rec, lam, u_lo, u_mid, u_hi, g_rho, nspec, c, stream)
   SEM_ORDER_SWITCH(n, SEM_CALL)
 #undef SEM_CALL
   return static_cast<int>(cudaErrorInvalidValue);
@@ -141,6 +161,43 @@ int launch_corrector(const DevProblem& p, void* stream) {
   corrector_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<float4*>(p.v), reinterpret_cast<float4*>(p.a), p.minv, n, p.shots,
       static_cast<float>(0.5 * p.dt));
+  return static_cast<int>(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------------------
+// Adjoint leapfrog (the discrete adjoint of the scheme above, run backward in time):
+//   lam_new = 2 lam - lam_old + dt^2 M^-1 F,  F = -K lam + R^T G / dt^2
+// written over lam_old. Receiver residuals are added to F by one thread in a fixed order
+// (receivers may share a node).
+// ---------------------------------------------------------------------------------------
+__global__ void adjoint_inject_kernel(float* __restrict__ F, const float* __restrict__ G, const int* __restrict__ rec_node,
+                                      int nrec, float inv_dt2) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int r = 0; r < nrec; ++r)
+    for (int c = 0; c < 3; ++c) F[kNodeStride * static_cast<size_t>(rec_node[r]) + c] += G[3 * r + c] * inv_dt2;
+}
+
+__global__ void adjoint_leapfrog_kernel(const float4* __restrict__ lam, float4* __restrict__ lam_old,
+                                        const float4* __restrict__ F, const float* __restrict__ minv, int nglob,
+                                        float dt2) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob; g += gridDim.x * blockDim.x) {
+    const float s = dt2 * minv[g];
+    const float4 l = lam[g], o = lam_old[g], f = F[g];
+    lam_old[g] = make_float4(2.f * l.x - o.x + s * f.x, 2.f * l.y - o.y + s * f.y, 2.f * l.z - o.z + s * f.z, 0.f);
+  }
+}
+
+int launch_adjoint_update(float* F, const float* G_dev, const int* rec_node, int nrec, const float* lam,
+                          float* lam_old, const float* minv, int nglob, double dt, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (G_dev && nrec > 0) {
+    adjoint_inject_kernel<<<1, 1, 0, s>>>(F, G_dev, rec_node, nrec, static_cast<float>(1.0 / (dt * dt)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return static_cast<int>(e);
+  }
+  adjoint_leapfrog_kernel<<<stream_grid(nglob), 256, 0, s>>>(
+      reinterpret_cast<const float4*>(lam), reinterpret_cast<float4*>(lam_old), reinterpret_cast<const float4*>(F),
+      minv, nglob, static_cast<float>(dt * dt));
   return static_cast<int>(cudaGetLastError());
 }
 

@@ -32,6 +32,7 @@ SIGNATURES = {
     "sem_destroy": (_I, [_P]),
     "sem_set_mesh": (_I, [_P, _I, _I, _P, _P]),
     "sem_set_material": (_I, [_P, _P, _P, _P]),
+    "sem_set_moduli": (_I, [_P, _P, _P, _P]),
     "sem_suggest_dt": (_I, [_P, _D, _P]),
     "sem_set_dt": (_I, [_P, _D]),
     "sem_locate_nodes": (_I, [_P, _I, _P, _P, _P]),
@@ -41,6 +42,7 @@ SIGNATURES = {
     "sem_set_shot_sources": (_I, [_P, _I, _P, _P, _P, _D, _D]),
     "sem_set_state": (_I, [_P, _P, _P, _P]),
     "sem_set_state_dev": (_I, [_P, _P, _P, _P]),
+    "sem_set_step": (_I, [_P, ctypes.c_longlong]),
     "sem_get_state": (_I, [_P, _P, _P, _P]),
     "sem_get_state_dev": (_I, [_P, _P, _P, _P]),
     "sem_step": (_I, [_P, _I]),
@@ -50,6 +52,10 @@ SIGNATURES = {
     "sem_apply_stiffness": (_I, [_P, _P, _P]),
     "sem_apply_stiffness_strided": (_I, [_P, _P, _P, _I]),
     "sem_energy": (_I, [_P, _P]),
+    "sem_adjoint_begin": (_I, [_P]),
+    "sem_adjoint_step": (_I, [_P, _P]),
+    "sem_adjoint_accumulate": (_I, [_P, _P, _P, _P]),
+    "sem_adjoint_gradients": (_I, [_P, _P, _P, _P]),
     "sem_energy_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
     "sem_sync": (_I, [_P]),
     "sem_info": (_I, [_P, _P]),
@@ -184,6 +190,14 @@ def sem_set_material(ctx: Ctx, rho, vp, vs):
     _check(lib().sem_set_material(ctx.handle, pr, pa, pb), "sem_set_material", ctx)
 
 
+def sem_set_moduli(ctx: Ctx, rho, kappa, mu):
+    shape = (ctx.nspec, ctx.ngll ** 3)
+    r, pr = _host(rho, np.float32, shape)
+    a, pa = _host(kappa, np.float32, shape)
+    b, pb = _host(mu, np.float32, shape)
+    _check(lib().sem_set_moduli(ctx.handle, pr, pa, pb), "sem_set_moduli", ctx)
+
+
 def sem_suggest_dt(ctx: Ctx, courant: float) -> float:
     out = ctypes.c_double(0.0)
     _check(lib().sem_suggest_dt(ctx.handle, float(courant), ctypes.byref(out)), "sem_suggest_dt", ctx)
@@ -250,6 +264,10 @@ def sem_set_state_dev(ctx: Ctx, u=None, v=None, a=None):
     _check(lib().sem_set_state_dev(ctx.handle, _dev(u, n), _dev(v, n), _dev(a, n)), "sem_set_state_dev", ctx)
 
 
+def sem_set_step(ctx: Ctx, step: int):
+    _check(lib().sem_set_step(ctx.handle, int(step)), "sem_set_step", ctx)
+
+
 def sem_get_state(ctx: Ctx, want=(True, True, True)):
     shape = (ctx.nglob, 3) if ctx.shots == 1 else (ctx.shots, ctx.nglob, 3)
     outs = [np.empty(shape, dtype=np.float32) if w else None for w in want]
@@ -313,6 +331,28 @@ def sem_energy_noalloc(ctx: Ctx, u_dev, v_dev, f_dev, nglob: int | None = None):
     _check(lib().sem_energy_noalloc(ctx.handle, n, _dev(u_dev, m), _dev(v_dev, m), _dev(f_dev, m),
                                     out.ctypes.data_as(_P)), "sem_energy_noalloc", ctx)
     return float(out[0]), float(out[1])
+
+
+def sem_adjoint_begin(ctx: Ctx):
+    _check(lib().sem_adjoint_begin(ctx.handle), "sem_adjoint_begin", ctx)
+
+
+def sem_adjoint_step(ctx: Ctx, G_dev=None):
+    _check(lib().sem_adjoint_step(ctx.handle, _dev(G_dev, 3 * ctx.nrec)), "sem_adjoint_step", ctx)
+
+
+def sem_adjoint_accumulate(ctx: Ctx, u_lo, u_mid, u_hi):
+    n = 3 * ctx.nglob
+    _check(lib().sem_adjoint_accumulate(ctx.handle, _dev(u_lo, n), _dev(u_mid, n), _dev(u_hi, n)),
+           "sem_adjoint_accumulate", ctx)
+
+
+def sem_adjoint_gradients(ctx: Ctx):
+    shape = (ctx.nspec, ctx.ngll ** 3)
+    outs = [np.empty(shape) for _ in range(3)]
+    _check(lib().sem_adjoint_gradients(ctx.handle, *[o.ctypes.data_as(_P) for o in outs]), "sem_adjoint_gradients",
+           ctx)
+    return tuple(outs)
 
 
 def sem_sync(ctx: Ctx):

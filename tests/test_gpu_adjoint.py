@@ -1,0 +1,160 @@
+"""GPU parity of the discrete adjoint and the material gradients with the FP64 oracle.
+
+The problem is the one the oracle's finite-difference pins use (jittered 3^3 mesh, NGLL 4,
+random per-point rho/kappa/mu, one point force, three receivers, 60 steps), with the
+material rounded to float32 on both sides. The same G^m = dL/ds^m (float64 on the oracle
+side, float32 on the device) drives both adjoints.
+
+Tolerances (relative L2 over all local points):
+* seismograms: 1e-4, the solver's stated seismogram accuracy;
+* g_kappa, g_mu: 1e-4. Each term is a product of an adjoint strain and a forward strain in
+  float32; relative errors of a product add, the forward field and the adjoint field (run
+  by the same kernels) each carry up to the solver's stated 2e-5, and the sum over time
+  and points cancels terms of opposite sign, which we allow for with a factor of 2.5;
+* g_rho: the mass term reads the second difference u^{n+1} - 2u^n + u^{n-1} of float32
+  snapshots, which cancels most of their digits. The tolerance is 1e-4 plus twice the
+  change that rounding the oracle's own snapshots to float32 causes in its g_rho.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2606_12850_gb300 import build, inputs, sem  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL_SEIS = 1e-4
+TOL_MODULI = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    return sem.lib()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def problem(oracle):
+    mesh = inputs.structured_hex_mesh(3, 4, 600.0, jitter=0.15, seed=4)
+    shape = mesh.ibool.shape
+    rho = inputs.uniform(2, shape, 2200, 2800, stream=1)
+    vp = inputs.uniform(2, shape, 3000, 4000, stream=2)
+    vs = vp / 1.8
+    m = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, rho, vp, vs, 4)
+    f32 = lambda x: x.astype(np.float32).astype(np.float64)  # noqa: E731
+    m = oracle.set_moduli(m, rho=f32(m.rho), kappa=f32(m.kappa), mu=f32(m.mu))
+    dt = m.cfl_dt(0.4)
+    src = m.nearest_nodes([[300.0, 300.0, 300.0]])
+    rec = m.nearest_nodes([[100.0, 500.0, 600.0], [500.0, 100.0, 600.0], [300.0, 300.0, 0.0]])
+    nsteps = 60
+    kw = dict(src_nodes=src, src_force=[[1e6, -2e6, 3e6]], f0=20.0, t0=0.04, rec_nodes=rec)
+    u_hist, seis = oracle.forward_history(m, dt, nsteps, **kw)
+    d_obs = 0.9 * seis + 1e-9 * np.sin(np.arange(seis.size)).reshape(seis.shape)
+    G = dt * (seis - d_obs)
+    grads = oracle.adjoint_gradient(m, dt, u_hist, rec, G)
+    return dict(mesh=mesh, m=m, dt=dt, kw=kw, nsteps=nsteps, u_hist=u_hist, seis=seis, d_obs=d_obs, G=G,
+                grads=grads)
+
+
+def make_sim(p, every):
+    from paper_2606_12850_gb300 import adjoint
+    mesh = p["mesh"]
+    ctx = sem.sem_create(mesh.ngll, 0)
+    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    kw = p["kw"]
+    sem.sem_set_sources(ctx, kw["src_nodes"], kw["src_force"], kw["f0"], kw["t0"])
+    sem.sem_set_receivers(ctx, kw["rec_nodes"])
+    return ctx, adjoint.Simulation(ctx, p["dt"], p["nsteps"], checkpoint_every=every)
+
+
+def material(p):
+    m = p["m"]
+    n3 = m.ngll ** 3
+    return [torch.from_numpy(x.reshape(-1, n3).astype(np.float32)).cuda() for x in (m.rho, m.kappa, m.mu)]
+
+
+def rho_tolerance(oracle, p):
+    """1e-4 plus twice the change of g_rho that float32 rounding of the displacement
+    snapshots causes by itself, measured with the oracle."""
+    m = p["m"]
+    u32 = p["u_hist"].astype(np.float32).astype(np.float64)
+    g32 = oracle.adjoint_gradient(m, p["dt"], u32, p["kw"]["rec_nodes"], p["G"])[0]
+    return TOL_MODULI + 2 * rel_l2(g32, p["grads"][0])
+
+
+def test_adjoint_matches_oracle(oracle, problem):
+    p = problem
+    ctx, sim = make_sim(p, every=50)
+    rho, kappa, mu = material(p)
+    seis = sim.forward(rho, kappa, mu).cpu().numpy()
+    assert rel_l2(seis, p["seis"]) <= TOL_SEIS
+    G = torch.from_numpy(p["G"].astype(np.float32)).cuda()
+    g_rho, g_kappa, g_mu = sim.gradient(G)
+    r_rho, r_kappa, r_mu = (x.reshape(g_rho.shape) for x in p["grads"])
+    e_kappa, e_mu, e_rho = rel_l2(g_kappa, r_kappa), rel_l2(g_mu, r_mu), rel_l2(g_rho, r_rho)
+    tol_rho = rho_tolerance(oracle, p)
+    print(f"adjoint rel L2: kappa {e_kappa:.2e} mu {e_mu:.2e} rho {e_rho:.2e} (rho tol {tol_rho:.2e})")
+    assert e_kappa <= TOL_MODULI
+    assert e_mu <= TOL_MODULI
+    assert e_rho <= tol_rho
+
+
+def test_checkpoint_interval_does_not_change_gradient(problem):
+    """Checkpoints every 7 steps (ragged last segment) against one segment of 60 steps."""
+    p = problem
+    G = torch.from_numpy(p["G"].astype(np.float32)).cuda()
+    out = []
+    for every in (7, 60):
+        ctx, sim = make_sim(p, every)
+        sim.forward(*material(p))
+        out.append(sim.gradient(G))
+    for a, b in zip(*out):
+        assert rel_l2(a, b) <= 1e-5
+
+
+def test_restart_from_saved_state(problem):
+    """A run restarted at step 30 from the saved state (sem_set_step) continues the source
+    time function: its last 30 seismogram samples equal those of the straight run."""
+    p = problem
+    ctx, sim = make_sim(p, 50)
+    mat = material(p)
+    sim.set_material(*mat)
+    sem.sem_set_state(ctx)
+    straight = sem.sem_run(ctx, 60)
+    sem.sem_set_state(ctx)
+    sem.sem_run(ctx, 30)
+    u, v, a = sem.sem_get_state(ctx)
+    sem.sem_set_state(ctx, u, v, a)
+    sem.sem_set_step(ctx, 30)
+    rest = sem.sem_run(ctx, 30)
+    assert rel_l2(rest, straight[:, :, 30:]) <= 1e-5
+    # without sem_set_step the source would restart at t_1
+    sem.sem_set_state(ctx, u, v, a)
+    wrong = sem.sem_run(ctx, 30)
+    assert rel_l2(wrong, straight[:, :, 30:]) > 1e-3
+
+
+def test_autograd_function(problem):
+    """loss.backward() through Seismograms gives the gradients of Simulation.gradient for
+    G = dL/ds of the same loss."""
+    from paper_2606_12850_gb300 import adjoint
+    p = problem
+    ctx, sim = make_sim(p, 20)
+    rho, kappa, mu = (x.clone().requires_grad_(True) for x in material(p))
+    seis = adjoint.Seismograms.apply(rho, kappa, mu, sim)
+    d_obs = torch.from_numpy(p["d_obs"].astype(np.float32)).cuda()
+    loss = 0.5 * p["dt"] * ((seis - d_obs) ** 2).sum()
+    loss.backward()
+    G = (p["dt"] * (seis - d_obs)).detach()
+    ctx2, sim2 = make_sim(p, 20)
+    sim2.forward(*material(p))
+    ref = sim2.gradient(G)
+    for t, r in zip((rho, kappa, mu), ref):
+        assert rel_l2(t.grad.cpu().numpy(), r) <= 1e-6
