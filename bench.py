@@ -51,6 +51,7 @@ def parse_args():
     p.add_argument("--shots", type=int, default=32, help="batched-shot measurement (0 = skip)")
     p.add_argument("--shot-steps", type=int, default=100)
     p.add_argument("--no-sweep", action="store_true", help="skip the NGLL 3/5/7/9 (h,p) sweep")
+    p.add_argument("--adjoint-steps", type=int, default=800, help="misfit-gradient measurement (0 = skip)")
     return p.parse_args()
 
 
@@ -327,6 +328,86 @@ def measure_hp_sweep(device: int, steps: int = 50):
     return out
 
 
+def measure_adjoint(device: int, nsteps: int = 800, every: int = 50):
+    """Cost of one misfit gradient against one plain forward run of the same model: the
+    three-layer jittered cube with 32^3 elements at NGLL=5, a 5 % Gaussian velocity anomaly
+    in the true model, 64 surface receivers, ``nsteps`` steps with a checkpoint every
+    ``every``. The observed data come from the true model; the L2 misfit's gradient in
+    (rho, kappa, mu) is taken at the unperturbed layers. ``fd_rel_err`` compares the
+    gradient's directional derivative along a seeded per-element direction with a central
+    difference of the float32 misfit (step 1e-3), a sanity check at full size; the parity
+    bar is the oracle comparison of the tests."""
+    import torch
+
+    from paper_2606_12850_gb300 import adjoint, inputs, sem
+
+    w = inputs.perturbed_layered_cube(n=32, ngll=5, nsteps=nsteps, nrec_side=8)
+    stream = torch.cuda.Stream(device=device)
+    s = sem.setup_workload(w, device=device, stream=stream)  # true model; its dt is the smaller one
+    ctx, nrec = s.ctx, len(s.rec_nodes)
+    dev = torch.device("cuda", device)
+    with torch.cuda.stream(stream):
+        d_obs = torch.empty((nrec, 3, nsteps), device=dev)
+    sem.sem_run_dev(ctx, nsteps, d_obs)
+    sem.sem_sync(ctx)
+    rho_b, vp_b, vs_b = (x.astype(np.float64) for x in w.extra["background"])
+    mu = rho_b * vs_b ** 2
+    kappa = rho_b * vp_b ** 2 - 4.0 / 3.0 * mu
+    mat = [torch.from_numpy(x.astype(np.float32)).to(dev) for x in (rho_b, kappa, mu)]
+    sim = adjoint.Simulation(ctx, s.dt, nsteps, checkpoint_every=every, device=device)
+
+    sim.set_material(*mat)  # plain forward of the same model, device-timed
+    sem.sem_set_state(ctx)
+    with torch.cuda.stream(stream):
+        buf = torch.empty((nrec, 3, nsteps), device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sem.sem_run_dev(ctx, nsteps, buf)
+    b.record(stream)
+    b.synchronize()
+    plain_ms = a.elapsed_time(b)
+
+    def misfit(seis):
+        return 0.5 * s.dt * float(torch.sum((seis.double() - d_obs.double()) ** 2))
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seis = sim.forward(*mat)
+    G = s.dt * (seis - d_obs)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g_rho, g_kappa, g_mu = sim.gradient(G)
+    t2 = time.perf_counter()
+    L0 = misfit(seis)
+
+    # float32 directional finite difference along a seeded per-element direction
+    nspec = w.mesh.nspec
+    r = [inputs.uniform(9, (nspec, 1), -1.0, 1.0, stream=k) for k in (1, 2, 3)]
+    base = (rho_b, kappa, mu)
+    dirs = [p_ * r_ for p_, r_ in zip(base, r)]
+    predicted = float(sum(np.sum(g * d) for g, d in zip((g_rho, g_kappa, g_mu), dirs)))
+    h = 1e-3
+    Ls = []
+    for sg in (+1, -1):
+        pert = [torch.from_numpy((p_ + sg * h * d).astype(np.float32)).to(dev) for p_, d in zip(base, dirs)]
+        sim.set_material(*pert)
+        sem.sem_set_state(ctx)
+        sem.sem_run_dev(ctx, nsteps, buf)
+        sem.sem_sync(ctx)
+        Ls.append(misfit(buf))
+    fd = (Ls[0] - Ls[1]) / (2 * h)
+    nglob = w.mesh.nglob
+    fwd_ms, bwd_ms = 1e3 * (t1 - t0), 1e3 * (t2 - t1)
+    return {"model": f"{w.name}, {nrec} surface receivers", "nsteps": nsteps, "checkpoint_every": every,
+            "plain_forward_ms": plain_ms, "checkpointed_forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "gradient_ms": fwd_ms + bwd_ms, "gradient_over_plain_forward": (fwd_ms + bwd_ms) / plain_ms,
+            "checkpoint_mb": len(sim.checkpoints) * 3 * 3 * nglob * 4 / 1e6,
+            "segment_mb": (every + 2) * 3 * nglob * 4 / 1e6, "misfit": L0,
+            "fd_directional": fd, "adjoint_directional": predicted,
+            "fd_rel_err": abs(fd - predicted) / abs(fd) if fd else None,
+            "timing": "plain forward: CUDA events; gradient: wall clock including host synchronisation"}
+
+
 def run_ours(args):
     import torch
 
@@ -432,6 +513,10 @@ def run_ours(args):
     if not args.no_sweep:
         sweep = measure_hp_sweep(local)
 
+    adj = None
+    if args.adjoint_steps > 0:
+        adj = measure_adjoint(local, args.adjoint_steps)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, _, _ = oracle_sample_rate(args.ngll, args.cpu_seconds)
@@ -457,7 +542,7 @@ def run_ours(args):
                                   "bytes_per_step": alg["step"]},
             "global_pt_updates_per_s": world * mesh.nglob * K / (ms / 1e3),
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clock_info,
-            "batched_shots": batched, "hp_sweep": sweep,
+            "batched_shots": batched, "hp_sweep": sweep, "adjoint": adj,
             "kernel_sources": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)

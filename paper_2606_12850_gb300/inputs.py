@@ -218,6 +218,26 @@ def layered_cube(ngll: int = 5, n: int | None = None, side: float = 4000.0, jitt
         receiver_xyz=rec, nsteps=nsteps, courant=0.4, receiver_surface_only=True)
 
 
+def perturbed_layered_cube(n: int = 32, ngll: int = 5, amplitude: float = 0.05, seed: int = 2606,
+                           nsteps: int = 800, nrec_side: int = 8, side: float = 4000.0) -> Workload:
+    """The three-layer jittered cube with a seeded Gaussian velocity anomaly: vp and vs of
+    every element are scaled by 1 + amplitude * exp(-|c - x0|^2 / (2 s^2)), c the mean of
+    the element's eight corners, x0 uniform in the middle half of the box (seeded) and
+    s = side / 8. ``nrec_side**2`` receivers on the top face. The unperturbed material is
+    kept in ``extra["background"]`` as (rho, vp, vs)."""
+    w = layered_cube(ngll, n=n, side=side, seed=seed, nsteps=nsteps, nrec_side=nrec_side)
+    x0 = uniform(seed, (3,), 0.25 * side, 0.75 * side, stream=13)
+    sig = side / 8.0
+    c = w.mesh.ctrl.mean(axis=1)
+    scale = (1.0 + amplitude * np.exp(-np.sum((c - x0) ** 2, axis=1) / (2.0 * sig * sig))).astype(np.float32)
+    w.extra["background"] = (w.rho.copy(), w.vp.copy(), w.vs.copy())
+    w.extra["anomaly_centre"] = x0
+    w.vp = w.vp * scale[:, None]
+    w.vs = w.vs * scale[:, None]
+    w.name = f"{w.name}, {100 * amplitude:g}% Gaussian velocity anomaly"
+    return w
+
+
 def random_field(nglob: int, seed: int, scale: float = 1.0, stream: int = 7) -> np.ndarray:
     """Seeded U(-scale, scale) wavefield, float32 [nglob][3]."""
     return uniform(seed, (nglob, 3), -scale, scale, stream=stream).astype(np.float32)
