@@ -94,6 +94,10 @@ int sem_set_material(sem_ctx* ctx, const float* rho, const float* vp, const floa
 /* Same with the moduli given directly: kappa (bulk) and mu (shear) per local point, float32
  * [nspec][ngll^3] each; SEM_EINVAL unless rho > 0, kappa > 0, mu >= 0. */
 int sem_set_moduli(sem_ctx* ctx, const float* rho, const float* kappa, const float* mu);
+/* Same as sem_set_moduli from device arrays float32 [nspec][ngll^3] on the context's GPU
+ * (caller-owned, read during the call); checked on the device (SEM_EINVAL names the first
+ * offending local point). Synchronous. For model updates that stay in device memory. */
+int sem_set_moduli_dev(sem_ctx* ctx, const float* rho_dev, const float* kappa_dev, const float* mu_dev);
 
 /* dt = courant * min over elements of (smallest distance between neighbouring GLL points
  * along a grid line / largest vp of the element) (Sec. IV-B, V-C). Requires material. */
@@ -160,6 +164,12 @@ int sem_run(sem_ctx* ctx, int nsteps, float* seis);
  * Asynchronous on the context's stream. */
 int sem_run_dev(sem_ctx* ctx, int nsteps, float* seis_dev);
 
+/* Advance nsteps time steps and store the displacement after every step: u_dev receives
+ * u^{n+1}, ..., u^{n+nsteps} as float32 [nsteps][shots][nglob][3] (device, caller-owned,
+ * borrowed until the stream reaches the end of the call). Used to recompute a segment of
+ * a checkpointed run for the adjoint. Asynchronous on the context's stream. */
+int sem_run_snapshots(sem_ctx* ctx, int nsteps, float* u_dev);
+
 /* Divergence watchdog: SEM_OK if every value of u, v and a is finite, SEM_EDIVERGED
  * otherwise (an explicit scheme run above its stability limit grows until it overflows).
  * Synchronous. */
@@ -191,6 +201,12 @@ int sem_adjoint_begin(sem_ctx* ctx);
 int sem_adjoint_step(sem_ctx* ctx, const float* G_dev);
 int sem_adjoint_accumulate(sem_ctx* ctx, const float* u_lo_dev, const float* u_mid_dev, const float* u_hi_dev);
 int sem_adjoint_gradients(sem_ctx* ctx, double* g_rho, double* g_kappa, double* g_mu);
+/* One segment of the backward sweep in a single call: with the adjoint at lam^{n0+count+1}
+ * (and lam^{n0+count+2}), runs j = count down to 1: sem_adjoint_step(G_dev[j-1]) then
+ * sem_adjoint_accumulate(u_dev[j-1], u_dev[j], u_dev[j+1]). G_dev: float32
+ * [count][nrec][3] with G_dev[j-1] = G^{n0+j+1} (device; NULL = zero); u_dev: float32
+ * [count+2][nglob][3] = u^{n0} .. u^{n0+count+1} (device). Asynchronous on the stream. */
+int sem_adjoint_segment(sem_ctx* ctx, int count, const float* G_dev, const float* u_dev);
 
 /* Kinetic and potential energy of the current state in float64:
  * out[0] = 1/2 sum_I M_I |v_I|^2, out[1] = 1/2 u^T K u. Synchronous. */

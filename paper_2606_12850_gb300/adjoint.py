@@ -44,8 +44,14 @@ class Simulation:
         return u, v, a
 
     def set_material(self, rho, kappa, mu):
-        to_np = lambda x: x.detach().cpu().numpy() if torch.is_tensor(x) else np.asarray(x)
-        sem.sem_set_moduli(self.ctx, to_np(rho), to_np(kappa), to_np(mu))
+        mats = (rho, kappa, mu)
+        if all(torch.is_tensor(x) and x.is_cuda for x in mats):
+            mats = [x.detach().to(self.device, torch.float32).contiguous() for x in mats]
+            torch.cuda.synchronize(self.device)
+            sem.sem_set_moduli_dev(self.ctx, *mats)
+        else:
+            to_np = lambda x: x.detach().cpu().numpy() if torch.is_tensor(x) else np.asarray(x)  # noqa: E731
+            sem.sem_set_moduli(self.ctx, *(to_np(x) for x in mats))
         sem.sem_set_dt(self.ctx, self.dt)
 
     def forward(self, rho, kappa, mu) -> torch.Tensor:
@@ -68,18 +74,13 @@ class Simulation:
 
     def _segment_displacements(self, n0: int, n1: int) -> torch.Tensor:
         """u^{n0} .. u^{n1} recomputed from the checkpoint at n0: [n1 - n0 + 1][nglob*3]."""
-        ck = [c for c in self.checkpoints if c[0] == n0][0]
-        _, u0, v0, a0 = ck
-        sem.sem_sync(self.ctx)
+        _, u0, v0, a0 = next(c for c in self.checkpoints if c[0] == n0)
+        out = torch.empty((n1 - n0 + 1, 3 * self.nglob), device=self.device)
+        out[0].copy_(u0)
         torch.cuda.synchronize(self.device)
         sem.sem_set_state_dev(self.ctx, u0, v0, a0)
         sem.sem_set_step(self.ctx, n0)
-        out = torch.empty((n1 - n0 + 1, 3 * self.nglob), device=self.device)
-        out[0] = u0
-        for m in range(1, n1 - n0 + 1):
-            sem.sem_step(self.ctx, 1)
-            sem.sem_get_state_dev(self.ctx, out[m], None, None)
-        sem.sem_sync(self.ctx)
+        sem.sem_run_snapshots(self.ctx, n1 - n0, out[1:])
         return out
 
     def gradient(self, G: torch.Tensor):
@@ -87,19 +88,16 @@ class Simulation:
         N = self.nsteps
         # Gt[m - 1] = G^m as a contiguous [nrec][3] block
         Gt = G.detach().to(self.device, torch.float32).permute(2, 0, 1).contiguous()
+        torch.cuda.synchronize(self.device)
         sem.sem_adjoint_begin(self.ctx)
-        m = N  # the next adjoint step makes lam^{m-1} from lam^m and lam^{m+1}
         for n0 in reversed([c[0] for c in self.checkpoints]):
-            # this segment accumulates the terms n = m - 1 in [n0 + 1, min(n0 + every, N - 1)],
-            # which read u^{n-1}, u^n, u^{n+1}: u^{n0} .. u^{hi}
-            hi = min(n0 + self.every + 1, N)
-            U = self._segment_displacements(n0, hi)
-            while m - 1 >= n0 + 1:
-                sem.sem_adjoint_step(self.ctx, Gt[m - 1])
-                n = m - 1
-                sem.sem_adjoint_accumulate(self.ctx, U[n - 1 - n0], U[n - n0], U[n + 1 - n0])
-                m -= 1
-        sem.sem_sync(self.ctx)
+            # the terms n = n0 + 1 .. n0 + count, which read u^{n0} .. u^{n0 + count + 1}
+            count = min(self.every, N - 1 - n0)
+            if count <= 0:
+                continue
+            U = self._segment_displacements(n0, n0 + count + 1)
+            sem.sem_adjoint_segment(self.ctx, count, Gt[n0 + 1:n0 + count + 1], U)
+            sem.sem_sync(self.ctx)  # U is released (or reused) after this
         return sem.sem_adjoint_gradients(self.ctx)
 
 

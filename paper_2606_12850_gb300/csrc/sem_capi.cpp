@@ -39,7 +39,6 @@ struct sem_ctx {
   std::vector<int> pos_of;          // caller element -> colour-sorted position
   std::vector<int> color_off;       // ncolors + 1
   std::vector<float> rec;           // colour-sorted element records (host copy)
-  std::vector<double> jac;          // caller order, per local point (for the mass)
   std::vector<double> dxmin;        // per caller element
   std::vector<double> node_xyz;     // [nglob][3]
   std::vector<double> vpmax;        // per caller element
@@ -47,6 +46,7 @@ struct sem_ctx {
 
   // device
   float* d_rec = nullptr;
+  int* d_order = nullptr;         // record slot -> caller element
   float *d_u = nullptr, *d_v = nullptr, *d_a = nullptr, *d_minv = nullptr;
   float* d_f = nullptr;           // scratch force buffer for sem_energy
   float *d_lam = nullptr, *d_lam_old = nullptr, *d_lamF = nullptr;  // adjoint fields [nglob][4]
@@ -113,12 +113,13 @@ int dev_alloc(sem_ctx* c, T** p, size_t count) {
 }
 
 void free_device(sem_ctx* c) {
-  void* ptrs[] = {c->d_rec, c->d_u, c->d_v, c->d_a, c->d_minv, c->d_f, c->d_partials, c->d_lam, c->d_lam_old,
+  void* ptrs[] = {c->d_rec, c->d_order, c->d_u, c->d_v, c->d_a, c->d_minv, c->d_f, c->d_partials, c->d_lam, c->d_lam_old,
                   c->d_lamF, c->d_grad,
                   c->d_ctl, c->d_src_node, c->d_src_shot, c->d_src_force, c->d_rec_node};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->d_rec = nullptr;
+  c->d_order = nullptr;
   c->d_u = c->d_v = c->d_a = c->d_minv = c->d_f = nullptr;
   c->d_lam = c->d_lam_old = c->d_lamF = nullptr;
   c->d_grad = nullptr;
@@ -384,7 +385,6 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
 
   // geometry per element (caller order)
   std::vector<double> xyz(3 * np), G(9 * np), J(np);
-  c->jac.assign(nloc, 0.0);
   c->dxmin.assign(nspec, 0.0);
   c->node_xyz.assign(3 * static_cast<size_t>(nglob), 0.0);
   std::vector<float> geom(static_cast<size_t>(nspec) * 10 * np);  // [e][10][p] in caller p order
@@ -408,7 +408,6 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
     c->dxmin[e] = dmin;
     for (int p = 0; p < np; ++p) {
       const size_t q = static_cast<size_t>(e) * np + p;
-      c->jac[q] = J[p];
       for (int d = 0; d < 3; ++d) c->node_xyz[3 * static_cast<size_t>(ibool[q]) + d] = xyz[3 * p + d];
       float* gq = geom.data() + static_cast<size_t>(e) * 10 * np;
       for (int a = 0; a < 9; ++a) gq[a * np + p] = static_cast<float>(G[9 * p + a]);
@@ -474,27 +473,64 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   c->d_ctl = keep_ctl;
   c->dev_bytes = sizeof(DevCtl);
   const size_t nf = kNodeStride * static_cast<size_t>(nglob) * c->shots;
-  if ((r = dev_alloc(c, &c->d_rec, c->rec.size())) || (r = dev_alloc(c, &c->d_u, nf)) ||
-      (r = dev_alloc(c, &c->d_v, nf)) || (r = dev_alloc(c, &c->d_a, nf)) ||
+  if ((r = dev_alloc(c, &c->d_rec, c->rec.size())) || (r = dev_alloc(c, &c->d_order, c->order.size())) ||
+      (r = dev_alloc(c, &c->d_u, nf)) || (r = dev_alloc(c, &c->d_v, nf)) || (r = dev_alloc(c, &c->d_a, nf)) ||
       (r = dev_alloc(c, &c->d_minv, static_cast<size_t>(nglob))))
     return r;
+  // geometry and ibool travel once; the material fields are written on the device
+  SEM_CUDA(c, cudaMemcpyAsync(c->d_rec, c->rec.data(), c->rec.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  SEM_CUDA(c, cudaMemcpyAsync(c->d_order, c->order.data(), c->order.size() * sizeof(int), cudaMemcpyHostToDevice,
+                              c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_u, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_v, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_a, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_minv, 0, nglob * sizeof(float), c->stream));
   SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<float>().swap(c->rec);  // the device copy is the only one from here on
   c->nsrc = 0;
   c->nrec = 0;
   return SEM_OK;
 }
 
+// Writes kappa and mu into the element records, assembles the mass and its inverse and the
+// per-element largest vp, all on the device, from per-point arrays already on the device.
+static int material_apply(sem_ctx* c, const float* rho, const float* p1, const float* p2, bool moduli) {
+  MaterialLaunch m{};
+  m.rec = c->d_rec;
+  m.order = c->d_order;
+  m.rho = rho;
+  m.p1 = p1;
+  m.p2 = p2;
+  m.moduli = moduli ? 1 : 0;
+  m.ngll = c->ngll;
+  m.nspec = c->nspec;
+  m.nglob = c->nglob;
+  for (int i = 0; i < c->ngll; ++i) m.w[i] = c->w[i];
+  double *mass = nullptr, *vpmax = nullptr;
+  SEM_CUDA(c, cudaMallocAsync(reinterpret_cast<void**>(&mass), c->nglob * sizeof(double), c->stream));
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&vpmax), c->nspec * sizeof(double), c->stream);
+  if (e == cudaSuccess)
+    e = static_cast<cudaError_t>(launch_material_apply(m, c->color_off.data(), c->ncolors, mass, c->d_minv, vpmax,
+                                                       c->stream));
+  c->vpmax.assign(c->nspec, 0.0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->vpmax.data(), vpmax, c->nspec * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(mass, c->stream);
+  if (vpmax) cudaFreeAsync(vpmax, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "material upload");
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->have_mat = true;
+  drop_graph(c);
+  return SEM_OK;
+}
+
 // Shared by sem_set_material and sem_set_moduli: per local point rho and (kappa, mu), either
-// given or derived from (vp, vs).
+// given or derived from (vp, vs); checked on the host, then applied on the device.
 static int set_material_impl(sem_ctx* c, const float* rho, const float* p1, const float* p2, bool moduli) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
   if (!rho || !p1 || !p2) return fail(c, SEM_EINVAL, "material: NULL array");
-  const int n = c->ngll, np = n * n * n, RW = rec_words(n);
+  const int n = c->ngll, np = n * n * n;
   const size_t nloc = static_cast<size_t>(c->nspec) * np;
   for (size_t q = 0; q < nloc; ++q) {
     if (!std::isfinite(rho[q]) || !std::isfinite(p1[q]) || !std::isfinite(p2[q]))
@@ -505,44 +541,21 @@ static int set_material_impl(sem_ctx* c, const float* rho, const float* p1, cons
                   std::string(moduli ? "moduli need rho > 0, kappa > 0, mu >= 0" : "material needs rho > 0, vs >= 0, vp > vs") +
                       " (local point " + std::to_string(q) + ")");
   }
-  std::vector<double> mass(c->nglob, 0.0);
-  c->vpmax.assign(c->nspec, 0.0);
-  for (int e = 0; e < c->nspec; ++e) {
-    float* r = c->rec.data() + static_cast<size_t>(c->pos_of[e]) * RW;
-    for (int k = 0; k < n; ++k)
-      for (int j = 0; j < n; ++j)
-        for (int i = 0; i < n; ++i) {
-          const int p = i + n * (j + n * k);
-          const size_t q = static_cast<size_t>(e) * np + p;
-          const double rh = rho[q];
-          double kappa, mu, vp;
-          if (moduli) {
-            kappa = p1[q];
-            mu = p2[q];
-            vp = std::sqrt((kappa + 4.0 * mu / 3.0) / rh);
-          } else {
-            const double a = p1[q], b = p2[q];
-            mu = rh * b * b;
-            kappa = rh * (a * a - 2.0 * b * b) + 2.0 * mu / 3.0;
-            vp = a;
-          }
-          const int qq = rec_pos(n, i, j, k);
-          r[kKappa * np + qq] = static_cast<float>(kappa);
-          r[kMu * np + qq] = static_cast<float>(mu);
-          mass[c->ibool[q]] += rh * c->jac[q] * c->w[i] * c->w[j] * c->w[k];
-          c->vpmax[e] = std::max(c->vpmax[e], vp);
-        }
-  }
-  std::vector<float> minv(c->nglob, 0.f);
-  for (int g = 0; g < c->nglob; ++g) minv[g] = static_cast<float>(1.0 / mass[g]);
   int r = set_device(c);
   if (r) return r;
-  SEM_CUDA(c, cudaMemcpyAsync(c->d_rec, c->rec.data(), c->rec.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-  SEM_CUDA(c, cudaMemcpyAsync(c->d_minv, minv.data(), minv.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
-  c->have_mat = true;
-  drop_graph(c);
-  return SEM_OK;
+  float* tmp = nullptr;
+  SEM_CUDA(c, cudaMallocAsync(reinterpret_cast<void**>(&tmp), 3 * nloc * sizeof(float), c->stream));
+  const float* src[3] = {rho, p1, p2};
+  cudaError_t e = cudaSuccess;
+  for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+    e = cudaMemcpyAsync(tmp + f * nloc, src[f], nloc * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(tmp, c->stream);
+    return cuda_fail(c, e, "material upload");
+  }
+  r = material_apply(c, tmp, tmp + nloc, tmp + 2 * nloc, moduli);
+  cudaFreeAsync(tmp, c->stream);
+  return r;
 }
 
 int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float* vs) {
@@ -551,6 +564,34 @@ int sem_set_material(sem_ctx* c, const float* rho, const float* vp, const float*
 
 int sem_set_moduli(sem_ctx* c, const float* rho, const float* kappa, const float* mu) {
   return set_material_impl(c, rho, kappa, mu, true);
+}
+
+int sem_set_moduli_dev(sem_ctx* c, const float* rho, const float* kappa, const float* mu) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (!rho || !kappa || !mu) return fail(c, SEM_EINVAL, "material: NULL array");
+  int r = set_device(c);
+  if (r) return r;
+  MaterialLaunch m{};
+  m.rho = rho;
+  m.p1 = kappa;
+  m.p2 = mu;
+  m.moduli = 1;
+  m.ngll = c->ngll;
+  m.nspec = c->nspec;
+  m.nglob = c->nglob;
+  unsigned long long* d_bad = nullptr;
+  unsigned long long bad = ~0ull;
+  SEM_CUDA(c, cudaMallocAsync(reinterpret_cast<void**>(&d_bad), sizeof(unsigned long long), c->stream));
+  cudaError_t e = cudaMemsetAsync(d_bad, 0xff, sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = static_cast<cudaError_t>(launch_material_check(m, d_bad, c->stream));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(d_bad, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "material check");
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (bad != ~0ull)
+    return fail(c, SEM_EINVAL, "moduli need finite rho > 0, kappa > 0, mu >= 0 (local point " + std::to_string(bad) + ")");
+  return material_apply(c, rho, kappa, mu, true);
 }
 
 int sem_suggest_dt(sem_ctx* c, double courant, double* dt_out) {
@@ -689,29 +730,41 @@ int sem_set_receivers(sem_ctx* c, int nrec, const int32_t* node) {
   return SEM_OK;
 }
 
+// Host arrays pass through a stream-ordered staging buffer in the caller layout, so every
+// transfer is one contiguous copy; the layout change is a kernel on the device.
 static int set_state_impl(sem_ctx* c, const float* u, const float* v, const float* a, cudaMemcpyKind kind) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
   int r = set_device(c);
   if (r) return r;
   const size_t n3 = 3 * static_cast<size_t>(c->nglob) * c->shots;
-  if (kind == cudaMemcpyHostToDevice) {
+  const bool host = kind == cudaMemcpyHostToDevice;
+  if (host) {
     if ((u && !finite_all(u, n3)) || (v && !finite_all(v, n3)) || (a && !finite_all(a, n3)))
       return fail(c, SEM_EINVAL, "non-finite state value");
   }
   const float* src[3] = {u, v, a};
   float* dst[3] = {c->d_u, c->d_v, c->d_a};
-  const size_t S = c->shots;
-  for (int q = 0; q < 3; ++q) {
-    SEM_CUDA(c, cudaMemsetAsync(dst[q], 0, kNodeStride * static_cast<size_t>(c->nglob) * S * sizeof(float),
-                                c->stream));
-    if (src[q])  // [shots][nglob][3] -> [nglob][shots][kNodeStride]
-      for (size_t sh = 0; sh < S; ++sh)
-        SEM_CUDA(c, cudaMemcpy2DAsync(dst[q] + kNodeStride * sh, kNodeStride * S * sizeof(float),
-                                      src[q] + 3 * static_cast<size_t>(c->nglob) * sh, 3 * sizeof(float),
-                                      3 * sizeof(float), c->nglob, kind, c->stream));
+  float* stage = nullptr;
+  if (host && (u || v || a)) SEM_CUDA(c, cudaMallocAsync(reinterpret_cast<void**>(&stage), n3 * sizeof(float), c->stream));
+  int rc = SEM_OK;
+  for (int q = 0; q < 3 && rc == SEM_OK; ++q) {
+    cudaError_t e = cudaSuccess;
+    if (!src[q]) {
+      e = cudaMemsetAsync(dst[q], 0, kNodeStride * static_cast<size_t>(c->nglob) * c->shots * sizeof(float), c->stream);
+    } else {
+      const float* from = src[q];
+      if (host) {
+        e = cudaMemcpyAsync(stage, src[q], n3 * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+        from = stage;
+      }
+      if (e == cudaSuccess) e = static_cast<cudaError_t>(launch_unpack(from, dst[q], c->nglob, c->shots, c->stream));
+    }
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "sem_set_state copy");
   }
-  if (kind == cudaMemcpyHostToDevice) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (stage) cudaFreeAsync(stage, c->stream);
+  if (rc) return rc;
+  if (host) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->pending = false;
   c->steps = 0;
   return SEM_OK;
@@ -730,16 +783,22 @@ static int get_state_impl(sem_ctx* c, float* u, float* v, float* a, cudaMemcpyKi
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
   int r = set_device(c);
   if (r || ((v || a) && (r = finish_state(c)))) return r;  // u is complete at any step
+  const size_t n3 = 3 * static_cast<size_t>(c->nglob) * c->shots;
+  const bool host = kind == cudaMemcpyDeviceToHost;
   float* dst[3] = {u, v, a};
   const float* src[3] = {c->d_u, c->d_v, c->d_a};
-  const size_t S = c->shots;
-  for (int q = 0; q < 3; ++q)
-    if (dst[q])  // [nglob][shots][kNodeStride] -> [shots][nglob][3]
-      for (size_t sh = 0; sh < S; ++sh)
-        SEM_CUDA(c, cudaMemcpy2DAsync(dst[q] + 3 * static_cast<size_t>(c->nglob) * sh, 3 * sizeof(float),
-                                      src[q] + kNodeStride * sh, kNodeStride * S * sizeof(float), 3 * sizeof(float),
-                                      c->nglob, kind, c->stream));
-  if (kind == cudaMemcpyDeviceToHost) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  float* stage = nullptr;
+  if (host && (u || v || a)) SEM_CUDA(c, cudaMallocAsync(reinterpret_cast<void**>(&stage), n3 * sizeof(float), c->stream));
+  int rc = SEM_OK;
+  for (int q = 0; q < 3 && rc == SEM_OK; ++q) {
+    if (!dst[q]) continue;
+    cudaError_t e = static_cast<cudaError_t>(launch_pack(src[q], host ? stage : dst[q], c->nglob, c->shots, c->stream));
+    if (e == cudaSuccess && host) e = cudaMemcpyAsync(dst[q], stage, n3 * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "sem_get_state copy");
+  }
+  if (stage) cudaFreeAsync(stage, c->stream);
+  if (rc) return rc;
+  if (host) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
   return SEM_OK;
 }
 
@@ -759,6 +818,19 @@ int sem_get_state_dev(sem_ctx* c, float* u, float* v, float* a) {
 int sem_step(sem_ctx* c, int nsteps) { return advance(c, nsteps, nullptr); }
 
 int sem_run_dev(sem_ctx* c, int nsteps, float* seis_dev) { return advance(c, nsteps, seis_dev); }
+
+int sem_run_snapshots(sem_ctx* c, int nsteps, float* u_dev) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (nsteps < 0) return fail(c, SEM_EINVAL, "nsteps must be >= 0");
+  if (nsteps > 0 && !u_dev) return fail(c, SEM_EINVAL, "sem_run_snapshots: NULL snapshot buffer");
+  const size_t per = 3 * static_cast<size_t>(c->nglob) * c->shots;
+  for (int k = 0; k < nsteps; ++k) {
+    if ((r = advance(c, 1, nullptr))) return r;
+    SEM_LAUNCH(c, launch_pack(c->d_u, u_dev + k * per, c->nglob, c->shots, c->stream));
+  }
+  return SEM_OK;
+}
 
 int sem_check_finite(sem_ctx* c) {
   int r = check_ready(c);
@@ -915,10 +987,23 @@ int sem_adjoint_accumulate(sem_ctx* c, const float* u_lo, const float* u_mid, co
   int r = set_device(c);
   if (r) return r;
   const size_t nloc = static_cast<size_t>(c->nspec) * c->ngll * c->ngll * c->ngll;
-  SEM_LAUNCH(c, launch_strain_products(c->ngll, c->d_rec, c->d_lam, u_mid, c->d_grad + nloc, c->d_grad + 2 * nloc,
-                                       c->nspec, -c->dt * c->dt, c->stream));
-  SEM_LAUNCH(c, launch_rho_products(c->ngll, c->d_rec, c->d_lam, u_lo, u_mid, u_hi, c->d_grad, c->nspec, -1.0,
-                                    c->stream));
+  SEM_LAUNCH(c, launch_sensitivity(c->ngll, c->d_rec, c->d_lam, u_lo, u_mid, u_hi, c->d_grad, c->d_grad + nloc,
+                                    c->d_grad + 2 * nloc, c->nspec, -1.0, -c->dt * c->dt, c->stream));
+  return SEM_OK;
+}
+
+int sem_adjoint_segment(sem_ctx* c, int count, const float* G_dev, const float* u_dev) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->adjoint) return fail(c, SEM_ESTATE, "sem_adjoint_begin has not been called");
+  if (count < 0) return fail(c, SEM_EINVAL, "count must be >= 0");
+  if (count > 0 && !u_dev) return fail(c, SEM_EINVAL, "sem_adjoint_segment: NULL snapshots");
+  const size_t n3 = 3 * static_cast<size_t>(c->nglob);
+  const size_t gstep = 3 * static_cast<size_t>(c->nrec);
+  for (int j = count; j >= 1; --j) {
+    int r = sem_adjoint_step(c, G_dev ? G_dev + (j - 1) * gstep : nullptr);
+    if (r) return r;
+    if ((r = sem_adjoint_accumulate(c, u_dev + (j - 1) * n3, u_dev + j * n3, u_dev + (j + 1) * n3))) return r;
+  }
   return SEM_OK;
 }
 

@@ -477,20 +477,25 @@ __global__ void __launch_bounds__(BatchCfg<N>::T)
 // ---------------------------------------------------------------------------------------
 // Material sensitivities (the discrete adjoint of the explicit scheme): at one adjoint step,
 // for every local point q of every element
-//   g_kappa[q] += c * w_q J_q tr e(lam) tr e(u)
-//   g_mu[q]    += c * w_q J_q 2 (e(lam) : e(u) - tr e(lam) tr e(u) / 3)
-// with e the discrete strain (the same derivatives and chain rule as the force kernel) and
-// c = -dt^2. lam is the adjoint field in the solver layout [nglob][4], u a displacement
-// snapshot [nglob][3]. Outputs are per local point in record order (element, q = i N^2 +
-// line), float64; no two threads write the same point, so there are no colours here.
+//   g_rho[q]   += c_m * w_q J_q lam_I . (u_hi - 2 u_mid + u_lo)_I          (I = ibool(q))
+//   g_kappa[q] += c_k * w_q J_q tr e(lam) tr e(u_mid)
+//   g_mu[q]    += c_k * w_q J_q 2 (e(lam) : e(u_mid) - tr e(lam) tr e(u_mid) / 3)
+// with e the discrete strain (the same derivatives and chain rule as the force kernel),
+// c_m = -1 and c_k = -dt^2. lam is the adjoint field in the solver layout [nglob][4], the
+// u_* displacement snapshots [nglob][3]. The terms are formed in float32 (the second
+// difference as (u_hi - u_mid) - (u_mid - u_lo), which keeps the digits the plain form
+// cancels) and added to float64 accumulators per local point in record order (element,
+// q = i N^2 + line). No two threads write the same point, so there are no colours here.
 // ---------------------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(ForceCfg<N>::T)
-    strain_products_kernel(const float* __restrict__ rec, const float* __restrict__ lam, const float* __restrict__ u,
-                           double* __restrict__ g_kappa, double* __restrict__ g_mu, int nspec, double c) {
+    sensitivity_kernel(const float* __restrict__ rec, const float* __restrict__ lam, const float* __restrict__ u_lo,
+                       const float* __restrict__ u_mid, const float* __restrict__ u_hi, double* __restrict__ g_rho,
+                       double* __restrict__ g_kappa, double* __restrict__ g_mu, int nspec, double c_m, double c_k) {
   using C = ForceCfg<N>;
   constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
   constexpr bool WT = C::WARP_TEAM;
+  static_assert(7 * NP <= ES, "element tile holds lam, u and the mass term");
   extern __shared__ float4 smem4[];
   const float* __restrict__ H = c_h;
   const float* __restrict__ W = c_w;
@@ -506,12 +511,16 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
     float* eb = ts + le * ES;
     const size_t g = __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + p)) & ~kFirstTouchBit;
     const float4 l4 = __ldg(reinterpret_cast<const float4*>(lam) + g);
-    eb[3 * p] = l4.x;
-    eb[3 * p + 1] = l4.y;
-    eb[3 * p + 2] = l4.z;
-    eb[3 * NP + 3 * p] = __ldg(u + 3 * g);
-    eb[3 * NP + 3 * p + 1] = __ldg(u + 3 * g + 1);
-    eb[3 * NP + 3 * p + 2] = __ldg(u + 3 * g + 2);
+    const float um[3] = {__ldg(u_mid + 3 * g), __ldg(u_mid + 3 * g + 1), __ldg(u_mid + 3 * g + 2)};
+    const float lv[3] = {l4.x, l4.y, l4.z};
+    float dot = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      eb[3 * p + a] = lv[a];
+      eb[3 * NP + 3 * p + a] = um[a];
+      dot += lv[a] * ((__ldg(u_hi + 3 * g + a) - um[a]) - (um[a] - __ldg(u_lo + 3 * g + a)));
+    }
+    eb[6 * NP + p] = dot;
   }
   team_sync<WT>();
   const int le = tl / NL;
@@ -521,6 +530,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
   if (le >= ne) return;  // no barrier follows
   const float* fl = ts + le * ES;
   const float* fu = fl + 3 * NP;
+  const float* fm = fl + 6 * NP;
   const float* __restrict__ r = rec + static_cast<size_t>(ebase + le) * REC;
   const size_t out = static_cast<size_t>(ebase + le) * NP;
 #pragma unroll
@@ -557,50 +567,17 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
         gl[a][d] = dl[a][0] * G[d] + dl[a][1] * G[3 + d] + dl[a][2] * G[6 + d];
         gu[a][d] = du[a][0] * G[d] + du[a][1] * G[3 + d] + du[a][2] * G[6 + d];
       }
-    double ee = 0.0;
+    float ee = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const double el = 0.5 * (static_cast<double>(gl[a][d]) + gl[d][a]);
-        const double eu = 0.5 * (static_cast<double>(gu[a][d]) + gu[d][a]);
-        ee += el * eu;
-      }
-    const double trl = static_cast<double>(gl[0][0]) + gl[1][1] + gl[2][2];
-    const double tru = static_cast<double>(gu[0][0]) + gu[1][1] + gu[2][2];
-    const double wJ = static_cast<double>(W[i]) * W[j] * W[k] * jac;
-    g_kappa[out + q] += c * wJ * trl * tru;
-    g_mu[out + q] += c * wJ * 2.0 * (ee - trl * tru / 3.0);
-  }
-}
-
-// g_rho[q] += c * w_q J_q lam_I . (u_hi - 2 u_mid + u_lo)_I at every local point (record
-// order), with c = -1; one thread per local point.
-template <int N>
-__global__ void rho_products_kernel(const float* __restrict__ rec, const float* __restrict__ lam,
-                                    const float* __restrict__ u_lo, const float* __restrict__ u_mid,
-                                    const float* __restrict__ u_hi, double* __restrict__ g_rho, int nspec, double c) {
-  using C = ForceCfg<N>;
-  constexpr int NP = C::NP, NL = C::NL, REC = C::REC;
-  const float* __restrict__ W = c_w;
-  const long long total = static_cast<long long>(nspec) * NP;
-  for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
-       t += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const long long e = t / NP;
-    const int q = static_cast<int>(t - e * NP);  // record order q = i N^2 + j + N k
-    const int i = q / NL, line = q - i * NL, j = line % N, k = line / N;
-    const int p = i + N * line;
-    const float* __restrict__ r = rec + static_cast<size_t>(e) * REC;
-    const size_t g = __float_as_uint(__ldg(r + p)) & ~kFirstTouchBit;
-    const float4 l4 = __ldg(reinterpret_cast<const float4*>(lam) + g);
-    double dot = 0.0;
-    const float lv[3] = {l4.x, l4.y, l4.z};
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      dot += static_cast<double>(lv[a]) *
-             (static_cast<double>(u_hi[3 * g + a]) - 2.0 * u_mid[3 * g + a] + static_cast<double>(u_lo[3 * g + a]));
-    const double wJ = static_cast<double>(W[i]) * W[j] * W[k] * __ldg(r + kJac * NP + q);
-    g_rho[static_cast<size_t>(e) * NP + q] += c * wJ * dot;
+      for (int d = 0; d < 3; ++d) ee += 0.25f * (gl[a][d] + gl[d][a]) * (gu[a][d] + gu[d][a]);
+    const float trl = gl[0][0] + gl[1][1] + gl[2][2];
+    const float tru = gu[0][0] + gu[1][1] + gu[2][2];
+    const float wJ = W[i] * W[j] * W[k] * jac;
+    g_rho[out + q] += c_m * static_cast<double>(wJ * fm[i + N * line]);
+    g_kappa[out + q] += c_k * static_cast<double>(wJ * trl * tru);
+    g_mu[out + q] += c_k * static_cast<double>(2.f * wJ * (ee - trl * tru * (1.f / 3.f)));
   }
 }
 
@@ -673,8 +650,9 @@ int SEM_CAT(launch_forces_, SEM_NGLL)(const ForceLaunch& L, void* stream) {
   return launch_forces_n(L, static_cast<cudaStream_t>(stream));
 }
 
-int SEM_CAT(launch_strain_products_, SEM_NGLL)(const float* rec, const float* lam, const float* u, double* g_kappa,
-                                              double* g_mu, int nspec, double c, void* stream) {
+int SEM_CAT(launch_sensitivity_, SEM_NGLL)(const float* rec, const float* lam, const float* u_lo, const float* u_mid,
+                                          const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec,
+                                          double c_m, double c_k, void* stream) {
   using C = ForceCfg<SEM_NGLL>;
   static unsigned long long attr_done = 0;
   const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
@@ -683,22 +661,13 @@ int SEM_CAT(launch_strain_products_, SEM_NGLL)(const float* rec, const float* la
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_done & bit)) {
     cudaError_t e =
-        cudaFuncSetAttribute(strain_products_kernel<SEM_NGLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(sensitivity_kernel<SEM_NGLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return static_cast<int>(e);
     attr_done |= bit;
   }
   const int grid = (nspec + C::EPC - 1) / C::EPC;
-  strain_products_kernel<SEM_NGLL><<<grid, C::T, smem, static_cast<cudaStream_t>(stream)>>>(rec, lam, u, g_kappa, g_mu,
-                                                                                           nspec, c);
-  return static_cast<int>(cudaGetLastError());
-}
-
-int SEM_CAT(launch_rho_products_, SEM_NGLL)(const float* rec, const float* lam, const float* u_lo, const float* u_mid,
-                                           const float* u_hi, double* g_rho, int nspec, double c, void* stream) {
-  const long long total = static_cast<long long>(nspec) * SEM_NGLL * SEM_NGLL * SEM_NGLL;
-  const int grid = static_cast<int>(min((total + 255) / 256, 1ll << 20));
-  rho_products_kernel<SEM_NGLL><<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(rec, lam, u_lo, u_mid, u_hi,
-                                                                                     g_rho, nspec, c);
+  sensitivity_kernel<SEM_NGLL><<<grid, C::T, smem, static_cast<cudaStream_t>(stream)>>>(
+      rec, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k);
   return static_cast<int>(cudaGetLastError());
 }
 

@@ -109,12 +109,35 @@ int launch_predictor(const DevProblem& p, void* stream);
 int launch_fused_newmark(const DevProblem& p, void* stream);
 int launch_corrector(const DevProblem& p, void* stream);
 int launch_sources_record(const DevProblem& p, void* stream);
-int launch_strain_products(int ngll, const float* rec, const float* lam, const float* u, double* g_kappa,
-                           double* g_mu, int nspec, double c, void* stream);
-int launch_rho_products(int ngll, const float* rec, const float* lam, const float* u_lo, const float* u_mid,
-                        const float* u_hi, double* g_rho, int nspec, double c, void* stream);
+int launch_sensitivity(int ngll, const float* rec, const float* lam, const float* u_lo, const float* u_mid,
+                       const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec, double c_m,
+                       double c_k, void* stream);
+// solver layout [nglob][shots][kNodeStride] <-> caller layout [shots][nglob][3]
+int launch_pack(const float* u, float* out, int nglob, int shots, void* stream);
+int launch_unpack(const float* in, float* u, int nglob, int shots, void* stream);
 int launch_adjoint_update(float* F, const float* G_dev, const int* rec_node, int nrec, const float* lam,
                           float* lam_old, const float* minv, int nglob, double dt, void* stream);
+// Material on the device (Sec. II-B moduli, Sec. I diagonal mass). rho, p1, p2: per local
+// point in caller order [nspec][ngll^3]; moduli: (p1, p2) = (kappa, mu), else (vp, vs).
+struct MaterialLaunch {
+  float* rec;          // colour-sorted element records
+  const int* order;    // record slot -> caller element
+  const float* rho;
+  const float* p1;
+  const float* p2;
+  int moduli;
+  int ngll;
+  int nspec;
+  int nglob;
+  double w[kMaxNgll];  // GLL weights
+};
+// index of the first local point that breaks rho > 0, mu (vs) >= 0, kappa > 0 (vp > vs) or
+// is not finite, as an atomic minimum into *first_bad (caller presets it to ~0ull)
+int launch_material_check(const MaterialLaunch& m, unsigned long long* first_bad, void* stream);
+// kappa and mu into the records, the mass by colour (no races inside a colour), 1/mass,
+// and the largest vp of every caller element (for the CFL suggestion)
+int launch_material_apply(const MaterialLaunch& m, const int* color_off, int ncolors, double* mass, float* minv,
+                          double* vpmax, void* stream);
 int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream);
 int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv,
                            int nglob, int shots, double* partials, int nblocks, void* stream);

@@ -15,10 +15,9 @@ namespace semgb {
   int upload_basis_##n(const double* w, const double* h, void* stream, int ngll);                         \
   int launch_forces_##n(const ForceLaunch& L, void* stream);                                              \
   int forces_smem_bytes_##n();                                                                            \
-  int launch_strain_products_##n(const float* rec, const float* lam, const float* u, double* g_kappa,     \
-                                 double* g_mu, int nspec, double c, void* stream);                        \
-  int launch_rho_products_##n(const float* rec, const float* lam, const float* u_lo, const float* u_mid, \
-                              const float* u_hi, double* g_rho, int nspec, double c, void* stream);
+  int launch_sensitivity_##n(const float* rec, const float* lam, const float* u_lo, const float* u_mid,  \
+                             const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec, \
+                             double c_m, double c_k, void* stream);
 SEM_DECLARE_ORDER(2)
 SEM_DECLARE_ORDER(3)
 SEM_DECLARE_ORDER(4)
@@ -57,17 +56,10 @@ int launch_forces(int n, const ForceLaunch& L, void* stream) {
   return static_cast<int>(cudaErrorInvalidValue);
 }
 
-int launch_strain_products(int n, const float* rec, const float* lam, const float* u, double* g_kappa, double* g_mu,
-                           int nspec, double c, void* stream) {
-#define SEM_CALL(k) launch_strain_products_##k(rec, lam, u, g_kappa, g_mu, nspec, c, stream)
-  SEM_ORDER_SWITCH(n, SEM_CALL)
-#undef SEM_CALL
-  return static_cast<int>(cudaErrorInvalidValue);
-}
-
-int launch_rho_products(int n, const float* rec, const float* lam, const float* u_lo, const float* u_mid,
-                        const float* u_hi, double* g_rho, int nspec, double c, void* stream) {
-#define SEM_CALL(k) launch_rho_products_##k(rec, lam, u_lo, u_mid, u_hi, g_rho, nspec, c, stream)
+int launch_sensitivity(int n, const float* rec, const float* lam, const float* u_lo, const float* u_mid,
+                       const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec, double c_m,
+                       double c_k, void* stream) {
+#define SEM_CALL(k) launch_sensitivity_##k(rec, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k, stream)
   SEM_ORDER_SWITCH(n, SEM_CALL)
 #undef SEM_CALL
   return static_cast<int>(cudaErrorInvalidValue);
@@ -198,6 +190,155 @@ int launch_adjoint_update(float* F, const float* G_dev, const int* rec_node, int
   adjoint_leapfrog_kernel<<<stream_grid(nglob), 256, 0, s>>>(
       reinterpret_cast<const float4*>(lam), reinterpret_cast<float4*>(lam_old), reinterpret_cast<const float4*>(F),
       minv, nglob, static_cast<float>(dt * dt));
+  return static_cast<int>(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------------------
+// Material (Sec. II-B: isotropic moduli; Sec. I: the diagonal mass M_I = sum rho J w w w
+// over the local points that share node I). One thread per local point of a record slot.
+// ---------------------------------------------------------------------------------------
+__device__ inline void point_moduli(const MaterialLaunch& m, size_t q, double* rho, double* kappa, double* mu,
+                                    double* vp) {
+  const double rh = m.rho[q], a = m.p1[q], b = m.p2[q];
+  *rho = rh;
+  if (m.moduli) {
+    *kappa = a;
+    *mu = b;
+    *vp = sqrt((a + 4.0 * b / 3.0) / rh);
+  } else {
+    *mu = rh * b * b;
+    *kappa = rh * (a * a - 2.0 * b * b) + 2.0 * *mu / 3.0;
+    *vp = a;
+  }
+}
+
+__global__ void material_check_kernel(MaterialLaunch m, unsigned long long* first_bad) {
+  const long long n = static_cast<long long>(m.nspec) * m.ngll * m.ngll * m.ngll;
+  for (long long q = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; q < n;
+       q += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float rh = m.rho[q], a = m.p1[q], b = m.p2[q];
+    const bool finite = isfinite(rh) && isfinite(a) && isfinite(b);
+    const bool ok = finite && (m.moduli ? (rh > 0.f && b >= 0.f && a > 0.f) : (rh > 0.f && b >= 0.f && a > b));
+    if (!ok) atomicMin(first_bad, static_cast<unsigned long long>(q));
+  }
+}
+
+__global__ void material_records_kernel(MaterialLaunch m) {
+  const int n = m.ngll, np = n * n * n;
+  const long long total = static_cast<long long>(m.nspec) * np;
+  const size_t RW = (static_cast<size_t>(kRecFields) * np + 3) / 4 * 4;
+  for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long s = t / np;
+    const int p = static_cast<int>(t - s * np);
+    const int i = p % n, j = (p / n) % n, k = p / (n * n);
+    const size_t q = static_cast<size_t>(m.order[s]) * np + p;
+    double rh, kappa, mu, vp;
+    point_moduli(m, q, &rh, &kappa, &mu, &vp);
+    float* r = m.rec + s * RW;
+    const int qq = i * n * n + j + n * k;
+    r[kKappa * np + qq] = static_cast<float>(kappa);
+    r[kMu * np + qq] = static_cast<float>(mu);
+  }
+}
+
+__global__ void mass_color_kernel(MaterialLaunch m, int e0, int e1, double* mass) {
+  const int n = m.ngll, np = n * n * n;
+  const long long total = static_cast<long long>(e1 - e0) * np;
+  const size_t RW = (static_cast<size_t>(kRecFields) * np + 3) / 4 * 4;
+  for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long s = e0 + t / np;
+    const int p = static_cast<int>(t - (s - e0) * np);
+    const int i = p % n, j = (p / n) % n, k = p / (n * n);
+    const float* r = m.rec + s * RW;
+    const uint32_t g = __float_as_uint(r[kIbool * np + p]) & ~kFirstTouchBit;
+    const double J = r[kJac * np + i * n * n + j + n * k];
+    const double rh = m.rho[static_cast<size_t>(m.order[s]) * np + p];
+    mass[g] += rh * J * m.w[i] * m.w[j] * m.w[k];  // elements of one colour share no node
+  }
+}
+
+__global__ void inverse_mass_kernel(const double* __restrict__ mass, float* __restrict__ minv, int nglob) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nglob; g += gridDim.x * blockDim.x)
+    minv[g] = static_cast<float>(1.0 / mass[g]);
+}
+
+__global__ void vpmax_kernel(MaterialLaunch m, double* vpmax) {
+  const int np = m.ngll * m.ngll * m.ngll;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.nspec; e += gridDim.x * blockDim.x) {
+    double best = 0.0;
+    for (int p = 0; p < np; ++p) {
+      double rh, kappa, mu, vp;
+      point_moduli(m, static_cast<size_t>(e) * np + p, &rh, &kappa, &mu, &vp);
+      best = fmax(best, vp);
+    }
+    vpmax[e] = best;
+  }
+}
+
+int launch_material_check(const MaterialLaunch& m, unsigned long long* first_bad, void* stream) {
+  const long long n = static_cast<long long>(m.nspec) * m.ngll * m.ngll * m.ngll;
+  material_check_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(m, first_bad);
+  return static_cast<int>(cudaGetLastError());
+}
+
+int launch_material_apply(const MaterialLaunch& m, const int* color_off, int ncolors, double* mass, float* minv,
+                          double* vpmax, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int np = m.ngll * m.ngll * m.ngll;
+  material_records_kernel<<<stream_grid(static_cast<long long>(m.nspec) * np), 256, 0, s>>>(m);
+  cudaError_t e = cudaMemsetAsync(mass, 0, static_cast<size_t>(m.nglob) * sizeof(double), s);
+  if (e != cudaSuccess) return static_cast<int>(e);
+  for (int c = 0; c < ncolors; ++c) {
+    const int e0 = color_off[c], e1 = color_off[c + 1];
+    if (e1 > e0) mass_color_kernel<<<stream_grid(static_cast<long long>(e1 - e0) * np), 256, 0, s>>>(m, e0, e1, mass);
+  }
+  inverse_mass_kernel<<<stream_grid(m.nglob), 256, 0, s>>>(mass, minv, m.nglob);
+  vpmax_kernel<<<stream_grid(m.nspec), 256, 0, s>>>(m, vpmax);
+  return static_cast<int>(cudaGetLastError());
+}
+
+// Layout changes between the solver's fields [nglob][shots][4] and the caller's arrays
+// [shots][nglob][3] (state copies, displacement snapshots). One thread per (node, shot).
+__global__ void pack_kernel(const float4* __restrict__ u, float* __restrict__ out, long long nglob, int shots) {
+  const long long n = nglob * shots;
+  for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long g = shots == 1 ? t : t / shots;
+    const long long sh = t - g * shots;
+    const float4 v = u[t];
+    float* o = out + 3 * (sh * nglob + g);
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+  }
+}
+
+__global__ void unpack_kernel(const float* __restrict__ in, float4* __restrict__ u, long long nglob, int shots) {
+  const long long n = nglob * shots;
+  for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long g = shots == 1 ? t : t / shots;
+    const long long sh = t - g * shots;
+    const float* i = in + 3 * (sh * nglob + g);
+    u[t] = make_float4(i[0], i[1], i[2], 0.f);
+  }
+}
+
+int launch_pack(const float* u, float* out, int nglob, int shots, void* stream) {
+  const long long n = static_cast<long long>(nglob) * shots;
+  if (n == 0) return 0;
+  pack_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(reinterpret_cast<const float4*>(u), out,
+                                                                             nglob, shots);
+  return static_cast<int>(cudaGetLastError());
+}
+
+int launch_unpack(const float* in, float* u, int nglob, int shots, void* stream) {
+  const long long n = static_cast<long long>(nglob) * shots;
+  if (n == 0) return 0;
+  unpack_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(in, reinterpret_cast<float4*>(u),
+                                                                               nglob, shots);
   return static_cast<int>(cudaGetLastError());
 }
 

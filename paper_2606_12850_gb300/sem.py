@@ -33,6 +33,7 @@ SIGNATURES = {
     "sem_set_mesh": (_I, [_P, _I, _I, _P, _P]),
     "sem_set_material": (_I, [_P, _P, _P, _P]),
     "sem_set_moduli": (_I, [_P, _P, _P, _P]),
+    "sem_set_moduli_dev": (_I, [_P, _P, _P, _P]),
     "sem_suggest_dt": (_I, [_P, _D, _P]),
     "sem_set_dt": (_I, [_P, _D]),
     "sem_locate_nodes": (_I, [_P, _I, _P, _P, _P]),
@@ -48,6 +49,7 @@ SIGNATURES = {
     "sem_step": (_I, [_P, _I]),
     "sem_run": (_I, [_P, _I, _P]),
     "sem_run_dev": (_I, [_P, _I, _P]),
+    "sem_run_snapshots": (_I, [_P, _I, _P]),
     "sem_check_finite": (_I, [_P]),
     "sem_apply_stiffness": (_I, [_P, _P, _P]),
     "sem_apply_stiffness_strided": (_I, [_P, _P, _P, _I]),
@@ -56,6 +58,7 @@ SIGNATURES = {
     "sem_adjoint_step": (_I, [_P, _P]),
     "sem_adjoint_accumulate": (_I, [_P, _P, _P, _P]),
     "sem_adjoint_gradients": (_I, [_P, _P, _P, _P]),
+    "sem_adjoint_segment": (_I, [_P, _I, _P, _P]),
     "sem_energy_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
     "sem_sync": (_I, [_P]),
     "sem_info": (_I, [_P, _P]),
@@ -198,6 +201,11 @@ def sem_set_moduli(ctx: Ctx, rho, kappa, mu):
     _check(lib().sem_set_moduli(ctx.handle, pr, pa, pb), "sem_set_moduli", ctx)
 
 
+def sem_set_moduli_dev(ctx: Ctx, rho, kappa, mu):
+    n = ctx.nspec * ctx.ngll ** 3
+    _check(lib().sem_set_moduli_dev(ctx.handle, _dev(rho, n), _dev(kappa, n), _dev(mu, n)), "sem_set_moduli_dev", ctx)
+
+
 def sem_suggest_dt(ctx: Ctx, courant: float) -> float:
     out = ctypes.c_double(0.0)
     _check(lib().sem_suggest_dt(ctx.handle, float(courant), ctypes.byref(out)), "sem_suggest_dt", ctx)
@@ -302,6 +310,11 @@ def sem_run_dev(ctx: Ctx, nsteps: int, seis_dev=None):
            "sem_run_dev", ctx)
 
 
+def sem_run_snapshots(ctx: Ctx, nsteps: int, u_dev):
+    n = 3 * ctx.nglob * ctx.shots * int(nsteps)
+    _check(lib().sem_run_snapshots(ctx.handle, int(nsteps), _dev(u_dev, n)), "sem_run_snapshots", ctx)
+
+
 def sem_check_finite(ctx: Ctx):
     _check(lib().sem_check_finite(ctx.handle), "sem_check_finite", ctx)
 
@@ -353,6 +366,11 @@ def sem_adjoint_gradients(ctx: Ctx):
     _check(lib().sem_adjoint_gradients(ctx.handle, *[o.ctypes.data_as(_P) for o in outs]), "sem_adjoint_gradients",
            ctx)
     return tuple(outs)
+
+
+def sem_adjoint_segment(ctx: Ctx, count: int, G_dev, u_dev):
+    _check(lib().sem_adjoint_segment(ctx.handle, int(count), _dev(G_dev, 3 * ctx.nrec * int(count)),
+                                     _dev(u_dev, 3 * ctx.nglob * (int(count) + 2))), "sem_adjoint_segment", ctx)
 
 
 def sem_sync(ctx: Ctx):

@@ -177,3 +177,48 @@ def test_adjoint_on_anomaly_copy(oracle):
     print("anomaly copy adjoint rel L2 (rho, kappa, mu):", " ".join(f"{e:.2e}" for e in errs))
     assert errs[0] <= rho_tolerance(oracle, p)
     assert max(errs[1:]) <= TOL_MODULI
+
+
+def test_run_snapshots_match_the_graph_run(problem):
+    """sem_run_snapshots stores u^{n+1} after every step, bit for bit the displacement of
+    the same steps taken by sem_run (CUDA graph of ten steps plus single steps)."""
+    p = problem
+    ctx, sim = make_sim(p, 50)
+    sim.set_material(*material(p))
+    sem.sem_set_state(ctx)
+    snaps = torch.empty((23, 3 * p["mesh"].nglob), device="cuda")
+    sem.sem_run_snapshots(ctx, 23, snaps)
+    sem.sem_sync(ctx)
+    for k in (0, 9, 22):
+        sem.sem_set_state(ctx)
+        sem.sem_run(ctx, k + 1)
+        u, _, _ = sem.sem_get_state(ctx, want=(True, False, False))
+        assert np.array_equal(snaps[k].cpu().numpy().reshape(u.shape), u)
+
+
+def test_device_moduli_match_host_moduli(problem):
+    """sem_set_moduli_dev gives the same operator, mass and CFL step as sem_set_moduli, and
+    rejects a bad value naming its local point."""
+    p = problem
+    mats = material(p)
+    ctx_h, _ = make_sim(p, 50)
+    ctx_d, _ = make_sim(p, 50)
+    sem.sem_set_moduli(ctx_h, *(x.cpu().numpy() for x in mats))
+    sem.sem_set_moduli_dev(ctx_d, *mats)
+    assert sem.sem_suggest_dt(ctx_h, 0.4) == sem.sem_suggest_dt(ctx_d, 0.4)
+    u = torch.from_numpy(inputs.random_field(p["mesh"].nglob, 3)).cuda()
+    out = []
+    for ctx in (ctx_h, ctx_d):
+        sem.sem_set_dt(ctx, p["dt"])
+        f = torch.empty_like(u)
+        torch.cuda.synchronize()
+        sem.sem_apply_stiffness(ctx, u, f)
+        sem.sem_sync(ctx)
+        sem.sem_set_state(ctx, None, u.cpu().numpy(), None)
+        out.append((f.cpu().numpy(), sem.sem_energy(ctx)))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]  # kinetic energy reads the mass
+    bad = mats[0].clone()
+    bad[1, 7] = -1.0
+    with pytest.raises(sem.SemError, match="local point 71"):
+        sem.sem_set_moduli_dev(ctx_d, bad, mats[1], mats[2])
