@@ -77,6 +77,16 @@ int sem_create(sem_ctx** out, int ngll, int device, void* cuda_stream);
 /* Free every device and host resource of the context. NULL is allowed. */
 int sem_destroy(sem_ctx* ctx);
 
+/* Tunables, applied by the next sem_set_mesh.
+ *   SEM_OPT_SWEEP_SLABS: the force sweep visits the elements slab by slab (equal-count
+ *   slabs along the longest axis of the element centroids) and colour by colour inside a
+ *   slab, so that a slab's nodes can stay in L2 across its colour launches; value = slab
+ *   count, 0 or 1 = colour by colour over the whole mesh (the default). Results change only
+ *   by the summation order at nodes. SEM_EINVAL for an unknown option or a value out of
+ *   range. */
+#define SEM_OPT_SWEEP_SLABS 1
+int sem_set_option(sem_ctx* ctx, int option, long long value);
+
 /* Set the mesh (Sec. II-B hexahedral mesh, Sec. IV-C global-to-local map).
  * Computes GLL point positions from the trilinear corners, the inverse Jacobian terms by
  * differentiating positions with hprime, the colouring, the colour-sorted element order
@@ -236,7 +246,8 @@ int sem_sync(sem_ctx* ctx);
 
 /* Sizes of the set-up problem: out[0] nspec, out[1] nglob, out[2] ngll, out[3] ncolors,
  * out[4] steps taken since sem_set_state, out[5] bytes of device memory held,
- * out[6] shots. out has room for 7 values; an entry not yet defined is 0. */
+ * out[6] shots, out[7] slabs of the sweep order, out[8] force-kernel launches per sweep.
+ * out has room for 9 values; an entry not yet defined is 0. */
 int sem_info(sem_ctx* ctx, int64_t* out);
 
 /* Element count of each colour, counts[ncolors] (see sem_info for ncolors). */

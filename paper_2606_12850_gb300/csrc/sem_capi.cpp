@@ -37,7 +37,10 @@ struct sem_ctx {
   std::vector<int32_t> ibool;       // caller order
   std::vector<int> order;           // colour-sorted position -> caller element
   std::vector<int> pos_of;          // caller element -> colour-sorted position
-  std::vector<int> color_off;       // ncolors + 1
+  std::vector<int> color_count;     // elements per colour
+  std::vector<int> sweep_off;       // record-slot ranges, one per (slab, colour) launch
+  int slabs = 1;                    // spatial slabs of the sweep order
+  int slabs_opt = 0;                // requested slab count (0 = automatic)
   std::vector<float> rec;           // colour-sorted element records (host copy)
   std::vector<double> dxmin;        // per caller element
   std::vector<double> node_xyz;     // [nglob][3]
@@ -168,7 +171,10 @@ int set_device(sem_ctx* c) {
   return SEM_OK;
 }
 
-// f = -K u over all colours in order (Sec. IV-C: colour by colour, no atomics).
+// f = -K u over all colours (Sec. IV-C: colour by colour, no atomics). The launches walk
+// the mesh slab by slab and, inside a slab, colour by colour: a launch holds elements of
+// one colour only, so no two of its elements share a node, and the nodes of one slab stay
+// in L2 across its colour launches.
 int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int shots) {
   ForceLaunch L{};
   L.rec = c->d_rec;
@@ -176,9 +182,9 @@ int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int
   L.f = f;
   L.node_stride = node_stride;
   L.shots = shots;
-  for (int col = 0; col < c->ncolors; ++col) {
-    L.e0 = c->color_off[col];
-    L.e1 = c->color_off[col + 1];
+  for (size_t k = 0; k + 1 < c->sweep_off.size(); ++k) {
+    L.e0 = c->sweep_off[k];
+    L.e1 = c->sweep_off[k + 1];
     SEM_LAUNCH(c, launch_forces(c->ngll, L, c->stream));
   }
   return SEM_OK;
@@ -361,6 +367,18 @@ int sem_destroy(sem_ctx* c) {
   return SEM_OK;
 }
 
+int sem_set_option(sem_ctx* c, int option, long long value) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  switch (option) {
+    case SEM_OPT_SWEEP_SLABS:
+      if (value < 0 || value > (1 << 20)) return fail(c, SEM_EINVAL, "slab count out of range");
+      c->slabs_opt = static_cast<int>(value);
+      return SEM_OK;
+    default:
+      return fail(c, SEM_EINVAL, "unknown option " + std::to_string(option));
+  }
+}
+
 int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const double* ctrl) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (nspec < 1 || nglob < 1 || !ibool || !ctrl) return fail(c, SEM_EINVAL, "sem_set_mesh: bad arguments");
@@ -415,16 +433,45 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
     }
   }
 
-  // colour-sorted element order (stable within a colour)
-  c->color_off.assign(ncolors + 1, 0);
-  for (int e = 0; e < nspec; ++e) c->color_off[color[e] + 1]++;
-  for (int k = 0; k < ncolors; ++k) c->color_off[k + 1] += c->color_off[k];
+  // sweep order: spatial slabs along the longest axis of the element centroids (equal
+  // element counts), colour by colour inside a slab, caller order inside a colour
+  const int K = std::max(1, std::min(c->slabs_opt, nspec));
+  std::vector<int> slab(nspec, 0);
+  if (K > 1) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    std::vector<double> cen(3 * static_cast<size_t>(nspec), 0.0);
+    for (int e = 0; e < nspec; ++e)
+      for (int d = 0; d < 3; ++d) {
+        double m = 0.0;
+        for (int v = 0; v < 8; ++v) m += ctrl[24 * static_cast<size_t>(e) + 3 * v + d];
+        cen[3 * static_cast<size_t>(e) + d] = m / 8.0;
+        lo[d] = std::min(lo[d], m / 8.0);
+        hi[d] = std::max(hi[d], m / 8.0);
+      }
+    int ax = 0;
+    for (int d = 1; d < 3; ++d)
+      if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
+    std::vector<int> byc(nspec);
+    for (int e = 0; e < nspec; ++e) byc[e] = e;
+    std::stable_sort(byc.begin(), byc.end(), [&](int a, int b) { return cen[3 * static_cast<size_t>(a) + ax] < cen[3 * static_cast<size_t>(b) + ax]; });
+    for (int r = 0; r < nspec; ++r) slab[byc[r]] = static_cast<int>(static_cast<long long>(r) * K / nspec);
+  }
+  c->color_count.assign(ncolors, 0);
+  for (int e = 0; e < nspec; ++e) c->color_count[color[e]]++;
+  std::vector<int> cnt(static_cast<size_t>(K) * ncolors, 0);
+  for (int e = 0; e < nspec; ++e) cnt[static_cast<size_t>(slab[e]) * ncolors + color[e]]++;
+  std::vector<int> off(cnt.size() + 1, 0);
+  for (size_t k = 0; k < cnt.size(); ++k) off[k + 1] = off[k] + cnt[k];
+  c->sweep_off.assign(1, 0);
+  for (size_t k = 0; k < cnt.size(); ++k)
+    if (cnt[k] > 0) c->sweep_off.push_back(off[k + 1]);
+  c->slabs = K;
   c->order.assign(nspec, 0);
   c->pos_of.assign(nspec, 0);
   {
-    std::vector<int> fillp(c->color_off.begin(), c->color_off.end() - 1);
+    std::vector<int> fillp(off.begin(), off.end() - 1);
     for (int e = 0; e < nspec; ++e) {
-      const int s = fillp[color[e]]++;
+      const int s = fillp[static_cast<size_t>(slab[e]) * ncolors + color[e]]++;
       c->order[s] = e;
       c->pos_of[e] = s;
     }
@@ -510,7 +557,7 @@ static int material_apply(sem_ctx* c, const float* rho, const float* p1, const f
   SEM_CUDA(c, cudaMallocAsync(reinterpret_cast<void**>(&mass), c->nglob * sizeof(double), c->stream));
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&vpmax), c->nspec * sizeof(double), c->stream);
   if (e == cudaSuccess)
-    e = static_cast<cudaError_t>(launch_material_apply(m, c->color_off.data(), c->ncolors, mass, c->d_minv, vpmax,
+    e = static_cast<cudaError_t>(launch_material_apply(m, c->sweep_off.data(), static_cast<int>(c->sweep_off.size()) - 1, mass, c->d_minv, vpmax,
                                                        c->stream));
   c->vpmax.assign(c->nspec, 0.0);
   if (e == cudaSuccess)
@@ -939,13 +986,15 @@ int sem_info(sem_ctx* c, int64_t* out) {
   out[4] = c->steps;
   out[5] = static_cast<int64_t>(c->dev_bytes);
   out[6] = c->shots;
+  out[7] = c->slabs;
+  out[8] = static_cast<int64_t>(c->sweep_off.size()) - 1;
   return SEM_OK;
 }
 
 int sem_color_counts(sem_ctx* c, int32_t* counts) {
   if (!c || !counts) return fail(c, SEM_EINVAL, "sem_color_counts: bad arguments");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
-  for (int k = 0; k < c->ncolors; ++k) counts[k] = c->color_off[k + 1] - c->color_off[k];
+  for (int k = 0; k < c->ncolors; ++k) counts[k] = c->color_count[k];
   return SEM_OK;
 }
 

@@ -67,6 +67,17 @@ struct ForceCfg {
 #endif
 };
 
+// Programmatic dependent launch (the colour launches of one sweep overlap): a colour's
+// CTAs may be scheduled while the previous launch drains, prefetch their element records
+// (constant for the whole run) into L2, and wait for the previous grid to complete, with
+// its memory visible, before they read any wavefield. Both instructions are no-ops for a
+// kernel launched without the programmatic attribute.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void wait_prerequisite_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependent_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <bool WARP>
 __device__ __forceinline__ void team_sync() {
   if (WARP)
@@ -94,6 +105,11 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
   const int ne = min(E, e1 - ebase);
   if (WT && ne <= 0) return;  // a warp team without elements (never a CTA team)
   float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
+
+  // 0. records to L2 while the previous grid finishes, then wait for its results
+  if (tl < ne) prefetch_l2(rec + static_cast<size_t>(ebase + tl) * REC, REC * sizeof(float));
+  wait_prerequisite_grid();
+  allow_dependent_grid();
 
   // 1. gather, one thread per local point
   for (int idx = tl; idx < ne * NP; idx += TEAM) {
@@ -316,6 +332,8 @@ __global__ void __launch_bounds__(BatchCfg<N>::T)
 
   const float4* r4 = reinterpret_cast<const float4*>(rec + static_cast<size_t>(e) * REC);
   for (int q = t; q < REC / 4; q += T) smem4[q] = __ldg(r4 + q);
+  wait_prerequisite_grid();  // the record is constant; the wavefields come from the previous grid
+  allow_dependent_grid();
   __syncthreads();
 
   const int team = t / NL;
@@ -595,9 +613,17 @@ int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
     if (e != cudaSuccess) return static_cast<int>(e);
     attr_done |= bit;
   }
-  const int grid = (L.e1 - L.e0 + C::EPC - 1) / C::EPC;
-  forces_kernel<SEM_NGLL, VS><<<grid, C::T, smem, s>>>(L.rec, L.u, L.f, L.e0, L.e1);
-  return static_cast<int>(cudaGetLastError());
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((L.e1 - L.e0 + C::EPC - 1) / C::EPC);
+  cfg.blockDim = dim3(C::T);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_kernel<SEM_NGLL, VS>, L.rec, L.u, L.f, L.e0, L.e1));
 }
 
 int launch_forces_batched(const ForceLaunch& L, cudaStream_t s) {
@@ -613,8 +639,17 @@ int launch_forces_batched(const ForceLaunch& L, cudaStream_t s) {
     if (e != cudaSuccess) return static_cast<int>(e);
     attr_done |= bit;
   }
-  forces_batched_kernel<SEM_NGLL><<<L.e1 - L.e0, C::T, smem, s>>>(L.rec, L.u, L.f, L.e0, L.shots);
-  return static_cast<int>(cudaGetLastError());
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.e1 - L.e0);
+  cfg.blockDim = dim3(C::T);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_batched_kernel<SEM_NGLL>, L.rec, L.u, L.f, L.e0, L.shots));
 }
 
 int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {

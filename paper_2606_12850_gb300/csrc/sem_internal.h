@@ -134,9 +134,10 @@ struct MaterialLaunch {
 // index of the first local point that breaks rho > 0, mu (vs) >= 0, kappa > 0 (vp > vs) or
 // is not finite, as an atomic minimum into *first_bad (caller presets it to ~0ull)
 int launch_material_check(const MaterialLaunch& m, unsigned long long* first_bad, void* stream);
-// kappa and mu into the records, the mass by colour (no races inside a colour), 1/mass,
+// kappa and mu into the records, the mass range by range of the sweep order (one colour per
+// range, so no races), 1/mass,
 // and the largest vp of every caller element (for the CFL suggestion)
-int launch_material_apply(const MaterialLaunch& m, const int* color_off, int ncolors, double* mass, float* minv,
+int launch_material_apply(const MaterialLaunch& m, const int* sweep_off, int nranges, double* mass, float* minv,
                           double* vpmax, void* stream);
 int launch_nonfinite_check(const DevProblem& p, int* flag, void* stream);
 int launch_energy_partials(const float* u, const float* v, const float* f, const float* minv,

@@ -283,15 +283,15 @@ int launch_material_check(const MaterialLaunch& m, unsigned long long* first_bad
   return static_cast<int>(cudaGetLastError());
 }
 
-int launch_material_apply(const MaterialLaunch& m, const int* color_off, int ncolors, double* mass, float* minv,
+int launch_material_apply(const MaterialLaunch& m, const int* sweep_off, int nranges, double* mass, float* minv,
                           double* vpmax, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int np = m.ngll * m.ngll * m.ngll;
   material_records_kernel<<<stream_grid(static_cast<long long>(m.nspec) * np), 256, 0, s>>>(m);
   cudaError_t e = cudaMemsetAsync(mass, 0, static_cast<size_t>(m.nglob) * sizeof(double), s);
   if (e != cudaSuccess) return static_cast<int>(e);
-  for (int c = 0; c < ncolors; ++c) {
-    const int e0 = color_off[c], e1 = color_off[c + 1];
+  for (int c = 0; c < nranges; ++c) {  // each range holds elements of one colour
+    const int e0 = sweep_off[c], e1 = sweep_off[c + 1];
     if (e1 > e0) mass_color_kernel<<<stream_grid(static_cast<long long>(e1 - e0) * np), 256, 0, s>>>(m, e0, e1, mass);
   }
   inverse_mass_kernel<<<stream_grid(m.nglob), 256, 0, s>>>(mass, minv, m.nglob);

@@ -30,6 +30,7 @@ SIGNATURES = {
     "sem_color_elements": (_I, [_I, _I, _I, _P, _P, _P]),
     "sem_create": (_I, [_P, _I, _I, _P]),
     "sem_destroy": (_I, [_P]),
+    "sem_set_option": (_I, [_P, _I, ctypes.c_longlong]),
     "sem_set_mesh": (_I, [_P, _I, _I, _P, _P]),
     "sem_set_material": (_I, [_P, _P, _P, _P]),
     "sem_set_moduli": (_I, [_P, _P, _P, _P]),
@@ -174,6 +175,13 @@ def sem_destroy(ctx: Ctx):
     if ctx.handle is not None:
         _check(lib().sem_destroy(ctx.handle), "sem_destroy")
         ctx.handle = None
+
+
+SEM_OPT_SWEEP_SLABS = 1
+
+
+def sem_set_option(ctx: Ctx, option: int, value: int):
+    _check(lib().sem_set_option(ctx.handle, int(option), int(value)), "sem_set_option", ctx)
 
 
 def sem_set_mesh(ctx: Ctx, ibool, ctrl, nglob: int):
@@ -378,9 +386,9 @@ def sem_sync(ctx: Ctx):
 
 
 def sem_info(ctx: Ctx) -> dict:
-    out = np.zeros(7, dtype=np.int64)
+    out = np.zeros(9, dtype=np.int64)
     _check(lib().sem_info(ctx.handle, out.ctypes.data_as(_P)), "sem_info", ctx)
-    keys = ("nspec", "nglob", "ngll", "ncolors", "steps", "device_bytes", "shots")
+    keys = ("nspec", "nglob", "ngll", "ncolors", "steps", "device_bytes", "shots", "slabs", "launches")
     return {k: int(v) for k, v in zip(keys, out)}
 
 

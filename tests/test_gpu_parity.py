@@ -320,3 +320,26 @@ def test_divergence_watchdog():
     sem.sem_set_state(s.ctx)
     sem.sem_run(s.ctx, 20)
     sem.sem_check_finite(s.ctx)
+
+
+def test_sweep_slabs_option(oracle):
+    """A slab-major sweep order (SEM_OPT_SWEEP_SLABS) gives the same stiffness action up to
+    the summation order at nodes, and sem_info reports the slabs and launches."""
+    mesh = inputs.structured_hex_mesh((6, 4, 4), 4, (1200.0, 800.0, 800.0), jitter=0.1, seed=3)
+    mat = random_material(mesh, 71)
+    u = inputs.random_field(mesh.nglob, 72)
+    out = []
+    for K in (1, 3):
+        ctx = sem.sem_create(mesh.ngll, 0)
+        sem.sem_set_option(ctx, sem.SEM_OPT_SWEEP_SLABS, K)
+        sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+        sem.sem_set_material(ctx, *mat)
+        info = sem.sem_info(ctx)
+        assert info["slabs"] == K
+        assert K * 2 <= info["launches"] <= K * info["ncolors"]
+        out.append(gpu_forces(ctx, u))
+    assert rel_l2(out[1], out[0].astype(np.float64)) <= 1e-6
+    m = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, *mat, mesh.ngll)
+    check_forces(out[1], m.forces(u.astype(np.float64)))
+    with pytest.raises(sem.SemError):
+        sem.sem_set_option(ctx, 99, 1)
