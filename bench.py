@@ -52,6 +52,8 @@ def parse_args():
     p.add_argument("--shot-steps", type=int, default=100)
     p.add_argument("--no-sweep", action="store_true", help="skip the NGLL 3/5/7/9 (h,p) sweep")
     p.add_argument("--adjoint-steps", type=int, default=800, help="misfit-gradient measurement (0 = skip)")
+    p.add_argument("--surrogate-runs", type=int, default=4096, help="surrogate training runs (0 = skip)")
+    p.add_argument("--surrogate-epochs", type=int, default=100)
     return p.parse_args()
 
 
@@ -410,6 +412,63 @@ def measure_adjoint(device: int, nsteps: int = 800, every: int = 50):
                       "after one untimed gradient"}
 
 
+def measure_surrogate(device: int, runs: int, epochs: int, heldout: int = 256, batch: int = 256):
+    """The learned surrogate of the 16^3 layered medium (NGLL 5, 64 surface receivers, 1000
+    steps, Ricker 0.5 Hz): ``runs`` solver runs with seeded random positions and unit moment
+    tensors (32 shots per launch), Adam training of the default network, then the held-out
+    error per run (relative L2 over receivers, components and samples) against new solver
+    runs, next to the answer without learning (the nearest training run), and the time per
+    source of the network (batch 4096) against the solver."""
+    import torch
+
+    from paper_2606_12850_gb300 import inputs, surrogate
+
+    w = inputs.surrogate_cube()
+    solver = surrogate.Solver(w, shots=32, device=device)
+    tr = surrogate.generate_runs(solver, runs, seed=1)
+    te = surrogate.generate_runs(solver, heldout, seed=2)
+    amp = solver.amplitude_model().fit(tr.xyz, surrogate.run_rms(tr.y))
+    yn = surrogate.training_targets(tr.y, amp(tr.xyz), 1.0)
+    scale = 1.0 / float(yn.pow(2).mean().sqrt())
+    yn.mul_(scale)
+    spec = surrogate.Spec()
+    model = surrogate.Model(spec, max_batch=batch, device=device)
+    model.set_params(spec.init_params(1))
+    x = torch.from_numpy(tr.x).to(torch.device("cuda", device))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    losses = surrogate.train(model, x, yn, epochs=epochs, batch=batch, lr=2e-3, seed=3)
+    train_s = time.perf_counter() - t
+    del yn
+    sur = surrogate.Surrogate(model, scale, w.mesh.lengths[0], amp, solver)
+    pred = sur.predict(te.xyz, te.moments)
+    err = surrogate.rel_l2_per_run(pred, te.y)
+    err_nn = surrogate.rel_l2_per_run(surrogate.nearest_run_baseline(tr, te), te.y)
+    n_inf = 4096
+    xi = x[:n_inf].contiguous() if runs >= n_inf else x.repeat((n_inf + runs - 1) // runs, 1)[:n_inf].contiguous()
+    yi = torch.empty((n_inf, spec.out_c, spec.out_l), device=x.device)
+    model.forward(xi, yi)
+    model.sync()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    model.forward(xi, yi)
+    model.sync()
+    infer_s = time.perf_counter() - t
+    solver_ms = 1e3 * (tr.seconds + te.seconds) / (runs + heldout)
+    net_ms = 1e3 * infer_s / n_inf
+    return {"medium": w.name, "train_runs": runs, "heldout_runs": heldout,
+            "network": f"MLP 9-512-512, seed [64][125], conv decoder x2 x2 x2 to 1000 samples, "
+                       f"6 x 192 channels combined with the moment tensor; {model.nparams} parameters, bf16 "
+                       "weights, fp32 accumulate",
+            "epochs": epochs, "batch": batch, "train_s": train_s, "final_loss": losses[-1],
+            "generation_s": tr.seconds + te.seconds, "solver_ms_per_run": solver_ms,
+            "network_ms_per_source_batch4096": net_ms, "speedup_per_source": solver_ms / net_ms,
+            "heldout_rel_l2": {"median": float(np.median(err)), "mean": float(err.mean()),
+                               "p90": float(np.percentile(err, 90))},
+            "nearest_run_rel_l2": {"median": float(np.median(err_nn)), "mean": float(err_nn.mean())},
+            "timing": "wall clock with device synchronisation"}
+
+
 def run_ours(args):
     import torch
 
@@ -519,6 +578,10 @@ def run_ours(args):
     if args.adjoint_steps > 0:
         adj = measure_adjoint(local, args.adjoint_steps)
 
+    sur = None
+    if args.surrogate_runs > 0:
+        sur = measure_surrogate(local, args.surrogate_runs, args.surrogate_epochs)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, _, _ = oracle_sample_rate(args.ngll, args.cpu_seconds)
@@ -544,7 +607,7 @@ def run_ours(args):
                                   "bytes_per_step": alg["step"]},
             "global_pt_updates_per_s": world * mesh.nglob * K / (ms / 1e3),
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clock_info,
-            "batched_shots": batched, "hp_sweep": sweep, "adjoint": adj,
+            "batched_shots": batched, "hp_sweep": sweep, "adjoint": adj, "surrogate": sur,
             "kernel_sources": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)

@@ -122,6 +122,10 @@ int sem_set_dt(sem_ctx* ctx, double dt);
 int sem_locate_nodes(sem_ctx* ctx, int npts, const double* xyz, const double* surface_z,
                      int32_t* node_out);
 
+/* Physical position of global nodes: xyz_out[i][0..2] of node[i] (GLL points of the
+ * trilinear elements, Sec. II-B), float64 host arrays. */
+int sem_node_xyz(sem_ctx* ctx, int npts, const int32_t* node, double* xyz_out);
+
 /* Point forces (Sec. V-C): at step n, accel_raw[node[s]] += force[s][0..2] * R(t_{n+1} - t0)
  * with the Ricker wavelet R(tau) = (1 - 2 a) exp(-a), a = (pi f0 tau)^2, evaluated in
  * float64. nsrc may be 0. */
@@ -140,6 +144,15 @@ int sem_set_shots(sem_ctx* ctx, int nshots);
  * shot). */
 int sem_set_shot_sources(sem_ctx* ctx, int nsrc, const int32_t* shot, const int32_t* node,
                          const double* force, double f0, double t0);
+
+/* Moment-tensor point sources per shot (the equivalent body force -M . grad(delta) of a
+ * source at node[s], with the Ricker time function of sem_set_sources): node I receives
+ * f_I = M grad(psi_I)(x_s), the gradient taken in the lowest-numbered element that holds
+ * node[s] (the Lagrange basis of Sec. II-B through its inverse Jacobian), so the forces sit
+ * on the 3 NGLL - 2 nodes of the three GLL lines through the source. moment: float64
+ * [nsrc][6] = (Mxx, Myy, Mzz, Mxy, Mxz, Myz) in N m. Replaces all sources. */
+int sem_set_shot_moment_sources(sem_ctx* ctx, int nsrc, const int32_t* shot, const int32_t* node,
+                                const double* moment, double f0, double t0);
 
 /* Receivers: the displacement at node[r] is recorded after every step of sem_run /
  * sem_run_dev, for every shot. nrec may be 0. */

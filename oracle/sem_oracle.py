@@ -328,6 +328,39 @@ def ricker(t, f0: float, t0: float):
     return (1.0 - 2.0 * a) * np.exp(-a)
 
 
+def moment_tensor_forces(model: Model, node: int, moment) -> tuple:
+    """Nodal forces of a moment-tensor point source at global node ``node``: the body force
+    -M . grad(delta(x - x_s)) tested against the Lagrange basis of Sec. II-B gives, after
+    integration by parts, f_I = M grad(psi_I)(x_s). The gradient is taken in the
+    lowest-numbered element that holds the node (a GLL node on an element face has one
+    one-sided gradient per element; this is the reading used). ``moment`` =
+    (Mxx, Myy, Mzz, Mxy, Mxz, Myz). Returns (nodes [m], forces [m, 3]) for the nodes whose
+    basis function has a nonzero gradient at x_s."""
+    n = model.ngll
+    ib = model.ibool.reshape(model.nspec, -1)
+    e = int(np.nonzero(np.any(ib == node, axis=1))[0][0])
+    p0 = int(np.nonzero(ib[e] == node)[0][0])
+    i0, j0, k0 = p0 % n, (p0 // n) % n, p0 // (n * n)
+    mxx, myy, mzz, mxy, mxz, myz = (float(v) for v in moment)
+    M = np.array([[mxx, mxy, mxz], [mxy, myy, myz], [mxz, myz, mzz]])
+    D = model.dxi_dx[e, :, :, k0, j0, i0]  # D[r, d] = d xi_r / d x_d at the source
+    H = model.basis.hprime  # H[a, b] = l_b'(xi_a)
+    nodes, forces = [], []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                # d psi_(i,j,k) / d xi_r at (xi_i0, xi_j0, xi_k0): psi = l_i(xi) l_j(eta) l_k(zeta)
+                dpsi = np.array([H[i0, i] * (j == j0) * (k == k0),
+                                 H[j0, j] * (i == i0) * (k == k0),
+                                 H[k0, k] * (i == i0) * (j == j0)], dtype=np.float64)
+                if not np.any(dpsi):
+                    continue
+                grad = dpsi @ D  # d psi / d x_d
+                nodes.append(int(ib[e, i + n * (j + n * k)]))
+                forces.append(M @ grad)
+    return np.array(nodes, dtype=np.int64), np.array(forces)
+
+
 def newmark_run(model: Model, dt: float, nsteps: int, u0=None, v0=None, a0=None,
                 src_nodes=(), src_force=(), f0: float = 10.0, t0: float = 0.12,
                 rec_nodes=(), energy: bool = False):

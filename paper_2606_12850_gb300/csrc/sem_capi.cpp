@@ -44,6 +44,7 @@ struct sem_ctx {
   std::vector<float> rec;           // colour-sorted element records (host copy)
   std::vector<double> dxmin;        // per caller element
   std::vector<double> node_xyz;     // [nglob][3]
+  std::vector<double> ctrl;         // [nspec][8][3] corner vertices (caller order)
   std::vector<double> vpmax;        // per caller element
   double dt = 0.0;
 
@@ -501,6 +502,7 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   }
 
   c->ibool.assign(ibool, ibool + nloc);
+  c->ctrl.assign(ctrl, ctrl + 24 * static_cast<size_t>(nspec));
   c->nspec = nspec;
   c->nglob = nglob;
   c->ncolors = ncolors;
@@ -665,6 +667,17 @@ int sem_set_dt(sem_ctx* c, double dt) {
   return SEM_OK;
 }
 
+int sem_node_xyz(sem_ctx* c, int npts, const int32_t* node, double* xyz_out) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (npts < 0 || (npts > 0 && (!node || !xyz_out))) return fail(c, SEM_EINVAL, "sem_node_xyz: bad arguments");
+  for (int i = 0; i < npts; ++i) {
+    if (node[i] < 0 || node[i] >= c->nglob) return fail(c, SEM_EINVAL, "node out of range");
+    for (int d = 0; d < 3; ++d) xyz_out[3 * i + d] = c->node_xyz[3 * static_cast<size_t>(node[i]) + d];
+  }
+  return SEM_OK;
+}
+
 int sem_locate_nodes(sem_ctx* c, int npts, const double* xyz, const double* surface_z, int32_t* node_out) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
@@ -729,6 +742,53 @@ int sem_set_shot_sources(sem_ctx* c, int nsrc, const int32_t* shot, const int32_
                          double f0, double t0) {
   if (nsrc > 0 && !shot) return fail(c, SEM_EINVAL, "sem_set_shot_sources: NULL shot array");
   return set_sources_impl(c, nsrc, shot, node, force, f0, t0);
+}
+
+int sem_set_shot_moment_sources(sem_ctx* c, int nsrc, const int32_t* shot, const int32_t* node, const double* moment,
+                                double f0, double t0) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (nsrc < 0 || (nsrc > 0 && (!shot || !node || !moment)))
+    return fail(c, SEM_EINVAL, "sem_set_shot_moment_sources: bad arguments");
+  const int n = c->ngll, np = n * n * n;
+  std::vector<int> owner_e(c->nglob, -1), owner_p(c->nglob, -1);  // lowest element holding a node
+  for (int e = c->nspec - 1; e >= 0; --e)
+    for (int p = 0; p < np; ++p) {
+      const int g = c->ibool[static_cast<size_t>(e) * np + p];
+      owner_e[g] = e;
+      owner_p[g] = p;
+    }
+  std::vector<double> xyz(3 * np), G(9 * np), J(np);
+  std::vector<int32_t> shots, nodes;
+  std::vector<double> forces;
+  for (int s = 0; s < nsrc; ++s) {
+    if (node[s] < 0 || node[s] >= c->nglob) return fail(c, SEM_EINVAL, "source node out of range");
+    if (shot[s] < 0 || shot[s] >= c->shots) return fail(c, SEM_EINVAL, "source shot out of range");
+    for (int q = 0; q < 6; ++q)
+      if (!std::isfinite(moment[6 * s + q])) return fail(c, SEM_EINVAL, "non-finite moment tensor");
+    const int e = owner_e[node[s]], p0 = owner_p[node[s]];
+    const int i0 = p0 % n, j0 = (p0 / n) % n, k0 = p0 / (n * n);
+    element_geometry(n, c->xi.data(), c->hprime.data(), c->ctrl.data() + 24 * static_cast<size_t>(e), xyz.data(),
+                     G.data(), J.data());
+    const double* m6 = moment + 6 * s;  // Mxx Myy Mzz Mxy Mxz Myz
+    const double M[3][3] = {{m6[0], m6[3], m6[4]}, {m6[3], m6[1], m6[5]}, {m6[4], m6[5], m6[2]}};
+    const double* g0 = G.data() + 9 * static_cast<size_t>(p0);  // dxi_r/dx_d at 3r + d
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          // reference gradient of psi_(i,j,k) at the source point (i0, j0, k0)
+          const double dr[3] = {(j == j0 && k == k0) ? c->hprime[i0 * n + i] : 0.0,
+                                (i == i0 && k == k0) ? c->hprime[j0 * n + j] : 0.0,
+                                (i == i0 && j == j0) ? c->hprime[k0 * n + k] : 0.0};
+          if (dr[0] == 0.0 && dr[1] == 0.0 && dr[2] == 0.0) continue;
+          double grad[3];
+          for (int d = 0; d < 3; ++d) grad[d] = dr[0] * g0[d] + dr[1] * g0[3 + d] + dr[2] * g0[6 + d];
+          shots.push_back(shot[s]);
+          nodes.push_back(c->ibool[static_cast<size_t>(e) * np + i + n * (j + n * k)]);
+          for (int a = 0; a < 3; ++a) forces.push_back(M[a][0] * grad[0] + M[a][1] * grad[1] + M[a][2] * grad[2]);
+        }
+  }
+  return set_sources_impl(c, static_cast<int>(nodes.size()), shots.data(), nodes.data(), forces.data(), f0, t0);
 }
 
 int sem_set_shots(sem_ctx* c, int nshots) {

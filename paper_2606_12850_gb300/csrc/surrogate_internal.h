@@ -1,0 +1,54 @@
+// Internal declarations of the surrogate network's CUDA kernels (surrogate_kernels.cu),
+// used by the model runtime (surrogate_capi.cpp). Activations are float32 [batch][C][L]
+// (or [batch][features]); weights are read as bfloat16; every reduction runs in a fixed
+// order, so results are bitwise reproducible.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace sgk {
+
+using bf16 = __nv_bfloat16;
+
+// Split-K workspace need (floats) of the weight-gradient products for an M x N result.
+size_t splitk_floats(int M, int N, int K);
+
+// Y = act(X W^T + b): X [B][K], W [N][K] (bf16), pre/out [B][N]; out may alias nothing.
+int linear_forward(int B, int K, int N, const float* X, const bf16* W, const float* bias, float* pre, float* out,
+                   bool gelu, cudaStream_t s);
+// dX [B][K] = dZ [B][N] W [N][K]
+int linear_backward_data(int B, int K, int N, const float* dZ, const bf16* W, float* dX, cudaStream_t s);
+// dW [N][K] = dZ^T X; db [N] = column sums of dZ
+int linear_backward_weight(int B, int K, int N, const float* dZ, const float* X, float* dW, float* db, float* ws,
+                           cudaStream_t s);
+
+// Width-3 'same' convolution of the input upsampled by `up` along time:
+// pre[b][o][t] = bias[o] + sum_{c,d} W[o][c][d] X[b][c][(t + d - 1) / up] (zero outside),
+// t < L = Lin * up; out = gelu(pre) when out != nullptr.
+int conv_forward(int B, int Ci, int Co, int Lin, int up, const float* X, const bf16* W, const float* bias,
+                 float* pre, float* out, cudaStream_t s);
+// dX [B][Ci][Lin] from dZ [B][Co][L] (the upsampling adjoint sums the repeated samples)
+int conv_backward_data(int B, int Ci, int Co, int Lin, int up, const float* dZ, const bf16* W, float* dX,
+                       cudaStream_t s);
+// dW [Co][Ci][3] and db [Co]
+int conv_backward_weight(int B, int Ci, int Co, int Lin, int up, const float* dZ, const float* X, float* dW,
+                         float* db, float* ws, cudaStream_t s);
+
+// dz[i] *= gelu'(pre[i])
+int gelu_backward(size_t n, const float* pre, float* dz, cudaStream_t s);
+// dy = 2 (y - t) / n; partials[kLossBlocks] = per-block sums of (y - t)^2 in float64
+constexpr int kLossBlocks = 608;
+int mse_grad(size_t n, const float* y, const float* t, float* dy, double* partials, cudaStream_t s);
+// Adam on n master parameters, then the bf16 mirror
+int adam_update(size_t n, float* p, const float* g, float* m, float* v, bf16* pb, float lr, float beta1, float beta2,
+                float eps, float inv_c1, float inv_c2, cudaStream_t s);
+int to_bf16(size_t n, const float* p, bf16* pb, cudaStream_t s);
+// y [B][C][L] = sum_k x[b][in_dim - K + k] D[b][k*C + c][t], and its adjoint in D
+int contract_forward(int B, int K, int C, int L, int in_dim, const float* x, const float* D, float* y, cudaStream_t s);
+int contract_backward(int B, int K, int C, int L, int in_dim, const float* x, const float* dy, float* dD,
+                      cudaStream_t s);
+
+}  // namespace sgk

@@ -57,6 +57,16 @@ def uniform(seed: int, shape, low: float = 0.0, high: float = 1.0, stream: int =
     return (low + (high - low) * u01).reshape(shape)
 
 
+def normal(seed: int, shape, stream: int = 0) -> np.ndarray:
+    """Seeded i.i.d. N(0, 1) doubles by the Box-Muller transform of two splitmix64 uniforms."""
+    shape = tuple(np.atleast_1d(shape).tolist()) if not isinstance(shape, tuple) else shape
+    count = int(np.prod(shape)) if len(shape) else 1
+    u1 = uniform(seed, (count,), stream=2 * stream + 1)
+    u2 = uniform(seed, (count,), stream=2 * stream + 2)
+    u1 = np.where(u1 > 0.0, u1, 2.0 ** -53)
+    return (np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)).reshape(shape)
+
+
 @dataclass
 class HexMesh:
     """A structured conforming hexahedral mesh given as corner vertices plus ``ibool``."""
@@ -236,6 +246,29 @@ def perturbed_layered_cube(n: int = 32, ngll: int = 5, amplitude: float = 0.05, 
     w.vs = w.vs * scale[:, None]
     w.name = f"{w.name}, {100 * amplitude:g}% Gaussian velocity anomaly"
     return w
+
+
+def surrogate_cube(n: int = 16, ngll: int = 5, nrec_side: int = 8, nsteps: int = 1000, f0: float = 0.5,
+                   t0: float = 2.0, side: float = 4000.0) -> Workload:
+    """The medium of the learned surrogate: the three-layer jittered cube (side 4 km) with
+    ``n`` elements per side, ``nrec_side**2`` surface receivers and a Ricker of dominant
+    frequency f0 delayed by t0. At 0.5 Hz the shortest S wavelength spans about seven
+    element widths at n = 16, so the traces vary smoothly enough with the source position
+    for a few thousand runs to sample them. The source term is set per run."""
+    w = layered_cube(ngll, n=n, side=side, nsteps=nsteps, nrec_side=nrec_side)
+    w.f0, w.t0 = f0, t0
+    w.name = f"{w.name}, {nrec_side * nrec_side} surface receivers, Ricker {f0:g} Hz"
+    return w
+
+
+def surrogate_sources(count: int, side: float, seed: int, margin: float = 0.05) -> tuple:
+    """Source positions i.i.d. uniform in [margin, 1 - margin]^3 * side and moment tensors
+    (Mxx, Myy, Mzz, Mxy, Mxz, Myz) with i.i.d. N(0, 1) entries scaled to unit Euclidean
+    norm. Returns (positions [count][3], moments [count][6])."""
+    pos = uniform(seed, (count, 3), margin * side, (1.0 - margin) * side, stream=21)
+    m = normal(seed, (count, 6), stream=22)
+    m /= np.linalg.norm(m, axis=1, keepdims=True)
+    return pos, m
 
 
 def random_field(nglob: int, seed: int, scale: float = 1.0, stream: int = 7) -> np.ndarray:

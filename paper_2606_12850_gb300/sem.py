@@ -38,10 +38,12 @@ SIGNATURES = {
     "sem_suggest_dt": (_I, [_P, _D, _P]),
     "sem_set_dt": (_I, [_P, _D]),
     "sem_locate_nodes": (_I, [_P, _I, _P, _P, _P]),
+    "sem_node_xyz": (_I, [_P, _I, _P, _P]),
     "sem_set_sources": (_I, [_P, _I, _P, _P, _D, _D]),
     "sem_set_receivers": (_I, [_P, _I, _P]),
     "sem_set_shots": (_I, [_P, _I]),
     "sem_set_shot_sources": (_I, [_P, _I, _P, _P, _P, _D, _D]),
+    "sem_set_shot_moment_sources": (_I, [_P, _I, _P, _P, _P, _D, _D]),
     "sem_set_state": (_I, [_P, _P, _P, _P]),
     "sem_set_state_dev": (_I, [_P, _P, _P, _P]),
     "sem_set_step": (_I, [_P, ctypes.c_longlong]),
@@ -233,6 +235,13 @@ def sem_locate_nodes(ctx: Ctx, xyz, surface_z=None) -> np.ndarray:
     return out
 
 
+def sem_node_xyz(ctx: Ctx, node) -> np.ndarray:
+    nd, pn = _host(np.atleast_1d(node), np.int32)
+    out = np.empty((nd.size, 3))
+    _check(lib().sem_node_xyz(ctx.handle, nd.size, pn, out.ctypes.data_as(_P)), "sem_node_xyz", ctx)
+    return out
+
+
 def sem_set_sources(ctx: Ctx, node, force, f0: float, t0: float):
     nd, pn = _host(np.atleast_1d(node), np.int32)
     fo, pf = _host(np.atleast_2d(force), np.float64, (nd.size, 3))
@@ -250,6 +259,14 @@ def sem_set_shot_sources(ctx: Ctx, shot, node, force, f0: float, t0: float):
     fo, pf = _host(np.atleast_2d(force), np.float64, (sh.size, 3))
     _check(lib().sem_set_shot_sources(ctx.handle, sh.size, ps, pn, pf, float(f0), float(t0)),
            "sem_set_shot_sources", ctx)
+
+
+def sem_set_shot_moment_sources(ctx: Ctx, shot, node, moment, f0: float, t0: float):
+    nd, pn = _host(np.atleast_1d(node), np.int32)
+    sh, ps = _host(np.atleast_1d(shot), np.int32, (nd.size,))
+    mo, pm = _host(np.atleast_2d(moment), np.float64, (nd.size, 6))
+    _check(lib().sem_set_shot_moment_sources(ctx.handle, nd.size, ps, pn, pm, float(f0), float(t0)),
+           "sem_set_shot_moment_sources", ctx)
 
 
 def sem_set_receivers(ctx: Ctx, node):

@@ -34,6 +34,40 @@ def test_header_symbols_exported_and_bound():
     assert sorted(sem.SIGNATURES) == declared
 
 
+def test_surrogate_header_symbols_exported_and_bound():
+    from paper_2606_12850_gb300 import surrogate
+    text = open(os.path.join(ROOT, "include", "surrogate.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    declared = sorted(set(re.findall(r"\b(sg_[a-z_]+)\s*\(", text)))
+    assert len(declared) >= 10
+    lib = surrogate.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(surrogate.SIGNATURES) == declared
+
+
+def test_surrogate_spec_sizes():
+    """The default network: 9 -> 512 -> 512 -> [64][125], decoder to 6 x 192 x 1000,
+    combined with the six moment entries into 192 x 1000."""
+    from paper_2606_12850_gb300 import surrogate
+    spec = surrogate.Spec()
+    assert (spec.out_c, spec.out_l) == (192, 1000)
+    n = sum(int(np.prod(s)) for _, s in spec.shapes())
+    assert n == 9 * 512 + 512 + 512 * 512 + 512 + 512 * 8000 + 8000 + (96 * 64 * 3 + 96) + 2 * (96 * 96 * 3 + 96) \
+        + (1152 * 96 * 3 + 1152)
+    flat = spec.init_params(1)
+    parts = spec.split(flat)
+    assert np.all(parts["b1"] == 0) and np.abs(parts["W1"]).max() <= np.sqrt(6 / 9)
+
+
+def test_surrogate_sources_are_unit_moments():
+    pos, m = inputs.surrogate_sources(2000, 4000.0, seed=3)
+    assert pos.min() >= 200.0 and pos.max() <= 3800.0
+    np.testing.assert_allclose(np.linalg.norm(m, axis=1), 1.0, rtol=0, atol=1e-12)
+    z = inputs.normal(5, (200000,))
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1.0) < 0.01
+
+
 def test_version():
     assert sem.sem_version() >= 100
 
