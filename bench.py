@@ -77,10 +77,12 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the force kernel's sources (template, per-order units, record layout): a
+    profile's counters stay valid while it matches."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_12850_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name in ("sem_forces.cuh", "sem_internal.h") or (name.startswith("sem_forces_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(f.read())
     return h.hexdigest()[:16]
