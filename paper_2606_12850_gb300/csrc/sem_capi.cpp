@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/sem.h"
+#include "sem.h"
 #include "sem_internal.h"
 
 using namespace semgb;

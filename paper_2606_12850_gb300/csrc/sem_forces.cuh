@@ -111,23 +111,46 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
   wait_prerequisite_grid();
   allow_dependent_grid();
 
-  // 1. gather, one thread per local point
-  for (int idx = tl; idx < ne * NP; idx += TEAM) {
-    const int le = idx / NP;
-    const int p = idx - le * NP;
-    float* eb = ts + le * ES;
-    const uint32_t w = __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + p));
-    reinterpret_cast<uint32_t*>(eb + 9 * NP)[p] = w;
-    const size_t g = w & ~kFirstTouchBit;
-    if (VS == 4) {
-      const float4 q = __ldg(reinterpret_cast<const float4*>(u) + g);
-      eb[3 * p] = q.x;
-      eb[3 * p + 1] = q.y;
-      eb[3 * p + 2] = q.z;
-    } else {
-      eb[3 * p] = __ldg(u + 3 * g);
-      eb[3 * p + 1] = __ldg(u + 3 * g + 1);
-      eb[3 * p + 2] = __ldg(u + 3 * g + 2);
+  // 1. gather, one thread per local point; GB points per thread at a time, their ibool
+  //    words first and then their nodes, so that the loads of a group are all in flight
+  constexpr int GB = 4;
+  for (int base = tl; base < ne * NP; base += GB * TEAM) {
+    uint32_t w[GB];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      const int le = idx / NP;
+      w[r] = idx < ne * NP ? __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + (idx - le * NP))) : 0u;
+    }
+    float q[GB][3];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const size_t g = w[r] & ~kFirstTouchBit;
+      if (base + r * TEAM < ne * NP) {
+        if (VS == 4) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(u) + g);
+          q[r][0] = v.x;
+          q[r][1] = v.y;
+          q[r][2] = v.z;
+        } else {
+          q[r][0] = __ldg(u + 3 * g);
+          q[r][1] = __ldg(u + 3 * g + 1);
+          q[r][2] = __ldg(u + 3 * g + 2);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      if (idx < ne * NP) {
+        const int le = idx / NP;
+        const int p = idx - le * NP;
+        float* eb = ts + le * ES;
+        reinterpret_cast<uint32_t*>(eb + 9 * NP)[p] = w[r];
+        eb[3 * p] = q[r][0];
+        eb[3 * p + 1] = q[r][1];
+        eb[3 * p + 2] = q[r][2];
+      }
     }
   }
   team_sync<WT>();
@@ -264,7 +287,36 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
   }
   team_sync<WT>();
 
-  // 4. scatter in the gather's coalesced order
+  // 4. scatter in the gather's coalesced order; for the padded layout the previous values
+  //    of a group of GB nodes are loaded before any of them is written back
+  if (VS == 4) {
+    for (int base = tl; base < ne * NP; base += GB * TEAM) {
+      uint32_t w[GB];
+      float4 prev[GB];
+#pragma unroll
+      for (int r = 0; r < GB; ++r) {
+        const int idx = base + r * TEAM;
+        w[r] = kFirstTouchBit;
+        prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < ne * NP) {
+          const int e = idx / NP;
+          w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
+          if (!(w[r] & kFirstTouchBit)) prev[r] = reinterpret_cast<const float4*>(f)[w[r] & ~kFirstTouchBit];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < GB; ++r) {
+        const int idx = base + r * TEAM;
+        if (idx < ne * NP) {
+          const int e = idx / NP;
+          const float* src = ts + e * ES + 3 * (idx - e * NP);
+          reinterpret_cast<float4*>(f)[w[r] & ~kFirstTouchBit] =
+              make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
+        }
+      }
+    }
+    return;
+  }
   for (int idx = tl; idx < ne * NP; idx += TEAM) {
     const int e = idx / NP;
     const int p = idx - e * NP;
@@ -272,17 +324,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     const uint32_t w = reinterpret_cast<const uint32_t*>(sb + 9 * NP)[p];
     const size_t g = w & ~kFirstTouchBit;
     const float* src = sb + 3 * p;
-    if (VS == 4) {
-      float4* f4 = reinterpret_cast<float4*>(f) + g;
-      float4 o = make_float4(src[0], src[1], src[2], 0.f);
-      if (!(w & kFirstTouchBit)) {
-        const float4 prev = *f4;
-        o.x += prev.x;
-        o.y += prev.y;
-        o.z += prev.z;
-      }
-      *f4 = o;
-    } else if (w & kFirstTouchBit) {
+    if (w & kFirstTouchBit) {
       f[3 * g] = src[0];
       f[3 * g + 1] = src[1];
       f[3 * g + 2] = src[2];

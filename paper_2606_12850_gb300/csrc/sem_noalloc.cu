@@ -6,7 +6,7 @@
 #include <atomic>
 #include <string>
 
-#include "../../include/sem.h"
+#include "sem.h"
 #include "sem_internal.h"
 
 namespace semgb {

@@ -8,8 +8,8 @@
 #include <string>
 #include <vector>
 
-#include "../../include/sem.h"
-#include "../../include/surrogate.h"
+#include "sem.h"
+#include "surrogate.h"
 #include "surrogate_internal.h"
 
 using sgk::bf16;
