@@ -354,10 +354,17 @@ struct BatchCfg {
   static constexpr int REC = (kRecFields * NP + 3) / 4 * 4;
   static constexpr int CS = ForceCfg<N>::ES;  // per-shot cube stride (bank-padded)
   static constexpr int SMEM_FLOATS = REC + SB * CS;
+  // CTAs per SM the register allocation must allow: 4 at NGLL <= 5 (from a GB300 sweep of
+  // 3/4/5 on 32 shots of the 48^3 mesh: 16.2/15.9/19.0 ms per step, 17.6 ms uncapped)
+#ifdef SEM_BATCH_MIN_BLOCKS
+  static constexpr int MIN_BLOCKS = SEM_BATCH_MIN_BLOCKS;
+#else
+  static constexpr int MIN_BLOCKS = NL <= 32 ? 4 : 1;
+#endif
 };
 
 template <int N>
-__global__ void __launch_bounds__(BatchCfg<N>::T)
+__global__ void __launch_bounds__(BatchCfg<N>::T, BatchCfg<N>::MIN_BLOCKS)
     forces_batched_kernel(const float* __restrict__ rec, const float* __restrict__ u, float* __restrict__ f,
                           int e0, int shots) {
   using C = BatchCfg<N>;
@@ -394,17 +401,30 @@ __global__ void __launch_bounds__(BatchCfg<N>::T)
   const float4* u4 = reinterpret_cast<const float4*>(u);
   float4* f4 = reinterpret_cast<float4*>(f);
 
+  constexpr int GB = 4;  // (point, shot) slots per thread whose loads are in flight together
   for (int s0 = 0; s0 < shots; s0 += SB) {
     const int ns = min(SB, shots - s0);
-    for (int idx = t; idx < NP * ns; idx += T) {
-      const int p = idx / ns;
-      const int sh = idx - p * ns;
-      const size_t g = sib[p] & ~kFirstTouchBit;
-      const float4 q4 = __ldg(u4 + g * shots + s0 + sh);
-      float* cb = cubes + sh * CS + 3 * p;
-      cb[0] = q4.x;
-      cb[1] = q4.y;
-      cb[2] = q4.z;
+    for (int base = t; base < NP * ns; base += GB * T) {
+      float4 q4[GB];
+#pragma unroll
+      for (int r = 0; r < GB; ++r) {
+        const int idx = base + r * T;
+        if (idx < NP * ns) {
+          const int p = idx / ns;
+          q4[r] = __ldg(u4 + (sib[p] & ~kFirstTouchBit) * shots + s0 + (idx - p * ns));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < GB; ++r) {
+        const int idx = base + r * T;
+        if (idx < NP * ns) {
+          const int p = idx / ns;
+          float* cb = cubes + (idx - p * ns) * CS + 3 * p;
+          cb[0] = q4[r].x;
+          cb[1] = q4[r].y;
+          cb[2] = q4[r].z;
+        }
+      }
     }
     __syncthreads();
 
@@ -514,21 +534,29 @@ __global__ void __launch_bounds__(BatchCfg<N>::T)
       }
     }
     __syncthreads();
-    for (int idx = t; idx < NP * ns; idx += T) {
-      const int p = idx / ns;
-      const int sh = idx - p * ns;
-      const uint32_t w = sib[p];
-      const size_t g = w & ~kFirstTouchBit;
-      const float* src = cubes + sh * CS + 3 * p;
-      float4* dst = f4 + g * shots + s0 + sh;
-      float4 o = make_float4(src[0], src[1], src[2], 0.f);
-      if (!(w & kFirstTouchBit)) {
-        const float4 prev = *dst;
-        o.x += prev.x;
-        o.y += prev.y;
-        o.z += prev.z;
+    for (int base = t; base < NP * ns; base += GB * T) {
+      float4 prev[GB];
+#pragma unroll
+      for (int r = 0; r < GB; ++r) {
+        const int idx = base + r * T;
+        prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < NP * ns) {
+          const int p = idx / ns;
+          const uint32_t w = sib[p];
+          if (!(w & kFirstTouchBit)) prev[r] = f4[(w & ~kFirstTouchBit) * shots + s0 + (idx - p * ns)];
+        }
       }
-      *dst = o;
+#pragma unroll
+      for (int r = 0; r < GB; ++r) {
+        const int idx = base + r * T;
+        if (idx < NP * ns) {
+          const int p = idx / ns;
+          const int sh = idx - p * ns;
+          const float* src = cubes + sh * CS + 3 * p;
+          f4[(sib[p] & ~kFirstTouchBit) * shots + s0 + sh] =
+              make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
+        }
+      }
     }
     __syncthreads();
   }
@@ -565,22 +593,46 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
   const int ne = min(E, nspec - ebase);
   if (WT && ne <= 0) return;
   float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
-  for (int idx = tl; idx < ne * NP; idx += TEAM) {
-    const int le = idx / NP;
-    const int p = idx - le * NP;
-    float* eb = ts + le * ES;
-    const size_t g = __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + p)) & ~kFirstTouchBit;
-    const float4 l4 = __ldg(reinterpret_cast<const float4*>(lam) + g);
-    const float um[3] = {__ldg(u_mid + 3 * g), __ldg(u_mid + 3 * g + 1), __ldg(u_mid + 3 * g + 2)};
-    const float lv[3] = {l4.x, l4.y, l4.z};
-    float dot = 0.f;
+  constexpr int GB = 2;  // points per thread whose loads are in flight together
+  for (int base = tl; base < ne * NP; base += GB * TEAM) {
+    size_t g[GB];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      eb[3 * p + a] = lv[a];
-      eb[3 * NP + 3 * p + a] = um[a];
-      dot += lv[a] * ((__ldg(u_hi + 3 * g + a) - um[a]) - (um[a] - __ldg(u_lo + 3 * g + a)));
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      const int le = idx / NP;
+      g[r] = idx < ne * NP
+                 ? __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + (idx - le * NP))) & ~kFirstTouchBit
+                 : 0;
     }
-    eb[6 * NP + p] = dot;
+    float4 l4[GB];
+    float um[GB][3], uh[GB][3], ul[GB][3];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      l4[r] = __ldg(reinterpret_cast<const float4*>(lam) + g[r]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        um[r][a] = __ldg(u_mid + 3 * g[r] + a);
+        uh[r][a] = __ldg(u_hi + 3 * g[r] + a);
+        ul[r][a] = __ldg(u_lo + 3 * g[r] + a);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      if (idx >= ne * NP) continue;
+      const int le = idx / NP;
+      const int p = idx - le * NP;
+      float* eb = ts + le * ES;
+      const float lv[3] = {l4[r].x, l4[r].y, l4[r].z};
+      float dot = 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        eb[3 * p + a] = lv[a];
+        eb[3 * NP + 3 * p + a] = um[r][a];
+        dot += lv[a] * ((uh[r][a] - um[r][a]) - (um[r][a] - ul[r][a]));
+      }
+      eb[6 * NP + p] = dot;
+    }
   }
   team_sync<WT>();
   const int le = tl / NL;
