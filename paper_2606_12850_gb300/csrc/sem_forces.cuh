@@ -26,20 +26,25 @@ __constant__ float c_w[SEM_NGLL];
 // Threads work in teams: one warp per team for NGLL <= 5 (a team then only needs
 // __syncwarp, so the warps of a CTA drift freely and hide each other's memory latency),
 // the whole CTA for NGLL >= 6. A team holds E = TEAM / NGLL^2 elements of one colour.
+//  0. (programmatic dependent launch) bulk-prefetch the team's element records into L2,
+//     then wait for the previous grid;
 //  1. gather, one thread per local point: consecutive threads take consecutive points p,
-//     so a warp reads whole xi-rows of the global arrays (instead of one scattered row
-//     per thread);
-//  2. one thread per xi-line (j, k): the xi-derivative and the xi-transposed product stay
-//     in registers; eta and zeta derivatives read the shared element cube; Jacobian map,
-//     Hooke stress and fluxes per point, eta/zeta fluxes to shared memory;
-//  3. eta and zeta transposed products from the shared fluxes; element forces back into
-//     the cube slots;
+//     so a warp reads whole xi-rows of the global arrays; each thread has the loads of
+//     four points in flight before it stores any of them;
+//  2. contractions, one thread per line of NGLL points. From NGLL = 4 up (line owners):
+//     a thread first owns an eta-line and a zeta-line and writes all N eta and zeta
+//     derivatives along them; then, owning a xi-line, it forms the xi derivatives in
+//     registers, the Jacobian map, the Hooke stress and the fluxes, keeps the xi-flux
+//     transposed product in registers and writes the eta/zeta fluxes; then the eta/zeta-line
+//     owners apply the weighted transposed products in place; at NGLL <= 3 each xi-line
+//     thread reads the eta/zeta neighbours of its own points instead;
+//  3. element forces into the (free) u slots;
 //  4. scatter in the gather's order: a store at the node's first touch, a
 //     read-modify-write otherwise (elements of one launch share no node: no atomics,
-//     fixed summation order).
-// Shared memory per element: u (then F), eta fluxes and zeta fluxes as [NP][3] each (the
-// odd per-line stride 3N keeps the per-line accesses conflict-free), ibool as [NP]; with
-// several elements per warp the element stride is padded so that they fall in
+//     fixed summation order), previous values of four points loaded before any store.
+// Shared memory per element: u (then F), eta and zeta derivatives (then fluxes) as [NP][3]
+// each (the odd per-line stride 3N keeps the xi-line accesses conflict-free), ibool as
+// [NP]; with several elements per warp the element stride is padded so that they fall in
 // disjoint banks (offsets chosen by simulating the warp's access patterns).
 // ---------------------------------------------------------------------------------------
 template <int N>
@@ -57,6 +62,11 @@ struct ForceCfg {
   static constexpr int TS = E * ES;                   // floats per team
   static constexpr int SMEM_FLOATS = TEAMS * TS;
   static constexpr int REC = (kRecFields * NP + 3) / 4 * 4;
+  // Line owners for the eta and zeta contractions (each shared value read a fixed number of
+  // times) from NGLL = 4 up; at NGLL = 3 the per-point form is faster (GB300, 128^3 mesh:
+  // 1.18 ms against 1.33 ms per sweep), at 5/7/9 the line owners (0.66/0.86/0.96 ms against
+  // 0.75/0.94/1.15 ms).
+  static constexpr bool LINE_OWNERS = N >= 4;
   // CTAs per SM the register allocation must allow, from a GB300 sweep of force-sweep time
   // against the register cap: 64 registers for NGLL <= 5, 85 for NGLL = 6-7, 128 for
   // NGLL = 8, no cap above (the larger live set of the NGLL = 9-10 contractions wins).
@@ -155,137 +165,299 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
   }
   team_sync<WT>();
 
-  // 2. per xi-line derivatives, stress and fluxes
-  const int le = tl / NL;
-  const int line = tl - le * NL;  // = j + N k
-  const int j = line % N;
-  const int k = line / N;
-  const bool active = le < ne;
-  float* su = ts + (active ? le : 0) * ES;  // u, then F: [NP][3]
-  float* se = su + 3 * NP;                   // eta fluxes [NP][3]
-  float* sz = su + 6 * NP;                   // zeta fluxes [NP][3]
-  const float* __restrict__ r = rec + static_cast<size_t>(ebase + (active ? le : 0)) * REC;
+  if constexpr (C::LINE_OWNERS) {
+    // Thread tl of the team owns one line of NGLL points of element le = tl / NL, indexed by
+    // line = a + N b: the xi-line (j, k) = (a, b) in phases 2b and 4, the eta-line
+    // (i, k) = (a, b) and the zeta-line (i, j) = (a, b) in phases 2a and 3. A line owner reads
+    // its line once and produces all N contractions along it, so every shared value is read
+    // a fixed number of times instead of N times.
+    const int le = tl / NL;
+    const int line = tl - le * NL;
+    const int a = line % N;
+    const int b = line / N;
+    const bool active = le < ne;
+    float* su = ts + (active ? le : 0) * ES;  // u, then F: [NP][3]
+    float* se = su + 3 * NP;                   // eta derivatives, then eta fluxes [NP][3]
+    float* sz = su + 6 * NP;                   // zeta derivatives, then zeta fluxes [NP][3]
+    const float* __restrict__ r = rec + static_cast<size_t>(ebase + (active ? le : 0)) * REC;
 
-  float ux[N], uy[N], uz[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const int p = i + N * line;
-    ux[i] = su[3 * p];
-    uy[i] = su[3 * p + 1];
-    uz[i] = su[3 * p + 2];
-  }
-  float hj[N], hk[N];
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    hj[l] = H[j * N + l];
-    hk[l] = H[k * N + l];
-  }
-  float fx[N], fy[N], fz[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) fx[i] = fy[i] = fz[i] = 0.f;
-
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
-    float det_x = 0.f, det_y = 0.f, det_z = 0.f;
-    float dze_x = 0.f, dze_y = 0.f, dze_z = 0.f;
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      const float h = H[i * N + l];
-      dxi_x += h * ux[l];
-      dxi_y += h * uy[l];
-      dxi_z += h * uz[l];
-      const int pe = 3 * (i + N * (l + N * k));
-      det_x += hj[l] * su[pe];
-      det_y += hj[l] * su[pe + 1];
-      det_z += hj[l] * su[pe + 2];
-      const int pz = 3 * (i + N * (j + N * l));
-      dze_x += hk[l] * su[pz];
-      dze_y += hk[l] * su[pz + 1];
-      dze_z += hk[l] * su[pz + 2];
-    }
-    const int q = i * NL + line;
-    float G[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) G[a] = active ? __ldg(r + (kG + a) * NP + q) : 0.f;
-    const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
-    const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
-    const float mu = active ? __ldg(r + kMu * NP + q) : 0.f;
-
-    const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
-    const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
-    const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
-    const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
-    const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
-    const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
-    const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
-    const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
-    const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
-
-    const float lam = kappa - (2.f / 3.f) * mu;
-    const float tr = uxx + uyy + uzz;
-    const float sxx = lam * tr + 2.f * mu * uxx;
-    const float syy = lam * tr + 2.f * mu * uyy;
-    const float szz = lam * tr + 2.f * mu * uzz;
-    const float sxy = mu * (uxy + uyx);
-    const float sxz = mu * (uxz + uzx);
-    const float syz = mu * (uyz + uzy);
-
-    const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
-    const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
-    const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
-#pragma unroll
-    for (int ip = 0; ip < N; ++ip) {
-      const float hw = HW[i * N + ip];
-      fx[ip] += hw * txi_x;
-      fy[ip] += hw * txi_y;
-      fz[ip] += hw * txi_z;
-    }
+    // 2a. eta derivatives along the eta-line (i, k) = (a, b), zeta derivatives along the
+    //     zeta-line (i, j) = (a, b)
     if (active) {
-      const int p3 = 3 * (i + N * line);
-      se[p3] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
-      se[p3 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
-      se[p3 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
-      sz[p3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
-      sz[p3 + 1] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
-      sz[p3 + 2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
+      float ve[3][N], vz[3][N];
+  #pragma unroll
+      for (int l = 0; l < N; ++l)
+  #pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          ve[c][l] = su[3 * (a + N * (l + N * b)) + c];
+          vz[c][l] = su[3 * (a + N * (b + N * l)) + c];
+        }
+  #pragma unroll
+      for (int m = 0; m < N; ++m)
+  #pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float de = 0.f, dz = 0.f;
+  #pragma unroll
+          for (int l = 0; l < N; ++l) {
+            de += H[m * N + l] * ve[c][l];
+            dz += H[m * N + l] * vz[c][l];
+          }
+          se[3 * (a + N * (m + N * b)) + c] = de;
+          sz[3 * (a + N * (b + N * m)) + c] = dz;
+        }
     }
-  }
-  team_sync<WT>();
+    team_sync<WT>();
 
-  // 3. eta and zeta transposed products; forces into the (now free) u slots
-  {
-    float hwj[N], hwk[N];
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      hwj[l] = HW[l * N + j];
-      hwk[l] = HW[l * N + k];
-    }
-    const float wj = W[j], wk = W[k];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float ex = 0.f, ey = 0.f, ez = 0.f, zx = 0.f, zy = 0.f, zz = 0.f;
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        const int pe = 3 * (i + N * (l + N * k));
-        ex += hwj[l] * se[pe];
-        ey += hwj[l] * se[pe + 1];
-        ez += hwj[l] * se[pe + 2];
-        const int pz = 3 * (i + N * (j + N * l));
-        zx += hwk[l] * sz[pz];
-        zy += hwk[l] * sz[pz + 1];
-        zz += hwk[l] * sz[pz + 2];
+    // 2b. along the xi-line (j, k) = (a, b): xi derivatives in registers, Jacobian map, Hooke
+    //     stress, fluxes; the xi-flux transposed product stays in registers, the eta and zeta
+    //     fluxes replace the derivatives they were made from
+    float fx[N], fy[N], fz[N];
+    {
+      float ux[N], uy[N], uz[N];
+  #pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int p = i + N * line;
+        ux[i] = su[3 * p];
+        uy[i] = su[3 * p + 1];
+        uz[i] = su[3 * p + 2];
+        fx[i] = fy[i] = fz[i] = 0.f;
       }
-      const float wi = W[i];
-      if (active) {
+  #pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
+  #pragma unroll
+        for (int l = 0; l < N; ++l) {
+          const float h = H[i * N + l];
+          dxi_x += h * ux[l];
+          dxi_y += h * uy[l];
+          dxi_z += h * uz[l];
+        }
+        const int p3 = 3 * (i + N * line);
+        const float det_x = se[p3], det_y = se[p3 + 1], det_z = se[p3 + 2];
+        const float dze_x = sz[p3], dze_y = sz[p3 + 1], dze_z = sz[p3 + 2];
+        const int q = i * NL + line;
+        float G[9];
+  #pragma unroll
+        for (int c = 0; c < 9; ++c) G[c] = active ? __ldg(r + (kG + c) * NP + q) : 0.f;
+        const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
+        const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
+        const float mu = active ? __ldg(r + kMu * NP + q) : 0.f;
+
+        const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
+        const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
+        const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
+        const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
+        const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
+        const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
+        const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
+        const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
+        const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
+
+        const float lam = kappa - (2.f / 3.f) * mu;
+        const float tr = uxx + uyy + uzz;
+        const float sxx = lam * tr + 2.f * mu * uxx;
+        const float syy = lam * tr + 2.f * mu * uyy;
+        const float szz = lam * tr + 2.f * mu * uzz;
+        const float sxy = mu * (uxy + uyx);
+        const float sxz = mu * (uxz + uzx);
+        const float syz = mu * (uyz + uzy);
+
+        const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
+        const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
+        const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
+  #pragma unroll
+        for (int ip = 0; ip < N; ++ip) {
+          const float hw = HW[i * N + ip];
+          fx[ip] += hw * txi_x;
+          fy[ip] += hw * txi_y;
+          fz[ip] += hw * txi_z;
+        }
+        if (active) {
+          se[p3] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
+          se[p3 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
+          se[p3 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
+          sz[p3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
+          sz[p3 + 1] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
+          sz[p3 + 2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
+        }
+      }
+    }
+    team_sync<WT>();
+
+    // 3. eta and zeta transposed products along the eta- and zeta-lines, in place
+    if (active) {
+      float ve[3][N], vz[3][N];
+  #pragma unroll
+      for (int l = 0; l < N; ++l)
+  #pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          ve[c][l] = se[3 * (a + N * (l + N * b)) + c];
+          vz[c][l] = sz[3 * (a + N * (b + N * l)) + c];
+        }
+  #pragma unroll
+      for (int m = 0; m < N; ++m)
+  #pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float te = 0.f, tz = 0.f;
+  #pragma unroll
+          for (int l = 0; l < N; ++l) {
+            te += HW[l * N + m] * ve[c][l];
+            tz += HW[l * N + m] * vz[c][l];
+          }
+          se[3 * (a + N * (m + N * b)) + c] = te;
+          sz[3 * (a + N * (b + N * m)) + c] = tz;
+        }
+    }
+    team_sync<WT>();
+
+    // 3b. element forces along the xi-line (j, k) = (a, b) into the (now free) u slots
+    if (active) {
+      const float wj = W[a], wk = W[b];
+  #pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const float wi = W[i];
         const int p = 3 * (i + N * line);
-        su[p] = -(wj * wk * fx[i] + wi * wk * ex + wi * wj * zx);
-        su[p + 1] = -(wj * wk * fy[i] + wi * wk * ey + wi * wj * zy);
-        su[p + 2] = -(wj * wk * fz[i] + wi * wk * ez + wi * wj * zz);
+        su[p] = -(wj * wk * fx[i] + wi * wk * se[p] + wi * wj * sz[p]);
+        su[p + 1] = -(wj * wk * fy[i] + wi * wk * se[p + 1] + wi * wj * sz[p + 1]);
+        su[p + 2] = -(wj * wk * fz[i] + wi * wk * se[p + 2] + wi * wj * sz[p + 2]);
       }
     }
+    team_sync<WT>();
+
+  } else {
+    // 2. per xi-line derivatives, stress and fluxes
+    const int le = tl / NL;
+    const int line = tl - le * NL;  // = j + N k
+    const int j = line % N;
+    const int k = line / N;
+    const bool active = le < ne;
+    float* su = ts + (active ? le : 0) * ES;  // u, then F: [NP][3]
+    float* se = su + 3 * NP;                   // eta fluxes [NP][3]
+    float* sz = su + 6 * NP;                   // zeta fluxes [NP][3]
+    const float* __restrict__ r = rec + static_cast<size_t>(ebase + (active ? le : 0)) * REC;
+
+    float ux[N], uy[N], uz[N];
+  #pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int p = i + N * line;
+      ux[i] = su[3 * p];
+      uy[i] = su[3 * p + 1];
+      uz[i] = su[3 * p + 2];
+    }
+    float hj[N], hk[N];
+  #pragma unroll
+    for (int l = 0; l < N; ++l) {
+      hj[l] = H[j * N + l];
+      hk[l] = H[k * N + l];
+    }
+    float fx[N], fy[N], fz[N];
+  #pragma unroll
+    for (int i = 0; i < N; ++i) fx[i] = fy[i] = fz[i] = 0.f;
+
+  #pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
+      float det_x = 0.f, det_y = 0.f, det_z = 0.f;
+      float dze_x = 0.f, dze_y = 0.f, dze_z = 0.f;
+  #pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const float h = H[i * N + l];
+        dxi_x += h * ux[l];
+        dxi_y += h * uy[l];
+        dxi_z += h * uz[l];
+        const int pe = 3 * (i + N * (l + N * k));
+        det_x += hj[l] * su[pe];
+        det_y += hj[l] * su[pe + 1];
+        det_z += hj[l] * su[pe + 2];
+        const int pz = 3 * (i + N * (j + N * l));
+        dze_x += hk[l] * su[pz];
+        dze_y += hk[l] * su[pz + 1];
+        dze_z += hk[l] * su[pz + 2];
+      }
+      const int q = i * NL + line;
+      float G[9];
+  #pragma unroll
+      for (int a = 0; a < 9; ++a) G[a] = active ? __ldg(r + (kG + a) * NP + q) : 0.f;
+      const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
+      const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
+      const float mu = active ? __ldg(r + kMu * NP + q) : 0.f;
+
+      const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
+      const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
+      const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
+      const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
+      const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
+      const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
+      const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
+      const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
+      const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
+
+      const float lam = kappa - (2.f / 3.f) * mu;
+      const float tr = uxx + uyy + uzz;
+      const float sxx = lam * tr + 2.f * mu * uxx;
+      const float syy = lam * tr + 2.f * mu * uyy;
+      const float szz = lam * tr + 2.f * mu * uzz;
+      const float sxy = mu * (uxy + uyx);
+      const float sxz = mu * (uxz + uzx);
+      const float syz = mu * (uyz + uzy);
+
+      const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
+      const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
+      const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
+  #pragma unroll
+      for (int ip = 0; ip < N; ++ip) {
+        const float hw = HW[i * N + ip];
+        fx[ip] += hw * txi_x;
+        fy[ip] += hw * txi_y;
+        fz[ip] += hw * txi_z;
+      }
+      if (active) {
+        const int p3 = 3 * (i + N * line);
+        se[p3] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
+        se[p3 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
+        se[p3 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
+        sz[p3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
+        sz[p3 + 1] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
+        sz[p3 + 2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
+      }
+    }
+    team_sync<WT>();
+
+    // 3. eta and zeta transposed products; forces into the (now free) u slots
+    {
+      float hwj[N], hwk[N];
+  #pragma unroll
+      for (int l = 0; l < N; ++l) {
+        hwj[l] = HW[l * N + j];
+        hwk[l] = HW[l * N + k];
+      }
+      const float wj = W[j], wk = W[k];
+  #pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float ex = 0.f, ey = 0.f, ez = 0.f, zx = 0.f, zy = 0.f, zz = 0.f;
+  #pragma unroll
+        for (int l = 0; l < N; ++l) {
+          const int pe = 3 * (i + N * (l + N * k));
+          ex += hwj[l] * se[pe];
+          ey += hwj[l] * se[pe + 1];
+          ez += hwj[l] * se[pe + 2];
+          const int pz = 3 * (i + N * (j + N * l));
+          zx += hwk[l] * sz[pz];
+          zy += hwk[l] * sz[pz + 1];
+          zz += hwk[l] * sz[pz + 2];
+        }
+        const float wi = W[i];
+        if (active) {
+          const int p = 3 * (i + N * line);
+          su[p] = -(wj * wk * fx[i] + wi * wk * ex + wi * wj * zx);
+          su[p + 1] = -(wj * wk * fy[i] + wi * wk * ey + wi * wj * zy);
+          su[p + 2] = -(wj * wk * fz[i] + wi * wk * ez + wi * wj * zz);
+        }
+      }
+    }
+    team_sync<WT>();
+
   }
-  team_sync<WT>();
 
   // 4. scatter in the gather's coalesced order; for the padded layout the previous values
   //    of a group of GB nodes are loaded before any of them is written back
