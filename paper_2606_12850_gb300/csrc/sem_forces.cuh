@@ -97,10 +97,14 @@ __device__ __forceinline__ void team_sync() {
 }
 
 // VS: floats per node in u and f (4 for the context's own padded fields, 3 for caller arrays).
-template <int N, int VS>
+// With S shots (VS = 4 only) the fields are [nglob][S][4] and the launch works on the items
+// (element, shot) of elements e0 .. e1-1, element-major: the teams of a CTA take the shots
+// of one element, so its record is read from DRAM once for all of them.
+template <int N, int VS, bool MS>
 __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     forces_kernel(const float* __restrict__ rec, const float* __restrict__ u, float* __restrict__ f, int e0,
-                  int e1) {
+                  int e1, int S_arg) {
+  const int S = MS ? S_arg : 1;  // shots (a compile-time 1 for the single-shot kernel)
   using C = ForceCfg<N>;
   constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
   constexpr bool WT = C::WARP_TEAM;
@@ -111,13 +115,16 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
 
   const int team = threadIdx.x / TEAM;
   const int tl = threadIdx.x - team * TEAM;
-  const int ebase = e0 + (blockIdx.x * C::TEAMS + team) * E;
-  const int ne = min(E, e1 - ebase);
-  if (WT && ne <= 0) return;  // a warp team without elements (never a CTA team)
+  const int ibase = (blockIdx.x * C::TEAMS + team) * E;  // first item of the team
+  const int ne = min(E, (e1 - e0) * S - ibase);
+  if (WT && ne <= 0) return;  // a warp team without items (never a CTA team)
   float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
+  // element and shot of the team's slot le
+  auto elem_of = [&](int le) { return e0 + (MS ? (ibase + le) / S : ibase + le); };
+  auto shot_of = [&](int le) { return MS ? (ibase + le) % S : 0; };
 
   // 0. records to L2 while the previous grid finishes, then wait for its results
-  if (tl < ne) prefetch_l2(rec + static_cast<size_t>(ebase + tl) * REC, REC * sizeof(float));
+  if (tl < ne) prefetch_l2(rec + static_cast<size_t>(elem_of(tl)) * REC, REC * sizeof(float));
   wait_prerequisite_grid();
   allow_dependent_grid();
 
@@ -130,7 +137,8 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     for (int r = 0; r < GB; ++r) {
       const int idx = base + r * TEAM;
       const int le = idx / NP;
-      w[r] = idx < ne * NP ? __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + (idx - le * NP))) : 0u;
+      w[r] = idx < ne * NP ? __float_as_uint(__ldg(rec + static_cast<size_t>(elem_of(le)) * REC + (idx - le * NP)))
+                           : 0u;
     }
     float q[GB][3];
 #pragma unroll
@@ -138,7 +146,8 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       const size_t g = w[r] & ~kFirstTouchBit;
       if (base + r * TEAM < ne * NP) {
         if (VS == 4) {
-          const float4 v = __ldg(reinterpret_cast<const float4*>(u) + g);
+          const int le = (base + r * TEAM) / NP;
+          const float4 v = __ldg(reinterpret_cast<const float4*>(u) + g * S + shot_of(le));
           q[r][0] = v.x;
           q[r][1] = v.y;
           q[r][2] = v.z;
@@ -179,7 +188,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     float* su = ts + (active ? le : 0) * ES;  // u, then F: [NP][3]
     float* se = su + 3 * NP;                   // eta derivatives, then eta fluxes [NP][3]
     float* sz = su + 6 * NP;                   // zeta derivatives, then zeta fluxes [NP][3]
-    const float* __restrict__ r = rec + static_cast<size_t>(ebase + (active ? le : 0)) * REC;
+    const float* __restrict__ r = rec + static_cast<size_t>(elem_of(active ? le : 0)) * REC;
 
     // 2a. eta derivatives along the eta-line (i, k) = (a, b), zeta derivatives along the
     //     zeta-line (i, j) = (a, b)
@@ -334,7 +343,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     float* su = ts + (active ? le : 0) * ES;  // u, then F: [NP][3]
     float* se = su + 3 * NP;                   // eta fluxes [NP][3]
     float* sz = su + 6 * NP;                   // zeta fluxes [NP][3]
-    const float* __restrict__ r = rec + static_cast<size_t>(ebase + (active ? le : 0)) * REC;
+    const float* __restrict__ r = rec + static_cast<size_t>(elem_of(active ? le : 0)) * REC;
 
     float ux[N], uy[N], uz[N];
   #pragma unroll
@@ -473,7 +482,8 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         if (idx < ne * NP) {
           const int e = idx / NP;
           w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
-          if (!(w[r] & kFirstTouchBit)) prev[r] = reinterpret_cast<const float4*>(f)[w[r] & ~kFirstTouchBit];
+          if (!(w[r] & kFirstTouchBit))
+            prev[r] = reinterpret_cast<const float4*>(f)[static_cast<size_t>(w[r] & ~kFirstTouchBit) * S + shot_of(e)];
         }
       }
 #pragma unroll
@@ -482,7 +492,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         if (idx < ne * NP) {
           const int e = idx / NP;
           const float* src = ts + e * ES + 3 * (idx - e * NP);
-          reinterpret_cast<float4*>(f)[w[r] & ~kFirstTouchBit] =
+          reinterpret_cast<float4*>(f)[static_cast<size_t>(w[r] & ~kFirstTouchBit) * S + shot_of(e)] =
               make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
         }
       }
@@ -505,232 +515,6 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       f[3 * g + 1] += src[1];
       f[3 * g + 2] += src[2];
     }
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// Batched force kernel: S shots on one mesh (same model, different sources), wavefields
-// [nglob][S][4] with the shot index innermost. One CTA per element: the element record is
-// staged in shared memory once and serves every shot, so the 52 bytes per local point of
-// geometry and moduli are read once per S shot-points instead of once per shot-point. The
-// CTA works on SB shots at a time, one team of NGLL^2 xi-line threads per shot, with the
-// same per-team arithmetic as forces_kernel; gather and scatter walk (point, shot) slots
-// with the shot fastest, so a warp moves whole 16-byte nodes of consecutive shots.
-// ---------------------------------------------------------------------------------------
-template <int N>
-struct BatchCfg {
-  static constexpr int NP = N * N * N;
-  static constexpr int NL = N * N;
-  static constexpr int SB = NL <= 32 ? 8 : (N <= 7 ? 4 : 2);  // shots in flight per CTA
-  static constexpr int T = SB * NL;
-  static constexpr int REC = (kRecFields * NP + 3) / 4 * 4;
-  static constexpr int CS = ForceCfg<N>::ES;  // per-shot cube stride (bank-padded)
-  static constexpr int SMEM_FLOATS = REC + SB * CS;
-  // CTAs per SM the register allocation must allow: 4 at NGLL <= 5 (from a GB300 sweep of
-  // 3/4/5 on 32 shots of the 48^3 mesh: 16.2/15.9/19.0 ms per step, 17.6 ms uncapped)
-#ifdef SEM_BATCH_MIN_BLOCKS
-  static constexpr int MIN_BLOCKS = SEM_BATCH_MIN_BLOCKS;
-#else
-  static constexpr int MIN_BLOCKS = NL <= 32 ? 4 : 1;
-#endif
-};
-
-template <int N>
-__global__ void __launch_bounds__(BatchCfg<N>::T, BatchCfg<N>::MIN_BLOCKS)
-    forces_batched_kernel(const float* __restrict__ rec, const float* __restrict__ u, float* __restrict__ f,
-                          int e0, int shots) {
-  using C = BatchCfg<N>;
-  constexpr int NP = C::NP, NL = C::NL, SB = C::SB, T = C::T, CS = C::CS, REC = C::REC;
-  extern __shared__ float4 smem4[];
-  const float* __restrict__ H = c_h;
-  const float* __restrict__ HW = c_hw;
-  const float* __restrict__ W = c_w;
-  float* sr = reinterpret_cast<float*>(smem4);  // the element record
-  float* cubes = sr + REC;                       // [SB][CS]
-  const uint32_t* sib = reinterpret_cast<const uint32_t*>(sr);  // ibool field, p order
-  const int t = threadIdx.x;
-  const int e = e0 + blockIdx.x;
-
-  const float4* r4 = reinterpret_cast<const float4*>(rec + static_cast<size_t>(e) * REC);
-  for (int q = t; q < REC / 4; q += T) smem4[q] = __ldg(r4 + q);
-  wait_prerequisite_grid();  // the record is constant; the wavefields come from the previous grid
-  allow_dependent_grid();
-  __syncthreads();
-
-  const int team = t / NL;
-  const int line = t - team * NL;
-  const int j = line % N;
-  const int k = line / N;
-  float hj[N], hk[N], hwj[N], hwk[N];
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    hj[l] = H[j * N + l];
-    hk[l] = H[k * N + l];
-    hwj[l] = HW[l * N + j];
-    hwk[l] = HW[l * N + k];
-  }
-  const float wj = W[j], wk = W[k];
-  const float4* u4 = reinterpret_cast<const float4*>(u);
-  float4* f4 = reinterpret_cast<float4*>(f);
-
-  constexpr int GB = 4;  // (point, shot) slots per thread whose loads are in flight together
-  for (int s0 = 0; s0 < shots; s0 += SB) {
-    const int ns = min(SB, shots - s0);
-    for (int base = t; base < NP * ns; base += GB * T) {
-      float4 q4[GB];
-#pragma unroll
-      for (int r = 0; r < GB; ++r) {
-        const int idx = base + r * T;
-        if (idx < NP * ns) {
-          const int p = idx / ns;
-          q4[r] = __ldg(u4 + (sib[p] & ~kFirstTouchBit) * shots + s0 + (idx - p * ns));
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < GB; ++r) {
-        const int idx = base + r * T;
-        if (idx < NP * ns) {
-          const int p = idx / ns;
-          float* cb = cubes + (idx - p * ns) * CS + 3 * p;
-          cb[0] = q4[r].x;
-          cb[1] = q4[r].y;
-          cb[2] = q4[r].z;
-        }
-      }
-    }
-    __syncthreads();
-
-    const bool active = team < ns;
-    float* su = cubes + (active ? team : 0) * CS;
-    float* se = su + 3 * NP;
-    float* sz = su + 6 * NP;
-    float ux[N], uy[N], uz[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int p = i + N * line;
-      ux[i] = su[3 * p];
-      uy[i] = su[3 * p + 1];
-      uz[i] = su[3 * p + 2];
-    }
-    float fx[N], fy[N], fz[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) fx[i] = fy[i] = fz[i] = 0.f;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
-      float det_x = 0.f, det_y = 0.f, det_z = 0.f;
-      float dze_x = 0.f, dze_y = 0.f, dze_z = 0.f;
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        const float h = H[i * N + l];
-        dxi_x += h * ux[l];
-        dxi_y += h * uy[l];
-        dxi_z += h * uz[l];
-        const int pe = 3 * (i + N * (l + N * k));
-        det_x += hj[l] * su[pe];
-        det_y += hj[l] * su[pe + 1];
-        det_z += hj[l] * su[pe + 2];
-        const int pz = 3 * (i + N * (j + N * l));
-        dze_x += hk[l] * su[pz];
-        dze_y += hk[l] * su[pz + 1];
-        dze_z += hk[l] * su[pz + 2];
-      }
-      const int q = i * NL + line;
-      float G[9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) G[a] = sr[(kG + a) * NP + q];
-      const float jac = sr[kJac * NP + q];
-      const float kappa = sr[kKappa * NP + q];
-      const float mu = sr[kMu * NP + q];
-
-      const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
-      const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
-      const float uxz = dxi_x * G[2] + det_x * G[5] + dze_x * G[8];
-      const float uyx = dxi_y * G[0] + det_y * G[3] + dze_y * G[6];
-      const float uyy = dxi_y * G[1] + det_y * G[4] + dze_y * G[7];
-      const float uyz = dxi_y * G[2] + det_y * G[5] + dze_y * G[8];
-      const float uzx = dxi_z * G[0] + det_z * G[3] + dze_z * G[6];
-      const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
-      const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
-
-      const float lam = kappa - (2.f / 3.f) * mu;
-      const float tr = uxx + uyy + uzz;
-      const float sxx = lam * tr + 2.f * mu * uxx;
-      const float syy = lam * tr + 2.f * mu * uyy;
-      const float szz = lam * tr + 2.f * mu * uzz;
-      const float sxy = mu * (uxy + uyx);
-      const float sxz = mu * (uxz + uzx);
-      const float syz = mu * (uyz + uzy);
-
-      const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
-      const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
-      const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
-#pragma unroll
-      for (int ip = 0; ip < N; ++ip) {
-        const float hw = HW[i * N + ip];
-        fx[ip] += hw * txi_x;
-        fy[ip] += hw * txi_y;
-        fz[ip] += hw * txi_z;
-      }
-      if (active) {
-        const int p3 = 3 * (i + N * line);
-        se[p3] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
-        se[p3 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
-        se[p3 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
-        sz[p3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
-        sz[p3 + 1] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
-        sz[p3 + 2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float ex = 0.f, ey = 0.f, ez = 0.f, zx = 0.f, zy = 0.f, zz = 0.f;
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        const int pe = 3 * (i + N * (l + N * k));
-        ex += hwj[l] * se[pe];
-        ey += hwj[l] * se[pe + 1];
-        ez += hwj[l] * se[pe + 2];
-        const int pz = 3 * (i + N * (j + N * l));
-        zx += hwk[l] * sz[pz];
-        zy += hwk[l] * sz[pz + 1];
-        zz += hwk[l] * sz[pz + 2];
-      }
-      const float wi = W[i];
-      if (active) {
-        const int p = 3 * (i + N * line);
-        su[p] = -(wj * wk * fx[i] + wi * wk * ex + wi * wj * zx);
-        su[p + 1] = -(wj * wk * fy[i] + wi * wk * ey + wi * wj * zy);
-        su[p + 2] = -(wj * wk * fz[i] + wi * wk * ez + wi * wj * zz);
-      }
-    }
-    __syncthreads();
-    for (int base = t; base < NP * ns; base += GB * T) {
-      float4 prev[GB];
-#pragma unroll
-      for (int r = 0; r < GB; ++r) {
-        const int idx = base + r * T;
-        prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < NP * ns) {
-          const int p = idx / ns;
-          const uint32_t w = sib[p];
-          if (!(w & kFirstTouchBit)) prev[r] = f4[(w & ~kFirstTouchBit) * shots + s0 + (idx - p * ns)];
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < GB; ++r) {
-        const int idx = base + r * T;
-        if (idx < NP * ns) {
-          const int p = idx / ns;
-          const int sh = idx - p * ns;
-          const float* src = cubes + sh * CS + 3 * p;
-          f4[(sib[p] & ~kFirstTouchBit) * shots + s0 + sh] =
-              make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
-        }
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -865,7 +649,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
   }
 }
 
-template <int VS>
+template <int VS, bool MS>
 int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   using C = ForceCfg<SEM_NGLL>;
   static unsigned long long attr_done = 0;  // one bit per device ordinal
@@ -875,12 +659,13 @@ int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_done & bit)) {
     cudaError_t e =
-        cudaFuncSetAttribute(forces_kernel<SEM_NGLL, VS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(forces_kernel<SEM_NGLL, VS, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return static_cast<int>(e);
     attr_done |= bit;
   }
+  const int S = MS ? L.shots : 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((L.e1 - L.e0 + C::EPC - 1) / C::EPC);
+  cfg.gridDim = dim3(((L.e1 - L.e0) * S + C::EPC - 1) / C::EPC);
   cfg.blockDim = dim3(C::T);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -889,40 +674,14 @@ int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_kernel<SEM_NGLL, VS>, L.rec, L.u, L.f, L.e0, L.e1));
-}
-
-int launch_forces_batched(const ForceLaunch& L, cudaStream_t s) {
-  using C = BatchCfg<SEM_NGLL>;
-  static unsigned long long attr_done = 0;
-  const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (!(attr_done & bit)) {
-    cudaError_t e =
-        cudaFuncSetAttribute(forces_batched_kernel<SEM_NGLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return static_cast<int>(e);
-    attr_done |= bit;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(L.e1 - L.e0);
-  cfg.blockDim = dim3(C::T);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_batched_kernel<SEM_NGLL>, L.rec, L.u, L.f, L.e0, L.shots));
+  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_kernel<SEM_NGLL, VS, MS>, L.rec, L.u, L.f, L.e0, L.e1, S));
 }
 
 int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
   if (L.e1 <= L.e0) return 0;
-  if (L.shots > 1) return L.node_stride == 4 ? launch_forces_batched(L, s) : static_cast<int>(cudaErrorInvalidValue);
-  if (L.node_stride == 4) return launch_forces_vs<4>(L, s);
-  if (L.node_stride == 3) return launch_forces_vs<3>(L, s);
+  if (L.shots > 1) return L.node_stride == 4 ? launch_forces_vs<4, true>(L, s) : static_cast<int>(cudaErrorInvalidValue);
+  if (L.node_stride == 4) return launch_forces_vs<4, false>(L, s);
+  if (L.node_stride == 3) return launch_forces_vs<3, false>(L, s);
   return static_cast<int>(cudaErrorInvalidValue);
 }
 
