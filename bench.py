@@ -53,6 +53,7 @@ def parse_args():
     p.add_argument("--no-sweep", action="store_true", help="skip the NGLL 3/5/7/9 (h,p) sweep")
     p.add_argument("--adjoint-steps", type=int, default=800, help="misfit-gradient measurement (0 = skip)")
     p.add_argument("--surrogate-runs", type=int, default=4096, help="surrogate training runs (0 = skip)")
+    p.add_argument("--models", type=int, default=16, help="uneven-models group measurement (0 = skip)")
     p.add_argument("--surrogate-epochs", type=int, default=100)
     return p.parse_args()
 
@@ -414,6 +415,54 @@ def measure_adjoint(device: int, nsteps: int = 800, every: int = 50):
                       "after one untimed gradient"}
 
 
+def measure_models(device: int, count: int = 16, steps: int = 50):
+    """Many independent models on one GPU: homogeneous cubes of 8^3 .. 40^3 elements with
+    NGLL cycling through 4 .. 8, each autotuned (contraction form), stepped one after
+    another (each with its own CUDA graphs) against all together (sem_group_step: one graph
+    launch per ten steps, every model a branch of its own)."""
+    import torch
+
+    from paper_2606_12850_gb300 import inputs, sem
+
+    sizes = np.linspace(8, 40, count).round().astype(int)
+    orders = [4 + k % 5 for k in range(count)]
+    stream = torch.cuda.Stream(device=device)
+    setups, desc, tuned = [], [], []
+    for n, ngll in zip(sizes, orders):
+        w = inputs.homogeneous_cube(int(n), ngll, nsteps=steps)
+        s = sem.setup_workload(w, device=device, stream=stream)
+        ms, choice = sem.sem_autotune(s.ctx, reps=3)
+        setups.append(s)
+        desc.append(f"{n}^3/{ngll}")
+        tuned.append({"model": f"{n}^3 NGLL {ngll}", "line_owners_ms": ms[0], "per_point_ms": ms[1],
+                      "form": "line owners" if choice == 1 else "per point"})
+    nloc = sum(int(s.ctx.nspec) * int(s.ctx.ngll) ** 3 for s in setups)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for s in setups:  # warm-up (graphs)
+        sem.sem_run_dev(s.ctx, 12, None)
+    stream.synchronize()
+    a, b = ev(), ev()
+    a.record(stream)
+    for s in setups:
+        sem.sem_run_dev(s.ctx, steps, None)
+    b.record(stream)
+    b.synchronize()
+    seq_ms = a.elapsed_time(b)
+    group = sem.Group([s.ctx for s in setups])
+    group.step(12)
+    group.sync()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    group.step(steps)
+    group.sync()
+    group_ms = 1e3 * (time.perf_counter() - t)
+    return {"models": desc, "steps": steps, "nlocal_total": nloc, "sequential_ms": seq_ms, "group_ms": group_ms,
+            "speedup": seq_ms / group_ms, "group_updates_per_s": nloc * steps / (group_ms * 1e-3),
+            "sequential_updates_per_s": nloc * steps / (seq_ms * 1e-3), "autotune": tuned,
+            "timing": "sequential: CUDA events on the models' stream; group: wall clock around "
+                      "sem_group_step and sem_group_sync"}
+
+
 def measure_surrogate(device: int, runs: int, epochs: int, heldout: int = 256, batch: int = 256):
     """The learned surrogate of the 16^3 layered medium (NGLL 5, 64 surface receivers, 1000
     steps, Ricker 0.5 Hz): ``runs`` solver runs with seeded random positions and unit moment
@@ -580,6 +629,10 @@ def run_ours(args):
     if args.adjoint_steps > 0:
         adj = measure_adjoint(local, args.adjoint_steps)
 
+    models = None
+    if args.models > 0:
+        models = measure_models(local, args.models)
+
     sur = None
     if args.surrogate_runs > 0:
         sur = measure_surrogate(local, args.surrogate_runs, args.surrogate_epochs)
@@ -609,7 +662,8 @@ def run_ours(args):
                                   "bytes_per_step": alg["step"]},
             "global_pt_updates_per_s": world * mesh.nglob * K / (ms / 1e3),
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clock_info,
-            "batched_shots": batched, "hp_sweep": sweep, "adjoint": adj, "surrogate": sur,
+            "batched_shots": batched, "uneven_models": models, "hp_sweep": sweep, "adjoint": adj,
+            "surrogate": sur,
             "kernel_sources": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)

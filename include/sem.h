@@ -77,14 +77,18 @@ int sem_create(sem_ctx** out, int ngll, int device, void* cuda_stream);
 /* Free every device and host resource of the context. NULL is allowed. */
 int sem_destroy(sem_ctx* ctx);
 
-/* Tunables, applied by the next sem_set_mesh.
- *   SEM_OPT_SWEEP_SLABS: the force sweep visits the elements slab by slab (equal-count
- *   slabs along the longest axis of the element centroids) and colour by colour inside a
- *   slab, so that a slab's nodes can stay in L2 across its colour launches; value = slab
- *   count, 0 or 1 = colour by colour over the whole mesh (the default). Results change only
- *   by the summation order at nodes. SEM_EINVAL for an unknown option or a value out of
- *   range. */
+/* Tunables.
+ *   SEM_OPT_SWEEP_SLABS (applied by the next sem_set_mesh): the force sweep visits the
+ *   elements slab by slab (equal-count slabs along the longest axis of the element
+ *   centroids) and colour by colour inside a slab, so that a slab's nodes can stay in L2
+ *   across its colour launches; value = slab count, 0 or 1 = colour by colour over the
+ *   whole mesh (the default). Results change only by the summation order at nodes.
+ * SEM_EINVAL for an unknown option or a value out of range. */
 #define SEM_OPT_SWEEP_SLABS 1
+/*   SEM_OPT_CONTRACTION (takes effect at once): the force kernel's eta/zeta contraction
+ *   form, 0 = the order's default (line owners from NGLL 4 up, per point below), 1 = line
+ *   owners, 2 = per point; sem_autotune sets it from measurement. */
+#define SEM_OPT_CONTRACTION 2
 int sem_set_option(sem_ctx* ctx, int option, long long value);
 
 /* Set the mesh (Sec. II-B hexahedral mesh, Sec. IV-C global-to-local map).
@@ -230,6 +234,28 @@ int sem_adjoint_gradients(sem_ctx* ctx, double* g_rho, double* g_kappa, double* 
  * [count][nrec][3] with G_dev[j-1] = G^{n0+j+1} (device; NULL = zero); u_dev: float32
  * [count+2][nglob][3] = u^{n0} .. u^{n0+count+1} (device). Asynchronous on the stream. */
 int sem_adjoint_segment(sem_ctx* ctx, int count, const float* G_dev, const float* u_dev);
+
+/* Autotuner of the force kernel's contraction form on this context's mesh (NGLL, element
+ * shapes, shots): times `reps` stiffness sweeps (CUDA events, after one warm-up) with the
+ * eta/zeta contractions done by line owners (form 1) and per point (form 2), keeps the
+ * faster for every later step, and returns ms_out[0..1] (per sweep; may be NULL) and the
+ * chosen form in *choice_out (may be NULL). Reads u, writes scratch only (completes a
+ * pending state first). Synchronous. Requires mesh, material and dt. */
+int sem_autotune(sem_ctx* ctx, int reps, double* ms_out, int* choice_out);
+
+/* Groups: several contexts on one GPU (different meshes, orders, shot counts) stepped
+ * together. sem_group_step advances every context nsteps steps (no seismograms): one eager
+ * step per context, then CUDA graphs in which every context's steps form a branch of their
+ * own, so that small models run side by side instead of one after another; each context's
+ * results equal those of sem_step on it alone, bit for bit. The contexts stay owned by the
+ * caller, must outlive the group, and may be changed between calls (the graphs are rebuilt).
+ * Asynchronous: every context's later calls are ordered after the group's work. */
+typedef struct sem_group sem_group;
+int sem_group_create(sem_group** out, int nctx, sem_ctx* const* ctxs);
+int sem_group_destroy(sem_group* group);
+int sem_group_step(sem_group* group, int nsteps);
+int sem_group_sync(sem_group* group);
+const char* sem_group_last_error(const sem_group* group);
 
 /* Kinetic and potential energy of the current state in float64:
  * out[0] = 1/2 sum_I M_I |v_I|^2, out[1] = 1/2 u^T K u. Synchronous. */

@@ -73,6 +73,8 @@ struct sem_ctx {
   long long steps = 0;
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
+  unsigned long long generation = 0;  // bumped whenever launches captured in graphs go stale
+  int variant = 0;                    // force-kernel contraction form (sem_autotune)
 };
 
 namespace {
@@ -141,6 +143,7 @@ void drop_graph(sem_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
   c->graph_valid = false;
+  ++c->generation;
 }
 
 DevProblem problem(const sem_ctx* c) {
@@ -183,6 +186,7 @@ int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int
   L.f = f;
   L.node_stride = node_stride;
   L.shots = shots;
+  L.variant = c->variant;
   for (size_t k = 0; k + 1 < c->sweep_off.size(); ++k) {
     L.e0 = c->sweep_off[k];
     L.e1 = c->sweep_off[k + 1];
@@ -374,6 +378,11 @@ int sem_set_option(sem_ctx* c, int option, long long value) {
     case SEM_OPT_SWEEP_SLABS:
       if (value < 0 || value > (1 << 20)) return fail(c, SEM_EINVAL, "slab count out of range");
       c->slabs_opt = static_cast<int>(value);
+      return SEM_OK;
+    case SEM_OPT_CONTRACTION:
+      if (value < 0 || value > 2) return fail(c, SEM_EINVAL, "contraction form must be 0, 1 or 2");
+      c->variant = static_cast<int>(value);
+      drop_graph(c);
       return SEM_OK;
     default:
       return fail(c, SEM_EINVAL, "unknown option " + std::to_string(option));
@@ -1140,6 +1149,216 @@ int sem_adjoint_gradients(sem_ctx* c, double* g_rho, double* g_kappa, double* g_
   }
   return SEM_OK;
 }
+
+int sem_autotune(sem_ctx* c, int reps, double* ms_out, int* choice_out) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (reps < 1) return fail(c, SEM_EINVAL, "sem_autotune: reps must be >= 1");
+  if ((r = set_device(c))) return r;
+  if ((r = finish_state(c))) return r;  // the timing sweeps read u and write scratch only
+  const size_t nf = kNodeStride * static_cast<size_t>(c->nglob) * c->shots;
+  float* f = nullptr;
+  SEM_CUDA(c, cudaMallocAsync(reinterpret_cast<void**>(&f), nf * sizeof(float), c->stream));
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double ms[2] = {0.0, 0.0};
+  const int keep = c->variant;
+  int rc = SEM_OK;
+  for (int k = 0; k < 2 && rc == SEM_OK; ++k) if (cudaEventCreate(&ev[k]) != cudaSuccess) rc = fail(c, SEM_ECUDA, "cudaEventCreate");
+  for (int v = 1; v <= 2 && rc == SEM_OK; ++v) {  // 1 line owners, 2 per point
+    c->variant = v;
+    rc = forces_all_colors(c, c->d_u, f, kNodeStride, c->shots);  // warm-up
+    if (rc == SEM_OK && cudaEventRecord(ev[0], c->stream) != cudaSuccess) rc = fail(c, SEM_ECUDA, "cudaEventRecord");
+    for (int i = 0; i < reps && rc == SEM_OK; ++i) rc = forces_all_colors(c, c->d_u, f, kNodeStride, c->shots);
+    float t = 0.f;
+    if (rc == SEM_OK && (cudaEventRecord(ev[1], c->stream) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                         cudaEventElapsedTime(&t, ev[0], ev[1]) != cudaSuccess))
+      rc = fail(c, SEM_ECUDA, "sem_autotune timing");
+    ms[v - 1] = static_cast<double>(t) / reps;
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  cudaFreeAsync(f, c->stream);
+  if (rc != SEM_OK) {
+    c->variant = keep;
+    return rc;
+  }
+  c->variant = ms[0] <= ms[1] ? 1 : 2;
+  drop_graph(c);
+  if (ms_out) {
+    ms_out[0] = ms[0];
+    ms_out[1] = ms[1];
+  }
+  if (choice_out) *choice_out = c->variant;
+  return SEM_OK;
+}
+
+}  // extern "C"
+
+// ---- groups of contexts stepped together ------------------------------------------------
+struct sem_group {
+  std::vector<sem_ctx*> ctx;
+  int device = 0;
+  cudaStream_t stream = nullptr;           // the group's launch stream
+  std::vector<cudaStream_t> branch;        // one per context, used while capturing
+  std::vector<cudaEvent_t> ev;             // fork/join events: [0] fork, [1 + i] join of branch i
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kStepsPerGraph steps of every context; one step
+  std::vector<unsigned long long> gen;     // the contexts' generations the graphs were built on
+  std::string err;
+};
+
+namespace {
+
+int group_fail(sem_group* g, int code, const std::string& msg) {
+  if (g)
+    g->err = msg;
+  else
+    g_err = msg;
+  return code;
+}
+
+void group_drop(sem_group* g) {
+  for (auto& x : g->graph)
+    if (x) {
+      cudaGraphExecDestroy(x);
+      x = nullptr;
+    }
+}
+
+// One graph advancing every context by `steps` pending steps, each context on a branch of
+// its own so that the contexts' kernels may run side by side.
+int group_build(sem_group* g, int which, int steps) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return group_fail(g, SEM_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  int rc = SEM_OK;
+  if (cudaEventRecord(g->ev[0], g->stream) != cudaSuccess) rc = group_fail(g, SEM_ECUDA, "fork event");
+  for (size_t i = 0; i < g->ctx.size() && rc == SEM_OK; ++i) {
+    sem_ctx* c = g->ctx[i];
+    if (cudaStreamWaitEvent(g->branch[i], g->ev[0], 0) != cudaSuccess) {
+      rc = group_fail(g, SEM_ECUDA, "branch wait");
+      break;
+    }
+    cudaStream_t own = c->stream;
+    c->stream = g->branch[i];
+    for (int s = 0; s < steps && rc == SEM_OK; ++s)
+      if (enqueue_pending_step(c) != SEM_OK) rc = group_fail(g, SEM_ECUDA, "capture of a step: " + c->err);
+    c->stream = own;
+    if (rc == SEM_OK && (cudaEventRecord(g->ev[1 + i], g->branch[i]) != cudaSuccess ||
+                         cudaStreamWaitEvent(g->stream, g->ev[1 + i], 0) != cudaSuccess))
+      rc = group_fail(g, SEM_ECUDA, "join event");
+  }
+  e = cudaStreamEndCapture(g->stream, &graph);
+  if (rc == SEM_OK && e != cudaSuccess) rc = group_fail(g, SEM_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  if (rc == SEM_OK) {
+    e = cudaGraphInstantiate(&g->graph[which], graph, 0);
+    if (e != cudaSuccess) rc = group_fail(g, SEM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  if (graph) cudaGraphDestroy(graph);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sem_group_create(sem_group** out, int n, sem_ctx* const* ctxs) {
+  if (!out || n < 1 || !ctxs) return group_fail(nullptr, SEM_EINVAL, "sem_group_create: bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return group_fail(nullptr, SEM_EINVAL, "sem_group_create: NULL context");
+    if (ctxs[i]->device != ctxs[0]->device)
+      return group_fail(nullptr, SEM_EINVAL, "sem_group_create: contexts on different devices");
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return group_fail(nullptr, SEM_EINVAL, "sem_group_create: a context appears twice");
+  }
+  sem_group* g = new sem_group();
+  g->ctx.assign(ctxs, ctxs + n);
+  g->device = ctxs[0]->device;
+  cudaError_t e = cudaSetDevice(g->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+  g->branch.assign(n, nullptr);
+  g->ev.assign(n + 1, nullptr);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&g->branch[i], cudaStreamNonBlocking);
+  for (int i = 0; i <= n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("sem_group_create: ") + cudaGetErrorString(e);
+    sem_group_destroy(g);
+    return group_fail(nullptr, SEM_ECUDA, msg);
+  }
+  *out = g;
+  return SEM_OK;
+}
+
+int sem_group_destroy(sem_group* g) {
+  if (!g) return SEM_OK;
+  cudaSetDevice(g->device);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  group_drop(g);
+  for (cudaEvent_t e : g->ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : g->branch)
+    if (s) cudaStreamDestroy(s);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return SEM_OK;
+}
+
+int sem_group_step(sem_group* g, int nsteps) {
+  if (!g) return group_fail(nullptr, SEM_EINVAL, "null group");
+  if (nsteps < 0) return group_fail(g, SEM_EINVAL, "nsteps must be >= 0");
+  if (nsteps == 0) return SEM_OK;
+  cudaError_t e = cudaSetDevice(g->device);
+  if (e != cudaSuccess) return group_fail(g, SEM_ECUDA, cudaGetErrorString(e));
+  const size_t n = g->ctx.size();
+  // each context: step counter, then one eager step on its own stream (a first step from a
+  // complete state, or a pending one), so that all of them continue in pending form
+  for (size_t i = 0; i < n; ++i) {
+    sem_ctx* c = g->ctx[i];
+    int r = check_ready(c);
+    if (r) return group_fail(g, r, "context " + std::to_string(i) + ": " + c->err);
+    if ((r = advance(c, 1, nullptr))) return group_fail(g, r, "context " + std::to_string(i) + ": " + c->err);
+    if (cudaEventRecord(g->ev[1 + i], c->stream) != cudaSuccess || cudaStreamWaitEvent(g->stream, g->ev[1 + i], 0) != cudaSuccess)
+      return group_fail(g, SEM_ECUDA, "ordering the group after its contexts");
+  }
+  int left = nsteps - 1;
+  bool stale = g->gen.size() != n;
+  for (size_t i = 0; i < n && !stale; ++i) stale = g->gen[i] != g->ctx[i]->generation;
+  if (stale) {
+    group_drop(g);
+    g->gen.clear();
+    for (sem_ctx* c : g->ctx) g->gen.push_back(c->generation);
+  }
+  if (left >= kStepsPerGraph && !g->graph[0]) {
+    int r = group_build(g, 0, kStepsPerGraph);
+    if (r) return r;
+  }
+  if (left % kStepsPerGraph && !g->graph[1]) {
+    int r = group_build(g, 1, 1);
+    if (r) return r;
+  }
+  for (; left >= kStepsPerGraph; left -= kStepsPerGraph)
+    if ((e = cudaGraphLaunch(g->graph[0], g->stream)) != cudaSuccess) return group_fail(g, SEM_ECUDA, cudaGetErrorString(e));
+  for (; left > 0; --left)
+    if ((e = cudaGraphLaunch(g->graph[1], g->stream)) != cudaSuccess) return group_fail(g, SEM_ECUDA, cudaGetErrorString(e));
+  // later work of every context waits for the group
+  if (cudaEventRecord(g->ev[0], g->stream) != cudaSuccess) return group_fail(g, SEM_ECUDA, "group completion event");
+  for (size_t i = 0; i < n; ++i) {
+    if (cudaStreamWaitEvent(g->ctx[i]->stream, g->ev[0], 0) != cudaSuccess)
+      return group_fail(g, SEM_ECUDA, "ordering a context after the group");
+    g->ctx[i]->steps += nsteps - 1;  // advance() counted the eager step
+  }
+  return SEM_OK;
+}
+
+int sem_group_sync(sem_group* g) {
+  if (!g) return group_fail(nullptr, SEM_EINVAL, "null group");
+  cudaSetDevice(g->device);
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return group_fail(g, SEM_ECUDA, cudaGetErrorString(e));
+  return SEM_OK;
+}
+
+const char* sem_group_last_error(const sem_group* g) { return g ? g->err.c_str() : g_err.c_str(); }
 
 const char* sem_last_error(const sem_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
 

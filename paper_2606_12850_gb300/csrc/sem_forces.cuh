@@ -62,10 +62,11 @@ struct ForceCfg {
   static constexpr int TS = E * ES;                   // floats per team
   static constexpr int SMEM_FLOATS = TEAMS * TS;
   static constexpr int REC = (kRecFields * NP + 3) / 4 * 4;
-  // Line owners for the eta and zeta contractions (each shared value read a fixed number of
-  // times) from NGLL = 4 up; at NGLL = 3 the per-point form is faster (GB300, 128^3 mesh:
-  // 1.18 ms against 1.33 ms per sweep), at 5/7/9 the line owners (0.66/0.86/0.96 ms against
-  // 0.75/0.94/1.15 ms).
+  // Default contraction form: line owners for the eta and zeta contractions (each shared
+  // value read a fixed number of times) from NGLL = 4 up; at NGLL = 3 the per-point form is
+  // faster (GB300, 128^3 mesh: 1.18 ms against 1.33 ms per sweep), at 5/7/9 the line owners
+  // (0.66/0.86/0.96 ms against 0.75/0.94/1.15 ms). sem_autotune can measure both on the
+  // caller's mesh and override it.
   static constexpr bool LINE_OWNERS = N >= 4;
   // CTAs per SM the register allocation must allow, from a GB300 sweep of force-sweep time
   // against the register cap: 64 registers for NGLL <= 5, 85 for NGLL = 6-7, 128 for
@@ -100,7 +101,7 @@ __device__ __forceinline__ void team_sync() {
 // With S shots (VS = 4 only) the fields are [nglob][S][4] and the launch works on the items
 // (element, shot) of elements e0 .. e1-1, element-major: the teams of a CTA take the shots
 // of one element, so its record is read from DRAM once for all of them.
-template <int N, int VS, bool MS>
+template <int N, int VS, bool MS, bool LO>
 __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     forces_kernel(const float* __restrict__ rec, const float* __restrict__ u, float* __restrict__ f, int e0,
                   int e1, int S_arg) {
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
   }
   team_sync<WT>();
 
-  if constexpr (C::LINE_OWNERS) {
+  if constexpr (LO) {
     // Thread tl of the team owns one line of NGLL points of element le = tl / NL, indexed by
     // line = a + N b: the xi-line (j, k) = (a, b) in phases 2b and 4, the eta-line
     // (i, k) = (a, b) and the zeta-line (i, j) = (a, b) in phases 2a and 3. A line owner reads
@@ -194,19 +195,19 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     //     zeta-line (i, j) = (a, b)
     if (active) {
       float ve[3][N], vz[3][N];
-  #pragma unroll
+#pragma unroll
       for (int l = 0; l < N; ++l)
-  #pragma unroll
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
           ve[c][l] = su[3 * (a + N * (l + N * b)) + c];
           vz[c][l] = su[3 * (a + N * (b + N * l)) + c];
         }
-  #pragma unroll
+#pragma unroll
       for (int m = 0; m < N; ++m)
-  #pragma unroll
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
           float de = 0.f, dz = 0.f;
-  #pragma unroll
+#pragma unroll
           for (int l = 0; l < N; ++l) {
             de += H[m * N + l] * ve[c][l];
             dz += H[m * N + l] * vz[c][l];
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     float fx[N], fy[N], fz[N];
     {
       float ux[N], uy[N], uz[N];
-  #pragma unroll
+#pragma unroll
       for (int i = 0; i < N; ++i) {
         const int p = i + N * line;
         ux[i] = su[3 * p];
@@ -231,10 +232,10 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         uz[i] = su[3 * p + 2];
         fx[i] = fy[i] = fz[i] = 0.f;
       }
-  #pragma unroll
+#pragma unroll
       for (int i = 0; i < N; ++i) {
         float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
-  #pragma unroll
+#pragma unroll
         for (int l = 0; l < N; ++l) {
           const float h = H[i * N + l];
           dxi_x += h * ux[l];
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         const float dze_x = sz[p3], dze_y = sz[p3 + 1], dze_z = sz[p3 + 2];
         const int q = i * NL + line;
         float G[9];
-  #pragma unroll
+#pragma unroll
         for (int c = 0; c < 9; ++c) G[c] = active ? __ldg(r + (kG + c) * NP + q) : 0.f;
         const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
         const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
         const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
         const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
-  #pragma unroll
+#pragma unroll
         for (int ip = 0; ip < N; ++ip) {
           const float hw = HW[i * N + ip];
           fx[ip] += hw * txi_x;
@@ -296,19 +297,19 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     // 3. eta and zeta transposed products along the eta- and zeta-lines, in place
     if (active) {
       float ve[3][N], vz[3][N];
-  #pragma unroll
+#pragma unroll
       for (int l = 0; l < N; ++l)
-  #pragma unroll
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
           ve[c][l] = se[3 * (a + N * (l + N * b)) + c];
           vz[c][l] = sz[3 * (a + N * (b + N * l)) + c];
         }
-  #pragma unroll
+#pragma unroll
       for (int m = 0; m < N; ++m)
-  #pragma unroll
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
           float te = 0.f, tz = 0.f;
-  #pragma unroll
+#pragma unroll
           for (int l = 0; l < N; ++l) {
             te += HW[l * N + m] * ve[c][l];
             tz += HW[l * N + m] * vz[c][l];
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     // 3b. element forces along the xi-line (j, k) = (a, b) into the (now free) u slots
     if (active) {
       const float wj = W[a], wk = W[b];
-  #pragma unroll
+#pragma unroll
       for (int i = 0; i < N; ++i) {
         const float wi = W[i];
         const int p = 3 * (i + N * line);
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     const float* __restrict__ r = rec + static_cast<size_t>(elem_of(active ? le : 0)) * REC;
 
     float ux[N], uy[N], uz[N];
-  #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) {
       const int p = i + N * line;
       ux[i] = su[3 * p];
@@ -354,21 +355,21 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       uz[i] = su[3 * p + 2];
     }
     float hj[N], hk[N];
-  #pragma unroll
+#pragma unroll
     for (int l = 0; l < N; ++l) {
       hj[l] = H[j * N + l];
       hk[l] = H[k * N + l];
     }
     float fx[N], fy[N], fz[N];
-  #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) fx[i] = fy[i] = fz[i] = 0.f;
 
-  #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) {
       float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
       float det_x = 0.f, det_y = 0.f, det_z = 0.f;
       float dze_x = 0.f, dze_y = 0.f, dze_z = 0.f;
-  #pragma unroll
+#pragma unroll
       for (int l = 0; l < N; ++l) {
         const float h = H[i * N + l];
         dxi_x += h * ux[l];
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       }
       const int q = i * NL + line;
       float G[9];
-  #pragma unroll
+#pragma unroll
       for (int a = 0; a < 9; ++a) G[a] = active ? __ldg(r + (kG + a) * NP + q) : 0.f;
       const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
       const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
       const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
       const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
-  #pragma unroll
+#pragma unroll
       for (int ip = 0; ip < N; ++ip) {
         const float hw = HW[i * N + ip];
         fx[ip] += hw * txi_x;
@@ -435,16 +436,16 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     // 3. eta and zeta transposed products; forces into the (now free) u slots
     {
       float hwj[N], hwk[N];
-  #pragma unroll
+#pragma unroll
       for (int l = 0; l < N; ++l) {
         hwj[l] = HW[l * N + j];
         hwk[l] = HW[l * N + k];
       }
       const float wj = W[j], wk = W[k];
-  #pragma unroll
+#pragma unroll
       for (int i = 0; i < N; ++i) {
         float ex = 0.f, ey = 0.f, ez = 0.f, zx = 0.f, zy = 0.f, zz = 0.f;
-  #pragma unroll
+#pragma unroll
         for (int l = 0; l < N; ++l) {
           const int pe = 3 * (i + N * (l + N * k));
           ex += hwj[l] * se[pe];
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
 
   // 4. scatter in the gather's coalesced order; for the padded layout the previous values
   //    of a group of GB nodes are loaded before any of them is written back
-  if (VS == 4) {
+  if constexpr (VS == 4) {
     for (int base = tl; base < ne * NP; base += GB * TEAM) {
       uint32_t w[GB];
       float4 prev[GB];
@@ -497,23 +498,23 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         }
       }
     }
-    return;
-  }
-  for (int idx = tl; idx < ne * NP; idx += TEAM) {
-    const int e = idx / NP;
-    const int p = idx - e * NP;
-    const float* sb = ts + e * ES;
-    const uint32_t w = reinterpret_cast<const uint32_t*>(sb + 9 * NP)[p];
-    const size_t g = w & ~kFirstTouchBit;
-    const float* src = sb + 3 * p;
-    if (w & kFirstTouchBit) {
-      f[3 * g] = src[0];
-      f[3 * g + 1] = src[1];
-      f[3 * g + 2] = src[2];
-    } else {
-      f[3 * g] += src[0];
-      f[3 * g + 1] += src[1];
-      f[3 * g + 2] += src[2];
+  } else {
+    for (int idx = tl; idx < ne * NP; idx += TEAM) {
+      const int e = idx / NP;
+      const int p = idx - e * NP;
+      const float* sb = ts + e * ES;
+      const uint32_t w = reinterpret_cast<const uint32_t*>(sb + 9 * NP)[p];
+      const size_t g = w & ~kFirstTouchBit;
+      const float* src = sb + 3 * p;
+      if (w & kFirstTouchBit) {
+        f[3 * g] = src[0];
+        f[3 * g + 1] = src[1];
+        f[3 * g + 2] = src[2];
+      } else {
+        f[3 * g] += src[0];
+        f[3 * g + 1] += src[1];
+        f[3 * g + 2] += src[2];
+      }
     }
   }
 }
@@ -649,7 +650,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
   }
 }
 
-template <int VS, bool MS>
+template <int VS, bool MS, bool LO>
 int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   using C = ForceCfg<SEM_NGLL>;
   static unsigned long long attr_done = 0;  // one bit per device ordinal
@@ -659,7 +660,7 @@ int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_done & bit)) {
     cudaError_t e =
-        cudaFuncSetAttribute(forces_kernel<SEM_NGLL, VS, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(forces_kernel<SEM_NGLL, VS, MS, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return static_cast<int>(e);
     attr_done |= bit;
   }
@@ -674,14 +675,19 @@ int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_kernel<SEM_NGLL, VS, MS>, L.rec, L.u, L.f, L.e0, L.e1, S));
+  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_kernel<SEM_NGLL, VS, MS, LO>, L.rec, L.u, L.f, L.e0, L.e1, S));
 }
 
 int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
   if (L.e1 <= L.e0) return 0;
-  if (L.shots > 1) return L.node_stride == 4 ? launch_forces_vs<4, true>(L, s) : static_cast<int>(cudaErrorInvalidValue);
-  if (L.node_stride == 4) return launch_forces_vs<4, false>(L, s);
-  if (L.node_stride == 3) return launch_forces_vs<3, false>(L, s);
+  using C = ForceCfg<SEM_NGLL>;
+  const bool lo = L.variant == 0 ? C::LINE_OWNERS : L.variant == 1;  // 0 default, 1 line owners, 2 per point
+  if (L.shots > 1) {
+    if (L.node_stride != 4) return static_cast<int>(cudaErrorInvalidValue);
+    return lo ? launch_forces_vs<4, true, true>(L, s) : launch_forces_vs<4, true, false>(L, s);
+  }
+  if (L.node_stride == 4) return lo ? launch_forces_vs<4, false, true>(L, s) : launch_forces_vs<4, false, false>(L, s);
+  if (L.node_stride == 3) return launch_forces_vs<3, false, C::LINE_OWNERS>(L, s);
   return static_cast<int>(cudaErrorInvalidValue);
 }
 

@@ -99,6 +99,7 @@ struct ForceLaunch {
   int e0, e1;
   int node_stride;  // floats per node in u and f: kNodeStride, or 3 for caller arrays
   int shots;        // > 1: u and f are [nglob][shots][kNodeStride], items (element, shot)
+  int variant;      // contraction form: 0 the order's default, 1 line owners, 2 per point
 };
 int launch_forces(int ngll, const ForceLaunch& launch, void* stream);
 int forces_kernel_smem_bytes(int ngll);

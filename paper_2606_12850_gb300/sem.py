@@ -64,6 +64,12 @@ SIGNATURES = {
     "sem_adjoint_segment": (_I, [_P, _I, _P, _P]),
     "sem_energy_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
     "sem_sync": (_I, [_P]),
+    "sem_autotune": (_I, [_P, _I, _P, _P]),
+    "sem_group_create": (_I, [_P, _I, _P]),
+    "sem_group_destroy": (_I, [_P]),
+    "sem_group_step": (_I, [_P, _I]),
+    "sem_group_sync": (_I, [_P]),
+    "sem_group_last_error": (ctypes.c_char_p, [_P]),
     "sem_info": (_I, [_P, _P]),
     "sem_color_counts": (_I, [_P, _P]),
     "sem_last_error": (ctypes.c_char_p, [_P]),
@@ -180,6 +186,7 @@ def sem_destroy(ctx: Ctx):
 
 
 SEM_OPT_SWEEP_SLABS = 1
+SEM_OPT_CONTRACTION = 2
 
 
 def sem_set_option(ctx: Ctx, option: int, value: int):
@@ -396,6 +403,46 @@ def sem_adjoint_gradients(ctx: Ctx):
 def sem_adjoint_segment(ctx: Ctx, count: int, G_dev, u_dev):
     _check(lib().sem_adjoint_segment(ctx.handle, int(count), _dev(G_dev, 3 * ctx.nrec * int(count)),
                                      _dev(u_dev, 3 * ctx.nglob * (int(count) + 2))), "sem_adjoint_segment", ctx)
+
+
+def sem_autotune(ctx: Ctx, reps: int = 5):
+    """Times both contraction forms on this context and keeps the faster; returns
+    (ms per sweep [line owners, per point], chosen form 1 or 2)."""
+    ms = np.zeros(2)
+    choice = ctypes.c_int(0)
+    _check(lib().sem_autotune(ctx.handle, int(reps), ms.ctypes.data_as(_P), ctypes.byref(choice)), "sem_autotune", ctx)
+    return ms, choice.value
+
+
+class Group:
+    """Several contexts stepped together (see sem_group_step in sem.h)."""
+
+    def __init__(self, ctxs):
+        self.ctxs = list(ctxs)  # keeps the contexts alive
+        arr = (_P * len(self.ctxs))(*[c.handle for c in self.ctxs])
+        out = _P()
+        code = lib().sem_group_create(ctypes.byref(out), len(self.ctxs), arr)
+        if code != SEM_OK:
+            raise SemError(code, "sem_group_create", (lib().sem_group_last_error(None) or b"").decode())
+        self.handle = out.value
+
+    def _check(self, code, where):
+        if code != SEM_OK:
+            raise SemError(code, where, (lib().sem_group_last_error(self.handle) or b"").decode())
+
+    def step(self, nsteps: int):
+        self._check(lib().sem_group_step(self.handle, int(nsteps)), "sem_group_step")
+
+    def sync(self):
+        self._check(lib().sem_group_sync(self.handle), "sem_group_sync")
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                lib().sem_group_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
 
 
 def sem_sync(ctx: Ctx):
