@@ -68,13 +68,14 @@ struct ForceCfg {
   // (0.66/0.86/0.96 ms against 0.75/0.94/1.15 ms). sem_autotune can measure both on the
   // caller's mesh and override it.
   static constexpr bool LINE_OWNERS = N >= 4;
-  // CTAs per SM the register allocation must allow, from a GB300 sweep of force-sweep time
+  // CTAs per SM the register allocation must allow, from GB300 sweeps of force-sweep time
   // against the register cap: 64 registers for NGLL <= 5, 85 for NGLL = 6-7, 128 for
-  // NGLL = 8, no cap above (the larger live set of the NGLL = 9-10 contractions wins).
+  // NGLL >= 8 (with the line owners the NGLL = 9 kernel fits 128 registers without spills:
+  // 0.72 ms per sweep against 0.96 ms uncapped at one CTA per SM).
 #ifdef SEM_FORCES_MIN_BLOCKS
   static constexpr int MIN_BLOCKS = SEM_FORCES_MIN_BLOCKS;
 #else
-  static constexpr int MIN_BLOCKS = WARP_TEAM ? 8 : (N <= 7 ? 3 : (N == 8 ? 2 : 1));
+  static constexpr int MIN_BLOCKS = WARP_TEAM ? 8 : (N <= 7 ? 3 : 2);
 #endif
 };
 
