@@ -163,7 +163,8 @@ int sem_set_shot_moment_sources(sem_ctx* ctx, int nsrc, const int32_t* shot, con
 int sem_set_receivers(sem_ctx* ctx, int nrec, const int32_t* node);
 
 /* Set (u, v, a) at t = 0 from host arrays [nglob][3] (NULL = zero) and reset the step
- * counter. Requires sem_set_mesh. Synchronous. */
+ * counter. SEM_EINVAL if a value is not finite (checked on the device; the state is then
+ * zero). Requires sem_set_mesh. Synchronous. */
 int sem_set_state(sem_ctx* ctx, const float* u, const float* v, const float* a);
 /* Same from device arrays (NULL = zero). Asynchronous on the context's stream. */
 int sem_set_state_dev(sem_ctx* ctx, const float* u_dev, const float* v_dev, const float* a_dev);

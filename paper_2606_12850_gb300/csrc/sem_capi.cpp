@@ -273,11 +273,6 @@ int finish_state(sem_ctx* c) {
   return SEM_OK;
 }
 
-bool finite_all(const float* p, size_t n) {
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(p[i])) return false;
-  return true;
-}
 
 }  // namespace
 
@@ -855,10 +850,6 @@ static int set_state_impl(sem_ctx* c, const float* u, const float* v, const floa
   if (r) return r;
   const size_t n3 = 3 * static_cast<size_t>(c->nglob) * c->shots;
   const bool host = kind == cudaMemcpyHostToDevice;
-  if (host) {
-    if ((u && !finite_all(u, n3)) || (v && !finite_all(v, n3)) || (a && !finite_all(a, n3)))
-      return fail(c, SEM_EINVAL, "non-finite state value");
-  }
   const float* src[3] = {u, v, a};
   float* dst[3] = {c->d_u, c->d_v, c->d_a};
   float* stage = nullptr;
@@ -880,9 +871,22 @@ static int set_state_impl(sem_ctx* c, const float* u, const float* v, const floa
   }
   if (stage) cudaFreeAsync(stage, c->stream);
   if (rc) return rc;
-  if (host) SEM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->pending = false;
   c->steps = 0;
+  if (host) {  // values from the host are checked on the device (one pass over the state)
+    int* flag = &c->d_ctl->err;
+    int bad = 0;
+    SEM_CUDA(c, cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+    SEM_LAUNCH(c, launch_nonfinite_check(problem(c), flag, c->stream));
+    SEM_CUDA(c, cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (bad) {
+      for (float* d : dst)
+        SEM_CUDA(c, cudaMemsetAsync(d, 0, kNodeStride * static_cast<size_t>(c->nglob) * c->shots * sizeof(float), c->stream));
+      SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+      return fail(c, SEM_EINVAL, "non-finite state value (the state was reset to zero)");
+    }
+  }
   return SEM_OK;
 }
 

@@ -273,6 +273,13 @@ def test_argument_errors():
         sem.sem_set_dt(ctx, -1.0)
     with pytest.raises(sem.SemError):
         sem.sem_set_sources(ctx, [mesh.nglob], [[0, 0, 1.0]], 10.0, 0.1)
+    v = np.ones((mesh.nglob, 3), dtype=np.float32)
+    v[3, 1] = np.nan
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_set_state(ctx, None, v, None)
+    assert ei.value.code == -1 and "non-finite" in str(ei.value)
+    _, v_now, _ = sem.sem_get_state(ctx)
+    assert not np.any(v_now)  # the rejected state was reset to zero
 
 
 def test_plane_wave_periodic(oracle):
