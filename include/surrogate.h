@@ -17,10 +17,12 @@
  * [batch][C][l0 * prod(up)], C = cout[nstages-1] / K (or cout[nstages-1] when K = 0).
  * Loss: mean squared error over all outputs.
  *
- * Precision: float32 master parameters; the forward and backward passes read bfloat16
- * copies of the weight matrices and convolution kernels (round to nearest even) and
- * accumulate in float32; biases stay float32. Adam (Kingma and Ba 2015) updates the master
- * parameters and refreshes the bfloat16 copies.
+ * Precision: float32 master parameters; every weight product (dense layers, convolutions
+ * and their backward products) runs on the tensor cores with bfloat16 operands (the
+ * bfloat16 copies of the weights, activations and gradients rounded to nearest even) and
+ * float32 accumulation; biases, activations, the loss and the moment contraction stay
+ * float32. Adam (Kingma and Ba 2015) updates the master parameters and refreshes the
+ * bfloat16 copies.
  *
  * Parameter order (every host array of parameters or gradients is this concatenation,
  * float32): W1 [hidden][in_dim], b1 [hidden], W2 [hidden][hidden], b2 [hidden],

@@ -84,7 +84,7 @@ class Surrogate:
     """Parameters as float64 arrays (the CUDA side keeps bfloat16 copies of the weights;
     tests pass the same bf16-rounded values here)."""
 
-    def __init__(self, params: dict, c0: int, l0: int, stages, contract: int = 0):
+    def __init__(self, params: dict, c0: int, l0: int, stages, contract: int = 0, bf16_operands: bool = False):
         """``stages``: list of (c_in, c_out, up) for the decoder; params holds W1, b1, W2, b2,
         W3, b3 and C{s}, c{s} (conv weight [c_out, c_in, 3], bias [c_out]) per stage. With
         ``contract`` = K > 0 the last stage's K * C channels D combine with the last K inputs:
@@ -94,6 +94,10 @@ class Surrogate:
         self.c0, self.l0 = c0, l0
         self.stages = list(stages)
         self.contract = int(contract)
+        # with bf16_operands every operand of a weight product (activations, gradients) is
+        # rounded to bfloat16 first, as on tensor cores; sums, biases, activations and the
+        # moment contraction stay exact
+        self.q = bf16_round if bf16_operands else (lambda v: v)
 
     def _combine(self, x, D):
         K = self.contract
@@ -106,19 +110,19 @@ class Surrogate:
 
     def forward(self, x):
         """Returns (y [n, C_out, L], cache)."""
-        p = self.p
+        p, q = self.p, self.q
         cache = {"x": x}
-        a1 = x @ p["W1"].T + p["b1"]
+        a1 = q(x) @ p["W1"].T + p["b1"]
         h1 = gelu(a1)
-        a2 = h1 @ p["W2"].T + p["b2"]
+        a2 = q(h1) @ p["W2"].T + p["b2"]
         h2 = gelu(a2)
-        a3 = h2 @ p["W3"].T + p["b3"]
+        a3 = q(h2) @ p["W3"].T + p["b3"]
         z = gelu(a3).reshape(x.shape[0], self.c0, self.l0)
         cache.update(a1=a1, h1=h1, a2=a2, h2=h2, a3=a3)
         last = len(self.stages) - 1
         for s, (_, _, up) in enumerate(self.stages):
             zi = upsample(z, up)
-            pre = conv3(zi, p[f"C{s}"], p[f"c{s}"])
+            pre = conv3(q(zi), p[f"C{s}"], p[f"c{s}"])
             cache[f"in{s}"] = zi
             cache[f"pre{s}"] = pre
             z = pre if s == last else gelu(pre)
@@ -132,7 +136,7 @@ class Surrogate:
 
     def backward(self, x, target):
         """Loss and its gradient for every parameter (dict of arrays)."""
-        p = self.p
+        p, q = self.p, self.q
         y, c = self.forward(x)
         n_out = y.size
         g = {}
@@ -143,16 +147,17 @@ class Surrogate:
         for s in range(last, -1, -1):
             up = self.stages[s][2]
             dpre = dz if s == last else dz * gelu_grad(c[f"pre{s}"])
-            dzi, g[f"C{s}"], g[f"c{s}"] = conv3_backward(c[f"in{s}"], p[f"C{s}"], dpre)
+            dzi, g[f"C{s}"], _ = conv3_backward(q(c[f"in{s}"]), p[f"C{s}"], q(dpre))
+            g[f"c{s}"] = dpre.sum(axis=(0, 2))
             dz = upsample_backward(dzi, up)
         da3 = dz.reshape(x.shape[0], -1) * gelu_grad(c["a3"])
-        g["W3"] = da3.T @ c["h2"]
+        g["W3"] = q(da3).T @ q(c["h2"])
         g["b3"] = da3.sum(axis=0)
-        da2 = (da3 @ p["W3"]) * gelu_grad(c["a2"])
-        g["W2"] = da2.T @ c["h1"]
+        da2 = (q(da3) @ p["W3"]) * gelu_grad(c["a2"])
+        g["W2"] = q(da2).T @ q(c["h1"])
         g["b2"] = da2.sum(axis=0)
-        da1 = (da2 @ p["W2"]) * gelu_grad(c["a1"])
-        g["W1"] = da1.T @ x
+        da1 = (q(da2) @ p["W2"]) * gelu_grad(c["a1"])
+        g["W1"] = q(da1).T @ q(x)
         g["b1"] = da1.sum(axis=0)
         return float(np.mean((y - target) ** 2)), g
 

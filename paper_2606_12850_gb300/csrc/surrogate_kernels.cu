@@ -1,8 +1,8 @@
-// CUDA kernels of the seismogram surrogate (sm_103a): one tiled float32 product kernel whose
-// operand loaders express the dense layers, the width-3 convolutions (with nearest
-// upsampling folded into the index map) and their backward products; bias, activation,
-// loss and Adam kernels. Weights are read as bfloat16 and widened to float32; every sum is
-// accumulated in float32 in a fixed order (split-K partial sums are added in split order).
+// CUDA kernels of the seismogram surrogate (sm_103a): one tiled tensor-core product kernel
+// (bfloat16 operands, float32 accumulation) whose operand loaders express the dense layers,
+// the width-3 convolutions (with nearest upsampling folded into the index map) and their
+// backward products; bias, activation, loss and Adam kernels. Every sum is accumulated in
+// float32 in a fixed order (split-K partial sums are added in split order).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -13,7 +13,7 @@
 namespace sgk {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, GT = 256;
+constexpr int BN = 64;
 constexpr float kGeluC = 0.7978845608028654f;  // sqrt(2 / pi)
 constexpr float kGeluA = 0.044715f;
 
@@ -25,67 +25,101 @@ __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * kGeluC * (1.f + 3.f * kGeluA * x * x);
 }
 
-// C[m][n] = sum_k A(m, k) B(k, n) over k in this CTA's split; A and B are loader functors
-// (kAlong: which index is contiguous in memory, so that consecutive threads load
-// consecutive words), EP the epilogue, or a split-K partial into ws[z][M][N].
-template <class LA, class LB, class EP>
-__global__ void __launch_bounds__(GT) gemm_kernel(int M, int N, int K, int kchunk, LA la, LB lb, EP ep, float* ws) {
-  __shared__ float As[BK][BM + 4];
-  __shared__ float Bs[BK][BN + 4];
+// C[m][n] = sum_k A(m, k) B(k, n) over k in this CTA's split, on the tensor cores: the
+// loader functors (kAlong: which index is contiguous in memory, so that consecutive threads
+// load consecutive words) read float32 operands, which are rounded to bfloat16 (nearest
+// even) into shared memory; warp-level mma.sync m16n8k16 (bf16 x bf16, float32
+// accumulators). 2 BM threads, a BM x 64 tile (BM = 128 or 256), each warp a 32 x 32 part
+// as 2 x 4 mma tiles, K in steps of 32. Tall tiles cut how often the activation operand of
+// the wide layers is read again (once per BM rows of the result). The result goes to the
+// epilogue EP, or as a split-K partial to ws[z][M][N].
+constexpr int BKM = 32;          // K step of the product kernel
+constexpr int SROW = BKM + 8;    // bf16 per shared row: 20 words, so 8 rows x 4 words hit 32 banks
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int BM, class LA, class LB, class EP>
+__global__ void __launch_bounds__(2 * BM) gemm_kernel(int M, int N, int K, int kchunk, LA la, LB lb, EP ep, float* ws) {
+  constexpr int MT = 2 * BM;  // BM / 32 warps along M, 2 along N
+  __shared__ __align__(16) bf16 As[BM][SROW];  // [m][k]
+  __shared__ __align__(16) bf16 Bs[BN][SROW];  // [n][k]
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int g = lane >> 2, t = lane & 3;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
-  const int tm = (tid >> 4) * 4, tn = (tid & 15) * 4;
-  float acc[4][4];
+  float acc[2][4][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-    for (int r = 0; r < BM * BK / GT; ++r) {
-      const int idx = tid + r * GT;
-      const int kk = LA::kAlongK ? idx % BK : idx / BM;
-      const int mm = LA::kAlongK ? idx / BK : idx % BM;
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  for (int k0 = kbeg; k0 < kend; k0 += BKM) {
+#pragma unroll
+    for (int r = 0; r < BM * BKM / MT; ++r) {
+      const int idx = tid + r * MT;
+      const int kk = LA::kAlongK ? idx % BKM : idx / BM;
+      const int mm = LA::kAlongK ? idx / BKM : idx % BM;
       const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < kend) ? la(m, k) : 0.f;
+      As[mm][kk] = __float2bfloat16_rn((m < M && k < kend) ? la(m, k) : 0.f);
     }
 #pragma unroll
-    for (int r = 0; r < BN * BK / GT; ++r) {
-      const int idx = tid + r * GT;
-      const int nn = LB::kAlongN ? idx % BN : idx / BK;
-      const int kk = LB::kAlongN ? idx / BN : idx % BK;
+    for (int r = 0; r < BN * BKM / MT; ++r) {
+      const int idx = tid + r * MT;
+      const int nn = LB::kAlongN ? idx % BN : idx / BKM;
+      const int kk = LB::kAlongN ? idx / BN : idx % BKM;
       const int n = n0 + nn, k = k0 + kk;
-      Bs[kk][nn] = (n < N && k < kend) ? lb(k, n) : 0.f;
+      Bs[nn][kk] = __float2bfloat16_rn((n < N && k < kend) ? lb(k, n) : 0.f);
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      float a[4], b[4];
+    for (int kk = 0; kk < BKM; kk += 16) {
+      uint32_t a[2][4], b[4][2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][tm + i];
+      for (int i = 0; i < 2; ++i) {
+        const int r0 = wm * 32 + i * 16 + g;
+        a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r0][kk + 2 * t]);
+        a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][kk + 2 * t]);
+        a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r0][kk + 2 * t + 8]);
+        a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][kk + 2 * t + 8]);
+      }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tn + j];
+      for (int j = 0; j < 4; ++j) {
+        const int c0 = wn * 32 + j * 8 + g;
+        b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c0][kk + 2 * t]);
+        b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c0][kk + 2 * t + 8]);
+      }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int m = m0 + tm + i, n = n0 + tn + j;
-      if (m < M && n < N) {
-        if (ws)
-          ws[(static_cast<size_t>(blockIdx.z) * M + m) * N + n] = acc[i][j];
-        else
-          ep(m, n, acc[i][j]);
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + wm * 32 + i * 16 + g + (r >= 2 ? 8 : 0);
+        const int n = n0 + wn * 32 + j * 8 + 2 * t + (r & 1);
+        if (m < M && n < N) {
+          if (ws)
+            ws[(static_cast<size_t>(blockIdx.z) * M + m) * N + n] = acc[i][j][r];
+          else
+            ep(m, n, acc[i][j][r]);
+        }
       }
-    }
 }
 
 template <class EP>
@@ -104,7 +138,10 @@ int grid_for(size_t n) {
   return static_cast<int>(g < 1 ? 1 : (g > 65535 * 16 ? 65535 * 16 : g));
 }
 
+int tile_rows(int M) { return M >= 512 ? 256 : 128; }
+
 int splits_for(int M, int N, int K) {
+  const int BM = tile_rows(M);
   const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   int s = (608 + tiles - 1) / tiles;
   const int kmax = (K + 255) / 256;
@@ -118,10 +155,13 @@ int run_gemm(int M, int N, int K, LA la, LB lb, EP ep, float* ws, bool allow_spl
   if (M <= 0 || N <= 0) return 0;
   const int splits = (allow_split && ws) ? splits_for(M, N, K) : 1;
   int kchunk = (K + splits - 1) / splits;
-  kchunk = (kchunk + BK - 1) / BK * BK;
+  kchunk = (kchunk + BKM - 1) / BKM * BKM;
   const int used = K > 0 ? (K + kchunk - 1) / kchunk : 1;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, used);
-  gemm_kernel<<<grid, GT, 0, s>>>(M, N, K, kchunk, la, lb, ep, used > 1 ? ws : nullptr);
+  float* part = used > 1 ? ws : nullptr;
+  if (tile_rows(M) == 256)
+    gemm_kernel<256><<<dim3((N + BN - 1) / BN, (M + 255) / 256, used), 512, 0, s>>>(M, N, K, kchunk, la, lb, ep, part);
+  else
+    gemm_kernel<128><<<dim3((N + BN - 1) / BN, (M + 127) / 128, used), 256, 0, s>>>(M, N, K, kchunk, la, lb, ep, part);
   if (used > 1)
     splitk_finalize_kernel<<<grid_for(static_cast<size_t>(M) * N), 256, 0, s>>>(M, N, used, ws, ep);
   return static_cast<int>(cudaGetLastError());

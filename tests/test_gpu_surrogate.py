@@ -2,9 +2,14 @@
 C ABI: forward outputs, the loss, every parameter gradient and an Adam step. The oracle
 takes the bfloat16-rounded weights the kernels read (biases stay float32).
 
-Tolerances: float32 accumulation over at most ~1000 terms with bf16 inputs exactly
-representable in float32: relative L2 <= 1e-5 for outputs and gradients (measured ~1e-7),
-1e-6 for the loss (a float64 sum of float32 squares)."""
+The kernels run their products on the tensor cores with bfloat16 operands (activations and
+gradients rounded to nearest even, weights stored so) and float32 accumulation; the oracle
+rounds the same operands (bf16_operands=True) in float64. Tolerances: relative L2 <= 2e-3
+for outputs and gradients, 1e-3 for the loss: an operand whose float32 and float64 values
+straddle a bfloat16 rounding boundary rounds differently on the two sides (2^-8 relative
+for that operand), which a handful of operands per output do; a transposed fragment or a
+wrong index gives errors of order one. Against the unrounded oracle the bound is 3e-2
+(a few roundings of 2^-9 relative along the layers)."""
 import numpy as np
 import pytest
 
@@ -34,12 +39,13 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def oracle_net(so, spec, flat):
+def oracle_net(so, spec, flat, bf16_operands=True):
     params = {}
     for name, arr in spec.split(flat.astype(np.float64)).items():
         params[name] = so.bf16_round(arr) if name[0] in "WC" else arr
     return so.Surrogate(params, spec.c0, spec.l0, list(zip((spec.c0,) + tuple(spec.stage_cout[:-1]),
-                                                           spec.stage_cout, spec.stage_up)), spec.contract)
+                                                           spec.stage_cout, spec.stage_up)), spec.contract,
+                        bf16_operands=bf16_operands)
 
 
 def tiny_spec():
@@ -68,14 +74,16 @@ def test_loss_and_gradients_match_oracle(so, contract):
     g = spec.split(m.get_grads())
     net = oracle_net(so, spec, flat)
     ref_loss, ref_g = net.backward(x.astype(np.float64), t.astype(np.float64))
-    assert abs(loss - ref_loss) <= 1e-6 * ref_loss
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss
     for name in ref_g:
-        assert rel_l2(g[name], ref_g[name]) <= 1e-5, name
+        assert rel_l2(g[name], ref_g[name]) <= 2e-3, name
     y = torch.empty((B, spec.out_c, spec.out_l), device="cuda")
     m.forward(xd, y)
     m.sync()
     ref_y, _ = net.forward(x.astype(np.float64))
-    assert rel_l2(y.cpu().numpy(), ref_y) <= 1e-5
+    assert rel_l2(y.cpu().numpy(), ref_y) <= 2e-3
+    exact_y, _ = oracle_net(so, spec, flat, bf16_operands=False).forward(x.astype(np.float64))
+    assert rel_l2(y.cpu().numpy(), exact_y) <= 3e-2
 
 
 def test_full_size_forward_matches_oracle(so):
@@ -92,7 +100,7 @@ def test_full_size_forward_matches_oracle(so):
     m.sync()
     ref, _ = oracle_net(so, spec, flat).forward(x.astype(np.float64))
     assert y.shape == ref.shape
-    assert rel_l2(y.cpu().numpy(), ref) <= 1e-5
+    assert rel_l2(y.cpu().numpy(), ref) <= 2e-3
 
 
 def test_adam_step_matches_oracle(so):
@@ -110,7 +118,7 @@ def test_adam_step_matches_oracle(so):
         g = m.get_grads().astype(np.float64)
         m.adam_step(1e-3)
         so.adam_step(p, g, mm, vv, step, 1e-3)
-        np.testing.assert_allclose(m.get_params(), p, rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(m.get_params(), p, rtol=1e-6, atol=1e-9)  # same gradients in, float32 update
 
 
 def test_training_fits_a_smooth_map():

@@ -171,3 +171,18 @@ def test_contracted_network_gradients_match_finite_differences(so):
         net.p[k] = base
         fd = (lp - lm) / (2 * h)
         assert abs(fd - float(np.sum(grads[k] * d))) <= 1e-6 * max(abs(fd), 1e-12), k
+
+
+def test_bf16_operand_mode_stays_close(so):
+    """Rounding every product operand to bfloat16 (the tensor-core arithmetic) moves the output
+    by no more than a few bfloat16 roundings (2^-9 relative each) along the layers, and the
+    rounding itself is the identity on values already in bfloat16."""
+    net = tiny_net(so)
+    rounded = so.Surrogate(net.p, 4, 5, net.stages, bf16_operands=True)
+    x = inputs.uniform(11, (3, 9), -1, 1)
+    y, _ = net.forward(x)
+    yr, _ = rounded.forward(x)
+    rel = np.linalg.norm(yr - y) / np.linalg.norm(y)
+    assert 0 < rel <= 3e-2
+    xb = so.bf16_round(x)
+    assert np.array_equal(so.bf16_round(xb), xb)
