@@ -54,7 +54,7 @@ def parse_args():
     p.add_argument("--adjoint-steps", type=int, default=800, help="misfit-gradient measurement (0 = skip)")
     p.add_argument("--surrogate-runs", type=int, default=4096, help="surrogate training runs (0 = skip)")
     p.add_argument("--models", type=int, default=16, help="uneven-models group measurement (0 = skip)")
-    p.add_argument("--surrogate-epochs", type=int, default=100)
+    p.add_argument("--surrogate-epochs", type=int, default=150)
     return p.parse_args()
 
 
