@@ -54,6 +54,7 @@ def parse_args():
     p.add_argument("--adjoint-steps", type=int, default=800, help="misfit-gradient measurement (0 = skip)")
     p.add_argument("--surrogate-runs", type=int, default=4096, help="surrogate training runs (0 = skip)")
     p.add_argument("--models", type=int, default=16, help="uneven-models group measurement (0 = skip)")
+    p.add_argument("--no-iso", action="store_true", help="skip the (h,p) iso-accuracy study")
     p.add_argument("--surrogate-epochs", type=int, default=150)
     return p.parse_args()
 
@@ -471,6 +472,97 @@ def measure_models(device: int, count: int = 16, steps: int = 50):
                       "sem_group_step and sem_group_sync"}
 
 
+def plane_wave_error(ngll: int, nz: int, periods: float, steps_per_period: int, device: int = 0) -> float:
+    """Waveform error (Sec. V-C-1: squared-norm ratio against the analytic solution, all
+    stations on a line along z) of a P plane wave of wavelength 1 km (vp 3 km/s) travelling
+    ``periods`` periods through a periodic 2 x 2 x nz-element box 4 wavelengths long, from its
+    exact initial displacement and velocity (acceleration from the discrete operator)."""
+    from paper_2606_12850_gb300 import inputs, sem
+    lam, vp = 1000.0, 3000.0
+    h = 4 * lam / nz
+    mesh = inputs.structured_hex_mesh((2, 2, nz), ngll, (2 * h, 2 * h, 4 * lam), periodic=True)
+    one = np.ones(mesh.nspec)
+    ctx = sem.sem_create(ngll, device)
+    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_material(ctx, inputs.per_point(mesh, 2500 * one), inputs.per_point(mesh, vp * one),
+                         inputs.per_point(mesh, 1730 * one))
+    k = 2 * np.pi / lam
+    w = vp * k
+    period = 2 * np.pi / w
+    dt = period / steps_per_period
+    n = int(round(periods * steps_per_period))
+    sem.sem_set_dt(ctx, dt)
+    X = sem.sem_node_xyz(ctx, np.arange(mesh.nglob))
+    u0 = np.zeros((mesh.nglob, 3), dtype=np.float32)
+    v0 = np.zeros((mesh.nglob, 3), dtype=np.float32)
+    u0[:, 2] = np.sin(k * X[:, 2])
+    v0[:, 2] = -w * np.cos(k * X[:, 2])
+    rec = np.nonzero(np.isclose(X[:, 0], 0.0) & np.isclose(X[:, 1], 0.0))[0]
+    sem.sem_set_receivers(ctx, rec)
+    sem.sem_set_state(ctx, u0, v0, None)
+    sem.sem_init_acceleration(ctx)
+    seis = sem.sem_run(ctx, n)
+    t = dt * np.arange(1, n + 1)
+    theory = np.sin(k * X[rec, 2][:, None] - w * t[None, :])
+    wz = seis[:, 2, :].astype(np.float64)
+    return float(np.sum((wz - theory) ** 2) / np.sum(theory ** 2))
+
+
+def measure_iso_accuracy(device: int, target: float = 1e-2, periods: float = 20.0, steps_per_period: int = 400):
+    """The (h, p) iso-accuracy study (Sec. V-C-1) on the GPU, elastic: for every order the
+    largest element (fewest elements per wavelength) whose plane-wave error after
+    ``periods`` periods stays within ``target``, at one time step for all (400 per period,
+    its temporal error far below the target); then the cost of p = 4 against p = 7 and
+    p = 9 on one domain at those element sizes: time per step and device memory at the
+    common time step (the paper's comparison, p = 15 being beyond this build's orders)."""
+    import torch
+
+    from paper_2606_12850_gb300 import inputs, sem
+
+    candidates = [2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48]
+    frontier = []
+    for ngll in (3, 4, 5, 6, 7, 8, 9, 10):
+        tried = []
+        for nz in candidates:
+            err = plane_wave_error(ngll, nz, periods, steps_per_period, device)
+            tried.append((nz / 4.0, err))
+            if err <= target:
+                break
+        epw, err = tried[-1]
+        frontier.append({"ngll": ngll, "p": ngll - 1, "elements_per_wavelength": epw,
+                         "h_over_wavelength": 1.0 / epw, "error": err, "met": err <= target,
+                         "tried": [[a, b] for a, b in tried]})
+    # cost on one domain: p = 4 on 64^3 elements, the others scaled by the frontier's h ratio
+    lam, vp = 1000.0, 3000.0
+    dt = 2 * np.pi / (vp * 2 * np.pi / lam) / steps_per_period
+    h = {f["p"]: lam / f["elements_per_wavelength"] for f in frontier}
+    side = 64 * h[4]
+    costs = []
+    stream = torch.cuda.Stream(device=device)
+    for p in (4, 7, 9):
+        n = max(2, int(round(side / h[p])))
+        w = inputs.homogeneous_cube(n, p + 1, side=side, vp=vp, vs=1730.0, nsteps=100)
+        s = sem.setup_workload(w, device=device, stream=stream, dt=dt)
+        info = sem.sem_info(s.ctx)
+        sem.sem_run_dev(s.ctx, 10, None)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sem.sem_run_dev(s.ctx, 100, None)
+        b.record(stream)
+        b.synchronize()
+        costs.append({"p": p, "elements": f"{n}^3", "h_m": side / n, "ms_per_step": a.elapsed_time(b) / 100,
+                      "device_mb": info["device_bytes"] / 1e6, "nglob": info["nglob"]})
+        del s
+    base = costs[0]
+    for c in costs:
+        c["time_reduction_vs_p4"] = base["ms_per_step"] / c["ms_per_step"]
+        c["memory_reduction_vs_p4"] = base["device_mb"] / c["device_mb"]
+    return {"target_error": target, "periods": periods, "steps_per_period": steps_per_period,
+            "frontier": frontier, "domain_m": side, "dt": dt, "costs": costs,
+            "paper_lx2": "p4 -> p7: 3.18x less memory, 3.85x less time; p7 -> p15: 1.8x / 1.4x (acoustic "
+                         "frontier, 160 periods, elastic runs of 15 000 steps)"}
+
+
 def measure_surrogate(device: int, runs: int, epochs: int, heldout: int = 256, batch: int = 256):
     """The learned surrogate of the 16^3 layered medium (NGLL 5, 64 surface receivers, 1000
     steps, Ricker 0.5 Hz): ``runs`` solver runs with seeded random positions and unit moment
@@ -637,6 +729,10 @@ def run_ours(args):
     if args.adjoint_steps > 0:
         adj = measure_adjoint(local, args.adjoint_steps)
 
+    iso = None
+    if not args.no_iso:
+        iso = measure_iso_accuracy(local)
+
     models = None
     if args.models > 0:
         models = measure_models(local, args.models)
@@ -669,7 +765,8 @@ def run_ours(args):
                                   "bytes_per_step": alg["step"]},
             "global_pt_updates_per_s": world * mesh.nglob * K / (ms / 1e3),
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clock_info,
-            "batched_shots": batched, "uneven_models": models, "hp_sweep": sweep, "adjoint": adj,
+            "batched_shots": batched, "uneven_models": models, "hp_sweep": sweep, "iso_accuracy": iso,
+            "adjoint": adj,
             "surrogate": sur,
             "kernel_sources": kernel_source_hash(),
         }

@@ -174,6 +174,11 @@ int sem_set_state_dev(sem_ctx* ctx, const float* u_dev, const float* v_dev, cons
  * saved at step n. Host-only, no device work. */
 int sem_set_step(sem_ctx* ctx, long long step);
 
+/* Replace a by the acceleration of the current displacement, a = M^-1 (-K u) (no source
+ * term), so that a state set from u and v alone (an initial condition) is consistent for
+ * the first step. Asynchronous on the context's stream. Requires mesh, material and dt. */
+int sem_init_acceleration(sem_ctx* ctx);
+
 /* Copy the current state (u^n, v^n, a^n) to host arrays [nglob][3] (NULL = skip).
  * Reading v or a completes the pending half step (the trajectory is unchanged up to
  * rounding); reading u alone does not touch the state. Synchronous. */

@@ -1008,6 +1008,17 @@ int sem_apply_stiffness_strided(sem_ctx* c, const float* u_dev, float* f_dev, in
   return forces_all_colors(c, u_dev, f_dev, node_stride, 1);
 }
 
+int sem_init_acceleration(sem_ctx* c) {
+  int r = check_ready(c);
+  if (r) return r;
+  if ((r = set_device(c)) || (r = finish_state(c))) return r;
+  if ((r = forces_all_colors(c, c->d_u, c->d_a, kNodeStride, c->shots))) return r;  // a = -K u
+  DevProblem p = problem(c);
+  p.dt = 0.0;  // the corrector with dt = 0 only scales a by 1/M and leaves v as it is
+  SEM_LAUNCH(c, launch_corrector(p, c->stream));
+  return SEM_OK;
+}
+
 int sem_apply_stiffness(sem_ctx* c, const float* u_dev, float* f_dev) {
   return sem_apply_stiffness_strided(c, u_dev, f_dev, 3);
 }

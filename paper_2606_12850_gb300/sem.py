@@ -47,6 +47,7 @@ SIGNATURES = {
     "sem_set_state": (_I, [_P, _P, _P, _P]),
     "sem_set_state_dev": (_I, [_P, _P, _P, _P]),
     "sem_set_step": (_I, [_P, ctypes.c_longlong]),
+    "sem_init_acceleration": (_I, [_P]),
     "sem_get_state": (_I, [_P, _P, _P, _P]),
     "sem_get_state_dev": (_I, [_P, _P, _P, _P]),
     "sem_step": (_I, [_P, _I]),
@@ -306,6 +307,10 @@ def sem_set_state_dev(ctx: Ctx, u=None, v=None, a=None):
 
 def sem_set_step(ctx: Ctx, step: int):
     _check(lib().sem_set_step(ctx.handle, int(step)), "sem_set_step", ctx)
+
+
+def sem_init_acceleration(ctx: Ctx):
+    _check(lib().sem_init_acceleration(ctx.handle), "sem_init_acceleration", ctx)
 
 
 def sem_get_state(ctx: Ctx, want=(True, True, True)):

@@ -63,3 +63,25 @@ def test_dispersion_error_gpu_matches_oracle(oracle):
         assert abs(e_gpu - e_ref) <= max(0.02 * e_ref, 2e-9), (ngll, e_gpu, e_ref)
         errs.append(e_gpu)
     assert all(a > b for a, b in zip(errs, errs[1:])), errs
+
+
+def test_init_acceleration_matches_oracle(oracle):
+    """sem_init_acceleration: a = M^-1 (-K u) of the current displacement, v untouched."""
+    mesh = inputs.structured_hex_mesh((3, 2, 2), 5, (900.0, 600.0, 600.0), jitter=0.2, seed=9)
+    shape = mesh.ibool.shape
+    rho = inputs.uniform(3, shape, 2000.0, 3000.0, stream=1).astype(np.float32)
+    vp = inputs.uniform(3, shape, 3000.0, 5000.0, stream=2).astype(np.float32)
+    vs = (vp / 1.8).astype(np.float32)
+    m = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, rho, vp, vs, 5)
+    ctx = sem.sem_create(5, 0)
+    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_material(ctx, rho, vp, vs)
+    sem.sem_set_dt(ctx, 1e-4)
+    u0 = inputs.random_field(mesh.nglob, 3)
+    v0 = inputs.random_field(mesh.nglob, 4)
+    sem.sem_set_state(ctx, u0, v0, None)
+    sem.sem_init_acceleration(ctx)
+    _, v, a = sem.sem_get_state(ctx)
+    ref = m.forces(u0.astype(np.float64)) / m.mass[:, None]
+    assert np.linalg.norm(a - ref) / np.linalg.norm(ref) <= 2e-6
+    assert np.array_equal(v, v0)
