@@ -22,6 +22,10 @@ paper is silent the reading used is stated in the docstring; these readings are:
   as O(N^-2); Sec. V-C: dt = min(dt_CFL, ...)).
 * Isotropic Hooke law with the stiffness tensor of Sec. II-B written with
   lambda = rho (vp^2 - 2 vs^2), mu = rho vs^2, kappa = lambda + 2 mu / 3.
+* Material sensitivities (not in the paper): the exact gradient of the discrete scheme
+  above, by its discrete adjoint.
+* Moment-tensor source at a node (not in the paper): f_I = M grad(psi_I)(x_s) with the
+  gradient of the lowest-numbered element that holds the node.
 
 Array conventions: element-local fields are numpy arrays shaped
 ``(nspec, ..., k, j, i)`` so that flattening the last three axes gives the local point

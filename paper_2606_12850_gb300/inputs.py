@@ -21,9 +21,12 @@ Conventions (the CUDA library's ``include/sem.h`` states the same):
   (the lattice index wraps modulo ``G``).
 
 The workloads follow the paper's experiments (Sec. V-C: homogeneous media, Ricker point
-source, stations at the surface) and the two solver configurations the project measures:
-a homogeneous 8x8x8 cube of side 1 km at NGLL=5, and a three-layer jittered cube of side
-4 km with 256 GLL intervals per side.
+source, stations at the surface) and the configurations the project measures: a
+homogeneous 8x8x8 cube of side 1 km at NGLL=5, a three-layer jittered cube of side 4 km
+with 256 GLL intervals per side, many shots on a 48^3 layered cube, the layered cube with a
+Gaussian velocity anomaly (sensitivity kernels), and the 16^3 layered medium of the
+learned surrogate with random moment-tensor sources. Random numbers come from splitmix64
+(uniform) and the Box-Muller transform (normal), seeded.
 """
 from __future__ import annotations
 
