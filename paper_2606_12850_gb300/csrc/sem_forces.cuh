@@ -24,8 +24,9 @@ __constant__ float c_w[SEM_NGLL];
 // Force kernel (Sec. II-B matrix-free stiffness action + Sec. IV-C coloured assembly).
 //
 // Threads work in teams: one warp per team for NGLL <= 5 (a team then only needs
-// __syncwarp, so the warps of a CTA drift freely and hide each other's memory latency),
-// the whole CTA for NGLL >= 6. A team holds E = TEAM / NGLL^2 elements of one colour.
+// __syncwarp, so the warps of a CTA drift freely and hide each other's memory latency), two
+// warps with a named barrier of their own for NGLL 7-8 (one element per team), the whole
+// CTA for NGLL 6 and 9-10. A team holds E = TEAM / NGLL^2 elements of one colour.
 //  0. (programmatic dependent launch) bulk-prefetch the team's element records into L2,
 //     then wait for the previous grid;
 //  1. gather, one thread per local point: consecutive threads take consecutive points p,
@@ -51,9 +52,12 @@ template <int N>
 struct ForceCfg {
   static constexpr int NP = N * N * N;
   static constexpr int NL = N * N;
-  static constexpr bool WARP_TEAM = NL <= 32;
-  static constexpr int T = WARP_TEAM ? 128 : 256;     // threads per CTA
-  static constexpr int TEAM = WARP_TEAM ? 32 : T;     // threads per team
+  // Team kind: 0 one warp (NGLL <= 5), 1 two warps under a named barrier of their own
+  // (NGLL 7-8, one element per team), 2 the whole CTA (NGLL 6 and 9-10).
+  static constexpr int KIND = NL <= 32 ? 0 : (N == 7 || N == 8) ? 1 : 2;
+  static constexpr bool WARP_TEAM = KIND == 0;
+  static constexpr int T = KIND == 2 ? 256 : 128;     // threads per CTA
+  static constexpr int TEAM = KIND == 0 ? 32 : KIND == 1 ? 64 : T;  // threads per team
   static constexpr int TEAMS = T / TEAM;              // teams per CTA
   static constexpr int E = TEAM / NL;                 // elements per team
   static constexpr int EPC = TEAMS * E;               // elements per CTA
@@ -75,7 +79,7 @@ struct ForceCfg {
 #ifdef SEM_FORCES_MIN_BLOCKS
   static constexpr int MIN_BLOCKS = SEM_FORCES_MIN_BLOCKS;
 #else
-  static constexpr int MIN_BLOCKS = WARP_TEAM ? 8 : (N <= 7 ? 3 : 2);
+  static constexpr int MIN_BLOCKS = KIND == 0 ? 8 : KIND == 1 ? (N == 7 ? 6 : 4) : (N <= 7 ? 3 : 2);
 #endif
 };
 
@@ -90,12 +94,17 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 __device__ __forceinline__ void wait_prerequisite_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_dependent_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <bool WARP>
-__device__ __forceinline__ void team_sync() {
-  if (WARP)
+// Barrier of one team: the warp, a named barrier (1 + team) over the team's two warps, or
+// the CTA.
+template <int KIND>
+__device__ __forceinline__ void team_sync(int team) {
+  if constexpr (KIND == 0) {
     __syncwarp();
-  else
+  } else if constexpr (KIND == 1) {
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + team) : "memory");
+  } else {
     __syncthreads();
+  }
 }
 
 // VS: floats per node in u and f (4 for the context's own padded fields, 3 for caller arrays).
@@ -109,7 +118,6 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
   const int S = MS ? S_arg : 1;  // shots (a compile-time 1 for the single-shot kernel)
   using C = ForceCfg<N>;
   constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
-  constexpr bool WT = C::WARP_TEAM;
   extern __shared__ float4 smem4[];
   const float* __restrict__ H = c_h;
   const float* __restrict__ HW = c_hw;
@@ -119,7 +127,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
   const int tl = threadIdx.x - team * TEAM;
   const int ibase = (blockIdx.x * C::TEAMS + team) * E;  // first item of the team
   const int ne = min(E, (e1 - e0) * S - ibase);
-  if (WT && ne <= 0) return;  // a warp team without items (never a CTA team)
+  if (C::KIND != 2 && ne <= 0) return;  // a team without items (its barrier is its own)
   float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
   // element and shot of the team's slot le
   auto elem_of = [&](int le) { return e0 + (MS ? (ibase + le) / S : ibase + le); };
@@ -174,7 +182,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       }
     }
   }
-  team_sync<WT>();
+  team_sync<C::KIND>(team);
 
   if constexpr (LO) {
     // Thread tl of the team owns one line of NGLL points of element le = tl / NL, indexed by
@@ -217,7 +225,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
           sz[3 * (a + N * (b + N * m)) + c] = dz;
         }
     }
-    team_sync<WT>();
+    team_sync<C::KIND>(team);
 
     // 2b. along the xi-line (j, k) = (a, b): xi derivatives in registers, Jacobian map, Hooke
     //     stress, fluxes; the xi-flux transposed product stays in registers, the eta and zeta
@@ -293,7 +301,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         }
       }
     }
-    team_sync<WT>();
+    team_sync<C::KIND>(team);
 
     // 3. eta and zeta transposed products along the eta- and zeta-lines, in place
     if (active) {
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
           sz[3 * (a + N * (b + N * m)) + c] = tz;
         }
     }
-    team_sync<WT>();
+    team_sync<C::KIND>(team);
 
     // 3b. element forces along the xi-line (j, k) = (a, b) into the (now free) u slots
     if (active) {
@@ -333,7 +341,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         su[p + 2] = -(wj * wk * fz[i] + wi * wk * se[p + 2] + wi * wj * sz[p + 2]);
       }
     }
-    team_sync<WT>();
+    team_sync<C::KIND>(team);
 
   } else {
     // 2. per xi-line derivatives, stress and fluxes
@@ -432,7 +440,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         sz[p3 + 2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
       }
     }
-    team_sync<WT>();
+    team_sync<C::KIND>(team);
 
     // 3. eta and zeta transposed products; forces into the (now free) u slots
     {
@@ -466,7 +474,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         }
       }
     }
-    team_sync<WT>();
+    team_sync<C::KIND>(team);
 
   }
 
@@ -540,7 +548,6 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
                        double* __restrict__ g_kappa, double* __restrict__ g_mu, int nspec, double c_m, double c_k) {
   using C = ForceCfg<N>;
   constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
-  constexpr bool WT = C::WARP_TEAM;
   static_assert(7 * NP <= ES, "element tile holds lam, u and the mass term");
   extern __shared__ float4 smem4[];
   const float* __restrict__ H = c_h;
@@ -549,7 +556,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
   const int tl = threadIdx.x - team * TEAM;
   const int ebase = (blockIdx.x * C::TEAMS + team) * E;
   const int ne = min(E, nspec - ebase);
-  if (WT && ne <= 0) return;
+  if (C::KIND != 2 && ne <= 0) return;
   float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
   constexpr int GB = 2;  // points per thread whose loads are in flight together
   for (int base = tl; base < ne * NP; base += GB * TEAM) {
@@ -592,7 +599,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
       eb[6 * NP + p] = dot;
     }
   }
-  team_sync<WT>();
+  team_sync<C::KIND>(team);
   const int le = tl / NL;
   const int line = tl - le * NL;
   const int j = line % N;
