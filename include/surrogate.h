@@ -2,7 +2,7 @@
  * source (location and moment tensor) to the three-component traces of the receivers of one
  * fixed medium, trained on runs of the spectral-element solver (include/sem.h). The
  * surrogate is not in arXiv 2606.12850; the solver it is trained on follows Sec. II-B and
- * Sec. V-C of the paper, and the solver stays the fallback and the judge of its error.
+ * Sec. V-C of the paper, and the solver stays the fallback and the measure of its error.
  *
  * Network (all sizes fixed at sg_create):
  *   h1 = gelu(x W1^T + b1)            in_dim -> hidden
