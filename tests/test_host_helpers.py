@@ -1,0 +1,56 @@
+"""Host-side helpers of the benchmark and the surrogate driver (no GPU): the algorithmic
+byte counts behind the roofline, the profile-hash guard on the committed DRAM traffic, the
+surrogate's input features and its fitted amplitude model."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2606_12850_gb300 import inputs
+
+
+def test_algorithmic_bytes():
+    import bench
+    a = bench.algorithmic_bytes(8, 5, 33 ** 3)
+    nloc = 8 * 125
+    assert a["nloc"] == nloc
+    assert a["forces"] == 52 * nloc + 24 * 33 ** 3
+    assert a["step"] == 52 * nloc + 76 * 33 ** 3
+
+
+def test_profiled_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    import bench
+    got = bench.profiled_traffic(5)
+    text = open(os.path.join(bench.ROOT, "profiles", "forces_kernel_ngll5_layered.md")).read()
+    if bench.kernel_source_hash() in text:
+        assert got is not None and got > 2.0e9  # the committed capture is of these sources
+    else:
+        assert got is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
+    assert bench.profiled_traffic(5) is None  # a changed kernel voids the counters
+
+
+def test_surrogate_features_and_amplitude_model():
+    from paper_2606_12850_gb300 import surrogate
+    side = 4000.0
+    pos, mom = inputs.surrogate_sources(500, side, seed=6)
+    x = surrogate.features(pos, mom, side)
+    assert x.shape == (500, 9) and x.dtype == np.float32
+    assert np.all(np.abs(x[:, :3]) <= 1.0)
+    rec = np.array([[1000.0, 1000.0, side], [3000.0, 3000.0, side]])
+    amp = surrogate.AmplitudeModel(side, rec)
+    coef = np.array([1.5, 0.7, -0.2, 0.1, -1.1])
+    rms = np.exp(amp.design(pos) @ coef)
+    amp.fit(pos, rms)
+    np.testing.assert_allclose(amp.coef, coef, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(amp(pos), rms, rtol=1e-9)
+
+
+def test_spec_split_roundtrip():
+    from paper_2606_12850_gb300 import surrogate
+    spec = surrogate.Spec(in_dim=9, hidden=8, c0=3, l0=5, stage_cout=(4, 12), stage_up=(2, 1), contract=6)
+    flat = spec.init_params(2)
+    parts = spec.split(flat)
+    assert list(parts) == [n for n, _ in spec.shapes()]
+    assert np.array_equal(np.concatenate([parts[n].ravel() for n in parts]), flat)
+    assert (spec.out_c, spec.out_l) == (2, 10)
