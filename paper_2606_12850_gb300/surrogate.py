@@ -1,4 +1,4 @@
-"""Binding of the learned seismogram surrogate (include/surrogate.h) and the driver code
+"""Binding of the learned seismogram surrogate (include/surrogate.h) and the host code
 around it: training data from solver runs, the training loop and the solver fallback.
 
 Every arithmetic step of the network (forward, backward, loss, Adam) runs in libsemgb's
