@@ -535,7 +535,8 @@ def measure_iso_accuracy(device: int, target: float = 1e-2, periods: float = 20.
                 break
         epw, err = tried[-1]
         frontier.append({"ngll": ngll, "p": ngll - 1, "elements_per_wavelength": epw,
-                         "h_over_wavelength": 1.0 / epw, "error": err, "met": err <= target,
+                         "h_over_wavelength": 1.0 / epw, "error": err, "error_sqrt": float(np.sqrt(err)),
+                         "met": err <= target,
                          "tried": [[a, b] for a, b in tried]})
     # cost on one domain: p = 4 on 64^3 elements, the others scaled by the frontier's h ratio
     lam, vp = 1000.0, 3000.0
