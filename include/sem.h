@@ -69,6 +69,18 @@ int sem_gll(int ngll, double* xi, double* w, double* hprime);
 int sem_color_elements(int nspec, int ngll, int nglob, const int32_t* ibool,
                        int32_t* color, int* ncolors);
 
+/* Geometry of trilinear hexahedra at their GLL points (Sec. II-B: the mapping of each
+ * element to the reference cube and its Jacobian), exactly as sem_set_mesh computes it:
+ * the GLL positions from the eight corners, dx/dxi by differentiating those positions with
+ * hprime, its inverse by cofactors, all in double precision. ctrl[nspec][8][3] as in
+ * sem_set_mesh (corner c at reference (2a-1, 2b-1, 2d-1), c = a + 2b + 4d). Outputs, each
+ * caller-owned and may be NULL: xyz[nspec][ngll^3][3], dxi_dx[nspec][ngll^3][3][3] with
+ * [r][d] = d xi_r / d x_d, jac[nspec][ngll^3] = det(dx/dxi); the point index is
+ * i + ngll*(j + ngll*k). SEM_EINVAL for bad sizes or non-finite corners, and, after all
+ * outputs are written, if any determinant is <= 0 (the message names the first such
+ * element). Host only, no GPU needed. */
+int sem_geometry(int ngll, int nspec, const double* ctrl, double* xyz, double* dxi_dx, double* jac);
+
 /* Create a solver context on CUDA device `device` for polynomial degree ngll-1.
  * `cuda_stream` is a cudaStream_t to issue all work on, or NULL for a stream the context
  * creates and owns. */

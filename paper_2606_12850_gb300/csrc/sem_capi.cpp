@@ -315,6 +315,32 @@ int sem_color_elements(int nspec, int ngll, int nglob, const int32_t* ibool, int
   return SEM_OK;
 }
 
+int sem_geometry(int ngll, int nspec, const double* ctrl, double* xyz, double* dxi_dx, double* jac) {
+  if (nspec < 1 || !ctrl || ngll < kMinNgll || ngll > kMaxNgll)
+    return fail(nullptr, SEM_EINVAL, "sem_geometry: bad arguments");
+  for (size_t q = 0; q < static_cast<size_t>(nspec) * 24; ++q)
+    if (!std::isfinite(ctrl[q])) return fail(nullptr, SEM_EINVAL, "non-finite corner coordinate");
+  std::vector<double> xi(ngll), w(ngll), h(static_cast<size_t>(ngll) * ngll);
+  std::string err;
+  if (gll_basis(ngll, xi.data(), w.data(), h.data(), &err)) return fail(nullptr, SEM_EINVAL, err);
+  const size_t np = static_cast<size_t>(ngll) * ngll * ngll;
+  std::vector<double> X(3 * np), G(9 * np), J(np);
+  int bad = -1;
+  for (int e = 0; e < nspec; ++e) {
+    const size_t e0 = static_cast<size_t>(e) * np;
+    if (!element_geometry(ngll, xi.data(), h.data(), ctrl + 24 * static_cast<size_t>(e), X.data(), G.data(),
+                          J.data()) &&
+        bad < 0)
+      bad = e;
+    if (xyz) std::memcpy(xyz + 3 * e0, X.data(), sizeof(double) * 3 * np);
+    if (dxi_dx) std::memcpy(dxi_dx + 9 * e0, G.data(), sizeof(double) * 9 * np);
+    if (jac) std::memcpy(jac + e0, J.data(), sizeof(double) * np);
+  }
+  if (bad >= 0)
+    return fail(nullptr, SEM_EINVAL, "element " + std::to_string(bad) + " has a Jacobian determinant <= 0");
+  return SEM_OK;
+}
+
 int sem_create(sem_ctx** out, int ngll, int device, void* cuda_stream) {
   if (!out) return fail(nullptr, SEM_EINVAL, "sem_create: out is NULL");
   *out = nullptr;

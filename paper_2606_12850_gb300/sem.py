@@ -28,6 +28,7 @@ SIGNATURES = {
     "sem_version": (_I, []),
     "sem_gll": (_I, [_I, _P, _P, _P]),
     "sem_color_elements": (_I, [_I, _I, _I, _P, _P, _P]),
+    "sem_geometry": (_I, [_I, _I, _P, _P, _P, _P]),
     "sem_create": (_I, [_P, _I, _I, _P]),
     "sem_destroy": (_I, [_P]),
     "sem_set_option": (_I, [_P, _I, ctypes.c_longlong]),
@@ -169,6 +170,20 @@ def sem_color_elements(ibool, ngll: int, nglob: int):
     _check(lib().sem_color_elements(nspec, ngll, nglob, p, color.ctypes.data_as(_P), ctypes.byref(nc)),
            "sem_color_elements")
     return color, nc.value
+
+
+def sem_geometry(ctrl, ngll: int):
+    """Library geometry of the elements ``ctrl`` [nspec][8][3]: returns xyz [nspec][ngll^3][3],
+    dxi_dx [nspec][ngll^3][3][3] ([r][d] = d xi_r / d x_d) and jac [nspec][ngll^3]."""
+    c, p = _host(ctrl, np.float64)
+    nspec = c.size // 24
+    n3 = ngll ** 3
+    xyz = np.empty((nspec, n3, 3))
+    g = np.empty((nspec, n3, 3, 3))
+    jac = np.empty((nspec, n3))
+    _check(lib().sem_geometry(ngll, nspec, p, xyz.ctypes.data_as(_P), g.ctypes.data_as(_P),
+                              jac.ctypes.data_as(_P)), "sem_geometry")
+    return xyz, g, jac
 
 
 def sem_create(ngll: int, device: int = 0, stream=None) -> Ctx:

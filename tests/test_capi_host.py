@@ -90,6 +90,49 @@ def test_gll_rejects_bad_order():
         assert ei.value.code == -1
 
 
+@pytest.mark.parametrize("ngll", [2, 3, 5, 7, 10])
+def test_geometry_matches_oracle(oracle, ngll):
+    """Library geometry (GLL positions differentiated with hprime, inverse by cofactors)
+    equals the oracle's (analytic derivatives of the trilinear map, numpy inverse and
+    determinant) on a strongly jittered mesh, in double precision."""
+    mesh = inputs.structured_hex_mesh(3, ngll, 1000.0, jitter=0.2, seed=11)
+    xyz, g, jac = sem.sem_geometry(mesh.ctrl, ngll)
+    ox, og, oj = oracle.element_geometry(mesh.ctrl, oracle.Basis(ngll))
+    nspec = mesh.nspec
+    ox = ox.reshape(nspec, 3, -1).transpose(0, 2, 1)
+    og = og.reshape(nspec, 3, 3, -1).transpose(0, 3, 1, 2)
+    oj = oj.reshape(nspec, -1)
+    for lib_v, ora_v in ((xyz, ox), (g, og), (jac, oj)):
+        assert np.abs(lib_v - ora_v).max() <= 1e-12 * np.abs(ora_v).max()
+
+
+def test_geometry_regular_lattice_closed_form():
+    """On a regular lattice of spacing h: d xi / d x = 2/h on the diagonal, 0 elsewhere,
+    J = (h/2)^3 at every point, and the GLL points of an edge are h/2 (1 + xi) apart from
+    its first corner."""
+    h = 250.0
+    mesh = inputs.structured_hex_mesh(2, 4, 2 * h)
+    xyz, g, jac = sem.sem_geometry(mesh.ctrl, 4)
+    np.testing.assert_allclose(g, np.broadcast_to(np.eye(3) * 2 / h, g.shape), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(jac, (h / 2) ** 3, rtol=1e-13)
+    xi, _, _ = sem.sem_gll(4)
+    e0 = xyz[0].reshape(4, 4, 4, 3)
+    np.testing.assert_allclose(e0[0, 0, :, 0] - mesh.ctrl[0, 0, 0], h / 2 * (1 + xi), rtol=0, atol=1e-12)
+
+
+def test_geometry_rejects_inverted_and_non_finite():
+    mesh = inputs.structured_hex_mesh(2, 3, 1.0)
+    ctrl = mesh.ctrl.copy()
+    ctrl[5] = ctrl[5][[1, 0, 3, 2, 5, 4, 7, 6]]  # mirror element 5 in x: J < 0
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_geometry(ctrl, 3)
+    assert ei.value.code == -1 and "element 5" in str(ei.value)
+    ctrl = mesh.ctrl.copy()
+    ctrl[2, 3, 1] = np.nan
+    with pytest.raises(sem.SemError, match="non-finite"):
+        sem.sem_geometry(ctrl, 3)
+
+
 def _check_coloring(ibool, color, ncolors):
     assert color.min() == 0 and color.max() == ncolors - 1
     for c in range(ncolors):
