@@ -67,6 +67,17 @@ def test_plane_wave_fixed_points_per_wavelength(oracle):
     assert errs[0] < 1e-4 and errs[-1] < 1e-7
 
 
+def test_shear_plane_wave_travels_at_vs(oracle):
+    """A transverse plane wave u_x (or u_y) = sin(k z - w t) with w = vs k is a solution of
+    the isotropic elastic equation: the recorded waveform error is small and falls with the
+    order at fixed points per wavelength, and the two polarisations agree (symmetry of the
+    box). A shear modulus with a wrong weight would move the wave at another speed."""
+    errs = [_plane_wave(oracle, ngll, nz, 0.1, comp=0) for ngll, nz in ((3, 6), (5, 3), (7, 2))]
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+    assert errs[0] < 1e-4 and errs[-1] < 1e-7
+    assert abs(_plane_wave(oracle, 5, 3, 0.1, comp=1) / errs[1] - 1.0) < 1e-9
+
+
 def test_newmark_second_order_in_time(oracle):
     """Halving dt at high order divides the squared-norm error ratio by about 2^4
     (amplitude error O(dt^2))."""
