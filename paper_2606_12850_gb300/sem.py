@@ -164,6 +164,8 @@ def sem_gll(ngll: int):
 
 def sem_color_elements(ibool, ngll: int, nglob: int):
     ib, p = _host(ibool, np.int32)
+    if ib.size == 0 or ib.size % ngll ** 3:
+        raise ValueError(f"ibool must hold [nspec][{ngll}^3] entries")
     nspec = ib.size // ngll ** 3
     color = np.empty(nspec, dtype=np.int32)
     nc = ctypes.c_int(0)
@@ -176,6 +178,8 @@ def sem_geometry(ctrl, ngll: int):
     """Library geometry of the elements ``ctrl`` [nspec][8][3]: returns xyz [nspec][ngll^3][3],
     dxi_dx [nspec][ngll^3][3][3] ([r][d] = d xi_r / d x_d) and jac [nspec][ngll^3]."""
     c, p = _host(ctrl, np.float64)
+    if c.size == 0 or c.size % 24:
+        raise ValueError("ctrl must hold [nspec][8][3] corner coordinates")
     nspec = c.size // 24
     n3 = ngll ** 3
     xyz = np.empty((nspec, n3, 3))
@@ -212,6 +216,8 @@ def sem_set_option(ctx: Ctx, option: int, value: int):
 def sem_set_mesh(ctx: Ctx, ibool, ctrl, nglob: int):
     n3 = ctx.ngll ** 3
     ib, pi = _host(ibool, np.int32)
+    if ib.size == 0 or ib.size % n3:
+        raise ValueError(f"ibool must hold [nspec][{ctx.ngll}^3] entries")
     nspec = ib.size // n3
     ct, pc = _host(ctrl, np.float64, (nspec, 8, 3))
     _check(lib().sem_set_mesh(ctx.handle, nspec, int(nglob), pi, pc), "sem_set_mesh", ctx)

@@ -183,6 +183,21 @@ def test_coloring_rejects_out_of_range():
         sem.sem_color_elements(bad, 3, mesh.nglob)
 
 
+def test_binding_checks_array_sizes():
+    """The binding refuses arrays whose size does not match the declared layout before the
+    library reads them."""
+    mesh = inputs.structured_hex_mesh(2, 3, 1.0)
+    with pytest.raises(ValueError):
+        sem.sem_color_elements(mesh.ibool.reshape(-1)[:-1], 3, mesh.nglob)
+    with pytest.raises(ValueError):
+        sem.sem_geometry(mesh.ctrl.reshape(-1)[:-2], 3)
+    ctx = sem.Ctx(0, 3)  # a null handle: nothing reaches the library
+    with pytest.raises(ValueError):
+        sem.sem_set_mesh(ctx, mesh.ibool.reshape(-1)[:-1], mesh.ctrl, mesh.nglob)
+    with pytest.raises(ValueError):
+        sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl[:-1], mesh.nglob)
+
+
 def test_missing_library_fails_loudly(monkeypatch):
     """No CPU fallback: with the library absent, the binding raises."""
     monkeypatch.setattr(sem, "_lib", None)
