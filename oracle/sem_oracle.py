@@ -26,6 +26,9 @@ paper is silent the reading used is stated in the docstring; these readings are:
   above, by its discrete adjoint.
 * Moment-tensor source at a node (not in the paper): f_I = M grad(psi_I)(x_s) with the
   gradient of the lowest-numbered element that holds the node.
+* Sources between nodes (not in the paper): tested against the Lagrange basis of the
+  lowest-numbered element holding the point, f_I = F psi_I(x_s) for a point force and
+  f_I = M grad(psi_I)(x_s) for a moment tensor.
 
 Array conventions: element-local fields are numpy arrays shaped
 ``(nspec, ..., k, j, i)`` so that flattening the last three axes gives the local point
@@ -268,6 +271,7 @@ class Model:
         n = ngll
         self.ngll = n
         self.ibool = np.asarray(ibool)
+        self.ctrl = np.asarray(ctrl, dtype=np.float64)
         self.nspec = self.ibool.shape[0]
         self.nglob = int(nglob)
         self.xyz, self.dxi_dx, self.jac = element_geometry(np.asarray(ctrl, dtype=np.float64), self.basis)
@@ -363,6 +367,95 @@ def moment_tensor_forces(model: Model, node: int, moment) -> tuple:
                 nodes.append(int(ib[e, i + n * (j + n * k)]))
                 forces.append(M @ grad)
     return np.array(nodes, dtype=np.int64), np.array(forces)
+
+
+def lagrange_basis_derivative(xi: np.ndarray, x) -> np.ndarray:
+    """l_i'(x) at arbitrary points: the product formula of Sec. II-B differentiated by the
+    product rule, l_i'(x) = sum_{m != i} 1/(xi_i - xi_m) prod_{q != i, m} (x - xi_q)/(xi_i - xi_q).
+    Returns [len(x), N+1]."""
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    n = len(xi)
+    out = np.zeros((len(x), n))
+    for i in range(n):
+        for m in range(n):
+            if m == i:
+                continue
+            term = np.full(len(x), 1.0 / (xi[i] - xi[m]))
+            for q in range(n):
+                if q != i and q != m:
+                    term = term * (x - xi[q]) / (xi[i] - xi[q])
+            out[:, i] += term
+    return out
+
+
+def locate_point(model: Model, x, tol: float = 1e-9):
+    """Element holding a physical point, and the point's reference coordinates. Elements are
+    tried in index order, those whose corner bounding box (widened by ``tol`` times its
+    largest side) contains x; for each, the trilinear map x(xi) = sum_c N_c(xi) X_c is
+    inverted by Newton's method from the element centre, and the first element whose
+    solution lies in [-1 - tol, 1 + tol]^3 is taken (so a point on a shared face goes to the
+    lowest-numbered element, the same tie rule as node location). Returns (e, xi[3]) with xi
+    clipped to [-1, 1]; ValueError if no element holds x."""
+    x = np.asarray(x, dtype=np.float64)
+    for e in range(model.nspec):
+        X = model.ctrl[e]
+        lo, hi = X.min(axis=0), X.max(axis=0)
+        pad = tol * float(np.max(hi - lo))
+        if np.any(x < lo - pad) or np.any(x > hi + pad):
+            continue
+        ref = np.zeros(3)
+        for _ in range(60):
+            N, dN = trilinear_shape(*ref)
+            A = X.T @ dN  # A[d, r] = d x_d / d xi_r
+            step = np.linalg.solve(A, N @ X - x)
+            ref = ref - step
+            if np.max(np.abs(step)) < 1e-15 or np.max(np.abs(ref)) > 10.0:
+                break
+        if np.all(np.abs(ref) <= 1.0 + tol):
+            return e, np.clip(ref, -1.0, 1.0)
+    raise ValueError(f"point {x} lies outside the mesh")
+
+
+def point_source_forces(model: Model, x_s, force=None, moment=None) -> tuple:
+    """Nodal forces of a point source at an arbitrary position x_s (a reading: the paper's
+    sources sit on nodes; between nodes the source is tested against the Lagrange basis of
+    Sec. II-B of the element that holds x_s, found by locate_point):
+      point force F delta(x - x_s)           ->  f_I = F psi_I(x_s),
+      moment tensor -M . grad delta(x - x_s)  ->  f_I = M grad psi_I(x_s),
+    with psi_(i,j,k) = l_i(xi) l_j(eta) l_k(zeta) at the reference coordinates of x_s and
+    grad psi = (d xi / d x)^T grad_xi psi, d xi / d x the inverse of the analytic trilinear
+    Jacobian at x_s. Exactly one of ``force`` (Fx, Fy, Fz) and ``moment`` (Mxx, Myy, Mzz,
+    Mxy, Mxz, Myz) is given. Returns (e, xi[3], nodes [m], forces [m, 3]) over the element's
+    points whose force is not exactly zero."""
+    if (force is None) == (moment is None):
+        raise ValueError("give exactly one of force and moment")
+    e, ref = locate_point(model, x_s)
+    n = model.ngll
+    xi = model.basis.xi
+    L = [lagrange_basis(xi, ref[r])[0] for r in range(3)]
+    dL = [lagrange_basis_derivative(xi, ref[r])[0] for r in range(3)]
+    _, dN = trilinear_shape(*ref)
+    D = np.linalg.inv(model.ctrl[e].T @ dN)  # D[r, d] = d xi_r / d x_d
+    if moment is not None:
+        mxx, myy, mzz, mxy, mxz, myz = (float(v) for v in moment)
+        M = np.array([[mxx, mxy, mxz], [mxy, myy, myz], [mxz, myz, mzz]])
+    ib = model.ibool.reshape(model.nspec, -1)
+    nodes, forces = [], []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                if force is not None:
+                    f = np.asarray(force, dtype=np.float64) * (L[0][i] * L[1][j] * L[2][k])
+                else:
+                    dpsi = np.array([dL[0][i] * L[1][j] * L[2][k],
+                                     L[0][i] * dL[1][j] * L[2][k],
+                                     L[0][i] * L[1][j] * dL[2][k]])
+                    f = M @ (dpsi @ D)
+                if not np.any(f):
+                    continue
+                nodes.append(int(ib[e, i + n * (j + n * k)]))
+                forces.append(f)
+    return e, ref, np.array(nodes, dtype=np.int64), np.array(forces)
 
 
 def newmark_run(model: Model, dt: float, nsteps: int, u0=None, v0=None, a0=None,
