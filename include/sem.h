@@ -81,6 +81,26 @@ int sem_color_elements(int nspec, int ngll, int nglob, const int32_t* ibool,
  * element). Host only, no GPU needed. */
 int sem_geometry(int ngll, int nspec, const double* ctrl, double* xyz, double* dxi_dx, double* jac);
 
+/* Point location in trilinear hexahedra: for each of npts points xyz[npts][3], the
+ * lowest-numbered element of ctrl[nspec][8][3] that holds it, elem_out[npts] (-1 for a point
+ * outside every element), and its reference coordinates ref_out[npts][3] in [-1, 1] (may be
+ * NULL; 0 for points outside). Elements are tried in index order when their corner bounding
+ * box (widened by 1e-9 of its largest side) holds the point; the trilinear map is inverted by
+ * Newton's method from the element centre; a solution within 1e-9 of the reference cube
+ * counts as inside. Host only, no GPU needed. SEM_EINVAL for bad sizes or non-finite input. */
+int sem_locate_points(int nspec, const double* ctrl, int npts, const double* xyz, int32_t* elem_out,
+                      double* ref_out);
+
+/* Nodal forces of a point source between nodes (Sec. II-B Lagrange basis psi_(i,j,k) =
+ * l_i(xi) l_j(eta) l_k(zeta) of the element with corners ctrl_e[8][3]), at reference
+ * coordinates ref[3] in [-1, 1]: with force[3] (N), f_out[p] = F psi_p(ref); with
+ * moment[6] = (Mxx, Myy, Mzz, Mxy, Mxz, Myz) (N m), f_out[p] = M grad psi_p(ref) (the body
+ * force -M . grad delta tested against psi_p), grad through the inverse of the trilinear
+ * Jacobian at ref. Exactly one of force and moment is non-NULL. f_out: [ngll^3][3] in local
+ * point order. Host only, no GPU needed. SEM_EINVAL for bad arguments. */
+int sem_point_source_forces(int ngll, const double* ctrl_e, const double* ref, const double* force,
+                            const double* moment, double* f_out);
+
 /* Create a solver context on CUDA device `device` for polynomial degree ngll-1.
  * `cuda_stream` is a cudaStream_t to issue all work on, or NULL for a stream the context
  * creates and owns. */
@@ -169,6 +189,17 @@ int sem_set_shot_sources(sem_ctx* ctx, int nsrc, const int32_t* shot, const int3
  * [nsrc][6] = (Mxx, Myy, Mzz, Mxy, Mxz, Myz) in N m. Replaces all sources. */
 int sem_set_shot_moment_sources(sem_ctx* ctx, int nsrc, const int32_t* shot, const int32_t* node,
                                 const double* moment, double f0, double t0);
+
+/* Sources at arbitrary positions xyz[nsrc][3] (metres) inside the mesh, spread over the
+ * nodes of the element that holds each one (sem_locate_points: lowest-numbered element) by
+ * sem_point_source_forces: either point forces force[nsrc][3] or moment tensors
+ * moment[nsrc][6] (exactly one non-NULL), with the Ricker time function of sem_set_sources.
+ * shot[nsrc] assigns each source to a shot (0 <= shot[s] < nshots); NULL applies every source
+ * in every shot. Forces that land on the same (shot, node) add. Replaces all sources.
+ * SEM_EINVAL for a source outside the mesh (the message names it) or non-finite values.
+ * Requires sem_set_mesh. */
+int sem_set_shot_sources_at(sem_ctx* ctx, int nsrc, const int32_t* shot, const double* xyz,
+                            const double* force, const double* moment, double f0, double t0);
 
 /* Receivers: the displacement at node[r] is recorded after every step of sem_run /
  * sem_run_dev, for every shot. nrec may be 0. */

@@ -8,9 +8,11 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "sem.h"
+#include "sem_sources.h"
 #include "sem_internal.h"
 
 using namespace semgb;
@@ -338,6 +340,41 @@ int sem_geometry(int ngll, int nspec, const double* ctrl, double* xyz, double* d
   }
   if (bad >= 0)
     return fail(nullptr, SEM_EINVAL, "element " + std::to_string(bad) + " has a Jacobian determinant <= 0");
+  return SEM_OK;
+}
+
+int sem_locate_points(int nspec, const double* ctrl, int npts, const double* xyz, int32_t* elem_out,
+                      double* ref_out) {
+  if (nspec < 1 || npts < 0 || !ctrl || (npts > 0 && (!xyz || !elem_out)))
+    return fail(nullptr, SEM_EINVAL, "sem_locate_points: bad arguments");
+  for (size_t q = 0; q < static_cast<size_t>(nspec) * 24; ++q)
+    if (!std::isfinite(ctrl[q])) return fail(nullptr, SEM_EINVAL, "non-finite corner coordinate");
+  for (size_t q = 0; q < static_cast<size_t>(npts) * 3; ++q)
+    if (!std::isfinite(xyz[q])) return fail(nullptr, SEM_EINVAL, "non-finite point coordinate");
+  for (int s = 0; s < npts; ++s) {
+    double ref[3] = {0.0, 0.0, 0.0};
+    elem_out[s] = locate_point(nspec, ctrl, xyz + 3 * static_cast<size_t>(s), ref);
+    if (ref_out)
+      for (int q = 0; q < 3; ++q) ref_out[3 * static_cast<size_t>(s) + q] = ref[q];
+  }
+  return SEM_OK;
+}
+
+int sem_point_source_forces(int ngll, const double* ctrl_e, const double* ref, const double* force,
+                            const double* moment, double* f_out) {
+  if (ngll < kMinNgll || ngll > kMaxNgll || !ctrl_e || !ref || !f_out || (!force) == (!moment))
+    return fail(nullptr, SEM_EINVAL, "sem_point_source_forces: bad arguments (give exactly one of force, moment)");
+  for (int q = 0; q < 24; ++q)
+    if (!std::isfinite(ctrl_e[q])) return fail(nullptr, SEM_EINVAL, "non-finite corner coordinate");
+  for (int q = 0; q < 3; ++q)
+    if (!(std::fabs(ref[q]) <= 1.0)) return fail(nullptr, SEM_EINVAL, "reference coordinate outside [-1, 1]");
+  const double* v = force ? force : moment;
+  for (int q = 0; q < (force ? 3 : 6); ++q)
+    if (!std::isfinite(v[q])) return fail(nullptr, SEM_EINVAL, "non-finite source value");
+  std::vector<double> xi(ngll), w(ngll), h(static_cast<size_t>(ngll) * ngll);
+  std::string err;
+  if (gll_basis(ngll, xi.data(), w.data(), h.data(), &err)) return fail(nullptr, SEM_EINVAL, err);
+  point_source_forces(ngll, xi.data(), h.data(), ctrl_e, ref, force, moment, f_out);
   return SEM_OK;
 }
 
@@ -727,6 +764,7 @@ static int set_sources_impl(sem_ctx* c, int nsrc, const int32_t* shot, const int
   // without a shot index a source acts in every shot
   std::vector<int> nodes, shots;
   std::vector<double> forces;
+  std::unordered_map<int64_t, size_t> entry;  // (shot, node) -> index of its entry
   for (int s = 0; s < nsrc; ++s) {
     if (node[s] < 0 || node[s] >= c->nglob) return fail(c, SEM_EINVAL, "source node out of range");
     if (shot && (shot[s] < 0 || shot[s] >= c->shots)) return fail(c, SEM_EINVAL, "source shot out of range");
@@ -734,9 +772,11 @@ static int set_sources_impl(sem_ctx* c, int nsrc, const int32_t* shot, const int
       if (!std::isfinite(force[3 * s + d])) return fail(c, SEM_EINVAL, "non-finite source force");
     const int first = shot ? shot[s] : 0, last = shot ? shot[s] : c->shots - 1;
     for (int sh = first; sh <= last; ++sh) {
-      size_t m = 0;
-      while (m < nodes.size() && !(nodes[m] == node[s] && shots[m] == sh)) ++m;
+      const int64_t key = static_cast<int64_t>(sh) * c->nglob + node[s];
+      const auto found = entry.find(key);
+      const size_t m = found == entry.end() ? nodes.size() : found->second;
       if (m == nodes.size()) {
+        entry.emplace(key, m);
         nodes.push_back(node[s]);
         shots.push_back(sh);
         forces.insert(forces.end(), force + 3 * s, force + 3 * s + 3);
@@ -772,6 +812,40 @@ int sem_set_shot_sources(sem_ctx* c, int nsrc, const int32_t* shot, const int32_
                          double f0, double t0) {
   if (nsrc > 0 && !shot) return fail(c, SEM_EINVAL, "sem_set_shot_sources: NULL shot array");
   return set_sources_impl(c, nsrc, shot, node, force, f0, t0);
+}
+
+int sem_set_shot_sources_at(sem_ctx* c, int nsrc, const int32_t* shot, const double* xyz, const double* force,
+                            const double* moment, double f0, double t0) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (nsrc < 0 || (nsrc > 0 && (!xyz || (!force) == (!moment))))
+    return fail(c, SEM_EINVAL, "sem_set_shot_sources_at: bad arguments (give xyz and exactly one of force, moment)");
+  const int n = c->ngll, np = n * n * n, nv = force ? 3 : 6;
+  std::vector<int32_t> shots, nodes;
+  std::vector<double> forces, f(3 * static_cast<size_t>(np));
+  for (int s = 0; s < nsrc; ++s) {
+    const double* x = xyz + 3 * static_cast<size_t>(s);
+    const double* v = (force ? force : moment) + static_cast<size_t>(nv) * s;
+    for (int q = 0; q < 3; ++q)
+      if (!std::isfinite(x[q])) return fail(c, SEM_EINVAL, "non-finite source position");
+    for (int q = 0; q < nv; ++q)
+      if (!std::isfinite(v[q])) return fail(c, SEM_EINVAL, "non-finite source value");
+    if (shot && (shot[s] < 0 || shot[s] >= c->shots)) return fail(c, SEM_EINVAL, "source shot out of range");
+    double ref[3];
+    const int e = locate_point(c->nspec, c->ctrl.data(), x, ref);
+    if (e < 0) return fail(c, SEM_EINVAL, "source " + std::to_string(s) + " lies outside the mesh");
+    point_source_forces(n, c->xi.data(), c->hprime.data(), c->ctrl.data() + 24 * static_cast<size_t>(e), ref,
+                        force ? v : nullptr, moment ? v : nullptr, f.data());
+    for (int p = 0; p < np; ++p) {
+      const double* fp = f.data() + 3 * p;
+      if (fp[0] == 0.0 && fp[1] == 0.0 && fp[2] == 0.0) continue;
+      if (shot) shots.push_back(shot[s]);
+      nodes.push_back(c->ibool[static_cast<size_t>(e) * np + p]);
+      forces.insert(forces.end(), fp, fp + 3);
+    }
+  }
+  return set_sources_impl(c, static_cast<int>(nodes.size()), shot ? shots.data() : nullptr, nodes.data(),
+                          forces.data(), f0, t0);
 }
 
 int sem_set_shot_moment_sources(sem_ctx* c, int nsrc, const int32_t* shot, const int32_t* node, const double* moment,

@@ -29,6 +29,8 @@ SIGNATURES = {
     "sem_gll": (_I, [_I, _P, _P, _P]),
     "sem_color_elements": (_I, [_I, _I, _I, _P, _P, _P]),
     "sem_geometry": (_I, [_I, _I, _P, _P, _P, _P]),
+    "sem_locate_points": (_I, [_I, _P, _I, _P, _P, _P]),
+    "sem_point_source_forces": (_I, [_I, _P, _P, _P, _P, _P]),
     "sem_create": (_I, [_P, _I, _I, _P]),
     "sem_destroy": (_I, [_P]),
     "sem_set_option": (_I, [_P, _I, ctypes.c_longlong]),
@@ -45,6 +47,7 @@ SIGNATURES = {
     "sem_set_shots": (_I, [_P, _I]),
     "sem_set_shot_sources": (_I, [_P, _I, _P, _P, _P, _D, _D]),
     "sem_set_shot_moment_sources": (_I, [_P, _I, _P, _P, _P, _D, _D]),
+    "sem_set_shot_sources_at": (_I, [_P, _I, _P, _P, _P, _P, _D, _D]),
     "sem_set_state": (_I, [_P, _P, _P, _P]),
     "sem_set_state_dev": (_I, [_P, _P, _P, _P]),
     "sem_set_step": (_I, [_P, ctypes.c_longlong]),
@@ -190,6 +193,36 @@ def sem_geometry(ctrl, ngll: int):
     return xyz, g, jac
 
 
+def sem_locate_points(ctrl, xyz):
+    """Element (lowest index; -1 outside) and reference coordinates of each point among the
+    trilinear elements ``ctrl`` [nspec][8][3]."""
+    c, pc = _host(ctrl, np.float64)
+    if c.size == 0 or c.size % 24:
+        raise ValueError("ctrl must hold [nspec][8][3] corner coordinates")
+    pts, pp = _host(np.atleast_2d(xyz), np.float64)
+    if pts.size % 3:
+        raise ValueError("xyz must hold [npts][3] coordinates")
+    n = pts.size // 3
+    elem = np.empty(n, dtype=np.int32)
+    ref = np.empty((n, 3))
+    _check(lib().sem_locate_points(c.size // 24, pc, n, pp, elem.ctypes.data_as(_P), ref.ctypes.data_as(_P)),
+           "sem_locate_points")
+    return elem, ref
+
+
+def sem_point_source_forces(ngll: int, ctrl_e, ref, force=None, moment=None):
+    """Nodal forces [ngll^3][3] of a point force or a moment tensor at reference coordinates
+    ``ref`` of the element with corners ``ctrl_e`` [8][3]."""
+    c, pc = _host(ctrl_e, np.float64, (8, 3))
+    r, pr = _host(ref, np.float64, (3,))
+    f = None if force is None else _host(force, np.float64, (3,))
+    m = None if moment is None else _host(moment, np.float64, (6,))
+    out = np.empty((ngll ** 3, 3))
+    _check(lib().sem_point_source_forces(ngll, pc, pr, f[1] if f else None, m[1] if m else None,
+                                         out.ctypes.data_as(_P)), "sem_point_source_forces")
+    return out
+
+
 def sem_create(ngll: int, device: int = 0, stream=None) -> Ctx:
     out = _P()
     s = None
@@ -296,6 +329,19 @@ def sem_set_shot_moment_sources(ctx: Ctx, shot, node, moment, f0: float, t0: flo
     mo, pm = _host(np.atleast_2d(moment), np.float64, (nd.size, 6))
     _check(lib().sem_set_shot_moment_sources(ctx.handle, nd.size, ps, pn, pm, float(f0), float(t0)),
            "sem_set_shot_moment_sources", ctx)
+
+
+def sem_set_shot_sources_at(ctx: Ctx, shot, xyz, force=None, moment=None, f0: float = 10.0, t0: float = 0.12):
+    """Sources at arbitrary positions (see sem.h); ``shot`` None applies each in every shot."""
+    pts, pp = _host(np.atleast_2d(xyz), np.float64)
+    if pts.size % 3:
+        raise ValueError("xyz must hold [nsrc][3] coordinates")
+    n = pts.size // 3
+    sh = None if shot is None else _host(np.atleast_1d(shot), np.int32, (n,))
+    fo = None if force is None else _host(np.atleast_2d(force), np.float64, (n, 3))
+    mo = None if moment is None else _host(np.atleast_2d(moment), np.float64, (n, 6))
+    _check(lib().sem_set_shot_sources_at(ctx.handle, n, sh[1] if sh else None, pp, fo[1] if fo else None,
+                                         mo[1] if mo else None, float(f0), float(t0)), "sem_set_shot_sources_at", ctx)
 
 
 def sem_set_receivers(ctx: Ctx, node):

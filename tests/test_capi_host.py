@@ -133,6 +133,70 @@ def test_geometry_rejects_inverted_and_non_finite():
         sem.sem_geometry(ctrl, 3)
 
 
+def _trilinear_point(X, ref):
+    x = np.zeros(3)
+    for c in range(8):
+        sa, sb, sd = (1 if c & 1 else -1), (1 if c & 2 else -1), (1 if c & 4 else -1)
+        x += (1 + sa * ref[0]) * (1 + sb * ref[1]) * (1 + sd * ref[2]) / 8.0 * X[c]
+    return x
+
+
+@pytest.fixture(scope="module")
+def jittered(oracle):
+    mesh = inputs.structured_hex_mesh(3, 5, 900.0, jitter=0.2, seed=11)
+    ones = np.ones(mesh.ibool.shape)
+    return mesh, oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, 2500 * ones, 4000 * ones, 2300 * ones, 5)
+
+
+def test_locate_points_matches_oracle(oracle, jittered):
+    """Library point location (Newton on the trilinear map in C++) equals the oracle's:
+    same element (lowest index on shared faces) and reference coordinates within 1e-12;
+    points outside the mesh get -1."""
+    mesh, m = jittered
+    pts = [_trilinear_point(mesh.ctrl[e], inputs.uniform(7 + e, (3,), -0.99, 0.99)) for e in range(mesh.nspec)]
+    pts += [_trilinear_point(mesh.ctrl[13], np.array([-1.0, 0.2, 0.4])), m.node_xyz[17]]
+    pts += list(inputs.uniform(3, (10, 3), 0.0, 900.0))
+    elem, ref = sem.sem_locate_points(mesh.ctrl, np.array(pts))
+    for x, e, r in zip(pts, elem, ref):
+        e2, r2 = oracle.locate_point(m, x)
+        assert e == e2
+        np.testing.assert_allclose(r, r2, rtol=0, atol=1e-12)
+    elem, _ = sem.sem_locate_points(mesh.ctrl, [[-5.0, 100.0, 100.0], [100.0, 100.0, 901.0]])
+    assert list(elem) == [-1, -1]
+
+
+@pytest.mark.parametrize("kind", ["force", "moment"])
+@pytest.mark.parametrize("ngll", [2, 5, 8])
+def test_point_source_forces_match_oracle(oracle, kind, ngll):
+    """Library interpolated source forces (barycentric Lagrange values, derivatives through
+    the nodal derivative matrix) equal the oracle's (product formula and its derivative)
+    within 1e-12 of the largest force, at random points, a face and a node."""
+    mesh = inputs.structured_hex_mesh(3, ngll, 900.0, jitter=0.2, seed=11)
+    ones = np.ones(mesh.ibool.shape)
+    m = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, 2500 * ones, 4000 * ones, 2300 * ones, ngll)
+    value = np.array([0.3, -1.2, 2.0]) if kind == "force" else inputs.uniform(5, (6,), -1.0, 1.0, stream=9)
+    refs = [inputs.uniform(50 + q, (3,), -0.95, 0.95) for q in range(3)] + [np.array([1.0, -0.3, 0.5])]
+    pts = [_trilinear_point(mesh.ctrl[13], r) for r in refs] + [m.node_xyz[int(mesh.ibool[13, ngll])]]
+    for x in pts:
+        e, ref, nodes, f = oracle.point_source_forces(m, x, **{kind: value})
+        lib_f = sem.sem_point_source_forces(ngll, mesh.ctrl[e], ref, **{kind: value})
+        dense_lib = np.zeros((mesh.nglob, 3))
+        np.add.at(dense_lib, mesh.ibool[e], lib_f)
+        dense_ora = np.zeros((mesh.nglob, 3))
+        np.add.at(dense_ora, nodes, f)
+        np.testing.assert_allclose(dense_lib, dense_ora, rtol=0, atol=1e-12 * np.abs(dense_ora).max())
+
+
+def test_point_source_forces_reject_bad_arguments():
+    ctrl = inputs.structured_hex_mesh(1, 3, 1.0).ctrl[0]
+    with pytest.raises(sem.SemError):
+        sem.sem_point_source_forces(3, ctrl, [0.0, 0.0, 0.0])  # neither force nor moment
+    with pytest.raises(sem.SemError):
+        sem.sem_point_source_forces(3, ctrl, [0.0, 0.0, 0.0], force=[1, 0, 0], moment=np.ones(6))
+    with pytest.raises(sem.SemError):
+        sem.sem_point_source_forces(3, ctrl, [1.5, 0.0, 0.0], force=[1, 0, 0])
+
+
 def _check_coloring(ibool, color, ncolors):
     assert color.min() == 0 and color.max() == ncolors - 1
     for c in range(ncolors):
