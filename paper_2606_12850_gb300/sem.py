@@ -570,3 +570,88 @@ def setup_workload(workload, device: int = 0, stream=None, dt: float | None = No
     sem_set_receivers(ctx, rec_nodes)
     sem_set_state(ctx)
     return Setup(ctx, dt, np.asarray(src_nodes), np.asarray(rec_nodes))
+
+
+def _is_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+class Solver:
+    """Object form of the C ABI for one model on one GPU: owns a context, and each method
+    issues the calls of include/sem.h in their required order. Host data are numpy arrays;
+    wavefields may also be CUDA tensors (then the *_dev calls are used, with no host copy)."""
+
+    def __init__(self, ngll: int, ibool, ctrl, nglob: int, rho, vp, vs, device: int = 0, stream=None,
+                 courant: float = 0.4, dt: float | None = None):
+        self.ctx = sem_create(ngll, device, stream)
+        sem_set_mesh(self.ctx, ibool, ctrl, nglob)
+        sem_set_material(self.ctx, rho, vp, vs)
+        self.dt = sem_suggest_dt(self.ctx, courant) if dt is None else float(dt)
+        sem_set_dt(self.ctx, self.dt)
+        self.top = float(np.max(np.asarray(ctrl)[..., 2]))
+
+    @classmethod
+    def from_workload(cls, workload, device: int = 0, stream=None, dt: float | None = None) -> "Solver":
+        """A solver for an ``inputs.Workload`` with its sources and receivers located (nearest
+        nodes; receivers on the top face when the workload asks for that) and a zero state."""
+        m = workload.mesh
+        s = cls(m.ngll, m.ibool, m.ctrl, m.nglob, workload.rho, workload.vp, workload.vs, device, stream,
+                workload.courant, dt)
+        s.set_sources(workload.source_xyz, workload.source_force, workload.f0, workload.t0)
+        s.set_receivers(workload.receiver_xyz, surface=workload.receiver_surface_only)
+        s.set_state()
+        return s
+
+    def locate(self, xyz, surface: bool = False) -> np.ndarray:
+        """Nearest global node of each point (on the top face with ``surface``)."""
+        return sem_locate_nodes(self.ctx, xyz, self.top if surface else None)
+
+    def set_sources(self, xyz, force=None, f0: float = 10.0, t0: float = 0.12, moment=None,
+                    snap: bool = True, shot=None):
+        """Point forces (or moment tensors) at xyz [n][3]: on the nearest nodes with ``snap``
+        (point forces only), else spread over the element that holds each point."""
+        if snap and moment is None:
+            nodes = self.locate(xyz)
+            if shot is None:
+                sem_set_sources(self.ctx, nodes, force, f0, t0)
+            else:
+                sem_set_shot_sources(self.ctx, shot, nodes, force, f0, t0)
+        else:
+            sem_set_shot_sources_at(self.ctx, shot, xyz, force=force, moment=moment, f0=f0, t0=t0)
+
+    def set_receivers(self, xyz, surface: bool = False) -> np.ndarray:
+        nodes = self.locate(xyz, surface)
+        sem_set_receivers(self.ctx, nodes)
+        return nodes
+
+    def set_shots(self, nshots: int):
+        sem_set_shots(self.ctx, nshots)
+
+    def set_state(self, u=None, v=None, a=None):
+        if any(_is_cuda(x) for x in (u, v, a)):
+            sem_set_state_dev(self.ctx, u, v, a)
+        else:
+            sem_set_state(self.ctx, u, v, a)
+
+    def state(self):
+        """(u, v, a) as host arrays."""
+        return sem_get_state(self.ctx)
+
+    def step(self, nsteps: int):
+        sem_step(self.ctx, nsteps)
+
+    def run(self, nsteps: int, seis_dev=None):
+        """Advance and record: host seismograms returned, or into a CUDA tensor."""
+        if seis_dev is not None:
+            sem_run_dev(self.ctx, nsteps, seis_dev)
+            return seis_dev
+        return sem_run(self.ctx, nsteps)
+
+    def apply_stiffness(self, u_dev, f_dev):
+        sem_apply_stiffness(self.ctx, u_dev, f_dev)
+
+    def energy(self):
+        return sem_energy(self.ctx)
+
+    def sync(self):
+        sem_sync(self.ctx)
