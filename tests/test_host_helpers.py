@@ -1,4 +1,4 @@
-"""Host-side helpers of the benchmark and the surrogate driver (no GPU): the algorithmic
+"""Host-side helpers of the benchmark and the surrogate host code (no GPU): the algorithmic
 byte counts behind the roofline, the profile-hash guard on the committed DRAM traffic, the
 surrogate's input features and its fitted amplitude model."""
 import os
