@@ -11,7 +11,7 @@ Every function cites the passage of arXiv 2606.12850 ("High-Order Spectral Eleme
 for Wave Propagation on ARM Multicore CPU with SME") it follows, by section. Where the
 paper is silent the reading used is stated in the docstring; these readings are:
 
-* Newmark variant: Sec. I and Sec. V-C name "second-order Newmark" and an explicit scheme
+* Newmark variant: Sec. I and Sec. V-C give the scheme's order (two) and an explicit scheme
   with a diagonal mass matrix; read as the explicit predictor/corrector with beta = 0,
   gamma = 1/2 (equivalent to central differences in displacement).
 * Step n advances u^n -> u^{n+1}; the source acts at t_{n+1} = (n+1) dt, and the record of
@@ -42,7 +42,7 @@ from __future__ import annotations
 import numpy as np
 
 # --------------------------------------------------------------------------------------
-# 1D basis (Sec. II-B, "Spectral Element Method")
+# 1D basis (Sec. II-B, the spectral element method)
 # --------------------------------------------------------------------------------------
 
 
