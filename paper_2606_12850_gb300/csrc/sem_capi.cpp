@@ -351,12 +351,9 @@ int sem_locate_points(int nspec, const double* ctrl, int npts, const double* xyz
     if (!std::isfinite(ctrl[q])) return fail(nullptr, SEM_EINVAL, "non-finite corner coordinate");
   for (size_t q = 0; q < static_cast<size_t>(npts) * 3; ++q)
     if (!std::isfinite(xyz[q])) return fail(nullptr, SEM_EINVAL, "non-finite point coordinate");
-  for (int s = 0; s < npts; ++s) {
-    double ref[3] = {0.0, 0.0, 0.0};
-    elem_out[s] = locate_point(nspec, ctrl, xyz + 3 * static_cast<size_t>(s), ref);
-    if (ref_out)
-      for (int q = 0; q < 3; ++q) ref_out[3 * static_cast<size_t>(s) + q] = ref[q];
-  }
+  std::vector<double> ref(3 * static_cast<size_t>(npts));
+  locate_points(nspec, ctrl, npts, xyz, elem_out, ref.data());
+  if (ref_out) std::copy(ref.begin(), ref.end(), ref_out);
   return SEM_OK;
 }
 
@@ -821,21 +818,25 @@ int sem_set_shot_sources_at(sem_ctx* c, int nsrc, const int32_t* shot, const dou
   if (nsrc < 0 || (nsrc > 0 && (!xyz || (!force) == (!moment))))
     return fail(c, SEM_EINVAL, "sem_set_shot_sources_at: bad arguments (give xyz and exactly one of force, moment)");
   const int n = c->ngll, np = n * n * n, nv = force ? 3 : 6;
-  std::vector<int32_t> shots, nodes;
-  std::vector<double> forces, f(3 * static_cast<size_t>(np));
   for (int s = 0; s < nsrc; ++s) {
-    const double* x = xyz + 3 * static_cast<size_t>(s);
     const double* v = (force ? force : moment) + static_cast<size_t>(nv) * s;
     for (int q = 0; q < 3; ++q)
-      if (!std::isfinite(x[q])) return fail(c, SEM_EINVAL, "non-finite source position");
+      if (!std::isfinite(xyz[3 * static_cast<size_t>(s) + q])) return fail(c, SEM_EINVAL, "non-finite source position");
     for (int q = 0; q < nv; ++q)
       if (!std::isfinite(v[q])) return fail(c, SEM_EINVAL, "non-finite source value");
     if (shot && (shot[s] < 0 || shot[s] >= c->shots)) return fail(c, SEM_EINVAL, "source shot out of range");
-    double ref[3];
-    const int e = locate_point(c->nspec, c->ctrl.data(), x, ref);
+  }
+  std::vector<int32_t> elem(nsrc > 0 ? nsrc : 1);
+  std::vector<double> refs(3 * static_cast<size_t>(nsrc > 0 ? nsrc : 1));
+  if (nsrc > 0) locate_points(c->nspec, c->ctrl.data(), nsrc, xyz, elem.data(), refs.data());
+  std::vector<int32_t> shots, nodes;
+  std::vector<double> forces, f(3 * static_cast<size_t>(np));
+  for (int s = 0; s < nsrc; ++s) {
+    const double* v = (force ? force : moment) + static_cast<size_t>(nv) * s;
+    const int e = elem[s];
     if (e < 0) return fail(c, SEM_EINVAL, "source " + std::to_string(s) + " lies outside the mesh");
-    point_source_forces(n, c->xi.data(), c->hprime.data(), c->ctrl.data() + 24 * static_cast<size_t>(e), ref,
-                        force ? v : nullptr, moment ? v : nullptr, f.data());
+    point_source_forces(n, c->xi.data(), c->hprime.data(), c->ctrl.data() + 24 * static_cast<size_t>(e),
+                        refs.data() + 3 * static_cast<size_t>(s), force ? v : nullptr, moment ? v : nullptr, f.data());
     for (int p = 0; p < np; ++p) {
       const double* fp = f.data() + 3 * p;
       if (fp[0] == 0.0 && fp[1] == 0.0 && fp[2] == 0.0) continue;

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "sem_internal.h"
 
@@ -84,47 +85,121 @@ void lagrange_at(int n, const double* xi, const double* h, double x, double* l, 
 // Elements in index order whose corner bounding box (widened by 1e-9 of its largest side)
 // holds x; Newton's method on the trilinear map from the element centre (at most 60
 // iterations); the first element whose solution lies within 1e-9 of the reference cube.
-int locate_point(int nspec, const double* ctrl, const double* x, double* ref) {
-  const double tol = 1e-9;
-  for (int e = 0; e < nspec; ++e) {
-    const double* X = ctrl + 24 * static_cast<size_t>(e);
-    double lo[3], hi[3];
-    for (int d = 0; d < 3; ++d) {
-      lo[d] = hi[d] = X[d];
-      for (int c = 1; c < 8; ++c) {
-        lo[d] = std::min(lo[d], X[3 * c + d]);
-        hi[d] = std::max(hi[d], X[3 * c + d]);
-      }
-    }
-    const double pad = tol * std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
-    bool inside_box = true;
-    for (int d = 0; d < 3; ++d) inside_box = inside_box && x[d] >= lo[d] - pad && x[d] <= hi[d] + pad;
-    if (!inside_box) continue;
-    double r[3] = {0.0, 0.0, 0.0};
-    bool ok = true;
-    for (int it = 0; it < 60; ++it) {
-      double p[3], A[3][3], B[3][3];
-      trilinear_map(X, r, p, A);
-      if (!invert3(A, B)) {
-        ok = false;
-        break;
-      }
-      double big = 0.0, rmax = 0.0;
-      for (int q = 0; q < 3; ++q) {
-        const double step = B[q][0] * (p[0] - x[0]) + B[q][1] * (p[1] - x[1]) + B[q][2] * (p[2] - x[2]);
-        r[q] -= step;
-        big = std::max(big, std::fabs(step));
-      }
-      for (int q = 0; q < 3; ++q) rmax = std::max(rmax, std::fabs(r[q]));
-      if (big < 1e-15 || rmax > 10.0) break;
-    }
-    if (!ok) continue;
-    if (std::fabs(r[0]) <= 1.0 + tol && std::fabs(r[1]) <= 1.0 + tol && std::fabs(r[2]) <= 1.0 + tol) {
-      for (int q = 0; q < 3; ++q) ref[q] = std::min(1.0, std::max(-1.0, r[q]));
-      return e;
+namespace {
+
+constexpr double kInsideTol = 1e-9;
+
+// Corner bounding box of element X[8][3], widened by kInsideTol of its largest side.
+void padded_box(const double* X, double* lo, double* hi) {
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = hi[d] = X[d];
+    for (int c = 1; c < 8; ++c) {
+      lo[d] = std::min(lo[d], X[3 * c + d]);
+      hi[d] = std::max(hi[d], X[3 * c + d]);
     }
   }
+  const double pad = kInsideTol * std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  for (int d = 0; d < 3; ++d) {
+    lo[d] -= pad;
+    hi[d] += pad;
+  }
+}
+
+// Whether element X holds x: its padded box does, and Newton's method on the trilinear map
+// from the element centre (at most 60 iterations) ends within kInsideTol of the reference
+// cube; then ref = the solution clipped to [-1, 1].
+bool element_holds(const double* X, const double* x, double* ref) {
+  double lo[3], hi[3];
+  padded_box(X, lo, hi);
+  for (int d = 0; d < 3; ++d)
+    if (!(x[d] >= lo[d] && x[d] <= hi[d])) return false;
+  double r[3] = {0.0, 0.0, 0.0};
+  for (int it = 0; it < 60; ++it) {
+    double p[3], A[3][3], B[3][3];
+    trilinear_map(X, r, p, A);
+    if (!invert3(A, B)) return false;
+    double big = 0.0, rmax = 0.0;
+    for (int q = 0; q < 3; ++q) {
+      const double step = B[q][0] * (p[0] - x[0]) + B[q][1] * (p[1] - x[1]) + B[q][2] * (p[2] - x[2]);
+      r[q] -= step;
+      big = std::max(big, std::fabs(step));
+    }
+    for (int q = 0; q < 3; ++q) rmax = std::max(rmax, std::fabs(r[q]));
+    if (big < 1e-15 || rmax > 10.0) break;
+  }
+  if (!(std::fabs(r[0]) <= 1.0 + kInsideTol && std::fabs(r[1]) <= 1.0 + kInsideTol &&
+        std::fabs(r[2]) <= 1.0 + kInsideTol))
+    return false;
+  for (int q = 0; q < 3; ++q) ref[q] = std::min(1.0, std::max(-1.0, r[q]));
+  return true;
+}
+
+}  // namespace
+
+// Elements in index order; the first that holds x.
+int locate_point(int nspec, const double* ctrl, const double* x, double* ref) {
+  for (int e = 0; e < nspec; ++e)
+    if (element_holds(ctrl + 24 * static_cast<size_t>(e), x, ref)) return e;
   return -1;
+}
+
+// Buckets: a uniform grid of about nspec cells over the union of the padded boxes; every
+// element is listed, in increasing index, in each cell its padded box overlaps. An element
+// that holds x has x in its padded box, so it is listed in x's cell, and the first element
+// of that list that holds x is the lowest-numbered one.
+void locate_points(int nspec, const double* ctrl, int npts, const double* xyz, int32_t* elem, double* ref) {
+  if (npts <= 8 || nspec <= 64) {
+    for (int s = 0; s < npts; ++s) {
+      ref[3 * s] = ref[3 * s + 1] = ref[3 * s + 2] = 0.0;
+      elem[s] = locate_point(nspec, ctrl, xyz + 3 * static_cast<size_t>(s), ref + 3 * static_cast<size_t>(s));
+    }
+    return;
+  }
+  std::vector<double> box(6 * static_cast<size_t>(nspec));
+  double gmin[3] = {0.0, 0.0, 0.0}, gmax[3] = {0.0, 0.0, 0.0};
+  for (int e = 0; e < nspec; ++e) {
+    double* b = box.data() + 6 * static_cast<size_t>(e);
+    padded_box(ctrl + 24 * static_cast<size_t>(e), b, b + 3);
+    for (int d = 0; d < 3; ++d) {
+      gmin[d] = e ? std::min(gmin[d], b[d]) : b[d];
+      gmax[d] = e ? std::max(gmax[d], b[3 + d]) : b[3 + d];
+    }
+  }
+  const int m = std::max(1, static_cast<int>(std::cbrt(static_cast<double>(nspec))));
+  double cell[3];
+  for (int d = 0; d < 3; ++d) cell[d] = std::max((gmax[d] - gmin[d]) / m, 1e-300);
+  auto index = [&](double v, int d) {
+    const double t = std::floor((v - gmin[d]) / cell[d]);
+    return static_cast<int>(std::min(static_cast<double>(m - 1), std::max(0.0, t)));
+  };
+  std::vector<std::vector<int32_t>> bucket(static_cast<size_t>(m) * m * m);
+  for (int e = 0; e < nspec; ++e) {
+    const double* b = box.data() + 6 * static_cast<size_t>(e);
+    int c0[3], c1[3];
+    for (int d = 0; d < 3; ++d) {
+      c0[d] = index(b[d], d);
+      c1[d] = index(b[3 + d], d);
+    }
+    for (int k = c0[2]; k <= c1[2]; ++k)
+      for (int j = c0[1]; j <= c1[1]; ++j)
+        for (int i = c0[0]; i <= c1[0]; ++i) bucket[(static_cast<size_t>(k) * m + j) * m + i].push_back(e);
+  }
+  for (int s = 0; s < npts; ++s) {
+    const double* x = xyz + 3 * static_cast<size_t>(s);
+    double* r = ref + 3 * static_cast<size_t>(s);
+    r[0] = r[1] = r[2] = 0.0;
+    elem[s] = -1;
+    bool inside = true;
+    for (int d = 0; d < 3; ++d) inside = inside && x[d] >= gmin[d] && x[d] <= gmax[d];
+    if (!inside) continue;
+    const auto& list = bucket[(static_cast<size_t>(index(x[2], 2)) * m + index(x[1], 1)) * m + index(x[0], 0)];
+    for (const int32_t e : list)
+      if (element_holds(ctrl + 24 * static_cast<size_t>(e), x, r)) {
+        elem[s] = e;
+        break;
+      }
+    if (elem[s] < 0) r[0] = r[1] = r[2] = 0.0;
+  }
 }
 
 void point_source_forces(int n, const double* xi, const double* h, const double* ctrl_e, const double* ref,

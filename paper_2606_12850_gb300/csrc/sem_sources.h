@@ -3,6 +3,8 @@
 // deterministic; used by sem_capi.cpp.
 #pragma once
 
+#include <cstdint>
+
 namespace semgb {
 
 // Lagrange basis of the ngll nodes xi at an arbitrary x in [-1, 1]: l[i] = l_i(x) and
@@ -12,6 +14,11 @@ void lagrange_at(int ngll, const double* xi, const double* hprime, double x, dou
 // Lowest-numbered element of ctrl[nspec][8][3] that holds the point x[3], and its reference
 // coordinates ref[3] in [-1, 1]; -1 if no element holds it.
 int locate_point(int nspec, const double* ctrl, const double* x, double* ref);
+
+// The same for npts points xyz[npts][3] (elem[npts], ref[npts][3]); for more than a few
+// points the candidate elements come from a uniform grid of buckets over the elements'
+// bounding boxes, with identical results.
+void locate_points(int nspec, const double* ctrl, int npts, const double* xyz, int32_t* elem, double* ref);
 
 // Nodal forces f[ngll^3][3] (local point order) of a point source at reference
 // coordinates ref[3] of the element with corners ctrl_e[8][3]: force[3] gives

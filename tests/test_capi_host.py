@@ -165,6 +165,34 @@ def test_locate_points_matches_oracle(oracle, jittered):
     assert list(elem) == [-1, -1]
 
 
+def test_locate_points_buckets_equal_the_element_scan(oracle):
+    """Many points on a larger mesh go through the bucket grid; the result equals the plain
+    scan over all elements (one point per call) and the oracle, including points on the
+    vertices, edges and faces that several elements share (lowest index) and points outside."""
+    mesh = inputs.structured_hex_mesh(6, 2, 1200.0, jitter=0.2, seed=4)
+    ones = np.ones(mesh.ibool.shape)
+    m = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, ones, 2 * ones, ones, 2)
+    pts = list(inputs.uniform(21, (300, 3), -20.0, 1220.0))
+    pts += [mesh.ctrl[e, c] for e in (43, 86, 129) for c in range(8)]  # vertices shared by up to 8
+    pts += [0.5 * (mesh.ctrl[100, 0] + mesh.ctrl[100, 7])]  # element centre
+    pts += [0.5 * (mesh.ctrl[100, 1] + mesh.ctrl[100, 7])]  # on a face
+    pts = np.array(pts)
+    elem, ref = sem.sem_locate_points(mesh.ctrl, pts)
+    assert (elem >= 0).sum() > 200 and (elem < 0).sum() > 0
+    for q in range(len(pts)):
+        e1, r1 = sem.sem_locate_points(mesh.ctrl, pts[q:q + 1])
+        assert e1[0] == elem[q]
+        np.testing.assert_array_equal(r1[0], ref[q])
+    for q in range(0, len(pts), 7):
+        if elem[q] >= 0:
+            e2, r2 = oracle.locate_point(m, pts[q])
+            assert e2 == elem[q]
+            np.testing.assert_allclose(ref[q], r2, rtol=0, atol=1e-12)
+        else:
+            with pytest.raises(ValueError):
+                oracle.locate_point(m, pts[q])
+
+
 @pytest.mark.parametrize("kind", ["force", "moment"])
 @pytest.mark.parametrize("ngll", [2, 5, 8])
 def test_point_source_forces_match_oracle(oracle, kind, ngll):
