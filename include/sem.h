@@ -69,6 +69,19 @@ int sem_gll(int ngll, double* xi, double* w, double* hprime);
 int sem_color_elements(int nspec, int ngll, int nglob, const int32_t* ibool,
                        int32_t* color, int* ncolors);
 
+/* The patches sem_set_mesh builds for the force sweep (see SEM_OPT_ASSEMBLY), for a mesh
+ * given by ibool alone. Lattice coordinates come from a walk across shared element faces
+ * (the neighbour across an element's own +xi face sits one step along x, and so on), the
+ * patches are bricks of those coordinates (shape from info[4..6]), coloured greedily so
+ * that no two patches of a colour share a node (Sec. IV-C's colouring applied to groups of
+ * elements). Outputs, each caller-owned and may be NULL: patch_of[nspec] the patch of every
+ * element (patches numbered in sweep order, colour after colour), color_of[nspec] the colour
+ * of patch P at index P (entries past the patch count are untouched), info[7] = patches,
+ * colours, largest patch node count, distinct patch tables, brick x, y, z. Host only, no GPU
+ * needed. SEM_EINVAL for bad sizes or an ibool entry out of range. */
+int sem_patch_plan(int ngll, int nspec, int nglob, const int32_t* ibool, int32_t* patch_of, int32_t* color_of,
+                   int64_t* info);
+
 /* Geometry of trilinear hexahedra at their GLL points (Sec. II-B: the mapping of each
  * element to the reference cube and its Jacobian), exactly as sem_set_mesh computes it:
  * the GLL positions from the eight corners, dx/dxi by differentiating those positions with
@@ -124,6 +137,16 @@ int sem_destroy(sem_ctx* ctx);
  *   form, 0 = the order's default (line owners from NGLL 4 up, per point below), 1 = line
  *   owners, 2 = per point; sem_autotune sets it from measurement. */
 #define SEM_OPT_CONTRACTION 2
+/*   SEM_OPT_ASSEMBLY (takes effect at once): how the force sweep assembles element forces
+ *   on the context's own single-shot fields. 0 (default) = patches: bricks of neighbouring
+ *   elements (2 x 2 x 2 at NGLL 5; sem_patch_info gives the shape) evaluated by one CTA
+ *   each, which gathers the brick's distinct nodes once, sums the forces meeting at each of
+ *   them in a fixed order and writes each once; the bricks are coloured so that no two of
+ *   a colour share a node (Sec. IV-C's colouring applied to groups of elements). 1 =
+ *   element by element, one launch per element colour (the form always used for several
+ *   shots and for caller-layout arrays). Both are deterministic; they differ only in the
+ *   order of the float32 sums at shared nodes. */
+#define SEM_OPT_ASSEMBLY 3
 int sem_set_option(sem_ctx* ctx, int option, long long value);
 
 /* Set the mesh (Sec. II-B hexahedral mesh, Sec. IV-C global-to-local map).
@@ -255,14 +278,26 @@ int sem_run_snapshots(sem_ctx* ctx, int nsteps, float* u_dev);
 int sem_check_finite(sem_ctx* ctx);
 
 /* One matrix-free stiffness application on the device: f_dev = -K u_dev, both
- * [nglob][3] float32 (Sec. II-B). Every node of f_dev is written. u_dev and f_dev must not
- * overlap. Asynchronous on the context's stream. Does not touch the solver state. */
+ * [nglob][3] float32 in the caller's node order (Sec. II-B), by the element kernel, colour
+ * by colour. Every node of f_dev is written. u_dev and f_dev must not overlap. Allocates
+ * nothing. Asynchronous on the context's stream. Does not touch the solver state. */
 int sem_apply_stiffness(sem_ctx* ctx, const float* u_dev, float* f_dev);
 
-/* Same with node_stride floats per node (3 or 4; with 4, x y z and an ignored 4th value,
- * arrays 16-byte aligned): [nglob][node_stride]. Stride 4 is the layout the solver keeps
- * its own fields in, so this times the force kernel exactly as a time step runs it. */
+/* Same with node_stride floats per node, 3 or 4. Stride 3 is sem_apply_stiffness. Stride 4
+ * is the solver's own field layout: [nglob][4] float32 (x, y, z and a 4th value that is
+ * ignored and written as 0, arrays 16-byte aligned) in the solver's internal node order
+ * (internal node i is caller node perm[i] of sem_node_order), evaluated by the kernel a
+ * time step runs (SEM_OPT_ASSEMBLY), so this times the force sweep exactly as a step does. */
 int sem_apply_stiffness_strided(sem_ctx* ctx, const float* u_dev, float* f_dev, int node_stride);
+
+/* The solver's internal node order: perm[i] = caller node of internal node i, int32[nglob].
+ * sem_set_mesh numbers the nodes so that every patch of the force sweep finds its nodes in
+ * runs: the nodes a patch touches first (patch colour by patch colour) get consecutive
+ * numbers, grouped by the set of patches that share them. Every call that takes or returns
+ * node data (states, snapshots, sources, receivers, sem_apply_stiffness, sem_node_xyz)
+ * uses the caller's order; only sem_apply_stiffness_strided with stride 4 uses this one.
+ * SEM_ESTATE before sem_set_mesh. */
+int sem_node_order(sem_ctx* ctx, int32_t* perm);
 
 /* Discrete adjoint and material sensitivities of a seismogram loss L (one shot). From a
  * zero state the scheme is the leapfrog M(u^{n+1} - 2u^n + u^{n-1}) + dt^2 (K u^n - f^n) = 0
@@ -318,8 +353,8 @@ int sem_energy(sem_ctx* ctx, double* out);
  * is owned by another runtime's pool, or a caller inside a region that must not allocate.
  * The paper has no counterpart; it is a variant of the reduction behind sem_energy.
  * Inputs: u_dev, v_dev, f_dev device arrays [nglob][3] float32 on the context's GPU, with
- * f_dev = -K u_dev (for instance from sem_apply_stiffness, which allocates nothing); the
- * context supplies the inverse mass. Output: out[0] = 1/2 sum_I M_I |v_I|^2,
+ * f_dev = -K u_dev (for instance from sem_apply_stiffness, which allocates nothing), all in
+ * the caller's node order; the context supplies the inverse mass. Output: out[0] = 1/2 sum_I M_I |v_I|^2,
  * out[1] = -1/2 u.f = 1/2 u^T K u, host memory, float64. nglob must equal the mesh's.
  * Scratch: the per-block partial sums go to a fixed 64 KiB array in the library's device
  * memory (one per GPU that loads the library, held until the process exits), never to
@@ -327,8 +362,10 @@ int sem_energy(sem_ctx* ctx, double* out);
  * 67,108,864 nodes and returns SEM_EINVAL with a message beyond that. All calls share the
  * array, which keeps the last call's contents, so calls that overlap on the GPU (from
  * several threads or contexts at once) race; each call rewrites every slot it reads.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture. Synchronous on the context's stream. */
+ * Every call looks up the array's device address on the context's device
+ * (cudaGetSymbolAddress, which allocates nothing). The call synchronizes with the context's
+ * stream, so it must not be made while that stream is capturing a graph: it then returns
+ * SEM_ESTATE without doing anything. Synchronous on the context's stream. */
 int sem_energy_noalloc(sem_ctx* ctx, int nglob, const float* u_dev, const float* v_dev, const float* f_dev,
                        double* out);
 
@@ -343,6 +380,13 @@ int sem_info(sem_ctx* ctx, int64_t* out);
 
 /* Element count of each colour, counts[ncolors] (see sem_info for ncolors). */
 int sem_color_counts(sem_ctx* ctx, int32_t* counts);
+
+/* The patches of the force sweep (SEM_OPT_ASSEMBLY): out[0] patches, out[1] patch colours
+ * (launches per sweep), out[2] largest patch node count, out[3] distinct patch tables (one
+ * for every patch of the same local structure), out[4..6] the brick in elements along the
+ * mesh's lattice x, y, z, out[7] the assembly option in force. out has room for 8 values.
+ * SEM_ESTATE before sem_set_mesh. */
+int sem_patch_info(sem_ctx* ctx, int64_t* out);
 
 /* Message of the last failed call on ctx, or of the last failed context-free call when
  * ctx is NULL. Owned by the library; valid until the next call on the same ctx. */

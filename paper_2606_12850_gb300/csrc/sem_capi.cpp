@@ -37,15 +37,20 @@ struct sem_ctx {
   bool have_mesh = false, have_mat = false, have_dt = false;
   int nspec = 0, nglob = 0, ncolors = 0;
   std::vector<int32_t> ibool;       // caller order
-  std::vector<int> order;           // colour-sorted position -> caller element
-  std::vector<int> pos_of;          // caller element -> colour-sorted position
+  std::vector<int> order;           // record slot -> caller element (patch sweep order)
+  std::vector<int> pos_of;          // caller element -> record slot
   std::vector<int> color_count;     // elements per colour
-  std::vector<int> sweep_off;       // record-slot ranges, one per (slab, colour) launch
+  std::vector<int> sweep_off;       // element-list ranges, one per (slab, colour) launch
+  std::vector<int> pcolor_off;      // patch ranges, one per patch colour
+  int npatch = 0, pmax_nodes = 0, ptables = 0;
+  int assembly = 0;                 // SEM_OPT_ASSEMBLY: 0 patches where they apply, 1 elements
   int slabs = 1;                    // spatial slabs of the sweep order
   int slabs_opt = 0;                // requested slab count (0 = automatic)
   std::vector<float> rec;           // colour-sorted element records (host copy)
   std::vector<double> dxmin;        // per caller element
-  std::vector<double> node_xyz;     // [nglob][3]
+  std::vector<double> node_xyz;     // [nglob][3], caller node order
+  std::vector<int> node_new;        // caller node -> internal node
+  std::vector<int> perm;            // internal node -> caller node
   std::vector<double> ctrl;         // [nspec][8][3] corner vertices (caller order)
   std::vector<double> vpmax;        // per caller element
   double dt = 0.0;
@@ -53,6 +58,12 @@ struct sem_ctx {
   // device
   float* d_rec = nullptr;
   int* d_order = nullptr;         // record slot -> caller element
+  int* d_elist = nullptr;         // record slots in element colour order
+  int* d_perm = nullptr;          // internal node -> caller node
+  int* d_node_new = nullptr;      // caller node -> internal node
+  PatchDesc* d_pdesc = nullptr;   // patches in sweep order
+  uint16_t* d_pslots = nullptr;   // patch tables: shared patch node -> local points meeting there
+  uint32_t* d_pexcl = nullptr;    // patch tables: local points alone at their patch node
   float *d_u = nullptr, *d_v = nullptr, *d_a = nullptr, *d_minv = nullptr;
   float* d_f = nullptr;           // scratch force buffer for sem_energy
   float *d_lam = nullptr, *d_lam_old = nullptr, *d_lamF = nullptr;  // adjoint fields [nglob][4]
@@ -121,13 +132,19 @@ int dev_alloc(sem_ctx* c, T** p, size_t count) {
 }
 
 void free_device(sem_ctx* c) {
-  void* ptrs[] = {c->d_rec, c->d_order, c->d_u, c->d_v, c->d_a, c->d_minv, c->d_f, c->d_partials, c->d_lam, c->d_lam_old,
-                  c->d_lamF, c->d_grad,
+  void* ptrs[] = {c->d_rec, c->d_order, c->d_elist, c->d_perm, c->d_node_new, c->d_pdesc, c->d_pslots, c->d_pexcl, c->d_u, c->d_v,
+                  c->d_a, c->d_minv, c->d_f, c->d_partials, c->d_lam, c->d_lam_old, c->d_lamF, c->d_grad,
                   c->d_ctl, c->d_src_node, c->d_src_shot, c->d_src_force, c->d_rec_node};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->d_rec = nullptr;
   c->d_order = nullptr;
+  c->d_elist = nullptr;
+  c->d_perm = nullptr;
+  c->d_node_new = nullptr;
+  c->d_pdesc = nullptr;
+  c->d_pslots = nullptr;
+  c->d_pexcl = nullptr;
   c->d_u = c->d_v = c->d_a = c->d_minv = c->d_f = nullptr;
   c->d_lam = c->d_lam_old = c->d_lamF = nullptr;
   c->d_grad = nullptr;
@@ -177,13 +194,32 @@ int set_device(sem_ctx* c) {
   return SEM_OK;
 }
 
-// f = -K u over all colours (Sec. IV-C: colour by colour, no atomics). The launches walk
-// the mesh slab by slab and, inside a slab, colour by colour: a launch holds elements of
-// one colour only, so no two of its elements share a node, and the nodes of one slab stay
-// in L2 across its colour launches.
+// f = -K u over all colours (Sec. IV-C: colour by colour, no atomics). On the context's own
+// single-shot fields the patch kernel takes the patch colours in order (one launch per
+// colour; patches of a colour share no node). Otherwise (several shots, caller arrays, or
+// SEM_OPT_ASSEMBLY = 1) the element kernel walks the element list slab by slab and, inside a
+// slab, colour by colour: a launch holds elements of one colour only.
 int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int shots) {
+  if (c->assembly == 0 && node_stride == kNodeStride && shots == 1 && c->npatch > 0) {
+    PatchLaunch P{};
+    P.rec = c->d_rec;
+    P.desc = c->d_pdesc;
+    P.slots = c->d_pslots;
+    P.excl = c->d_pexcl;
+    P.u = u;
+    P.f = f;
+    P.variant = c->variant;
+    for (size_t k = 0; k + 1 < c->pcolor_off.size(); ++k) {
+      P.p0 = c->pcolor_off[k];
+      P.p1 = c->pcolor_off[k + 1];
+      SEM_LAUNCH(c, launch_patch_forces(c->ngll, P, c->stream));
+    }
+    return SEM_OK;
+  }
   ForceLaunch L{};
   L.rec = c->d_rec;
+  L.elist = c->d_elist;
+  L.perm = c->d_perm;
   L.u = u;
   L.f = f;
   L.node_stride = node_stride;
@@ -287,6 +323,7 @@ int ctx_view(sem_ctx* c, CtxView* out) {
   out->stream = c->stream;
   out->nglob = c->nglob;
   out->minv = c->d_minv;
+  out->node_new = c->d_node_new;
   return SEM_OK;
 }
 
@@ -314,6 +351,37 @@ int sem_color_elements(int nspec, int ngll, int nglob, const int32_t* ibool, int
   std::string err;
   if (color_elements(nspec, ngll, nglob, ibool, &col, ncolors, &err)) return fail(nullptr, SEM_EINVAL, err);
   std::memcpy(color, col.data(), sizeof(int32_t) * nspec);
+  return SEM_OK;
+}
+
+int sem_patch_plan(int ngll, int nspec, int nglob, const int32_t* ibool, int32_t* patch_of, int32_t* color_of,
+                   int64_t* info) {
+  if (nspec < 1 || nglob < 1 || !ibool || ngll < kMinNgll || ngll > kMaxNgll)
+    return fail(nullptr, SEM_EINVAL, "sem_patch_plan: bad arguments");
+  const int np = ngll * ngll * ngll;
+  const size_t nloc = static_cast<size_t>(nspec) * np;
+  for (size_t q = 0; q < nloc; ++q)
+    if (ibool[q] < 0 || ibool[q] >= nglob) return fail(nullptr, SEM_EINVAL, "ibool entry out of range");
+  PatchShape shape;
+  PatchPlan plan;
+  std::string err;
+  if (patch_shape(ngll, &shape) || build_patches(nspec, ngll, nglob, ibool, shape, &plan, &err))
+    return fail(nullptr, SEM_EINVAL, "sem_patch_plan: " + err);
+  for (int c = 0; c < plan.ncolors; ++c)
+    for (int P = plan.color_off[c]; P < plan.color_off[c + 1]; ++P) {
+      if (color_of) color_of[P] = c;
+      if (patch_of)
+        for (int s = plan.patch_off[P]; s < plan.patch_off[P + 1]; ++s) patch_of[plan.elem[s]] = P;
+    }
+  if (info) {
+    info[0] = plan.npatch;
+    info[1] = plan.ncolors;
+    info[2] = plan.max_nodes;
+    info[3] = static_cast<int64_t>(plan.tab_nelem.size());
+    info[4] = shape.bx;
+    info[5] = shape.by;
+    info[6] = shape.bz;
+  }
   return SEM_OK;
 }
 
@@ -439,6 +507,11 @@ int sem_set_option(sem_ctx* c, int option, long long value) {
       c->variant = static_cast<int>(value);
       drop_graph(c);
       return SEM_OK;
+    case SEM_OPT_ASSEMBLY:
+      if (value < 0 || value > 1) return fail(c, SEM_EINVAL, "assembly must be 0 (patches) or 1 (elements)");
+      c->assembly = static_cast<int>(value);
+      drop_graph(c);
+      return SEM_OK;
     default:
       return fail(c, SEM_EINVAL, "unknown option " + std::to_string(option));
   }
@@ -498,8 +571,21 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
     }
   }
 
-  // sweep order: spatial slabs along the longest axis of the element centroids (equal
-  // element counts), colour by colour inside a slab, caller order inside a colour
+  // patches (bricks of the lattice coordinates, coloured) give the record order
+  PatchShape shape;
+  PatchPlan plan;
+  if (patch_shape(n, &shape) || build_patches(nspec, n, nglob, ibool, shape, &plan, &err))
+    return fail(c, SEM_EINVAL, "patches: " + err);
+  c->order = plan.elem;
+  c->node_new = plan.node_new;
+  c->perm.assign(nglob, 0);
+  for (int g = 0; g < nglob; ++g) c->perm[c->node_new[g]] = g;
+  c->pos_of.assign(nspec, 0);
+  for (int s = 0; s < nspec; ++s) c->pos_of[c->order[s]] = s;
+
+  // element list for the element kernel: spatial slabs along the longest axis of the
+  // element centroids (equal element counts), colour by colour inside a slab, caller order
+  // inside a colour
   const int K = std::max(1, std::min(c->slabs_opt, nspec));
   std::vector<int> slab(nspec, 0);
   if (K > 1) {
@@ -531,22 +617,19 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   for (size_t k = 0; k < cnt.size(); ++k)
     if (cnt[k] > 0) c->sweep_off.push_back(off[k + 1]);
   c->slabs = K;
-  c->order.assign(nspec, 0);
-  c->pos_of.assign(nspec, 0);
+  std::vector<int> elist(nspec, 0);
   {
     std::vector<int> fillp(off.begin(), off.end() - 1);
-    for (int e = 0; e < nspec; ++e) {
-      const int s = fillp[static_cast<size_t>(slab[e]) * ncolors + color[e]]++;
-      c->order[s] = e;
-      c->pos_of[e] = s;
-    }
+    for (int e = 0; e < nspec; ++e) elist[fillp[static_cast<size_t>(slab[e]) * ncolors + color[e]]++] = c->pos_of[e];
   }
 
-  // element records, colour-sorted, with the first-touch flag on ibool
+  // element records in patch sweep order; the ibool words carry the first-touch flag of the
+  // element kernel's order (the patch kernel has its own, in the patch node lists)
   const int RW = rec_words(n);
   c->rec.assign(static_cast<size_t>(nspec) * RW, 0.f);
   std::vector<char> touched(nglob, 0);
-  for (int s = 0; s < nspec; ++s) {
+  for (int t = 0; t < nspec; ++t) {
+    const int s = elist[t];
     const int e = c->order[s];
     float* r = c->rec.data() + static_cast<size_t>(s) * RW;
     const float* gq = geom.data() + static_cast<size_t>(e) * 10 * np;
@@ -555,15 +638,43 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
         for (int i = 0; i < n; ++i) {
           const int p = i + n * (j + n * k);
           const int q = rec_pos(n, i, j, k);
-          uint32_t g = static_cast<uint32_t>(ibool[static_cast<size_t>(e) * np + p]);
+          uint32_t g = static_cast<uint32_t>(c->node_new[ibool[static_cast<size_t>(e) * np + p]]);
           if (!touched[g]) {
             touched[g] = 1;
             g |= kFirstTouchBit;
           }
           std::memcpy(&r[kIbool * np + p], &g, sizeof(uint32_t));
-          for (int a = 0; a < 10; ++a) r[(kG + a) * np + q] = gq[a * np + p];
+          for (int a = 0; a < 9; ++a) r[(kG + a) * np + q] = gq[a * np + p];
+          r[kJac * np + q] = gq[9 * np + p];
         }
   }
+  // patch descriptors; the first touch of every node in patch-colour order is flagged on the
+  // ibool word of its first local point in that patch's table
+  std::vector<PatchDesc> pdesc(plan.npatch);
+  for (int P = 0; P < plan.npatch; ++P) {
+    PatchDesc& d = pdesc[P];
+    const int t = plan.table_of[P];
+    d.slot0 = plan.patch_off[P];
+    d.nelem = plan.patch_off[P + 1] - plan.patch_off[P];
+    d.nshared = plan.tab_nshared[t];
+    d.slot_off = plan.tab_csr_off[t];
+    d.excl_off = plan.tab_excl_off[t];
+    d.pad0 = d.pad1 = d.pad2 = 0;
+    const int nnode = plan.node_off[P + 1] - plan.node_off[P];
+    for (int k = 0; k < nnode; ++k) {
+      if (!(plan.nodes[plan.node_off[P] + k] & kFirstTouchBit)) continue;
+      const int q0 = plan.first_q[static_cast<size_t>(plan.tab_first_off[t]) + k];
+      float* r = c->rec.data() + static_cast<size_t>(d.slot0 + q0 / np) * RW;
+      uint32_t wd;
+      std::memcpy(&wd, &r[kIbool * np + q0 % np], sizeof(uint32_t));
+      wd |= kPatchFirstBit;
+      std::memcpy(&r[kIbool * np + q0 % np], &wd, sizeof(uint32_t));
+    }
+  }
+  c->pcolor_off = plan.color_off;
+  c->npatch = plan.npatch;
+  c->pmax_nodes = plan.max_nodes;
+  c->ptables = static_cast<int>(plan.tab_nelem.size());
 
   c->ibool.assign(ibool, ibool + nloc);
   c->ctrl.assign(ctrl, ctrl + 24 * static_cast<size_t>(nspec));
@@ -587,13 +698,29 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   c->dev_bytes = sizeof(DevCtl);
   const size_t nf = kNodeStride * static_cast<size_t>(nglob) * c->shots;
   if ((r = dev_alloc(c, &c->d_rec, c->rec.size())) || (r = dev_alloc(c, &c->d_order, c->order.size())) ||
-      (r = dev_alloc(c, &c->d_u, nf)) || (r = dev_alloc(c, &c->d_v, nf)) || (r = dev_alloc(c, &c->d_a, nf)) ||
+      (r = dev_alloc(c, &c->d_elist, elist.size())) || (r = dev_alloc(c, &c->d_pdesc, pdesc.size())) ||
+      (r = dev_alloc(c, &c->d_perm, c->perm.size())) || (r = dev_alloc(c, &c->d_node_new, c->node_new.size())) ||
+      (r = dev_alloc(c, &c->d_pslots, std::max<size_t>(plan.csr.size(), kPatchSlots))) ||
+      (r = dev_alloc(c, &c->d_pexcl, plan.excl.size())) || (r = dev_alloc(c, &c->d_u, nf)) ||
+      (r = dev_alloc(c, &c->d_v, nf)) || (r = dev_alloc(c, &c->d_a, nf)) ||
       (r = dev_alloc(c, &c->d_minv, static_cast<size_t>(nglob))))
     return r;
   // geometry and ibool travel once; the material fields are written on the device
   SEM_CUDA(c, cudaMemcpyAsync(c->d_rec, c->rec.data(), c->rec.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   SEM_CUDA(c, cudaMemcpyAsync(c->d_order, c->order.data(), c->order.size() * sizeof(int), cudaMemcpyHostToDevice,
                               c->stream));
+  SEM_CUDA(c, cudaMemcpyAsync(c->d_elist, elist.data(), elist.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  SEM_CUDA(c, cudaMemcpyAsync(c->d_perm, c->perm.data(), c->perm.size() * sizeof(int), cudaMemcpyHostToDevice,
+                              c->stream));
+  SEM_CUDA(c, cudaMemcpyAsync(c->d_node_new, c->node_new.data(), c->node_new.size() * sizeof(int),
+                              cudaMemcpyHostToDevice, c->stream));
+  SEM_CUDA(c, cudaMemcpyAsync(c->d_pdesc, pdesc.data(), pdesc.size() * sizeof(PatchDesc), cudaMemcpyHostToDevice,
+                              c->stream));
+  if (!plan.csr.empty())
+    SEM_CUDA(c, cudaMemcpyAsync(c->d_pslots, plan.csr.data(), plan.csr.size() * sizeof(uint16_t),
+                                cudaMemcpyHostToDevice, c->stream));
+  SEM_CUDA(c, cudaMemcpyAsync(c->d_pexcl, plan.excl.data(), plan.excl.size() * sizeof(uint32_t),
+                              cudaMemcpyHostToDevice, c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_u, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_v, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_a, 0, nf * sizeof(float), c->stream));
@@ -611,6 +738,7 @@ static int material_apply(sem_ctx* c, const float* rho, const float* p1, const f
   MaterialLaunch m{};
   m.rec = c->d_rec;
   m.order = c->d_order;
+  m.elist = c->d_elist;
   m.rho = rho;
   m.p1 = p1;
   m.p2 = p2;
@@ -769,12 +897,13 @@ static int set_sources_impl(sem_ctx* c, int nsrc, const int32_t* shot, const int
       if (!std::isfinite(force[3 * s + d])) return fail(c, SEM_EINVAL, "non-finite source force");
     const int first = shot ? shot[s] : 0, last = shot ? shot[s] : c->shots - 1;
     for (int sh = first; sh <= last; ++sh) {
-      const int64_t key = static_cast<int64_t>(sh) * c->nglob + node[s];
+      const int g = c->node_new[node[s]];  // internal node
+      const int64_t key = static_cast<int64_t>(sh) * c->nglob + g;
       const auto found = entry.find(key);
       const size_t m = found == entry.end() ? nodes.size() : found->second;
       if (m == nodes.size()) {
         entry.emplace(key, m);
-        nodes.push_back(node[s]);
+        nodes.push_back(g);
         shots.push_back(sh);
         forces.insert(forces.end(), force + 3 * s, force + 3 * s + 3);
       } else {
@@ -937,7 +1066,9 @@ int sem_set_receivers(sem_ctx* c, int nrec, const int32_t* node) {
   c->dev_bytes -= c->nrec * sizeof(int);
   c->nrec = nrec;
   if ((r = dev_alloc(c, &c->d_rec_node, static_cast<size_t>(nrec)))) return r;
-  if (nrec > 0) SEM_CUDA(c, cudaMemcpy(c->d_rec_node, node, nrec * sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<int> internal(nrec);
+  for (int k = 0; k < nrec; ++k) internal[k] = c->node_new[node[k]];
+  if (nrec > 0) SEM_CUDA(c, cudaMemcpy(c->d_rec_node, internal.data(), nrec * sizeof(int), cudaMemcpyHostToDevice));
   drop_graph(c);
   return SEM_OK;
 }
@@ -966,7 +1097,8 @@ static int set_state_impl(sem_ctx* c, const float* u, const float* v, const floa
         e = cudaMemcpyAsync(stage, src[q], n3 * sizeof(float), cudaMemcpyHostToDevice, c->stream);
         from = stage;
       }
-      if (e == cudaSuccess) e = static_cast<cudaError_t>(launch_unpack(from, dst[q], c->nglob, c->shots, c->stream));
+      if (e == cudaSuccess)
+        e = static_cast<cudaError_t>(launch_unpack(from, dst[q], c->d_perm, c->nglob, c->shots, c->stream));
     }
     if (e != cudaSuccess) rc = cuda_fail(c, e, "sem_set_state copy");
   }
@@ -1013,7 +1145,8 @@ static int get_state_impl(sem_ctx* c, float* u, float* v, float* a, cudaMemcpyKi
   int rc = SEM_OK;
   for (int q = 0; q < 3 && rc == SEM_OK; ++q) {
     if (!dst[q]) continue;
-    cudaError_t e = static_cast<cudaError_t>(launch_pack(src[q], host ? stage : dst[q], c->nglob, c->shots, c->stream));
+    cudaError_t e =
+        static_cast<cudaError_t>(launch_pack(src[q], host ? stage : dst[q], c->d_perm, c->nglob, c->shots, c->stream));
     if (e == cudaSuccess && host) e = cudaMemcpyAsync(dst[q], stage, n3 * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) rc = cuda_fail(c, e, "sem_get_state copy");
   }
@@ -1048,7 +1181,7 @@ int sem_run_snapshots(sem_ctx* c, int nsteps, float* u_dev) {
   const size_t per = 3 * static_cast<size_t>(c->nglob) * c->shots;
   for (int k = 0; k < nsteps; ++k) {
     if ((r = advance(c, 1, nullptr))) return r;
-    SEM_LAUNCH(c, launch_pack(c->d_u, u_dev + k * per, c->nglob, c->shots, c->stream));
+    SEM_LAUNCH(c, launch_pack(c->d_u, u_dev + k * per, c->d_perm, c->nglob, c->shots, c->stream));
   }
   return SEM_OK;
 }
@@ -1107,6 +1240,13 @@ int sem_apply_stiffness_strided(sem_ctx* c, const float* u_dev, float* f_dev, in
   int r = set_device(c);
   if (r) return r;
   return forces_all_colors(c, u_dev, f_dev, node_stride, 1);
+}
+
+int sem_node_order(sem_ctx* c, int32_t* perm) {
+  if (!c || !perm) return fail(c, SEM_EINVAL, "sem_node_order: bad arguments");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  std::memcpy(perm, c->perm.data(), c->perm.size() * sizeof(int32_t));
+  return SEM_OK;
 }
 
 int sem_init_acceleration(sem_ctx* c) {
@@ -1176,6 +1316,22 @@ int sem_info(sem_ctx* c, int64_t* out) {
   return SEM_OK;
 }
 
+int sem_patch_info(sem_ctx* c, int64_t* out) {
+  if (!c || !out) return fail(c, SEM_EINVAL, "sem_patch_info: bad arguments");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  PatchShape shape;
+  patch_shape(c->ngll, &shape);
+  out[0] = c->npatch;
+  out[1] = static_cast<int64_t>(c->pcolor_off.size()) - 1;
+  out[2] = c->pmax_nodes;
+  out[3] = c->ptables;
+  out[4] = shape.bx;
+  out[5] = shape.by;
+  out[6] = shape.bz;
+  out[7] = c->assembly;
+  return SEM_OK;
+}
+
 int sem_color_counts(sem_ctx* c, int32_t* counts) {
   if (!c || !counts) return fail(c, SEM_EINVAL, "sem_color_counts: bad arguments");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
@@ -1221,8 +1377,8 @@ int sem_adjoint_accumulate(sem_ctx* c, const float* u_lo, const float* u_mid, co
   int r = set_device(c);
   if (r) return r;
   const size_t nloc = static_cast<size_t>(c->nspec) * c->ngll * c->ngll * c->ngll;
-  SEM_LAUNCH(c, launch_sensitivity(c->ngll, c->d_rec, c->d_lam, u_lo, u_mid, u_hi, c->d_grad, c->d_grad + nloc,
-                                    c->d_grad + 2 * nloc, c->nspec, -1.0, -c->dt * c->dt, c->stream));
+  SEM_LAUNCH(c, launch_sensitivity(c->ngll, c->d_rec, c->d_perm, c->d_lam, u_lo, u_mid, u_hi, c->d_grad,
+                                    c->d_grad + nloc, c->d_grad + 2 * nloc, c->nspec, -1.0, -c->dt * c->dt, c->stream));
   return SEM_OK;
 }
 

@@ -4,6 +4,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "sem_internal.h"
 
 #define SEM_CAT2(a, b) a##b
@@ -19,6 +21,21 @@ namespace {
 __constant__ float c_h[SEM_NGLL * SEM_NGLL];   // hprime[i*n + l] = l_l'(xi_i)
 __constant__ float c_hw[SEM_NGLL * SEM_NGLL];  // [l*n + i] = w_l * hprime[l][i]
 __constant__ float c_w[SEM_NGLL];
+__constant__ float2 c_h2[SEM_NGLL * SEM_NGLL];   // (hprime, hprime) pairs, c_h layout
+__constant__ float2 c_hw2[SEM_NGLL * SEM_NGLL];  // (w hprime, w hprime) pairs, c_hw layout
+
+// Packed float32 pair: d = a * b + c on both halves, each rounded to nearest as a scalar
+// fma would be (one instruction for the pair on sm_100 and later).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long ra, rb, rc, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
 
 // ---------------------------------------------------------------------------------------
 // Force kernel (Sec. II-B matrix-free stiffness action + Sec. IV-C coloured assembly).
@@ -94,96 +111,30 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 __device__ __forceinline__ void wait_prerequisite_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_dependent_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Barrier of one team: the warp, a named barrier (1 + team) over the team's two warps, or
-// the CTA.
-template <int KIND>
+// Barrier of one team: the warp, a named barrier (1 + team) over the team's TEAM threads
+// (several warps), or the CTA.
+template <int KIND, int TEAM>
 __device__ __forceinline__ void team_sync(int team) {
   if constexpr (KIND == 0) {
     __syncwarp();
   } else if constexpr (KIND == 1) {
-    asm volatile("bar.sync %0, 64;" ::"r"(1 + team) : "memory");
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "n"(TEAM) : "memory");
   } else {
     __syncthreads();
   }
 }
 
-// VS: floats per node in u and f (4 for the context's own padded fields, 3 for caller arrays).
-// With S shots (VS = 4 only) the fields are [nglob][S][4] and the launch works on the items
-// (element, shot) of elements e0 .. e1-1, element-major: the teams of a CTA take the shots
-// of one element, so its record is read from DRAM once for all of them.
-template <int N, int VS, bool MS, bool LO>
-__global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
-    forces_kernel(const float* __restrict__ rec, const float* __restrict__ u, float* __restrict__ f, int e0,
-                  int e1, int S_arg) {
-  const int S = MS ? S_arg : 1;  // shots (a compile-time 1 for the single-shot kernel)
-  using C = ForceCfg<N>;
-  constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
-  extern __shared__ float4 smem4[];
+// Phases 2-3 of one team's elements (Sec. II-B): on entry the u slots of every active
+// element workspace (ES floats per element, E = TEAM / NGLL^2 elements from ts on) hold the
+// element's displacement [NP][3]; on return they hold its forces F = -K_e u_e [NP][3].
+// rec_of(le) gives the record of the team's element le. Shared by the element kernel and
+// the patch kernel, which differ only in how they gather u and assemble F.
+template <int N, int KIND, int TEAM, int ES, bool LO, class RecOf>
+__device__ __forceinline__ void team_element_forces(float* ts, int tl, int ne, int team, RecOf rec_of) {
+  constexpr int NP = N * N * N, NL = N * N;
   const float* __restrict__ H = c_h;
   const float* __restrict__ HW = c_hw;
   const float* __restrict__ W = c_w;
-
-  const int team = threadIdx.x / TEAM;
-  const int tl = threadIdx.x - team * TEAM;
-  const int ibase = (blockIdx.x * C::TEAMS + team) * E;  // first item of the team
-  const int ne = min(E, (e1 - e0) * S - ibase);
-  if (C::KIND != 2 && ne <= 0) return;  // a team without items (its barrier is its own)
-  float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
-  // element and shot of the team's slot le
-  auto elem_of = [&](int le) { return e0 + (MS ? (ibase + le) / S : ibase + le); };
-  auto shot_of = [&](int le) { return MS ? (ibase + le) % S : 0; };
-
-  // 0. records to L2 while the previous grid finishes, then wait for its results
-  if (tl < ne) prefetch_l2(rec + static_cast<size_t>(elem_of(tl)) * REC, REC * sizeof(float));
-  wait_prerequisite_grid();
-  allow_dependent_grid();
-
-  // 1. gather, one thread per local point; GB points per thread at a time, their ibool
-  //    words first and then their nodes, so that the loads of a group are all in flight
-  constexpr int GB = 4;
-  for (int base = tl; base < ne * NP; base += GB * TEAM) {
-    uint32_t w[GB];
-#pragma unroll
-    for (int r = 0; r < GB; ++r) {
-      const int idx = base + r * TEAM;
-      const int le = idx / NP;
-      w[r] = idx < ne * NP ? __float_as_uint(__ldg(rec + static_cast<size_t>(elem_of(le)) * REC + (idx - le * NP)))
-                           : 0u;
-    }
-    float q[GB][3];
-#pragma unroll
-    for (int r = 0; r < GB; ++r) {
-      const size_t g = w[r] & ~kFirstTouchBit;
-      if (base + r * TEAM < ne * NP) {
-        if (VS == 4) {
-          const int le = (base + r * TEAM) / NP;
-          const float4 v = __ldg(reinterpret_cast<const float4*>(u) + g * S + shot_of(le));
-          q[r][0] = v.x;
-          q[r][1] = v.y;
-          q[r][2] = v.z;
-        } else {
-          q[r][0] = __ldg(u + 3 * g);
-          q[r][1] = __ldg(u + 3 * g + 1);
-          q[r][2] = __ldg(u + 3 * g + 2);
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < GB; ++r) {
-      const int idx = base + r * TEAM;
-      if (idx < ne * NP) {
-        const int le = idx / NP;
-        const int p = idx - le * NP;
-        float* eb = ts + le * ES;
-        reinterpret_cast<uint32_t*>(eb + 9 * NP)[p] = w[r];
-        eb[3 * p] = q[r][0];
-        eb[3 * p + 1] = q[r][1];
-        eb[3 * p + 2] = q[r][2];
-      }
-    }
-  }
-  team_sync<C::KIND>(team);
-
   if constexpr (LO) {
     // Thread tl of the team owns one line of NGLL points of element le = tl / NL, indexed by
     // line = a + N b: the xi-line (j, k) = (a, b) in phases 2b and 4, the eta-line
@@ -198,59 +149,58 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     float* su = ts + (active ? le : 0) * ES;  // u, then F: [NP][3]
     float* se = su + 3 * NP;                   // eta derivatives, then eta fluxes [NP][3]
     float* sz = su + 6 * NP;                   // zeta derivatives, then zeta fluxes [NP][3]
-    const float* __restrict__ r = rec + static_cast<size_t>(elem_of(active ? le : 0)) * REC;
+    const float* __restrict__ r = rec_of(active ? le : 0);
 
     // 2a. eta derivatives along the eta-line (i, k) = (a, b), zeta derivatives along the
     //     zeta-line (i, j) = (a, b)
+    //     (each eta value paired with the zeta value it shares a coefficient with: one
+    //     packed fma per pair)
     if (active) {
-      float ve[3][N], vz[3][N];
+      float2 v[3][N];  // (eta-line value, zeta-line value)
 #pragma unroll
       for (int l = 0; l < N; ++l)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          ve[c][l] = su[3 * (a + N * (l + N * b)) + c];
-          vz[c][l] = su[3 * (a + N * (b + N * l)) + c];
-        }
+        for (int c = 0; c < 3; ++c)
+          v[c][l] = make_float2(su[3 * (a + N * (l + N * b)) + c], su[3 * (a + N * (b + N * l)) + c]);
 #pragma unroll
       for (int m = 0; m < N; ++m)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          float de = 0.f, dz = 0.f;
+          float2 d = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int l = 0; l < N; ++l) {
-            de += H[m * N + l] * ve[c][l];
-            dz += H[m * N + l] * vz[c][l];
-          }
-          se[3 * (a + N * (m + N * b)) + c] = de;
-          sz[3 * (a + N * (b + N * m)) + c] = dz;
+          for (int l = 0; l < N; ++l) d = ffma2(c_h2[m * N + l], v[c][l], d);
+          se[3 * (a + N * (m + N * b)) + c] = d.x;
+          sz[3 * (a + N * (b + N * m)) + c] = d.y;
         }
     }
-    team_sync<C::KIND>(team);
+    team_sync<KIND, TEAM>(team);
 
     // 2b. along the xi-line (j, k) = (a, b): xi derivatives in registers, Jacobian map, Hooke
     //     stress, fluxes; the xi-flux transposed product stays in registers, the eta and zeta
     //     fluxes replace the derivatives they were made from
-    float fx[N], fy[N], fz[N];
+    float2 fxy[N];  // (x, y) and z of the xi-flux transposed product
+    float fz[N];
     {
-      float ux[N], uy[N], uz[N];
+      float2 uxy[N];
+      float uz[N];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const int p = i + N * line;
-        ux[i] = su[3 * p];
-        uy[i] = su[3 * p + 1];
+        uxy[i] = make_float2(su[3 * p], su[3 * p + 1]);
         uz[i] = su[3 * p + 2];
-        fx[i] = fy[i] = fz[i] = 0.f;
+        fxy[i] = make_float2(0.f, 0.f);
+        fz[i] = 0.f;
       }
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        float dxi_x = 0.f, dxi_y = 0.f, dxi_z = 0.f;
+        float2 dxy = make_float2(0.f, 0.f);
+        float dxi_z = 0.f;
 #pragma unroll
         for (int l = 0; l < N; ++l) {
-          const float h = H[i * N + l];
-          dxi_x += h * ux[l];
-          dxi_y += h * uy[l];
-          dxi_z += h * uz[l];
+          dxy = ffma2(c_h2[i * N + l], uxy[l], dxy);
+          dxi_z += H[i * N + l] * uz[l];
         }
+        const float dxi_x = dxy.x, dxi_y = dxy.y;
         const int p3 = 3 * (i + N * line);
         const float det_x = se[p3], det_y = se[p3 + 1], det_z = se[p3 + 2];
         const float dze_x = sz[p3], dze_y = sz[p3 + 1], dze_z = sz[p3 + 2];
@@ -258,9 +208,8 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         float G[9];
 #pragma unroll
         for (int c = 0; c < 9; ++c) G[c] = active ? __ldg(r + (kG + c) * NP + q) : 0.f;
-        const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
-        const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
-        const float mu = active ? __ldg(r + kMu * NP + q) : 0.f;
+        const float kappa = active ? __ldg(r + kJKappa * NP + q) : 0.f;  // J kappa
+        const float mu = active ? __ldg(r + kJMu * NP + q) : 0.f;        // J mu
 
         const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
         const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
@@ -272,6 +221,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
         const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
 
+        // J sigma (the record holds J kappa and J mu, so the fluxes need no J multiply)
         const float lam = kappa - (2.f / 3.f) * mu;
         const float tr = uxx + uyy + uzz;
         const float sxx = lam * tr + 2.f * mu * uxx;
@@ -281,53 +231,47 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         const float sxz = mu * (uxz + uzx);
         const float syz = mu * (uyz + uzy);
 
-        const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
-        const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
-        const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
+        const float txi_x = (sxx * G[0] + sxy * G[1] + sxz * G[2]);
+        const float txi_y = (sxy * G[0] + syy * G[1] + syz * G[2]);
+        const float txi_z = (sxz * G[0] + syz * G[1] + szz * G[2]);
+        const float2 txy = make_float2(txi_x, txi_y);
 #pragma unroll
         for (int ip = 0; ip < N; ++ip) {
-          const float hw = HW[i * N + ip];
-          fx[ip] += hw * txi_x;
-          fy[ip] += hw * txi_y;
-          fz[ip] += hw * txi_z;
+          fxy[ip] = ffma2(c_hw2[i * N + ip], txy, fxy[ip]);
+          fz[ip] += HW[i * N + ip] * txi_z;
         }
         if (active) {
-          se[p3] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
-          se[p3 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
-          se[p3 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
-          sz[p3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
-          sz[p3 + 1] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
-          sz[p3 + 2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
+          se[p3] = (sxx * G[3] + sxy * G[4] + sxz * G[5]);
+          se[p3 + 1] = (sxy * G[3] + syy * G[4] + syz * G[5]);
+          se[p3 + 2] = (sxz * G[3] + syz * G[4] + szz * G[5]);
+          sz[p3] = (sxx * G[6] + sxy * G[7] + sxz * G[8]);
+          sz[p3 + 1] = (sxy * G[6] + syy * G[7] + syz * G[8]);
+          sz[p3 + 2] = (sxz * G[6] + syz * G[7] + szz * G[8]);
         }
       }
     }
-    team_sync<C::KIND>(team);
+    team_sync<KIND, TEAM>(team);
 
     // 3. eta and zeta transposed products along the eta- and zeta-lines, in place
     if (active) {
-      float ve[3][N], vz[3][N];
+      float2 v[3][N];  // (eta-line flux, zeta-line flux)
 #pragma unroll
       for (int l = 0; l < N; ++l)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          ve[c][l] = se[3 * (a + N * (l + N * b)) + c];
-          vz[c][l] = sz[3 * (a + N * (b + N * l)) + c];
-        }
+        for (int c = 0; c < 3; ++c)
+          v[c][l] = make_float2(se[3 * (a + N * (l + N * b)) + c], sz[3 * (a + N * (b + N * l)) + c]);
 #pragma unroll
       for (int m = 0; m < N; ++m)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          float te = 0.f, tz = 0.f;
+          float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int l = 0; l < N; ++l) {
-            te += HW[l * N + m] * ve[c][l];
-            tz += HW[l * N + m] * vz[c][l];
-          }
-          se[3 * (a + N * (m + N * b)) + c] = te;
-          sz[3 * (a + N * (b + N * m)) + c] = tz;
+          for (int l = 0; l < N; ++l) t = ffma2(c_hw2[l * N + m], v[c][l], t);
+          se[3 * (a + N * (m + N * b)) + c] = t.x;
+          sz[3 * (a + N * (b + N * m)) + c] = t.y;
         }
     }
-    team_sync<C::KIND>(team);
+    team_sync<KIND, TEAM>(team);
 
     // 3b. element forces along the xi-line (j, k) = (a, b) into the (now free) u slots
     if (active) {
@@ -336,12 +280,12 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       for (int i = 0; i < N; ++i) {
         const float wi = W[i];
         const int p = 3 * (i + N * line);
-        su[p] = -(wj * wk * fx[i] + wi * wk * se[p] + wi * wj * sz[p]);
-        su[p + 1] = -(wj * wk * fy[i] + wi * wk * se[p + 1] + wi * wj * sz[p + 1]);
+        su[p] = -(wj * wk * fxy[i].x + wi * wk * se[p] + wi * wj * sz[p]);
+        su[p + 1] = -(wj * wk * fxy[i].y + wi * wk * se[p + 1] + wi * wj * sz[p + 1]);
         su[p + 2] = -(wj * wk * fz[i] + wi * wk * se[p + 2] + wi * wj * sz[p + 2]);
       }
     }
-    team_sync<C::KIND>(team);
+    team_sync<KIND, TEAM>(team);
 
   } else {
     // 2. per xi-line derivatives, stress and fluxes
@@ -353,7 +297,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     float* su = ts + (active ? le : 0) * ES;  // u, then F: [NP][3]
     float* se = su + 3 * NP;                   // eta fluxes [NP][3]
     float* sz = su + 6 * NP;                   // zeta fluxes [NP][3]
-    const float* __restrict__ r = rec + static_cast<size_t>(elem_of(active ? le : 0)) * REC;
+    const float* __restrict__ r = rec_of(active ? le : 0);
 
     float ux[N], uy[N], uz[N];
 #pragma unroll
@@ -397,9 +341,8 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       float G[9];
 #pragma unroll
       for (int a = 0; a < 9; ++a) G[a] = active ? __ldg(r + (kG + a) * NP + q) : 0.f;
-      const float jac = active ? __ldg(r + kJac * NP + q) : 0.f;
-      const float kappa = active ? __ldg(r + kKappa * NP + q) : 0.f;
-      const float mu = active ? __ldg(r + kMu * NP + q) : 0.f;
+      const float kappa = active ? __ldg(r + kJKappa * NP + q) : 0.f;  // J kappa
+      const float mu = active ? __ldg(r + kJMu * NP + q) : 0.f;        // J mu
 
       const float uxx = dxi_x * G[0] + det_x * G[3] + dze_x * G[6];
       const float uxy = dxi_x * G[1] + det_x * G[4] + dze_x * G[7];
@@ -411,6 +354,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       const float uzy = dxi_z * G[1] + det_z * G[4] + dze_z * G[7];
       const float uzz = dxi_z * G[2] + det_z * G[5] + dze_z * G[8];
 
+      // J sigma (the record holds J kappa and J mu, so the fluxes need no J multiply)
       const float lam = kappa - (2.f / 3.f) * mu;
       const float tr = uxx + uyy + uzz;
       const float sxx = lam * tr + 2.f * mu * uxx;
@@ -420,9 +364,9 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       const float sxz = mu * (uxz + uzx);
       const float syz = mu * (uyz + uzy);
 
-      const float txi_x = jac * (sxx * G[0] + sxy * G[1] + sxz * G[2]);
-      const float txi_y = jac * (sxy * G[0] + syy * G[1] + syz * G[2]);
-      const float txi_z = jac * (sxz * G[0] + syz * G[1] + szz * G[2]);
+      const float txi_x = (sxx * G[0] + sxy * G[1] + sxz * G[2]);
+      const float txi_y = (sxy * G[0] + syy * G[1] + syz * G[2]);
+      const float txi_z = (sxz * G[0] + syz * G[1] + szz * G[2]);
 #pragma unroll
       for (int ip = 0; ip < N; ++ip) {
         const float hw = HW[i * N + ip];
@@ -432,15 +376,15 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
       }
       if (active) {
         const int p3 = 3 * (i + N * line);
-        se[p3] = jac * (sxx * G[3] + sxy * G[4] + sxz * G[5]);
-        se[p3 + 1] = jac * (sxy * G[3] + syy * G[4] + syz * G[5]);
-        se[p3 + 2] = jac * (sxz * G[3] + syz * G[4] + szz * G[5]);
-        sz[p3] = jac * (sxx * G[6] + sxy * G[7] + sxz * G[8]);
-        sz[p3 + 1] = jac * (sxy * G[6] + syy * G[7] + syz * G[8]);
-        sz[p3 + 2] = jac * (sxz * G[6] + syz * G[7] + szz * G[8]);
+        se[p3] = (sxx * G[3] + sxy * G[4] + sxz * G[5]);
+        se[p3 + 1] = (sxy * G[3] + syy * G[4] + syz * G[5]);
+        se[p3 + 2] = (sxz * G[3] + syz * G[4] + szz * G[5]);
+        sz[p3] = (sxx * G[6] + sxy * G[7] + sxz * G[8]);
+        sz[p3 + 1] = (sxy * G[6] + syy * G[7] + syz * G[8]);
+        sz[p3 + 2] = (sxz * G[6] + syz * G[7] + szz * G[8]);
       }
     }
-    team_sync<C::KIND>(team);
+    team_sync<KIND, TEAM>(team);
 
     // 3. eta and zeta transposed products; forces into the (now free) u slots
     {
@@ -474,47 +418,102 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         }
       }
     }
-    team_sync<C::KIND>(team);
+    team_sync<KIND, TEAM>(team);
 
   }
+}
 
-  // 4. scatter in the gather's coalesced order; for the padded layout the previous values
-  //    of a group of GB nodes are loaded before any of them is written back
-  if constexpr (VS == 4) {
-    for (int base = tl; base < ne * NP; base += GB * TEAM) {
-      uint32_t w[GB];
-      float4 prev[GB];
+// Element kernel: one colour of elements per launch, each element gathered and scattered
+// on its own through the ibool words of its record.
+// CALLER false: u and f are the context's own padded fields [nglob][S][4] (internal node
+// order). CALLER true (one shot): caller arrays [nglob][3] in caller node order, reached
+// through perm (internal -> caller node). With S shots the launch works on the items
+// (element, shot) of elements e0 .. e1-1 of elist, element-major: the teams of a CTA take the
+// shots of one element, so its record is read from DRAM once for all of them.
+template <int N, bool MS, bool LO, bool CALLER>
+__global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
+    forces_kernel(const float* __restrict__ rec, const int* __restrict__ elist, const int* __restrict__ perm,
+                  const float* __restrict__ u, float* __restrict__ f, int e0, int e1, int S_arg) {
+  const int S = MS ? S_arg : 1;  // shots (a compile-time 1 for the single-shot kernel)
+  using C = ForceCfg<N>;
+  constexpr int NP = C::NP, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
+  extern __shared__ float4 smem4[];
+
+  const int team = threadIdx.x / TEAM;
+  const int tl = threadIdx.x - team * TEAM;
+  const int ibase = (blockIdx.x * C::TEAMS + team) * E;  // first item of the team
+  const int ne = min(E, (e1 - e0) * S - ibase);
+  if (C::KIND != 2 && ne <= 0) return;  // a team without items (its barrier is its own)
+  float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
+  // record slot and shot of the team's item le (elist: record slots in colour order)
+  auto elem_of = [&](int le) { return elist[e0 + (MS ? (ibase + le) / S : ibase + le)]; };
+  auto shot_of = [&](int le) { return MS ? (ibase + le) % S : 0; };
+
+  // 0. records to L2 while the previous grid finishes, then wait for its results
+  if (tl < ne) prefetch_l2(rec + static_cast<size_t>(elem_of(tl)) * REC, kForceFields * NP * sizeof(float));
+  wait_prerequisite_grid();
+  allow_dependent_grid();
+
+  // 1. gather, one thread per local point; GB points per thread at a time, their ibool
+  //    words first and then their nodes, so that the loads of a group are all in flight
+  constexpr int GB = 4;
+  for (int base = tl; base < ne * NP; base += GB * TEAM) {
+    uint32_t w[GB];
 #pragma unroll
-      for (int r = 0; r < GB; ++r) {
-        const int idx = base + r * TEAM;
-        w[r] = kFirstTouchBit;
-        prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < ne * NP) {
-          const int e = idx / NP;
-          w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
-          if (!(w[r] & kFirstTouchBit))
-            prev[r] = reinterpret_cast<const float4*>(f)[static_cast<size_t>(w[r] & ~kFirstTouchBit) * S + shot_of(e)];
-        }
-      }
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      const int le = idx / NP;
+      w[r] = idx < ne * NP ? __float_as_uint(__ldg(rec + static_cast<size_t>(elem_of(le)) * REC + (idx - le * NP)))
+                           : 0u;
+    }
+    float q[GB][3];
 #pragma unroll
-      for (int r = 0; r < GB; ++r) {
-        const int idx = base + r * TEAM;
-        if (idx < ne * NP) {
-          const int e = idx / NP;
-          const float* src = ts + e * ES + 3 * (idx - e * NP);
-          reinterpret_cast<float4*>(f)[static_cast<size_t>(w[r] & ~kFirstTouchBit) * S + shot_of(e)] =
-              make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
+    for (int r = 0; r < GB; ++r) {
+      const size_t g = w[r] & kNodeMask;
+      if (base + r * TEAM < ne * NP) {
+        if constexpr (CALLER) {
+          const size_t gc = static_cast<size_t>(__ldg(perm + g));
+          q[r][0] = __ldg(u + 3 * gc);
+          q[r][1] = __ldg(u + 3 * gc + 1);
+          q[r][2] = __ldg(u + 3 * gc + 2);
+        } else {
+          const int le = (base + r * TEAM) / NP;
+          const float4 v = __ldg(reinterpret_cast<const float4*>(u) + g * S + shot_of(le));
+          q[r][0] = v.x;
+          q[r][1] = v.y;
+          q[r][2] = v.z;
         }
       }
     }
-  } else {
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      if (idx < ne * NP) {
+        const int le = idx / NP;
+        const int p = idx - le * NP;
+        float* eb = ts + le * ES;
+        reinterpret_cast<uint32_t*>(eb + 9 * NP)[p] = w[r];
+        eb[3 * p] = q[r][0];
+        eb[3 * p + 1] = q[r][1];
+        eb[3 * p + 2] = q[r][2];
+      }
+    }
+  }
+  team_sync<C::KIND, C::TEAM>(team);
+
+  team_element_forces<N, C::KIND, TEAM, ES, LO>(ts, tl, ne, team, [&](int le) {
+    return rec + static_cast<size_t>(elem_of(le)) * REC;
+  });
+
+  // 4. scatter in the gather's coalesced order; the previous values of a group of GB nodes
+  //    are loaded before any of them is written back
+  if constexpr (CALLER) {
     for (int idx = tl; idx < ne * NP; idx += TEAM) {
       const int e = idx / NP;
-      const int p = idx - e * NP;
       const float* sb = ts + e * ES;
-      const uint32_t w = reinterpret_cast<const uint32_t*>(sb + 9 * NP)[p];
-      const size_t g = w & ~kFirstTouchBit;
-      const float* src = sb + 3 * p;
+      const uint32_t w = reinterpret_cast<const uint32_t*>(sb + 9 * NP)[idx - e * NP];
+      const size_t g = static_cast<size_t>(__ldg(perm + (w & kNodeMask)));
+      const float* src = sb + 3 * (idx - e * NP);
       if (w & kFirstTouchBit) {
         f[3 * g] = src[0];
         f[3 * g + 1] = src[1];
@@ -523,6 +522,232 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
         f[3 * g] += src[0];
         f[3 * g + 1] += src[1];
         f[3 * g + 2] += src[2];
+      }
+    }
+    return;
+  }
+  for (int base = tl; base < ne * NP; base += GB * TEAM) {
+    uint32_t w[GB];
+    float4 prev[GB];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      w[r] = kFirstTouchBit;
+      prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (idx < ne * NP) {
+        const int e = idx / NP;
+        w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
+        if (!(w[r] & kFirstTouchBit))
+          prev[r] = reinterpret_cast<const float4*>(f)[static_cast<size_t>(w[r] & kNodeMask) * S + shot_of(e)];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      if (idx < ne * NP) {
+        const int e = idx / NP;
+        const float* src = ts + e * ES + 3 * (idx - e * NP);
+        reinterpret_cast<float4*>(f)[static_cast<size_t>(w[r] & kNodeMask) * S + shot_of(e)] =
+            make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Patch kernel (Sec. II-B stiffness action with the Sec. IV-C coloured assembly applied to
+// patches of elements): one CTA per patch, a brick of up to PE neighbouring elements whose
+// records are consecutive; the launches of one sweep take the patch colours in order.
+//  0. bulk-prefetch the patch's records into L2, then wait for the previous grid;
+//  1. every team gathers its own elements' points through the records' ibool words, as the
+//     element kernel does (teams run independently; the nodes the patch's elements share
+//     are read once from DRAM and then from L1);
+//  2-3. every element's forces (team_element_forces);
+//  4a. each team adds the forces of its points that are alone at their patch node (inside
+//     one element of the patch: 512 of the 729 nodes of a 2 x 2 x 2 brick at NGLL 5) to the
+//     node, with no wait for the other teams;
+//  4b. after one CTA barrier, per shared patch node: the forces of the local points that
+//     meet there summed in the fixed order of the patch table (ascending element, then
+//     point; kPatchSlots slots per node read as one 16-byte word), then added to the node.
+//  A node is stored instead of added at its first touch in patch-colour order
+//  (kPatchFirstBit on the ibool word of the node's first local point in the patch).
+//  Patches of one colour share no node, so there are no atomics, and the order of every
+//  sum is fixed (bitwise reproducible results).
+// Shared memory: one ES-float workspace per element, as in the element kernel.
+// ---------------------------------------------------------------------------------------
+template <int N>
+struct PatchCfg {
+  static constexpr int NP = N * N * N;
+  static constexpr int NL = N * N;
+  // Teams of TEAM threads holding E = TEAM / NL elements, one thread per line: one warp up
+  // to NGLL 5, two warps under a named barrier for NGLL 6-8, the CTA for NGLL 9-10. (Teams
+  // of several warps with more elements fill more lanes at NGLL 5-7, but the warps then wait
+  // for each other at every phase: GB300, 64^3 at NGLL 5, 0.92 ms per sweep against 0.70.)
+  static constexpr int TEAM = N <= 5 ? 32 : N <= 8 ? 64 : 256;
+  // 0 one warp, 1 a named barrier over the team's warps, 2 the CTA
+  static constexpr int KIND = TEAM == 32 ? 0 : TEAM < 256 ? 1 : 2;
+  static constexpr int E = TEAM / NL;  // elements per team
+  // the brick, in elements along the lattice x, y, z
+  static constexpr int BX = N == 2 ? 4 : N == 3 ? 3 : N == 4 ? 4 : N <= 8 ? 2 : N == 9 ? 3 : 2;
+  static constexpr int BY = N == 2 ? 4 : N == 3 ? 3 : N <= 8 ? 2 : 1;
+  static constexpr int BZ = N == 2 ? 4 : N == 3 ? 3 : N <= 5 ? 2 : 1;
+  static constexpr int PE = BX * BY * BZ;
+  static constexpr int TEAMS = (PE + E - 1) / E;
+  static constexpr int T = TEAMS * TEAM;
+  // floats per element workspace (at least 10 NP: u/F, eta and zeta values, ibool words)
+  static constexpr int ES = KIND == ForceCfg<N>::KIND ? ForceCfg<N>::ES : 10 * NP + 1;
+  static constexpr int TS = E * ES;
+  static constexpr int REC = ForceCfg<N>::REC;
+  static constexpr int SMEM = TEAMS * TS * 4;
+  static constexpr int MIN_BLOCKS = N == 3 ? 3 : N <= 5 ? 4 : N <= 7 ? 3 : 2;
+  static_assert(E >= 1 && 10 * NP <= ES, "team and workspace sizes");
+};
+
+template <int N, bool LO>
+__global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
+    patch_forces_kernel(const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
+                        const uint16_t* __restrict__ slot_tab, const uint32_t* __restrict__ excl_tab,
+                        const float4* __restrict__ u, float4* __restrict__ f, int p0) {
+  using C = PatchCfg<N>;
+  constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, REC = C::REC, T = C::T;
+  constexpr uint32_t kAlone = 0x80000000u;  // in the shared-memory copy of an ibool word: the
+                                            // point is the only one at its patch node
+  extern __shared__ float4 smem4[];
+  float* wsb = reinterpret_cast<float*>(smem4);
+  const PatchDesc d = desc[p0 + blockIdx.x];
+  const int tid = threadIdx.x;
+  const int team = tid / TEAM;
+  const int tl = tid - team * TEAM;
+  auto ws_of = [&](int le) { return wsb + (le / E) * C::TS + (le % E) * ES; };
+  const int ne = min(E, d.nelem - team * E);  // this team's elements
+  const float* __restrict__ trec = rec + static_cast<size_t>(d.slot0 + team * E) * REC;
+  const uint32_t* __restrict__ excl = excl_tab + d.excl_off;
+
+  // 0. records to L2 while the previous grid finishes, then wait for its results
+  if (tid < d.nelem)
+    prefetch_l2(rec + static_cast<size_t>(d.slot0 + tid) * REC, kForceFields * NP * sizeof(float));
+  wait_prerequisite_grid();
+  allow_dependent_grid();
+
+  // 1. gather, one thread per local point of the team's elements, GB points in flight; the
+  //    shared-memory word keeps the node, the patch first-touch flag and kAlone
+  constexpr int GB = 4;
+  float* ts = wsb + team * C::TS;
+  for (int base = tl; base < ne * NP; base += GB * TEAM) {
+    uint32_t w[GB];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      const int le = idx / NP;
+      w[r] = 0u;
+      if (idx < ne * NP) {
+        const int c = team * E * NP + idx;  // local point index in the patch table
+        const uint32_t alone = (__ldg(excl + c / 32) >> (c % 32)) & 1u;
+        w[r] = (__float_as_uint(__ldg(trec + static_cast<size_t>(le) * REC + (idx - le * NP))) & ~kFirstTouchBit) |
+               (alone ? kAlone : 0u);
+      }
+    }
+    float4 q[GB];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) q[r] = __ldg(u + (w[r] & kNodeMask));
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      if (idx < ne * NP) {
+        const int le = idx / NP;
+        const int p = idx - le * NP;
+        float* eb = ts + le * ES;
+        reinterpret_cast<uint32_t*>(eb + 9 * NP)[p] = w[r];
+        eb[3 * p] = q[r].x;
+        eb[3 * p + 1] = q[r].y;
+        eb[3 * p + 2] = q[r].z;
+      }
+    }
+  }
+
+  // 2-3. element forces, team by team; 4a. every team adds the forces of its points that are
+  //      alone at their patch node to the node (store at its first touch), as the element
+  //      kernel does, before any CTA barrier
+  if (C::KIND == 2 || ne > 0) {
+    team_sync<C::KIND, TEAM>(team);
+    team_element_forces<N, C::KIND, TEAM, ES, LO>(ts, tl, ne, team,
+                                                  [&](int le) { return trec + static_cast<size_t>(le) * REC; });
+    for (int base = tl; base < ne * NP; base += GB * TEAM) {
+      uint32_t w[GB];
+      float4 prev[GB];
+#pragma unroll
+      for (int r = 0; r < GB; ++r) {
+        const int idx = base + r * TEAM;
+        w[r] = 0u;
+        prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < ne * NP) {
+          const int e = idx / NP;
+          w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
+          if ((w[r] & kAlone) && !(w[r] & kPatchFirstBit)) prev[r] = f[w[r] & kNodeMask];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < GB; ++r) {
+        const int idx = base + r * TEAM;
+        if (w[r] & kAlone) {
+          const int e = idx / NP;
+          const float* src = ts + e * ES + 3 * (idx - e * NP);
+          f[w[r] & kNodeMask] = make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // 4b. per shared patch node: the sum of its local points' forces in table order (its slots
+  //     read as one 16-byte word), then one store (first touch) or one read-modify-write; the
+  //     previous values of GB nodes are loaded before any of them is written
+  const uint4* __restrict__ slots = reinterpret_cast<const uint4*>(slot_tab + d.slot_off);
+  for (int base = tid; base < d.nshared; base += GB * T) {
+    uint4 sl[GB];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int t = base + r * T;
+      sl[r] = __ldg(slots + (t < d.nshared ? t : 0));
+    }
+    uint32_t w[GB];
+    float4 prev[GB];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int t = base + r * T;
+      const int q0 = static_cast<int>(sl[r].x & 0xFFFFu);  // first slot: never empty, never a chain
+      const int le0 = q0 / NP;
+      w[r] = t < d.nshared ? reinterpret_cast<const uint32_t*>(ws_of(le0) + 9 * NP)[q0 - le0 * NP] : kPatchFirstBit;
+      prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!(w[r] & kPatchFirstBit)) prev[r] = f[w[r] & kNodeMask];
+    }
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int t = base + r * T;
+      if (t < d.nshared) {
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        uint4 g4 = sl[r];
+        while (true) {
+          const uint32_t wd[4] = {g4.x, g4.y, g4.z, g4.w};
+          uint32_t chain = 0;
+#pragma unroll
+          for (int k = 0; k < kPatchSlots; ++k) {
+            const uint32_t q = (wd[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+            if (q == kPatchNoSlot) continue;
+            if (q & kPatchChain) {
+              chain = q;
+              continue;
+            }
+            const int le = static_cast<int>(q) / NP;
+            const float* F = ws_of(le) + 3 * (static_cast<int>(q) - le * NP);
+            sx += F[0];
+            sy += F[1];
+            sz += F[2];
+          }
+          if (!chain) break;
+          g4 = __ldg(slots + (chain & ~static_cast<uint32_t>(kPatchChain)));
+        }
+        f[w[r] & kNodeMask] = make_float4(prev[r].x + sx, prev[r].y + sy, prev[r].z + sz, 0.f);
       }
     }
   }
@@ -535,15 +760,16 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
 //   g_kappa[q] += c_k * w_q J_q tr e(lam) tr e(u_mid)
 //   g_mu[q]    += c_k * w_q J_q 2 (e(lam) : e(u_mid) - tr e(lam) tr e(u_mid) / 3)
 // with e the discrete strain (the same derivatives and chain rule as the force kernel),
-// c_m = -1 and c_k = -dt^2. lam is the adjoint field in the solver layout [nglob][4], the
-// u_* displacement snapshots [nglob][3]. The terms are formed in float32 (the second
+// c_m = -1 and c_k = -dt^2. lam is the adjoint field in the solver layout [nglob][4] (internal
+// node order), the u_* displacement snapshots [nglob][3] in caller node order (perm maps). The terms are formed in float32 (the second
 // difference as (u_hi - u_mid) - (u_mid - u_lo), which keeps the digits the plain form
 // cancels) and added to float64 accumulators per local point in record order (element,
 // q = i N^2 + line). No two threads write the same point, so there are no colours here.
 // ---------------------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(ForceCfg<N>::T)
-    sensitivity_kernel(const float* __restrict__ rec, const float* __restrict__ lam, const float* __restrict__ u_lo,
+    sensitivity_kernel(const float* __restrict__ rec, const int* __restrict__ perm, const float* __restrict__ lam,
+                       const float* __restrict__ u_lo,
                        const float* __restrict__ u_mid, const float* __restrict__ u_hi, double* __restrict__ g_rho,
                        double* __restrict__ g_kappa, double* __restrict__ g_mu, int nspec, double c_m, double c_k) {
   using C = ForceCfg<N>;
@@ -566,19 +792,22 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
       const int idx = base + r * TEAM;
       const int le = idx / NP;
       g[r] = idx < ne * NP
-                 ? __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + (idx - le * NP))) & ~kFirstTouchBit
+                 ? __float_as_uint(__ldg(rec + static_cast<size_t>(ebase + le) * REC + (idx - le * NP))) & kNodeMask
                  : 0;
     }
     float4 l4[GB];
     float um[GB][3], uh[GB][3], ul[GB][3];
+    size_t gc[GB];  // caller node of each point (the snapshots are in caller order)
+#pragma unroll
+    for (int r = 0; r < GB; ++r) gc[r] = static_cast<size_t>(__ldg(perm + g[r]));
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
       l4[r] = __ldg(reinterpret_cast<const float4*>(lam) + g[r]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        um[r][a] = __ldg(u_mid + 3 * g[r] + a);
-        uh[r][a] = __ldg(u_hi + 3 * g[r] + a);
-        ul[r][a] = __ldg(u_lo + 3 * g[r] + a);
+        um[r][a] = __ldg(u_mid + 3 * gc[r] + a);
+        uh[r][a] = __ldg(u_hi + 3 * gc[r] + a);
+        ul[r][a] = __ldg(u_lo + 3 * gc[r] + a);
       }
     }
 #pragma unroll
@@ -599,7 +828,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
       eb[6 * NP + p] = dot;
     }
   }
-  team_sync<C::KIND>(team);
+  team_sync<C::KIND, C::TEAM>(team);
   const int le = tl / NL;
   const int line = tl - le * NL;
   const int j = line % N;
@@ -658,20 +887,25 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
   }
 }
 
-template <int VS, bool MS, bool LO>
-int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
-  using C = ForceCfg<SEM_NGLL>;
-  static unsigned long long attr_done = 0;  // one bit per device ordinal
-  const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
+// Raises a kernel's dynamic shared-memory limit once per device (bit per ordinal).
+template <class K>
+int raise_smem_limit(std::atomic<unsigned long long>& done, K kernel, int bytes) {
   int dev = 0;
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
-  if (!(attr_done & bit)) {
-    cudaError_t e =
-        cudaFuncSetAttribute(forces_kernel<SEM_NGLL, VS, MS, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return static_cast<int>(e);
-    attr_done |= bit;
-  }
+  if (done.load(std::memory_order_acquire) & bit) return 0;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return static_cast<int>(e);
+  done.fetch_or(bit, std::memory_order_acq_rel);
+  return 0;
+}
+
+template <bool MS, bool LO, bool CALLER>
+int launch_forces_ms(const ForceLaunch& L, cudaStream_t s) {
+  using C = ForceCfg<SEM_NGLL>;
+  static std::atomic<unsigned long long> attr_done{0};
+  const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
+  if (int r = raise_smem_limit(attr_done, forces_kernel<SEM_NGLL, MS, LO, CALLER>, smem)) return r;
   const int S = MS ? L.shots : 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(((L.e1 - L.e0) * S + C::EPC - 1) / C::EPC);
@@ -683,20 +917,47 @@ int launch_forces_vs(const ForceLaunch& L, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_kernel<SEM_NGLL, VS, MS, LO>, L.rec, L.u, L.f, L.e0, L.e1, S));
+  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_kernel<SEM_NGLL, MS, LO, CALLER>, L.rec, L.elist, L.perm, L.u, L.f, L.e0, L.e1, S));
 }
 
 int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
   if (L.e1 <= L.e0) return 0;
   using C = ForceCfg<SEM_NGLL>;
   const bool lo = L.variant == 0 ? C::LINE_OWNERS : L.variant == 1;  // 0 default, 1 line owners, 2 per point
-  if (L.shots > 1) {
-    if (L.node_stride != 4) return static_cast<int>(cudaErrorInvalidValue);
-    return lo ? launch_forces_vs<4, true, true>(L, s) : launch_forces_vs<4, true, false>(L, s);
+  if (L.node_stride == 3) {
+    if (L.shots != 1 || !L.perm) return static_cast<int>(cudaErrorInvalidValue);
+    return launch_forces_ms<false, C::LINE_OWNERS, true>(L, s);
   }
-  if (L.node_stride == 4) return lo ? launch_forces_vs<4, false, true>(L, s) : launch_forces_vs<4, false, false>(L, s);
-  if (L.node_stride == 3) return launch_forces_vs<3, false, C::LINE_OWNERS>(L, s);
-  return static_cast<int>(cudaErrorInvalidValue);
+  if (L.node_stride != kNodeStride) return static_cast<int>(cudaErrorInvalidValue);
+  if (L.shots > 1) return lo ? launch_forces_ms<true, true, false>(L, s) : launch_forces_ms<true, false, false>(L, s);
+  return lo ? launch_forces_ms<false, true, false>(L, s) : launch_forces_ms<false, false, false>(L, s);
+}
+
+template <bool LO>
+int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
+  using C = PatchCfg<SEM_NGLL>;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (int r = raise_smem_limit(attr_done, patch_forces_kernel<SEM_NGLL, LO>, C::SMEM)) return r;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.p1 - L.p0);
+  cfg.blockDim = dim3(C::T);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO>, L.rec, L.desc, L.slots, L.excl,
+                                             reinterpret_cast<const float4*>(L.u), reinterpret_cast<float4*>(L.f),
+                                             L.p0));
+}
+
+int launch_patch_n(const PatchLaunch& L, cudaStream_t s) {
+  if (L.p1 <= L.p0) return 0;
+  using C = ForceCfg<SEM_NGLL>;
+  const bool lo = L.variant == 0 ? C::LINE_OWNERS : L.variant == 1;
+  return lo ? launch_patch_lo<true>(L, s) : launch_patch_lo<false>(L, s);
 }
 
 }  // namespace
@@ -716,6 +977,13 @@ int SEM_CAT(upload_basis_, SEM_NGLL)(const double* w, const double* h, void* str
   cudaError_t e = cudaMemcpyToSymbolAsync(c_h, hf, sizeof(hf), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_hw, hwf, sizeof(hwf), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_w, wf, sizeof(wf), 0, cudaMemcpyHostToDevice, s);
+  float2 h2[N * N], hw2[N * N];
+  for (int q = 0; q < N * N; ++q) {
+    h2[q] = make_float2(hf[q], hf[q]);
+    hw2[q] = make_float2(hwf[q], hwf[q]);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_h2, h2, sizeof(h2), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_hw2, hw2, sizeof(hw2), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return static_cast<int>(e);
 }
@@ -724,27 +992,30 @@ int SEM_CAT(launch_forces_, SEM_NGLL)(const ForceLaunch& L, void* stream) {
   return launch_forces_n(L, static_cast<cudaStream_t>(stream));
 }
 
-int SEM_CAT(launch_sensitivity_, SEM_NGLL)(const float* rec, const float* lam, const float* u_lo, const float* u_mid,
-                                          const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec,
-                                          double c_m, double c_k, void* stream) {
+int SEM_CAT(launch_sensitivity_, SEM_NGLL)(const float* rec, const int* perm, const float* lam, const float* u_lo,
+                                          const float* u_mid, const float* u_hi, double* g_rho, double* g_kappa,
+                                          double* g_mu, int nspec, double c_m, double c_k, void* stream) {
   using C = ForceCfg<SEM_NGLL>;
-  static unsigned long long attr_done = 0;
+  static std::atomic<unsigned long long> attr_done{0};
   const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (!(attr_done & bit)) {
-    cudaError_t e =
-        cudaFuncSetAttribute(sensitivity_kernel<SEM_NGLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return static_cast<int>(e);
-    attr_done |= bit;
-  }
+  if (int r = raise_smem_limit(attr_done, sensitivity_kernel<SEM_NGLL>, smem)) return r;
   const int grid = (nspec + C::EPC - 1) / C::EPC;
   sensitivity_kernel<SEM_NGLL><<<grid, C::T, smem, static_cast<cudaStream_t>(stream)>>>(
-      rec, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k);
+      rec, perm, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k);
   return static_cast<int>(cudaGetLastError());
 }
 
 int SEM_CAT(forces_smem_bytes_, SEM_NGLL)() { return ForceCfg<SEM_NGLL>::SMEM_FLOATS * 4; }
+
+int SEM_CAT(launch_patch_forces_, SEM_NGLL)(const PatchLaunch& L, void* stream) {
+  return launch_patch_n(L, static_cast<cudaStream_t>(stream));
+}
+
+void SEM_CAT(patch_shape_, SEM_NGLL)(PatchShape* out) {
+  using C = PatchCfg<SEM_NGLL>;
+  out->bx = C::BX;
+  out->by = C::BY;
+  out->bz = C::BZ;
+}
 
 }  // namespace semgb

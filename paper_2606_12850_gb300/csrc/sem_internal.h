@@ -17,9 +17,12 @@ constexpr int kMaxNgll = 10;
 constexpr int kMinNgll = 2;
 
 // Words per local point in the element record: ibool, nine inverse-Jacobian terms
-// dxi_r/dx_d (r-major: xix xiy xiz etax etay etaz gammax gammay gammaz), J, kappa, mu.
+// dxi_r/dx_d (r-major: xix xiy xiz etax etay etaz gammax gammay gammaz), J kappa, J mu, J.
+// The force kernels read the first kForceFields fields only (J sigma from J kappa and J mu
+// needs no separate J); J serves the mass and the material sensitivities.
 constexpr int kRecFields = 13;
-enum RecField { kIbool = 0, kG = 1, kJac = 10, kKappa = 11, kMu = 12 };
+constexpr int kForceFields = 12;
+enum RecField { kIbool = 0, kG = 1, kJKappa = 10, kJMu = 11, kJac = 12 };
 
 // The context's own wavefields u, v, a are float32 [nglob][kNodeStride]: x, y, z and a zero
 // pad, so that every node is one aligned 16-byte access in the gather, the scatter and the
@@ -30,6 +33,11 @@ constexpr int kNodeStride = 4;
 // colour-by-colour processing order: the force kernel stores instead of adding there,
 // so the assembled array needs no zeroing pass.
 constexpr uint32_t kFirstTouchBit = 0x80000000u;
+// Bit 30 marks the same for the patch kernel's order (patch colour by patch colour), on the
+// word of the first local point (in patch-table order) of each patch node; node ids are
+// below 2^30.
+constexpr uint32_t kPatchFirstBit = 0x40000000u;
+constexpr uint32_t kNodeMask = 0x3FFFFFFFu;
 
 inline int rec_words(int ngll) {
   const int np = ngll * ngll * ngll;
@@ -55,6 +63,43 @@ int color_elements(int nspec, int ngll, int nglob, const int32_t* ibool,
 
 int locate_nodes(int nglob, const double* node_xyz, int npts, const double* xyz,
                  const double* surface_z, int32_t* out);
+
+// Patches for the force sweep (sem_patches.cpp): bricks of bx x by x bz elements of the
+// mesh's lattice coordinates, coloured so that no two patches of a colour share a node.
+struct PatchShape {
+  int bx = 1, by = 1, bz = 1;
+};
+struct PatchPlan {
+  int ngll = 0;
+  int npatch = 0;
+  int ncolors = 0;
+  int max_nodes = 0;              // largest patch node count
+  int max_elems = 0;              // largest patch element count
+  std::vector<int> elem;          // caller elements in sweep order, patch after patch
+  std::vector<int> patch_off;     // [npatch + 1] into elem (sweep order)
+  std::vector<int> color_off;     // [ncolors + 1] patch ranges of the sweep order
+  std::vector<int> node_off;      // [npatch + 1] into nodes
+  std::vector<uint32_t> nodes;    // patch node lists: caller node | kFirstTouchBit
+  std::vector<int> table_of;      // per patch: its table
+  std::vector<int> tab_nelem, tab_nnode, tab_nshared, tab_lid_off, tab_csr_off, tab_excl_off, tab_first_off;
+  std::vector<uint16_t> lid;      // per table: [nelem][np] patch-local node of each local point
+  std::vector<int> node_new;      // [nglob] internal id of every caller node
+  std::vector<uint16_t> csr;      // per table: per shared patch node (one met by several local
+                                  // points) kPatchSlots slots holding those local points
+                                  // (le*np + p, ascending)
+  std::vector<uint32_t> excl;     // per table: bit le*np + p set when that local point is the
+                                  // only one at its patch node
+  std::vector<uint16_t> first_q;  // per table: per patch node, its first local point
+};
+// Contribution slots per patch node: 8 (the elements meeting at a vertex of a structured
+// hexahedral mesh), read as one 16-byte word. An unused slot holds kPatchNoSlot; a node met
+// by more local points continues in another group of slots, named by its last slot as
+// kPatchChain | group.
+constexpr int kPatchSlots = 8;
+constexpr uint16_t kPatchNoSlot = 0xFFFFu;
+constexpr uint16_t kPatchChain = 0x8000u;
+int build_patches(int nspec, int ngll, int nglob, const int32_t* ibool, const PatchShape& shape, PatchPlan* plan,
+                  std::string* err);
 
 // ---- device side (sem_kernels.cu) ------------------------------------------------------
 struct DevCtl {
@@ -94,14 +139,41 @@ int upload_basis(int ngll, const double* w, const double* hprime, void* stream);
 // is stored at its first touch in colour order and accumulated afterwards.
 struct ForceLaunch {
   const float* rec;
+  const int* elist;  // record slots in colour order; e0, e1 index this list
+  const int* perm;   // internal -> caller node (caller arrays, node_stride 3)
   const float* u;
   float* f;
   int e0, e1;
-  int node_stride;  // floats per node in u and f: kNodeStride, or 3 for caller arrays
+  int node_stride;  // floats per node in u and f: kNodeStride (internal order), or 3 for caller
+                    // arrays in caller order
   int shots;        // > 1: u and f are [nglob][shots][kNodeStride], items (element, shot)
   int variant;      // contraction form: 0 the order's default, 1 line owners, 2 per point
 };
 int launch_forces(int ngll, const ForceLaunch& launch, void* stream);
+
+// One patch colour [p0, p1) of the patch sweep order on the context's own [nglob][4] fields
+// (single shot): f (=|+=) -K u.
+struct alignas(16) PatchDesc {
+  int slot0;     // record slot of the patch's first element (its elements are consecutive)
+  int nelem;
+  int nshared;   // patch nodes met by several of its local points
+  int slot_off;  // its table: per shared node, kPatchSlots slots of the local points meeting there
+  int excl_off;  // its table: bit mask of the local points alone at their patch node
+  int pad0, pad1, pad2;
+};
+struct PatchLaunch {
+  const float* rec;
+  const PatchDesc* desc;
+  const uint16_t* slots;
+  const uint32_t* excl;
+  const float* u;
+  float* f;
+  int p0, p1;
+  int variant;  // contraction form as in ForceLaunch
+};
+int launch_patch_forces(int ngll, const PatchLaunch& launch, void* stream);
+// the brick each order's patch kernel is compiled for
+int patch_shape(int ngll, PatchShape* out);
 int forces_kernel_smem_bytes(int ngll);
 int forces_elements_per_cta(int ngll);
 
@@ -110,12 +182,14 @@ int launch_predictor(const DevProblem& p, void* stream);
 int launch_fused_newmark(const DevProblem& p, void* stream);
 int launch_corrector(const DevProblem& p, void* stream);
 int launch_sources_record(const DevProblem& p, void* stream);
-int launch_sensitivity(int ngll, const float* rec, const float* lam, const float* u_lo, const float* u_mid,
-                       const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec, double c_m,
-                       double c_k, void* stream);
-// solver layout [nglob][shots][kNodeStride] <-> caller layout [shots][nglob][3]
-int launch_pack(const float* u, float* out, int nglob, int shots, void* stream);
-int launch_unpack(const float* in, float* u, int nglob, int shots, void* stream);
+// u_lo, u_mid, u_hi: caller layout and order [nglob][3] (perm: internal -> caller node)
+int launch_sensitivity(int ngll, const float* rec, const int* perm, const float* lam, const float* u_lo,
+                       const float* u_mid, const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec,
+                       double c_m, double c_k, void* stream);
+// solver layout [nglob][shots][kNodeStride] in internal node order <-> caller layout
+// [shots][nglob][3] in caller node order (perm: internal -> caller node)
+int launch_pack(const float* u, float* out, const int* perm, int nglob, int shots, void* stream);
+int launch_unpack(const float* in, float* u, const int* perm, int nglob, int shots, void* stream);
 int launch_adjoint_update(float* F, const float* G_dev, const int* rec_node, int nrec, const float* lam,
                           float* lam_old, const float* minv, int nglob, double dt, void* stream);
 // Material on the device (Sec. II-B moduli, Sec. I diagonal mass). rho, p1, p2: per local
@@ -123,6 +197,7 @@ int launch_adjoint_update(float* F, const float* G_dev, const int* rec_node, int
 struct MaterialLaunch {
   float* rec;          // colour-sorted element records
   const int* order;    // record slot -> caller element
+  const int* elist;    // record slots in element colour order (the ranges below index it)
   const float* rho;
   const float* p1;
   const float* p2;
@@ -150,7 +225,8 @@ struct CtxView {
   int device;
   void* stream;
   int nglob;
-  const float* minv;
+  const float* minv;     // internal node order
+  const int* node_new;   // caller node -> internal node
 };
 // SEM_OK and the view when the material is set; otherwise an error code (message set).
 int ctx_view(sem_ctx_fwd* c, CtxView* out);

@@ -15,9 +15,11 @@ namespace semgb {
   int upload_basis_##n(const double* w, const double* h, void* stream, int ngll);                         \
   int launch_forces_##n(const ForceLaunch& L, void* stream);                                              \
   int forces_smem_bytes_##n();                                                                            \
-  int launch_sensitivity_##n(const float* rec, const float* lam, const float* u_lo, const float* u_mid,  \
-                             const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec, \
-                             double c_m, double c_k, void* stream);
+  int launch_patch_forces_##n(const PatchLaunch& L, void* stream);                                        \
+  void patch_shape_##n(PatchShape* out);                                                                  \
+  int launch_sensitivity_##n(const float* rec, const int* perm, const float* lam, const float* u_lo,       \
+                             const float* u_mid, const float* u_hi, double* g_rho, double* g_kappa,     \
+                             double* g_mu, int nspec, double c_m, double c_k, void* stream);
 SEM_DECLARE_ORDER(2)
 SEM_DECLARE_ORDER(3)
 SEM_DECLARE_ORDER(4)
@@ -56,13 +58,28 @@ int launch_forces(int n, const ForceLaunch& L, void* stream) {
   return static_cast<int>(cudaErrorInvalidValue);
 }
 
-int launch_sensitivity(int n, const float* rec, const float* lam, const float* u_lo, const float* u_mid,
-                       const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec, double c_m,
-                       double c_k, void* stream) {
-#define SEM_CALL(k) launch_sensitivity_##k(rec, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k, stream)
+int launch_sensitivity(int n, const float* rec, const int* perm, const float* lam, const float* u_lo,
+                       const float* u_mid, const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec,
+                       double c_m, double c_k, void* stream) {
+#define SEM_CALL(k) \
+  launch_sensitivity_##k(rec, perm, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k, stream)
   SEM_ORDER_SWITCH(n, SEM_CALL)
 #undef SEM_CALL
   return static_cast<int>(cudaErrorInvalidValue);
+}
+
+int launch_patch_forces(int n, const PatchLaunch& L, void* stream) {
+#define SEM_CALL(k) launch_patch_forces_##k(L, stream)
+  SEM_ORDER_SWITCH(n, SEM_CALL)
+#undef SEM_CALL
+  return static_cast<int>(cudaErrorInvalidValue);
+}
+
+int patch_shape(int n, PatchShape* out) {
+#define SEM_CALL(k) (patch_shape_##k(out), 0)
+  SEM_ORDER_SWITCH(n, SEM_CALL)
+#undef SEM_CALL
+  return -1;
 }
 
 int forces_kernel_smem_bytes(int n) {
@@ -237,8 +254,9 @@ __global__ void material_records_kernel(MaterialLaunch m) {
     point_moduli(m, q, &rh, &kappa, &mu, &vp);
     float* r = m.rec + s * RW;
     const int qq = i * n * n + j + n * k;
-    r[kKappa * np + qq] = static_cast<float>(kappa);
-    r[kMu * np + qq] = static_cast<float>(mu);
+    const double J = r[kJac * np + qq];
+    r[kJKappa * np + qq] = static_cast<float>(J * kappa);
+    r[kJMu * np + qq] = static_cast<float>(J * mu);
   }
 }
 
@@ -248,11 +266,12 @@ __global__ void mass_color_kernel(MaterialLaunch m, int e0, int e1, double* mass
   const size_t RW = (static_cast<size_t>(kRecFields) * np + 3) / 4 * 4;
   for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
        t += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const long long s = e0 + t / np;
-    const int p = static_cast<int>(t - (s - e0) * np);
+    const long long it = t / np;
+    const long long s = m.elist[e0 + it];  // record slot
+    const int p = static_cast<int>(t - it * np);
     const int i = p % n, j = (p / n) % n, k = p / (n * n);
     const float* r = m.rec + s * RW;
-    const uint32_t g = __float_as_uint(r[kIbool * np + p]) & ~kFirstTouchBit;
+    const uint32_t g = __float_as_uint(r[kIbool * np + p]) & kNodeMask;
     const double J = r[kJac * np + i * n * n + j + n * k];
     const double rh = m.rho[static_cast<size_t>(m.order[s]) * np + p];
     mass[g] += rh * J * m.w[i] * m.w[j] * m.w[k];  // elements of one colour share no node
@@ -299,46 +318,49 @@ int launch_material_apply(const MaterialLaunch& m, const int* sweep_off, int nra
   return static_cast<int>(cudaGetLastError());
 }
 
-// Layout changes between the solver's fields [nglob][shots][4] and the caller's arrays
-// [shots][nglob][3] (state copies, displacement snapshots). One thread per (node, shot).
-__global__ void pack_kernel(const float4* __restrict__ u, float* __restrict__ out, long long nglob, int shots) {
+// Layout changes between the solver's fields [nglob][shots][4] (internal node order) and the
+// caller's arrays [shots][nglob][3] (caller node order): state copies, displacement
+// snapshots. One thread per (node, shot).
+__global__ void pack_kernel(const float4* __restrict__ u, float* __restrict__ out, const int* __restrict__ perm,
+                            long long nglob, int shots) {
   const long long n = nglob * shots;
   for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
        t += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long g = shots == 1 ? t : t / shots;
     const long long sh = t - g * shots;
     const float4 v = u[t];
-    float* o = out + 3 * (sh * nglob + g);
+    float* o = out + 3 * (sh * nglob + perm[g]);
     o[0] = v.x;
     o[1] = v.y;
     o[2] = v.z;
   }
 }
 
-__global__ void unpack_kernel(const float* __restrict__ in, float4* __restrict__ u, long long nglob, int shots) {
+__global__ void unpack_kernel(const float* __restrict__ in, float4* __restrict__ u, const int* __restrict__ perm,
+                              long long nglob, int shots) {
   const long long n = nglob * shots;
   for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
        t += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long g = shots == 1 ? t : t / shots;
     const long long sh = t - g * shots;
-    const float* i = in + 3 * (sh * nglob + g);
+    const float* i = in + 3 * (sh * nglob + perm[g]);
     u[t] = make_float4(i[0], i[1], i[2], 0.f);
   }
 }
 
-int launch_pack(const float* u, float* out, int nglob, int shots, void* stream) {
+int launch_pack(const float* u, float* out, const int* perm, int nglob, int shots, void* stream) {
   const long long n = static_cast<long long>(nglob) * shots;
   if (n == 0) return 0;
   pack_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(reinterpret_cast<const float4*>(u), out,
-                                                                             nglob, shots);
+                                                                             perm, nglob, shots);
   return static_cast<int>(cudaGetLastError());
 }
 
-int launch_unpack(const float* in, float* u, int nglob, int shots, void* stream) {
+int launch_unpack(const float* in, float* u, const int* perm, int nglob, int shots, void* stream) {
   const long long n = static_cast<long long>(nglob) * shots;
   if (n == 0) return 0;
   unpack_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(in, reinterpret_cast<float4*>(u),
-                                                                               nglob, shots);
+                                                                               perm, nglob, shots);
   return static_cast<int>(cudaGetLastError());
 }
 

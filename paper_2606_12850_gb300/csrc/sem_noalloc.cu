@@ -3,7 +3,6 @@
 // instead of memory from cudaMalloc; the caller passes u, v and f = -K u.
 #include <cuda_runtime.h>
 
-#include <atomic>
 #include <string>
 
 #include "sem.h"
@@ -22,19 +21,16 @@ constexpr long long kNoAllocMaxNodes = static_cast<long long>(kNoAllocSlots) * k
 // process exits. All calls share it; a call overwrites the slots it uses before reading them.
 static __device__ __align__(256) double g_energy_scratch[2 * kNoAllocSlots];
 
-// Device address of g_energy_scratch per device ordinal (host code may not use the symbol
-// itself as an address).
-std::atomic<double*> g_scratch_addr[64];
-
 __global__ void __launch_bounds__(kNoAllocThreads)
     block_sums_kernel(const float* __restrict__ u, const float* __restrict__ v, const float* __restrict__ f,
-                      const float* __restrict__ minv, int nglob, double* __restrict__ scratch) {
+                      const float* __restrict__ minv, const int* __restrict__ node_new, int nglob,
+                      double* __restrict__ scratch) {
   __shared__ double sk[kNoAllocThreads], sp[kNoAllocThreads];
   const long long first = static_cast<long long>(blockIdx.x) * kNoAllocNodesPerBlock;
   const long long last = min(first + kNoAllocNodesPerBlock, static_cast<long long>(nglob));
   double kin = 0.0, pot = 0.0;
   for (long long g = first + threadIdx.x; g < last; g += kNoAllocThreads) {
-    const float m = minv[g];
+    const float m = minv[node_new[g]];  // u, v, f are in caller node order, minv internal
     const double vx = v[3 * g], vy = v[3 * g + 1], vz = v[3 * g + 2];
     if (m > 0.f) kin += (vx * vx + vy * vy + vz * vz) / static_cast<double>(m);
     pot += static_cast<double>(u[3 * g]) * f[3 * g] + static_cast<double>(u[3 * g + 1]) * f[3 * g + 1] +
@@ -88,7 +84,8 @@ using namespace semgb;
 
 extern "C" int sem_energy_noalloc(sem_ctx* ctx, int nglob, const float* u_dev, const float* v_dev,
                                   const float* f_dev, double* out) {
-  if (nglob > kNoAllocMaxNodes || nglob < 0)
+  if (nglob < 0) return ctx_fail(ctx, SEM_EINVAL, "sem_energy_noalloc: nglob must be >= 0");
+  if (nglob > kNoAllocMaxNodes)
     return ctx_fail(ctx, SEM_EINVAL,
                     ("sem_energy_noalloc: nglob = " + std::to_string(nglob) + " exceeds the maximum of " +
                      std::to_string(kNoAllocMaxNodes) + " nodes that its fixed scratch array supports")
@@ -100,19 +97,21 @@ extern "C" int sem_energy_noalloc(sem_ctx* ctx, int nglob, const float* u_dev, c
   if (!u_dev || !v_dev || !f_dev || !out) return ctx_fail(ctx, SEM_EINVAL, "sem_energy_noalloc: NULL pointer");
   cudaError_t e = cudaSetDevice(cv.device);
   if (e != cudaSuccess) return ctx_fail(ctx, SEM_ECUDA, cudaGetErrorString(e));
-  if (cv.device < 0 || cv.device >= 64) return ctx_fail(ctx, SEM_EINVAL, "sem_energy_noalloc: device ordinal >= 64");
-  double* scratch = g_scratch_addr[cv.device].load();
-  if (!scratch) {  // first call on this device: resolve the array's device address
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_energy_scratch);
-    if (e != cudaSuccess)
-      return ctx_fail(ctx, SEM_ECUDA, (std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
-    scratch = static_cast<double*>(p);
-    g_scratch_addr[cv.device].store(scratch);
-  }
   cudaStream_t s = static_cast<cudaStream_t>(cv.stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return ctx_fail(ctx, SEM_ECUDA, cudaGetErrorString(e));
+  if (cap != cudaStreamCaptureStatusNone)
+    return ctx_fail(ctx, SEM_ESTATE, "sem_energy_noalloc: the context's stream is capturing (the call synchronizes)");
+  // the array's device address on the current device, looked up on every call (cheap, no
+  // allocation, and never stale)
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_energy_scratch);
+  if (e != cudaSuccess)
+    return ctx_fail(ctx, SEM_ECUDA, (std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
+  double* scratch = static_cast<double*>(p);
   const int nblocks = nglob > 0 ? (nglob + kNoAllocNodesPerBlock - 1) / kNoAllocNodesPerBlock : 1;
-  block_sums_kernel<<<nblocks, kNoAllocThreads, 0, s>>>(u_dev, v_dev, f_dev, cv.minv, nglob, scratch);
+  block_sums_kernel<<<nblocks, kNoAllocThreads, 0, s>>>(u_dev, v_dev, f_dev, cv.minv, cv.node_new, nglob, scratch);
   final_sum_kernel<<<1, kNoAllocThreads, 0, s>>>(scratch, nblocks);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -28,6 +28,7 @@ SIGNATURES = {
     "sem_version": (_I, []),
     "sem_gll": (_I, [_I, _P, _P, _P]),
     "sem_color_elements": (_I, [_I, _I, _I, _P, _P, _P]),
+    "sem_patch_plan": (_I, [_I, _I, _I, _P, _P, _P, _P]),
     "sem_geometry": (_I, [_I, _I, _P, _P, _P, _P]),
     "sem_locate_points": (_I, [_I, _P, _I, _P, _P, _P]),
     "sem_point_source_forces": (_I, [_I, _P, _P, _P, _P, _P]),
@@ -61,6 +62,7 @@ SIGNATURES = {
     "sem_check_finite": (_I, [_P]),
     "sem_apply_stiffness": (_I, [_P, _P, _P]),
     "sem_apply_stiffness_strided": (_I, [_P, _P, _P, _I]),
+    "sem_node_order": (_I, [_P, _P]),
     "sem_energy": (_I, [_P, _P]),
     "sem_adjoint_begin": (_I, [_P]),
     "sem_adjoint_step": (_I, [_P, _P]),
@@ -77,6 +79,7 @@ SIGNATURES = {
     "sem_group_last_error": (ctypes.c_char_p, [_P]),
     "sem_info": (_I, [_P, _P]),
     "sem_color_counts": (_I, [_P, _P]),
+    "sem_patch_info": (_I, [_P, _P]),
     "sem_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -122,14 +125,20 @@ def _host(a, dtype, shape=None):
     return arr, arr.ctypes.data_as(_P)
 
 
-def _dev(t, nvalues=None):
-    """Device address of a contiguous float32 CUDA tensor (or an int address)."""
+def _dev(t, nvalues=None, ctx=None):
+    """Device address of a contiguous float32 CUDA tensor on the context's GPU (or an int
+    address, taken as is). Checked before any library call: a tensor of another dtype would
+    be read or written at the wrong byte size, one on another GPU at a foreign address."""
     if t is None:
         return None
     if isinstance(t, int):
         return _P(t)
     if not (hasattr(t, "is_cuda") and t.is_cuda):
         raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != "torch.float32":
+        raise TypeError(f"device tensor must be float32, got {t.dtype}")
+    if ctx is not None and t.device.index != ctx.device:
+        raise ValueError(f"device tensor is on cuda:{t.device.index}, the context on cuda:{ctx.device}")
     if not t.is_contiguous():
         raise ValueError("device tensor must be contiguous")
     if nvalues is not None and t.numel() < nvalues:
@@ -147,6 +156,7 @@ class Ctx:
         self.nspec = 0
         self.nrec = 0
         self.shots = 1
+        self.device = 0
 
     def __del__(self):
         if getattr(self, "handle", None) is not None and _lib is not None:
@@ -229,7 +239,9 @@ def sem_create(ngll: int, device: int = 0, stream=None) -> Ctx:
     if stream is not None:
         s = _P(stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().sem_create(ctypes.byref(out), ngll, device, s), "sem_create")
-    return Ctx(out.value, ngll)
+    c = Ctx(out.value, ngll)
+    c.device = int(device)
+    return c
 
 
 def sem_destroy(ctx: Ctx):
@@ -240,6 +252,7 @@ def sem_destroy(ctx: Ctx):
 
 SEM_OPT_SWEEP_SLABS = 1
 SEM_OPT_CONTRACTION = 2
+SEM_OPT_ASSEMBLY = 3
 
 
 def sem_set_option(ctx: Ctx, option: int, value: int):
@@ -275,7 +288,8 @@ def sem_set_moduli(ctx: Ctx, rho, kappa, mu):
 
 def sem_set_moduli_dev(ctx: Ctx, rho, kappa, mu):
     n = ctx.nspec * ctx.ngll ** 3
-    _check(lib().sem_set_moduli_dev(ctx.handle, _dev(rho, n), _dev(kappa, n), _dev(mu, n)), "sem_set_moduli_dev", ctx)
+    _check(lib().sem_set_moduli_dev(ctx.handle, _dev(rho, n, ctx), _dev(kappa, n, ctx), _dev(mu, n, ctx)),
+           "sem_set_moduli_dev", ctx)
 
 
 def sem_suggest_dt(ctx: Ctx, courant: float) -> float:
@@ -369,7 +383,8 @@ def sem_set_state(ctx: Ctx, u=None, v=None, a=None):
 
 def sem_set_state_dev(ctx: Ctx, u=None, v=None, a=None):
     n = 3 * ctx.nglob * ctx.shots
-    _check(lib().sem_set_state_dev(ctx.handle, _dev(u, n), _dev(v, n), _dev(a, n)), "sem_set_state_dev", ctx)
+    _check(lib().sem_set_state_dev(ctx.handle, _dev(u, n, ctx), _dev(v, n, ctx), _dev(a, n, ctx)), "sem_set_state_dev",
+           ctx)
 
 
 def sem_set_step(ctx: Ctx, step: int):
@@ -390,7 +405,8 @@ def sem_get_state(ctx: Ctx, want=(True, True, True)):
 
 def sem_get_state_dev(ctx: Ctx, u=None, v=None, a=None):
     n = 3 * ctx.nglob * ctx.shots
-    _check(lib().sem_get_state_dev(ctx.handle, _dev(u, n), _dev(v, n), _dev(a, n)), "sem_get_state_dev", ctx)
+    _check(lib().sem_get_state_dev(ctx.handle, _dev(u, n, ctx), _dev(v, n, ctx), _dev(a, n, ctx)), "sem_get_state_dev",
+           ctx)
 
 
 def sem_step(ctx: Ctx, nsteps: int):
@@ -410,13 +426,13 @@ def sem_run(ctx: Ctx, nsteps: int, record: bool = True, out=None):
 
 
 def sem_run_dev(ctx: Ctx, nsteps: int, seis_dev=None):
-    _check(lib().sem_run_dev(ctx.handle, int(nsteps), _dev(seis_dev, ctx.shots * ctx.nrec * 3 * nsteps)),
+    _check(lib().sem_run_dev(ctx.handle, int(nsteps), _dev(seis_dev, ctx.shots * ctx.nrec * 3 * nsteps, ctx)),
            "sem_run_dev", ctx)
 
 
 def sem_run_snapshots(ctx: Ctx, nsteps: int, u_dev):
     n = 3 * ctx.nglob * ctx.shots * int(nsteps)
-    _check(lib().sem_run_snapshots(ctx.handle, int(nsteps), _dev(u_dev, n)), "sem_run_snapshots", ctx)
+    _check(lib().sem_run_snapshots(ctx.handle, int(nsteps), _dev(u_dev, n, ctx)), "sem_run_snapshots", ctx)
 
 
 def sem_check_finite(ctx: Ctx):
@@ -425,12 +441,12 @@ def sem_check_finite(ctx: Ctx):
 
 def sem_apply_stiffness(ctx: Ctx, u_dev, f_dev):
     n = 3 * ctx.nglob
-    _check(lib().sem_apply_stiffness(ctx.handle, _dev(u_dev, n), _dev(f_dev, n)), "sem_apply_stiffness", ctx)
+    _check(lib().sem_apply_stiffness(ctx.handle, _dev(u_dev, n, ctx), _dev(f_dev, n, ctx)), "sem_apply_stiffness", ctx)
 
 
 def sem_apply_stiffness_strided(ctx: Ctx, u_dev, f_dev, node_stride: int):
     n = node_stride * ctx.nglob
-    _check(lib().sem_apply_stiffness_strided(ctx.handle, _dev(u_dev, n), _dev(f_dev, n), int(node_stride)),
+    _check(lib().sem_apply_stiffness_strided(ctx.handle, _dev(u_dev, n, ctx), _dev(f_dev, n, ctx), int(node_stride)),
            "sem_apply_stiffness_strided", ctx)
 
 
@@ -445,7 +461,7 @@ def sem_energy_noalloc(ctx: Ctx, u_dev, v_dev, f_dev, nglob: int | None = None):
     n = ctx.nglob if nglob is None else int(nglob)
     out = np.zeros(2)
     m = 3 * min(n, ctx.nglob)
-    _check(lib().sem_energy_noalloc(ctx.handle, n, _dev(u_dev, m), _dev(v_dev, m), _dev(f_dev, m),
+    _check(lib().sem_energy_noalloc(ctx.handle, n, _dev(u_dev, m, ctx), _dev(v_dev, m, ctx), _dev(f_dev, m, ctx),
                                     out.ctypes.data_as(_P)), "sem_energy_noalloc", ctx)
     return float(out[0]), float(out[1])
 
@@ -455,12 +471,12 @@ def sem_adjoint_begin(ctx: Ctx):
 
 
 def sem_adjoint_step(ctx: Ctx, G_dev=None):
-    _check(lib().sem_adjoint_step(ctx.handle, _dev(G_dev, 3 * ctx.nrec)), "sem_adjoint_step", ctx)
+    _check(lib().sem_adjoint_step(ctx.handle, _dev(G_dev, 3 * ctx.nrec, ctx)), "sem_adjoint_step", ctx)
 
 
 def sem_adjoint_accumulate(ctx: Ctx, u_lo, u_mid, u_hi):
     n = 3 * ctx.nglob
-    _check(lib().sem_adjoint_accumulate(ctx.handle, _dev(u_lo, n), _dev(u_mid, n), _dev(u_hi, n)),
+    _check(lib().sem_adjoint_accumulate(ctx.handle, _dev(u_lo, n, ctx), _dev(u_mid, n, ctx), _dev(u_hi, n, ctx)),
            "sem_adjoint_accumulate", ctx)
 
 
@@ -473,8 +489,8 @@ def sem_adjoint_gradients(ctx: Ctx):
 
 
 def sem_adjoint_segment(ctx: Ctx, count: int, G_dev, u_dev):
-    _check(lib().sem_adjoint_segment(ctx.handle, int(count), _dev(G_dev, 3 * ctx.nrec * int(count)),
-                                     _dev(u_dev, 3 * ctx.nglob * (int(count) + 2))), "sem_adjoint_segment", ctx)
+    _check(lib().sem_adjoint_segment(ctx.handle, int(count), _dev(G_dev, 3 * ctx.nrec * int(count), ctx),
+                                     _dev(u_dev, 3 * ctx.nglob * (int(count) + 2), ctx)), "sem_adjoint_segment", ctx)
 
 
 def sem_autotune(ctx: Ctx, reps: int = 5):
@@ -526,6 +542,36 @@ def sem_info(ctx: Ctx) -> dict:
     _check(lib().sem_info(ctx.handle, out.ctypes.data_as(_P)), "sem_info", ctx)
     keys = ("nspec", "nglob", "ngll", "ncolors", "steps", "device_bytes", "shots", "slabs", "launches")
     return {k: int(v) for k, v in zip(keys, out)}
+
+
+def sem_node_order(ctx: Ctx) -> np.ndarray:
+    """perm[i] = caller node of the solver's internal node i."""
+    out = np.zeros(ctx.nglob, dtype=np.int32)
+    _check(lib().sem_node_order(ctx.handle, out.ctypes.data_as(_P)), "sem_node_order", ctx)
+    return out
+
+
+def sem_patch_info(ctx: Ctx) -> dict:
+    out = np.zeros(8, dtype=np.int64)
+    _check(lib().sem_patch_info(ctx.handle, out.ctypes.data_as(_P)), "sem_patch_info", ctx)
+    keys = ("patches", "colors", "max_nodes", "tables", "bx", "by", "bz", "assembly")
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
+def sem_patch_plan(ngll: int, ibool, nglob: int):
+    """Host-only: (patch of every element, colour of every patch, info dict) of the patches
+    the library builds for this mesh."""
+    ib = np.ascontiguousarray(ibool, dtype=np.int32)
+    nspec = ib.size // (ngll ** 3)
+    patch_of = np.zeros(nspec, dtype=np.int32)
+    color_of = np.full(nspec, -1, dtype=np.int32)
+    info = np.zeros(7, dtype=np.int64)
+    _check(lib().sem_patch_plan(int(ngll), int(nspec), int(nglob), ib.ctypes.data_as(_P),
+                                patch_of.ctypes.data_as(_P), color_of.ctypes.data_as(_P),
+                                info.ctypes.data_as(_P)), "sem_patch_plan")
+    keys = ("patches", "colors", "max_nodes", "tables", "bx", "by", "bz")
+    d = {k: int(v) for k, v in zip(keys, info)}
+    return patch_of, color_of[:d["patches"]], d
 
 
 def sem_color_counts(ctx: Ctx) -> np.ndarray:

@@ -94,20 +94,24 @@ def test_stiffness_several_tiles(oracle, ngll, n):
 
 
 def test_stiffness_strided_matches(oracle):
-    """The stride-4 entry point (the solver's own field layout) gives the same forces."""
+    """The stride-4 entry point (the solver's own field layout, internal node order) gives
+    the same forces."""
     mesh = inputs.structured_hex_mesh((4, 3, 3), 5, 600.0, jitter=0.2, seed=2)
     mat = random_material(mesh, 3)
     ctx = make_ctx(mesh, *mat)
+    perm = sem.sem_node_order(ctx)
+    assert np.array_equal(np.sort(perm), np.arange(mesh.nglob))
     u = inputs.random_field(mesh.nglob, 4)
     u4 = np.zeros((mesh.nglob, 4), dtype=np.float32)
-    u4[:, :3] = u
+    u4[:, :3] = u[perm]
     torch.cuda.synchronize()
     ud = torch.from_numpy(u4).cuda()
     fd = torch.full_like(ud, float("nan"))
     torch.cuda.synchronize()
     sem.sem_apply_stiffness_strided(ctx, ud, fd, 4)
     sem.sem_sync(ctx)
-    f4 = fd.cpu().numpy()
+    f4 = np.empty((mesh.nglob, 4), dtype=np.float32)
+    f4[perm] = fd.cpu().numpy()
     f_ref = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, *mat, 5).forces(u.astype(np.float64))
     check_forces(f4[:, :3], f_ref)
     assert np.all(f4[:, 3] == 0.0)

@@ -70,3 +70,51 @@ def test_splitmix64_known_answers():
     assert abs(z.mean()) < 4 * se and abs(z.var() - 1.0) < 4 * np.sqrt(2.0) * se
     assert np.array_equal(inputs.uniform(7, (5,), stream=3), inputs.uniform(7, (5,), stream=3))
     assert not np.array_equal(inputs.uniform(7, (5,), stream=3), inputs.uniform(7, (5,), stream=4))
+
+
+class _FakeDevice:
+    def __init__(self, index):
+        self.index = index
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor: only the attributes the binding inspects."""
+
+    is_cuda = True
+
+    def __init__(self, dtype, device, n=12, contiguous=True):
+        self.dtype = dtype
+        self.device = _FakeDevice(device)
+        self._n = n
+        self._contiguous = contiguous
+
+    def is_contiguous(self):
+        return self._contiguous
+
+    def numel(self):
+        return self._n
+
+    def data_ptr(self):  # never reached by the rejected cases
+        raise AssertionError("the address of a rejected tensor was taken")
+
+
+def test_device_arrays_checked_before_any_library_call():
+    """A float16/bfloat16 tensor (half the byte size the kernels assume), a tensor on
+    another GPU, a non-contiguous or too-small tensor are refused by the binding itself."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    from paper_2606_12850_gb300 import sem
+    ctx = sem.Ctx(0, 5)
+    ctx.handle = None  # no library context: a call that got through would fail differently
+    ctx.device, ctx.nglob = 0, 4
+    for dt in (torch.float16, torch.bfloat16, torch.float64, torch.int32):
+        with pytest.raises(TypeError):
+            sem._dev(_FakeCudaTensor(dt, 0), 12, ctx)
+    with pytest.raises(ValueError, match="cuda:1"):
+        sem._dev(_FakeCudaTensor(torch.float32, 1), 12, ctx)
+    with pytest.raises(ValueError, match="contiguous"):
+        sem._dev(_FakeCudaTensor(torch.float32, 0, contiguous=False), 12, ctx)
+    with pytest.raises(ValueError, match="needs 12"):
+        sem._dev(_FakeCudaTensor(torch.float32, 0, n=11), 12, ctx)
+    with pytest.raises(TypeError):
+        sem.sem_apply_stiffness(ctx, _FakeCudaTensor(torch.float16, 0), _FakeCudaTensor(torch.float32, 0))
