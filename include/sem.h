@@ -138,15 +138,27 @@ int sem_destroy(sem_ctx* ctx);
  *   owners, 2 = per point; sem_autotune sets it from measurement. */
 #define SEM_OPT_CONTRACTION 2
 /*   SEM_OPT_ASSEMBLY (takes effect at once): how the force sweep assembles element forces
- *   on the context's own single-shot fields. 0 (default) = patches: bricks of neighbouring
- *   elements (2 x 2 x 2 at NGLL 5; sem_patch_info gives the shape) evaluated by one CTA
- *   each, which gathers the brick's distinct nodes once, sums the forces meeting at each of
- *   them in a fixed order and writes each once; the bricks are coloured so that no two of
- *   a colour share a node (Sec. IV-C's colouring applied to groups of elements). 1 =
- *   element by element, one launch per element colour (the form always used for several
- *   shots and for caller-layout arrays). Both are deterministic; they differ only in the
- *   order of the float32 sums at shared nodes. */
+ *   on the context's own single-shot fields. Patches are bricks of neighbouring elements
+ *   (2 x 2 x 2 at NGLL 5; sem_patch_info gives the shape) evaluated by one CTA each, which
+ *   sums the forces meeting at each of the brick's nodes in a fixed order and writes each
+ *   node once; the bricks are coloured so that no two of a colour share a node (Sec. IV-C's
+ *   colouring applied to groups of elements).
+ *     0 (default) = patches, one launch per patch colour;
+ *     1 = element by element, one launch per element colour (the form always used for
+ *       several shots and for caller-layout arrays);
+ *     2 = patches, all colours in one persistent launch: CTAs take patches in sweep order
+ *       and a patch writes only after every patch of the previous colour has finished (a
+ *       bounded wait; if one gives up, the next sem_sync, sem_run or sem_check_finite
+ *       returns SEM_ETIMEOUT).
+ *   0 and 2 give bitwise equal results; 1 differs from them only in the order of the
+ *   float32 sums at shared nodes. All are deterministic. */
 #define SEM_OPT_ASSEMBLY 3
+/*   SEM_OPT_SWEEP_STALL_TEST (failure-detection test, one-shot): 1 makes the next direct
+ *   persistent sweep (SEM_OPT_ASSEMBLY 2, sem_apply_stiffness_strided with stride 4) wait
+ *   for a count that never arrives, so that its bounded waits give up and the next sem_sync
+ *   returns SEM_ETIMEOUT; the sweep after that runs normally. Sweeps replayed from a
+ *   captured time step are not affected. */
+#define SEM_OPT_SWEEP_STALL_TEST 4
 int sem_set_option(sem_ctx* ctx, int option, long long value);
 
 /* Set the mesh (Sec. II-B hexahedral mesh, Sec. IV-C global-to-local map).

@@ -43,7 +43,9 @@ struct sem_ctx {
   std::vector<int> sweep_off;       // element-list ranges, one per (slab, colour) launch
   std::vector<int> pcolor_off;      // patch ranges, one per patch colour
   int npatch = 0, pmax_nodes = 0, ptables = 0;
-  int assembly = 0;                 // SEM_OPT_ASSEMBLY: 0 patches where they apply, 1 elements
+  int stall_test = 0;               // SEM_OPT_SWEEP_STALL_TEST (one-shot)
+  int assembly = 0;                 // SEM_OPT_ASSEMBLY: 0 patches, one launch per colour,
+                                    // 1 elements, 2 persistent patch sweep
   int slabs = 1;                    // spatial slabs of the sweep order
   int slabs_opt = 0;                // requested slab count (0 = automatic)
   std::vector<float> rec;           // colour-sorted element records (host copy)
@@ -64,6 +66,8 @@ struct sem_ctx {
   PatchDesc* d_pdesc = nullptr;   // patches in sweep order
   uint16_t* d_pslots = nullptr;   // patch tables: shared patch node -> local points meeting there
   uint32_t* d_pexcl = nullptr;    // patch tables: local points alone at their patch node
+  int* d_pcolor_end = nullptr;    // per patch colour, the end of its patch range
+  SweepSync* d_sync = nullptr;    // counters of the persistent sweep
   float *d_u = nullptr, *d_v = nullptr, *d_a = nullptr, *d_minv = nullptr;
   float* d_f = nullptr;           // scratch force buffer for sem_energy
   float *d_lam = nullptr, *d_lam_old = nullptr, *d_lamF = nullptr;  // adjoint fields [nglob][4]
@@ -132,7 +136,7 @@ int dev_alloc(sem_ctx* c, T** p, size_t count) {
 }
 
 void free_device(sem_ctx* c) {
-  void* ptrs[] = {c->d_rec, c->d_order, c->d_elist, c->d_perm, c->d_node_new, c->d_pdesc, c->d_pslots, c->d_pexcl, c->d_u, c->d_v,
+  void* ptrs[] = {c->d_rec, c->d_order, c->d_elist, c->d_perm, c->d_node_new, c->d_pdesc, c->d_pslots, c->d_pexcl, c->d_pcolor_end, c->d_sync, c->d_u, c->d_v,
                   c->d_a, c->d_minv, c->d_f, c->d_partials, c->d_lam, c->d_lam_old, c->d_lamF, c->d_grad,
                   c->d_ctl, c->d_src_node, c->d_src_shot, c->d_src_force, c->d_rec_node};
   for (void* p : ptrs)
@@ -145,6 +149,8 @@ void free_device(sem_ctx* c) {
   c->d_pdesc = nullptr;
   c->d_pslots = nullptr;
   c->d_pexcl = nullptr;
+  c->d_pcolor_end = nullptr;
+  c->d_sync = nullptr;
   c->d_u = c->d_v = c->d_a = c->d_minv = c->d_f = nullptr;
   c->d_lam = c->d_lam_old = c->d_lamF = nullptr;
   c->d_grad = nullptr;
@@ -200,7 +206,7 @@ int set_device(sem_ctx* c) {
 // SEM_OPT_ASSEMBLY = 1) the element kernel walks the element list slab by slab and, inside a
 // slab, colour by colour: a launch holds elements of one colour only.
 int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int shots) {
-  if (c->assembly == 0 && node_stride == kNodeStride && shots == 1 && c->npatch > 0) {
+  if (c->assembly != 1 && node_stride == kNodeStride && shots == 1 && c->npatch > 0) {
     PatchLaunch P{};
     P.rec = c->d_rec;
     P.desc = c->d_pdesc;
@@ -209,6 +215,17 @@ int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int
     P.u = u;
     P.f = f;
     P.variant = c->variant;
+    const int npc = static_cast<int>(c->pcolor_off.size()) - 1;
+    if (c->assembly == 2 && npc <= kMaxSweepColors) {
+      P.sync = c->d_sync;
+      P.color_end = c->d_pcolor_end;
+      P.npatch = c->npatch;
+      P.ncolors = npc;
+      P.stall = c->stall_test;
+      c->stall_test = 0;
+      SEM_LAUNCH(c, launch_patch_forces(c->ngll, P, c->stream));
+      return SEM_OK;
+    }
     for (size_t k = 0; k + 1 < c->pcolor_off.size(); ++k) {
       P.p0 = c->pcolor_off[k];
       P.p1 = c->pcolor_off[k + 1];
@@ -301,6 +318,19 @@ int advance(sem_ctx* c, int nsteps, float* seis_dev) {
   }
   c->steps += nsteps;
   return SEM_OK;
+}
+
+// After the stream is idle: SEM_ETIMEOUT (and the flag cleared) if a wait of the persistent
+// sweep gave up since the last check.
+int check_sweep_timeout(sem_ctx* c) {
+  if (!c->d_sync) return SEM_OK;
+  int err = 0;
+  SEM_CUDA(c, cudaMemcpyAsync(&err, &c->d_sync->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (!err) return SEM_OK;
+  SEM_CUDA(c, cudaMemsetAsync(&c->d_sync->err, 0, sizeof(int), c->stream));
+  SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return fail(c, SEM_ETIMEOUT, "a bounded wait of the force sweep gave up (the forces of that sweep are incomplete)");
 }
 
 // Completes a pending state: a = M^-1 a_raw, v = v_half + dt/2 a.
@@ -507,8 +537,13 @@ int sem_set_option(sem_ctx* c, int option, long long value) {
       c->variant = static_cast<int>(value);
       drop_graph(c);
       return SEM_OK;
+    case SEM_OPT_SWEEP_STALL_TEST:
+      if (value < 0 || value > 1) return fail(c, SEM_EINVAL, "stall test must be 0 or 1");
+      c->stall_test = static_cast<int>(value);
+      return SEM_OK;
     case SEM_OPT_ASSEMBLY:
-      if (value < 0 || value > 1) return fail(c, SEM_EINVAL, "assembly must be 0 (patches) or 1 (elements)");
+      if (value < 0 || value > 2)
+        return fail(c, SEM_EINVAL, "assembly must be 0 (patch colours), 1 (elements) or 2 (persistent patch sweep)");
       c->assembly = static_cast<int>(value);
       drop_graph(c);
       return SEM_OK;
@@ -701,7 +736,9 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
       (r = dev_alloc(c, &c->d_elist, elist.size())) || (r = dev_alloc(c, &c->d_pdesc, pdesc.size())) ||
       (r = dev_alloc(c, &c->d_perm, c->perm.size())) || (r = dev_alloc(c, &c->d_node_new, c->node_new.size())) ||
       (r = dev_alloc(c, &c->d_pslots, std::max<size_t>(plan.csr.size(), kPatchSlots))) ||
-      (r = dev_alloc(c, &c->d_pexcl, plan.excl.size())) || (r = dev_alloc(c, &c->d_u, nf)) ||
+      (r = dev_alloc(c, &c->d_pexcl, plan.excl.size())) ||
+      (r = dev_alloc(c, &c->d_pcolor_end, static_cast<size_t>(plan.ncolors))) || (r = dev_alloc(c, &c->d_sync, 1)) ||
+      (r = dev_alloc(c, &c->d_u, nf)) ||
       (r = dev_alloc(c, &c->d_v, nf)) || (r = dev_alloc(c, &c->d_a, nf)) ||
       (r = dev_alloc(c, &c->d_minv, static_cast<size_t>(nglob))))
     return r;
@@ -721,6 +758,9 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
                                 cudaMemcpyHostToDevice, c->stream));
   SEM_CUDA(c, cudaMemcpyAsync(c->d_pexcl, plan.excl.data(), plan.excl.size() * sizeof(uint32_t),
                               cudaMemcpyHostToDevice, c->stream));
+  SEM_CUDA(c, cudaMemcpyAsync(c->d_pcolor_end, plan.color_off.data() + 1, plan.ncolors * sizeof(int),
+                              cudaMemcpyHostToDevice, c->stream));
+  SEM_CUDA(c, cudaMemsetAsync(c->d_sync, 0, sizeof(SweepSync), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_u, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_v, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_a, 0, nf * sizeof(float), c->stream));
@@ -1196,6 +1236,7 @@ int sem_check_finite(sem_ctx* c) {
   int bad = 0;
   SEM_CUDA(c, cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   SEM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if ((r = check_sweep_timeout(c))) return r;
   if (bad)
     return fail(c, SEM_EDIVERGED,
                 "non-finite displacement, velocity or acceleration after " + std::to_string(c->steps) +
@@ -1299,7 +1340,7 @@ int sem_sync(sem_ctx* c) {
   int r = set_device(c);
   if (r) return r;
   SEM_CUDA(c, cudaStreamSynchronize(c->stream));
-  return SEM_OK;
+  return check_sweep_timeout(c);
 }
 
 int sem_info(sem_ctx* c, int64_t* out) {

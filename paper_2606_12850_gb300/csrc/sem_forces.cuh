@@ -109,6 +109,13 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void wait_prerequisite_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Iterations of a bounded spin (each with a 128 ns sleep): about half a second.
+constexpr unsigned int kSweepSpinLimit = 1u << 22;
 __device__ __forceinline__ void allow_dependent_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Barrier of one team: the warp, a named barrier (1 + team) over the team's TEAM threads
@@ -603,34 +610,23 @@ struct PatchCfg {
   static_assert(E >= 1 && 10 * NP <= ES, "team and workspace sizes");
 };
 
+constexpr uint32_t kAlone = 0x80000000u;  // in the shared-memory copy of an ibool word: the
+                                          // point is the only one at its patch node
+
+// Phases 1-3 of one patch for the calling thread's team: gather through the records' ibool
+// words (GB points per thread in flight; the shared-memory word keeps the node, the patch
+// first-touch flag and kAlone), then the element forces.
 template <int N, bool LO>
-__global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
-    patch_forces_kernel(const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
-                        const uint16_t* __restrict__ slot_tab, const uint32_t* __restrict__ excl_tab,
-                        const float4* __restrict__ u, float4* __restrict__ f, int p0) {
+__device__ __forceinline__ void patch_gather_compute(const PatchDesc& d, const float* __restrict__ rec,
+                                                     const uint32_t* __restrict__ excl_tab,
+                                                     const float4* __restrict__ u, float* wsb) {
   using C = PatchCfg<N>;
-  constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, REC = C::REC, T = C::T;
-  constexpr uint32_t kAlone = 0x80000000u;  // in the shared-memory copy of an ibool word: the
-                                            // point is the only one at its patch node
-  extern __shared__ float4 smem4[];
-  float* wsb = reinterpret_cast<float*>(smem4);
-  const PatchDesc d = desc[p0 + blockIdx.x];
-  const int tid = threadIdx.x;
-  const int team = tid / TEAM;
-  const int tl = tid - team * TEAM;
-  auto ws_of = [&](int le) { return wsb + (le / E) * C::TS + (le % E) * ES; };
+  constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, REC = C::REC;
+  const int team = threadIdx.x / TEAM;
+  const int tl = threadIdx.x - team * TEAM;
   const int ne = min(E, d.nelem - team * E);  // this team's elements
   const float* __restrict__ trec = rec + static_cast<size_t>(d.slot0 + team * E) * REC;
   const uint32_t* __restrict__ excl = excl_tab + d.excl_off;
-
-  // 0. records to L2 while the previous grid finishes, then wait for its results
-  if (tid < d.nelem)
-    prefetch_l2(rec + static_cast<size_t>(d.slot0 + tid) * REC, kForceFields * NP * sizeof(float));
-  wait_prerequisite_grid();
-  allow_dependent_grid();
-
-  // 1. gather, one thread per local point of the team's elements, GB points in flight; the
-  //    shared-memory word keeps the node, the patch first-touch flag and kAlone
   constexpr int GB = 4;
   float* ts = wsb + team * C::TS;
   for (int base = tl; base < ne * NP; base += GB * TEAM) {
@@ -664,46 +660,70 @@ __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
       }
     }
   }
-
-  // 2-3. element forces, team by team; 4a. every team adds the forces of its points that are
-  //      alone at their patch node to the node (store at its first touch), as the element
-  //      kernel does, before any CTA barrier
   if (C::KIND == 2 || ne > 0) {
     team_sync<C::KIND, TEAM>(team);
     team_element_forces<N, C::KIND, TEAM, ES, LO>(ts, tl, ne, team,
                                                   [&](int le) { return trec + static_cast<size_t>(le) * REC; });
-    for (int base = tl; base < ne * NP; base += GB * TEAM) {
-      uint32_t w[GB];
-      float4 prev[GB];
+  }
+}
+
+// Previous value of a node of f: through L1 (COHERENT false: f was last written by an
+// earlier grid) or from L2 (COHERENT true: other CTAs of this grid wrote it).
+template <bool COHERENT>
+__device__ __forceinline__ float4 load_f(const float4* p) {
+  if constexpr (COHERENT)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
+// Phase 4a for the calling thread's team: the forces of its points that are alone at their
+// patch node added to the node (stored at its first touch).
+template <int N, bool COHERENT>
+__device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __restrict__ f, const float* wsb) {
+  using C = PatchCfg<N>;
+  constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, GB = 4;
+  const int team = threadIdx.x / TEAM;
+  const int tl = threadIdx.x - team * TEAM;
+  const int ne = min(E, d.nelem - team * E);
+  const float* ts = wsb + team * C::TS;
+  for (int base = tl; base < ne * NP; base += GB * TEAM) {
+    uint32_t w[GB];
+    float4 prev[GB];
 #pragma unroll
-      for (int r = 0; r < GB; ++r) {
-        const int idx = base + r * TEAM;
-        w[r] = 0u;
-        prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < ne * NP) {
-          const int e = idx / NP;
-          w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
-          if ((w[r] & kAlone) && !(w[r] & kPatchFirstBit)) prev[r] = f[w[r] & kNodeMask];
-        }
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      w[r] = 0u;
+      prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (idx < ne * NP) {
+        const int e = idx / NP;
+        w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
+        if ((w[r] & kAlone) && !(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + (w[r] & kNodeMask));
       }
+    }
 #pragma unroll
-      for (int r = 0; r < GB; ++r) {
-        const int idx = base + r * TEAM;
-        if (w[r] & kAlone) {
-          const int e = idx / NP;
-          const float* src = ts + e * ES + 3 * (idx - e * NP);
-          f[w[r] & kNodeMask] = make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
-        }
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      if (w[r] & kAlone) {
+        const int e = idx / NP;
+        const float* src = ts + e * ES + 3 * (idx - e * NP);
+        f[w[r] & kNodeMask] = make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
       }
     }
   }
-  __syncthreads();
+}
 
-  // 4b. per shared patch node: the sum of its local points' forces in table order (its slots
-  //     read as one 16-byte word), then one store (first touch) or one read-modify-write; the
-  //     previous values of GB nodes are loaded before any of them is written
+// Phase 4b over the CTA: per shared patch node, the sum of its local points' forces in table
+// order (its slots read as one 16-byte word), then one store (first touch) or one
+// read-modify-write; the previous values of GB nodes are loaded before any is written.
+template <int N, bool COHERENT>
+__device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uint16_t* __restrict__ slot_tab,
+                                                   float4* __restrict__ f, const float* wsb) {
+  using C = PatchCfg<N>;
+  constexpr int NP = C::NP, E = C::E, ES = C::ES, T = C::T, GB = 4;
+  auto ws_of = [&](int le) { return wsb + (le / E) * C::TS + (le % E) * ES; };
   const uint4* __restrict__ slots = reinterpret_cast<const uint4*>(slot_tab + d.slot_off);
-  for (int base = tid; base < d.nshared; base += GB * T) {
+  for (int base = threadIdx.x; base < d.nshared; base += GB * T) {
     uint4 sl[GB];
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
@@ -719,7 +739,7 @@ __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
       const int le0 = q0 / NP;
       w[r] = t < d.nshared ? reinterpret_cast<const uint32_t*>(ws_of(le0) + 9 * NP)[q0 - le0 * NP] : kPatchFirstBit;
       prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (!(w[r] & kPatchFirstBit)) prev[r] = f[w[r] & kNodeMask];
+      if (!(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + (w[r] & kNodeMask));
     }
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
@@ -749,6 +769,148 @@ __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
         }
         f[w[r] & kNodeMask] = make_float4(prev[r].x + sx, prev[r].y + sy, prev[r].z + sz, 0.f);
       }
+    }
+  }
+}
+
+// One launch per patch colour: one CTA per patch of the colour [p0, p0 + gridDim.x).
+template <int N, bool LO>
+__global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
+    patch_forces_kernel(const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
+                        const uint16_t* __restrict__ slot_tab, const uint32_t* __restrict__ excl_tab,
+                        const float4* __restrict__ u, float4* __restrict__ f, int p0) {
+  using C = PatchCfg<N>;
+  extern __shared__ float4 smem4[];
+  float* wsb = reinterpret_cast<float*>(smem4);
+  const PatchDesc d = desc[p0 + blockIdx.x];
+  // 0. records to L2 while the previous grid finishes, then wait for its results
+  if (threadIdx.x < d.nelem)
+    prefetch_l2(rec + static_cast<size_t>(d.slot0 + threadIdx.x) * C::REC, kForceFields * C::NP * sizeof(float));
+  wait_prerequisite_grid();
+  allow_dependent_grid();
+  patch_gather_compute<N, LO>(d, rec, excl_tab, u, wsb);
+  patch_write_alone<N, false>(d, f, wsb);  // no wait for the other teams
+  __syncthreads();
+  patch_write_shared<N, false>(d, slot_tab, f, wsb);
+}
+
+// Persistent form: one sweep (all patch colours) in one launch. CTAs take patches in sweep
+// order from sync->next, the next one as soon as they start on the current one (whose
+// records are then bulk-prefetched into L2 while the current one is processed). A patch of
+// colour c > 0 writes f only once every patch of colour c - 1 has finished
+// (sync->done[c - 1] == the colour's patch count; one thread waits with a bounded spin,
+// then the CTA reads f from L2), then counts itself into sync->done[c]. Every patch waits
+// only on patches taken before it, so the sweep completes however many CTAs are resident.
+// The last CTA to leave resets the counters for the next sweep. A wait that gives up sets
+// sync->err and ends its CTA early (the host reports SEM_ETIMEOUT).
+struct SweepShared {
+  PatchDesc d;  // the current patch
+  int next;     // the patch taken next
+  int color;    // colour of the current patch
+  int ready;    // every patch of the previous colour had finished when the patch began
+  int abort;
+};
+
+template <int N>
+__device__ __forceinline__ void prefetch_patch_records(const float* __restrict__ rec,
+                                                       const PatchDesc* __restrict__ desc, int P, int npatch) {
+  using C = PatchCfg<N>;
+  if (P < npatch && threadIdx.x < 32) {
+    const PatchDesc dn = desc[P];
+    if (static_cast<int>(threadIdx.x) < dn.nelem)
+      prefetch_l2(rec + static_cast<size_t>(dn.slot0 + threadIdx.x) * C::REC, kForceFields * C::NP * sizeof(float));
+  }
+}
+
+// Patches of the previous colour (c - 1) needed before a patch of colour c may write.
+__device__ __forceinline__ unsigned int prior_colour_count(const int* __restrict__ color_end, int c,
+                                                           unsigned int stall) {
+  // (stall != 0: a count that never arrives, so that a test can make the wait give up)
+  return stall ? 0xFFFFFFFFu : static_cast<unsigned int>(color_end[c - 1] - (c > 1 ? color_end[c - 2] : 0));
+}
+
+// One patch of the persistent sweep (kept out of line so that nothing of its body is held
+// in registers across patches). Returns the patch taken next, or -1 after a wait gave up.
+// When the previous colour had already finished as the patch began (the common case once a
+// colour is under way), the teams write their lone points as soon as their elements are
+// done, as in the per-colour kernel; otherwise one thread waits (bounded) first.
+template <int N, bool LO>
+__device__ __noinline__ int sweep_one_patch(int P, const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
+                                            const uint16_t* __restrict__ slot_tab,
+                                            const uint32_t* __restrict__ excl_tab, const float4* __restrict__ u,
+                                            float4* __restrict__ f, int npatch, const int* __restrict__ color_end,
+                                            unsigned int stall, SweepSync* sync, SweepShared* sh, float* wsb) {
+  __syncthreads();  // every thread is done with sh before it is replaced
+  if (threadIdx.x == 0) {
+    sh->d = desc[P];
+    sh->next = static_cast<int>(atomicAdd(&sync->next, 1u));
+    int c = 0;  // the first colour whose range ends beyond P
+    while (color_end[c] <= P) ++c;
+    sh->color = c;
+    sh->ready = c == 0 || ld_acquire_gpu(&sync->done[c - 1]) >= prior_colour_count(color_end, c, stall);
+  }
+  __syncthreads();
+  const PatchDesc& d = sh->d;
+  prefetch_patch_records<N>(rec, desc, sh->next, npatch);
+  patch_gather_compute<N, LO>(d, rec, excl_tab, u, wsb);
+  const int c = sh->color;
+  if (sh->ready) {
+    patch_write_alone<N, true>(d, f, wsb);
+    __syncthreads();
+  } else {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned int need = prior_colour_count(color_end, c, stall);
+      unsigned int spins = 0;
+      while (ld_acquire_gpu(&sync->done[c - 1]) < need) {
+        if (++spins > kSweepSpinLimit) {
+          atomicExch(&sync->err, 1);
+          sh->abort = 1;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __syncthreads();  // the wait is over for the CTA
+    if (sh->abort) return -1;
+    patch_write_alone<N, true>(d, f, wsb);
+  }
+  patch_write_shared<N, true>(d, slot_tab, f, wsb);
+  __syncthreads();  // all of the patch's writes issued before it counts as done
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&sync->done[c], 1u);
+  }
+  return sh->next;
+}
+
+template <int N, bool LO>
+__global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
+    patch_sweep_kernel(const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
+                       const uint16_t* __restrict__ slot_tab, const uint32_t* __restrict__ excl_tab,
+                       const float4* __restrict__ u, float4* __restrict__ f, int npatch,
+                       const int* __restrict__ color_end, int ncolors, unsigned int stall, SweepSync* sync) {
+  extern __shared__ float4 smem4[];
+  float* wsb = reinterpret_cast<float*>(smem4);
+  __shared__ SweepShared sh;
+  wait_prerequisite_grid();  // the previous sweep's counter reset and the previous grid's u, f
+  if (threadIdx.x == 0) {
+    sh.next = static_cast<int>(atomicAdd(&sync->next, 1u));
+    sh.abort = 0;
+    sh.ready = 0;
+  }
+  __syncthreads();
+  int P = sh.next;
+  prefetch_patch_records<N>(rec, desc, P, npatch);
+  while (P >= 0 && P < npatch)
+    P = sweep_one_patch<N, LO>(P, rec, desc, slot_tab, excl_tab, u, f, npatch, color_end, stall, sync, &sh, wsb);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&sync->exited, 1u) == gridDim.x - 1) {  // every CTA has left: reset
+      sync->next = 0u;
+      for (int c = 0; c < ncolors; ++c) sync->done[c] = 0u;
+      sync->exited = 0u;
+      __threadfence();
     }
   }
 }
@@ -936,10 +1098,9 @@ int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
 template <bool LO>
 int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
   using C = PatchCfg<SEM_NGLL>;
-  static std::atomic<unsigned long long> attr_done{0};
-  if (int r = raise_smem_limit(attr_done, patch_forces_kernel<SEM_NGLL, LO>, C::SMEM)) return r;
+  static std::atomic<unsigned long long> attr_done{0}, attr_done_p{0};
+  static std::atomic<int> resident[64];  // CTAs of the persistent kernel per SM, per device
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(L.p1 - L.p0);
   cfg.blockDim = dim3(C::T);
   cfg.dynamicSmemBytes = C::SMEM;
   cfg.stream = s;
@@ -948,13 +1109,35 @@ int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (L.sync) {  // one persistent launch for the whole sweep
+    if (int r = raise_smem_limit(attr_done_p, patch_sweep_kernel<SEM_NGLL, LO>, C::SMEM)) return r;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per_sm = resident[dev & 63].load();
+    if (per_sm <= 0) {
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, patch_sweep_kernel<SEM_NGLL, LO>, C::T,
+                                                                    C::SMEM);
+      if (e != cudaSuccess) return static_cast<int>(e);
+      per_sm = per_sm < 1 ? 1 : per_sm;
+      resident[dev & 63].store(per_sm);
+    }
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    cfg.gridDim = dim3(static_cast<unsigned>(sms * per_sm));
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_sweep_kernel<SEM_NGLL, LO>, L.rec, L.desc, L.slots, L.excl,
+                                               reinterpret_cast<const float4*>(L.u), reinterpret_cast<float4*>(L.f),
+                                               L.npatch, L.color_end, L.ncolors, L.stall ? 1u : 0u, L.sync));
+  }
+  if (int r = raise_smem_limit(attr_done, patch_forces_kernel<SEM_NGLL, LO>, C::SMEM)) return r;
+  cfg.gridDim = dim3(L.p1 - L.p0);
   return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO>, L.rec, L.desc, L.slots, L.excl,
                                              reinterpret_cast<const float4*>(L.u), reinterpret_cast<float4*>(L.f),
                                              L.p0));
 }
 
 int launch_patch_n(const PatchLaunch& L, cudaStream_t s) {
-  if (L.p1 <= L.p0) return 0;
+  if (L.sync ? L.npatch <= 0 : L.p1 <= L.p0) return 0;
   using C = ForceCfg<SEM_NGLL>;
   const bool lo = L.variant == 0 ? C::LINE_OWNERS : L.variant == 1;
   return lo ? launch_patch_lo<true>(L, s) : launch_patch_lo<false>(L, s);

@@ -161,11 +161,25 @@ struct alignas(16) PatchDesc {
   int excl_off;  // its table: bit mask of the local points alone at their patch node
   int pad0, pad1, pad2;
 };
+// Counters of a persistent sweep (all patch colours in one launch): patches taken, CTAs
+// that have left, a wait that gave up, patches finished per colour. Zero between sweeps.
+constexpr int kMaxSweepColors = 64;
+struct SweepSync {
+  unsigned int next;
+  unsigned int exited;
+  int err;
+  int pad;
+  unsigned int done[kMaxSweepColors];
+};
 struct PatchLaunch {
   const float* rec;
   const PatchDesc* desc;
   const uint16_t* slots;
   const uint32_t* excl;
+  SweepSync* sync;        // non-null: one persistent launch over all colours
+  const int* color_end;   // per colour, the end of its patch range (persistent launch)
+  int npatch, ncolors;    // (persistent launch)
+  int stall;              // (persistent launch) wait for a count that never arrives (tests)
   const float* u;
   float* f;
   int p0, p1;

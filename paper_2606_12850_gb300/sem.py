@@ -253,6 +253,7 @@ def sem_destroy(ctx: Ctx):
 SEM_OPT_SWEEP_SLABS = 1
 SEM_OPT_CONTRACTION = 2
 SEM_OPT_ASSEMBLY = 3
+SEM_OPT_SWEEP_STALL_TEST = 4
 
 
 def sem_set_option(ctx: Ctx, option: int, value: int):

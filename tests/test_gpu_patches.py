@@ -161,3 +161,44 @@ def test_patch_degenerate_meshes(oracle, shape):
     u = inputs.random_field(mesh.nglob, 12)
     f_ref = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, *mat, 5).forces(u.astype(np.float64))
     check_forces(sweep_stride4(ctx, u, 0), f_ref)
+
+
+def test_persistent_sweep_equals_colour_launches():
+    """All colours in one persistent launch (assembly 2) against one launch per patch colour
+    (assembly 0): the same sums in the same order, so bitwise equal; repeated sweeps too
+    (the launch's counters reset themselves)."""
+    mesh = inputs.structured_hex_mesh((9, 7, 6), 5, 1000.0, jitter=0.1, seed=3)
+    mat = material(mesh, 13)
+    ctx = make_ctx(5, mesh.ibool, mesh.ctrl, mesh.nglob, mat)
+    u = inputs.random_field(mesh.nglob, 14)
+    f0 = sweep_stride4(ctx, u, 0)
+    f2 = sweep_stride4(ctx, u, 2)
+    assert np.array_equal(f0, f2)
+    for _ in range(3):
+        assert np.array_equal(sweep_stride4(ctx, u, 2), f0)
+
+
+def test_persistent_sweep_wait_gives_up_and_recovers(oracle):
+    """Failure detection without a fault: a sweep whose waits target a count that never
+    arrives gives up within its bound, the host reads SEM_ETIMEOUT, and the next sweep is
+    complete and correct."""
+    mesh = inputs.structured_hex_mesh((6, 4, 4), 5, 800.0, jitter=0.1, seed=5)
+    mat = material(mesh, 15)
+    ctx = make_ctx(5, mesh.ibool, mesh.ctrl, mesh.nglob, mat)
+    u = inputs.random_field(mesh.nglob, 16)
+    sem.sem_set_option(ctx, sem.SEM_OPT_ASSEMBLY, 2)
+    sem.sem_set_option(ctx, sem.SEM_OPT_SWEEP_STALL_TEST, 1)
+    perm = sem.sem_node_order(ctx)
+    u4 = np.zeros((len(perm), 4), dtype=np.float32)
+    u4[:, :3] = u[perm]
+    torch.cuda.synchronize()
+    ud = torch.from_numpy(u4).cuda()
+    fd = torch.zeros_like(ud)
+    torch.cuda.synchronize()
+    sem.sem_apply_stiffness_strided(ctx, ud, fd, 4)
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_sync(ctx)
+    assert ei.value.code == -5 and "gave up" in str(ei.value)
+    sem.sem_sync(ctx)  # the flag was cleared
+    f_ref = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, *mat, 5).forces(u.astype(np.float64))
+    check_forces(sweep_stride4(ctx, u, 2), f_ref)
