@@ -47,7 +47,8 @@ def parse_args():
     p.add_argument("--stiffness-reps", type=int, default=40)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    p.add_argument("--cpu-seconds", type=float, default=20.0,
+                   help="target time of the all-cores CPU baseline (steps of the full mesh, at most 20)")
     p.add_argument("--shots", type=int, default=32, help="batched-shot measurement (0 = skip)")
     p.add_argument("--shot-steps", type=int, default=100)
     p.add_argument("--no-sweep", action="store_true", help="skip the NGLL 3/5/7/9 (h,p) sweep")
@@ -55,6 +56,7 @@ def parse_args():
     p.add_argument("--surrogate-runs", type=int, default=4096, help="surrogate training runs (0 = skip)")
     p.add_argument("--models", type=int, default=16, help="uneven-models group measurement (0 = skip)")
     p.add_argument("--no-iso", action="store_true", help="skip the (h,p) iso-accuracy study")
+    p.add_argument("--no-ablation", action="store_true", help="skip the colouring/atomics assembly ablation")
     p.add_argument("--surrogate-epochs", type=int, default=150)
     return p.parse_args()
 
@@ -84,7 +86,8 @@ def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_12850_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name in ("sem_forces.cuh", "sem_internal.h") or (name.startswith("sem_forces_") and name.endswith(".cu")):
+        if name in ("sem_forces.cuh", "sem_internal.h", "sem_patches.cpp") or (
+                name.startswith("sem_forces_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(f.read())
     return h.hexdigest()[:16]
@@ -93,7 +96,7 @@ def kernel_source_hash() -> str:
 def profiled_traffic(ngll: int):
     """DRAM bytes per force-kernel launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", f"forces_kernel_ngll{ngll}_layered.md")
+    path = os.path.join(ROOT, "profiles", f"patch_forces_kernel_ngll{ngll}_layered.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -179,35 +182,57 @@ def dist_env():
     return rank, world, local
 
 
-def oracle_sample_rate(ngll: int, seconds: float, steps_hint: int | None = None):
-    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: a smaller
-    cube of the same recipe (same NGLL, layering, jitter, receivers), enough steps for about
-    ``seconds`` of CPU time. Returns (local-pt updates/s, sample description, steps, time)."""
-    from oracle import sem_oracle
+def host_cpu() -> dict:
+    """Cores this process may run on and the CPU model (from /proc/cpuinfo)."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = "unknown"
+    try:
+        info = open("/proc/cpuinfo").read()
+        m = re.search(r"^model name\s*:\s*(.+)$", info, re.M)
+        if m:
+            model = m.group(1).strip()
+        else:  # Arm: implementer and part numbers
+            imp = re.search(r"^CPU implementer\s*:\s*(\S+)", info, re.M)
+            part = re.search(r"^CPU part\s*:\s*(\S+)", info, re.M)
+            if imp and part:
+                model = f"Arm implementer {imp.group(1)} part {part.group(1)}"
+    except OSError:
+        pass
+    return {"cores": cores, "model": model}
+
+
+def compiled_baseline(ngll: int, elems: int | None, seconds: float = 20.0, max_steps: int = 20):
+    """The compiled FP64 CPU baseline (oracle/sem_cpu.c, pinned to the numpy oracle) on the
+    full workload mesh: all host cores (OpenMP over the elements of one colour) for up to
+    ``max_steps`` steps sized to about ``seconds``, and one core for one step. Returns a dict
+    with local-pt updates/s per mode, the steps timed and the host description."""
+    from oracle import sem_cpu, sem_oracle
     from paper_2606_12850_gb300 import inputs
 
-    probe = inputs.layered_cube(ngll, n=6, nsteps=2)
-    m = sem_oracle.build_model(probe)
+    w = inputs.layered_cube(ngll, n=elems, nsteps=max_steps)
     t = time.perf_counter()
-    sem_oracle.newmark_run(m, 1e-4, 2)
-    per_elem_step = (time.perf_counter() - t) / (2 * probe.mesh.nspec)
-    n = 16
-    nsteps = max(2, int(seconds / (per_elem_step * n ** 3)))
-    if steps_hint is not None:
-        nsteps = steps_hint
-    w = inputs.layered_cube(ngll, n=n, nsteps=nsteps)
     m = sem_oracle.build_model(w)
     dt = m.cfl_dt(w.courant)
-    src, rec = sem_oracle.locate_workload(m, w)
-    t = time.perf_counter()
-    sem_oracle.newmark_run(m, dt, nsteps, src_nodes=src, src_force=w.source_force, f0=w.f0, t0=w.t0,
-                           rec_nodes=rec)
-    el = time.perf_counter() - t
-    rate = w.mesh.nlocal * nsteps / el
-    desc = (f"FP64 numpy oracle, {n}^3-element three-layer jittered cube at NGLL={ngll} "
-            f"(1/{(inputs.LAYERED_ELEMS.get(ngll, 64) / n) ** 3:.0f} of the benchmark mesh), {nsteps} steps, "
-            f"{el:.1f} s, single thread")
-    return rate, desc, nsteps, el
+    src, _ = sem_oracle.locate_workload(m, w)
+    setup_s = time.perf_counter() - t
+    host = host_cpu()
+    nloc = w.mesh.nlocal
+    out = {"host": host, "setup_s": setup_s, "mesh": f"{w.mesh.nx}^3 NGLL={ngll}", "nlocal": nloc}
+    kw = dict(src_node=int(src[0]), src_force=w.source_force[0], f0=w.f0, t0=w.t0)
+    for mode, threads in (("all_cores", host["cores"]), ("one_core", 1)):
+        cb = sem_cpu.CpuBaseline(m, threads)
+        t = time.perf_counter()
+        u, v, a = cb.run(dt, 1, **kw)
+        one = time.perf_counter() - t
+        steps = 1
+        el = one
+        if mode == "all_cores":
+            steps = int(max(1, min(max_steps, seconds / max(one, 1e-9))))
+            t = time.perf_counter()
+            cb.run(dt, steps, u=u, v=v, a=a, **kw)
+            el = time.perf_counter() - t
+        out[mode] = {"threads": threads, "steps": steps, "seconds": el, "updates_per_s": nloc * steps / el}
+    return out
 
 
 def workload_name(args) -> str:
@@ -219,45 +244,92 @@ def workload_name(args) -> str:
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands (its compiled FP64 baseline, pinned to the
+    numpy oracle) on the host cores, on the same workload; the whole mesh when K + W steps
+    of it fit in about two and a half minutes, else each step on the largest sub-cube of
+    the same recipe that does."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle import sem_oracle
+    from oracle import sem_cpu, sem_oracle
     from paper_2606_12850_gb300 import inputs
 
-    # each step: one oracle time step on a sub-cube sized so that the run takes ~2 minutes
-    budget = 120.0
-    probe = inputs.layered_cube(args.ngll, n=6, nsteps=2)
-    m = sem_oracle.build_model(probe)
+    budget = 150.0
+    host = host_cpu()
+    full = args.elems or inputs.LAYERED_ELEMS.get(args.ngll, 64)
+    n = full
+    while True:
+        w = inputs.layered_cube(args.ngll, n=n, nsteps=args.steps)
+        m = sem_oracle.build_model(w)
+        cb = sem_cpu.CpuBaseline(m, host["cores"])
+        dt = m.cfl_dt(w.courant)
+        src, _ = sem_oracle.locate_workload(m, w)
+        kw = dict(src_node=int(src[0]), src_force=w.source_force[0], f0=w.f0, t0=w.t0)
+        t = time.perf_counter()
+        u, v, a = cb.run(dt, 1, **kw)
+        one = time.perf_counter() - t
+        if (args.steps + args.warmup) * one <= budget or n <= 4:
+            break
+        n = max(4, int(n * ((budget / ((args.steps + args.warmup) * one)) ** (1 / 3))))
+    u, v, a = cb.run(dt, max(0, args.warmup - 1), u=u, v=v, a=a, **kw)
     t = time.perf_counter()
-    sem_oracle.newmark_run(m, 1e-4, 2)
-    per_elem_step = (time.perf_counter() - t) / (2 * probe.mesh.nspec)
-    per_step = budget / max(1, args.steps + args.warmup)
-    n = int(max(2, min(16, round((per_step / per_elem_step) ** (1 / 3)))))
-    w = inputs.layered_cube(args.ngll, n=n, nsteps=args.steps)
-    m = sem_oracle.build_model(w)
-    dt = m.cfl_dt(w.courant)
-    src, rec = sem_oracle.locate_workload(m, w)
-    kw = dict(src_nodes=src, src_force=w.source_force, f0=w.f0, t0=w.t0, rec_nodes=rec)
-    _, u, v, a = sem_oracle.newmark_run(m, dt, args.warmup, **kw)
-    t = time.perf_counter()
-    sem_oracle.newmark_run(m, dt, args.steps, u0=u, v0=v, a0=a, **kw)
+    cb.run(dt, args.steps, u=u, v=v, a=a, **kw)
     el = time.perf_counter() - t
     value = w.mesh.nlocal * args.steps / el
-    sample = (f"FP64 numpy oracle, each step on a {n}^3-element cube of the same recipe "
-              f"(three-layer, jittered, NGLL={args.ngll}), single thread")
+    sample = (f"compiled FP64 CPU baseline of the oracle (oracle/sem_cpu.c, pinned to the numpy oracle) on "
+              f"{host['cores']} host threads ({host['model']}), each step on the "
+              + ("full workload mesh" if n == full else f"{n}^3-element cube of the same recipe (a bounded sample)"))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_name(args), "ngll": args.ngll, "parallelism": "single host thread",
-                   "sample_per_step": f"{n}^3 elements of the same recipe (a bounded sample of the workload)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": workload_name(args), "ngll": args.ngll,
+                   "parallelism": f"{host['cores']} host threads, colour by colour",
+                   "sample_per_step": "the full mesh" if n == full else f"{n}^3 elements of the same recipe"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": host["cores"], "kind": "oracle", "sample": sample,
+                         "cpu_model": host["model"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_assembly_ablation(device: int, reps: int = 20):
+    """Sec. V-D-1's colouring ablation on GB300: one stiffness sweep of the benchmark mesh
+    (NGLL 5: 64^3, NGLL 9: 32^3) with the default patch assembly, the element-by-element
+    coloured assembly, and the element kernel with float atomics instead of colours (one
+    launch, f zeroed first). CUDA events, mean of ``reps`` sweeps after three untimed ones."""
+    import torch
+
+    from paper_2606_12850_gb300 import inputs, sem
+
+    out = []
+    for ngll in (5, 9):
+        w = inputs.layered_cube(ngll, nsteps=10)
+        stream = torch.cuda.Stream(device=device)
+        s = sem.setup_workload(w, device=device, stream=stream)
+        with torch.cuda.stream(stream):
+            ud = (torch.rand(4 * w.mesh.nglob, device="cuda") - 0.5) * 2e-3
+            fd = torch.empty_like(ud)
+        stream.synchronize()
+        row = {"ngll": ngll, "elements": f"{w.mesh.nx}^3"}
+        for name, asm in (("patch_colours_ms", 0), ("element_colours_ms", 1), ("element_atomic_ms", 3)):
+            sem.sem_set_option(s.ctx, sem.SEM_OPT_ASSEMBLY, asm)
+            for _ in range(3):
+                sem.sem_apply_stiffness_strided(s.ctx, ud, fd, 4)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a, b in evs:
+                a.record(stream)
+                sem.sem_apply_stiffness_strided(s.ctx, ud, fd, 4)
+                b.record(stream)
+            stream.synchronize()
+            row[name] = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        row["atomic_over_element_colours"] = row["element_atomic_ms"] / row["element_colours_ms"]
+        out.append(row)
+        del s
+        torch.cuda.empty_cache()
+    return {"rows": out, "paper_lx2": "removing the colouring (atomics) costs 1.16x at p = 15 (Sec. V-D-1)"}
 
 
 def measure_batched(args, device: int):
@@ -286,7 +358,7 @@ def measure_batched(args, device: int):
         b.synchronize()
         return a.elapsed_time(b) / steps
 
-    sem.sem_set_sources(plain.ctx, nodes[:1], force[:1], w.f0, w.t0)
+    sem.sem_set_source_nodes(plain.ctx, nodes[:1], force[:1], w.f0, w.t0)
     ms_plain = timed(plain.ctx, K)
     batch = sem.setup_workload(w, device=device, stream=stream, src_nodes=nodes[:1], rec_nodes=plain.rec_nodes)
     sem.sem_set_shots(batch.ctx, S)
@@ -299,7 +371,7 @@ def measure_batched(args, device: int):
     u_b, _, _ = sem.sem_get_state(batch.ctx, want=(True, False, False))
     errs = []
     for sh in (0, S - 1):
-        sem.sem_set_sources(plain.ctx, nodes[sh:sh + 1], force[sh:sh + 1], w.f0, w.t0)
+        sem.sem_set_source_nodes(plain.ctx, nodes[sh:sh + 1], force[sh:sh + 1], w.f0, w.t0)
         sem.sem_set_state(plain.ctx)
         sem.sem_run(plain.ctx, 200)
         u_p, _, _ = sem.sem_get_state(plain.ctx, want=(True, False, False))
@@ -483,7 +555,7 @@ def plane_wave_error(ngll: int, nz: int, periods: float, steps_per_period: int, 
     mesh = inputs.structured_hex_mesh((2, 2, nz), ngll, (2 * h, 2 * h, 8 * lam), periodic=True)
     one = np.ones(mesh.nspec)
     ctx = sem.sem_create(ngll, device)
-    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
     sem.sem_set_material(ctx, inputs.per_point(mesh, 2500 * one), inputs.per_point(mesh, vp * one),
                          inputs.per_point(mesh, 1730 * one))
     k = 2 * np.pi / lam
@@ -503,7 +575,7 @@ def plane_wave_error(ngll: int, nz: int, periods: float, steps_per_period: int, 
     rec = np.nonzero(on_x & on_y)[0]
     if rec.size == 0:
         raise RuntimeError("no station line found")
-    sem.sem_set_receivers(ctx, rec)
+    sem.sem_set_receiver_nodes(ctx, rec)
     sem.sem_set_state(ctx, u0, v0, None)
     sem.sem_init_acceleration(ctx)
     seis = sem.sem_run(ctx, n)
@@ -645,7 +717,8 @@ def run_ours(args):
     s = sem.setup_workload(w, device=local, stream=stream)
     ctx = s.ctx
     info = sem.sem_info(ctx)
-    ncolors = info["ncolors"]
+    pinfo = sem.sem_patch_info(ctx)
+    ncolors = pinfo["colors"]
     alg = algorithmic_bytes(mesh.nspec, mesh.ngll, mesh.nglob)
     nrec = len(s.rec_nodes)
 
@@ -739,6 +812,10 @@ def run_ours(args):
     if not args.no_iso:
         iso = measure_iso_accuracy(local)
 
+    ablation = None
+    if not args.no_ablation:
+        ablation = measure_assembly_ablation(local)
+
     models = None
     if args.models > 0:
         models = measure_models(local, args.models)
@@ -749,8 +826,15 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, desc, _, _ = oracle_sample_rate(args.ngll, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        cb = compiled_baseline(args.ngll, args.elems, seconds=args.cpu_seconds)
+        h = cb["host"]
+        cpu = {"value": cb["all_cores"]["updates_per_s"], "unit": UNIT, "cores": h["cores"], "kind": "oracle",
+               "sample": (f"compiled FP64 CPU baseline of the oracle (oracle/sem_cpu.c, pinned to the numpy oracle), "
+                          f"the full {cb['mesh']} workload mesh, {cb['all_cores']['steps']} steps on "
+                          f"{h['cores']} host threads (OpenMP over the elements of one colour)"),
+               "cpu_model": h["model"],
+               "one_core": {"value": cb["one_core"]["updates_per_s"], "steps": 1},
+               "all_cores": cb["all_cores"], "setup_s": cb["setup_s"]}
 
     if rank == 0:
         line = {
@@ -764,14 +848,16 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": f"forces_kernel<{mesh.ngll}> (all {ncolors} colour launches of one stiffness "
-                                   "application)",
+                         "kernel": f"patch_forces_kernel<{mesh.ngll}> (all {ncolors} patch-colour launches of one "
+                                   f"stiffness application; bricks of {pinfo['bx']}x{pinfo['by']}x{pinfo['bz']} "
+                                   "elements)",
                          "sweep_ms": sweep_ms, "peak_source": peak_src},
             "hbm_roofline_step": {"achieved": step_gbs, "frac": step_gbs / peak, "unit": "GB/s",
                                   "bytes_per_step": alg["step"]},
             "global_pt_updates_per_s": world * mesh.nglob * K / (ms / 1e3),
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clock_info,
             "batched_shots": batched, "uneven_models": models, "hp_sweep": sweep, "iso_accuracy": iso,
+            "assembly_ablation": ablation,
             "adjoint": adj,
             "surrogate": sur,
             "kernel_sources": kernel_source_hash(),

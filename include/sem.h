@@ -94,6 +94,13 @@ int sem_patch_plan(int ngll, int nspec, int nglob, const int32_t* ibool, int32_t
  * element). Host only, no GPU needed. */
 int sem_geometry(int ngll, int nspec, const double* ctrl, double* xyz, double* dxi_dx, double* jac);
 
+/* The geometry sem_set_mesh computes from per-point positions xyz[nspec][ngll^3][3] (the
+ * isoparametric map: dx/dxi by differentiating the positions with hprime along each
+ * reference direction, its inverse by cofactors and its determinant, float64). Outputs as
+ * in sem_geometry, each caller-owned and may be NULL. SEM_EINVAL for bad sizes, non-finite
+ * positions, or (after all outputs are written) a determinant <= 0. Host only. */
+int sem_geometry_points(int ngll, int nspec, const double* xyz, double* dxi_dx, double* jac);
+
 /* Point location in trilinear hexahedra: for each of npts points xyz[npts][3], the
  * lowest-numbered element of ctrl[nspec][8][3] that holds it, elem_out[npts] (-1 for a point
  * outside every element), and its reference coordinates ref_out[npts][3] in [-1, 1] (may be
@@ -150,8 +157,12 @@ int sem_destroy(sem_ctx* ctx);
  *       and a patch writes only after every patch of the previous colour has finished (a
  *       bounded wait; if one gives up, the next sem_sync, sem_run or sem_check_finite
  *       returns SEM_ETIMEOUT).
+ *     3 = the colouring ablation (Sec. V-D-1 compares the colouring with atomics): the
+ *       element kernel of 1 over every element in one launch, each point's forces added to
+ *       its node with a float atomic add into f zeroed first. Not deterministic (the order
+ *       of the additions varies from run to run); for timing comparisons only.
  *   0 and 2 give bitwise equal results; 1 differs from them only in the order of the
- *   float32 sums at shared nodes. All are deterministic. */
+ *   float32 sums at shared nodes. 0, 1 and 2 are deterministic. */
 #define SEM_OPT_ASSEMBLY 3
 /*   SEM_OPT_SWEEP_STALL_TEST (failure-detection test, one-shot): 1 makes the next direct
  *   persistent sweep (SEM_OPT_ASSEMBLY 2, sem_apply_stiffness_strided with stride 4) wait
@@ -161,12 +172,28 @@ int sem_destroy(sem_ctx* ctx);
 #define SEM_OPT_SWEEP_STALL_TEST 4
 int sem_set_option(sem_ctx* ctx, int option, long long value);
 
-/* Set the mesh (Sec. II-B hexahedral mesh, Sec. IV-C global-to-local map).
- * Computes GLL point positions from the trilinear corners, the inverse Jacobian terms by
- * differentiating positions with hprime, the colouring, the colour-sorted element order
- * and the device copies. SEM_EINVAL if nspec < 1, an ibool entry is outside [0, nglob),
- * an element repeats a node, some node in [0, nglob) is never referenced, or J <= 0. */
-int sem_set_mesh(sem_ctx* ctx, int nspec, int nglob, const int32_t* ibool, const double* ctrl);
+/* Set the mesh (Sec. II-B: hexahedral elements mapped to the reference cube, the
+ * solution interpolated at the tensor-product GLL points; Sec. IV-C: the global-to-local
+ * map ibool). xyz[nspec][ngll^3][3] (float64, metres) is the position of every LOCAL point
+ * in local point order, so any element geometry the GLL points can describe (curved faces,
+ * topography) is allowed, and a periodic ibool stays well defined (a node may appear with
+ * different coordinates in different elements). The library computes dx/dxi at every GLL
+ * point by differentiating the positions with hprime along each reference direction (the
+ * isoparametric map), its inverse and determinant in float64, the element colouring, the
+ * force-sweep patches and the internal node order, and the device copies. Point location
+ * and sources between nodes (sem_locate_points, sem_set_shot_sources_at) use the trilinear
+ * map of each element's corner GLL points. Node coordinates (sem_node_xyz,
+ * sem_locate_nodes, sem_set_sources, sem_set_receivers) are read from the local points
+ * (the last element naming a node wins). SEM_EINVAL if nspec < 1, an ibool entry is
+ * outside [0, nglob), an element repeats a node, some node in [0, nglob) is never
+ * referenced, a coordinate is not finite, or J <= 0 somewhere (the message names the
+ * element). Replaces the previous mesh, material, dt, sources, receivers and state. */
+int sem_set_mesh(sem_ctx* ctx, int nspec, int nglob, const int32_t* ibool, const double* xyz);
+
+/* sem_set_mesh for trilinear hexahedra given by their corners ctrl[nspec][8][3] (corner
+ * c = a + 2b + 4d at reference (2a-1, 2b-1, 2d-1)): the GLL point positions come from the
+ * trilinear map (sem_geometry), then everything as sem_set_mesh. */
+int sem_set_mesh_corners(sem_ctx* ctx, int nspec, int nglob, const int32_t* ibool, const double* ctrl);
 
 /* Set the isotropic material per local point, float32 [nspec][ngll^3] each
  * (Sec. II-B: density rho and stiffness C; here C from the wave speeds with
@@ -200,10 +227,16 @@ int sem_locate_nodes(sem_ctx* ctx, int npts, const double* xyz, const double* su
  * trilinear elements, Sec. II-B), float64 host arrays. */
 int sem_node_xyz(sem_ctx* ctx, int npts, const int32_t* node, double* xyz_out);
 
+/* Point forces at positions xyz[nsrc][3] (metres), each snapped to the nearest global GLL
+ * node (ties: lowest index), with force[nsrc][3] (N) and the Ricker time function of
+ * sem_set_source_nodes. Replaces all sources; nsrc may be 0. Requires sem_set_mesh.
+ * SEM_EINVAL for non-finite positions or forces. */
+int sem_set_sources(sem_ctx* ctx, int nsrc, const double* xyz, const double* force, double f0, double t0);
+
 /* Point forces (Sec. V-C): at step n, accel_raw[node[s]] += force[s][0..2] * R(t_{n+1} - t0)
  * with the Ricker wavelet R(tau) = (1 - 2 a) exp(-a), a = (pi f0 tau)^2, evaluated in
  * float64. nsrc may be 0. */
-int sem_set_sources(sem_ctx* ctx, int nsrc, const int32_t* node, const double* force,
+int sem_set_source_nodes(sem_ctx* ctx, int nsrc, const int32_t* node, const double* force,
                     double f0, double t0);
 
 /* Several shots on one model (same mesh, material, dt and receivers; each shot its own
@@ -239,9 +272,16 @@ int sem_set_shot_moment_sources(sem_ctx* ctx, int nsrc, const int32_t* shot, con
 int sem_set_shot_sources_at(sem_ctx* ctx, int nsrc, const int32_t* shot, const double* xyz,
                             const double* force, const double* moment, double f0, double t0);
 
-/* Receivers: the displacement at node[r] is recorded after every step of sem_run /
- * sem_run_dev, for every shot. nrec may be 0. */
-int sem_set_receivers(sem_ctx* ctx, int nrec, const int32_t* node);
+/* Receivers at positions xyz[nrec][3] (metres), each snapped to the nearest global GLL node
+ * (ties: lowest index); node_out[nrec] (may be NULL) receives those nodes. The displacement
+ * there is recorded after every step of sem_run / sem_run_dev, for every shot. Replaces
+ * all receivers; nrec may be 0. Requires sem_set_mesh. SEM_EINVAL for non-finite
+ * positions. (Receivers confined to a surface: sem_locate_nodes with surface_z, then
+ * sem_set_receiver_nodes.) */
+int sem_set_receivers(sem_ctx* ctx, int nrec, const double* xyz, int32_t* node_out);
+
+/* Receivers at global nodes node[nrec]. nrec may be 0. */
+int sem_set_receiver_nodes(sem_ctx* ctx, int nrec, const int32_t* node);
 
 /* Set (u, v, a) at t = 0 from host arrays [nglob][3] (NULL = zero) and reset the step
  * counter. SEM_EINVAL if a value is not finite (checked on the device; the state is then

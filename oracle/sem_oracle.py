@@ -172,6 +172,26 @@ def element_geometry(ctrl: np.ndarray, basis: Basis):
     return xyz, dxi_dx, jac
 
 
+def isoparametric_geometry(xyz: np.ndarray, basis: Basis):
+    """Inverse Jacobian and determinant at every GLL point from the positions of the GLL
+    points themselves (Sec. II-B: every element is a map of the reference cube, here the
+    map interpolated by the same tensor-product Lagrange basis as the displacement):
+    dx_d/dxi_r at a point is the sum over l of l_l'(xi) times x_d at the l-th point of the
+    grid line through it along direction r; then numpy's 3x3 inverse and determinant.
+
+    ``xyz [nspec,3,k,j,i]``; returns ``dxi_dx [nspec,3(r),3(d),k,j,i]`` and ``jac
+    [nspec,k,j,i]`` as element_geometry does."""
+    H = basis.hprime
+    A = np.empty(xyz.shape[:2] + (3,) + xyz.shape[2:])  # [e, d, r, k, j, i] = dx_d / dxi_r
+    A[:, :, 0] = np.einsum("il,edkjl->edkji", H, xyz)
+    A[:, :, 1] = np.einsum("jl,edkli->edkji", H, xyz)
+    A[:, :, 2] = np.einsum("kl,edlji->edkji", H, xyz)
+    Am = np.moveaxis(A, (1, 2), (4, 5))  # [e, k, j, i, d, r]
+    jac = np.linalg.det(Am)
+    inv = np.linalg.inv(Am)  # [e, k, j, i, r, d] = dxi_r / dx_d
+    return np.moveaxis(inv, (4, 5), (1, 2)), jac
+
+
 def global_coordinates(xyz: np.ndarray, ibool: np.ndarray, nglob: int) -> np.ndarray:
     """Coordinates of every global node, read from any local point that maps to it."""
     nspec = xyz.shape[0]
@@ -264,17 +284,31 @@ def assemble(F_e: np.ndarray, ibool: np.ndarray, nglob: int) -> np.ndarray:
 
 
 class Model:
-    """Mesh + material + basis with every derived array the solver needs (all float64)."""
+    """Mesh + material + basis with every derived array the solver needs (all float64).
 
-    def __init__(self, ibool, ctrl, nglob, rho, vp, vs, ngll):
+    The mesh is ``ctrl`` (trilinear corners [nspec][8][3]; geometry by element_geometry) or,
+    with ``points`` [nspec][ngll^3][3] (the position of every local point in local point
+    order), any element shape (geometry by isoparametric_geometry; ``ctrl`` may then be None
+    and is taken from the corner points)."""
+
+    def __init__(self, ibool, ctrl, nglob, rho, vp, vs, ngll, points=None):
         self.basis = Basis(ngll)
         n = ngll
         self.ngll = n
         self.ibool = np.asarray(ibool)
-        self.ctrl = np.asarray(ctrl, dtype=np.float64)
         self.nspec = self.ibool.shape[0]
         self.nglob = int(nglob)
-        self.xyz, self.dxi_dx, self.jac = element_geometry(np.asarray(ctrl, dtype=np.float64), self.basis)
+        if points is None:
+            self.ctrl = np.asarray(ctrl, dtype=np.float64)
+            self.xyz, self.dxi_dx, self.jac = element_geometry(self.ctrl, self.basis)
+        else:
+            pts = np.asarray(points, dtype=np.float64).reshape(self.nspec, n, n, n, 3)
+            self.xyz = np.ascontiguousarray(np.moveaxis(pts, 4, 1))  # [e, 3, k, j, i]
+            self.dxi_dx, self.jac = isoparametric_geometry(self.xyz, self.basis)
+            N = n - 1
+            corner = [(a * N, b * N, d * N) for d in (0, 1) for b in (0, 1) for a in (0, 1)]
+            self.ctrl = np.stack([pts[:, k, j, i, :] for (i, j, k) in corner], axis=1) if ctrl is None \
+                else np.asarray(ctrl, dtype=np.float64)
         shape = (self.nspec, n, n, n)
         self.rho = np.asarray(rho, dtype=np.float64).reshape(shape)
         self.vp = np.asarray(vp, dtype=np.float64).reshape(shape)

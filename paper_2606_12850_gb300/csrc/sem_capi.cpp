@@ -45,7 +45,7 @@ struct sem_ctx {
   int npatch = 0, pmax_nodes = 0, ptables = 0;
   int stall_test = 0;               // SEM_OPT_SWEEP_STALL_TEST (one-shot)
   int assembly = 0;                 // SEM_OPT_ASSEMBLY: 0 patches, one launch per colour,
-                                    // 1 elements, 2 persistent patch sweep
+                                    // 1 elements, 2 persistent patch sweep, 3 atomic ablation
   int slabs = 1;                    // spatial slabs of the sweep order
   int slabs_opt = 0;                // requested slab count (0 = automatic)
   std::vector<float> rec;           // colour-sorted element records (host copy)
@@ -237,6 +237,19 @@ int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int
   L.rec = c->d_rec;
   L.elist = c->d_elist;
   L.perm = c->d_perm;
+  if (c->assembly == 3 && node_stride == kNodeStride && shots == 1) {  // colouring ablation
+    L.u = u;
+    L.f = f;
+    L.node_stride = node_stride;
+    L.shots = 1;
+    L.variant = c->variant;
+    L.atomic = 1;
+    L.e0 = 0;
+    L.e1 = c->nspec;
+    SEM_CUDA(c, cudaMemsetAsync(f, 0, kNodeStride * static_cast<size_t>(c->nglob) * sizeof(float), c->stream));
+    SEM_LAUNCH(c, launch_forces(c->ngll, L, c->stream));
+    return SEM_OK;
+  }
   L.u = u;
   L.f = f;
   L.node_stride = node_stride;
@@ -441,6 +454,28 @@ int sem_geometry(int ngll, int nspec, const double* ctrl, double* xyz, double* d
   return SEM_OK;
 }
 
+int sem_geometry_points(int ngll, int nspec, const double* xyz, double* dxi_dx, double* jac) {
+  if (nspec < 1 || !xyz || ngll < kMinNgll || ngll > kMaxNgll)
+    return fail(nullptr, SEM_EINVAL, "sem_geometry_points: bad arguments");
+  const size_t np = static_cast<size_t>(ngll) * ngll * ngll;
+  for (size_t q = 0; q < 3 * np * nspec; ++q)
+    if (!std::isfinite(xyz[q])) return fail(nullptr, SEM_EINVAL, "non-finite point coordinate");
+  std::vector<double> xi(ngll), w(ngll), h(static_cast<size_t>(ngll) * ngll);
+  std::string err;
+  if (gll_basis(ngll, xi.data(), w.data(), h.data(), &err)) return fail(nullptr, SEM_EINVAL, err);
+  std::vector<double> G(9 * np), J(np);
+  int bad = -1;
+  for (int e = 0; e < nspec; ++e) {
+    const size_t e0 = static_cast<size_t>(e) * np;
+    if (!geometry_from_positions(ngll, h.data(), xyz + 3 * e0, G.data(), J.data()) && bad < 0) bad = e;
+    if (dxi_dx) std::memcpy(dxi_dx + 9 * e0, G.data(), sizeof(double) * 9 * np);
+    if (jac) std::memcpy(jac + e0, J.data(), sizeof(double) * np);
+  }
+  if (bad >= 0)
+    return fail(nullptr, SEM_EINVAL, "element " + std::to_string(bad) + " has a Jacobian determinant <= 0");
+  return SEM_OK;
+}
+
 int sem_locate_points(int nspec, const double* ctrl, int npts, const double* xyz, int32_t* elem_out,
                       double* ref_out) {
   if (nspec < 1 || npts < 0 || !ctrl || (npts > 0 && (!xyz || !elem_out)))
@@ -542,8 +577,10 @@ int sem_set_option(sem_ctx* c, int option, long long value) {
       c->stall_test = static_cast<int>(value);
       return SEM_OK;
     case SEM_OPT_ASSEMBLY:
-      if (value < 0 || value > 2)
-        return fail(c, SEM_EINVAL, "assembly must be 0 (patch colours), 1 (elements) or 2 (persistent patch sweep)");
+      if (value < 0 || value > 3)
+        return fail(c, SEM_EINVAL,
+                    "assembly must be 0 (patch colours), 1 (elements), 2 (persistent patch sweep) or 3 (atomic "
+                    "ablation)");
       c->assembly = static_cast<int>(value);
       drop_graph(c);
       return SEM_OK;
@@ -552,9 +589,12 @@ int sem_set_option(sem_ctx* c, int option, long long value) {
   }
 }
 
-int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const double* ctrl) {
+// Mesh set-up shared by sem_set_mesh (per-point positions pts[nspec][np][3]) and
+// sem_set_mesh_corners (trilinear corners ctrl[nspec][8][3]); exactly one is non-null.
+static int set_mesh_impl(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const double* ctrl_in,
+                         const double* pts) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
-  if (nspec < 1 || nglob < 1 || !ibool || !ctrl) return fail(c, SEM_EINVAL, "sem_set_mesh: bad arguments");
+  if (nspec < 1 || nglob < 1 || !ibool || (!ctrl_in) == (!pts)) return fail(c, SEM_EINVAL, "sem_set_mesh: bad arguments");
   const int n = c->ngll, np = n * n * n;
   const size_t nloc = static_cast<size_t>(nspec) * np;
   if (nloc > (1ull << 31) - 1 || nglob > (1 << 30)) return fail(c, SEM_EINVAL, "mesh too large for int32 indexing");
@@ -566,6 +606,24 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   }
   for (int g = 0; g < nglob; ++g)
     if (!seen[g]) return fail(c, SEM_EINVAL, "global node " + std::to_string(g) + " is not referenced by ibool");
+  // corner vertices: given, or the corner GLL points of the per-point positions (used by
+  // point location and by sources between nodes, which take the trilinear map of the
+  // corners)
+  std::vector<double> corners;
+  const double* ctrl = ctrl_in;
+  if (pts) {
+    for (size_t q = 0; q < 3 * nloc; ++q)
+      if (!std::isfinite(pts[q])) return fail(c, SEM_EINVAL, "non-finite point coordinate");
+    corners.resize(static_cast<size_t>(nspec) * 24);
+    const int N = n - 1;
+    for (int e = 0; e < nspec; ++e)
+      for (int v = 0; v < 8; ++v) {
+        const int p = ((v & 1) ? N : 0) + n * (((v >> 1) & 1) ? N : 0) + n * n * (((v >> 2) & 1) ? N : 0);
+        for (int d = 0; d < 3; ++d)
+          corners[24 * static_cast<size_t>(e) + 3 * v + d] = pts[3 * (static_cast<size_t>(e) * np + p) + d];
+      }
+    ctrl = corners.data();
+  }
   for (size_t q = 0; q < static_cast<size_t>(nspec) * 24; ++q)
     if (!std::isfinite(ctrl[q])) return fail(c, SEM_EINVAL, "non-finite corner coordinate");
 
@@ -580,9 +638,15 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   c->node_xyz.assign(3 * static_cast<size_t>(nglob), 0.0);
   std::vector<float> geom(static_cast<size_t>(nspec) * 10 * np);  // [e][10][p] in caller p order
   for (int e = 0; e < nspec; ++e) {
-    if (!element_geometry(n, c->xi.data(), c->hprime.data(), ctrl + 24 * static_cast<size_t>(e), xyz.data(),
-                          G.data(), J.data()))
-      return fail(c, SEM_EINVAL, "element " + std::to_string(e) + " has a Jacobian determinant <= 0");
+    bool ok;
+    if (pts) {
+      std::memcpy(xyz.data(), pts + 3 * static_cast<size_t>(e) * np, sizeof(double) * 3 * np);
+      ok = geometry_from_positions(n, c->hprime.data(), xyz.data(), G.data(), J.data());
+    } else {
+      ok = element_geometry(n, c->xi.data(), c->hprime.data(), ctrl + 24 * static_cast<size_t>(e), xyz.data(),
+                            G.data(), J.data());
+    }
+    if (!ok) return fail(c, SEM_EINVAL, "element " + std::to_string(e) + " has a Jacobian determinant <= 0");
     double dmin = 1e300;
     for (int k = 0; k < n; ++k)
       for (int j = 0; j < n; ++j)
@@ -770,6 +834,16 @@ int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const d
   c->nsrc = 0;
   c->nrec = 0;
   return SEM_OK;
+}
+
+int sem_set_mesh(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const double* xyz) {
+  if (!xyz) return fail(c, SEM_EINVAL, "sem_set_mesh: NULL coordinates");
+  return set_mesh_impl(c, nspec, nglob, ibool, nullptr, xyz);
+}
+
+int sem_set_mesh_corners(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const double* ctrl) {
+  if (!ctrl) return fail(c, SEM_EINVAL, "sem_set_mesh_corners: NULL corners");
+  return set_mesh_impl(c, nspec, nglob, ibool, ctrl, nullptr);
 }
 
 // Writes kappa and mu into the element records, assembles the mass and its inverse and the
@@ -970,8 +1044,19 @@ static int set_sources_impl(sem_ctx* c, int nsrc, const int32_t* shot, const int
   return SEM_OK;
 }
 
-int sem_set_sources(sem_ctx* c, int nsrc, const int32_t* node, const double* force, double f0, double t0) {
+int sem_set_source_nodes(sem_ctx* c, int nsrc, const int32_t* node, const double* force, double f0, double t0) {
   return set_sources_impl(c, nsrc, nullptr, node, force, f0, t0);
+}
+
+int sem_set_sources(sem_ctx* c, int nsrc, const double* xyz, const double* force, double f0, double t0) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (nsrc < 0 || (nsrc > 0 && (!xyz || !force))) return fail(c, SEM_EINVAL, "sem_set_sources: bad arguments");
+  for (size_t q = 0; q < 3 * static_cast<size_t>(nsrc); ++q)
+    if (!std::isfinite(xyz[q])) return fail(c, SEM_EINVAL, "non-finite source position");
+  std::vector<int32_t> node(nsrc > 0 ? nsrc : 1);
+  if (nsrc > 0) locate_nodes(c->nglob, c->node_xyz.data(), nsrc, xyz, nullptr, node.data());
+  return set_sources_impl(c, nsrc, nullptr, node.data(), force, f0, t0);
 }
 
 int sem_set_shot_sources(sem_ctx* c, int nsrc, const int32_t* shot, const int32_t* node, const double* force,
@@ -1094,10 +1179,23 @@ int sem_set_shots(sem_ctx* c, int nshots) {
   return SEM_OK;
 }
 
-int sem_set_receivers(sem_ctx* c, int nrec, const int32_t* node) {
+int sem_set_receivers(sem_ctx* c, int nrec, const double* xyz, int32_t* node_out) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
-  if (nrec < 0 || (nrec > 0 && !node)) return fail(c, SEM_EINVAL, "sem_set_receivers: bad arguments");
+  if (nrec < 0 || (nrec > 0 && !xyz)) return fail(c, SEM_EINVAL, "sem_set_receivers: bad arguments");
+  for (size_t q = 0; q < 3 * static_cast<size_t>(nrec); ++q)
+    if (!std::isfinite(xyz[q])) return fail(c, SEM_EINVAL, "non-finite receiver position");
+  std::vector<int32_t> node(nrec > 0 ? nrec : 1);
+  if (nrec > 0) locate_nodes(c->nglob, c->node_xyz.data(), nrec, xyz, nullptr, node.data());
+  const int r = sem_set_receiver_nodes(c, nrec, node.data());
+  if (r == SEM_OK && node_out && nrec > 0) std::memcpy(node_out, node.data(), sizeof(int32_t) * nrec);
+  return r;
+}
+
+int sem_set_receiver_nodes(sem_ctx* c, int nrec, const int32_t* node) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
+  if (nrec < 0 || (nrec > 0 && !node)) return fail(c, SEM_EINVAL, "sem_set_receiver_nodes: bad arguments");
   for (int r = 0; r < nrec; ++r)
     if (node[r] < 0 || node[r] >= c->nglob) return fail(c, SEM_EINVAL, "receiver node out of range");
   int r = set_device(c);

@@ -437,7 +437,7 @@ __device__ __forceinline__ void team_element_forces(float* ts, int tl, int ne, i
 // through perm (internal -> caller node). With S shots the launch works on the items
 // (element, shot) of elements e0 .. e1-1 of elist, element-major: the teams of a CTA take the
 // shots of one element, so its record is read from DRAM once for all of them.
-template <int N, bool MS, bool LO, bool CALLER>
+template <int N, bool MS, bool LO, bool CALLER, bool ATOMIC = false>
 __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
     forces_kernel(const float* __restrict__ rec, const int* __restrict__ elist, const int* __restrict__ perm,
                   const float* __restrict__ u, float* __restrict__ f, int e0, int e1, int S_arg) {
@@ -514,6 +514,17 @@ __global__ void __launch_bounds__(ForceCfg<N>::T, ForceCfg<N>::MIN_BLOCKS)
 
   // 4. scatter in the gather's coalesced order; the previous values of a group of GB nodes
   //    are loaded before any of them is written back
+  if constexpr (ATOMIC) {  // the colouring ablation: every element in one launch, f zeroed first
+    for (int idx = tl; idx < ne * NP; idx += TEAM) {
+      const int e = idx / NP;
+      const float* sb = ts + e * ES;
+      const uint32_t w = reinterpret_cast<const uint32_t*>(sb + 9 * NP)[idx - e * NP];
+      const float* src = sb + 3 * (idx - e * NP);
+      atomicAdd(reinterpret_cast<float4*>(f) + static_cast<size_t>(w & kNodeMask),
+                make_float4(src[0], src[1], src[2], 0.f));
+    }
+    return;
+  }
   if constexpr (CALLER) {
     for (int idx = tl; idx < ne * NP; idx += TEAM) {
       const int e = idx / NP;
@@ -1062,12 +1073,12 @@ int raise_smem_limit(std::atomic<unsigned long long>& done, K kernel, int bytes)
   return 0;
 }
 
-template <bool MS, bool LO, bool CALLER>
+template <bool MS, bool LO, bool CALLER, bool ATOMIC = false>
 int launch_forces_ms(const ForceLaunch& L, cudaStream_t s) {
   using C = ForceCfg<SEM_NGLL>;
   static std::atomic<unsigned long long> attr_done{0};
   const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
-  if (int r = raise_smem_limit(attr_done, forces_kernel<SEM_NGLL, MS, LO, CALLER>, smem)) return r;
+  if (int r = raise_smem_limit(attr_done, forces_kernel<SEM_NGLL, MS, LO, CALLER, ATOMIC>, smem)) return r;
   const int S = MS ? L.shots : 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(((L.e1 - L.e0) * S + C::EPC - 1) / C::EPC);
@@ -1079,7 +1090,7 @@ int launch_forces_ms(const ForceLaunch& L, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_kernel<SEM_NGLL, MS, LO, CALLER>, L.rec, L.elist, L.perm, L.u, L.f, L.e0, L.e1, S));
+  return static_cast<int>(cudaLaunchKernelEx(&cfg, forces_kernel<SEM_NGLL, MS, LO, CALLER, ATOMIC>, L.rec, L.elist, L.perm, L.u, L.f, L.e0, L.e1, S));
 }
 
 int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
@@ -1091,6 +1102,10 @@ int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
     return launch_forces_ms<false, C::LINE_OWNERS, true>(L, s);
   }
   if (L.node_stride != kNodeStride) return static_cast<int>(cudaErrorInvalidValue);
+  if (L.atomic) {
+    if (L.shots != 1) return static_cast<int>(cudaErrorInvalidValue);
+    return launch_forces_ms<false, C::LINE_OWNERS, false, true>(L, s);
+  }
   if (L.shots > 1) return lo ? launch_forces_ms<true, true, false>(L, s) : launch_forces_ms<true, false, false>(L, s);
   return lo ? launch_forces_ms<false, true, false>(L, s) : launch_forces_ms<false, false, false>(L, s);
 }

@@ -57,6 +57,8 @@ int gll_basis(int ngll, double* xi, double* w, double* hprime, std::string* err)
 // xyz[np][3], G[np][9] (dxi_r/dx_d at 3r+d), J[np]; returns false if some J <= 0.
 bool element_geometry(int ngll, const double* xi, const double* hprime, const double* ctrl,
                       double* xyz, double* G, double* J);
+// The same from the positions xyz[np][3] of the element's GLL points (any geometry).
+bool geometry_from_positions(int ngll, const double* hprime, const double* xyz, double* G, double* J);
 
 int color_elements(int nspec, int ngll, int nglob, const int32_t* ibool,
                    std::vector<int32_t>* color, int* ncolors, std::string* err);
@@ -148,6 +150,7 @@ struct ForceLaunch {
                     // arrays in caller order
   int shots;        // > 1: u and f are [nglob][shots][kNodeStride], items (element, shot)
   int variant;      // contraction form: 0 the order's default, 1 line owners, 2 per point
+  int atomic;       // colouring ablation: float atomic adds into a zeroed f, any element order
 };
 int launch_forces(int ngll, const ForceLaunch& launch, void* stream);
 

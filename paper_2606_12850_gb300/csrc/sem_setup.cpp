@@ -83,12 +83,11 @@ int gll_basis(int ngll, double* xi_out, double* w_out, double* h_out, std::strin
   return 0;
 }
 
-// GLL positions from the trilinear map of the 8 corners, then dx/dxi by differentiating
-// those positions with the 1D derivative matrix along each reference direction (exact for
-// the trilinear map, which has degree 1 <= N per direction), then the inverse by cofactors.
+// GLL positions from the trilinear map of the 8 corners, then the geometry from those
+// positions (geometry_from_positions; exact for the trilinear map, of degree 1 <= N per
+// direction).
 bool element_geometry(int n, const double* xi, const double* h, const double* ctrl,
                       double* xyz, double* G, double* J) {
-  const int np = n * n * n;
   for (int k = 0; k < n; ++k)
     for (int j = 0; j < n; ++j)
       for (int i = 0; i < n; ++i) {
@@ -101,6 +100,14 @@ bool element_geometry(int n, const double* xi, const double* h, const double* ct
         }
         for (int d = 0; d < 3; ++d) xyz[3 * p + d] = pos[d];
       }
+  return geometry_from_positions(n, h, xyz, G, J);
+}
+
+// dx/dxi at every GLL point by differentiating the positions with the 1D derivative matrix
+// along each reference direction (exact for any map of degree <= N per direction, such as
+// the trilinear one, and the isoparametric geometry otherwise), then the inverse by
+// cofactors and the determinant.
+bool geometry_from_positions(int n, const double* h, const double* xyz, double* G, double* J) {
   bool ok = true;
   for (int k = 0; k < n; ++k)
     for (int j = 0; j < n; ++j)
@@ -135,7 +142,6 @@ bool element_geometry(int n, const double* xi, const double* h, const double* ct
         g[7] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * inv;
         g[8] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * inv;
       }
-  (void)np;
   return ok;
 }
 

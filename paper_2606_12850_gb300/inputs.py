@@ -149,6 +149,20 @@ def structured_hex_mesh(n, ngll: int, length, jitter: float = 0.0, seed: int = 2
     return HexMesh(nx, ny, nz, ngll, (Lx, Ly, Lz), periodic, ibool, ctrl, Gx * Gy * Gz, elem_ijk)
 
 
+def bent_map(x: np.ndarray, lengths, amplitude=(0.15, 0.10, 0.12)) -> np.ndarray:
+    """A smooth polynomial bending of the box [0,Lx]x[0,Ly]x[0,Lz] onto a curved solid, for
+    meshes whose elements are not trilinear: in units of the box, (x, y, z) ->
+    (x + a y^2, y + b z^2, z + c x^2) (quadratic in each coordinate, so a GLL interpolant of
+    degree >= 2 reproduces it exactly; the Jacobian determinant is 1 + 8 a b c x y z > 0 and
+    the image has volume (1 + a b c) Lx Ly Lz). ``x`` is [..., 3] physical coordinates."""
+    L = np.asarray(lengths, dtype=np.float64)
+    a, b, c = amplitude
+    s = np.asarray(x, dtype=np.float64) / L
+    out = np.stack([s[..., 0] + a * s[..., 1] ** 2, s[..., 1] + b * s[..., 2] ** 2, s[..., 2] + c * s[..., 0] ** 2],
+                   axis=-1)
+    return out * L
+
+
 def per_point(mesh: HexMesh, per_element: np.ndarray) -> np.ndarray:
     """Broadcast a per-element value to every local GLL point, float32 [nspec][ngll^3]."""
     return np.repeat(np.asarray(per_element, dtype=np.float32)[:, None], mesh.ibool.shape[1], axis=1)

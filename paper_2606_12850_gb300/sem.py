@@ -30,12 +30,14 @@ SIGNATURES = {
     "sem_color_elements": (_I, [_I, _I, _I, _P, _P, _P]),
     "sem_patch_plan": (_I, [_I, _I, _I, _P, _P, _P, _P]),
     "sem_geometry": (_I, [_I, _I, _P, _P, _P, _P]),
+    "sem_geometry_points": (_I, [_I, _I, _P, _P, _P]),
     "sem_locate_points": (_I, [_I, _P, _I, _P, _P, _P]),
     "sem_point_source_forces": (_I, [_I, _P, _P, _P, _P, _P]),
     "sem_create": (_I, [_P, _I, _I, _P]),
     "sem_destroy": (_I, [_P]),
     "sem_set_option": (_I, [_P, _I, ctypes.c_longlong]),
     "sem_set_mesh": (_I, [_P, _I, _I, _P, _P]),
+    "sem_set_mesh_corners": (_I, [_P, _I, _I, _P, _P]),
     "sem_set_material": (_I, [_P, _P, _P, _P]),
     "sem_set_moduli": (_I, [_P, _P, _P, _P]),
     "sem_set_moduli_dev": (_I, [_P, _P, _P, _P]),
@@ -44,7 +46,9 @@ SIGNATURES = {
     "sem_locate_nodes": (_I, [_P, _I, _P, _P, _P]),
     "sem_node_xyz": (_I, [_P, _I, _P, _P]),
     "sem_set_sources": (_I, [_P, _I, _P, _P, _D, _D]),
-    "sem_set_receivers": (_I, [_P, _I, _P]),
+    "sem_set_source_nodes": (_I, [_P, _I, _P, _P, _D, _D]),
+    "sem_set_receivers": (_I, [_P, _I, _P, _P]),
+    "sem_set_receiver_nodes": (_I, [_P, _I, _P]),
     "sem_set_shots": (_I, [_P, _I]),
     "sem_set_shot_sources": (_I, [_P, _I, _P, _P, _P, _D, _D]),
     "sem_set_shot_moment_sources": (_I, [_P, _I, _P, _P, _P, _D, _D]),
@@ -203,6 +207,19 @@ def sem_geometry(ctrl, ngll: int):
     return xyz, g, jac
 
 
+def sem_geometry_points(ngll: int, xyz):
+    """Host-only geometry from per-point positions xyz [nspec][ngll^3][3]: (dxi_dx
+    [nspec][ngll^3][3][3], jac [nspec][ngll^3])."""
+    pts, pp = _host(xyz, np.float64)
+    n3 = ngll ** 3
+    nspec = pts.size // (3 * n3)
+    G = np.empty((nspec, n3, 3, 3))
+    J = np.empty((nspec, n3))
+    _check(lib().sem_geometry_points(int(ngll), nspec, pp, G.ctypes.data_as(_P), J.ctypes.data_as(_P)),
+           "sem_geometry_points")
+    return G, J
+
+
 def sem_locate_points(ctrl, xyz):
     """Element (lowest index; -1 outside) and reference coordinates of each point among the
     trilinear elements ``ctrl`` [nspec][8][3]."""
@@ -260,14 +277,27 @@ def sem_set_option(ctx: Ctx, option: int, value: int):
     _check(lib().sem_set_option(ctx.handle, int(option), int(value)), "sem_set_option", ctx)
 
 
-def sem_set_mesh(ctx: Ctx, ibool, ctrl, nglob: int):
+def sem_set_mesh(ctx: Ctx, ibool, xyz, nglob: int):
+    """Mesh from the positions of every local point, xyz [nspec][ngll^3][3]."""
+    n3 = ctx.ngll ** 3
+    ib, pi = _host(ibool, np.int32)
+    if ib.size == 0 or ib.size % n3:
+        raise ValueError(f"ibool must hold [nspec][{ctx.ngll}^3] entries")
+    nspec = ib.size // n3
+    pts, pp = _host(xyz, np.float64, (nspec, n3, 3))
+    _check(lib().sem_set_mesh(ctx.handle, nspec, int(nglob), pi, pp), "sem_set_mesh", ctx)
+    ctx.nspec, ctx.nglob = nspec, int(nglob)
+
+
+def sem_set_mesh_corners(ctx: Ctx, ibool, ctrl, nglob: int):
+    """Mesh of trilinear hexahedra from their corners, ctrl [nspec][8][3]."""
     n3 = ctx.ngll ** 3
     ib, pi = _host(ibool, np.int32)
     if ib.size == 0 or ib.size % n3:
         raise ValueError(f"ibool must hold [nspec][{ctx.ngll}^3] entries")
     nspec = ib.size // n3
     ct, pc = _host(ctrl, np.float64, (nspec, 8, 3))
-    _check(lib().sem_set_mesh(ctx.handle, nspec, int(nglob), pi, pc), "sem_set_mesh", ctx)
+    _check(lib().sem_set_mesh_corners(ctx.handle, nspec, int(nglob), pi, pc), "sem_set_mesh_corners", ctx)
     ctx.nspec, ctx.nglob = nspec, int(nglob)
 
 
@@ -319,10 +349,19 @@ def sem_node_xyz(ctx: Ctx, node) -> np.ndarray:
     return out
 
 
-def sem_set_sources(ctx: Ctx, node, force, f0: float, t0: float):
+def sem_set_sources(ctx: Ctx, xyz, force, f0: float, t0: float):
+    """Point forces at positions xyz [nsrc][3], snapped to the nearest nodes."""
+    pts, pp = _host(np.atleast_2d(xyz), np.float64)
+    n = pts.size // 3
+    fo, pf = _host(np.atleast_2d(force), np.float64, (n, 3))
+    _check(lib().sem_set_sources(ctx.handle, n, pp, pf, float(f0), float(t0)), "sem_set_sources", ctx)
+
+
+def sem_set_source_nodes(ctx: Ctx, node, force, f0: float, t0: float):
     nd, pn = _host(np.atleast_1d(node), np.int32)
     fo, pf = _host(np.atleast_2d(force), np.float64, (nd.size, 3))
-    _check(lib().sem_set_sources(ctx.handle, nd.size, pn, pf, float(f0), float(t0)), "sem_set_sources", ctx)
+    _check(lib().sem_set_source_nodes(ctx.handle, nd.size, pn, pf, float(f0), float(t0)), "sem_set_source_nodes",
+           ctx)
 
 
 def sem_set_shots(ctx: Ctx, nshots: int):
@@ -359,9 +398,19 @@ def sem_set_shot_sources_at(ctx: Ctx, shot, xyz, force=None, moment=None, f0: fl
                                          mo[1] if mo else None, float(f0), float(t0)), "sem_set_shot_sources_at", ctx)
 
 
-def sem_set_receivers(ctx: Ctx, node):
+def sem_set_receivers(ctx: Ctx, xyz) -> np.ndarray:
+    """Receivers at positions xyz [nrec][3], snapped to the nearest nodes; returns the nodes."""
+    pts, pp = _host(np.atleast_2d(xyz), np.float64)
+    n = pts.size // 3
+    out = np.empty(n, dtype=np.int32)
+    _check(lib().sem_set_receivers(ctx.handle, n, pp, out.ctypes.data_as(_P)), "sem_set_receivers", ctx)
+    ctx.nrec = n
+    return out
+
+
+def sem_set_receiver_nodes(ctx: Ctx, node):
     nd, pn = _host(np.atleast_1d(node), np.int32)
-    _check(lib().sem_set_receivers(ctx.handle, nd.size, pn), "sem_set_receivers", ctx)
+    _check(lib().sem_set_receiver_nodes(ctx.handle, nd.size, pn), "sem_set_receiver_nodes", ctx)
     ctx.nrec = nd.size
 
 
@@ -603,7 +652,7 @@ def setup_workload(workload, device: int = 0, stream=None, dt: float | None = No
     (unless given), sources, receivers, zero state."""
     m = workload.mesh
     ctx = sem_create(m.ngll, device, stream)
-    sem_set_mesh(ctx, m.ibool, m.ctrl, m.nglob)
+    sem_set_mesh_corners(ctx, m.ibool, m.ctrl, m.nglob)
     sem_set_material(ctx, workload.rho, workload.vp, workload.vs)
     if dt is None:
         dt = sem_suggest_dt(ctx, workload.courant)
@@ -613,8 +662,8 @@ def setup_workload(workload, device: int = 0, stream=None, dt: float | None = No
     if rec_nodes is None:
         surf = m.lengths[2] if workload.receiver_surface_only else None
         rec_nodes = sem_locate_nodes(ctx, workload.receiver_xyz, surf)
-    sem_set_sources(ctx, src_nodes, workload.source_force, workload.f0, workload.t0)
-    sem_set_receivers(ctx, rec_nodes)
+    sem_set_source_nodes(ctx, src_nodes, workload.source_force, workload.f0, workload.t0)
+    sem_set_receiver_nodes(ctx, rec_nodes)
     sem_set_state(ctx)
     return Setup(ctx, dt, np.asarray(src_nodes), np.asarray(rec_nodes))
 
@@ -631,7 +680,7 @@ class Solver:
     def __init__(self, ngll: int, ibool, ctrl, nglob: int, rho, vp, vs, device: int = 0, stream=None,
                  courant: float = 0.4, dt: float | None = None):
         self.ctx = sem_create(ngll, device, stream)
-        sem_set_mesh(self.ctx, ibool, ctrl, nglob)
+        sem_set_mesh_corners(self.ctx, ibool, ctrl, nglob)
         sem_set_material(self.ctx, rho, vp, vs)
         self.dt = sem_suggest_dt(self.ctx, courant) if dt is None else float(dt)
         sem_set_dt(self.ctx, self.dt)
@@ -660,7 +709,7 @@ class Solver:
         if snap and moment is None:
             nodes = self.locate(xyz)
             if shot is None:
-                sem_set_sources(self.ctx, nodes, force, f0, t0)
+                sem_set_source_nodes(self.ctx, nodes, force, f0, t0)
             else:
                 sem_set_shot_sources(self.ctx, shot, nodes, force, f0, t0)
         else:
@@ -668,7 +717,7 @@ class Solver:
 
     def set_receivers(self, xyz, surface: bool = False) -> np.ndarray:
         nodes = self.locate(xyz, surface)
-        sem_set_receivers(self.ctx, nodes)
+        sem_set_receiver_nodes(self.ctx, nodes)
         return nodes
 
     def set_shots(self, nshots: int):

@@ -242,7 +242,7 @@ class Solver:
         self.setup = sem.setup_workload(workload, device=device, stream=self.stream)
         self.ctx = self.setup.ctx
         sem.sem_set_shots(self.ctx, self.shots)
-        sem.sem_set_receivers(self.ctx, self.setup.rec_nodes)
+        sem.sem_set_receiver_nodes(self.ctx, self.setup.rec_nodes)
         self.nrec = len(self.setup.rec_nodes)
         self.rec_xyz = sem.sem_node_xyz(self.ctx, self.setup.rec_nodes)
 

@@ -285,9 +285,9 @@ def test_binding_checks_array_sizes():
         sem.sem_geometry(mesh.ctrl.reshape(-1)[:-2], 3)
     ctx = sem.Ctx(0, 3)  # a null handle: nothing reaches the library
     with pytest.raises(ValueError):
-        sem.sem_set_mesh(ctx, mesh.ibool.reshape(-1)[:-1], mesh.ctrl, mesh.nglob)
+        sem.sem_set_mesh_corners(ctx, mesh.ibool.reshape(-1)[:-1], mesh.ctrl, mesh.nglob)
     with pytest.raises(ValueError):
-        sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl[:-1], mesh.nglob)
+        sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl[:-1], mesh.nglob)
 
 
 def test_missing_library_fails_loudly(monkeypatch):
@@ -311,3 +311,29 @@ def test_create_without_gpu_reports_cuda_error():
     with pytest.raises(sem.SemError) as ei:
         sem.sem_create(5)
     assert ei.value.code == -3
+
+
+@pytest.mark.parametrize("ngll", [3, 5, 7])
+def test_library_geometry_from_points_matches_oracle(ngll):
+    """sem_geometry_points (the isoparametric route of sem_set_mesh) on a bent mesh against the
+    oracle's isoparametric_geometry; each side builds its own GLL point positions (library:
+    sem_geometry's trilinear points; oracle: its element_geometry) and bends them with the
+    same map from the input module."""
+    from oracle import sem_oracle as so
+    mesh = inputs.structured_hex_mesh((2, 3, 2), ngll, (1.0, 1.5, 0.8), jitter=0.1, seed=3)
+    amp = (0.2, 0.1, 0.15)
+    lib_xyz, _, _ = sem.sem_geometry(mesh.ctrl, ngll)
+    lib_pts = inputs.bent_map(lib_xyz, mesh.lengths, amp)
+    G, J = sem.sem_geometry_points(ngll, lib_pts)
+    xyz_o, _, _ = so.element_geometry(mesh.ctrl, so.Basis(ngll))
+    pts_o = inputs.bent_map(np.moveaxis(xyz_o, 1, 4).reshape(mesh.nspec, -1, 3), mesh.lengths, amp)
+    dxi_o, jac_o = so.isoparametric_geometry(np.moveaxis(pts_o.reshape(mesh.nspec, ngll, ngll, ngll, 3), 4, 1),
+                                             so.Basis(ngll))
+    J_o = jac_o.reshape(mesh.nspec, -1)
+    G_o = np.moveaxis(dxi_o.reshape(mesh.nspec, 3, 3, -1), 3, 1)  # [e, p, r, d]
+    assert np.max(np.abs(J - J_o)) <= 1e-12 * np.max(np.abs(J_o))
+    assert np.max(np.abs(G - G_o)) <= 1e-12 * np.max(np.abs(G_o))
+    bad = lib_pts.copy()
+    bad[0, 0] = bad[0, -1]  # folds the first element
+    with pytest.raises(sem.SemError):
+        sem.sem_geometry_points(ngll, bad)

@@ -67,10 +67,10 @@ def make_sim(p, every):
     from paper_2606_12850_gb300 import adjoint
     mesh = p["mesh"]
     ctx = sem.sem_create(mesh.ngll, 0)
-    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
     kw = p["kw"]
-    sem.sem_set_sources(ctx, kw["src_nodes"], kw["src_force"], kw["f0"], kw["t0"])
-    sem.sem_set_receivers(ctx, kw["rec_nodes"])
+    sem.sem_set_source_nodes(ctx, kw["src_nodes"], kw["src_force"], kw["f0"], kw["t0"])
+    sem.sem_set_receiver_nodes(ctx, kw["rec_nodes"])
     return ctx, adjoint.Simulation(ctx, p["dt"], p["nsteps"], checkpoint_every=every)
 
 

@@ -42,10 +42,10 @@ def _plane_wave_errors(oracle, ngll, nz, courant=0.1, periods=2.0):
     rec = np.nonzero(line)[0]
     seis_ref, *_ = oracle.newmark_run(m, dt, n, u0=u0, v0=v0, a0=a0, rec_nodes=rec)
     ctx = sem.sem_create(ngll, 0)
-    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
     sem.sem_set_material(ctx, *mat)
     sem.sem_set_dt(ctx, dt)
-    sem.sem_set_receivers(ctx, rec)
+    sem.sem_set_receiver_nodes(ctx, rec)
     sem.sem_set_state(ctx, u0.astype(np.float32), v0.astype(np.float32), a0.astype(np.float32))
     seis = sem.sem_run(ctx, n)
     t = dt * np.arange(1, n + 1)
@@ -74,7 +74,7 @@ def test_init_acceleration_matches_oracle(oracle):
     vs = (vp / 1.8).astype(np.float32)
     m = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, rho, vp, vs, 5)
     ctx = sem.sem_create(5, 0)
-    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
     sem.sem_set_material(ctx, rho, vp, vs)
     sem.sem_set_dt(ctx, 1e-4)
     u0 = inputs.random_field(mesh.nglob, 3)

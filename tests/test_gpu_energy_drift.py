@@ -30,7 +30,7 @@ def test_discrete_energy_drift_fp32(oracle):
     vs = (vp / 1.8).astype(np.float32)
     m = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, rho, vp, vs, 5)  # FP64 mass for the a^T M a term
     ctx = sem.sem_create(5, 0)
-    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
     sem.sem_set_material(ctx, rho, vp, vs)
     dt = sem.sem_suggest_dt(ctx, 0.4)
     sem.sem_set_dt(ctx, dt)

@@ -39,6 +39,7 @@ def test_layered_cube_full_size(oracle, ngll):
     assert info["nspec"] == mesh.nspec and info["nglob"] == mesh.nglob
     counts = sem.sem_color_counts(s.ctx)
     assert counts.sum() == mesh.nspec and len(counts) == 8
+    assert sem.sem_patch_info(s.ctx)["colors"] == 8
 
     nodes = sample_nodes(mesh, 48, ngll, extra=s.src_nodes)
     elems = oracle.elements_touching(mesh.ibool, nodes)
@@ -57,6 +58,23 @@ def test_layered_cube_full_size(oracle, ngll):
     err = np.linalg.norm(f[nodes] - f_ref) / np.linalg.norm(f_ref)
     assert err <= TOL_L2, err
     assert np.abs(f[nodes] - f_ref).max() <= TOL_MAX * np.abs(f_ref).max()
+    # the same through the patch kernel (the force sweep a time step runs: stride 4, the
+    # solver's internal node order)
+    perm = sem.sem_node_order(s.ctx)
+    u4 = np.zeros((mesh.nglob, 4), dtype=np.float32)
+    u4[:, :3] = u[perm]
+    torch.cuda.synchronize()
+    u4d = torch.from_numpy(u4).cuda()
+    f4d = torch.empty_like(u4d)
+    torch.cuda.synchronize()
+    sem.sem_apply_stiffness_strided(s.ctx, u4d, f4d, 4)
+    sem.sem_sync(s.ctx)
+    f4 = np.empty((mesh.nglob, 4), dtype=np.float32)
+    f4[perm] = f4d.cpu().numpy()
+    del u4d, f4d
+    e4 = np.linalg.norm(f4[nodes, :3] - f_ref) / np.linalg.norm(f_ref)
+    assert e4 <= TOL_L2, e4
+    assert np.abs(f4[nodes, :3] - f_ref).max() <= TOL_MAX * np.abs(f_ref).max()
     # any size: K annihilates a rigid translation (exactly up to FP32 rounding of -K 1)
     ud.fill_(1.0)
     torch.cuda.synchronize()
@@ -96,3 +114,41 @@ def test_layered_cube_locate_and_dt(oracle):
     assert list(s.src_nodes) == list(src)
     assert list(s.rec_nodes) == list(rec)
     assert abs(s.dt / m.cfl_dt(w.courant) - 1.0) < 1e-12
+
+
+def test_layered_cube_steady_state_steps(oracle):
+    """Eleven steps of the full NGLL=5 benchmark mesh from a random state with the source
+    active: one step from the complete state, then one replay of the captured ten-step graph
+    (fused corrector/predictor pass, patch force sweep, source, in the benchmark's launch
+    configuration). The oracle runs the same steps on the elements within K + 1 = 12
+    element layers of two sampled nodes (the source node and a random interior node): an
+    explicit step moves information by one element, so the oracle's values there are exact
+    for the whole mesh. Displacement, velocity and acceleration at the nodes of the sampled
+    nodes' elements: relative L2 within 2e-5."""
+    K = 11
+    w = inputs.layered_cube(5)
+    mesh = w.mesh
+    s = sem.setup_workload(w)
+    u0 = inputs.random_field(mesh.nglob, 11, scale=1e-4)
+    v0 = inputs.random_field(mesh.nglob, 12, scale=1e-3)
+    a0 = inputs.random_field(mesh.nglob, 13, scale=1e-1)
+    sem.sem_set_state(s.ctx, u0, v0, a0)
+    sem.sem_step(s.ctx, K)
+    u, v, a = (x.reshape(-1, 3) for x in sem.sem_get_state(s.ctx))
+    ijk = mesh.elem_ijk
+    centre_nodes = [int(s.src_nodes[0]), int(inputs.uniform(31, 1, 0.3 * mesh.nglob, 0.7 * mesh.nglob)[0])]
+    keep = np.zeros(mesh.nspec, dtype=bool)
+    check = []
+    for node in centre_nodes:
+        e0 = oracle.elements_touching(mesh.ibool, [node])
+        c = ijk[e0[0]]
+        keep |= np.max(np.abs(ijk - c[None, :]), axis=1) <= K + 1
+        check.append(np.unique(mesh.ibool[e0]))
+    check = np.unique(np.concatenate(check))
+    sub = oracle.build_model(w, np.nonzero(keep)[0])
+    with np.errstate(divide="ignore", invalid="ignore"):  # nodes outside the kept elements
+        _, u_ref, v_ref, a_ref = oracle.newmark_run(sub, s.dt, K, u0=u0, v0=v0, a0=a0, src_nodes=s.src_nodes,
+                                                   src_force=w.source_force, f0=w.f0, t0=w.t0)
+    for got, ref in ((u, u_ref), (v, v_ref), (a, a_ref)):
+        e = np.linalg.norm(got[check] - ref[check]) / np.linalg.norm(ref[check])
+        assert e <= TOL_L2, e

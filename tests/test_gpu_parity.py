@@ -47,7 +47,7 @@ def random_material(mesh, seed):
 
 def make_ctx(mesh, rho, vp, vs):
     ctx = sem.sem_create(mesh.ngll, 0)
-    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
     sem.sem_set_material(ctx, rho, vp, vs)
     return ctx
 
@@ -224,8 +224,8 @@ def test_energy_matches_oracle(oracle):
 def test_zero_steps_and_empty_sources(cube_reference):
     w, _ = cube_reference
     s = sem.setup_workload(w)
-    sem.sem_set_sources(s.ctx, [], np.zeros((0, 3)), w.f0, w.t0)
-    sem.sem_set_receivers(s.ctx, [])
+    sem.sem_set_source_nodes(s.ctx, [], np.zeros((0, 3)), w.f0, w.t0)
+    sem.sem_set_receiver_nodes(s.ctx, [])
     assert sem.sem_run(s.ctx, 0) is None
     assert sem.sem_run(s.ctx, 15) is None
     u, v, a = sem.sem_get_state(s.ctx)
@@ -241,7 +241,7 @@ def test_duplicate_sources_merge(oracle):
     seis1 = sem.sem_run(s1.ctx, 30)
     s2 = sem.setup_workload(w)
     f = w.source_force[0]
-    sem.sem_set_sources(s2.ctx, [node, node], [0.25 * f, 0.75 * f], w.f0, w.t0)
+    sem.sem_set_source_nodes(s2.ctx, [node, node], [0.25 * f, 0.75 * f], w.f0, w.t0)
     seis2 = sem.sem_run(s2.ctx, 30)
     assert rel_l2(seis2, seis1.astype(np.float64)) < 1e-6
 
@@ -256,16 +256,16 @@ def test_argument_errors():
     bad = mesh.ibool.copy()
     bad[0, 0] = -1
     with pytest.raises(sem.SemError) as ei:
-        sem.sem_set_mesh(ctx, bad, mesh.ctrl, mesh.nglob)
+        sem.sem_set_mesh_corners(ctx, bad, mesh.ctrl, mesh.nglob)
     assert ei.value.code == -1
     with pytest.raises(sem.SemError):
-        sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob + 1)  # unreferenced node
+        sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob + 1)  # unreferenced node
     inverted = mesh.ctrl.copy()
     inverted[0, [0, 1]] = inverted[0, [1, 0]]
     with pytest.raises(sem.SemError) as ei:
-        sem.sem_set_mesh(ctx, mesh.ibool, inverted, mesh.nglob)
+        sem.sem_set_mesh_corners(ctx, mesh.ibool, inverted, mesh.nglob)
     assert "Jacobian" in str(ei.value)
-    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
     with pytest.raises(sem.SemError) as ei:
         sem.sem_step(ctx, 1)
     assert ei.value.code == -4
@@ -276,7 +276,7 @@ def test_argument_errors():
     with pytest.raises(sem.SemError):
         sem.sem_set_dt(ctx, -1.0)
     with pytest.raises(sem.SemError):
-        sem.sem_set_sources(ctx, [mesh.nglob], [[0, 0, 1.0]], 10.0, 0.1)
+        sem.sem_set_source_nodes(ctx, [mesh.nglob], [[0, 0, 1.0]], 10.0, 0.1)
     v = np.ones((mesh.nglob, 3), dtype=np.float32)
     v[3, 1] = np.nan
     with pytest.raises(sem.SemError) as ei:
@@ -307,7 +307,7 @@ def test_plane_wave_periodic(oracle):
     seis_ref, u_ref, *_ = oracle.newmark_run(m, dt, n, u0=u0, v0=v0, a0=a0, rec_nodes=rec)
     ctx = make_ctx(mesh, *mat)
     sem.sem_set_dt(ctx, dt)
-    sem.sem_set_receivers(ctx, rec)
+    sem.sem_set_receiver_nodes(ctx, rec)
     sem.sem_set_state(ctx, u0.astype(np.float32), v0.astype(np.float32), a0.astype(np.float32))
     seis = sem.sem_run(ctx, n)
     assert rel_l2(seis, seis_ref) <= TOL_SEIS
@@ -343,7 +343,7 @@ def test_sweep_slabs_option(oracle):
     for K in (1, 3):
         ctx = sem.sem_create(mesh.ngll, 0)
         sem.sem_set_option(ctx, sem.SEM_OPT_SWEEP_SLABS, K)
-        sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+        sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
         sem.sem_set_material(ctx, *mat)
         info = sem.sem_info(ctx)
         assert info["slabs"] == K

@@ -53,7 +53,7 @@ def material(mesh, seed):
 
 def make_ctx(ngll, ibool, ctrl, nglob, mat):
     ctx = sem.sem_create(ngll, 0)
-    sem.sem_set_mesh(ctx, ibool, ctrl, nglob)
+    sem.sem_set_mesh_corners(ctx, ibool, ctrl, nglob)
     sem.sem_set_material(ctx, *mat)
     return ctx
 
@@ -125,8 +125,8 @@ def test_scrambled_caller_numbering(oracle):
     src = np.array([nperm[mesh.nglob // 2]], dtype=np.int32)
     rec = nperm[np.arange(0, mesh.nglob, mesh.nglob // 7)[:6]].astype(np.int32)
     force = np.array([[0.0, 0.0, 1e10]])
-    sem.sem_set_sources(ctx, src, force, 10.0, 0.12)
-    sem.sem_set_receivers(ctx, rec)
+    sem.sem_set_source_nodes(ctx, src, force, 10.0, 0.12)
+    sem.sem_set_receiver_nodes(ctx, rec)
     sem.sem_set_state(ctx)
     nsteps = 60
     seis = sem.sem_run(ctx, nsteps)
@@ -202,3 +202,18 @@ def test_persistent_sweep_wait_gives_up_and_recovers(oracle):
     sem.sem_sync(ctx)  # the flag was cleared
     f_ref = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, *mat, 5).forces(u.astype(np.float64))
     check_forces(sweep_stride4(ctx, u, 2), f_ref)
+
+
+@pytest.mark.parametrize("ngll", [5, 9])
+def test_atomic_ablation_agrees_within_rounding(oracle, ngll):
+    """The colouring ablation (one launch, float atomics; assembly 3) computes the same
+    forces up to the order of float32 sums: within the stiffness bar of the oracle and 1e-6
+    of the coloured element kernel."""
+    mesh = inputs.structured_hex_mesh((4, 3, 3), ngll, 900.0, jitter=0.1, seed=21)
+    mat = material(mesh, 22)
+    ctx = make_ctx(ngll, mesh.ibool, mesh.ctrl, mesh.nglob, mat)
+    u = inputs.random_field(mesh.nglob, 23)
+    f_atomic = sweep_stride4(ctx, u, 3)
+    f_elem = sweep_stride4(ctx, u, 1)
+    check_forces(f_atomic, oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, *mat, ngll).forces(u.astype(np.float64)))
+    assert rel_l2(f_atomic, f_elem.astype(np.float64)) <= 1e-6

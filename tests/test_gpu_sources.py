@@ -35,7 +35,7 @@ def test_moment_sources_match_oracle(oracle):
     s = sem.setup_workload(w, dt=dt, src_nodes=nodes[:1], rec_nodes=rec)
     sem.sem_set_shots(s.ctx, 3)
     sem.sem_set_shot_moment_sources(s.ctx, np.arange(3), nodes, moments, w.f0, w.t0)
-    sem.sem_set_receivers(s.ctx, rec)
+    sem.sem_set_receiver_nodes(s.ctx, rec)
     sem.sem_set_state(s.ctx)
     seis = sem.sem_run(s.ctx, 100)
     u, _, _ = sem.sem_get_state(s.ctx, want=(True, False, False))

@@ -39,7 +39,7 @@ def test_sources_between_nodes_match_oracle(oracle, kind):
     s = sem.setup_workload(w, dt=dt, src_nodes=[0], rec_nodes=rec)
     sem.sem_set_shots(s.ctx, 3)
     sem.sem_set_shot_sources_at(s.ctx, np.arange(3), pos, f0=w.f0, t0=w.t0, **{kind: values})
-    sem.sem_set_receivers(s.ctx, rec)
+    sem.sem_set_receiver_nodes(s.ctx, rec)
     sem.sem_set_state(s.ctx)
     seis = sem.sem_run(s.ctx, 100)
     u, _, _ = sem.sem_get_state(s.ctx, want=(True, False, False))

@@ -33,7 +33,7 @@ def _context(n, seed):
     vp = inputs.uniform(seed, shape, 3000.0, 5000.0, stream=2).astype(np.float32)
     vs = (vp / 1.8).astype(np.float32)
     ctx = sem.sem_create(5, 0)
-    sem.sem_set_mesh(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
     sem.sem_set_material(ctx, rho, vp, vs)
     sem.sem_set_dt(ctx, sem.sem_suggest_dt(ctx, 0.4))
     u0 = inputs.random_field(mesh.nglob, seed, scale=1e-3)
