@@ -164,6 +164,13 @@ int sem_destroy(sem_ctx* ctx);
  *   0 and 2 give bitwise equal results; 1 differs from them only in the order of the
  *   float32 sums at shared nodes. 0, 1 and 2 are deterministic. */
 #define SEM_OPT_ASSEMBLY 3
+/*   SEM_OPT_NODE_ORDER (takes effect at once): the node order of the device arrays of
+ *   sem_set_state_dev, sem_get_state_dev, sem_run_snapshots and of the snapshots
+ *   sem_adjoint_accumulate / sem_adjoint_segment read: 0 (default) the caller's order, 1 the
+ *   solver's internal order (sem_node_order), which saves a permutation per node and copy
+ *   for arrays that only travel between these calls (checkpoints and snapshots of the
+ *   adjoint). Host arrays always use the caller's order. */
+#define SEM_OPT_NODE_ORDER 5
 /*   SEM_OPT_SWEEP_STALL_TEST (failure-detection test, one-shot): 1 makes the next direct
  *   persistent sweep (SEM_OPT_ASSEMBLY 2, sem_apply_stiffness_strided with stride 4) wait
  *   for a count that never arrives, so that its bounded waits give up and the next sem_sync

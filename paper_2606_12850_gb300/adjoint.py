@@ -20,6 +20,7 @@ class Simulation:
 
     ``ctx`` is a context with its mesh, sources and receivers set; ``dt`` the time step. The
     material is given per call as float tensors/arrays [nspec][ngll^3] (rho, kappa, mu).
+    The simulation sets the context's SEM_OPT_NODE_ORDER to the internal order.
     """
 
     def __init__(self, ctx: sem.Ctx, dt: float, nsteps: int, checkpoint_every: int = 50, device: int = 0):
@@ -32,7 +33,10 @@ class Simulation:
         self.device = torch.device("cuda", device)
         self.nglob = self.ctx.nglob
         self.nrec = self.ctx.nrec
-        self.checkpoints = []  # (step, u, v, a) device tensors [nglob*3]
+        self.checkpoints = []  # (step, u, v, a) device tensors [nglob*3], solver node order
+        # checkpoints and snapshots only travel between library calls: keep them in the
+        # solver's internal node order (no permutation on every copy)
+        sem.sem_set_option(self.ctx, sem.SEM_OPT_NODE_ORDER, 1)
 
     def _state(self):
         n3 = 3 * self.nglob

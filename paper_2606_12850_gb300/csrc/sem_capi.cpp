@@ -65,13 +65,20 @@ struct sem_ctx {
   int* d_node_new = nullptr;      // caller node -> internal node
   PatchDesc* d_pdesc = nullptr;   // patches in sweep order
   uint16_t* d_pslots = nullptr;   // patch tables: shared patch node -> local points meeting there
-  uint32_t* d_pexcl = nullptr;    // patch tables: local points alone at their patch node
+  uint16_t* d_pwords = nullptr;   // patch tables: shared patch node -> its first point's ibool word
   int* d_pcolor_end = nullptr;    // per patch colour, the end of its patch range
   SweepSync* d_sync = nullptr;    // counters of the persistent sweep
   float *d_u = nullptr, *d_v = nullptr, *d_a = nullptr, *d_minv = nullptr;
   float* d_f = nullptr;           // scratch force buffer for sem_energy
   float *d_lam = nullptr, *d_lam_old = nullptr, *d_lamF = nullptr;  // adjoint fields [nglob][4]
   double* d_grad = nullptr;       // [3][nlocal] sensitivities (rho, kappa, mu), record order
+  float* d_grad32 = nullptr;      // [3][nlocal] float32 partial sums, flushed into d_grad
+  int since_flush = 0;            // adjoint steps accumulated in d_grad32
+  int node_order = 0;             // SEM_OPT_NODE_ORDER: device state arrays in caller (0) or internal (1) order
+  int* d_rnode = nullptr;         // distinct receiver nodes (internal ids)
+  int* d_roff = nullptr;          // their receivers: d_rlist[d_roff[t] .. d_roff[t+1])
+  int* d_rlist = nullptr;
+  int nrnodes = 0;
   bool adjoint = false;
   double* d_partials = nullptr;   // scratch partial sums for sem_energy
   DevCtl* d_ctl = nullptr;
@@ -136,8 +143,9 @@ int dev_alloc(sem_ctx* c, T** p, size_t count) {
 }
 
 void free_device(sem_ctx* c) {
-  void* ptrs[] = {c->d_rec, c->d_order, c->d_elist, c->d_perm, c->d_node_new, c->d_pdesc, c->d_pslots, c->d_pexcl, c->d_pcolor_end, c->d_sync, c->d_u, c->d_v,
+  void* ptrs[] = {c->d_rec, c->d_order, c->d_elist, c->d_perm, c->d_node_new, c->d_pdesc, c->d_pslots, c->d_pwords, c->d_pcolor_end, c->d_sync, c->d_u, c->d_v,
                   c->d_a, c->d_minv, c->d_f, c->d_partials, c->d_lam, c->d_lam_old, c->d_lamF, c->d_grad,
+                  c->d_grad32, c->d_rnode, c->d_roff, c->d_rlist,
                   c->d_ctl, c->d_src_node, c->d_src_shot, c->d_src_force, c->d_rec_node};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -148,12 +156,15 @@ void free_device(sem_ctx* c) {
   c->d_node_new = nullptr;
   c->d_pdesc = nullptr;
   c->d_pslots = nullptr;
-  c->d_pexcl = nullptr;
+  c->d_pwords = nullptr;
   c->d_pcolor_end = nullptr;
   c->d_sync = nullptr;
   c->d_u = c->d_v = c->d_a = c->d_minv = c->d_f = nullptr;
   c->d_lam = c->d_lam_old = c->d_lamF = nullptr;
   c->d_grad = nullptr;
+  c->d_grad32 = nullptr;
+  c->d_rnode = c->d_roff = c->d_rlist = nullptr;
+  c->nrnodes = 0;
   c->adjoint = false;
   c->d_partials = nullptr;
   c->d_ctl = nullptr;
@@ -211,7 +222,7 @@ int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int
     P.rec = c->d_rec;
     P.desc = c->d_pdesc;
     P.slots = c->d_pslots;
-    P.excl = c->d_pexcl;
+    P.words = c->d_pwords;
     P.u = u;
     P.f = f;
     P.variant = c->variant;
@@ -344,6 +355,18 @@ int check_sweep_timeout(sem_ctx* c) {
   SEM_CUDA(c, cudaMemsetAsync(&c->d_sync->err, 0, sizeof(int), c->stream));
   SEM_CUDA(c, cudaStreamSynchronize(c->stream));
   return fail(c, SEM_ETIMEOUT, "a bounded wait of the force sweep gave up (the forces of that sweep are incomplete)");
+}
+
+// The float32 sensitivity partials of the steps since the last flush, added into the float64
+// accumulators (every kFlushEvery adjoint steps, at the end of a segment, and before the
+// gradients are read: a float32 sum of a few dozen terms keeps about six digits).
+constexpr int kFlushEvery = 64;
+int flush_gradients(sem_ctx* c) {
+  if (!c->since_flush) return SEM_OK;
+  const long long n = 3ll * c->nspec * c->ngll * c->ngll * c->ngll;
+  SEM_LAUNCH(c, launch_flush_partials(c->d_grad32, c->d_grad, n, c->stream));
+  c->since_flush = 0;
+  return SEM_OK;
 }
 
 // Completes a pending state: a = M^-1 a_raw, v = v_half + dt/2 a.
@@ -572,6 +595,10 @@ int sem_set_option(sem_ctx* c, int option, long long value) {
       c->variant = static_cast<int>(value);
       drop_graph(c);
       return SEM_OK;
+    case SEM_OPT_NODE_ORDER:
+      if (value < 0 || value > 1) return fail(c, SEM_EINVAL, "node order must be 0 (caller) or 1 (internal)");
+      c->node_order = static_cast<int>(value);
+      return SEM_OK;
     case SEM_OPT_SWEEP_STALL_TEST:
       if (value < 0 || value > 1) return fail(c, SEM_EINVAL, "stall test must be 0 or 1");
       c->stall_test = static_cast<int>(value);
@@ -597,7 +624,7 @@ static int set_mesh_impl(sem_ctx* c, int nspec, int nglob, const int32_t* ibool,
   if (nspec < 1 || nglob < 1 || !ibool || (!ctrl_in) == (!pts)) return fail(c, SEM_EINVAL, "sem_set_mesh: bad arguments");
   const int n = c->ngll, np = n * n * n;
   const size_t nloc = static_cast<size_t>(nspec) * np;
-  if (nloc > (1ull << 31) - 1 || nglob > (1 << 30)) return fail(c, SEM_EINVAL, "mesh too large for int32 indexing");
+  if (nloc > (1ull << 31) - 1 || nglob > kMaxNodes) return fail(c, SEM_EINVAL, "mesh too large for int32 indexing");
   std::vector<char> seen(nglob, 0);
   for (size_t q = 0; q < nloc; ++q) {
     if (ibool[q] < 0 || ibool[q] >= nglob)
@@ -748,8 +775,43 @@ static int set_mesh_impl(sem_ctx* c, int nspec, int nglob, const int32_t* ibool,
         }
   }
   // patch descriptors; the first touch of every node in patch-colour order is flagged on the
-  // ibool word of its first local point in that patch's table
+  // ibool word of its first local point in that patch's table, the points alone at their
+  // patch node on their own words; the slot tables become shared-memory offsets of the
+  // patch kernel's workspaces
+  int ES = 0, TS = 0, EPT = 0;
+  if (patch_layout(n, &ES, &TS, &EPT)) return fail(c, SEM_EINVAL, "no patch layout for this order");
+  auto ws_float = [&](int le) { return (le / EPT) * TS + (le % EPT) * ES; };
+  std::vector<uint16_t> slots(plan.csr.size(), kPatchNoSlot), words;
+  std::vector<int> word_off(plan.tab_nelem.size(), 0);
+  for (size_t t = 0; t < plan.tab_nelem.size(); ++t) {
+    const size_t g0 = plan.tab_csr_off[t];
+    const size_t g1 = t + 1 < plan.tab_nelem.size() ? plan.tab_csr_off[t + 1] : plan.csr.size();
+    word_off[t] = static_cast<int>(words.size());
+    for (size_t q = g0; q < g1; ++q) {
+      const uint16_t v = plan.csr[q];
+      if (v == kPatchNoSlot || (v & kPatchChain)) {
+        slots[q] = v;
+        continue;
+      }
+      const int le = v / np, pp = v % np;
+      const int off = ws_float(le) + 3 * pp;
+      if (off >= kPatchChain) return fail(c, SEM_EINVAL, "patch workspace offsets exceed the slot range");
+      slots[q] = static_cast<uint16_t>(off);
+      if ((q - g0) % kPatchSlots == 0 && (q - g0) / kPatchSlots < static_cast<size_t>(plan.tab_nshared[t])) {
+        const int wo = ws_float(le) + 9 * np + pp;  // a shared node's first slot
+        if (wo > 0xFFFF) return fail(c, SEM_EINVAL, "patch workspace offsets exceed the word range");
+        words.push_back(static_cast<uint16_t>(wo));
+      }
+    }
+  }
   std::vector<PatchDesc> pdesc(plan.npatch);
+  auto flag_word = [&](int slot, int pp, uint32_t bit) {
+    float* r = c->rec.data() + static_cast<size_t>(slot) * RW;
+    uint32_t wd;
+    std::memcpy(&wd, &r[kIbool * np + pp], sizeof(uint32_t));
+    wd |= bit;
+    std::memcpy(&r[kIbool * np + pp], &wd, sizeof(uint32_t));
+  };
   for (int P = 0; P < plan.npatch; ++P) {
     PatchDesc& d = pdesc[P];
     const int t = plan.table_of[P];
@@ -757,18 +819,17 @@ static int set_mesh_impl(sem_ctx* c, int nspec, int nglob, const int32_t* ibool,
     d.nelem = plan.patch_off[P + 1] - plan.patch_off[P];
     d.nshared = plan.tab_nshared[t];
     d.slot_off = plan.tab_csr_off[t];
-    d.excl_off = plan.tab_excl_off[t];
+    d.word_off = word_off[t];
     d.pad0 = d.pad1 = d.pad2 = 0;
     const int nnode = plan.node_off[P + 1] - plan.node_off[P];
     for (int k = 0; k < nnode; ++k) {
       if (!(plan.nodes[plan.node_off[P] + k] & kFirstTouchBit)) continue;
       const int q0 = plan.first_q[static_cast<size_t>(plan.tab_first_off[t]) + k];
-      float* r = c->rec.data() + static_cast<size_t>(d.slot0 + q0 / np) * RW;
-      uint32_t wd;
-      std::memcpy(&wd, &r[kIbool * np + q0 % np], sizeof(uint32_t));
-      wd |= kPatchFirstBit;
-      std::memcpy(&r[kIbool * np + q0 % np], &wd, sizeof(uint32_t));
+      flag_word(d.slot0 + q0 / np, q0 % np, kPatchFirstBit);
     }
+    const uint32_t* ex = plan.excl.data() + plan.tab_excl_off[t];
+    for (int q = 0; q < d.nelem * np; ++q)
+      if ((ex[q / 32] >> (q % 32)) & 1u) flag_word(d.slot0 + q / np, q % np, kAloneBit);
   }
   c->pcolor_off = plan.color_off;
   c->npatch = plan.npatch;
@@ -799,8 +860,8 @@ static int set_mesh_impl(sem_ctx* c, int nspec, int nglob, const int32_t* ibool,
   if ((r = dev_alloc(c, &c->d_rec, c->rec.size())) || (r = dev_alloc(c, &c->d_order, c->order.size())) ||
       (r = dev_alloc(c, &c->d_elist, elist.size())) || (r = dev_alloc(c, &c->d_pdesc, pdesc.size())) ||
       (r = dev_alloc(c, &c->d_perm, c->perm.size())) || (r = dev_alloc(c, &c->d_node_new, c->node_new.size())) ||
-      (r = dev_alloc(c, &c->d_pslots, std::max<size_t>(plan.csr.size(), kPatchSlots))) ||
-      (r = dev_alloc(c, &c->d_pexcl, plan.excl.size())) ||
+      (r = dev_alloc(c, &c->d_pslots, std::max<size_t>(slots.size(), kPatchSlots))) ||
+      (r = dev_alloc(c, &c->d_pwords, std::max<size_t>(words.size(), 1))) ||
       (r = dev_alloc(c, &c->d_pcolor_end, static_cast<size_t>(plan.ncolors))) || (r = dev_alloc(c, &c->d_sync, 1)) ||
       (r = dev_alloc(c, &c->d_u, nf)) ||
       (r = dev_alloc(c, &c->d_v, nf)) || (r = dev_alloc(c, &c->d_a, nf)) ||
@@ -817,11 +878,12 @@ static int set_mesh_impl(sem_ctx* c, int nspec, int nglob, const int32_t* ibool,
                               cudaMemcpyHostToDevice, c->stream));
   SEM_CUDA(c, cudaMemcpyAsync(c->d_pdesc, pdesc.data(), pdesc.size() * sizeof(PatchDesc), cudaMemcpyHostToDevice,
                               c->stream));
-  if (!plan.csr.empty())
-    SEM_CUDA(c, cudaMemcpyAsync(c->d_pslots, plan.csr.data(), plan.csr.size() * sizeof(uint16_t),
-                                cudaMemcpyHostToDevice, c->stream));
-  SEM_CUDA(c, cudaMemcpyAsync(c->d_pexcl, plan.excl.data(), plan.excl.size() * sizeof(uint32_t),
-                              cudaMemcpyHostToDevice, c->stream));
+  if (!slots.empty())
+    SEM_CUDA(c, cudaMemcpyAsync(c->d_pslots, slots.data(), slots.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                                c->stream));
+  if (!words.empty())
+    SEM_CUDA(c, cudaMemcpyAsync(c->d_pwords, words.data(), words.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                                c->stream));
   SEM_CUDA(c, cudaMemcpyAsync(c->d_pcolor_end, plan.color_off.data() + 1, plan.ncolors * sizeof(int),
                               cudaMemcpyHostToDevice, c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_sync, 0, sizeof(SweepSync), c->stream));
@@ -1201,12 +1263,33 @@ int sem_set_receiver_nodes(sem_ctx* c, int nrec, const int32_t* node) {
   int r = set_device(c);
   if (r) return r;
   cudaStreamSynchronize(c->stream);
-  c->dev_bytes -= c->nrec * sizeof(int);
+  c->dev_bytes -= c->nrec * sizeof(int) + (2 * c->nrnodes + 1 + c->nrec) * sizeof(int);
   c->nrec = nrec;
-  if ((r = dev_alloc(c, &c->d_rec_node, static_cast<size_t>(nrec)))) return r;
   std::vector<int> internal(nrec);
   for (int k = 0; k < nrec; ++k) internal[k] = c->node_new[node[k]];
-  if (nrec > 0) SEM_CUDA(c, cudaMemcpy(c->d_rec_node, internal.data(), nrec * sizeof(int), cudaMemcpyHostToDevice));
+  // distinct receiver nodes and their receivers in ascending order (adjoint injection)
+  std::vector<int> byn(nrec);
+  for (int k = 0; k < nrec; ++k) byn[k] = k;
+  std::stable_sort(byn.begin(), byn.end(), [&](int x, int y) { return internal[x] < internal[y]; });
+  std::vector<int> rnode, roff(1, 0);
+  for (int k = 0; k < nrec; ++k) {
+    if (k == 0 || internal[byn[k]] != internal[byn[k - 1]]) {
+      if (k > 0) roff.push_back(k);
+      rnode.push_back(internal[byn[k]]);
+    }
+  }
+  if (nrec > 0) roff.push_back(nrec);
+  c->nrnodes = static_cast<int>(rnode.size());
+  if ((r = dev_alloc(c, &c->d_rec_node, static_cast<size_t>(nrec))) ||
+      (r = dev_alloc(c, &c->d_rnode, rnode.size())) || (r = dev_alloc(c, &c->d_roff, rnode.empty() ? 0 : roff.size())) ||
+      (r = dev_alloc(c, &c->d_rlist, byn.size())))
+    return r;
+  if (nrec > 0) {
+    SEM_CUDA(c, cudaMemcpy(c->d_rec_node, internal.data(), nrec * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA(c, cudaMemcpy(c->d_rnode, rnode.data(), rnode.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA(c, cudaMemcpy(c->d_roff, roff.data(), roff.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA(c, cudaMemcpy(c->d_rlist, byn.data(), byn.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   drop_graph(c);
   return SEM_OK;
 }
@@ -1235,8 +1318,8 @@ static int set_state_impl(sem_ctx* c, const float* u, const float* v, const floa
         e = cudaMemcpyAsync(stage, src[q], n3 * sizeof(float), cudaMemcpyHostToDevice, c->stream);
         from = stage;
       }
-      if (e == cudaSuccess)
-        e = static_cast<cudaError_t>(launch_unpack(from, dst[q], c->d_perm, c->nglob, c->shots, c->stream));
+      const int* perm = (!host && c->node_order == 1) ? nullptr : c->d_perm;
+      if (e == cudaSuccess) e = static_cast<cudaError_t>(launch_unpack(from, dst[q], perm, c->nglob, c->shots, c->stream));
     }
     if (e != cudaSuccess) rc = cuda_fail(c, e, "sem_set_state copy");
   }
@@ -1283,8 +1366,9 @@ static int get_state_impl(sem_ctx* c, float* u, float* v, float* a, cudaMemcpyKi
   int rc = SEM_OK;
   for (int q = 0; q < 3 && rc == SEM_OK; ++q) {
     if (!dst[q]) continue;
+    const int* perm = (!host && c->node_order == 1) ? nullptr : c->d_perm;
     cudaError_t e =
-        static_cast<cudaError_t>(launch_pack(src[q], host ? stage : dst[q], c->d_perm, c->nglob, c->shots, c->stream));
+        static_cast<cudaError_t>(launch_pack(src[q], host ? stage : dst[q], perm, c->nglob, c->shots, c->stream));
     if (e == cudaSuccess && host) e = cudaMemcpyAsync(dst[q], stage, n3 * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) rc = cuda_fail(c, e, "sem_get_state copy");
   }
@@ -1319,7 +1403,8 @@ int sem_run_snapshots(sem_ctx* c, int nsteps, float* u_dev) {
   const size_t per = 3 * static_cast<size_t>(c->nglob) * c->shots;
   for (int k = 0; k < nsteps; ++k) {
     if ((r = advance(c, 1, nullptr))) return r;
-    SEM_LAUNCH(c, launch_pack(c->d_u, u_dev + k * per, c->d_perm, c->nglob, c->shots, c->stream));
+    SEM_LAUNCH(c, launch_pack(c->d_u, u_dev + k * per, c->node_order == 1 ? nullptr : c->d_perm, c->nglob, c->shots,
+                              c->stream));
   }
   return SEM_OK;
 }
@@ -1487,12 +1572,15 @@ int sem_adjoint_begin(sem_ctx* c) {
   const size_t nloc = static_cast<size_t>(c->nspec) * c->ngll * c->ngll * c->ngll;
   if (!c->d_lam) {
     if ((r = dev_alloc(c, &c->d_lam, nf)) || (r = dev_alloc(c, &c->d_lam_old, nf)) ||
-        (r = dev_alloc(c, &c->d_lamF, nf)) || (r = dev_alloc(c, &c->d_grad, 3 * nloc)))
+        (r = dev_alloc(c, &c->d_lamF, nf)) || (r = dev_alloc(c, &c->d_grad, 3 * nloc)) ||
+        (r = dev_alloc(c, &c->d_grad32, 3 * nloc)))
       return r;
   }
   SEM_CUDA(c, cudaMemsetAsync(c->d_lam, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_lam_old, 0, nf * sizeof(float), c->stream));
   SEM_CUDA(c, cudaMemsetAsync(c->d_grad, 0, 3 * nloc * sizeof(double), c->stream));
+  SEM_CUDA(c, cudaMemsetAsync(c->d_grad32, 0, 3 * nloc * sizeof(float), c->stream));
+  c->since_flush = 0;
   c->adjoint = true;
   return SEM_OK;
 }
@@ -1503,8 +1591,8 @@ int sem_adjoint_step(sem_ctx* c, const float* G_dev) {
   int r = set_device(c);
   if (r) return r;
   if ((r = forces_all_colors(c, c->d_lam, c->d_lamF, kNodeStride, 1))) return r;
-  SEM_LAUNCH(c, launch_adjoint_update(c->d_lamF, G_dev, c->d_rec_node, c->nrec, c->d_lam, c->d_lam_old, c->d_minv,
-                                      c->nglob, c->dt, c->stream));
+  SEM_LAUNCH(c, launch_adjoint_update(c->d_lamF, G_dev, c->d_rnode, c->d_roff, c->d_rlist, c->nrnodes, c->d_lam,
+                                      c->d_lam_old, c->d_minv, c->nglob, c->dt, c->stream));
   std::swap(c->d_lam, c->d_lam_old);  // lam <- lam^{m-1}, lam_old <- lam^m
   return SEM_OK;
 }
@@ -1516,12 +1604,14 @@ int sem_adjoint_accumulate(sem_ctx* c, const float* u_lo, const float* u_mid, co
   int r = set_device(c);
   if (r) return r;
   const size_t nloc = static_cast<size_t>(c->nspec) * c->ngll * c->ngll * c->ngll;
-  SEM_LAUNCH(c, launch_sensitivity(c->ngll, c->d_rec, c->d_perm, c->d_lam, u_lo, u_mid, u_hi, c->d_grad,
-                                    c->d_grad + nloc, c->d_grad + 2 * nloc, c->nspec, -1.0, -c->dt * c->dt, c->stream));
+  SEM_LAUNCH(c, launch_sensitivity(c->ngll, c->d_rec, c->node_order == 1 ? nullptr : c->d_perm, c->d_lam, u_lo, u_mid,
+                                    u_hi, c->d_grad32, c->d_grad32 + nloc, c->d_grad32 + 2 * nloc, c->nspec, -1.0,
+                                    -c->dt * c->dt, c->stream));
+  if (++c->since_flush >= kFlushEvery) return flush_gradients(c);
   return SEM_OK;
 }
 
-int sem_adjoint_segment(sem_ctx* c, int count, const float* G_dev, const float* u_dev) {
+static int adjoint_segment_steps(sem_ctx* c, int count, const float* G_dev, const float* u_dev) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->adjoint) return fail(c, SEM_ESTATE, "sem_adjoint_begin has not been called");
   if (count < 0) return fail(c, SEM_EINVAL, "count must be >= 0");
@@ -1536,11 +1626,17 @@ int sem_adjoint_segment(sem_ctx* c, int count, const float* G_dev, const float* 
   return SEM_OK;
 }
 
+int sem_adjoint_segment(sem_ctx* c, int count, const float* G_dev, const float* u_dev) {
+  int rs = adjoint_segment_steps(c, count, G_dev, u_dev);
+  if (rs) return rs;
+  return flush_gradients(c);
+}
+
 int sem_adjoint_gradients(sem_ctx* c, double* g_rho, double* g_kappa, double* g_mu) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->adjoint) return fail(c, SEM_ESTATE, "sem_adjoint_begin has not been called");
   int r = set_device(c);
-  if (r) return r;
+  if (r || (r = flush_gradients(c))) return r;
   const int n = c->ngll, np = n * n * n, nl = n * n;
   const size_t nloc = static_cast<size_t>(c->nspec) * np;
   std::vector<double> h(3 * nloc);

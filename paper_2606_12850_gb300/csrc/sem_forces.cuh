@@ -621,23 +621,18 @@ struct PatchCfg {
   static_assert(E >= 1 && 10 * NP <= ES, "team and workspace sizes");
 };
 
-constexpr uint32_t kAlone = 0x80000000u;  // in the shared-memory copy of an ibool word: the
-                                          // point is the only one at its patch node
-
 // Phases 1-3 of one patch for the calling thread's team: gather through the records' ibool
-// words (GB points per thread in flight; the shared-memory word keeps the node, the patch
-// first-touch flag and kAlone), then the element forces.
+// words (GB points per thread in flight; the shared-memory copy of each word keeps the node,
+// the patch first-touch flag and kAloneBit), then the element forces.
 template <int N, bool LO>
 __device__ __forceinline__ void patch_gather_compute(const PatchDesc& d, const float* __restrict__ rec,
-                                                     const uint32_t* __restrict__ excl_tab,
-                                                     const float4* __restrict__ u, float* wsb) {
+                                                     const float4* __restrict__ u, float* wsb, bool u_from_l2) {
   using C = PatchCfg<N>;
   constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, REC = C::REC;
   const int team = threadIdx.x / TEAM;
   const int tl = threadIdx.x - team * TEAM;
   const int ne = min(E, d.nelem - team * E);  // this team's elements
   const float* __restrict__ trec = rec + static_cast<size_t>(d.slot0 + team * E) * REC;
-  const uint32_t* __restrict__ excl = excl_tab + d.excl_off;
   constexpr int GB = 4;
   float* ts = wsb + team * C::TS;
   for (int base = tl; base < ne * NP; base += GB * TEAM) {
@@ -646,17 +641,16 @@ __device__ __forceinline__ void patch_gather_compute(const PatchDesc& d, const f
     for (int r = 0; r < GB; ++r) {
       const int idx = base + r * TEAM;
       const int le = idx / NP;
-      w[r] = 0u;
-      if (idx < ne * NP) {
-        const int c = team * E * NP + idx;  // local point index in the patch table
-        const uint32_t alone = (__ldg(excl + c / 32) >> (c % 32)) & 1u;
-        w[r] = (__float_as_uint(__ldg(trec + static_cast<size_t>(le) * REC + (idx - le * NP))) & ~kFirstTouchBit) |
-               (alone ? kAlone : 0u);
-      }
+      w[r] = idx < ne * NP ? __float_as_uint(__ldg(trec + static_cast<size_t>(le) * REC + (idx - le * NP))) : 0u;
     }
     float4 q[GB];
+    if (u_from_l2) {
 #pragma unroll
-    for (int r = 0; r < GB; ++r) q[r] = __ldg(u + (w[r] & kNodeMask));
+      for (int r = 0; r < GB; ++r) q[r] = __ldcg(u + (w[r] & kNodeMask));
+    } else {
+#pragma unroll
+      for (int r = 0; r < GB; ++r) q[r] = __ldg(u + (w[r] & kNodeMask));
+    }
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
       const int idx = base + r * TEAM;
@@ -709,13 +703,13 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
       if (idx < ne * NP) {
         const int e = idx / NP;
         w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
-        if ((w[r] & kAlone) && !(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + (w[r] & kNodeMask));
+        if ((w[r] & kAloneBit) && !(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + (w[r] & kNodeMask));
       }
     }
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
       const int idx = base + r * TEAM;
-      if (w[r] & kAlone) {
+      if (w[r] & kAloneBit) {
         const int e = idx / NP;
         const float* src = ts + e * ES + 3 * (idx - e * NP);
         f[w[r] & kNodeMask] = make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
@@ -725,30 +719,30 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
 }
 
 // Phase 4b over the CTA: per shared patch node, the sum of its local points' forces in table
-// order (its slots read as one 16-byte word), then one store (first touch) or one
-// read-modify-write; the previous values of GB nodes are loaded before any is written.
+// order (its slots, shared-memory offsets of those forces, read as one 16-byte word), then
+// one store (first touch) or one read-modify-write; the previous values of GB nodes are
+// loaded before any is written.
 template <int N, bool COHERENT>
 __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uint16_t* __restrict__ slot_tab,
-                                                   float4* __restrict__ f, const float* wsb) {
+                                                   const uint16_t* __restrict__ word_tab, float4* __restrict__ f,
+                                                   const float* wsb) {
   using C = PatchCfg<N>;
-  constexpr int NP = C::NP, E = C::E, ES = C::ES, T = C::T, GB = 4;
-  auto ws_of = [&](int le) { return wsb + (le / E) * C::TS + (le % E) * ES; };
+  constexpr int T = C::T, GB = 4;
   const uint4* __restrict__ slots = reinterpret_cast<const uint4*>(slot_tab + d.slot_off);
+  const uint16_t* __restrict__ words = word_tab + d.word_off;
   for (int base = threadIdx.x; base < d.nshared; base += GB * T) {
     uint4 sl[GB];
-#pragma unroll
-    for (int r = 0; r < GB; ++r) {
-      const int t = base + r * T;
-      sl[r] = __ldg(slots + (t < d.nshared ? t : 0));
-    }
     uint32_t w[GB];
     float4 prev[GB];
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
       const int t = base + r * T;
-      const int q0 = static_cast<int>(sl[r].x & 0xFFFFu);  // first slot: never empty, never a chain
-      const int le0 = q0 / NP;
-      w[r] = t < d.nshared ? reinterpret_cast<const uint32_t*>(ws_of(le0) + 9 * NP)[q0 - le0 * NP] : kPatchFirstBit;
+      const int tt = t < d.nshared ? t : 0;
+      sl[r] = __ldg(slots + tt);
+      w[r] = t < d.nshared ? reinterpret_cast<const uint32_t*>(wsb)[__ldg(words + tt)] : kPatchFirstBit;
+    }
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
       prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (!(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + (w[r] & kNodeMask));
     }
@@ -769,8 +763,7 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
               chain = q;
               continue;
             }
-            const int le = static_cast<int>(q) / NP;
-            const float* F = ws_of(le) + 3 * (static_cast<int>(q) - le * NP);
+            const float* F = wsb + q;
             sx += F[0];
             sy += F[1];
             sz += F[2];
@@ -785,24 +778,33 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
 }
 
 // One launch per patch colour: one CTA per patch of the colour [p0, p0 + gridDim.x).
+// The launches of one sweep are programmatic dependent launches: a colour's CTAs may start
+// while the previous colour drains. The first colour of a sweep (p0 == 0) waits for the
+// previous grid before anything (that grid may have written u). A later colour reads only u
+// (which no colour writes, and which was complete before the first colour began; read from
+// L2) and the records until it writes f, so it gathers and evaluates its elements first and
+// waits for the previous colour only before its writes.
 template <int N, bool LO>
 __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
     patch_forces_kernel(const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
-                        const uint16_t* __restrict__ slot_tab, const uint32_t* __restrict__ excl_tab,
+                        const uint16_t* __restrict__ slot_tab, const uint16_t* __restrict__ word_tab,
                         const float4* __restrict__ u, float4* __restrict__ f, int p0) {
   using C = PatchCfg<N>;
   extern __shared__ float4 smem4[];
   float* wsb = reinterpret_cast<float*>(smem4);
   const PatchDesc d = desc[p0 + blockIdx.x];
-  // 0. records to L2 while the previous grid finishes, then wait for its results
+  // 0. records to L2
   if (threadIdx.x < d.nelem)
     prefetch_l2(rec + static_cast<size_t>(d.slot0 + threadIdx.x) * C::REC, kForceFields * C::NP * sizeof(float));
-  wait_prerequisite_grid();
+  if (p0 == 0) wait_prerequisite_grid();
   allow_dependent_grid();
-  patch_gather_compute<N, LO>(d, rec, excl_tab, u, wsb);
+  // before the wait, u comes from L2 (the coherence point), never from a line this SM's L1
+  // may hold from before the grid that wrote u
+  patch_gather_compute<N, LO>(d, rec, u, wsb, p0 != 0);
+  if (p0 != 0) wait_prerequisite_grid();  // the previous colour's writes to f
   patch_write_alone<N, false>(d, f, wsb);  // no wait for the other teams
   __syncthreads();
-  patch_write_shared<N, false>(d, slot_tab, f, wsb);
+  patch_write_shared<N, false>(d, slot_tab, word_tab, f, wsb);
 }
 
 // Persistent form: one sweep (all patch colours) in one launch. CTAs take patches in sweep
@@ -848,7 +850,7 @@ __device__ __forceinline__ unsigned int prior_colour_count(const int* __restrict
 template <int N, bool LO>
 __device__ __noinline__ int sweep_one_patch(int P, const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
                                             const uint16_t* __restrict__ slot_tab,
-                                            const uint32_t* __restrict__ excl_tab, const float4* __restrict__ u,
+                                            const uint16_t* __restrict__ word_tab, const float4* __restrict__ u,
                                             float4* __restrict__ f, int npatch, const int* __restrict__ color_end,
                                             unsigned int stall, SweepSync* sync, SweepShared* sh, float* wsb) {
   __syncthreads();  // every thread is done with sh before it is replaced
@@ -863,7 +865,7 @@ __device__ __noinline__ int sweep_one_patch(int P, const float* __restrict__ rec
   __syncthreads();
   const PatchDesc& d = sh->d;
   prefetch_patch_records<N>(rec, desc, sh->next, npatch);
-  patch_gather_compute<N, LO>(d, rec, excl_tab, u, wsb);
+  patch_gather_compute<N, LO>(d, rec, u, wsb, false);
   const int c = sh->color;
   if (sh->ready) {
     patch_write_alone<N, true>(d, f, wsb);
@@ -886,7 +888,7 @@ __device__ __noinline__ int sweep_one_patch(int P, const float* __restrict__ rec
     if (sh->abort) return -1;
     patch_write_alone<N, true>(d, f, wsb);
   }
-  patch_write_shared<N, true>(d, slot_tab, f, wsb);
+  patch_write_shared<N, true>(d, slot_tab, word_tab, f, wsb);
   __syncthreads();  // all of the patch's writes issued before it counts as done
   if (threadIdx.x == 0) {
     __threadfence();
@@ -898,7 +900,7 @@ __device__ __noinline__ int sweep_one_patch(int P, const float* __restrict__ rec
 template <int N, bool LO>
 __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
     patch_sweep_kernel(const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
-                       const uint16_t* __restrict__ slot_tab, const uint32_t* __restrict__ excl_tab,
+                       const uint16_t* __restrict__ slot_tab, const uint16_t* __restrict__ word_tab,
                        const float4* __restrict__ u, float4* __restrict__ f, int npatch,
                        const int* __restrict__ color_end, int ncolors, unsigned int stall, SweepSync* sync) {
   extern __shared__ float4 smem4[];
@@ -914,7 +916,7 @@ __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
   int P = sh.next;
   prefetch_patch_records<N>(rec, desc, P, npatch);
   while (P >= 0 && P < npatch)
-    P = sweep_one_patch<N, LO>(P, rec, desc, slot_tab, excl_tab, u, f, npatch, color_end, stall, sync, &sh, wsb);
+    P = sweep_one_patch<N, LO>(P, rec, desc, slot_tab, word_tab, u, f, npatch, color_end, stall, sync, &sh, wsb);
   if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(&sync->exited, 1u) == gridDim.x - 1) {  // every CTA has left: reset
@@ -934,23 +936,26 @@ __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
 //   g_mu[q]    += c_k * w_q J_q 2 (e(lam) : e(u_mid) - tr e(lam) tr e(u_mid) / 3)
 // with e the discrete strain (the same derivatives and chain rule as the force kernel),
 // c_m = -1 and c_k = -dt^2. lam is the adjoint field in the solver layout [nglob][4] (internal
-// node order), the u_* displacement snapshots [nglob][3] in caller node order (perm maps). The terms are formed in float32 (the second
-// difference as (u_hi - u_mid) - (u_mid - u_lo), which keeps the digits the plain form
-// cancels) and added to float64 accumulators per local point in record order (element,
-// q = i N^2 + line). No two threads write the same point, so there are no colours here.
+// node order), the u_* displacement snapshots [nglob][3] in caller node order (perm maps) or,
+// with perm null, in internal order. The terms are formed in float32 (the second difference
+// as (u_hi - u_mid) - (u_mid - u_lo), which keeps the digits the plain form cancels) and
+// added to float32 partial sums per local point in record order (element, q = i N^2 +
+// line), which the host flushes into float64 accumulators every few dozen steps. No two
+// threads write the same point, so there are no colours here.
 // ---------------------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(ForceCfg<N>::T)
     sensitivity_kernel(const float* __restrict__ rec, const int* __restrict__ perm, const float* __restrict__ lam,
                        const float* __restrict__ u_lo,
-                       const float* __restrict__ u_mid, const float* __restrict__ u_hi, double* __restrict__ g_rho,
-                       double* __restrict__ g_kappa, double* __restrict__ g_mu, int nspec, double c_m, double c_k) {
+                       const float* __restrict__ u_mid, const float* __restrict__ u_hi, float* __restrict__ g_rho,
+                       float* __restrict__ g_kappa, float* __restrict__ g_mu, int nspec, double c_m, double c_k) {
   using C = ForceCfg<N>;
   constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
   static_assert(7 * NP <= ES, "element tile holds lam, u and the mass term");
   extern __shared__ float4 smem4[];
   const float* __restrict__ H = c_h;
   const float* __restrict__ W = c_w;
+  const float cm = static_cast<float>(c_m), ck = static_cast<float>(c_k);
   const int team = threadIdx.x / TEAM;
   const int tl = threadIdx.x - team * TEAM;
   const int ebase = (blockIdx.x * C::TEAMS + team) * E;
@@ -972,7 +977,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
     float um[GB][3], uh[GB][3], ul[GB][3];
     size_t gc[GB];  // caller node of each point (the snapshots are in caller order)
 #pragma unroll
-    for (int r = 0; r < GB; ++r) gc[r] = static_cast<size_t>(__ldg(perm + g[r]));
+    for (int r = 0; r < GB; ++r) gc[r] = perm ? static_cast<size_t>(__ldg(perm + g[r])) : g[r];
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
       l4[r] = __ldg(reinterpret_cast<const float4*>(lam) + g[r]);
@@ -1054,9 +1059,9 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
     const float trl = gl[0][0] + gl[1][1] + gl[2][2];
     const float tru = gu[0][0] + gu[1][1] + gu[2][2];
     const float wJ = W[i] * W[j] * W[k] * jac;
-    g_rho[out + q] += c_m * static_cast<double>(wJ * fm[i + N * line]);
-    g_kappa[out + q] += c_k * static_cast<double>(wJ * trl * tru);
-    g_mu[out + q] += c_k * static_cast<double>(2.f * wJ * (ee - trl * tru * (1.f / 3.f)));
+    g_rho[out + q] += cm * (wJ * fm[i + N * line]);
+    g_kappa[out + q] += ck * (wJ * trl * tru);
+    g_mu[out + q] += ck * (2.f * wJ * (ee - trl * tru * (1.f / 3.f)));
   }
 }
 
@@ -1140,13 +1145,13 @@ int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return static_cast<int>(e);
     cfg.gridDim = dim3(static_cast<unsigned>(sms * per_sm));
-    return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_sweep_kernel<SEM_NGLL, LO>, L.rec, L.desc, L.slots, L.excl,
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_sweep_kernel<SEM_NGLL, LO>, L.rec, L.desc, L.slots, L.words,
                                                reinterpret_cast<const float4*>(L.u), reinterpret_cast<float4*>(L.f),
                                                L.npatch, L.color_end, L.ncolors, L.stall ? 1u : 0u, L.sync));
   }
   if (int r = raise_smem_limit(attr_done, patch_forces_kernel<SEM_NGLL, LO>, C::SMEM)) return r;
   cfg.gridDim = dim3(L.p1 - L.p0);
-  return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO>, L.rec, L.desc, L.slots, L.excl,
+  return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO>, L.rec, L.desc, L.slots, L.words,
                                              reinterpret_cast<const float4*>(L.u), reinterpret_cast<float4*>(L.f),
                                              L.p0));
 }
@@ -1191,8 +1196,8 @@ int SEM_CAT(launch_forces_, SEM_NGLL)(const ForceLaunch& L, void* stream) {
 }
 
 int SEM_CAT(launch_sensitivity_, SEM_NGLL)(const float* rec, const int* perm, const float* lam, const float* u_lo,
-                                          const float* u_mid, const float* u_hi, double* g_rho, double* g_kappa,
-                                          double* g_mu, int nspec, double c_m, double c_k, void* stream) {
+                                          const float* u_mid, const float* u_hi, float* g_rho, float* g_kappa,
+                                          float* g_mu, int nspec, double c_m, double c_k, void* stream) {
   using C = ForceCfg<SEM_NGLL>;
   static std::atomic<unsigned long long> attr_done{0};
   const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
@@ -1207,6 +1212,13 @@ int SEM_CAT(forces_smem_bytes_, SEM_NGLL)() { return ForceCfg<SEM_NGLL>::SMEM_FL
 
 int SEM_CAT(launch_patch_forces_, SEM_NGLL)(const PatchLaunch& L, void* stream) {
   return launch_patch_n(L, static_cast<cudaStream_t>(stream));
+}
+
+void SEM_CAT(patch_layout_, SEM_NGLL)(int* es, int* ts, int* e) {
+  using C = PatchCfg<SEM_NGLL>;
+  *es = C::ES;
+  *ts = C::TS;
+  *e = C::E;
 }
 
 void SEM_CAT(patch_shape_, SEM_NGLL)(PatchShape* out) {

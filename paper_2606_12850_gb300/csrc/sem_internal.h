@@ -34,10 +34,13 @@ constexpr int kNodeStride = 4;
 // so the assembled array needs no zeroing pass.
 constexpr uint32_t kFirstTouchBit = 0x80000000u;
 // Bit 30 marks the same for the patch kernel's order (patch colour by patch colour), on the
-// word of the first local point (in patch-table order) of each patch node; node ids are
-// below 2^30.
+// word of the first local point (in patch-table order) of each patch node. Bit 29 marks a
+// local point that is the only one of its patch at its node (its element's team writes it
+// alone). Node ids are below 2^29.
 constexpr uint32_t kPatchFirstBit = 0x40000000u;
-constexpr uint32_t kNodeMask = 0x3FFFFFFFu;
+constexpr uint32_t kAloneBit = 0x20000000u;
+constexpr uint32_t kNodeMask = 0x1FFFFFFFu;
+constexpr int kMaxNodes = 1 << 29;
 
 inline int rec_words(int ngll) {
   const int np = ngll * ngll * ngll;
@@ -160,8 +163,10 @@ struct alignas(16) PatchDesc {
   int slot0;     // record slot of the patch's first element (its elements are consecutive)
   int nelem;
   int nshared;   // patch nodes met by several of its local points
-  int slot_off;  // its table: per shared node, kPatchSlots slots of the local points meeting there
-  int excl_off;  // its table: bit mask of the local points alone at their patch node
+  int slot_off;  // its table: per shared node, kPatchSlots slots (shared-memory offsets of the
+                 // forces of the local points meeting there)
+  int word_off;  // its table: per shared node, the shared-memory offset of its first local
+                 // point's ibool word
   int pad0, pad1, pad2;
 };
 // Counters of a persistent sweep (all patch colours in one launch): patches taken, CTAs
@@ -178,7 +183,7 @@ struct PatchLaunch {
   const float* rec;
   const PatchDesc* desc;
   const uint16_t* slots;
-  const uint32_t* excl;
+  const uint16_t* words;
   SweepSync* sync;        // non-null: one persistent launch over all colours
   const int* color_end;   // per colour, the end of its patch range (persistent launch)
   int npatch, ncolors;    // (persistent launch)
@@ -189,6 +194,9 @@ struct PatchLaunch {
   int variant;  // contraction form as in ForceLaunch
 };
 int launch_patch_forces(int ngll, const PatchLaunch& launch, void* stream);
+// Shared-memory layout of the patch kernel for this order: workspace floats per element,
+// per team, and elements per team (the slot tables hold offsets into it).
+int patch_layout(int ngll, int* es, int* ts, int* e);
 // the brick each order's patch kernel is compiled for
 int patch_shape(int ngll, PatchShape* out);
 int forces_kernel_smem_bytes(int ngll);
@@ -199,16 +207,21 @@ int launch_predictor(const DevProblem& p, void* stream);
 int launch_fused_newmark(const DevProblem& p, void* stream);
 int launch_corrector(const DevProblem& p, void* stream);
 int launch_sources_record(const DevProblem& p, void* stream);
-// u_lo, u_mid, u_hi: caller layout and order [nglob][3] (perm: internal -> caller node)
+// u_lo, u_mid, u_hi: [nglob][3] in caller order (perm: internal -> caller node) or in
+// internal order (perm null); the terms are added to float32 partials g_* [nlocal]
 int launch_sensitivity(int ngll, const float* rec, const int* perm, const float* lam, const float* u_lo,
-                       const float* u_mid, const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec,
+                       const float* u_mid, const float* u_hi, float* g_rho, float* g_kappa, float* g_mu, int nspec,
                        double c_m, double c_k, void* stream);
 // solver layout [nglob][shots][kNodeStride] in internal node order <-> caller layout
 // [shots][nglob][3] in caller node order (perm: internal -> caller node)
 int launch_pack(const float* u, float* out, const int* perm, int nglob, int shots, void* stream);
 int launch_unpack(const float* in, float* u, const int* perm, int nglob, int shots, void* stream);
-int launch_adjoint_update(float* F, const float* G_dev, const int* rec_node, int nrec, const float* lam,
-                          float* lam_old, const float* minv, int nglob, double dt, void* stream);
+// rnode[nnodes]: distinct receiver nodes; rlist[roff[t] .. roff[t+1]): their receivers
+int launch_adjoint_update(float* F, const float* G_dev, const int* rnode, const int* roff, const int* rlist,
+                          int nnodes, const float* lam, float* lam_old, const float* minv, int nglob, double dt,
+                          void* stream);
+// acc[t] += part[t] (float64), part[t] = 0, for t < n
+int launch_flush_partials(float* part, double* acc, long long n, void* stream);
 // Material on the device (Sec. II-B moduli, Sec. I diagonal mass). rho, p1, p2: per local
 // point in caller order [nspec][ngll^3]; moduli: (p1, p2) = (kappa, mu), else (vp, vs).
 struct MaterialLaunch {

@@ -17,9 +17,10 @@ namespace semgb {
   int forces_smem_bytes_##n();                                                                            \
   int launch_patch_forces_##n(const PatchLaunch& L, void* stream);                                        \
   void patch_shape_##n(PatchShape* out);                                                                  \
+  void patch_layout_##n(int* es, int* ts, int* e);                                                        \
   int launch_sensitivity_##n(const float* rec, const int* perm, const float* lam, const float* u_lo,       \
-                             const float* u_mid, const float* u_hi, double* g_rho, double* g_kappa,     \
-                             double* g_mu, int nspec, double c_m, double c_k, void* stream);
+                             const float* u_mid, const float* u_hi, float* g_rho, float* g_kappa,       \
+                             float* g_mu, int nspec, double c_m, double c_k, void* stream);
 SEM_DECLARE_ORDER(2)
 SEM_DECLARE_ORDER(3)
 SEM_DECLARE_ORDER(4)
@@ -59,7 +60,7 @@ int launch_forces(int n, const ForceLaunch& L, void* stream) {
 }
 
 int launch_sensitivity(int n, const float* rec, const int* perm, const float* lam, const float* u_lo,
-                       const float* u_mid, const float* u_hi, double* g_rho, double* g_kappa, double* g_mu, int nspec,
+                       const float* u_mid, const float* u_hi, float* g_rho, float* g_kappa, float* g_mu, int nspec,
                        double c_m, double c_k, void* stream) {
 #define SEM_CALL(k) \
   launch_sensitivity_##k(rec, perm, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k, stream)
@@ -77,6 +78,13 @@ int launch_patch_forces(int n, const PatchLaunch& L, void* stream) {
 
 int patch_shape(int n, PatchShape* out) {
 #define SEM_CALL(k) (patch_shape_##k(out), 0)
+  SEM_ORDER_SWITCH(n, SEM_CALL)
+#undef SEM_CALL
+  return -1;
+}
+
+int patch_layout(int n, int* es, int* ts, int* e) {
+#define SEM_CALL(k) (patch_layout_##k(es, ts, e), 0)
   SEM_ORDER_SWITCH(n, SEM_CALL)
 #undef SEM_CALL
   return -1;
@@ -176,14 +184,21 @@ int launch_corrector(const DevProblem& p, void* stream) {
 // ---------------------------------------------------------------------------------------
 // Adjoint leapfrog (the discrete adjoint of the scheme above, run backward in time):
 //   lam_new = 2 lam - lam_old + dt^2 M^-1 F,  F = -K lam + R^T G / dt^2
-// written over lam_old. Receiver residuals are added to F by one thread in a fixed order
-// (receivers may share a node).
+// written over lam_old. Receiver residuals are added to F by one thread per receiver node,
+// its receivers in ascending order (receivers may share a node).
 // ---------------------------------------------------------------------------------------
-__global__ void adjoint_inject_kernel(float* __restrict__ F, const float* __restrict__ G, const int* __restrict__ rec_node,
-                                      int nrec, float inv_dt2) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  for (int r = 0; r < nrec; ++r)
-    for (int c = 0; c < 3; ++c) F[kNodeStride * static_cast<size_t>(rec_node[r]) + c] += G[3 * r + c] * inv_dt2;
+__global__ void adjoint_inject_kernel(float* __restrict__ F, const float* __restrict__ G,
+                                      const int* __restrict__ rnode, const int* __restrict__ roff,
+                                      const int* __restrict__ rlist, int nnodes, float inv_dt2) {
+  // one thread per distinct receiver node; its receivers in ascending order (the order a
+  // single thread walking the receivers would add them in)
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nnodes; t += gridDim.x * blockDim.x) {
+    float* Fn = F + kNodeStride * static_cast<size_t>(rnode[t]);
+    for (int q = roff[t]; q < roff[t + 1]; ++q) {
+      const int r = rlist[q];
+      for (int c = 0; c < 3; ++c) Fn[c] += G[3 * r + c] * inv_dt2;
+    }
+  }
 }
 
 __global__ void adjoint_leapfrog_kernel(const float4* __restrict__ lam, float4* __restrict__ lam_old,
@@ -196,11 +211,27 @@ __global__ void adjoint_leapfrog_kernel(const float4* __restrict__ lam, float4* 
   }
 }
 
-int launch_adjoint_update(float* F, const float* G_dev, const int* rec_node, int nrec, const float* lam,
-                          float* lam_old, const float* minv, int nglob, double dt, void* stream) {
+__global__ void flush_partials_kernel(float* __restrict__ part, double* __restrict__ acc, long long n) {
+  for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    acc[t] += static_cast<double>(part[t]);
+    part[t] = 0.f;
+  }
+}
+
+int launch_flush_partials(float* part, double* acc, long long n, void* stream) {
+  if (n <= 0) return 0;
+  flush_partials_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(part, acc, n);
+  return static_cast<int>(cudaGetLastError());
+}
+
+int launch_adjoint_update(float* F, const float* G_dev, const int* rnode, const int* roff, const int* rlist,
+                          int nnodes, const float* lam, float* lam_old, const float* minv, int nglob, double dt,
+                          void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (G_dev && nrec > 0) {
-    adjoint_inject_kernel<<<1, 1, 0, s>>>(F, G_dev, rec_node, nrec, static_cast<float>(1.0 / (dt * dt)));
+  if (G_dev && nnodes > 0) {
+    adjoint_inject_kernel<<<(nnodes + 127) / 128, 128, 0, s>>>(F, G_dev, rnode, roff, rlist, nnodes,
+                                                             static_cast<float>(1.0 / (dt * dt)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return static_cast<int>(e);
   }
@@ -319,8 +350,8 @@ int launch_material_apply(const MaterialLaunch& m, const int* sweep_off, int nra
 }
 
 // Layout changes between the solver's fields [nglob][shots][4] (internal node order) and the
-// caller's arrays [shots][nglob][3] (caller node order): state copies, displacement
-// snapshots. One thread per (node, shot).
+// caller's arrays [shots][nglob][3] (caller node order through perm, or internal order when
+// perm is null): state copies, displacement snapshots. One thread per (node, shot).
 __global__ void pack_kernel(const float4* __restrict__ u, float* __restrict__ out, const int* __restrict__ perm,
                             long long nglob, int shots) {
   const long long n = nglob * shots;
@@ -329,7 +360,7 @@ __global__ void pack_kernel(const float4* __restrict__ u, float* __restrict__ ou
     const long long g = shots == 1 ? t : t / shots;
     const long long sh = t - g * shots;
     const float4 v = u[t];
-    float* o = out + 3 * (sh * nglob + perm[g]);
+    float* o = out + 3 * (sh * nglob + (perm ? perm[g] : g));
     o[0] = v.x;
     o[1] = v.y;
     o[2] = v.z;
@@ -343,7 +374,7 @@ __global__ void unpack_kernel(const float* __restrict__ in, float4* __restrict__
        t += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long g = shots == 1 ? t : t / shots;
     const long long sh = t - g * shots;
-    const float* i = in + 3 * (sh * nglob + perm[g]);
+    const float* i = in + 3 * (sh * nglob + (perm ? perm[g] : g));
     u[t] = make_float4(i[0], i[1], i[2], 0.f);
   }
 }

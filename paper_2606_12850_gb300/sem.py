@@ -271,6 +271,7 @@ SEM_OPT_SWEEP_SLABS = 1
 SEM_OPT_CONTRACTION = 2
 SEM_OPT_ASSEMBLY = 3
 SEM_OPT_SWEEP_STALL_TEST = 4
+SEM_OPT_NODE_ORDER = 5
 
 
 def sem_set_option(ctx: Ctx, option: int, value: int):
