@@ -212,12 +212,12 @@ int set_device(sem_ctx* c) {
 }
 
 // f = -K u over all colours (Sec. IV-C: colour by colour, no atomics). On the context's own
-// single-shot fields the patch kernel takes the patch colours in order (one launch per
-// colour; patches of a colour share no node). Otherwise (several shots, caller arrays, or
+// fields the patch kernel takes the patch colours in order (one launch per colour, one CTA
+// per patch and shot; patches of a colour share no node). Otherwise (caller arrays, or
 // SEM_OPT_ASSEMBLY = 1) the element kernel walks the element list slab by slab and, inside a
 // slab, colour by colour: a launch holds elements of one colour only.
 int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int shots) {
-  if (c->assembly != 1 && node_stride == kNodeStride && shots == 1 && c->npatch > 0) {
+  if ((c->assembly == 0 || c->assembly == 2) && node_stride == kNodeStride && c->npatch > 0) {
     PatchLaunch P{};
     P.rec = c->d_rec;
     P.desc = c->d_pdesc;
@@ -226,8 +226,9 @@ int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int
     P.u = u;
     P.f = f;
     P.variant = c->variant;
+    P.shots = shots;
     const int npc = static_cast<int>(c->pcolor_off.size()) - 1;
-    if (c->assembly == 2 && npc <= kMaxSweepColors) {
+    if (c->assembly == 2 && shots == 1 && npc <= kMaxSweepColors) {
       P.sync = c->d_sync;
       P.color_end = c->d_pcolor_end;
       P.npatch = c->npatch;

@@ -621,12 +621,22 @@ struct PatchCfg {
   static_assert(E >= 1 && 10 * NP <= ES, "team and workspace sizes");
 };
 
+// Index of a node's 16-byte slot in a [nglob][S][4] field (S = 1 for a single shot).
+template <bool MS>
+__device__ __forceinline__ size_t node_slot(uint32_t w, int S, int shot) {
+  if constexpr (MS)
+    return static_cast<size_t>(w & kNodeMask) * S + shot;
+  else
+    return static_cast<size_t>(w & kNodeMask);
+}
+
 // Phases 1-3 of one patch for the calling thread's team: gather through the records' ibool
 // words (GB points per thread in flight; the shared-memory copy of each word keeps the node,
 // the patch first-touch flag and kAloneBit), then the element forces.
-template <int N, bool LO>
+template <int N, bool LO, bool MS = false>
 __device__ __forceinline__ void patch_gather_compute(const PatchDesc& d, const float* __restrict__ rec,
-                                                     const float4* __restrict__ u, float* wsb, bool u_from_l2) {
+                                                     const float4* __restrict__ u, float* wsb, bool u_from_l2,
+                                                     int S = 1, int shot = 0) {
   using C = PatchCfg<N>;
   constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, REC = C::REC;
   const int team = threadIdx.x / TEAM;
@@ -646,10 +656,10 @@ __device__ __forceinline__ void patch_gather_compute(const PatchDesc& d, const f
     float4 q[GB];
     if (u_from_l2) {
 #pragma unroll
-      for (int r = 0; r < GB; ++r) q[r] = __ldcg(u + (w[r] & kNodeMask));
+      for (int r = 0; r < GB; ++r) q[r] = __ldcg(u + node_slot<MS>(w[r], S, shot));
     } else {
 #pragma unroll
-      for (int r = 0; r < GB; ++r) q[r] = __ldg(u + (w[r] & kNodeMask));
+      for (int r = 0; r < GB; ++r) q[r] = __ldg(u + node_slot<MS>(w[r], S, shot));
     }
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
@@ -684,8 +694,9 @@ __device__ __forceinline__ float4 load_f(const float4* p) {
 
 // Phase 4a for the calling thread's team: the forces of its points that are alone at their
 // patch node added to the node (stored at its first touch).
-template <int N, bool COHERENT>
-__device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __restrict__ f, const float* wsb) {
+template <int N, bool COHERENT, bool MS = false>
+__device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __restrict__ f, const float* wsb,
+                                                  int S = 1, int shot = 0) {
   using C = PatchCfg<N>;
   constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, GB = 4;
   const int team = threadIdx.x / TEAM;
@@ -703,7 +714,7 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
       if (idx < ne * NP) {
         const int e = idx / NP;
         w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
-        if ((w[r] & kAloneBit) && !(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + (w[r] & kNodeMask));
+        if ((w[r] & kAloneBit) && !(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + node_slot<MS>(w[r], S, shot));
       }
     }
 #pragma unroll
@@ -712,7 +723,7 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
       if (w[r] & kAloneBit) {
         const int e = idx / NP;
         const float* src = ts + e * ES + 3 * (idx - e * NP);
-        f[w[r] & kNodeMask] = make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
+        f[node_slot<MS>(w[r], S, shot)] = make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
       }
     }
   }
@@ -722,10 +733,10 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
 // order (its slots, shared-memory offsets of those forces, read as one 16-byte word), then
 // one store (first touch) or one read-modify-write; the previous values of GB nodes are
 // loaded before any is written.
-template <int N, bool COHERENT>
+template <int N, bool COHERENT, bool MS = false>
 __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uint16_t* __restrict__ slot_tab,
                                                    const uint16_t* __restrict__ word_tab, float4* __restrict__ f,
-                                                   const float* wsb) {
+                                                   const float* wsb, int S = 1, int shot = 0) {
   using C = PatchCfg<N>;
   constexpr int T = C::T, GB = 4;
   const uint4* __restrict__ slots = reinterpret_cast<const uint4*>(slot_tab + d.slot_off);
@@ -744,7 +755,7 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
       prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (!(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + (w[r] & kNodeMask));
+      if (!(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + node_slot<MS>(w[r], S, shot));
     }
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
@@ -771,7 +782,7 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
           if (!chain) break;
           g4 = __ldg(slots + (chain & ~static_cast<uint32_t>(kPatchChain)));
         }
-        f[w[r] & kNodeMask] = make_float4(prev[r].x + sx, prev[r].y + sy, prev[r].z + sz, 0.f);
+        f[node_slot<MS>(w[r], S, shot)] = make_float4(prev[r].x + sx, prev[r].y + sy, prev[r].z + sz, 0.f);
       }
     }
   }
@@ -784,27 +795,33 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
 // (which no colour writes, and which was complete before the first colour began; read from
 // L2) and the records until it writes f, so it gathers and evaluates its elements first and
 // waits for the previous colour only before its writes.
-template <int N, bool LO>
+// With S shots (MS true) the fields are [nglob][S][4] and CTA b takes patch p0 + b / S for
+// shot b % S: consecutive CTAs take the shots of one patch, so its records come from DRAM
+// once (the first shot's prefetch) and from L2 for the others.
+template <int N, bool LO, bool MS>
 __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
     patch_forces_kernel(const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
                         const uint16_t* __restrict__ slot_tab, const uint16_t* __restrict__ word_tab,
-                        const float4* __restrict__ u, float4* __restrict__ f, int p0) {
+                        const float4* __restrict__ u, float4* __restrict__ f, int p0, int S_arg) {
   using C = PatchCfg<N>;
   extern __shared__ float4 smem4[];
   float* wsb = reinterpret_cast<float*>(smem4);
-  const PatchDesc d = desc[p0 + blockIdx.x];
-  // 0. records to L2
-  if (threadIdx.x < d.nelem)
+  const int S = MS ? S_arg : 1;
+  const int P = p0 + (MS ? static_cast<int>(blockIdx.x) / S : static_cast<int>(blockIdx.x));
+  const int shot = MS ? static_cast<int>(blockIdx.x) - (P - p0) * S : 0;
+  const PatchDesc d = desc[P];
+  // 0. records to L2 (by the patch's first shot)
+  if (shot == 0 && threadIdx.x < d.nelem)
     prefetch_l2(rec + static_cast<size_t>(d.slot0 + threadIdx.x) * C::REC, kForceFields * C::NP * sizeof(float));
   if (p0 == 0) wait_prerequisite_grid();
   allow_dependent_grid();
   // before the wait, u comes from L2 (the coherence point), never from a line this SM's L1
   // may hold from before the grid that wrote u
-  patch_gather_compute<N, LO>(d, rec, u, wsb, p0 != 0);
+  patch_gather_compute<N, LO, MS>(d, rec, u, wsb, p0 != 0, S, shot);
   if (p0 != 0) wait_prerequisite_grid();  // the previous colour's writes to f
-  patch_write_alone<N, false>(d, f, wsb);  // no wait for the other teams
+  patch_write_alone<N, false, MS>(d, f, wsb, S, shot);  // no wait for the other teams
   __syncthreads();
-  patch_write_shared<N, false>(d, slot_tab, word_tab, f, wsb);
+  patch_write_shared<N, false, MS>(d, slot_tab, word_tab, f, wsb, S, shot);
 }
 
 // Persistent form: one sweep (all patch colours) in one launch. CTAs take patches in sweep
@@ -1115,7 +1132,7 @@ int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
   return lo ? launch_forces_ms<false, true, false>(L, s) : launch_forces_ms<false, false, false>(L, s);
 }
 
-template <bool LO>
+template <bool LO, bool MS>
 int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
   using C = PatchCfg<SEM_NGLL>;
   static std::atomic<unsigned long long> attr_done{0}, attr_done_p{0};
@@ -1129,7 +1146,7 @@ int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (L.sync) {  // one persistent launch for the whole sweep
+  if (L.sync && !MS) {  // one persistent launch for the whole sweep
     if (int r = raise_smem_limit(attr_done_p, patch_sweep_kernel<SEM_NGLL, LO>, C::SMEM)) return r;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1149,18 +1166,20 @@ int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
                                                reinterpret_cast<const float4*>(L.u), reinterpret_cast<float4*>(L.f),
                                                L.npatch, L.color_end, L.ncolors, L.stall ? 1u : 0u, L.sync));
   }
-  if (int r = raise_smem_limit(attr_done, patch_forces_kernel<SEM_NGLL, LO>, C::SMEM)) return r;
-  cfg.gridDim = dim3(L.p1 - L.p0);
-  return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO>, L.rec, L.desc, L.slots, L.words,
-                                             reinterpret_cast<const float4*>(L.u), reinterpret_cast<float4*>(L.f),
-                                             L.p0));
+  if (int r = raise_smem_limit(attr_done, patch_forces_kernel<SEM_NGLL, LO, MS>, C::SMEM)) return r;
+  const int S = MS ? L.shots : 1;
+  cfg.gridDim = dim3(static_cast<unsigned>((L.p1 - L.p0) * S));
+  return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, MS>, L.rec, L.desc, L.slots,
+                                             L.words, reinterpret_cast<const float4*>(L.u),
+                                             reinterpret_cast<float4*>(L.f), L.p0, S));
 }
 
 int launch_patch_n(const PatchLaunch& L, cudaStream_t s) {
   if (L.sync ? L.npatch <= 0 : L.p1 <= L.p0) return 0;
   using C = ForceCfg<SEM_NGLL>;
   const bool lo = L.variant == 0 ? C::LINE_OWNERS : L.variant == 1;
-  return lo ? launch_patch_lo<true>(L, s) : launch_patch_lo<false>(L, s);
+  if (L.shots > 1) return lo ? launch_patch_lo<true, true>(L, s) : launch_patch_lo<false, true>(L, s);
+  return lo ? launch_patch_lo<true, false>(L, s) : launch_patch_lo<false, false>(L, s);
 }
 
 }  // namespace

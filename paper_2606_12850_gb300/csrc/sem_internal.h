@@ -157,8 +157,8 @@ struct ForceLaunch {
 };
 int launch_forces(int ngll, const ForceLaunch& launch, void* stream);
 
-// One patch colour [p0, p1) of the patch sweep order on the context's own [nglob][4] fields
-// (single shot): f (=|+=) -K u.
+// One patch colour [p0, p1) of the patch sweep order on the context's own [nglob][shots][4]
+// fields: f (=|+=) -K u.
 struct alignas(16) PatchDesc {
   int slot0;     // record slot of the patch's first element (its elements are consecutive)
   int nelem;
@@ -192,6 +192,7 @@ struct PatchLaunch {
   float* f;
   int p0, p1;
   int variant;  // contraction form as in ForceLaunch
+  int shots;    // > 1: fields [nglob][shots][kNodeStride], one CTA per (patch, shot)
 };
 int launch_patch_forces(int ngll, const PatchLaunch& launch, void* stream);
 // Shared-memory layout of the patch kernel for this order: workspace floats per element,
