@@ -145,15 +145,17 @@ int sem_destroy(sem_ctx* ctx);
  *   owners, 2 = per point; sem_autotune sets it from measurement. */
 #define SEM_OPT_CONTRACTION 2
 /*   SEM_OPT_ASSEMBLY (takes effect at once): how the force sweep assembles element forces
- *   on the context's own single-shot fields. Patches are bricks of neighbouring elements
+ *   on the context's own fields. Patches are bricks of neighbouring elements
  *   (2 x 2 x 2 at NGLL 5; sem_patch_info gives the shape) evaluated by one CTA each, which
  *   sums the forces meeting at each of the brick's nodes in a fixed order and writes each
  *   node once; the bricks are coloured so that no two of a colour share a node (Sec. IV-C's
  *   colouring applied to groups of elements).
- *     0 (default) = patches, one launch per patch colour;
+ *     0 (default) = patches, one launch per patch colour (with several shots one CTA per
+ *       patch and shot);
  *     1 = element by element, one launch per element colour (the form always used for
- *       several shots and for caller-layout arrays);
- *     2 = patches, all colours in one persistent launch: CTAs take patches in sweep order
+ *       caller-layout arrays);
+ *     2 = patches, all colours in one persistent launch (single shot; several shots use 0):
+ *       CTAs take patches in sweep order
  *       and a patch writes only after every patch of the previous colour has finished (a
  *       bounded wait; if one gives up, the next sem_sync, sem_run or sem_check_finite
  *       returns SEM_ETIMEOUT).
@@ -177,6 +179,24 @@ int sem_destroy(sem_ctx* ctx);
  *   returns SEM_ETIMEOUT; the sweep after that runs normally. Sweeps replayed from a
  *   captured time step are not affected. */
 #define SEM_OPT_SWEEP_STALL_TEST 4
+/*   SEM_OPT_FUSED_NEWMARK (takes effect at once; used with SEM_OPT_ASSEMBLY 0): 2 (default)
+ *   = 1 for a single shot, 0 for several (where the separate pass over the shot-innermost
+ *   fields measures faster); 1 = time steps run the Newmark update (Sec. I) inside the force
+ *   sweep: the patch that touches a node last in the sweep adds the step's point sources to
+ *   the node's complete force and runs the corrector of step n fused with the predictor of
+ *   step n+1 there, so a
+ *   step is one receiver-sampling launch plus the sweep, with no separate pass over the
+ *   nodes; sem_step / sem_run start with a predictor pass and end with a sweep that runs the
+ *   corrector alone, so the state is complete between calls. 0 = separate Newmark passes
+ *   (one fused corrector/predictor pass per step; the state between calls is completed on
+ *   demand). Both give bitwise equal wavefields and seismograms. */
+#define SEM_OPT_FUSED_NEWMARK 6
+/*   SEM_OPT_SHOT_PAIRS (takes effect at once; several shots, SEM_OPT_ASSEMBLY 0): 1 (default)
+ *   = each CTA of the patch sweep takes one patch for two shots, every thread carrying both
+ *   shots as float32 pairs (one packed fma for both; each geometry and modulus value read
+ *   once for both); 0 = one CTA per patch and shot. The same arithmetic per shot; results
+ *   differ only by the rounding order of a few sums. */
+#define SEM_OPT_SHOT_PAIRS 7
 int sem_set_option(sem_ctx* ctx, int option, long long value);
 
 /* Set the mesh (Sec. II-B: hexahedral elements mapped to the reference cube, the
@@ -388,6 +408,15 @@ int sem_adjoint_segment(sem_ctx* ctx, int count, const float* G_dev, const float
  * chosen form in *choice_out (may be NULL). Reads u, writes scratch only (completes a
  * pending state first). Synchronous. Requires mesh, material and dt. */
 int sem_autotune(sem_ctx* ctx, int reps, double* ms_out, int* choice_out);
+
+/* Profile nsteps time steps (Sec. I, IV-C), launched one by one with CUDA events on the
+ * context's stream around each step's force sweep: ms_out[0] = mean milliseconds of the
+ * sweep (all of its colour launches; with SEM_OPT_FUSED_NEWMARK the Newmark update and the
+ * sources included), ms_out[1] = mean milliseconds per step of everything else (receiver
+ * sampling, separate Newmark passes, the predictor that starts a run). The state advances
+ * as with sem_step (same results); no seismogram is recorded. Blocks until the steps are
+ * done. SEM_EINVAL if nsteps < 1 or ms_out is NULL. */
+int sem_profile_steps(sem_ctx* ctx, int nsteps, double* ms_out);
 
 /* Groups: several contexts on one GPU (different meshes, orders, shot counts) stepped
  * together. sem_group_step advances every context nsteps steps (no seismograms): one eager

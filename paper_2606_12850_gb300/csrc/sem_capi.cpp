@@ -44,6 +44,11 @@ struct sem_ctx {
   std::vector<int> pcolor_off;      // patch ranges, one per patch colour
   int npatch = 0, pmax_nodes = 0, ptables = 0;
   int stall_test = 0;               // SEM_OPT_SWEEP_STALL_TEST (one-shot)
+  int fuse_newmark = 2;             // SEM_OPT_FUSED_NEWMARK: Newmark update in the patch sweep
+                                    // (1 on, 0 off, 2 on for a single shot)
+  int shot_pairs = 1;               // SEM_OPT_SHOT_PAIRS: patch CTAs per shot pair (1) or shot (0)
+  std::vector<PatchDesc> pdesc;     // host copy of the patch descriptors
+  std::vector<int> last_patch;      // internal node -> the patch that touches it last
   int assembly = 0;                 // SEM_OPT_ASSEMBLY: 0 patches, one launch per colour,
                                     // 1 elements, 2 persistent patch sweep, 3 atomic ablation
   int slabs = 1;                    // spatial slabs of the sweep order
@@ -68,6 +73,7 @@ struct sem_ctx {
   uint16_t* d_pwords = nullptr;   // patch tables: shared patch node -> its first point's ibool word
   int* d_pcolor_end = nullptr;    // per patch colour, the end of its patch range
   SweepSync* d_sync = nullptr;    // counters of the persistent sweep
+  PatchSrc* d_psrc = nullptr;     // point sources by the patch that touches their node last
   float *d_u = nullptr, *d_v = nullptr, *d_a = nullptr, *d_minv = nullptr;
   float* d_f = nullptr;           // scratch force buffer for sem_energy
   float *d_lam = nullptr, *d_lam_old = nullptr, *d_lamF = nullptr;  // adjoint fields [nglob][4]
@@ -97,6 +103,7 @@ struct sem_ctx {
   long long steps = 0;
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
+  bool graph_fused = false;           // the graph holds steps of the fused sweep
   unsigned long long generation = 0;  // bumped whenever launches captured in graphs go stale
   int variant = 0;                    // force-kernel contraction form (sem_autotune)
 };
@@ -143,7 +150,7 @@ int dev_alloc(sem_ctx* c, T** p, size_t count) {
 }
 
 void free_device(sem_ctx* c) {
-  void* ptrs[] = {c->d_rec, c->d_order, c->d_elist, c->d_perm, c->d_node_new, c->d_pdesc, c->d_pslots, c->d_pwords, c->d_pcolor_end, c->d_sync, c->d_u, c->d_v,
+  void* ptrs[] = {c->d_rec, c->d_order, c->d_elist, c->d_perm, c->d_node_new, c->d_pdesc, c->d_pslots, c->d_pwords, c->d_pcolor_end, c->d_sync, c->d_psrc, c->d_u, c->d_v,
                   c->d_a, c->d_minv, c->d_f, c->d_partials, c->d_lam, c->d_lam_old, c->d_lamF, c->d_grad,
                   c->d_grad32, c->d_rnode, c->d_roff, c->d_rlist,
                   c->d_ctl, c->d_src_node, c->d_src_shot, c->d_src_force, c->d_rec_node};
@@ -159,6 +166,7 @@ void free_device(sem_ctx* c) {
   c->d_pwords = nullptr;
   c->d_pcolor_end = nullptr;
   c->d_sync = nullptr;
+  c->d_psrc = nullptr;
   c->d_u = c->d_v = c->d_a = c->d_minv = c->d_f = nullptr;
   c->d_lam = c->d_lam_old = c->d_lamF = nullptr;
   c->d_grad = nullptr;
@@ -216,9 +224,13 @@ int set_device(sem_ctx* c) {
 // per patch and shot; patches of a colour share no node). Otherwise (caller arrays, or
 // SEM_OPT_ASSEMBLY = 1) the element kernel walks the element list slab by slab and, inside a
 // slab, colour by colour: a launch holds elements of one colour only.
-int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int shots) {
+// With nm (mode 1 or 2; only on the per-colour patch path, see fused_sweep) the sweep also
+// runs the Newmark update of every node at the patch that touches it last.
+int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int shots,
+                      const SweepNewmark* nm = nullptr) {
   if ((c->assembly == 0 || c->assembly == 2) && node_stride == kNodeStride && c->npatch > 0) {
     PatchLaunch P{};
+    if (nm) P.nm = *nm;
     P.rec = c->d_rec;
     P.desc = c->d_pdesc;
     P.slots = c->d_pslots;
@@ -227,8 +239,9 @@ int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int
     P.f = f;
     P.variant = c->variant;
     P.shots = shots;
+    P.pairs = c->shot_pairs;
     const int npc = static_cast<int>(c->pcolor_off.size()) - 1;
-    if (c->assembly == 2 && shots == 1 && npc <= kMaxSweepColors) {
+    if (c->assembly == 2 && shots == 1 && npc <= kMaxSweepColors && P.nm.mode == 0) {
       P.sync = c->d_sync;
       P.color_end = c->d_pcolor_end;
       P.npatch = c->npatch;
@@ -275,6 +288,45 @@ int forces_all_colors(sem_ctx* c, const float* u, float* f, int node_stride, int
   return SEM_OK;
 }
 
+// Whether time steps run the fused sweep: the per-colour patch sweep (SEM_OPT_ASSEMBLY 0)
+// with SEM_OPT_FUSED_NEWMARK on (by default for a single shot only: with several shots the
+// separate pass over the [nglob][S][4] fields is faster on GB300, 48^3 at NGLL 5 with 32
+// shots: 11.8 ms per step against 13.1 ms).
+bool fused_sweep(const sem_ctx* c) {
+  return (c->fuse_newmark == 1 || (c->fuse_newmark == 2 && c->shots == 1)) && c->assembly == 0 && c->npatch > 0;
+}
+
+SweepNewmark sweep_newmark(const sem_ctx* c, int mode) {
+  SweepNewmark nm{};
+  nm.mode = mode;
+  nm.u = c->d_u;
+  nm.v = c->d_v;
+  nm.a = c->d_a;
+  nm.minv = c->d_minv;
+  nm.src = c->d_psrc;
+  nm.step = &c->d_ctl->step;
+  nm.f0 = c->f0;
+  nm.t0 = c->t0;
+  nm.dtd = c->dt;
+  nm.dt = static_cast<float>(c->dt);
+  nm.hdt = static_cast<float>(0.5 * c->dt);
+  nm.hdt2 = static_cast<float>(0.5 * c->dt * c->dt);
+  return nm;
+}
+
+// One step of the fused sweep from u_{n+1} (predicted) and the half-step velocity: the
+// receivers sample u_{n+1} and the step counter advances to n+1, then the sweep assembles
+// the forces and, at each node's last touch, adds the step's point sources and runs the
+// corrector of step n fused with the predictor of step n+1 (mode 1), or the corrector alone
+// (mode 2, the last step of a run: the state is complete afterwards).
+int enqueue_fused_step(sem_ctx* c, int mode) {
+  DevProblem p = problem(c);
+  p.nsrc = 0;  // the sweep adds the sources
+  SEM_LAUNCH(c, launch_sources_record(p, c->stream));
+  const SweepNewmark nm = sweep_newmark(c, mode);
+  return forces_all_colors(c, c->d_u, c->d_a, kNodeStride, c->shots, &nm);
+}
+
 // One time step in the "pending" representation (a holds M a_raw of the previous step, v
 // the half-step velocity): corrector(n-1) fused with predictor(n), forces, sources,
 // receivers. The first step from a complete state uses the predictor alone.
@@ -295,9 +347,10 @@ int enqueue_first_step(sem_ctx* c) { return enqueue_step(c, true); }
 int build_graph(sem_ctx* c) {
   drop_graph(c);
   cudaGraph_t g = nullptr;
+  const bool fused = fused_sweep(c);
   SEM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   int r = SEM_OK;
-  for (int s = 0; s < kStepsPerGraph && r == SEM_OK; ++s) r = enqueue_pending_step(c);
+  for (int s = 0; s < kStepsPerGraph && r == SEM_OK; ++s) r = fused ? enqueue_fused_step(c, 1) : enqueue_pending_step(c);
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (r != SEM_OK) {
     if (g) cudaGraphDestroy(g);
@@ -308,7 +361,25 @@ int build_graph(sem_ctx* c) {
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
   c->graph_valid = true;
+  c->graph_fused = fused;
   return SEM_OK;
+}
+
+int finish_state(sem_ctx* c);
+
+// nsteps steps of the fused sweep from a complete state, which they leave complete: the
+// predictor, nsteps - 1 steps of mode 1 (in graphs of kStepsPerGraph steps), one of mode 2.
+int advance_fused(sem_ctx* c, int nsteps) {
+  int r = finish_state(c);  // a pending state left by steps of another assembly
+  if (r) return r;
+  SEM_LAUNCH(c, launch_predictor(problem(c), c->stream));
+  int left = nsteps - 1;
+  if (left >= kStepsPerGraph && (!c->graph_valid || !c->graph_fused))
+    if ((r = build_graph(c))) return r;
+  for (; left >= kStepsPerGraph; left -= kStepsPerGraph) SEM_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+  for (; left > 0; --left)
+    if ((r = enqueue_fused_step(c, 1))) return r;
+  return enqueue_fused_step(c, 2);
 }
 
 int check_ready(sem_ctx* c) {
@@ -319,19 +390,26 @@ int check_ready(sem_ctx* c) {
   return SEM_OK;
 }
 
-int advance(sem_ctx* c, int nsteps, float* seis_dev) {
+// nsteps time steps; fused false keeps the separate Newmark passes (the state is then left
+// pending), as the group step needs.
+int advance(sem_ctx* c, int nsteps, float* seis_dev, bool fused = true) {
   int r = check_ready(c);
   if (r) return r;
   if (nsteps < 0) return fail(c, SEM_EINVAL, "nsteps must be >= 0");
   if ((r = set_device(c))) return r;
   SEM_LAUNCH(c, launch_set_ctl(c->d_ctl, c->steps, seis_dev ? nsteps : 0, seis_dev, c->stream));
+  if (fused && fused_sweep(c)) {
+    if (nsteps > 0 && (r = advance_fused(c, nsteps))) return r;
+    c->steps += nsteps;
+    return SEM_OK;
+  }
   int left = nsteps;
   if (left > 0 && !c->pending) {
     if ((r = enqueue_first_step(c))) return r;
     c->pending = true;
     --left;
   }
-  if (left >= kStepsPerGraph && !c->graph_valid)
+  if (left >= kStepsPerGraph && (!c->graph_valid || c->graph_fused))
     if ((r = build_graph(c))) return r;
   while (left >= kStepsPerGraph) {
     SEM_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
@@ -604,6 +682,16 @@ int sem_set_option(sem_ctx* c, int option, long long value) {
       if (value < 0 || value > 1) return fail(c, SEM_EINVAL, "stall test must be 0 or 1");
       c->stall_test = static_cast<int>(value);
       return SEM_OK;
+    case SEM_OPT_SHOT_PAIRS:
+      if (value < 0 || value > 1) return fail(c, SEM_EINVAL, "shot pairs must be 0 or 1");
+      c->shot_pairs = static_cast<int>(value);
+      drop_graph(c);
+      return SEM_OK;
+    case SEM_OPT_FUSED_NEWMARK:
+      if (value < 0 || value > 2) return fail(c, SEM_EINVAL, "fused Newmark must be 0, 1 or 2");
+      c->fuse_newmark = static_cast<int>(value);
+      drop_graph(c);
+      return SEM_OK;
     case SEM_OPT_ASSEMBLY:
       if (value < 0 || value > 3)
         return fail(c, SEM_EINVAL,
@@ -813,6 +901,11 @@ static int set_mesh_impl(sem_ctx* c, int nspec, int nglob, const int32_t* ibool,
     wd |= bit;
     std::memcpy(&r[kIbool * np + pp], &wd, sizeof(uint32_t));
   };
+  // the patch that touches each node last in the sweep (patches are in sweep order); its
+  // local points at the node carry kPatchLastBit
+  std::vector<int> last_patch(nglob, -1);
+  for (int P = 0; P < plan.npatch; ++P)
+    for (int k = plan.node_off[P]; k < plan.node_off[P + 1]; ++k) last_patch[plan.nodes[k] & ~kFirstTouchBit] = P;
   for (int P = 0; P < plan.npatch; ++P) {
     PatchDesc& d = pdesc[P];
     const int t = plan.table_of[P];
@@ -821,7 +914,11 @@ static int set_mesh_impl(sem_ctx* c, int nspec, int nglob, const int32_t* ibool,
     d.nshared = plan.tab_nshared[t];
     d.slot_off = plan.tab_csr_off[t];
     d.word_off = word_off[t];
-    d.pad0 = d.pad1 = d.pad2 = 0;
+    d.src_off = d.nsrc = d.pad = 0;
+    const uint16_t* lid = plan.lid.data() + plan.tab_lid_off[t];
+    for (int q = 0; q < d.nelem * np; ++q)
+      if (last_patch[plan.nodes[plan.node_off[P] + lid[q]] & ~kFirstTouchBit] == P)
+        flag_word(d.slot0 + q / np, q % np, kPatchLastBit);
     const int nnode = plan.node_off[P + 1] - plan.node_off[P];
     for (int k = 0; k < nnode; ++k) {
       if (!(plan.nodes[plan.node_off[P] + k] & kFirstTouchBit)) continue;
@@ -832,6 +929,9 @@ static int set_mesh_impl(sem_ctx* c, int nspec, int nglob, const int32_t* ibool,
     for (int q = 0; q < d.nelem * np; ++q)
       if ((ex[q / 32] >> (q % 32)) & 1u) flag_word(d.slot0 + q / np, q % np, kAloneBit);
   }
+  c->last_patch.assign(nglob, -1);
+  for (int g = 0; g < nglob; ++g) c->last_patch[plan.node_new[g]] = last_patch[g];
+  c->pdesc = pdesc;
   c->pcolor_off = plan.color_off;
   c->npatch = plan.npatch;
   c->pmax_nodes = plan.max_nodes;
@@ -1056,6 +1156,35 @@ int sem_locate_nodes(sem_ctx* c, int npts, const double* xyz, const double* surf
   return SEM_OK;
 }
 
+// The point sources of the fused sweep: entry s (internal node, shot, force) goes to the patch
+// that touches its node last; the descriptors name each patch's range.
+static int set_patch_sources(sem_ctx* c, const std::vector<int>& nodes, const std::vector<int>& shots,
+                             const std::vector<double>& forces) {
+  if (c->npatch <= 0) return SEM_OK;
+  std::vector<std::pair<int, int>> by_patch;  // (patch, entry), in entry order within a patch
+  for (size_t s = 0; s < nodes.size(); ++s) by_patch.emplace_back(c->last_patch[nodes[s]], static_cast<int>(s));
+  std::stable_sort(by_patch.begin(), by_patch.end(),
+                   [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first < y.first; });
+  std::vector<PatchSrc> list(by_patch.size());
+  for (PatchDesc& d : c->pdesc) d.src_off = d.nsrc = 0;
+  for (size_t k = 0; k < by_patch.size(); ++k) {
+    const int P = by_patch[k].first, s = by_patch[k].second;
+    PatchSrc& e = list[k];
+    e.node = nodes[s];
+    e.shot = shots[s];
+    for (int d = 0; d < 3; ++d) e.f[d] = forces[3 * static_cast<size_t>(s) + d];
+    PatchDesc& d = c->pdesc[P];
+    if (d.nsrc == 0) d.src_off = static_cast<int>(k);
+    ++d.nsrc;
+  }
+  int r = dev_alloc(c, &c->d_psrc, list.size());
+  if (r) return r;
+  if (!list.empty())
+    SEM_CUDA(c, cudaMemcpy(c->d_psrc, list.data(), list.size() * sizeof(PatchSrc), cudaMemcpyHostToDevice));
+  SEM_CUDA(c, cudaMemcpy(c->d_pdesc, c->pdesc.data(), c->pdesc.size() * sizeof(PatchDesc), cudaMemcpyHostToDevice));
+  return SEM_OK;
+}
+
 static int set_sources_impl(sem_ctx* c, int nsrc, const int32_t* shot, const int32_t* node, const double* force,
                             double f0, double t0) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
@@ -1101,6 +1230,7 @@ static int set_sources_impl(sem_ctx* c, int nsrc, const int32_t* shot, const int
     SEM_CUDA(c, cudaMemcpy(c->d_src_shot, shots.data(), shots.size() * sizeof(int), cudaMemcpyHostToDevice));
     SEM_CUDA(c, cudaMemcpy(c->d_src_force, forces.data(), forces.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
+  if ((r = set_patch_sources(c, nodes, shots, forces))) return r;
   c->f0 = f0;
   c->t0 = t0;
   drop_graph(c);
@@ -1238,6 +1368,8 @@ int sem_set_shots(sem_ctx* c, int nshots) {
   c->pending = false;
   c->steps = 0;
   c->nsrc = 0;  // sources name shots: set them again
+  int rs = set_patch_sources(c, {}, {}, {});
+  if (rs) return rs;
   drop_graph(c);
   return SEM_OK;
 }
@@ -1658,6 +1790,66 @@ int sem_adjoint_gradients(sem_ctx* c, double* g_rho, double* g_kappa, double* g_
   return SEM_OK;
 }
 
+int sem_profile_steps(sem_ctx* c, int nsteps, double* ms_out) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (nsteps < 1 || !ms_out) return fail(c, SEM_EINVAL, "sem_profile_steps: nsteps >= 1 and ms_out required");
+  if ((r = set_device(c))) return r;
+  const bool fused = fused_sweep(c);
+  if (fused && (r = finish_state(c))) return r;
+  SEM_LAUNCH(c, launch_set_ctl(c->d_ctl, c->steps, 0, nullptr, c->stream));
+  std::vector<cudaEvent_t> ev(2 * static_cast<size_t>(nsteps) + 2, nullptr);
+  int rc = SEM_OK;
+  for (cudaEvent_t& e : ev)
+    if (rc == SEM_OK && cudaEventCreate(&e) != cudaSuccess) rc = fail(c, SEM_ECUDA, "cudaEventCreate");
+  auto mark = [&](size_t k) {
+    if (rc == SEM_OK && cudaEventRecord(ev[k], c->stream) != cudaSuccess) rc = fail(c, SEM_ECUDA, "cudaEventRecord");
+  };
+  // event 0: the start, 1 + 2s: before step s's force sweep, 2 + 2s: after it, the last: the end
+  const DevProblem p = problem(c);
+  mark(0);
+  if (rc == SEM_OK && fused) rc = launch_predictor(p, c->stream) ? fail(c, SEM_ECUDA, "predictor launch") : SEM_OK;
+  if (rc == SEM_OK && !fused && !c->pending)
+    rc = launch_predictor(p, c->stream) ? fail(c, SEM_ECUDA, "predictor launch") : SEM_OK;
+  for (int s = 0; s < nsteps && rc == SEM_OK; ++s) {
+    if (fused) {
+      DevProblem q = p;
+      q.nsrc = 0;
+      if (launch_sources_record(q, c->stream)) rc = fail(c, SEM_ECUDA, "receiver launch");
+      mark(1 + 2 * s);
+      const SweepNewmark nm = sweep_newmark(c, s + 1 < nsteps ? 1 : 2);
+      if (rc == SEM_OK) rc = forces_all_colors(c, c->d_u, c->d_a, kNodeStride, c->shots, &nm);
+      mark(2 + 2 * s);
+    } else {
+      if (s > 0 || c->pending)
+        if (launch_fused_newmark(p, c->stream)) rc = fail(c, SEM_ECUDA, "Newmark launch");
+      mark(1 + 2 * s);
+      if (rc == SEM_OK) rc = forces_all_colors(c, c->d_u, c->d_a, kNodeStride, c->shots);
+      mark(2 + 2 * s);
+      if (rc == SEM_OK && launch_sources_record(p, c->stream)) rc = fail(c, SEM_ECUDA, "source launch");
+    }
+  }
+  mark(ev.size() - 1);
+  double sweep = 0.0, total = 0.0;
+  if (rc == SEM_OK && cudaEventSynchronize(ev.back()) != cudaSuccess) rc = fail(c, SEM_ECUDA, "sem_profile_steps");
+  for (int s = 0; s < nsteps && rc == SEM_OK; ++s) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ev[1 + 2 * s], ev[2 + 2 * s]) != cudaSuccess) rc = fail(c, SEM_ECUDA, "event time");
+    sweep += t;
+  }
+  float t = 0.f;
+  if (rc == SEM_OK && cudaEventElapsedTime(&t, ev[0], ev.back()) != cudaSuccess) rc = fail(c, SEM_ECUDA, "event time");
+  total = t;
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  if (rc != SEM_OK) return rc;
+  if (!fused) c->pending = true;
+  c->steps += nsteps;
+  ms_out[0] = sweep / nsteps;
+  ms_out[1] = (total - sweep) / nsteps;
+  return SEM_OK;
+}
+
 int sem_autotune(sem_ctx* c, int reps, double* ms_out, int* choice_out) {
   int r = check_ready(c);
   if (r) return r;
@@ -1824,7 +2016,7 @@ int sem_group_step(sem_group* g, int nsteps) {
     sem_ctx* c = g->ctx[i];
     int r = check_ready(c);
     if (r) return group_fail(g, r, "context " + std::to_string(i) + ": " + c->err);
-    if ((r = advance(c, 1, nullptr))) return group_fail(g, r, "context " + std::to_string(i) + ": " + c->err);
+    if ((r = advance(c, 1, nullptr, false))) return group_fail(g, r, "context " + std::to_string(i) + ": " + c->err);
     if (cudaEventRecord(g->ev[1 + i], c->stream) != cudaSuccess || cudaStreamWaitEvent(g->stream, g->ev[1 + i], 0) != cudaSuccess)
       return group_fail(g, SEM_ECUDA, "ordering the group after its contexts");
   }

@@ -108,6 +108,9 @@ struct ForceCfg {
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void prefetch_l2_line(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ void wait_prerequisite_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
   unsigned int v;
@@ -633,10 +636,12 @@ __device__ __forceinline__ size_t node_slot(uint32_t w, int S, int shot) {
 // Phases 1-3 of one patch for the calling thread's team: gather through the records' ibool
 // words (GB points per thread in flight; the shared-memory copy of each word keeps the node,
 // the patch first-touch flag and kAloneBit), then the element forces.
-template <int N, bool LO, bool MS = false>
+// (NM: the half-step velocity and 1/M of the nodes the patch touches last are prefetched into
+// L2 as their points are gathered, for the Newmark update at the end of the patch.)
+template <int N, bool LO, bool MS = false, bool NM = false>
 __device__ __forceinline__ void patch_gather_compute(const PatchDesc& d, const float* __restrict__ rec,
                                                      const float4* __restrict__ u, float* wsb, bool u_from_l2,
-                                                     int S = 1, int shot = 0) {
+                                                     int S = 1, int shot = 0, const SweepNewmark* nm = nullptr) {
   using C = PatchCfg<N>;
   constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, REC = C::REC;
   const int team = threadIdx.x / TEAM;
@@ -652,6 +657,14 @@ __device__ __forceinline__ void patch_gather_compute(const PatchDesc& d, const f
       const int idx = base + r * TEAM;
       const int le = idx / NP;
       w[r] = idx < ne * NP ? __float_as_uint(__ldg(trec + static_cast<size_t>(le) * REC + (idx - le * NP))) : 0u;
+    }
+    if constexpr (NM) {
+#pragma unroll
+      for (int r = 0; r < GB; ++r)
+        if (w[r] & kPatchLastBit) {
+          prefetch_l2_line(reinterpret_cast<const float4*>(nm->v) + node_slot<MS>(w[r], S, shot));
+          prefetch_l2_line(nm->minv + (w[r] & kNodeMask));
+        }
     }
     float4 q[GB];
     if (u_from_l2) {
@@ -692,20 +705,77 @@ __device__ __forceinline__ float4 load_f(const float4* p) {
     return *p;
 }
 
+// Point sources of the step at a node the patch touches last (Sec. V-C): the Ricker wavelet
+// at t_{n+1} = step dt (the counter, advanced before the sweep, read from L2) times each
+// force, added to the node's complete force in the order the entries are listed.
+__device__ __forceinline__ void add_point_sources(const PatchDesc& d, const SweepNewmark& nm, uint32_t node, int shot,
+                                                  float& fx, float& fy, float& fz) {
+  for (int i = 0; i < d.nsrc; ++i) {
+    const PatchSrc& s = nm.src[d.src_off + i];
+    if (s.node != static_cast<int>(node) || s.shot != shot) continue;
+    const long long n = __ldcg(nm.step);
+    const double tau = static_cast<double>(n) * nm.dtd - nm.t0;
+    const double x = M_PI * nm.f0 * tau;
+    const double aa = x * x;
+    const double R = (1.0 - 2.0 * aa) * exp(-aa);
+    fx += static_cast<float>(s.f[0] * R);
+    fy += static_cast<float>(s.f[1] * R);
+    fz += static_cast<float>(s.f[2] * R);
+  }
+}
+
+// The inputs of a node's Newmark update, loaded with the previous force values so that all
+// of a thread's loads are in flight together: 1/M, the half-step velocity and (mode 1) the
+// displacement.
+struct NodeState {
+  float m;
+  float4 v, u;
+};
+template <bool MS>
+__device__ __forceinline__ void load_node_state(const SweepNewmark& nm, uint32_t w, int S, int shot, NodeState& st) {
+  const size_t g = node_slot<MS>(w, S, shot);
+  st.m = __ldg(nm.minv + (w & kNodeMask));
+  st.v = __ldcg(reinterpret_cast<const float4*>(nm.v) + g);
+  if (nm.mode == 1) st.u = __ldcg(reinterpret_cast<const float4*>(nm.u) + g);
+}
+
+// Newmark update of a node whose complete force (fx, fy, fz) is known (mode 1 or 2):
+//   a = M^-1 f ; v = v_half + dt/2 a ; mode 1: u <- u + dt v + dt^2/2 a, v_half <- v + dt/2 a ;
+//   mode 2: v and a stored.
+template <bool MS>
+__device__ __forceinline__ void newmark_node(const SweepNewmark& nm, uint32_t w, int S, int shot, const NodeState& st,
+                                             float fx, float fy, float fz) {
+  const size_t g = node_slot<MS>(w, S, shot);
+  const float ax = fx * st.m, ay = fy * st.m, az = fz * st.m;
+  const float vx = st.v.x + nm.hdt * ax, vy = st.v.y + nm.hdt * ay, vz = st.v.z + nm.hdt * az;
+  if (nm.mode == 1) {
+    reinterpret_cast<float4*>(nm.u)[g] = make_float4((st.u.x + nm.dt * vx) + nm.hdt2 * ax,
+                                                     (st.u.y + nm.dt * vy) + nm.hdt2 * ay,
+                                                     (st.u.z + nm.dt * vz) + nm.hdt2 * az, 0.f);
+    reinterpret_cast<float4*>(nm.v)[g] = make_float4(vx + nm.hdt * ax, vy + nm.hdt * ay, vz + nm.hdt * az, 0.f);
+  } else {
+    reinterpret_cast<float4*>(nm.v)[g] = make_float4(vx, vy, vz, 0.f);
+    reinterpret_cast<float4*>(nm.a)[g] = make_float4(ax, ay, az, 0.f);
+  }
+}
+
 // Phase 4a for the calling thread's team: the forces of its points that are alone at their
-// patch node added to the node (stored at its first touch).
-template <int N, bool COHERENT, bool MS = false>
+// patch node added to the node (stored at its first touch; with a Newmark mode, used for the
+// node's update at its last touch and not stored).
+template <int N, bool COHERENT, bool MS = false, bool NM = false>
 __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __restrict__ f, const float* wsb,
-                                                  int S = 1, int shot = 0) {
+                                                  const SweepNewmark& nm, int S = 1, int shot = 0) {
   using C = PatchCfg<N>;
-  constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, GB = 4;
+  constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, GB = NM ? 2 : 4;
   const int team = threadIdx.x / TEAM;
   const int tl = threadIdx.x - team * TEAM;
   const int ne = min(E, d.nelem - team * E);
   const float* ts = wsb + team * C::TS;
+  constexpr uint32_t last_bit = NM ? kPatchLastBit : 0u;
   for (int base = tl; base < ne * NP; base += GB * TEAM) {
     uint32_t w[GB];
     float4 prev[GB];
+    NodeState st[GB];
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
       const int idx = base + r * TEAM;
@@ -715,6 +785,7 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
         const int e = idx / NP;
         w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
         if ((w[r] & kAloneBit) && !(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + node_slot<MS>(w[r], S, shot));
+        if ((w[r] & kAloneBit) && (w[r] & last_bit)) load_node_state<MS>(nm, w[r], S, shot, st[r]);
       }
     }
 #pragma unroll
@@ -723,7 +794,13 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
       if (w[r] & kAloneBit) {
         const int e = idx / NP;
         const float* src = ts + e * ES + 3 * (idx - e * NP);
-        f[node_slot<MS>(w[r], S, shot)] = make_float4(src[0] + prev[r].x, src[1] + prev[r].y, src[2] + prev[r].z, 0.f);
+        float fx = src[0] + prev[r].x, fy = src[1] + prev[r].y, fz = src[2] + prev[r].z;
+        if (w[r] & last_bit) {
+          if (d.nsrc) add_point_sources(d, nm, w[r] & kNodeMask, shot, fx, fy, fz);
+          newmark_node<MS>(nm, w[r], S, shot, st[r], fx, fy, fz);
+        } else {
+          f[node_slot<MS>(w[r], S, shot)] = make_float4(fx, fy, fz, 0.f);
+        }
       }
     }
   }
@@ -731,20 +808,23 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
 
 // Phase 4b over the CTA: per shared patch node, the sum of its local points' forces in table
 // order (its slots, shared-memory offsets of those forces, read as one 16-byte word), then
-// one store (first touch) or one read-modify-write; the previous values of GB nodes are
-// loaded before any is written.
-template <int N, bool COHERENT, bool MS = false>
+// one store (first touch) or one read-modify-write, or at the node's last touch (with a
+// Newmark mode) its update; the previous values of GB nodes are loaded before any is written.
+template <int N, bool COHERENT, bool MS = false, bool NM = false>
 __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uint16_t* __restrict__ slot_tab,
                                                    const uint16_t* __restrict__ word_tab, float4* __restrict__ f,
-                                                   const float* wsb, int S = 1, int shot = 0) {
+                                                   const float* wsb, const SweepNewmark& nm, int S = 1,
+                                                   int shot = 0) {
   using C = PatchCfg<N>;
-  constexpr int T = C::T, GB = 4;
+  constexpr int T = C::T, GB = NM ? 2 : 4;
   const uint4* __restrict__ slots = reinterpret_cast<const uint4*>(slot_tab + d.slot_off);
   const uint16_t* __restrict__ words = word_tab + d.word_off;
+  constexpr uint32_t last_bit = NM ? kPatchLastBit : 0u;
   for (int base = threadIdx.x; base < d.nshared; base += GB * T) {
     uint4 sl[GB];
     uint32_t w[GB];
     float4 prev[GB];
+    NodeState st[GB];
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
       const int t = base + r * T;
@@ -756,6 +836,7 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
     for (int r = 0; r < GB; ++r) {
       prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (!(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + node_slot<MS>(w[r], S, shot));
+      if (w[r] & last_bit) load_node_state<MS>(nm, w[r], S, shot, st[r]);
     }
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
@@ -782,7 +863,13 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
           if (!chain) break;
           g4 = __ldg(slots + (chain & ~static_cast<uint32_t>(kPatchChain)));
         }
-        f[node_slot<MS>(w[r], S, shot)] = make_float4(prev[r].x + sx, prev[r].y + sy, prev[r].z + sz, 0.f);
+        float fx = prev[r].x + sx, fy = prev[r].y + sy, fz = prev[r].z + sz;
+        if (w[r] & last_bit) {
+          if (d.nsrc) add_point_sources(d, nm, w[r] & kNodeMask, shot, fx, fy, fz);
+          newmark_node<MS>(nm, w[r], S, shot, st[r], fx, fy, fz);
+        } else {
+          f[node_slot<MS>(w[r], S, shot)] = make_float4(fx, fy, fz, 0.f);
+        }
       }
     }
   }
@@ -798,11 +885,12 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
 // With S shots (MS true) the fields are [nglob][S][4] and CTA b takes patch p0 + b / S for
 // shot b % S: consecutive CTAs take the shots of one patch, so its records come from DRAM
 // once (the first shot's prefetch) and from L2 for the others.
-template <int N, bool LO, bool MS>
+template <int N, bool LO, bool MS, bool NM>
 __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
     patch_forces_kernel(const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
                         const uint16_t* __restrict__ slot_tab, const uint16_t* __restrict__ word_tab,
-                        const float4* __restrict__ u, float4* __restrict__ f, int p0, int S_arg) {
+                        const float4* __restrict__ u, float4* __restrict__ f, int p0, int S_arg,
+                        const SweepNewmark nm) {
   using C = PatchCfg<N>;
   extern __shared__ float4 smem4[];
   float* wsb = reinterpret_cast<float*>(smem4);
@@ -817,11 +905,437 @@ __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
   allow_dependent_grid();
   // before the wait, u comes from L2 (the coherence point), never from a line this SM's L1
   // may hold from before the grid that wrote u
-  patch_gather_compute<N, LO, MS>(d, rec, u, wsb, p0 != 0, S, shot);
+  patch_gather_compute<N, LO, MS, NM>(d, rec, u, wsb, p0 != 0, S, shot, &nm);
   if (p0 != 0) wait_prerequisite_grid();  // the previous colour's writes to f
-  patch_write_alone<N, false, MS>(d, f, wsb, S, shot);  // no wait for the other teams
+  patch_write_alone<N, false, MS, NM>(d, f, wsb, nm, S, shot);  // no wait for the other teams
   __syncthreads();
-  patch_write_shared<N, false, MS>(d, slot_tab, word_tab, f, wsb, S, shot);
+  patch_write_shared<N, false, MS, NM>(d, slot_tab, word_tab, f, wsb, nm, S, shot);
+}
+
+// ---------------------------------------------------------------------------------------
+// Shot pairs. With several shots of one model (fields [nglob][S][4]), a CTA takes one patch
+// for two shots: every thread carries both shots' values as float32 pairs (shot 2k in .x,
+// 2k + 1 in .y), so one packed fma serves both shots, and every geometry and modulus value
+// read from the records serves both. The workspace is the single-shot layout with every
+// float widened to a pair (an element at twice its single-shot offset; u/F, eta and zeta
+// values as [NP][3] pairs, the ibool words at stride 2), so the patch tables' shared-memory
+// offsets apply doubled. Line owners throughout (Sec. II-B phases as in the single-shot core).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 bcast2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+
+// Phases 2-3 of one team's elements for a shot pair (ES2 floats per element workspace).
+template <int N, int KIND, int TEAM, int ES2, class RecOf>
+__device__ __forceinline__ void team_element_forces_pair(float* ts2, int tl, int ne, int team, RecOf rec_of) {
+  constexpr int NP = N * N * N, NL = N * N;
+  const float* __restrict__ W = c_w;
+  const int le = tl / NL;
+  const int line = tl - le * NL;
+  const int a = line % N;
+  const int b = line / N;
+  const bool active = le < ne;
+  float2* su = reinterpret_cast<float2*>(ts2 + (active ? le : 0) * ES2);  // u, then F: [NP][3]
+  float2* se = su + 3 * NP;                                                 // eta values [NP][3]
+  float2* sz = su + 6 * NP;                                                 // zeta values [NP][3]
+  const float* __restrict__ r = rec_of(active ? le : 0);
+
+  // 2a. eta derivatives along the eta-line (i, k) = (a, b), zeta derivatives along the
+  //     zeta-line (i, j) = (a, b), component by component
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float2 ve[N], vz[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        ve[l] = su[3 * (a + N * (l + N * b)) + c];
+        vz[l] = su[3 * (a + N * (b + N * l)) + c];
+      }
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        float2 de = make_float2(0.f, 0.f), dz = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          de = ffma2(c_h2[m * N + l], ve[l], de);
+          dz = ffma2(c_h2[m * N + l], vz[l], dz);
+        }
+        se[3 * (a + N * (m + N * b)) + c] = de;
+        sz[3 * (a + N * (b + N * m)) + c] = dz;
+      }
+    }
+  }
+  team_sync<KIND, TEAM>(team);
+
+  // 2b. along the xi-line (j, k) = (a, b): xi derivatives, Jacobian map, Hooke stress,
+  //     fluxes (the record values broadcast to both shots); the xi-flux transposed product in
+  //     registers, the eta and zeta fluxes over the derivatives
+  float2 fx[N], fy[N], fz[N];
+  {
+    float2 ux[N], uy[N], uz[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int p = i + N * line;
+      ux[i] = su[3 * p];
+      uy[i] = su[3 * p + 1];
+      uz[i] = su[3 * p + 2];
+      fx[i] = fy[i] = fz[i] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float2 dxi_x = make_float2(0.f, 0.f), dxi_y = dxi_x, dxi_z = dxi_x;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        dxi_x = ffma2(c_h2[i * N + l], ux[l], dxi_x);
+        dxi_y = ffma2(c_h2[i * N + l], uy[l], dxi_y);
+        dxi_z = ffma2(c_h2[i * N + l], uz[l], dxi_z);
+      }
+      const int p3 = 3 * (i + N * line);
+      const float2 det_x = se[p3], det_y = se[p3 + 1], det_z = se[p3 + 2];
+      const float2 dze_x = sz[p3], dze_y = sz[p3 + 1], dze_z = sz[p3 + 2];
+      const int q = i * NL + line;
+      float2 G[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) G[c] = bcast2(active ? __ldg(r + (kG + c) * NP + q) : 0.f);
+      const float kappa = active ? __ldg(r + kJKappa * NP + q) : 0.f;  // J kappa
+      const float mu = active ? __ldg(r + kJMu * NP + q) : 0.f;        // J mu
+
+      const float2 uxx = ffma2(dze_x, G[6], ffma2(det_x, G[3], fmul2(dxi_x, G[0])));
+      const float2 uxy = ffma2(dze_x, G[7], ffma2(det_x, G[4], fmul2(dxi_x, G[1])));
+      const float2 uxz = ffma2(dze_x, G[8], ffma2(det_x, G[5], fmul2(dxi_x, G[2])));
+      const float2 uyx = ffma2(dze_y, G[6], ffma2(det_y, G[3], fmul2(dxi_y, G[0])));
+      const float2 uyy = ffma2(dze_y, G[7], ffma2(det_y, G[4], fmul2(dxi_y, G[1])));
+      const float2 uyz = ffma2(dze_y, G[8], ffma2(det_y, G[5], fmul2(dxi_y, G[2])));
+      const float2 uzx = ffma2(dze_z, G[6], ffma2(det_z, G[3], fmul2(dxi_z, G[0])));
+      const float2 uzy = ffma2(dze_z, G[7], ffma2(det_z, G[4], fmul2(dxi_z, G[1])));
+      const float2 uzz = ffma2(dze_z, G[8], ffma2(det_z, G[5], fmul2(dxi_z, G[2])));
+
+      // J sigma (J kappa and J mu from the record)
+      const float2 lam = bcast2(kappa - (2.f / 3.f) * mu);
+      const float2 mu2 = bcast2(2.f * mu), mu1 = bcast2(mu);
+      const float2 ltr = fmul2(lam, fadd2(fadd2(uxx, uyy), uzz));
+      const float2 sxx = ffma2(mu2, uxx, ltr);
+      const float2 syy = ffma2(mu2, uyy, ltr);
+      const float2 szz = ffma2(mu2, uzz, ltr);
+      const float2 sxy = fmul2(mu1, fadd2(uxy, uyx));
+      const float2 sxz = fmul2(mu1, fadd2(uxz, uzx));
+      const float2 syz = fmul2(mu1, fadd2(uyz, uzy));
+
+      const float2 txi_x = ffma2(sxz, G[2], ffma2(sxy, G[1], fmul2(sxx, G[0])));
+      const float2 txi_y = ffma2(syz, G[2], ffma2(syy, G[1], fmul2(sxy, G[0])));
+      const float2 txi_z = ffma2(szz, G[2], ffma2(syz, G[1], fmul2(sxz, G[0])));
+#pragma unroll
+      for (int ip = 0; ip < N; ++ip) {
+        fx[ip] = ffma2(c_hw2[i * N + ip], txi_x, fx[ip]);
+        fy[ip] = ffma2(c_hw2[i * N + ip], txi_y, fy[ip]);
+        fz[ip] = ffma2(c_hw2[i * N + ip], txi_z, fz[ip]);
+      }
+      if (active) {
+        se[p3] = ffma2(sxz, G[5], ffma2(sxy, G[4], fmul2(sxx, G[3])));
+        se[p3 + 1] = ffma2(syz, G[5], ffma2(syy, G[4], fmul2(sxy, G[3])));
+        se[p3 + 2] = ffma2(szz, G[5], ffma2(syz, G[4], fmul2(sxz, G[3])));
+        sz[p3] = ffma2(sxz, G[8], ffma2(sxy, G[7], fmul2(sxx, G[6])));
+        sz[p3 + 1] = ffma2(syz, G[8], ffma2(syy, G[7], fmul2(sxy, G[6])));
+        sz[p3 + 2] = ffma2(szz, G[8], ffma2(syz, G[7], fmul2(sxz, G[6])));
+      }
+    }
+  }
+  team_sync<KIND, TEAM>(team);
+
+  // 3. eta and zeta transposed products along the eta- and zeta-lines, in place
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float2 ve[N], vz[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        ve[l] = se[3 * (a + N * (l + N * b)) + c];
+        vz[l] = sz[3 * (a + N * (b + N * l)) + c];
+      }
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        float2 te = make_float2(0.f, 0.f), tz = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          te = ffma2(c_hw2[l * N + m], ve[l], te);
+          tz = ffma2(c_hw2[l * N + m], vz[l], tz);
+        }
+        se[3 * (a + N * (m + N * b)) + c] = te;
+        sz[3 * (a + N * (b + N * m)) + c] = tz;
+      }
+    }
+  }
+  team_sync<KIND, TEAM>(team);
+
+  // 3b. element forces along the xi-line into the (now free) u slots
+  if (active) {
+    const float wj = W[a], wk = W[b];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const float wi = W[i];
+      const float2 cjk = bcast2(-(wj * wk)), cik = bcast2(-(wi * wk)), cij = bcast2(-(wi * wj));
+      const int p = 3 * (i + N * line);
+      su[p] = ffma2(cij, sz[p], ffma2(cik, se[p], fmul2(cjk, fx[i])));
+      su[p + 1] = ffma2(cij, sz[p + 1], ffma2(cik, se[p + 1], fmul2(cjk, fy[i])));
+      su[p + 2] = ffma2(cij, sz[p + 2], ffma2(cik, se[p + 2], fmul2(cjk, fz[i])));
+    }
+  }
+  team_sync<KIND, TEAM>(team);
+}
+
+// Points a thread gathers per pass in the pair kernel (all their loads in flight together),
+// lone points and shared nodes it writes per pass (GB300, 48^3 at NGLL 5, 32 shots: a
+// gather batch of 2 beats 4; write batches of 2 beat 1 by 7 %).
+constexpr int kPairGatherBatch = 2;
+constexpr int kPairWriteBatch = 4;
+constexpr int kPairSharedBatch = 2;
+
+// Phases 1-3 of one patch for a shot pair (s0, s0 + 1; the second absent when has1 is false:
+// its lanes then carry a copy of the first, never written back).
+template <int N, bool NM>
+__device__ __forceinline__ void patch_gather_compute_pair(const PatchDesc& d, const float* __restrict__ rec,
+                                                          const float4* __restrict__ u, float* wsb2, bool u_from_l2,
+                                                          int S, int s0, bool has1, const SweepNewmark& nm) {
+  using C = PatchCfg<N>;
+  constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES2 = 2 * C::ES, REC = C::REC, GB = kPairGatherBatch;
+  const int team = threadIdx.x / TEAM;
+  const int tl = threadIdx.x - team * TEAM;
+  const int ne = min(E, d.nelem - team * E);
+  const float* __restrict__ trec = rec + static_cast<size_t>(d.slot0 + team * E) * REC;
+  const int s1 = has1 ? s0 + 1 : s0;
+  float* ts2 = wsb2 + team * 2 * C::TS;
+  for (int base = tl; base < ne * NP; base += GB * TEAM) {
+    uint32_t w[GB];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      const int le = idx / NP;
+      w[r] = idx < ne * NP ? __float_as_uint(__ldg(trec + static_cast<size_t>(le) * REC + (idx - le * NP))) : 0u;
+    }
+    if constexpr (NM) {
+#pragma unroll
+      for (int r = 0; r < GB; ++r)
+        if (w[r] & kPatchLastBit) {
+          prefetch_l2_line(reinterpret_cast<const float4*>(nm.v) + node_slot<true>(w[r], S, s0));
+          prefetch_l2_line(nm.minv + (w[r] & kNodeMask));
+        }
+    }
+    float4 q0[GB], q1[GB];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const float4* pu = u + node_slot<true>(w[r], S, s0);
+      q0[r] = u_from_l2 ? __ldcg(pu) : __ldg(pu);
+      q1[r] = u_from_l2 ? __ldcg(pu + (s1 - s0)) : __ldg(pu + (s1 - s0));
+    }
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      if (idx < ne * NP) {
+        const int le = idx / NP;
+        const int p = idx - le * NP;
+        float* eb2 = ts2 + le * ES2;
+        reinterpret_cast<uint32_t*>(eb2 + 18 * NP)[2 * p] = w[r];
+        float2* pu2 = reinterpret_cast<float2*>(eb2) + 3 * p;
+        pu2[0] = make_float2(q0[r].x, q1[r].x);
+        pu2[1] = make_float2(q0[r].y, q1[r].y);
+        pu2[2] = make_float2(q0[r].z, q1[r].z);
+      }
+    }
+  }
+  if (C::KIND == 2 || ne > 0) {
+    team_sync<C::KIND, TEAM>(team);
+    team_element_forces_pair<N, C::KIND, TEAM, ES2>(ts2, tl, ne, team,
+                                                    [&](int le) { return trec + static_cast<size_t>(le) * REC; });
+  }
+}
+
+// The write of one node for one shot of the pair: stored (first touch), added (later
+// touches), or (NM, last touch) the sources and the Newmark update.
+template <bool NM>
+__device__ __forceinline__ void write_node_shot(const PatchDesc& d, const SweepNewmark& nm, float4* __restrict__ f,
+                                                uint32_t w, int S, int shot, float4 prev, const NodeState& st,
+                                                float fx, float fy, float fz) {
+  fx += prev.x;
+  fy += prev.y;
+  fz += prev.z;
+  if (NM && (w & kPatchLastBit)) {
+    if (d.nsrc) add_point_sources(d, nm, w & kNodeMask, shot, fx, fy, fz);
+    newmark_node<true>(nm, w, S, shot, st, fx, fy, fz);
+  } else {
+    f[node_slot<true>(w, S, shot)] = make_float4(fx, fy, fz, 0.f);
+  }
+}
+
+// Phase 4a for a shot pair (the points alone at their patch node, team by team; the loads
+// of GB points in flight before any is written).
+template <int N, bool NM>
+__device__ __forceinline__ void patch_write_alone_pair(const PatchDesc& d, float4* __restrict__ f, const float* wsb2,
+                                                       const SweepNewmark& nm, int S, int s0, bool has1) {
+  using C = PatchCfg<N>;
+  constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES2 = 2 * C::ES, GB = kPairWriteBatch;
+  const int team = threadIdx.x / TEAM;
+  const int tl = threadIdx.x - team * TEAM;
+  const int ne = min(E, d.nelem - team * E);
+  const float* ts2 = wsb2 + team * 2 * C::TS;
+  const int s1 = has1 ? s0 + 1 : s0;
+  for (int base = tl; base < ne * NP; base += GB * TEAM) {
+    uint32_t w[GB];
+    float4 prev0[GB], prev1[GB];
+    NodeState st0[GB], st1[GB];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      w[r] = 0u;
+      prev0[r] = prev1[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (idx < ne * NP) {
+        const int e = idx / NP;
+        w[r] = reinterpret_cast<const uint32_t*>(ts2 + e * ES2 + 18 * NP)[2 * (idx - e * NP)];
+        if ((w[r] & kAloneBit) && !(w[r] & kPatchFirstBit)) {
+          prev0[r] = load_f<false>(f + node_slot<true>(w[r], S, s0));
+          prev1[r] = load_f<false>(f + node_slot<true>(w[r], S, s1));
+        }
+        if (NM && (w[r] & kAloneBit) && (w[r] & kPatchLastBit)) {
+          load_node_state<true>(nm, w[r], S, s0, st0[r]);
+          load_node_state<true>(nm, w[r], S, s1, st1[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int idx = base + r * TEAM;
+      if (w[r] & kAloneBit) {
+        const int e = idx / NP;
+        const float2* F = reinterpret_cast<const float2*>(ts2 + e * ES2) + 3 * (idx - e * NP);
+        const float2 Fx = F[0], Fy = F[1], Fz = F[2];
+        write_node_shot<NM>(d, nm, f, w[r], S, s0, prev0[r], st0[r], Fx.x, Fy.x, Fz.x);
+        if (has1) write_node_shot<NM>(d, nm, f, w[r], S, s1, prev1[r], st1[r], Fx.y, Fy.y, Fz.y);
+      }
+    }
+  }
+}
+
+// Phase 4b for a shot pair over the CTA (the shared patch nodes, their slots summed as pairs;
+// the loads of GB nodes in flight before any is written).
+template <int N, bool NM>
+__device__ __forceinline__ void patch_write_shared_pair(const PatchDesc& d, const uint16_t* __restrict__ slot_tab,
+                                                        const uint16_t* __restrict__ word_tab, float4* __restrict__ f,
+                                                        const float* wsb2, const SweepNewmark& nm, int S, int s0,
+                                                        bool has1) {
+  using C = PatchCfg<N>;
+  constexpr int T = C::T, GB = kPairSharedBatch;
+  const uint4* __restrict__ slots = reinterpret_cast<const uint4*>(slot_tab + d.slot_off);
+  const uint16_t* __restrict__ words = word_tab + d.word_off;
+  const int s1 = has1 ? s0 + 1 : s0;
+  for (int base = threadIdx.x; base < d.nshared; base += GB * T) {
+    uint4 sl[GB];
+    uint32_t w[GB];
+    float4 prev0[GB], prev1[GB];
+    NodeState st0[GB], st1[GB];
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      const int t = base + r * T;
+      const int tt = t < d.nshared ? t : 0;
+      sl[r] = __ldg(slots + tt);
+      w[r] = t < d.nshared ? reinterpret_cast<const uint32_t*>(wsb2)[2 * static_cast<uint32_t>(__ldg(words + tt))]
+                           : kPatchFirstBit;
+    }
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      prev0[r] = prev1[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!(w[r] & kPatchFirstBit)) {
+        prev0[r] = load_f<false>(f + node_slot<true>(w[r], S, s0));
+        prev1[r] = load_f<false>(f + node_slot<true>(w[r], S, s1));
+      }
+      if (NM && (w[r] & kPatchLastBit)) {
+        load_node_state<true>(nm, w[r], S, s0, st0[r]);
+        load_node_state<true>(nm, w[r], S, s1, st1[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < GB; ++r) {
+      if (base + r * T >= d.nshared) continue;
+      float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx;
+      uint4 g4 = sl[r];
+      while (true) {
+        const uint32_t wd[4] = {g4.x, g4.y, g4.z, g4.w};
+        uint32_t chain = 0;
+#pragma unroll
+        for (int k = 0; k < kPatchSlots; ++k) {
+          const uint32_t q = (wd[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+          if (q == kPatchNoSlot) continue;
+          if (q & kPatchChain) {
+            chain = q;
+            continue;
+          }
+          const float2* F = reinterpret_cast<const float2*>(wsb2 + 2 * q);
+          sx = fadd2(sx, F[0]);
+          sy = fadd2(sy, F[1]);
+          sz = fadd2(sz, F[2]);
+        }
+        if (!chain) break;
+        g4 = __ldg(slots + (chain & ~static_cast<uint32_t>(kPatchChain)));
+      }
+      write_node_shot<NM>(d, nm, f, w[r], S, s0, prev0[r], st0[r], sx.x, sy.x, sz.x);
+      if (has1) write_node_shot<NM>(d, nm, f, w[r], S, s1, prev1[r], st1[r], sx.y, sy.y, sz.y);
+    }
+  }
+}
+
+// Shared memory of the pair kernel and the CTAs per SM it is compiled for.
+template <int N>
+struct PairCfg {
+  static constexpr int SMEM = 2 * PatchCfg<N>::SMEM;
+  static constexpr int FIT = (227 * 1024) / (SMEM + 1024);
+  // at most the CTAs whose register share holds the pair core without large spills (about
+  // 128 registers a thread from NGLL 5 up)
+  static constexpr int CAP = N >= 5 ? 2 : 3;
+  static constexpr int MIN_BLOCKS = FIT < 1 ? 1 : FIT > CAP ? CAP : FIT;
+  static_assert(SMEM <= 227 * 1024, "pair workspace exceeds shared memory");
+};
+
+// One launch per patch colour for S shots: CTA b takes patch p0 + b / ceil(S/2) for the shot
+// pair (2k, 2k + 1), k = b % ceil(S/2) (with odd S the last pair has one shot). The pairs of
+// one patch are consecutive CTAs, so its records come from DRAM once (the first pair's
+// prefetch) and from L2 for the others. Launch order and waits as in patch_forces_kernel.
+template <int N, bool NM>
+__global__ void __launch_bounds__(PatchCfg<N>::T, PairCfg<N>::MIN_BLOCKS)
+    patch_forces_pair_kernel(const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
+                             const uint16_t* __restrict__ slot_tab, const uint16_t* __restrict__ word_tab,
+                             const float4* __restrict__ u, float4* __restrict__ f, int p0, int S,
+                             const SweepNewmark nm) {
+  using C = PatchCfg<N>;
+  extern __shared__ float4 smem4[];
+  float* wsb2 = reinterpret_cast<float*>(smem4);
+  const int SP = (S + 1) / 2;
+  const int P = p0 + static_cast<int>(blockIdx.x) / SP;
+  const int k = static_cast<int>(blockIdx.x) - (P - p0) * SP;
+  const int s0 = 2 * k;
+  const bool has1 = s0 + 1 < S;
+  const PatchDesc d = desc[P];
+  if (k == 0 && threadIdx.x < d.nelem)
+    prefetch_l2(rec + static_cast<size_t>(d.slot0 + threadIdx.x) * C::REC, kForceFields * C::NP * sizeof(float));
+  if (p0 == 0) wait_prerequisite_grid();
+  allow_dependent_grid();
+  patch_gather_compute_pair<N, NM>(d, rec, u, wsb2, p0 != 0, S, s0, has1, nm);
+  if (p0 != 0) wait_prerequisite_grid();
+  patch_write_alone_pair<N, NM>(d, f, wsb2, nm, S, s0, has1);
+  __syncthreads();
+  patch_write_shared_pair<N, NM>(d, slot_tab, word_tab, f, wsb2, nm, S, s0, has1);
 }
 
 // Persistent form: one sweep (all patch colours) in one launch. CTAs take patches in sweep
@@ -881,11 +1395,12 @@ __device__ __noinline__ int sweep_one_patch(int P, const float* __restrict__ rec
   }
   __syncthreads();
   const PatchDesc& d = sh->d;
+  const SweepNewmark none{};  // the persistent sweep assembles forces only
   prefetch_patch_records<N>(rec, desc, sh->next, npatch);
   patch_gather_compute<N, LO>(d, rec, u, wsb, false);
   const int c = sh->color;
   if (sh->ready) {
-    patch_write_alone<N, true>(d, f, wsb);
+    patch_write_alone<N, true>(d, f, wsb, none);
     __syncthreads();
   } else {
     __syncthreads();
@@ -903,9 +1418,9 @@ __device__ __noinline__ int sweep_one_patch(int P, const float* __restrict__ rec
     }
     __syncthreads();  // the wait is over for the CTA
     if (sh->abort) return -1;
-    patch_write_alone<N, true>(d, f, wsb);
+    patch_write_alone<N, true>(d, f, wsb, none);
   }
-  patch_write_shared<N, true>(d, slot_tab, word_tab, f, wsb);
+  patch_write_shared<N, true>(d, slot_tab, word_tab, f, wsb, none);
   __syncthreads();  // all of the patch's writes issued before it counts as done
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1132,10 +1647,10 @@ int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
   return lo ? launch_forces_ms<false, true, false>(L, s) : launch_forces_ms<false, false, false>(L, s);
 }
 
-template <bool LO, bool MS>
+template <bool LO, bool PAIRS>
 int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
   using C = PatchCfg<SEM_NGLL>;
-  static std::atomic<unsigned long long> attr_done{0}, attr_done_p{0};
+  static std::atomic<unsigned long long> attr_done{0}, attr_done_n{0}, attr_done_s{0}, attr_done_sn{0}, attr_done_p{0};
   static std::atomic<int> resident[64];  // CTAs of the persistent kernel per SM, per device
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(C::T);
@@ -1146,7 +1661,7 @@ int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (L.sync && !MS) {  // one persistent launch for the whole sweep
+  if (L.sync && !PAIRS) {  // one persistent launch for the whole sweep
     if (int r = raise_smem_limit(attr_done_p, patch_sweep_kernel<SEM_NGLL, LO>, C::SMEM)) return r;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1166,19 +1681,54 @@ int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
                                                reinterpret_cast<const float4*>(L.u), reinterpret_cast<float4*>(L.f),
                                                L.npatch, L.color_end, L.ncolors, L.stall ? 1u : 0u, L.sync));
   }
-  if (int r = raise_smem_limit(attr_done, patch_forces_kernel<SEM_NGLL, LO, MS>, C::SMEM)) return r;
-  const int S = MS ? L.shots : 1;
-  cfg.gridDim = dim3(static_cast<unsigned>((L.p1 - L.p0) * S));
-  return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, MS>, L.rec, L.desc, L.slots,
-                                             L.words, reinterpret_cast<const float4*>(L.u),
-                                             reinterpret_cast<float4*>(L.f), L.p0, S));
+  if constexpr (PAIRS) {
+    using PC = PairCfg<SEM_NGLL>;
+    cfg.dynamicSmemBytes = PC::SMEM;
+    cfg.gridDim = dim3(static_cast<unsigned>((L.p1 - L.p0) * ((L.shots + 1) / 2)));
+    if (L.nm.mode) {
+      if (int r = raise_smem_limit(attr_done_n, patch_forces_pair_kernel<SEM_NGLL, true>, PC::SMEM)) return r;
+      return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_pair_kernel<SEM_NGLL, true>, L.rec, L.desc,
+                                                 L.slots, L.words, reinterpret_cast<const float4*>(L.u),
+                                                 reinterpret_cast<float4*>(L.f), L.p0, L.shots, L.nm));
+    }
+    if (int r = raise_smem_limit(attr_done, patch_forces_pair_kernel<SEM_NGLL, false>, PC::SMEM)) return r;
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_pair_kernel<SEM_NGLL, false>, L.rec, L.desc,
+                                               L.slots, L.words, reinterpret_cast<const float4*>(L.u),
+                                               reinterpret_cast<float4*>(L.f), L.p0, L.shots, L.nm));
+  } else if (L.shots > 1) {  // one CTA per (patch, shot)
+    const int S = L.shots;
+    cfg.gridDim = dim3(static_cast<unsigned>((L.p1 - L.p0) * S));
+    if (L.nm.mode) {
+      if (int r = raise_smem_limit(attr_done_sn, patch_forces_kernel<SEM_NGLL, LO, true, true>, C::SMEM)) return r;
+      return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, true, true>, L.rec, L.desc,
+                                                 L.slots, L.words, reinterpret_cast<const float4*>(L.u),
+                                                 reinterpret_cast<float4*>(L.f), L.p0, S, L.nm));
+    }
+    if (int r = raise_smem_limit(attr_done_s, patch_forces_kernel<SEM_NGLL, LO, true, false>, C::SMEM)) return r;
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, true, false>, L.rec, L.desc,
+                                               L.slots, L.words, reinterpret_cast<const float4*>(L.u),
+                                               reinterpret_cast<float4*>(L.f), L.p0, S, L.nm));
+  } else {
+    const int S = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(L.p1 - L.p0));
+    if (L.nm.mode) {
+      if (int r = raise_smem_limit(attr_done_n, patch_forces_kernel<SEM_NGLL, LO, false, true>, C::SMEM)) return r;
+      return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, false, true>, L.rec, L.desc,
+                                                 L.slots, L.words, reinterpret_cast<const float4*>(L.u),
+                                                 reinterpret_cast<float4*>(L.f), L.p0, S, L.nm));
+    }
+    if (int r = raise_smem_limit(attr_done, patch_forces_kernel<SEM_NGLL, LO, false, false>, C::SMEM)) return r;
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, false, false>, L.rec, L.desc,
+                                               L.slots, L.words, reinterpret_cast<const float4*>(L.u),
+                                               reinterpret_cast<float4*>(L.f), L.p0, S, L.nm));
+  }
 }
 
 int launch_patch_n(const PatchLaunch& L, cudaStream_t s) {
   if (L.sync ? L.npatch <= 0 : L.p1 <= L.p0) return 0;
   using C = ForceCfg<SEM_NGLL>;
   const bool lo = L.variant == 0 ? C::LINE_OWNERS : L.variant == 1;
-  if (L.shots > 1) return lo ? launch_patch_lo<true, true>(L, s) : launch_patch_lo<false, true>(L, s);
+  if (L.shots > 1 && L.pairs) return launch_patch_lo<true, true>(L, s);  // shot pairs: line owners
   return lo ? launch_patch_lo<true, false>(L, s) : launch_patch_lo<false, false>(L, s);
 }
 

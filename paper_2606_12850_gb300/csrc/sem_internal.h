@@ -36,11 +36,14 @@ constexpr uint32_t kFirstTouchBit = 0x80000000u;
 // Bit 30 marks the same for the patch kernel's order (patch colour by patch colour), on the
 // word of the first local point (in patch-table order) of each patch node. Bit 29 marks a
 // local point that is the only one of its patch at its node (its element's team writes it
-// alone). Node ids are below 2^29.
+// alone). Bit 28 marks, on every local point of a patch node, that this patch is the node's
+// last toucher in the sweep (its force is complete there: the Newmark update of the node can
+// run in the same pass). Node ids are below 2^28.
 constexpr uint32_t kPatchFirstBit = 0x40000000u;
 constexpr uint32_t kAloneBit = 0x20000000u;
-constexpr uint32_t kNodeMask = 0x1FFFFFFFu;
-constexpr int kMaxNodes = 1 << 29;
+constexpr uint32_t kPatchLastBit = 0x10000000u;
+constexpr uint32_t kNodeMask = 0x0FFFFFFFu;
+constexpr int kMaxNodes = 1 << 28;
 
 inline int rec_words(int ngll) {
   const int np = ngll * ngll * ngll;
@@ -167,7 +170,31 @@ struct alignas(16) PatchDesc {
                  // forces of the local points meeting there)
   int word_off;  // its table: per shared node, the shared-memory offset of its first local
                  // point's ibool word
-  int pad0, pad1, pad2;
+  int src_off;   // its point sources (PatchSrc entries [src_off, src_off + nsrc)): the ones at
+  int nsrc;      // nodes it touches last, added there to the complete force
+  int pad;
+};
+// A point source in the patch sweep: internal node, shot, force vector (Sec. V-C).
+struct PatchSrc {
+  int node;
+  int shot;
+  double f[3];
+};
+// The explicit Newmark update (Sec. I) run by the patch sweep at each node's last toucher:
+// mode 1 corrector of step n fused with the predictor of step n+1
+//   a = M^-1 f ; v = v_half + dt/2 a ; u <- u + dt v + dt^2/2 a ; v_half <- v + dt/2 a
+// (f is then not stored), mode 2 the corrector alone (v <- v_half + dt/2 a, a stored), mode 0
+// none (f stored). The point sources of the step, at t = ctl->step dt, are added to f first.
+struct SweepNewmark {
+  int mode;
+  float* u;           // [nglob][shots][4], written at last touch (mode 1)
+  float* v;           // [nglob][shots][4], half-step velocity in, out as above
+  float* a;           // [nglob][shots][4], acceleration out (mode 2)
+  const float* minv;  // [nglob]
+  const PatchSrc* src;
+  const long long* step;  // the step counter (t_{n+1} = step dt)
+  double f0, t0, dtd;     // Ricker centre frequency and delay, step (double)
+  float dt, hdt, hdt2;
 };
 // Counters of a persistent sweep (all patch colours in one launch): patches taken, CTAs
 // that have left, a wait that gave up, patches finished per colour. Zero between sweeps.
@@ -192,7 +219,9 @@ struct PatchLaunch {
   float* f;
   int p0, p1;
   int variant;  // contraction form as in ForceLaunch
-  int shots;    // > 1: fields [nglob][shots][kNodeStride], one CTA per (patch, shot)
+  int shots;    // > 1: fields [nglob][shots][kNodeStride]
+  int pairs;    // with shots > 1: one CTA per (patch, shot pair) (else one per (patch, shot))
+  SweepNewmark nm;  // mode 0: forces only
 };
 int launch_patch_forces(int ngll, const PatchLaunch& launch, void* stream);
 // Shared-memory layout of the patch kernel for this order: workspace floats per element,

@@ -76,6 +76,7 @@ SIGNATURES = {
     "sem_energy_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
     "sem_sync": (_I, [_P]),
     "sem_autotune": (_I, [_P, _I, _P, _P]),
+    "sem_profile_steps": (_I, [_P, _I, _P]),
     "sem_group_create": (_I, [_P, _I, _P]),
     "sem_group_destroy": (_I, [_P]),
     "sem_group_step": (_I, [_P, _I]),
@@ -272,6 +273,8 @@ SEM_OPT_CONTRACTION = 2
 SEM_OPT_ASSEMBLY = 3
 SEM_OPT_SWEEP_STALL_TEST = 4
 SEM_OPT_NODE_ORDER = 5
+SEM_OPT_FUSED_NEWMARK = 6
+SEM_OPT_SHOT_PAIRS = 7
 
 
 def sem_set_option(ctx: Ctx, option: int, value: int):
@@ -551,6 +554,14 @@ def sem_autotune(ctx: Ctx, reps: int = 5):
     choice = ctypes.c_int(0)
     _check(lib().sem_autotune(ctx.handle, int(reps), ms.ctypes.data_as(_P), ctypes.byref(choice)), "sem_autotune", ctx)
     return ms, choice.value
+
+
+def sem_profile_steps(ctx: Ctx, nsteps: int):
+    """Runs nsteps time steps launched one by one with CUDA events around each force sweep;
+    returns (mean ms of the sweep per step, mean ms of the rest per step)."""
+    ms = np.zeros(2)
+    _check(lib().sem_profile_steps(ctx.handle, int(nsteps), ms.ctypes.data_as(_P)), "sem_profile_steps", ctx)
+    return float(ms[0]), float(ms[1])
 
 
 class Group:
