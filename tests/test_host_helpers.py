@@ -21,7 +21,7 @@ def test_algorithmic_bytes():
 def test_profiled_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
     import bench
     got = bench.profiled_traffic(5)
-    text = open(os.path.join(bench.ROOT, "profiles", "forces_kernel_ngll5_layered.md")).read()
+    text = open(os.path.join(bench.ROOT, "profiles", "patch_forces_kernel_ngll5_layered.md")).read()
     if bench.kernel_source_hash() in text:
         assert got is not None and got > 2.0e9  # the committed capture is of these sources
     else:
