@@ -82,9 +82,6 @@ void lagrange_at(int n, const double* xi, const double* h, double x, double* l, 
   }
 }
 
-// Elements in index order whose corner bounding box (widened by 1e-9 of its largest side)
-// holds x; Newton's method on the trilinear map from the element centre (at most 60
-// iterations); the first element whose solution lies within 1e-9 of the reference cube.
 namespace {
 
 constexpr double kInsideTol = 1e-9;

@@ -378,7 +378,10 @@ class Surrogate:
     def predict_or_solve(self, xyz, moments, tol: float, check: int = 4, seed: int = 0):
         """The surrogate's traces if the solver, run on ``check`` of the sources chosen at
         random, finds them within ``tol`` (relative L2 per run); else the solver's traces for
-        all sources. Returns (traces, used_solver, checked errors)."""
+        all sources. Acceptance is a sample check: the sources not among the ``check`` may
+        miss ``tol``. Returns (traces, used_solver, checked errors)."""
+        if self.solver is None:
+            raise ValueError("predict_or_solve needs a solver to check against (Surrogate(..., solver))")
         xyz = np.atleast_2d(xyz)
         pred = self.predict(xyz, moments)
         pick = np.argsort(inputs.uniform(seed, (len(xyz),), stream=77))[:min(check, len(xyz))]

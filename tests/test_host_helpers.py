@@ -118,3 +118,11 @@ def test_device_arrays_checked_before_any_library_call():
         sem._dev(_FakeCudaTensor(torch.float32, 0, n=11), 12, ctx)
     with pytest.raises(TypeError):
         sem.sem_apply_stiffness(ctx, _FakeCudaTensor(torch.float16, 0), _FakeCudaTensor(torch.float32, 0))
+
+
+def test_predict_or_solve_requires_a_solver():
+    from paper_2606_12850_gb300 import surrogate
+    amp = surrogate.AmplitudeModel(4000.0, np.array([[1000.0, 1000.0, 4000.0]]))
+    sur = surrogate.Surrogate(None, 1.0, 4000.0, amp, solver=None)
+    with pytest.raises(ValueError, match="solver"):
+        sur.predict_or_solve(np.zeros((2, 3)), np.zeros((2, 6)), tol=0.5)
