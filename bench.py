@@ -440,7 +440,7 @@ def measure_adjoint(device: int, nsteps: int = 800, every: int = 50):
     mu = rho_b * vs_b ** 2
     kappa = rho_b * vp_b ** 2 - 4.0 / 3.0 * mu
     mat = [torch.from_numpy(x.astype(np.float32)).to(dev) for x in (rho_b, kappa, mu)]
-    sim = adjoint.Simulation(ctx, s.dt, nsteps, checkpoint_every=every, device=device)
+    sim = adjoint.Simulation(ctx, s.dt, nsteps, checkpoint_every=every, device=device)  # keeps all if they fit
 
     sim.set_material(*mat)  # plain forward of the same model, device-timed
     sem.sem_set_state(ctx)
@@ -456,16 +456,28 @@ def measure_adjoint(device: int, nsteps: int = 800, every: int = 50):
     def misfit(seis):
         return 0.5 * s.dt * float(torch.sum((seis.double() - d_obs.double()) ** 2))
 
-    sim.gradient(s.dt * (sim.forward(*mat) - d_obs))  # warm-up: the allocator's first blocks
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    seis = sim.forward(*mat)
-    G = s.dt * (seis - d_obs)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    g_rho, g_kappa, g_mu = sim.gradient(G)
-    t2 = time.perf_counter()
+    def timed_gradient(sm):
+        sm.gradient(s.dt * (sm.forward(*mat) - d_obs))  # warm-up: the allocator's first blocks
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        seis = sm.forward(*mat)
+        G = s.dt * (seis - d_obs)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        grads = sm.gradient(G)
+        t2 = time.perf_counter()
+        return seis, grads, 1e3 * (t1 - t0), 1e3 * (t2 - t1)
+
+    # every step's displacement kept on the device (no recomputation), the default when it fits
+    seis, (g_rho, g_kappa, g_mu), fwd_ms, bwd_ms = timed_gradient(sim)
+    kept = sim.snapshots is not None
+    kept_mb = sim.snapshots.numel() * 4 / 1e6 if kept else 0.0
+    sim.snapshots = None
     L0 = misfit(seis)
+    # checkpoints every `every` steps and recomputed segments (when memory is short)
+    sim_ck = adjoint.Simulation(ctx, s.dt, nsteps, checkpoint_every=every, device=device, keep_all=False)
+    _, g_ck, ck_fwd_ms, ck_bwd_ms = timed_gradient(sim_ck)
+    ck_diff = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(g_ck, (g_rho, g_kappa, g_mu)))
 
     # float32 directional finite difference along a seeded per-element direction
     nspec = w.mesh.nspec
@@ -484,12 +496,17 @@ def measure_adjoint(device: int, nsteps: int = 800, every: int = 50):
         Ls.append(misfit(buf))
     fd = (Ls[0] - Ls[1]) / (2 * h)
     nglob = w.mesh.nglob
-    fwd_ms, bwd_ms = 1e3 * (t1 - t0), 1e3 * (t2 - t1)
-    return {"model": f"{w.name}, {nrec} surface receivers", "nsteps": nsteps, "checkpoint_every": every,
-            "plain_forward_ms": plain_ms, "checkpointed_forward_ms": fwd_ms, "backward_ms": bwd_ms,
+    return {"model": f"{w.name}, {nrec} surface receivers", "nsteps": nsteps,
+            "plain_forward_ms": plain_ms, "mode": "every displacement kept" if kept else "checkpointed",
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms,
             "gradient_ms": fwd_ms + bwd_ms, "gradient_over_plain_forward": (fwd_ms + bwd_ms) / plain_ms,
-            "checkpoint_mb": len(sim.checkpoints) * 3 * 3 * nglob * 4 / 1e6,
-            "segment_mb": (every + 2) * 3 * nglob * 4 / 1e6, "misfit": L0,
+            "snapshots_mb": kept_mb,
+            "checkpointed": {"checkpoint_every": every, "forward_ms": ck_fwd_ms, "backward_ms": ck_bwd_ms,
+                             "gradient_over_plain_forward": (ck_fwd_ms + ck_bwd_ms) / plain_ms,
+                             "checkpoint_mb": len(sim_ck.checkpoints) * 3 * 3 * nglob * 4 / 1e6,
+                             "segment_mb": (every + 2) * 3 * nglob * 4 / 1e6,
+                             "max_rel_l2_vs_kept": ck_diff},
+            "misfit": L0,
             "fd_directional": fd, "adjoint_directional": predicted,
             "fd_rel_err": abs(fd - predicted) / abs(fd) if fd else None,
             "timing": "plain forward: CUDA events; gradient: wall clock including host synchronisation, "

@@ -350,6 +350,12 @@ int sem_run_dev(sem_ctx* ctx, int nsteps, float* seis_dev);
  * borrowed until the stream reaches the end of the call). Used to recompute a segment of
  * a checkpointed run for the adjoint. Asynchronous on the context's stream. */
 int sem_run_snapshots(sem_ctx* ctx, int nsteps, float* u_dev);
+/* The same, also recording seismograms into the device buffer seis_dev[nrec][3][nsteps]
+ * (may be NULL) as sem_run_dev does: a forward run that keeps every displacement for the
+ * adjoint (no recomputation), when [nsteps][nglob][3] floats fit in device memory. With the
+ * fused sweep the snapshot of a step is taken when its receivers are sampled, before the
+ * sweep; the wavefields and seismograms equal those of sem_run_dev bit for bit. */
+int sem_run_record_snapshots(sem_ctx* ctx, int nsteps, float* seis_dev, float* u_dev);
 
 /* Divergence watchdog: SEM_OK if every value of u, v and a is finite, SEM_EDIVERGED
  * otherwise (an explicit scheme run above its stability limit grows until it overflows).

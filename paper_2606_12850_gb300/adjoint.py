@@ -1,11 +1,13 @@
 """Seismograms as a differentiable function of the material (rho, kappa, mu per local point).
 
-The forward pass runs the solver from rest and keeps a checkpoint of the complete state every
-``checkpoint_every`` steps; the backward pass walks the checkpoints in reverse, recomputes the
-displacements of one segment from its checkpoint, and runs the discrete adjoint of the
-explicit scheme backward through it (see ``sem_adjoint_begin`` in include/sem.h). All
-arithmetic runs in the CUDA library; this module only orders the calls and holds the device
-buffers (PyTorch tensors).
+When the displacement of every step fits in device memory (by default: in half of what is
+free), the forward pass keeps all of them and the backward pass runs the discrete adjoint of
+the explicit scheme over the whole run in one call, with no recomputation. Otherwise the
+forward pass keeps a checkpoint of the complete state every ``checkpoint_every`` steps, and
+the backward pass walks the checkpoints in reverse, recomputes the displacements of one
+segment from its checkpoint and runs the adjoint backward through it (see
+``sem_adjoint_begin`` in include/sem.h). All arithmetic runs in the CUDA library; this
+module only orders the calls and holds the device buffers (PyTorch tensors).
 """
 from __future__ import annotations
 
@@ -23,9 +25,15 @@ class Simulation:
     The simulation sets the context's SEM_OPT_NODE_ORDER to the internal order.
     """
 
-    def __init__(self, ctx: sem.Ctx, dt: float, nsteps: int, checkpoint_every: int = 50, device: int = 0):
+    def __init__(self, ctx: sem.Ctx, dt: float, nsteps: int, checkpoint_every: int = 50, device: int = 0,
+                 keep_all="auto"):
+        """keep_all: True keeps every step's displacement from the forward run (no
+        recomputation in the backward run), False checkpoints, "auto" keeps all when they
+        take at most half of the free device memory."""
         if ctx.shots != 1:
             raise ValueError("one shot per simulation")
+        self.keep_all = keep_all
+        self.snapshots = None  # [nsteps + 1][nglob*3] when every displacement is kept
         self.ctx = ctx
         self.dt = float(dt)
         self.nsteps = int(nsteps)
@@ -58,6 +66,13 @@ class Simulation:
             sem.sem_set_moduli(self.ctx, *(to_np(x) for x in mats))
         sem.sem_set_dt(self.ctx, self.dt)
 
+    def keeps_all(self) -> bool:
+        if self.keep_all == "auto":
+            need = (self.nsteps + 1) * 3 * self.nglob * 4
+            free, _ = torch.cuda.mem_get_info(self.device)
+            return need <= free // 2
+        return bool(self.keep_all)
+
     def forward(self, rho, kappa, mu) -> torch.Tensor:
         """Seismograms [nrec][3][nsteps] (s^1 .. s^N) on the device."""
         self.set_material(rho, kappa, mu)
@@ -65,6 +80,15 @@ class Simulation:
         N = self.nsteps
         seis = torch.empty((self.nrec, 3, N), device=self.device)
         self.checkpoints = []
+        self.snapshots = None
+        if self.keeps_all():
+            U = torch.empty((N + 1, 3 * self.nglob), device=self.device)
+            U[0].copy_(self._state()[0])
+            torch.cuda.synchronize(self.device)
+            sem.sem_run_record_snapshots(self.ctx, N, seis, U[1:])
+            sem.sem_sync(self.ctx)
+            self.snapshots = U
+            return seis
         n = 0
         while n < N:
             self.checkpoints.append((n,) + self._state())
@@ -94,6 +118,11 @@ class Simulation:
         Gt = G.detach().to(self.device, torch.float32).permute(2, 0, 1).contiguous()
         torch.cuda.synchronize(self.device)
         sem.sem_adjoint_begin(self.ctx)
+        if self.snapshots is not None:  # the terms n = 1 .. N - 1 read u^0 .. u^N
+            if N > 1:
+                sem.sem_adjoint_segment(self.ctx, N - 1, Gt[1:N], self.snapshots)
+            sem.sem_sync(self.ctx)
+            return sem.sem_adjoint_gradients(self.ctx)
         for n0 in reversed([c[0] for c in self.checkpoints]):
             # the terms n = n0 + 1 .. n0 + count, which read u^{n0} .. u^{n0 + count + 1}
             count = min(self.every, N - 1 - n0)

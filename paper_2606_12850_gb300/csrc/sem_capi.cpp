@@ -1528,18 +1528,48 @@ int sem_step(sem_ctx* c, int nsteps) { return advance(c, nsteps, nullptr); }
 
 int sem_run_dev(sem_ctx* c, int nsteps, float* seis_dev) { return advance(c, nsteps, seis_dev); }
 
-int sem_run_snapshots(sem_ctx* c, int nsteps, float* u_dev) {
+int sem_run_record_snapshots(sem_ctx* c, int nsteps, float* seis_dev, float* u_dev) {
   int r = check_ready(c);
   if (r) return r;
   if (nsteps < 0) return fail(c, SEM_EINVAL, "nsteps must be >= 0");
   if (nsteps > 0 && !u_dev) return fail(c, SEM_EINVAL, "sem_run_snapshots: NULL snapshot buffer");
+  if ((r = set_device(c))) return r;
   const size_t per = 3 * static_cast<size_t>(c->nglob) * c->shots;
-  for (int k = 0; k < nsteps; ++k) {
-    if ((r = advance(c, 1, nullptr))) return r;
-    SEM_LAUNCH(c, launch_pack(c->d_u, u_dev + k * per, c->node_order == 1 ? nullptr : c->d_perm, c->nglob, c->shots,
-                              c->stream));
+  const int* perm = c->node_order == 1 ? nullptr : c->d_perm;
+  if (!fused_sweep(c)) {
+    SEM_LAUNCH(c, launch_set_ctl(c->d_ctl, c->steps, seis_dev ? nsteps : 0, seis_dev, c->stream));
+    for (int k = 0; k < nsteps; ++k) {
+      if (!c->pending) {
+        if ((r = enqueue_first_step(c))) return r;
+        c->pending = true;
+      } else if ((r = enqueue_pending_step(c))) {
+        return r;
+      }
+      SEM_LAUNCH(c, launch_pack(c->d_u, u_dev + k * per, perm, c->nglob, c->shots, c->stream));
+    }
+    c->steps += nsteps;
+    return SEM_OK;
   }
+  // fused sweep: the predictor once, then per step the receivers sample u^{n+1}, which is
+  // also the snapshot (the sweep overwrites it with the next prediction), then the sweep
+  if (nsteps == 0) return SEM_OK;
+  if ((r = finish_state(c))) return r;
+  SEM_LAUNCH(c, launch_set_ctl(c->d_ctl, c->steps, seis_dev ? nsteps : 0, seis_dev, c->stream));
+  SEM_LAUNCH(c, launch_predictor(problem(c), c->stream));
+  for (int k = 0; k < nsteps; ++k) {
+    DevProblem q = problem(c);
+    q.nsrc = 0;
+    SEM_LAUNCH(c, launch_sources_record(q, c->stream));
+    SEM_LAUNCH(c, launch_pack(c->d_u, u_dev + k * per, perm, c->nglob, c->shots, c->stream));
+    const SweepNewmark nm = sweep_newmark(c, k + 1 < nsteps ? 1 : 2);
+    if ((r = forces_all_colors(c, c->d_u, c->d_a, kNodeStride, c->shots, &nm))) return r;
+  }
+  c->steps += nsteps;
   return SEM_OK;
+}
+
+int sem_run_snapshots(sem_ctx* c, int nsteps, float* u_dev) {
+  return sem_run_record_snapshots(c, nsteps, nullptr, u_dev);
 }
 
 int sem_check_finite(sem_ctx* c) {

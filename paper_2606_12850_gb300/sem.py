@@ -63,6 +63,7 @@ SIGNATURES = {
     "sem_run": (_I, [_P, _I, _P]),
     "sem_run_dev": (_I, [_P, _I, _P]),
     "sem_run_snapshots": (_I, [_P, _I, _P]),
+    "sem_run_record_snapshots": (_I, [_P, _I, _P, _P]),
     "sem_check_finite": (_I, [_P]),
     "sem_apply_stiffness": (_I, [_P, _P, _P]),
     "sem_apply_stiffness_strided": (_I, [_P, _P, _P, _I]),
@@ -487,6 +488,14 @@ def sem_run_dev(ctx: Ctx, nsteps: int, seis_dev=None):
 def sem_run_snapshots(ctx: Ctx, nsteps: int, u_dev):
     n = 3 * ctx.nglob * ctx.shots * int(nsteps)
     _check(lib().sem_run_snapshots(ctx.handle, int(nsteps), _dev(u_dev, n, ctx)), "sem_run_snapshots", ctx)
+
+
+def sem_run_record_snapshots(ctx: Ctx, nsteps: int, seis_dev, u_dev):
+    n = 3 * ctx.nglob * ctx.shots * int(nsteps)
+    ns = ctx.shots * ctx.nrec * 3 * int(nsteps)
+    seis_ptr = _dev(seis_dev, ns, ctx) if seis_dev is not None else None
+    _check(lib().sem_run_record_snapshots(ctx.handle, int(nsteps), seis_ptr, _dev(u_dev, n, ctx)),
+           "sem_run_record_snapshots", ctx)
 
 
 def sem_check_finite(ctx: Ctx):

@@ -51,6 +51,12 @@ class FakeLibrary:
             out[j].fill_(self.n + 1 + j)
         self.n += k
 
+    def sem_run_record_snapshots(self, ctx, k, seis, out):
+        for j in range(k):
+            seis[:, :, j] = self.n + 1 + j
+            out[j].fill_(self.n + 1 + j)
+        self.n += k
+
     def sem_adjoint_begin(self, ctx):
         self.visits = []
 
@@ -64,7 +70,7 @@ class FakeLibrary:
         return (np.zeros(1),) * 3
 
 
-def _run(monkeypatch, nsteps, every):
+def _run(monkeypatch, nsteps, every, keep_all=False):
     fake = FakeLibrary()
     for name in dir(fake):
         if name.startswith("sem_"):
@@ -77,8 +83,12 @@ def _run(monkeypatch, nsteps, every):
     sim = adjoint.Simulation.__new__(adjoint.Simulation)  # the initialiser wants a CUDA device
     sim.ctx, sim.dt, sim.nsteps, sim.every = Ctx(), 1e-3, nsteps, every
     sim.device, sim.nglob, sim.nrec, sim.checkpoints = torch.device("cpu"), 4, 2, []
+    sim.keep_all, sim.snapshots = keep_all, None
     seis = sim.forward(np.ones(1), np.ones(1), np.ones(1))
-    assert [c[0] for c in sim.checkpoints] == list(range(0, nsteps, every))
+    if keep_all:
+        assert sim.checkpoints == [] and sim.snapshots.shape[0] == nsteps + 1
+    else:
+        assert [c[0] for c in sim.checkpoints] == list(range(0, nsteps, every))
     assert np.array_equal(seis[0, 0].numpy(), np.arange(1, nsteps + 1))
     G = torch.arange(1, nsteps + 1, dtype=torch.float32).expand(2, 3, nsteps)  # G^m = m
     sim.gradient(G)
@@ -93,6 +103,15 @@ def _schedule_ok(visits, nsteps):
 @pytest.mark.parametrize("nsteps,every", [(50, 7), (60, 60), (61, 60), (10, 1), (200, 50), (3, 5)])
 def test_checkpoint_schedule(monkeypatch, nsteps, every):
     _, visits = _run(monkeypatch, nsteps, every)
+    assert _schedule_ok(visits, nsteps)
+
+
+@pytest.mark.parametrize("nsteps", [50, 2, 1])
+def test_kept_snapshots_schedule(monkeypatch, nsteps):
+    """Every displacement kept from the forward run: one segment visits m = N .. 2 with G^m
+    and u^{m-2}, u^{m-1}, u^m."""
+    seis, visits = _run(monkeypatch, nsteps, 7, keep_all=True)
+    assert np.array_equal(seis[0, 0].numpy(), np.arange(1, nsteps + 1))
     assert _schedule_ok(visits, nsteps)
 
 

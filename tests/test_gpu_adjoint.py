@@ -63,7 +63,7 @@ def problem(oracle):
                 grads=grads)
 
 
-def make_sim(p, every):
+def make_sim(p, every, keep_all=False):
     from paper_2606_12850_gb300 import adjoint
     mesh = p["mesh"]
     ctx = sem.sem_create(mesh.ngll, 0)
@@ -71,7 +71,7 @@ def make_sim(p, every):
     kw = p["kw"]
     sem.sem_set_source_nodes(ctx, kw["src_nodes"], kw["src_force"], kw["f0"], kw["t0"])
     sem.sem_set_receiver_nodes(ctx, kw["rec_nodes"])
-    return ctx, adjoint.Simulation(ctx, p["dt"], p["nsteps"], checkpoint_every=every)
+    return ctx, adjoint.Simulation(ctx, p["dt"], p["nsteps"], checkpoint_every=every, keep_all=keep_all)
 
 
 def material(p):
@@ -119,6 +119,52 @@ def test_checkpoint_interval_does_not_change_gradient(problem):
         out.append(sim.gradient(G))
     for a, b in zip(*out):
         assert rel_l2(a, b) <= 1e-5
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_kept_snapshots_match_checkpoints(oracle, problem, fused):
+    """Every displacement kept from the forward run (sem_run_record_snapshots, one adjoint
+    segment, no recomputation) against checkpoints every 7 steps: the same seismograms bit
+    for bit, gradients within 1e-5 (the float32 partial sums are flushed on another
+    schedule), and the oracle bar; with the fused sweep and with separate Newmark passes."""
+    p = problem
+    G = torch.from_numpy(p["G"].astype(np.float32)).cuda()
+    seis, grads = [], []
+    for keep in (False, True):
+        ctx, sim = make_sim(p, 7, keep_all=keep)
+        sem.sem_set_option(ctx, sem.SEM_OPT_FUSED_NEWMARK, fused)
+        seis.append(sim.forward(*material(p)).cpu().numpy())
+        assert (sim.snapshots is not None) == keep
+        grads.append(sim.gradient(G))
+    assert np.array_equal(seis[0], seis[1])
+    for a, b in zip(*grads):
+        assert rel_l2(b, a) <= 1e-5
+    r_rho, r_kappa, r_mu = (x.reshape(grads[1][0].shape) for x in p["grads"])
+    assert rel_l2(grads[1][1], r_kappa) <= TOL_MODULI and rel_l2(grads[1][2], r_mu) <= TOL_MODULI
+    assert rel_l2(grads[1][0], r_rho) <= rho_tolerance(oracle, p)
+
+
+def test_segment_equals_single_steps(problem):
+    """sem_adjoint_segment (the mass term formed per node by the leapfrog pass) against
+    sem_adjoint_step + sem_adjoint_accumulate one step at a time (formed at every local
+    point): bitwise equal gradients."""
+    p = problem
+    ctx, sim = make_sim(p, 7, keep_all=True)
+    sim.forward(*material(p))
+    U = sim.snapshots
+    N = p["nsteps"]
+    Gt = torch.from_numpy(p["G"].astype(np.float32)).cuda().permute(2, 0, 1).contiguous()
+    torch.cuda.synchronize()
+    sem.sem_adjoint_begin(ctx)
+    sem.sem_adjoint_segment(ctx, N - 1, Gt[1:N], U)
+    seg = sem.sem_adjoint_gradients(ctx)
+    sem.sem_adjoint_begin(ctx)
+    for j in range(N - 1, 0, -1):
+        sem.sem_adjoint_step(ctx, Gt[j])
+        sem.sem_adjoint_accumulate(ctx, U[j - 1], U[j], U[j + 1])
+    one = sem.sem_adjoint_gradients(ctx)
+    for a, b in zip(seg, one):
+        assert np.array_equal(a, b)
 
 
 def test_restart_from_saved_state(problem):
