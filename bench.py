@@ -57,6 +57,7 @@ def parse_args():
     p.add_argument("--models", type=int, default=16, help="uneven-models group measurement (0 = skip)")
     p.add_argument("--no-iso", action="store_true", help="skip the (h,p) iso-accuracy study")
     p.add_argument("--no-ablation", action="store_true", help="skip the colouring/atomics assembly ablation")
+    p.add_argument("--no-tiles", action="store_true", help="skip the element-tile autotuner measurement")
     p.add_argument("--surrogate-epochs", type=int, default=150)
     return p.parse_args()
 
@@ -513,6 +514,30 @@ def measure_adjoint(device: int, nsteps: int = 800, every: int = 50):
                       "after one untimed gradient"}
 
 
+def measure_tiles(device: int, reps: int = 10):
+    """Element tiles per NGLL picked by the autotuner (sem_tune_patch_shape): every brick shape
+    of the order's patch CTA timed on the three-layer jittered cube at 128 GLL intervals per
+    side (32^3 / 22^3 / 16^3 elements at NGLL 5 / 7 / 9), ms of one time step's sweep."""
+    from paper_2606_12850_gb300 import inputs, sem
+
+    out = []
+    for ngll, n in ((5, 32), (7, 22), (9, 16)):
+        w = inputs.layered_cube(ngll, n=n, nsteps=10)
+        ctx = sem.sem_create(ngll, device)
+        rows, best = sem.sem_tune_patch_shape(ctx, w.mesh.ibool, w.mesh.nglob, w.rho, w.vp, w.vs,
+                                              ctrl=w.mesh.ctrl, reps=reps)
+        tiny = inputs.structured_hex_mesh((2, 2, 2), ngll, 1.0)  # the order's default brick
+        info = sem.sem_patch_plan(ngll, tiny.ibool, tiny.nglob)[2]
+        default = (info["bx"], info["by"], info["bz"])
+        ms = dict(rows)
+        out.append({"ngll": ngll, "elements": f"{n}^3",
+                    "shapes_ms": {"x".join(map(str, k)): v for k, v in rows},
+                    "chosen": "x".join(map(str, best)), "default": "x".join(map(str, default)),
+                    "chosen_over_default": ms[tuple(default)] / ms[best]})
+        del ctx
+    return out
+
+
 def measure_models(device: int, count: int = 16, steps: int = 50):
     """Many independent models on one GPU: homogeneous cubes of 8^3 .. 40^3 elements with
     NGLL cycling through 4 .. 8, each autotuned (contraction form), stepped one after
@@ -841,6 +866,10 @@ def run_ours(args):
     if args.models > 0:
         models = measure_models(local, args.models)
 
+    tiles = None
+    if not args.no_tiles:
+        tiles = measure_tiles(local)
+
     sur = None
     if args.surrogate_runs > 0:
         sur = measure_surrogate(local, args.surrogate_runs, args.surrogate_epochs)
@@ -883,7 +912,7 @@ def run_ours(args):
                                   "bytes_per_step": alg["step"]},
             "global_pt_updates_per_s": world * mesh.nglob * K / (ms / 1e3),
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clock_info,
-            "batched_shots": batched, "uneven_models": models, "hp_sweep": sweep, "iso_accuracy": iso,
+            "batched_shots": batched, "uneven_models": models, "element_tiles": tiles, "hp_sweep": sweep, "iso_accuracy": iso,
             "assembly_ablation": ablation,
             "adjoint": adj,
             "surrogate": sur,

@@ -197,6 +197,13 @@ int sem_destroy(sem_ctx* ctx);
  *   once for both); 0 = one CTA per patch and shot. The same arithmetic per shot; results
  *   differ only by the rounding order of a few sums. */
 #define SEM_OPT_SHOT_PAIRS 7
+/*   SEM_OPT_PATCH_SHAPE (applied by the next sem_set_mesh): the brick of elements one CTA of
+ *   the patch sweep takes, value = bx | by << 8 | bz << 16 in elements along the mesh's
+ *   lattice x, y, z; 0 = the order's default (sem_patch_info reports the shape in use).
+ *   bx*by*bz may not exceed the elements a patch CTA holds at this order (8 at NGLL 5; the
+ *   default brick's count); every brick shape with that count runs the same kernel.
+ *   sem_tune_patch_shape measures them and sets the fastest. */
+#define SEM_OPT_PATCH_SHAPE 8
 int sem_set_option(sem_ctx* ctx, int option, long long value);
 
 /* Set the mesh (Sec. II-B: hexahedral elements mapped to the reference cube, the
@@ -414,6 +421,21 @@ int sem_adjoint_segment(sem_ctx* ctx, int count, const float* G_dev, const float
  * chosen form in *choice_out (may be NULL). Reads u, writes scratch only (completes a
  * pending state first). Synchronous. Requires mesh, material and dt. */
 int sem_autotune(sem_ctx* ctx, int reps, double* ms_out, int* choice_out);
+
+/* Autotuner of the element tile (the patch brick) for this order on the caller's mesh:
+ * every brick shape bx x by x bz whose element count is the one a patch CTA holds at this
+ * order (8 at NGLL 5: 2x2x2, 4x2x1, 8x1x1, ...; each side at most 16) is built on a scratch
+ * context of the same order, device and stream from the given mesh (ibool with per-point
+ * positions xyz[nspec][ngll^3][3] or trilinear corners ctrl[nspec][8][3]: exactly one
+ * non-NULL) and material (rho, vp, vs per local point), and `reps` of its time steps (fused
+ * sweep, dt at Courant number 0.4, from rest) are timed with sem_profile_steps after two of
+ * warm-up. SEM_OPT_PATCH_SHAPE of ctx is set to the fastest, for the next sem_set_mesh on
+ * ctx. shapes_out[k] (encoded as for SEM_OPT_PATCH_SHAPE) and ms_out[k] (ms of one step's
+ * sweep) for the first max_shapes candidates (either may be NULL); *nshapes_out = the
+ * number of candidates. Synchronous; allocates one scratch mesh at a time. */
+int sem_tune_patch_shape(sem_ctx* ctx, int nspec, int nglob, const int32_t* ibool, const double* xyz,
+                         const double* ctrl, const float* rho, const float* vp, const float* vs, int reps,
+                         int max_shapes, int32_t* shapes_out, double* ms_out, int* nshapes_out);
 
 /* Profile nsteps time steps (Sec. I, IV-C), launched one by one with CUDA events on the
  * context's stream around each step's force sweep: ms_out[0] = mean milliseconds of the

@@ -47,6 +47,8 @@ struct sem_ctx {
   int fuse_newmark = 2;             // SEM_OPT_FUSED_NEWMARK: Newmark update in the patch sweep
                                     // (1 on, 0 off, 2 on for a single shot)
   int shot_pairs = 1;               // SEM_OPT_SHOT_PAIRS: patch CTAs per shot pair (1) or shot (0)
+  PatchShape shape_opt{0, 0, 0};    // SEM_OPT_PATCH_SHAPE for the next sem_set_mesh (0: the order's)
+  PatchShape shape{0, 0, 0};        // the bricks of the current mesh
   std::vector<PatchDesc> pdesc;     // host copy of the patch descriptors
   std::vector<int> last_patch;      // internal node -> the patch that touches it last
   int assembly = 0;                 // SEM_OPT_ASSEMBLY: 0 patches, one launch per colour,
@@ -687,6 +689,22 @@ int sem_set_option(sem_ctx* c, int option, long long value) {
       c->shot_pairs = static_cast<int>(value);
       drop_graph(c);
       return SEM_OK;
+    case SEM_OPT_PATCH_SHAPE: {
+      PatchShape def;
+      if (patch_shape(c->ngll, &def)) return fail(c, SEM_EINVAL, "no patch kernel for this order");
+      if (value == 0) {
+        c->shape_opt = PatchShape{0, 0, 0};
+        return SEM_OK;
+      }
+      const int bx = static_cast<int>(value & 0xFF), by = static_cast<int>((value >> 8) & 0xFF),
+                bz = static_cast<int>((value >> 16) & 0xFF);
+      if (value < 0 || (value >> 24) != 0 || bx < 1 || by < 1 || bz < 1 || bx * by * bz > def.bx * def.by * def.bz)
+        return fail(c, SEM_EINVAL,
+                    "patch shape must be bx | by << 8 | bz << 16 with bx, by, bz >= 1 and bx*by*bz <= " +
+                        std::to_string(def.bx * def.by * def.bz) + " (the elements a patch CTA holds at this order)");
+      c->shape_opt = PatchShape{bx, by, bz};
+      return SEM_OK;
+    }
     case SEM_OPT_FUSED_NEWMARK:
       if (value < 0 || value > 2) return fail(c, SEM_EINVAL, "fused Newmark must be 0, 1 or 2");
       c->fuse_newmark = static_cast<int>(value);
@@ -789,8 +807,10 @@ static int set_mesh_impl(sem_ctx* c, int nspec, int nglob, const int32_t* ibool,
   // patches (bricks of the lattice coordinates, coloured) give the record order
   PatchShape shape;
   PatchPlan plan;
-  if (patch_shape(n, &shape) || build_patches(nspec, n, nglob, ibool, shape, &plan, &err))
-    return fail(c, SEM_EINVAL, "patches: " + err);
+  if (patch_shape(n, &shape)) return fail(c, SEM_EINVAL, "no patch kernel for this order");
+  if (c->shape_opt.bx > 0) shape = c->shape_opt;
+  if (build_patches(nspec, n, nglob, ibool, shape, &plan, &err)) return fail(c, SEM_EINVAL, "patches: " + err);
+  c->shape = shape;
   c->order = plan.elem;
   c->node_new = plan.node_new;
   c->perm.assign(nglob, 0);
@@ -1706,8 +1726,7 @@ int sem_info(sem_ctx* c, int64_t* out) {
 int sem_patch_info(sem_ctx* c, int64_t* out) {
   if (!c || !out) return fail(c, SEM_EINVAL, "sem_patch_info: bad arguments");
   if (!c->have_mesh) return fail(c, SEM_ESTATE, "sem_set_mesh has not been called");
-  PatchShape shape;
-  patch_shape(c->ngll, &shape);
+  const PatchShape shape = c->shape;
   out[0] = c->npatch;
   out[1] = static_cast<int64_t>(c->pcolor_off.size()) - 1;
   out[2] = c->pmax_nodes;
@@ -1817,6 +1836,52 @@ int sem_adjoint_gradients(sem_ctx* c, double* g_rho, double* g_kappa, double* g_
       }
     }
   }
+  return SEM_OK;
+}
+
+int sem_tune_patch_shape(sem_ctx* c, int nspec, int nglob, const int32_t* ibool, const double* xyz,
+                         const double* ctrl, const float* rho, const float* vp, const float* vs, int reps,
+                         int max_shapes, int32_t* shapes_out, double* ms_out, int* nshapes_out) {
+  if (!c) return fail(nullptr, SEM_EINVAL, "null context");
+  if (reps < 1 || !ibool || (!xyz) == (!ctrl) || !rho || !vp || !vs)
+    return fail(c, SEM_EINVAL, "sem_tune_patch_shape: bad arguments");
+  PatchShape def;
+  if (patch_shape(c->ngll, &def)) return fail(c, SEM_EINVAL, "no patch kernel for this order");
+  const int pe = def.bx * def.by * def.bz;  // elements a patch CTA holds at this order
+  std::vector<PatchShape> cand;
+  for (int bz = 1; bz <= pe; ++bz)
+    for (int by = 1; by <= pe; ++by)
+      for (int bx = 1; bx <= pe; ++bx)
+        if (bx * by * bz == pe && bx <= 16 && by <= 16 && bz <= 16) cand.push_back(PatchShape{bx, by, bz});
+  std::vector<double> ms(cand.size(), 0.0);
+  int best = -1;
+  for (size_t k = 0; k < cand.size(); ++k) {
+    sem_ctx* t = nullptr;
+    int r = sem_create(&t, c->ngll, c->device, c->stream);
+    if (r) return fail(c, r, "sem_tune_patch_shape: " + g_err);
+    const long long code = cand[k].bx | (cand[k].by << 8) | (cand[k].bz << 16);
+    double dt = 0.0, prof[2] = {0.0, 0.0};
+    if (!r) r = sem_set_option(t, SEM_OPT_PATCH_SHAPE, code);
+    if (!r) r = xyz ? sem_set_mesh(t, nspec, nglob, ibool, xyz) : sem_set_mesh_corners(t, nspec, nglob, ibool, ctrl);
+    if (!r) r = sem_set_material(t, rho, vp, vs);
+    if (!r) r = sem_suggest_dt(t, 0.4, &dt);
+    if (!r) r = sem_set_dt(t, dt);
+    if (!r) r = sem_set_state(t, nullptr, nullptr, nullptr);
+    if (!r) r = sem_profile_steps(t, 2, prof);  // warm-up
+    if (!r) r = sem_profile_steps(t, reps, prof);
+    const std::string msg = r ? t->err : std::string();
+    sem_destroy(t);
+    if (r) return fail(c, r, "sem_tune_patch_shape: " + msg);
+    ms[k] = prof[0];
+    if (best < 0 || ms[k] < ms[best]) best = static_cast<int>(k);
+  }
+  c->shape_opt = cand[best];
+  const int nout = std::min<int>(max_shapes, static_cast<int>(cand.size()));
+  for (int k = 0; k < nout; ++k) {
+    if (shapes_out) shapes_out[k] = cand[k].bx | (cand[k].by << 8) | (cand[k].bz << 16);
+    if (ms_out) ms_out[k] = ms[k];
+  }
+  if (nshapes_out) *nshapes_out = static_cast<int>(cand.size());
   return SEM_OK;
 }
 

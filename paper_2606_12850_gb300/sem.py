@@ -78,6 +78,7 @@ SIGNATURES = {
     "sem_sync": (_I, [_P]),
     "sem_autotune": (_I, [_P, _I, _P, _P]),
     "sem_profile_steps": (_I, [_P, _I, _P]),
+    "sem_tune_patch_shape": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _I, _I, _P, _P, _P]),
     "sem_group_create": (_I, [_P, _I, _P]),
     "sem_group_destroy": (_I, [_P]),
     "sem_group_step": (_I, [_P, _I]),
@@ -276,6 +277,7 @@ SEM_OPT_SWEEP_STALL_TEST = 4
 SEM_OPT_NODE_ORDER = 5
 SEM_OPT_FUSED_NEWMARK = 6
 SEM_OPT_SHOT_PAIRS = 7
+SEM_OPT_PATCH_SHAPE = 8
 
 
 def sem_set_option(ctx: Ctx, option: int, value: int):
@@ -571,6 +573,40 @@ def sem_profile_steps(ctx: Ctx, nsteps: int):
     ms = np.zeros(2)
     _check(lib().sem_profile_steps(ctx.handle, int(nsteps), ms.ctypes.data_as(_P)), "sem_profile_steps", ctx)
     return float(ms[0]), float(ms[1])
+
+
+def patch_shape_code(bx: int, by: int, bz: int) -> int:
+    """SEM_OPT_PATCH_SHAPE value of a bx x by x bz brick."""
+    return int(bx) | (int(by) << 8) | (int(bz) << 16)
+
+
+def sem_tune_patch_shape(ctx: Ctx, ibool, nglob: int, rho, vp, vs, xyz=None, ctrl=None, reps: int = 5):
+    """Times every brick shape this order's patch kernel can take on the given mesh and
+    material (per-point positions xyz or trilinear corners ctrl) and sets the fastest for
+    the context's next sem_set_mesh; returns [((bx, by, bz), ms per step's sweep)] and the
+    chosen (bx, by, bz)."""
+    if (xyz is None) == (ctrl is None):
+        raise ValueError("give exactly one of xyz (per-point positions) and ctrl (corners)")
+    n3 = ctx.ngll ** 3
+    ib, pi = _host(ibool, np.int32)
+    nspec = ib.size // n3
+    if xyz is not None:
+        pts, px = _host(xyz, np.float64, (nspec, n3, 3))
+        pc = None
+    else:
+        cts, pc = _host(ctrl, np.float64, (nspec, 8, 3))
+        px = None
+    mats = [_host(m, np.float32, (nspec, n3)) for m in (rho, vp, vs)]
+    cap = 64
+    shapes = np.zeros(cap, dtype=np.int32)
+    ms = np.zeros(cap)
+    count = ctypes.c_int(0)
+    _check(lib().sem_tune_patch_shape(ctx.handle, nspec, int(nglob), pi, px, pc, *(m[1] for m in mats), int(reps),
+                                      cap, shapes.ctypes.data_as(_P), ms.ctypes.data_as(_P), ctypes.byref(count)),
+           "sem_tune_patch_shape", ctx)
+    dec = lambda v: (int(v) & 0xFF, (int(v) >> 8) & 0xFF, (int(v) >> 16) & 0xFF)  # noqa: E731
+    rows = [(dec(shapes[k]), float(ms[k])) for k in range(min(cap, count.value))]
+    return rows, min(rows, key=lambda r: r[1])[0]
 
 
 class Group:

@@ -217,3 +217,52 @@ def test_atomic_ablation_agrees_within_rounding(oracle, ngll):
     f_elem = sweep_stride4(ctx, u, 1)
     check_forces(f_atomic, oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, *mat, ngll).forces(u.astype(np.float64)))
     assert rel_l2(f_atomic, f_elem.astype(np.float64)) <= 1e-6
+
+
+def test_patch_shape_tuner_and_option(oracle):
+    """The element-tile autotuner times every brick shape of the order's patch CTA (8
+    elements at NGLL 5) on the caller's mesh and sets the fastest for the next sem_set_mesh;
+    non-default bricks (elongated 8x1x1, 1x2x4) through SEM_OPT_PATCH_SHAPE meet the
+    stiffness bar, a brick larger than the CTA holds is refused, and a time step on a
+    non-default brick runs the fused Newmark update bitwise like the separate passes."""
+    mesh = inputs.structured_hex_mesh((6, 5, 4), 5, 1000.0, jitter=0.1, seed=31)
+    mat = material(mesh, 33)
+    ctx = sem.sem_create(5, 0)
+    rows, best = sem.sem_tune_patch_shape(ctx, mesh.ibool, mesh.nglob, *mat, ctrl=mesh.ctrl, reps=3)
+    shapes = [r[0] for r in rows]
+    assert len(shapes) == 10 and (2, 2, 2) in shapes and all(bx * by * bz == 8 for bx, by, bz in shapes)
+    assert all(ms > 0 for _, ms in rows)
+    sem.sem_set_mesh_corners(ctx, mesh.ibool, mesh.ctrl, mesh.nglob)
+    sem.sem_set_material(ctx, *mat)
+    info = sem.sem_patch_info(ctx)
+    assert (info["bx"], info["by"], info["bz"]) == best
+    u = inputs.random_field(mesh.nglob, 34)
+    f_ref = oracle.Model(mesh.ibool, mesh.ctrl, mesh.nglob, *mat, 5).forces(u.astype(np.float64))
+    check_forces(sweep_stride4(ctx, u, 0), f_ref)
+    with pytest.raises(sem.SemError):
+        sem.sem_set_option(ctx, sem.SEM_OPT_PATCH_SHAPE, sem.patch_shape_code(3, 3, 1))
+    for shape in ((8, 1, 1), (1, 2, 4)):
+        c2 = sem.sem_create(5, 0)
+        sem.sem_set_option(c2, sem.SEM_OPT_PATCH_SHAPE, sem.patch_shape_code(*shape))
+        sem.sem_set_mesh_corners(c2, mesh.ibool, mesh.ctrl, mesh.nglob)
+        sem.sem_set_material(c2, *mat)
+        info = sem.sem_patch_info(c2)
+        assert (info["bx"], info["by"], info["bz"]) == shape
+        check_forces(sweep_stride4(c2, u, 0), f_ref)
+    outs = []
+    for fused in (0, 1):
+        c3 = sem.sem_create(5, 0)
+        sem.sem_set_option(c3, sem.SEM_OPT_PATCH_SHAPE, sem.patch_shape_code(4, 2, 1))
+        sem.sem_set_mesh_corners(c3, mesh.ibool, mesh.ctrl, mesh.nglob)
+        sem.sem_set_material(c3, *mat)
+        sem.sem_set_option(c3, sem.SEM_OPT_FUSED_NEWMARK, fused)
+        sem.sem_set_dt(c3, sem.sem_suggest_dt(c3, 0.4))
+        sem.sem_set_source_nodes(c3, np.array([mesh.ibool[mesh.nspec // 2, 0]], dtype=np.int32),
+                                 np.array([[1e10, 2e10, -1e10]]), 10.0, 0.0)
+        sem.sem_set_receiver_nodes(c3, np.arange(0, mesh.nglob, 101, dtype=np.int32))
+        sem.sem_set_state(c3)
+        seis = sem.sem_run(c3, 14)
+        outs.append((seis,) + tuple(sem.sem_get_state(c3)))
+    assert np.abs(outs[0][0]).max() > 0
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
