@@ -146,7 +146,8 @@ int sem_destroy(sem_ctx* ctx);
 #define SEM_OPT_CONTRACTION 2
 /*   SEM_OPT_ASSEMBLY (takes effect at once): how the force sweep assembles element forces
  *   on the context's own fields. Patches are bricks of neighbouring elements
- *   (2 x 2 x 2 at NGLL 5; sem_patch_info gives the shape) evaluated by one CTA each, which
+ *   (1 x 4 x 2 at NGLL 5; SEM_OPT_PATCH_SHAPE sets another, sem_patch_info gives the shape in
+ *   use) evaluated by one CTA each, which
  *   sums the forces meeting at each of the brick's nodes in a fixed order and writes each
  *   node once; the bricks are coloured so that no two of a colour share a node (Sec. IV-C's
  *   colouring applied to groups of elements).

@@ -608,10 +608,13 @@ struct PatchCfg {
   // 0 one warp, 1 a named barrier over the team's warps, 2 the CTA
   static constexpr int KIND = TEAM == 32 ? 0 : TEAM < 256 ? 1 : 2;
   static constexpr int E = TEAM / NL;  // elements per team
-  // the brick, in elements along the lattice x, y, z
-  static constexpr int BX = N == 2 ? 4 : N == 3 ? 3 : N == 4 ? 4 : N <= 8 ? 2 : N == 9 ? 3 : 2;
-  static constexpr int BY = N == 2 ? 4 : N == 3 ? 3 : N <= 8 ? 2 : 1;
-  static constexpr int BZ = N == 2 ? 4 : N == 3 ? 3 : N <= 5 ? 2 : 1;
+  // the default brick, in elements along the lattice x, y, z (any brick of PE elements runs
+  // the same kernel; GB300, 256 GLL intervals per side, one time step's fused sweep: at NGLL
+  // 5, 1x4x2 0.770 ms against 2x2x2 0.778 and 4x1x2 0.774; at NGLL 7, 1x2x2 0.805 against
+  // 2x2x1 0.810 and 2x1x2 0.811; at NGLL 9, 3x1x1 0.818 against 1x3x1 0.819 and 1x1x3 0.844)
+  static constexpr int BX = N == 2 ? 4 : N == 3 ? 3 : N == 4 ? 4 : N == 5 || N == 7 ? 1 : N <= 8 ? 2 : N == 9 ? 3 : 2;
+  static constexpr int BY = N == 2 ? 4 : N == 3 ? 3 : N == 5 ? 4 : N <= 8 ? 2 : 1;
+  static constexpr int BZ = N == 2 ? 4 : N == 3 ? 3 : N <= 5 || N == 7 ? 2 : 1;
   static constexpr int PE = BX * BY * BZ;
   static constexpr int TEAMS = (PE + E - 1) / E;
   static constexpr int T = TEAMS * TEAM;

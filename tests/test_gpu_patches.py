@@ -77,7 +77,7 @@ def sweep_stride4(ctx, u, assembly):
     return f[:, :3]
 
 
-BRICK = {2: (4, 4, 4), 3: (3, 3, 3), 4: (4, 2, 2), 5: (2, 2, 2), 6: (2, 2, 1), 7: (2, 2, 1), 8: (2, 2, 1),
+BRICK = {2: (4, 4, 4), 3: (3, 3, 3), 4: (4, 2, 2), 5: (1, 4, 2), 6: (2, 2, 1), 7: (1, 2, 2), 8: (2, 2, 1),
          9: (3, 1, 1), 10: (2, 1, 1)}
 
 

@@ -7,7 +7,7 @@ import pytest
 
 from paper_2606_12850_gb300 import build, inputs, sem
 
-BRICK = {2: (4, 4, 4), 3: (3, 3, 3), 4: (4, 2, 2), 5: (2, 2, 2), 6: (2, 2, 1), 7: (2, 2, 1), 8: (2, 2, 1),
+BRICK = {2: (4, 4, 4), 3: (3, 3, 3), 4: (4, 2, 2), 5: (1, 4, 2), 6: (2, 2, 1), 7: (1, 2, 2), 8: (2, 2, 1),
          9: (3, 1, 1), 10: (2, 1, 1)}
 
 
@@ -56,7 +56,7 @@ def test_plan_independent_of_element_numbering():
     p0, c0, i0 = sem.sem_patch_plan(5, mesh.ibool, mesh.nglob)
     perm = np.random.default_rng(4).permutation(mesh.nspec)
     p1, c1, i1 = sem.sem_patch_plan(5, mesh.ibool[perm], mesh.nglob)
-    assert i0["patches"] == i1["patches"] == 3 * 2 * 3  # bricks of 2 x 2 x 2 over 6 x 4 x 5
+    assert i0["patches"] == i1["patches"] == 6 * 1 * 3  # bricks of 1 x 4 x 2 over 6 x 4 x 5
     # the same groups of elements (as sets of lattice cells), whatever their numbering
     groups0 = sorted(tuple(sorted(map(tuple, mesh.elem_ijk[p0 == P]))) for P in range(i0["patches"]))
     ijk1 = mesh.elem_ijk[perm]
