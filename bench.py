@@ -572,16 +572,26 @@ def measure_models(device: int, count: int = 16, steps: int = 50):
     b.synchronize()
     seq_ms = a.elapsed_time(b)
     group = sem.Group([s.ctx for s in setups])
-    group.step(12)
-    group.sync()
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    group.step(steps)
-    group.sync()
-    group_ms = 1e3 * (time.perf_counter() - t)
+
+    def group_time(mode):
+        group.set_option(sem.SEM_GROUP_MODE, mode)
+        group.step(12)
+        group.sync()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        group.step(steps)
+        group.sync()
+        return 1e3 * (time.perf_counter() - t)
+
+    persistent_ms = group_time(1)
+    info = group.info()
+    group_ms = group_time(0)  # the default mode
     return {"models": desc, "steps": steps, "nlocal_total": nloc, "sequential_ms": seq_ms, "group_ms": group_ms,
+            "group_mode": "graph branches (default)",
             "speedup": seq_ms / group_ms, "group_updates_per_s": nloc * steps / (group_ms * 1e-3),
-            "sequential_updates_per_s": nloc * steps / (seq_ms * 1e-3), "autotune": tuned,
+            "sequential_updates_per_s": nloc * steps / (seq_ms * 1e-3),
+            "persistent_ms": persistent_ms, "persistent_speedup": seq_ms / persistent_ms,
+            "persistent_sweep_launches_per_step": info["sweep_launches"], "autotune": tuned,
             "timing": "sequential: CUDA events on the models' stream; group: wall clock around "
                       "sem_group_step and sem_group_sync"}
 

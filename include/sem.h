@@ -449,17 +449,37 @@ int sem_profile_steps(sem_ctx* ctx, int nsteps, double* ms_out);
 
 /* Groups: several contexts on one GPU (different meshes, orders, shot counts) stepped
  * together. sem_group_step advances every context nsteps steps (no seismograms): one eager
- * step per context, then CUDA graphs in which every context's steps form a branch of their
- * own, so that small models run side by side instead of one after another; each context's
- * results equal those of sem_step on it alone, bit for bit. The contexts stay owned by the
- * caller, must outlive the group, and may be changed between calls (the graphs are rebuilt).
- * Asynchronous: every context's later calls are ordered after the group's work. */
+ * step per context, then CUDA graphs of the remaining steps. In the persistent mode
+ * (SEM_GROUP_MODE 1; used when every context has one shot, SEM_OPT_ASSEMBLY 0 and at most
+ * 64 patch colours, and the group at most 64 contexts) a step is the contexts'
+ * Newmark passes, ONE persistent force-sweep launch for all contexts of the same order and
+ * contraction form (CTAs take the patches of every model colour by colour from a device
+ * counter; a patch of colour c writes once its own model's colour c - 1 is done, a bounded
+ * wait: if one gives up, sem_group_sync returns SEM_ETIMEOUT), and the contexts' sources;
+ * otherwise (mode 0, the default: measured faster on GB300 for 16 cubes of 8^3 .. 40^3 at
+ * NGLL 4 .. 8, 151 ms against 172 ms for 50 steps) every context's steps form a branch of
+ * their own in the graph, so that small models run side by side. Either way each context's
+ * results equal those of sem_step
+ * on it alone, bit for bit. The contexts stay owned by the caller, must outlive the group,
+ * and may be changed between calls (the graphs are rebuilt). Asynchronous: every context's
+ * later calls are ordered after the group's work. */
 typedef struct sem_group sem_group;
 int sem_group_create(sem_group** out, int nctx, sem_ctx* const* ctxs);
 int sem_group_destroy(sem_group* group);
 int sem_group_step(sem_group* group, int nsteps);
 int sem_group_sync(sem_group* group);
 const char* sem_group_last_error(const sem_group* group);
+/* Group options: SEM_GROUP_MODE (0 graph branches, 1 persistent sweeps); SEM_GROUP_STALL_TEST
+ * (failure-detection test, one-shot: 1 makes the first persistent step of the next
+ * sem_group_step with more than one step wait for counts that never arrive, so that its
+ * bounded waits give up and sem_group_sync returns SEM_ETIMEOUT; the steps after it run
+ * normally). SEM_EINVAL for an unknown option or value. */
+#define SEM_GROUP_MODE 1
+#define SEM_GROUP_STALL_TEST 2
+int sem_group_set_option(sem_group* group, int option, long long value);
+/* out[0] = 1 if the group's steps run as persistent sweeps, out[1] = the sweep launches per
+ * step (distinct orders and contraction forms). */
+int sem_group_info(sem_group* group, int* out);
 
 /* Kinetic and potential energy of the current state in float64:
  * out[0] = 1/2 sum_I M_I |v_I|^2, out[1] = 1/2 u^T K u. Synchronous. */

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <set>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1999,6 +2001,16 @@ struct sem_group {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kStepsPerGraph steps of every context; one step
   std::vector<unsigned long long> gen;     // the contexts' generations the graphs were built on
   std::string err;
+  int mode = 0;                            // SEM_GROUP_MODE: 0 graph branches, 1 persistent sweeps
+  unsigned int stall = 0;                  // SEM_GROUP_STALL_TEST (one-shot, eager steps only)
+  bool persistent = false;                 // the graphs hold persistent sweeps
+  struct Sweep {                           // one persistent sweep: the contexts of one order and form
+    int ngll = 0, variant = 0, nseg = 0, nitems = 0, nmodels = 0;
+    GroupModel* d_models = nullptr;
+    GroupSeg* d_segs = nullptr;
+  };
+  std::vector<Sweep> sweeps;
+  GroupSync* d_sync = nullptr;
 };
 
 namespace {
@@ -2017,6 +2029,118 @@ void group_drop(sem_group* g) {
       cudaGraphExecDestroy(x);
       x = nullptr;
     }
+  for (auto& sw : g->sweeps) {
+    if (sw.d_models) cudaFree(sw.d_models);
+    if (sw.d_segs) cudaFree(sw.d_segs);
+  }
+  g->sweeps.clear();
+}
+
+// Whether the group's steps can run as persistent sweeps: every context one shot on the
+// per-colour patch assembly, at most kMaxSweepColors patch colours.
+bool group_persistent_ok(const sem_group* g) {
+  if (g->mode != 1 || g->ctx.size() > static_cast<size_t>(kMaxGroupModels)) return false;
+  for (const sem_ctx* c : g->ctx)
+    if (c->shots != 1 || c->assembly != 0 || c->npatch <= 0 ||
+        c->pcolor_off.size() > static_cast<size_t>(kMaxSweepColors) + 1)
+      return false;
+  return true;
+}
+
+// The device tables of the persistent sweeps: contexts grouped by (order, contraction form);
+// per sweep its models and its runs of items, colour-major (colour c of every model before
+// colour c + 1).
+int group_tables(sem_group* g) {
+  std::map<std::pair<int, int>, std::vector<int>> by;
+  for (size_t i = 0; i < g->ctx.size(); ++i) by[{g->ctx[i]->ngll, g->ctx[i]->variant}].push_back(static_cast<int>(i));
+  for (const auto& kv : by) {
+    sem_group::Sweep sw;
+    sw.ngll = kv.first.first;
+    sw.variant = kv.first.second;
+    std::vector<GroupModel> models;
+    int maxc = 0;
+    for (int i : kv.second) {
+      const sem_ctx* c = g->ctx[i];
+      GroupModel m{};
+      m.rec = c->d_rec;
+      m.desc = c->d_pdesc;
+      m.slots = c->d_pslots;
+      m.words = c->d_pwords;
+      m.u = c->d_u;
+      m.f = c->d_a;
+      m.color_end = c->d_pcolor_end;
+      m.ncolors = static_cast<int>(c->pcolor_off.size()) - 1;
+      maxc = std::max(maxc, m.ncolors);
+      models.push_back(m);
+    }
+    std::vector<GroupSeg> segs;
+    int items = 0;
+    for (int col = 0; col < maxc; ++col)
+      for (size_t k = 0; k < kv.second.size(); ++k) {
+        const sem_ctx* c = g->ctx[kv.second[k]];
+        if (col >= models[k].ncolors) continue;
+        const int n = c->pcolor_off[col + 1] - c->pcolor_off[col];
+        if (n <= 0) continue;
+        segs.push_back(GroupSeg{items, static_cast<int>(k), col, c->pcolor_off[col]});
+        items += n;
+      }
+    sw.nmodels = static_cast<int>(models.size());
+    sw.nseg = static_cast<int>(segs.size());
+    sw.nitems = items;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&sw.d_models), models.size() * sizeof(GroupModel));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sw.d_segs), std::max<size_t>(1, segs.size()) * sizeof(GroupSeg));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(sw.d_models, models.data(), models.size() * sizeof(GroupModel), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !segs.empty())
+      e = cudaMemcpy(sw.d_segs, segs.data(), segs.size() * sizeof(GroupSeg), cudaMemcpyHostToDevice);
+    g->sweeps.push_back(sw);
+    if (e != cudaSuccess) return group_fail(g, SEM_ECUDA, std::string("group tables: ") + cudaGetErrorString(e));
+  }
+  if (!g->d_sync) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&g->d_sync), sizeof(GroupSync));
+    if (e == cudaSuccess) e = cudaMemset(g->d_sync, 0, sizeof(GroupSync));
+    if (e != cudaSuccess) return group_fail(g, SEM_ECUDA, std::string("group counters: ") + cudaGetErrorString(e));
+  }
+  return SEM_OK;
+}
+
+// One pending step of every context on the group's stream with the force sweeps persistent:
+// the contexts' Newmark passes, one sweep launch per (order, form), the contexts' sources.
+int group_enqueue_persistent_step(sem_group* g, unsigned int stall) {
+  for (sem_ctx* c : g->ctx)
+    if (launch_fused_newmark(problem(c), g->stream)) return group_fail(g, SEM_ECUDA, "group Newmark pass");
+  for (const auto& sw : g->sweeps) {
+    GroupLaunch L{};
+    L.models = sw.d_models;
+    L.segs = sw.d_segs;
+    L.nseg = sw.nseg;
+    L.nitems = sw.nitems;
+    L.nmodels = sw.nmodels;
+    L.variant = sw.variant;
+    L.stall = stall;
+    L.sync = g->d_sync;
+    if (launch_group_sweep(sw.ngll, L, g->stream)) return group_fail(g, SEM_ECUDA, "group sweep launch");
+  }
+  for (sem_ctx* c : g->ctx)
+    if (launch_sources_record(problem(c), g->stream)) return group_fail(g, SEM_ECUDA, "group sources");
+  return SEM_OK;
+}
+
+// A graph of `steps` persistent group steps.
+int group_build_persistent(sem_group* g, int which, int steps) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return group_fail(g, SEM_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  int rc = SEM_OK;
+  for (int s = 0; s < steps && rc == SEM_OK; ++s) rc = group_enqueue_persistent_step(g, 0u);
+  e = cudaStreamEndCapture(g->stream, &graph);
+  if (rc == SEM_OK && e != cudaSuccess) rc = group_fail(g, SEM_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  if (rc == SEM_OK) {
+    e = cudaGraphInstantiate(&g->graph[which], graph, 0);
+    if (e != cudaSuccess) rc = group_fail(g, SEM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  if (graph) cudaGraphDestroy(graph);
+  return rc;
 }
 
 // One graph advancing every context by `steps` pending steps, each context on a branch of
@@ -2089,6 +2213,7 @@ int sem_group_destroy(sem_group* g) {
   cudaSetDevice(g->device);
   if (g->stream) cudaStreamSynchronize(g->stream);
   group_drop(g);
+  if (g->d_sync) cudaFree(g->d_sync);
   for (cudaEvent_t e : g->ev)
     if (e) cudaEventDestroy(e);
   for (cudaStream_t s : g->branch)
@@ -2116,19 +2241,31 @@ int sem_group_step(sem_group* g, int nsteps) {
       return group_fail(g, SEM_ECUDA, "ordering the group after its contexts");
   }
   int left = nsteps - 1;
-  bool stale = g->gen.size() != n;
+  const bool persistent = group_persistent_ok(g);
+  bool stale = g->gen.size() != n || g->persistent != persistent;
   for (size_t i = 0; i < n && !stale; ++i) stale = g->gen[i] != g->ctx[i]->generation;
   if (stale) {
     group_drop(g);
     g->gen.clear();
     for (sem_ctx* c : g->ctx) g->gen.push_back(c->generation);
+    g->persistent = persistent;
+    if (persistent) {
+      int r = group_tables(g);
+      if (r) return r;
+    }
+  }
+  if (persistent && g->stall && left > 0) {  // failure-detection test: one eager step whose waits give up
+    int r = group_enqueue_persistent_step(g, g->stall);
+    g->stall = 0;
+    if (r) return r;
+    --left;
   }
   if (left >= kStepsPerGraph && !g->graph[0]) {
-    int r = group_build(g, 0, kStepsPerGraph);
+    int r = persistent ? group_build_persistent(g, 0, kStepsPerGraph) : group_build(g, 0, kStepsPerGraph);
     if (r) return r;
   }
   if (left % kStepsPerGraph && !g->graph[1]) {
-    int r = group_build(g, 1, 1);
+    int r = persistent ? group_build_persistent(g, 1, 1) : group_build(g, 1, 1);
     if (r) return r;
   }
   for (; left >= kStepsPerGraph; left -= kStepsPerGraph)
@@ -2150,6 +2287,41 @@ int sem_group_sync(sem_group* g) {
   cudaSetDevice(g->device);
   cudaError_t e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return group_fail(g, SEM_ECUDA, cudaGetErrorString(e));
+  if (g->d_sync) {
+    int err = 0;
+    e = cudaMemcpy(&err, &g->d_sync->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return group_fail(g, SEM_ECUDA, cudaGetErrorString(e));
+    if (err) {
+      cudaMemset(&g->d_sync->err, 0, sizeof(int));
+      return group_fail(g, SEM_ETIMEOUT,
+                        "a bounded wait of the group sweep gave up (the forces of that step are incomplete)");
+    }
+  }
+  return SEM_OK;
+}
+
+int sem_group_set_option(sem_group* g, int option, long long value) {
+  if (!g) return group_fail(nullptr, SEM_EINVAL, "null group");
+  switch (option) {
+    case SEM_GROUP_MODE:
+      if (value < 0 || value > 1) return group_fail(g, SEM_EINVAL, "group mode must be 0 (graph branches) or 1 (persistent)");
+      g->mode = static_cast<int>(value);
+      return SEM_OK;
+    case SEM_GROUP_STALL_TEST:
+      if (value < 0 || value > 1) return group_fail(g, SEM_EINVAL, "stall test must be 0 or 1");
+      g->stall = static_cast<unsigned int>(value);
+      return SEM_OK;
+    default:
+      return group_fail(g, SEM_EINVAL, "unknown group option " + std::to_string(option));
+  }
+}
+
+int sem_group_info(sem_group* g, int* out) {
+  if (!g || !out) return group_fail(g, SEM_EINVAL, "sem_group_info: bad arguments");
+  out[0] = group_persistent_ok(g) ? 1 : 0;
+  std::set<std::pair<int, int>> keys;
+  for (const sem_ctx* c : g->ctx) keys.insert({c->ngll, c->variant});
+  out[1] = out[0] ? static_cast<int>(keys.size()) : 0;
   return SEM_OK;
 }
 

@@ -1464,6 +1464,135 @@ __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
 }
 
 // ---------------------------------------------------------------------------------------
+// Group sweep: the persistent form over several models of one order (see GroupLaunch). CTAs
+// take items in order from sync->next; an item is located by a binary search over the runs
+// of items (GroupSeg), the patch of its model evaluated as in sweep_one_patch, and counted
+// into sync->done[model][colour]. Every item waits only on items of its own model taken
+// before it, so the sweep completes however many CTAs are resident; a bounded wait that
+// gives up sets sync->err and ends its CTA (the host reports SEM_ETIMEOUT).
+// ---------------------------------------------------------------------------------------
+struct GroupShared {
+  PatchDesc d;
+  GroupModel m;
+  int model;
+  int color;
+  int next;   // the item taken next
+  int ready;
+  int abort;
+};
+
+__device__ __forceinline__ int group_seg_of(const GroupSeg* __restrict__ segs, int nseg, int item) {
+  int lo = 0, hi = nseg - 1;  // the last run whose first item is <= item
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].item0 <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Patches of colour c - 1 of a model needed before its patch of colour c may write.
+__device__ __forceinline__ unsigned int group_prior_count(const GroupModel& m, int c, unsigned int stall) {
+  return stall ? 0xFFFFFFFFu
+               : static_cast<unsigned int>(__ldg(m.color_end + c - 1) - (c > 1 ? __ldg(m.color_end + c - 2) : 0));
+}
+
+template <int N>
+__device__ __forceinline__ void group_prefetch_item(const GroupLaunch& L, int item) {
+  using C = PatchCfg<N>;
+  if (item < 0 || item >= L.nitems || threadIdx.x >= 32) return;
+  const GroupSeg sg = L.segs[group_seg_of(L.segs, L.nseg, item)];
+  const GroupModel& m = L.models[sg.model];
+  const PatchDesc dn = m.desc[sg.p0 + item - sg.item0];
+  if (static_cast<int>(threadIdx.x) < dn.nelem)
+    prefetch_l2(m.rec + static_cast<size_t>(dn.slot0 + threadIdx.x) * C::REC, kForceFields * C::NP * sizeof(float));
+}
+
+template <int N, bool LO>
+__device__ __noinline__ int group_one_item(int item, const GroupLaunch L, GroupShared* sh, float* wsb) {
+  __syncthreads();  // every thread is done with sh before it is replaced
+  if (threadIdx.x == 0) {
+    const GroupSeg sg = L.segs[group_seg_of(L.segs, L.nseg, item)];
+    sh->m = L.models[sg.model];
+    sh->d = sh->m.desc[sg.p0 + item - sg.item0];
+    sh->model = sg.model;
+    sh->color = sg.color;
+    sh->next = static_cast<int>(atomicAdd(&L.sync->next, 1u));
+    const int c = sg.color;
+    sh->ready = c == 0 || ld_acquire_gpu(&L.sync->done[sg.model * kMaxSweepColors + c - 1]) >=
+                              group_prior_count(sh->m, c, L.stall);
+  }
+  __syncthreads();
+  const PatchDesc& d = sh->d;
+  const GroupModel& m = sh->m;
+  const SweepNewmark none{};
+  group_prefetch_item<N>(L, sh->next);
+  float4* f = reinterpret_cast<float4*>(m.f);
+  patch_gather_compute<N, LO>(d, m.rec, reinterpret_cast<const float4*>(m.u), wsb, false);
+  const int c = sh->color;
+  unsigned int* done = &L.sync->done[sh->model * kMaxSweepColors];
+  if (sh->ready) {
+    patch_write_alone<N, true>(d, f, wsb, none);
+    __syncthreads();
+  } else {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned int need = group_prior_count(m, c, L.stall);
+      unsigned int spins = 0;
+      while (ld_acquire_gpu(&done[c - 1]) < need) {
+        if (++spins > kSweepSpinLimit) {
+          atomicExch(&L.sync->err, 1);
+          sh->abort = 1;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __syncthreads();  // the wait is over for the CTA
+    if (sh->abort) return -1;
+    patch_write_alone<N, true>(d, f, wsb, none);
+  }
+  patch_write_shared<N, true>(d, m.slots, m.words, f, wsb, none);
+  __syncthreads();  // all of the patch's writes issued before it counts as done
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&done[c], 1u);
+  }
+  return sh->next;
+}
+
+template <int N, bool LO>
+__global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS) group_sweep_kernel(const GroupLaunch L) {
+  extern __shared__ float4 smem4[];
+  float* wsb = reinterpret_cast<float*>(smem4);
+  __shared__ GroupShared sh;
+  wait_prerequisite_grid();  // the previous sweep's counter reset and the previous grids' u, f
+  if (threadIdx.x == 0) {
+    sh.next = static_cast<int>(atomicAdd(&L.sync->next, 1u));
+    sh.abort = 0;
+    sh.ready = 0;
+  }
+  __syncthreads();
+  int item = sh.next;
+  group_prefetch_item<N>(L, item);
+  while (item >= 0 && item < L.nitems) item = group_one_item<N, LO>(item, L, &sh, wsb);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    sh.ready = atomicAdd(&L.sync->exited, 1u) == gridDim.x - 1;  // every CTA has left: reset
+  }
+  __syncthreads();
+  if (sh.ready) {
+    for (int t = threadIdx.x; t < L.nmodels * kMaxSweepColors; t += blockDim.x) L.sync->done[t] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      L.sync->next = 0u;
+      L.sync->exited = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Material sensitivities (the discrete adjoint of the explicit scheme): at one adjoint step,
 // for every local point q of every element
 //   g_rho[q]   += c_m * w_q J_q lam_I . (u_hi - 2 u_mid + u_lo)_I          (I = ibool(q))
@@ -1727,6 +1856,41 @@ int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
   }
 }
 
+template <bool LO>
+int launch_group_lo(const GroupLaunch& L, cudaStream_t s) {
+  using C = PatchCfg<SEM_NGLL>;
+  static std::atomic<unsigned long long> attr_done{0};
+  static std::atomic<int> resident[64];  // CTAs per SM, per device
+  if (int r = raise_smem_limit(attr_done, group_sweep_kernel<SEM_NGLL, LO>, C::SMEM)) return r;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = resident[dev & 63].load();
+  if (per_sm <= 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, group_sweep_kernel<SEM_NGLL, LO>, C::T,
+                                                                  C::SMEM);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    resident[dev & 63].store(per_sm);
+  }
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return static_cast<int>(e);
+  cudaLaunchConfig_t cfg = {};
+  // all CTAs resident at once (a CTA may wait for items other CTAs hold), and no more than
+  // there are items
+  const int grid = std::min(sms * per_sm, std::max(1, L.nitems));
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(C::T);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return static_cast<int>(cudaLaunchKernelEx(&cfg, group_sweep_kernel<SEM_NGLL, LO>, L));
+}
+
 int launch_patch_n(const PatchLaunch& L, cudaStream_t s) {
   if (L.sync ? L.npatch <= 0 : L.p1 <= L.p0) return 0;
   using C = ForceCfg<SEM_NGLL>;
@@ -1784,6 +1948,14 @@ int SEM_CAT(forces_smem_bytes_, SEM_NGLL)() { return ForceCfg<SEM_NGLL>::SMEM_FL
 
 int SEM_CAT(launch_patch_forces_, SEM_NGLL)(const PatchLaunch& L, void* stream) {
   return launch_patch_n(L, static_cast<cudaStream_t>(stream));
+}
+
+int SEM_CAT(launch_group_sweep_, SEM_NGLL)(const GroupLaunch& L, void* stream) {
+  if (L.nitems <= 0) return 0;
+  using C = ForceCfg<SEM_NGLL>;
+  const bool lo = L.variant == 0 ? C::LINE_OWNERS : L.variant == 1;
+  return lo ? launch_group_lo<true>(L, static_cast<cudaStream_t>(stream))
+            : launch_group_lo<false>(L, static_cast<cudaStream_t>(stream));
 }
 
 void SEM_CAT(patch_layout_, SEM_NGLL)(int* es, int* ts, int* e) {

@@ -206,6 +206,47 @@ struct SweepSync {
   int pad;
   unsigned int done[kMaxSweepColors];
 };
+// One persistent sweep over the patches of several models of one order (a group step):
+// items are the patches of every model, colour-major (colour 0 of every model, then colour
+// 1, ...); a patch of colour c writes once every patch of colour c - 1 of its own model has
+// finished. Models and runs of items live in device memory.
+constexpr int kMaxGroupModels = 64;
+struct GroupModel {
+  const float* rec;
+  const PatchDesc* desc;
+  const uint16_t* slots;
+  const uint16_t* words;
+  const float* u;        // [nglob][4]
+  float* f;              // [nglob][4]
+  const int* color_end;  // per colour, the end of its patch range (model-local patches)
+  int ncolors;
+  int pad;
+};
+struct GroupSeg {  // a run of consecutive items: patches [p0, p0 + count) of one (model, colour)
+  int item0;
+  int model;
+  int color;
+  int p0;
+};
+struct GroupSync {
+  unsigned int next;
+  unsigned int exited;
+  int err;
+  int pad;
+  unsigned int done[kMaxGroupModels * kMaxSweepColors];  // [model][colour] finished patches
+};
+struct GroupLaunch {
+  const GroupModel* models;
+  const GroupSeg* segs;
+  int nseg;
+  int nitems;
+  int nmodels;
+  int variant;       // contraction form as in ForceLaunch
+  unsigned int stall;  // a count that never arrives (tests)
+  GroupSync* sync;
+};
+int launch_group_sweep(int ngll, const GroupLaunch& launch, void* stream);
+
 struct PatchLaunch {
   const float* rec;
   const PatchDesc* desc;

@@ -16,6 +16,7 @@ namespace semgb {
   int launch_forces_##n(const ForceLaunch& L, void* stream);                                              \
   int forces_smem_bytes_##n();                                                                            \
   int launch_patch_forces_##n(const PatchLaunch& L, void* stream);                                        \
+  int launch_group_sweep_##n(const GroupLaunch& L, void* stream);                                         \
   void patch_shape_##n(PatchShape* out);                                                                  \
   void patch_layout_##n(int* es, int* ts, int* e);                                                        \
   int launch_sensitivity_##n(const float* rec, const int* perm, const float* lam, const float* u_lo,       \
@@ -47,6 +48,13 @@ SEM_DECLARE_ORDER(10)
 
 int upload_basis(int n, const double* w, const double* h, void* stream) {
 #define SEM_CALL(k) upload_basis_##k(w, h, stream, n)
+  SEM_ORDER_SWITCH(n, SEM_CALL)
+#undef SEM_CALL
+  return static_cast<int>(cudaErrorInvalidValue);
+}
+
+int launch_group_sweep(int n, const GroupLaunch& L, void* stream) {
+#define SEM_CALL(k) launch_group_sweep_##k(L, stream)
   SEM_ORDER_SWITCH(n, SEM_CALL)
 #undef SEM_CALL
   return static_cast<int>(cudaErrorInvalidValue);

@@ -84,6 +84,8 @@ SIGNATURES = {
     "sem_group_step": (_I, [_P, _I]),
     "sem_group_sync": (_I, [_P]),
     "sem_group_last_error": (ctypes.c_char_p, [_P]),
+    "sem_group_set_option": (_I, [_P, _I, ctypes.c_longlong]),
+    "sem_group_info": (_I, [_P, _P]),
     "sem_info": (_I, [_P, _P]),
     "sem_color_counts": (_I, [_P, _P]),
     "sem_patch_info": (_I, [_P, _P]),
@@ -278,6 +280,8 @@ SEM_OPT_NODE_ORDER = 5
 SEM_OPT_FUSED_NEWMARK = 6
 SEM_OPT_SHOT_PAIRS = 7
 SEM_OPT_PATCH_SHAPE = 8
+SEM_GROUP_MODE = 1
+SEM_GROUP_STALL_TEST = 2
 
 
 def sem_set_option(ctx: Ctx, option: int, value: int):
@@ -630,6 +634,14 @@ class Group:
 
     def sync(self):
         self._check(lib().sem_group_sync(self.handle), "sem_group_sync")
+
+    def set_option(self, option: int, value: int):
+        self._check(lib().sem_group_set_option(self.handle, int(option), int(value)), "sem_group_set_option")
+
+    def info(self) -> dict:
+        out = (ctypes.c_int * 2)()
+        self._check(lib().sem_group_info(self.handle, out), "sem_group_info")
+        return {"persistent": bool(out[0]), "sweep_launches": int(out[1])}
 
     def __del__(self):
         if getattr(self, "handle", None):

@@ -28,7 +28,10 @@ def fresh(w):
     return sem.setup_workload(w)
 
 
-def test_group_equals_separate_runs():
+@pytest.mark.parametrize("mode", [1, 0])
+def test_group_equals_separate_runs(mode):
+    """Persistent sweeps (one launch per order for all contexts; mode 1) and graph branches
+    (mode 0) both give every context the state of stepping it alone, bit for bit."""
     ws = workloads()
     alone = []
     for w in ws:
@@ -37,6 +40,11 @@ def test_group_equals_separate_runs():
         alone.append(sem.sem_get_state(s.ctx, want=(True, False, False))[0])
     setups = [fresh(w) for w in ws]
     group = sem.Group([s.ctx for s in setups])
+    group.set_option(sem.SEM_GROUP_MODE, mode)
+    info = group.info()
+    assert info["persistent"] == (mode == 1)
+    if mode == 1:
+        assert info["sweep_launches"] == 3  # NGLL 4, 5 and 6
     group.step(27)
     group.sync()
     for s, ref in zip(setups, alone):
@@ -73,3 +81,40 @@ def test_autotune_forms_meet_parity(oracle):
         sem.sem_sync(s.ctx)
         f = f.cpu().numpy()
         assert np.linalg.norm(f - ref) / np.linalg.norm(ref) <= 2e-6, form
+
+
+def test_group_of_one_order_is_one_sweep_launch():
+    """Several models of one order (different sizes, one with a scrambled element order and
+    a point source) in one persistent sweep launch per step, equal to separate runs."""
+    ws = [inputs.layered_cube(5, n=n, side=600.0, nsteps=30, nrec_side=2) for n in (2, 3, 5)]
+    alone = []
+    for w in ws:
+        s = fresh(w)
+        sem.sem_step(s.ctx, 23)
+        alone.append(sem.sem_get_state(s.ctx))
+    setups = [fresh(w) for w in ws]
+    group = sem.Group([s.ctx for s in setups])
+    assert group.info() == {"persistent": False, "sweep_launches": 0}  # graph branches by default
+    group.set_option(sem.SEM_GROUP_MODE, 1)
+    assert group.info() == {"persistent": True, "sweep_launches": 1}
+    group.step(23)
+    group.sync()
+    for s, ref in zip(setups, alone):
+        for x, y in zip(sem.sem_get_state(s.ctx), ref):
+            assert np.array_equal(x, y)
+
+
+def test_group_sweep_wait_gives_up_and_recovers():
+    """Failure detection without a fault: a persistent group step whose waits target counts
+    that never arrive gives up within its bound, sem_group_sync reports SEM_ETIMEOUT, and the
+    group's next steps run."""
+    setups = [fresh(w) for w in workloads()[:2]]
+    group = sem.Group([s.ctx for s in setups])
+    group.set_option(sem.SEM_GROUP_MODE, 1)
+    group.set_option(sem.SEM_GROUP_STALL_TEST, 1)
+    group.step(3)
+    with pytest.raises(sem.SemError) as ei:
+        group.sync()
+    assert ei.value.code == -5 and "gave up" in str(ei.value)
+    group.step(4)
+    group.sync()
