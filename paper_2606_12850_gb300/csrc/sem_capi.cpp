@@ -85,6 +85,8 @@ struct sem_ctx {
   float* d_grad32 = nullptr;      // [3][nlocal] float32 partial sums, flushed into d_grad
   int since_flush = 0;            // adjoint steps accumulated in d_grad32
   int node_order = 0;             // SEM_OPT_NODE_ORDER: device state arrays in caller (0) or internal (1) order
+  PatchRecv* d_precv = nullptr;   // receivers by the patch that touches their node last
+  int* d_precv_range = nullptr;   // [npatch][2] first, count into d_precv
   int* d_rnode = nullptr;         // distinct receiver nodes (internal ids)
   int* d_roff = nullptr;          // their receivers: d_rlist[d_roff[t] .. d_roff[t+1])
   int* d_rlist = nullptr;
@@ -108,6 +110,10 @@ struct sem_ctx {
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
   bool graph_fused = false;           // the graph holds steps of the fused sweep
+  cudaGraphExec_t graph_snap = nullptr;  // fused steps that also store the displacement
+  cudaGraphExec_t graph_adj = nullptr;   // adjoint steps indexed by the device counter
+  const float* graph_adj_lam = nullptr;  // d_lam when graph_adj was captured
+  bool graph_adj_G = false;              // graph_adj injects receiver residuals
   unsigned long long generation = 0;  // bumped whenever launches captured in graphs go stale
   int variant = 0;                    // force-kernel contraction form (sem_autotune)
 };
@@ -156,7 +162,7 @@ int dev_alloc(sem_ctx* c, T** p, size_t count) {
 void free_device(sem_ctx* c) {
   void* ptrs[] = {c->d_rec, c->d_order, c->d_elist, c->d_perm, c->d_node_new, c->d_pdesc, c->d_pslots, c->d_pwords, c->d_pcolor_end, c->d_sync, c->d_psrc, c->d_u, c->d_v,
                   c->d_a, c->d_minv, c->d_f, c->d_partials, c->d_lam, c->d_lam_old, c->d_lamF, c->d_grad,
-                  c->d_grad32, c->d_rnode, c->d_roff, c->d_rlist,
+                  c->d_grad32, c->d_precv, c->d_precv_range, c->d_rnode, c->d_roff, c->d_rlist,
                   c->d_ctl, c->d_src_node, c->d_src_shot, c->d_src_force, c->d_rec_node};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -176,6 +182,8 @@ void free_device(sem_ctx* c) {
   c->d_grad = nullptr;
   c->d_grad32 = nullptr;
   c->d_rnode = c->d_roff = c->d_rlist = nullptr;
+  c->d_precv = nullptr;
+  c->d_precv_range = nullptr;
   c->nrnodes = 0;
   c->adjoint = false;
   c->d_partials = nullptr;
@@ -190,6 +198,10 @@ void free_device(sem_ctx* c) {
 void drop_graph(sem_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
+  if (c->graph_snap) cudaGraphExecDestroy(c->graph_snap);
+  c->graph_snap = nullptr;
+  if (c->graph_adj) cudaGraphExecDestroy(c->graph_adj);
+  c->graph_adj = nullptr;
   c->graph_valid = false;
   ++c->generation;
 }
@@ -443,7 +455,7 @@ int check_sweep_timeout(sem_ctx* c) {
 // The float32 sensitivity partials of the steps since the last flush, added into the float64
 // accumulators (every kFlushEvery adjoint steps, at the end of a segment, and before the
 // gradients are read: a float32 sum of a few dozen terms keeps about six digits).
-constexpr int kFlushEvery = 64;
+constexpr int kFlushEvery = 60;  // a multiple of kStepsPerGraph
 int flush_gradients(sem_ctx* c) {
   if (!c->since_flush) return SEM_OK;
   const long long n = 3ll * c->nspec * c->ngll * c->ngll * c->ngll;
@@ -681,6 +693,7 @@ int sem_set_option(sem_ctx* c, int option, long long value) {
     case SEM_OPT_NODE_ORDER:
       if (value < 0 || value > 1) return fail(c, SEM_EINVAL, "node order must be 0 (caller) or 1 (internal)");
       c->node_order = static_cast<int>(value);
+      drop_graph(c);  // the snapshot graph maps nodes in this order
       return SEM_OK;
     case SEM_OPT_SWEEP_STALL_TEST:
       if (value < 0 || value > 1) return fail(c, SEM_EINVAL, "stall test must be 0 or 1");
@@ -1445,6 +1458,25 @@ int sem_set_receiver_nodes(sem_ctx* c, int nrec, const int32_t* node) {
     SEM_CUDA(c, cudaMemcpy(c->d_roff, roff.data(), roff.size() * sizeof(int), cudaMemcpyHostToDevice));
     SEM_CUDA(c, cudaMemcpy(c->d_rlist, byn.data(), byn.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
+  // the same receivers by the patch that touches their node last (the fused adjoint sweep),
+  // ascending receiver index within a patch
+  if (c->npatch > 0) {
+    std::vector<std::pair<int, int>> by_patch;  // (patch, receiver)
+    for (int k = 0; k < nrec; ++k) by_patch.emplace_back(c->last_patch[internal[k]], k);
+    std::sort(by_patch.begin(), by_patch.end());
+    std::vector<PatchRecv> list(by_patch.size());
+    std::vector<int> range(2 * static_cast<size_t>(c->npatch), 0);
+    for (size_t k = 0; k < by_patch.size(); ++k) {
+      const int P = by_patch[k].first, rr = by_patch[k].second;
+      list[k] = PatchRecv{internal[rr], rr};
+      if (range[2 * P + 1] == 0) range[2 * P] = static_cast<int>(k);
+      ++range[2 * P + 1];
+    }
+    if ((r = dev_alloc(c, &c->d_precv, list.size())) || (r = dev_alloc(c, &c->d_precv_range, range.size()))) return r;
+    if (!list.empty())
+      SEM_CUDA(c, cudaMemcpy(c->d_precv, list.data(), list.size() * sizeof(PatchRecv), cudaMemcpyHostToDevice));
+    SEM_CUDA(c, cudaMemcpy(c->d_precv_range, range.data(), range.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   drop_graph(c);
   return SEM_OK;
 }
@@ -1573,19 +1605,38 @@ int sem_run_record_snapshots(sem_ctx* c, int nsteps, float* seis_dev, float* u_d
     return SEM_OK;
   }
   // fused sweep: the predictor once, then per step the receivers sample u^{n+1}, which is
-  // also the snapshot (the sweep overwrites it with the next prediction), then the sweep
+  // also the snapshot (the sweep overwrites it with the next prediction), then the sweep; the
+  // snapshot slot comes from the device's step counter, so the steps replay as graphs
   if (nsteps == 0) return SEM_OK;
   if ((r = finish_state(c))) return r;
-  SEM_LAUNCH(c, launch_set_ctl(c->d_ctl, c->steps, seis_dev ? nsteps : 0, seis_dev, c->stream));
+  SEM_LAUNCH(c, launch_set_ctl(c->d_ctl, c->steps, seis_dev ? nsteps : 0, seis_dev, c->stream, u_dev,
+                               static_cast<long long>(per)));
   SEM_LAUNCH(c, launch_predictor(problem(c), c->stream));
-  for (int k = 0; k < nsteps; ++k) {
+  auto snap_step = [&](int mode) -> int {
     DevProblem q = problem(c);
     q.nsrc = 0;
     SEM_LAUNCH(c, launch_sources_record(q, c->stream));
-    SEM_LAUNCH(c, launch_pack(c->d_u, u_dev + k * per, perm, c->nglob, c->shots, c->stream));
-    const SweepNewmark nm = sweep_newmark(c, k + 1 < nsteps ? 1 : 2);
-    if ((r = forces_all_colors(c, c->d_u, c->d_a, kNodeStride, c->shots, &nm))) return r;
+    SEM_LAUNCH(c, launch_snapshot(c->d_u, c->d_ctl, perm, c->nglob, c->shots, c->stream));
+    const SweepNewmark nm = sweep_newmark(c, mode);
+    return forces_all_colors(c, c->d_u, c->d_a, kNodeStride, c->shots, &nm);
+  };
+  int left = nsteps - 1;
+  if (left >= kStepsPerGraph && !c->graph_snap) {
+    cudaGraph_t g = nullptr;
+    SEM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = SEM_OK;
+    for (int s = 0; s < kStepsPerGraph && rc == SEM_OK; ++s) rc = snap_step(1);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc == SEM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_snap, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(c, e, "snapshot graph");
   }
+  for (; left >= kStepsPerGraph; left -= kStepsPerGraph) SEM_CUDA(c, cudaGraphLaunch(c->graph_snap, c->stream));
+  for (; left > 0; --left)
+    if ((r = snap_step(1))) return r;
+  if ((r = snap_step(2))) return r;
+  SEM_LAUNCH(c, launch_set_ctl(c->d_ctl, c->steps + nsteps, 0, nullptr, c->stream));  // forget the buffers
   c->steps += nsteps;
   return SEM_OK;
 }
@@ -1769,16 +1820,45 @@ int sem_adjoint_begin(sem_ctx* c) {
   return SEM_OK;
 }
 
+// Whether adjoint steps run the leapfrog inside the sweep of lam (the per-colour patch
+// sweep with SEM_OPT_FUSED_NEWMARK not 0, and the receivers' patch lists built).
+bool fused_adjoint(const sem_ctx* c) {
+  return c->fuse_newmark != 0 && c->assembly == 0 && c->npatch > 0 && (c->nrec == 0 || c->d_precv_range);
+}
+
+// One adjoint step: the sweep of lam with, at each node's last touch, the residual injection
+// and the leapfrog (or, unfused, the sweep, then the injection and leapfrog passes). G_dev is
+// the residual [nrec][3]; with idx it is taken from the device's adjoint counter (G_dev then
+// only says whether there is one).
+static int adjoint_sweep_step(sem_ctx* c, const float* G_dev, const DevCtl* idx) {
+  if (fused_adjoint(c)) {
+    SweepNewmark nm{};
+    nm.mode = 3;
+    nm.u = c->d_lam;
+    nm.lam_old = c->d_lam_old;
+    nm.minv = c->d_minv;
+    nm.recv_range = c->nrec > 0 && G_dev ? c->d_precv_range : nullptr;
+    nm.recv = c->d_precv;
+    nm.G = idx ? nullptr : G_dev;
+    nm.idx = G_dev ? idx : nullptr;
+    nm.inv_dt2 = static_cast<float>(1.0 / (c->dt * c->dt));
+    nm.dt2 = static_cast<float>(c->dt * c->dt);
+    if (int r = forces_all_colors(c, c->d_lam, c->d_lamF, kNodeStride, 1, &nm)) return r;
+  } else {
+    if (int r = forces_all_colors(c, c->d_lam, c->d_lamF, kNodeStride, 1)) return r;
+    SEM_LAUNCH(c, launch_adjoint_update(c->d_lamF, G_dev, c->d_rnode, c->d_roff, c->d_rlist, c->nrnodes, c->d_lam,
+                                        c->d_lam_old, c->d_minv, c->nglob, c->dt, c->stream, idx));
+  }
+  std::swap(c->d_lam, c->d_lam_old);  // lam <- lam^{m-1}, lam_old <- lam^m
+  return SEM_OK;
+}
+
 int sem_adjoint_step(sem_ctx* c, const float* G_dev) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->adjoint) return fail(c, SEM_ESTATE, "sem_adjoint_begin has not been called");
   int r = set_device(c);
   if (r) return r;
-  if ((r = forces_all_colors(c, c->d_lam, c->d_lamF, kNodeStride, 1))) return r;
-  SEM_LAUNCH(c, launch_adjoint_update(c->d_lamF, G_dev, c->d_rnode, c->d_roff, c->d_rlist, c->nrnodes, c->d_lam,
-                                      c->d_lam_old, c->d_minv, c->nglob, c->dt, c->stream));
-  std::swap(c->d_lam, c->d_lam_old);  // lam <- lam^{m-1}, lam_old <- lam^m
-  return SEM_OK;
+  return adjoint_sweep_step(c, G_dev, nullptr);
 }
 
 int sem_adjoint_accumulate(sem_ctx* c, const float* u_lo, const float* u_mid, const float* u_hi) {
@@ -1795,6 +1875,19 @@ int sem_adjoint_accumulate(sem_ctx* c, const float* u_lo, const float* u_mid, co
   return SEM_OK;
 }
 
+// One adjoint step (sweep of lam, residual injection and leapfrog, sensitivity terms) with
+// its residual and snapshots named by the device's adjoint counter, which it then lowers.
+static int adjoint_indexed_step(sem_ctx* c, bool hasG) {
+  // (with the counter the residual comes from it; the pointer only marks that there is one)
+  if (int r = adjoint_sweep_step(c, hasG ? c->d_lamF : nullptr, c->d_ctl)) return r;
+  const size_t nloc = static_cast<size_t>(c->nspec) * c->ngll * c->ngll * c->ngll;
+  SEM_LAUNCH(c, launch_sensitivity(c->ngll, c->d_rec, c->node_order == 1 ? nullptr : c->d_perm, c->d_lam, nullptr,
+                                    nullptr, nullptr, c->d_grad32, c->d_grad32 + nloc, c->d_grad32 + 2 * nloc,
+                                    c->nspec, -1.0, -c->dt * c->dt, c->stream, c->d_ctl));
+  SEM_LAUNCH(c, launch_adjoint_next(c->d_ctl, c->stream));
+  return SEM_OK;
+}
+
 static int adjoint_segment_steps(sem_ctx* c, int count, const float* G_dev, const float* u_dev) {
   if (!c) return fail(nullptr, SEM_EINVAL, "null context");
   if (!c->adjoint) return fail(c, SEM_ESTATE, "sem_adjoint_begin has not been called");
@@ -1802,7 +1895,39 @@ static int adjoint_segment_steps(sem_ctx* c, int count, const float* G_dev, cons
   if (count > 0 && !u_dev) return fail(c, SEM_EINVAL, "sem_adjoint_segment: NULL snapshots");
   const size_t n3 = 3 * static_cast<size_t>(c->nglob);
   const size_t gstep = 3 * static_cast<size_t>(c->nrec);
-  for (int j = count; j >= 1; --j) {
+  int j0 = count;
+  if (count >= kStepsPerGraph) {
+    // steps in graphs of kStepsPerGraph (an even count: the lam buffers end in their roles),
+    // residuals and snapshots named by the device counter; the same kernels and sums as the
+    // steps one by one below
+    const bool hasG = G_dev != nullptr;
+    SEM_LAUNCH(c, launch_adjoint_index(c->d_ctl, G_dev, u_dev, static_cast<long long>(n3), static_cast<int>(gstep),
+                                       count, c->stream));
+    if (c->graph_adj && (c->graph_adj_lam != c->d_lam || c->graph_adj_G != hasG)) {
+      cudaGraphExecDestroy(c->graph_adj);
+      c->graph_adj = nullptr;
+    }
+    if (!c->graph_adj) {
+      c->graph_adj_lam = c->d_lam;
+      c->graph_adj_G = hasG;
+      cudaGraph_t g = nullptr;
+      SEM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      int rc = SEM_OK;
+      for (int s = 0; s < kStepsPerGraph && rc == SEM_OK; ++s) rc = adjoint_indexed_step(c, hasG);
+      cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+      if (rc == SEM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_adj, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (rc) return rc;
+      if (e != cudaSuccess) return cuda_fail(c, e, "adjoint graph");
+    }
+    for (; j0 >= kStepsPerGraph; j0 -= kStepsPerGraph) {
+      SEM_CUDA(c, cudaGraphLaunch(c->graph_adj, c->stream));
+      c->since_flush += kStepsPerGraph;
+      if (c->since_flush >= kFlushEvery)
+        if (int r = flush_gradients(c)) return r;
+    }
+  }
+  for (int j = j0; j >= 1; --j) {
     int r = sem_adjoint_step(c, G_dev ? G_dev + (j - 1) * gstep : nullptr);
     if (r) return r;
     if ((r = sem_adjoint_accumulate(c, u_dev + (j - 1) * n3, u_dev + j * n3, u_dev + (j + 1) * n3))) return r;

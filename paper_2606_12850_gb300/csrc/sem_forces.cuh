@@ -639,9 +639,10 @@ __device__ __forceinline__ size_t node_slot(uint32_t w, int S, int shot) {
 // Phases 1-3 of one patch for the calling thread's team: gather through the records' ibool
 // words (GB points per thread in flight; the shared-memory copy of each word keeps the node,
 // the patch first-touch flag and kAloneBit), then the element forces.
-// (NM: the half-step velocity and 1/M of the nodes the patch touches last are prefetched into
-// L2 as their points are gathered, for the Newmark update at the end of the patch.)
-template <int N, bool LO, bool MS = false, bool NM = false>
+// (NM 1: the half-step velocity and 1/M of the nodes the patch touches last are prefetched
+// into L2 as their points are gathered, for the Newmark update at the end of the patch; NM 2:
+// the older adjoint field and 1/M, for the adjoint leapfrog.)
+template <int N, bool LO, bool MS = false, int NM = 0>
 __device__ __forceinline__ void patch_gather_compute(const PatchDesc& d, const float* __restrict__ rec,
                                                      const float4* __restrict__ u, float* wsb, bool u_from_l2,
                                                      int S = 1, int shot = 0, const SweepNewmark* nm = nullptr) {
@@ -661,11 +662,12 @@ __device__ __forceinline__ void patch_gather_compute(const PatchDesc& d, const f
       const int le = idx / NP;
       w[r] = idx < ne * NP ? __float_as_uint(__ldg(trec + static_cast<size_t>(le) * REC + (idx - le * NP))) : 0u;
     }
-    if constexpr (NM) {
+    if constexpr (NM != 0) {
 #pragma unroll
       for (int r = 0; r < GB; ++r)
         if (w[r] & kPatchLastBit) {
-          prefetch_l2_line(reinterpret_cast<const float4*>(nm->v) + node_slot<MS>(w[r], S, shot));
+          prefetch_l2_line(reinterpret_cast<const float4*>(NM == 1 ? nm->v : nm->lam_old) +
+                           node_slot<MS>(w[r], S, shot));
           prefetch_l2_line(nm->minv + (w[r] & kNodeMask));
         }
     }
@@ -762,12 +764,44 @@ __device__ __forceinline__ void newmark_node(const SweepNewmark& nm, uint32_t w,
   }
 }
 
+// The adjoint step at a node whose force f = -K lam is complete (NM 2): the receiver
+// residuals of the step at this node added to f in ascending receiver order (G / dt^2), then
+// the leapfrog lam_old <- 2 lam - lam_old + dt^2 M^-1 f (the same float operations as the
+// separate injection and leapfrog passes).
+__device__ __forceinline__ void adjoint_receivers(const SweepNewmark& nm, int2 rr, uint32_t node, float& fx, float& fy,
+                                                  float& fz) {
+  const float* G = nm.idx ? nm.idx->adj_G + static_cast<long long>(nm.idx->adj_j - 1) * nm.idx->adj_gstep : nm.G;
+  if (!G) return;
+  for (int i = rr.x; i < rr.x + rr.y; ++i) {
+    const PatchRecv e = nm.recv[i];
+    if (e.node != static_cast<int>(node)) continue;
+    fx += G[3 * e.r] * nm.inv_dt2;
+    fy += G[3 * e.r + 1] * nm.inv_dt2;
+    fz += G[3 * e.r + 2] * nm.inv_dt2;
+  }
+}
+__device__ __forceinline__ void load_adjoint_state(const SweepNewmark& nm, uint32_t w, NodeState& st) {
+  const size_t g = w & kNodeMask;
+  st.m = __ldg(nm.minv + g);
+  st.u = __ldcg(reinterpret_cast<const float4*>(nm.u) + g);        // lam^m
+  st.v = __ldcg(reinterpret_cast<const float4*>(nm.lam_old) + g);  // lam^{m+1}
+}
+__device__ __forceinline__ void adjoint_node(const SweepNewmark& nm, uint32_t w, const NodeState& st, float fx,
+                                             float fy, float fz) {
+  const size_t g = w & kNodeMask;
+  const float s = nm.dt2 * st.m;
+  const float4 l = st.u, o = st.v;
+  reinterpret_cast<float4*>(nm.lam_old)[g] =
+      make_float4(2.f * l.x - o.x + s * fx, 2.f * l.y - o.y + s * fy, 2.f * l.z - o.z + s * fz, 0.f);
+}
+
 // Phase 4a for the calling thread's team: the forces of its points that are alone at their
 // patch node added to the node (stored at its first touch; with a Newmark mode, used for the
 // node's update at its last touch and not stored).
-template <int N, bool COHERENT, bool MS = false, bool NM = false>
+template <int N, bool COHERENT, bool MS = false, int NM = 0>
 __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __restrict__ f, const float* wsb,
-                                                  const SweepNewmark& nm, int S = 1, int shot = 0) {
+                                                  const SweepNewmark& nm, int S = 1, int shot = 0,
+                                                  int2 rr = make_int2(0, 0)) {
   using C = PatchCfg<N>;
   constexpr int NP = C::NP, E = C::E, TEAM = C::TEAM, ES = C::ES, GB = NM ? 2 : 4;
   const int team = threadIdx.x / TEAM;
@@ -788,7 +822,12 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
         const int e = idx / NP;
         w[r] = reinterpret_cast<const uint32_t*>(ts + e * ES + 9 * NP)[idx - e * NP];
         if ((w[r] & kAloneBit) && !(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + node_slot<MS>(w[r], S, shot));
-        if ((w[r] & kAloneBit) && (w[r] & last_bit)) load_node_state<MS>(nm, w[r], S, shot, st[r]);
+        if ((w[r] & kAloneBit) && (w[r] & last_bit)) {
+          if constexpr (NM == 2)
+            load_adjoint_state(nm, w[r], st[r]);
+          else
+            load_node_state<MS>(nm, w[r], S, shot, st[r]);
+        }
       }
     }
 #pragma unroll
@@ -799,8 +838,13 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
         const float* src = ts + e * ES + 3 * (idx - e * NP);
         float fx = src[0] + prev[r].x, fy = src[1] + prev[r].y, fz = src[2] + prev[r].z;
         if (w[r] & last_bit) {
-          if (d.nsrc) add_point_sources(d, nm, w[r] & kNodeMask, shot, fx, fy, fz);
-          newmark_node<MS>(nm, w[r], S, shot, st[r], fx, fy, fz);
+          if constexpr (NM == 2) {
+            if (rr.y) adjoint_receivers(nm, rr, w[r] & kNodeMask, fx, fy, fz);
+            adjoint_node(nm, w[r], st[r], fx, fy, fz);
+          } else {
+            if (d.nsrc) add_point_sources(d, nm, w[r] & kNodeMask, shot, fx, fy, fz);
+            newmark_node<MS>(nm, w[r], S, shot, st[r], fx, fy, fz);
+          }
         } else {
           f[node_slot<MS>(w[r], S, shot)] = make_float4(fx, fy, fz, 0.f);
         }
@@ -813,11 +857,11 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
 // order (its slots, shared-memory offsets of those forces, read as one 16-byte word), then
 // one store (first touch) or one read-modify-write, or at the node's last touch (with a
 // Newmark mode) its update; the previous values of GB nodes are loaded before any is written.
-template <int N, bool COHERENT, bool MS = false, bool NM = false>
+template <int N, bool COHERENT, bool MS = false, int NM = 0>
 __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uint16_t* __restrict__ slot_tab,
                                                    const uint16_t* __restrict__ word_tab, float4* __restrict__ f,
                                                    const float* wsb, const SweepNewmark& nm, int S = 1,
-                                                   int shot = 0) {
+                                                   int shot = 0, int2 rr = make_int2(0, 0)) {
   using C = PatchCfg<N>;
   constexpr int T = C::T, GB = NM ? 2 : 4;
   const uint4* __restrict__ slots = reinterpret_cast<const uint4*>(slot_tab + d.slot_off);
@@ -839,7 +883,12 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
     for (int r = 0; r < GB; ++r) {
       prev[r] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (!(w[r] & kPatchFirstBit)) prev[r] = load_f<COHERENT>(f + node_slot<MS>(w[r], S, shot));
-      if (w[r] & last_bit) load_node_state<MS>(nm, w[r], S, shot, st[r]);
+      if (w[r] & last_bit) {
+        if constexpr (NM == 2)
+          load_adjoint_state(nm, w[r], st[r]);
+        else
+          load_node_state<MS>(nm, w[r], S, shot, st[r]);
+      }
     }
 #pragma unroll
     for (int r = 0; r < GB; ++r) {
@@ -868,8 +917,13 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
         }
         float fx = prev[r].x + sx, fy = prev[r].y + sy, fz = prev[r].z + sz;
         if (w[r] & last_bit) {
-          if (d.nsrc) add_point_sources(d, nm, w[r] & kNodeMask, shot, fx, fy, fz);
-          newmark_node<MS>(nm, w[r], S, shot, st[r], fx, fy, fz);
+          if constexpr (NM == 2) {
+            if (rr.y) adjoint_receivers(nm, rr, w[r] & kNodeMask, fx, fy, fz);
+            adjoint_node(nm, w[r], st[r], fx, fy, fz);
+          } else {
+            if (d.nsrc) add_point_sources(d, nm, w[r] & kNodeMask, shot, fx, fy, fz);
+            newmark_node<MS>(nm, w[r], S, shot, st[r], fx, fy, fz);
+          }
         } else {
           f[node_slot<MS>(w[r], S, shot)] = make_float4(fx, fy, fz, 0.f);
         }
@@ -888,7 +942,7 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
 // With S shots (MS true) the fields are [nglob][S][4] and CTA b takes patch p0 + b / S for
 // shot b % S: consecutive CTAs take the shots of one patch, so its records come from DRAM
 // once (the first shot's prefetch) and from L2 for the others.
-template <int N, bool LO, bool MS, bool NM>
+template <int N, bool LO, bool MS, int NM>
 __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
     patch_forces_kernel(const float* __restrict__ rec, const PatchDesc* __restrict__ desc,
                         const uint16_t* __restrict__ slot_tab, const uint16_t* __restrict__ word_tab,
@@ -910,9 +964,10 @@ __global__ void __launch_bounds__(PatchCfg<N>::T, PatchCfg<N>::MIN_BLOCKS)
   // may hold from before the grid that wrote u
   patch_gather_compute<N, LO, MS, NM>(d, rec, u, wsb, p0 != 0, S, shot, &nm);
   if (p0 != 0) wait_prerequisite_grid();  // the previous colour's writes to f
-  patch_write_alone<N, false, MS, NM>(d, f, wsb, nm, S, shot);  // no wait for the other teams
+  const int2 rr = NM == 2 && nm.recv_range ? make_int2(nm.recv_range[2 * P], nm.recv_range[2 * P + 1]) : make_int2(0, 0);
+  patch_write_alone<N, false, MS, NM>(d, f, wsb, nm, S, shot, rr);  // no wait for the other teams
   __syncthreads();
-  patch_write_shared<N, false, MS, NM>(d, slot_tab, word_tab, f, wsb, nm, S, shot);
+  patch_write_shared<N, false, MS, NM>(d, slot_tab, word_tab, f, wsb, nm, S, shot, rr);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1612,8 +1667,15 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
     sensitivity_kernel(const float* __restrict__ rec, const int* __restrict__ perm, const float* __restrict__ lam,
                        const float* __restrict__ u_lo,
                        const float* __restrict__ u_mid, const float* __restrict__ u_hi, float* __restrict__ g_rho,
-                       float* __restrict__ g_kappa, float* __restrict__ g_mu, int nspec, double c_m, double c_k) {
+                       float* __restrict__ g_kappa, float* __restrict__ g_mu, int nspec, double c_m, double c_k,
+                       const DevCtl* __restrict__ idx) {
   using C = ForceCfg<N>;
+  if (idx) {  // the snapshots of the step the device's adjoint counter names
+    const float* base = idx->adj_u + static_cast<long long>(idx->adj_j - 1) * idx->adj_n3;
+    u_lo = base;
+    u_mid = base + idx->adj_n3;
+    u_hi = base + 2 * idx->adj_n3;
+  }
   constexpr int NP = C::NP, NL = C::NL, E = C::E, REC = C::REC, TEAM = C::TEAM, ES = C::ES;
   static_assert(7 * NP <= ES, "element tile holds lam, u and the mass term");
   extern __shared__ float4 smem4[];
@@ -1782,7 +1844,7 @@ int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
 template <bool LO, bool PAIRS>
 int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
   using C = PatchCfg<SEM_NGLL>;
-  static std::atomic<unsigned long long> attr_done{0}, attr_done_n{0}, attr_done_s{0}, attr_done_sn{0}, attr_done_p{0};
+  static std::atomic<unsigned long long> attr_done{0}, attr_done_n{0}, attr_done_s{0}, attr_done_sn{0}, attr_done_a{0}, attr_done_p{0};
   static std::atomic<int> resident[64];  // CTAs of the persistent kernel per SM, per device
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(C::T);
@@ -1831,26 +1893,32 @@ int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
     const int S = L.shots;
     cfg.gridDim = dim3(static_cast<unsigned>((L.p1 - L.p0) * S));
     if (L.nm.mode) {
-      if (int r = raise_smem_limit(attr_done_sn, patch_forces_kernel<SEM_NGLL, LO, true, true>, C::SMEM)) return r;
-      return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, true, true>, L.rec, L.desc,
+      if (int r = raise_smem_limit(attr_done_sn, patch_forces_kernel<SEM_NGLL, LO, true, 1>, C::SMEM)) return r;
+      return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, true, 1>, L.rec, L.desc,
                                                  L.slots, L.words, reinterpret_cast<const float4*>(L.u),
                                                  reinterpret_cast<float4*>(L.f), L.p0, S, L.nm));
     }
-    if (int r = raise_smem_limit(attr_done_s, patch_forces_kernel<SEM_NGLL, LO, true, false>, C::SMEM)) return r;
-    return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, true, false>, L.rec, L.desc,
+    if (int r = raise_smem_limit(attr_done_s, patch_forces_kernel<SEM_NGLL, LO, true, 0>, C::SMEM)) return r;
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, true, 0>, L.rec, L.desc,
                                                L.slots, L.words, reinterpret_cast<const float4*>(L.u),
                                                reinterpret_cast<float4*>(L.f), L.p0, S, L.nm));
   } else {
     const int S = 1;
     cfg.gridDim = dim3(static_cast<unsigned>(L.p1 - L.p0));
-    if (L.nm.mode) {
-      if (int r = raise_smem_limit(attr_done_n, patch_forces_kernel<SEM_NGLL, LO, false, true>, C::SMEM)) return r;
-      return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, false, true>, L.rec, L.desc,
+    if (L.nm.mode == 3) {  // the adjoint leapfrog at each node's last touch
+      if (int r = raise_smem_limit(attr_done_a, patch_forces_kernel<SEM_NGLL, LO, false, 2>, C::SMEM)) return r;
+      return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, false, 2>, L.rec, L.desc,
                                                  L.slots, L.words, reinterpret_cast<const float4*>(L.u),
                                                  reinterpret_cast<float4*>(L.f), L.p0, S, L.nm));
     }
-    if (int r = raise_smem_limit(attr_done, patch_forces_kernel<SEM_NGLL, LO, false, false>, C::SMEM)) return r;
-    return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, false, false>, L.rec, L.desc,
+    if (L.nm.mode) {
+      if (int r = raise_smem_limit(attr_done_n, patch_forces_kernel<SEM_NGLL, LO, false, 1>, C::SMEM)) return r;
+      return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, false, 1>, L.rec, L.desc,
+                                                 L.slots, L.words, reinterpret_cast<const float4*>(L.u),
+                                                 reinterpret_cast<float4*>(L.f), L.p0, S, L.nm));
+    }
+    if (int r = raise_smem_limit(attr_done, patch_forces_kernel<SEM_NGLL, LO, false, 0>, C::SMEM)) return r;
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, false, 0>, L.rec, L.desc,
                                                L.slots, L.words, reinterpret_cast<const float4*>(L.u),
                                                reinterpret_cast<float4*>(L.f), L.p0, S, L.nm));
   }
@@ -1933,14 +2001,15 @@ int SEM_CAT(launch_forces_, SEM_NGLL)(const ForceLaunch& L, void* stream) {
 
 int SEM_CAT(launch_sensitivity_, SEM_NGLL)(const float* rec, const int* perm, const float* lam, const float* u_lo,
                                           const float* u_mid, const float* u_hi, float* g_rho, float* g_kappa,
-                                          float* g_mu, int nspec, double c_m, double c_k, void* stream) {
+                                          float* g_mu, int nspec, double c_m, double c_k, void* stream,
+                                          const DevCtl* idx) {
   using C = ForceCfg<SEM_NGLL>;
   static std::atomic<unsigned long long> attr_done{0};
   const int smem = C::SMEM_FLOATS * static_cast<int>(sizeof(float));
   if (int r = raise_smem_limit(attr_done, sensitivity_kernel<SEM_NGLL>, smem)) return r;
   const int grid = (nspec + C::EPC - 1) / C::EPC;
   sensitivity_kernel<SEM_NGLL><<<grid, C::T, smem, static_cast<cudaStream_t>(stream)>>>(
-      rec, perm, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k);
+      rec, perm, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k, idx);
   return static_cast<int>(cudaGetLastError());
 }
 

@@ -117,6 +117,15 @@ struct DevCtl {
   float* seis;     // [nrec][3][ncols] or null
   int err;
   int pad;
+  float* snap;          // displacement snapshots [col][shots][nglob][3], or null
+  long long snap_per;   // floats per snapshot
+  // adjoint steps replayed from a graph: step j reads residual adj_G + (j - 1) adj_gstep and
+  // snapshots adj_u + (j - 1 .. j + 1) adj_n3; j counts down
+  const float* adj_G;
+  const float* adj_u;
+  long long adj_n3;
+  int adj_gstep;
+  int adj_j;
 };
 
 struct DevProblem {
@@ -174,6 +183,12 @@ struct alignas(16) PatchDesc {
   int nsrc;      // nodes it touches last, added there to the complete force
   int pad;
 };
+// A receiver in the adjoint sweep: internal node, receiver index (its residual G[3 r + c]).
+struct PatchRecv {
+  int node;
+  int r;
+};
+struct DevCtl;
 // A point source in the patch sweep: internal node, shot, force vector (Sec. V-C).
 struct PatchSrc {
   int node;
@@ -186,7 +201,7 @@ struct PatchSrc {
 // (f is then not stored), mode 2 the corrector alone (v <- v_half + dt/2 a, a stored), mode 0
 // none (f stored). The point sources of the step, at t = ctl->step dt, are added to f first.
 struct SweepNewmark {
-  int mode;
+  int mode;           // 3: the adjoint leapfrog (u = lam^m; lam_old: lam^{m+1} in, lam^{m-1} out)
   float* u;           // [nglob][shots][4], written at last touch (mode 1)
   float* v;           // [nglob][shots][4], half-step velocity in, out as above
   float* a;           // [nglob][shots][4], acceleration out (mode 2)
@@ -195,6 +210,16 @@ struct SweepNewmark {
   const long long* step;  // the step counter (t_{n+1} = step dt)
   double f0, t0, dtd;     // Ricker centre frequency and delay, step (double)
   float dt, hdt, hdt2;
+  // adjoint (mode 3): the receivers at the nodes each patch touches last (recv_range[2 P],
+  // recv_range[2 P + 1] = first, count into recv, ascending receiver within a patch), the
+  // residual G [nrec][3]
+  // (or, with idx, the one the device's adjoint counter names), 1/dt^2 and dt^2
+  float* lam_old;
+  const int* recv_range;
+  const PatchRecv* recv;
+  const float* G;
+  const DevCtl* idx;
+  float inv_dt2, dt2;
 };
 // Counters of a persistent sweep (all patch colours in one launch): patches taken, CTAs
 // that have left, a wait that gave up, patches finished per colour. Zero between sweeps.
@@ -273,24 +298,32 @@ int patch_shape(int ngll, PatchShape* out);
 int forces_kernel_smem_bytes(int ngll);
 int forces_elements_per_cta(int ngll);
 
-int launch_set_ctl(DevCtl* ctl, long long step, int ncols, float* seis, void* stream);
+int launch_set_ctl(DevCtl* ctl, long long step, int ncols, float* seis, void* stream, float* snap = nullptr,
+                   long long snap_per = 0);
+// the displacement into snapshot ctl->col - 1 (the column the receivers just sampled)
+int launch_snapshot(const float* u, DevCtl* ctl, const int* perm, int nglob, int shots, void* stream);
 int launch_predictor(const DevProblem& p, void* stream);
 int launch_fused_newmark(const DevProblem& p, void* stream);
 int launch_corrector(const DevProblem& p, void* stream);
 int launch_sources_record(const DevProblem& p, void* stream);
 // u_lo, u_mid, u_hi: [nglob][3] in caller order (perm: internal -> caller node) or in
 // internal order (perm null); the terms are added to float32 partials g_* [nlocal]
+// (idx non-null: the snapshots are idx->adj_u + (j - 1 .. j + 1) idx->adj_n3, j = idx->adj_j)
 int launch_sensitivity(int ngll, const float* rec, const int* perm, const float* lam, const float* u_lo,
                        const float* u_mid, const float* u_hi, float* g_rho, float* g_kappa, float* g_mu, int nspec,
-                       double c_m, double c_k, void* stream);
+                       double c_m, double c_k, void* stream, const DevCtl* idx = nullptr);
 // solver layout [nglob][shots][kNodeStride] in internal node order <-> caller layout
 // [shots][nglob][3] in caller node order (perm: internal -> caller node)
 int launch_pack(const float* u, float* out, const int* perm, int nglob, int shots, void* stream);
 int launch_unpack(const float* in, float* u, const int* perm, int nglob, int shots, void* stream);
 // rnode[nnodes]: distinct receiver nodes; rlist[roff[t] .. roff[t+1]): their receivers
+// (idx non-null: G_dev is taken from idx->adj_G at step idx->adj_j; G_dev then only says
+// whether there is one)
 int launch_adjoint_update(float* F, const float* G_dev, const int* rnode, const int* roff, const int* rlist,
                           int nnodes, const float* lam, float* lam_old, const float* minv, int nglob, double dt,
-                          void* stream);
+                          void* stream, const DevCtl* idx = nullptr);
+int launch_adjoint_index(DevCtl* ctl, const float* G, const float* u, long long n3, int gstep, int j, void* stream);
+int launch_adjoint_next(DevCtl* ctl, void* stream);  // j -= 1
 // acc[t] += part[t] (float64), part[t] = 0, for t < n
 int launch_flush_partials(float* part, double* acc, long long n, void* stream);
 // Material on the device (Sec. II-B moduli, Sec. I diagonal mass). rho, p1, p2: per local

@@ -21,7 +21,8 @@ namespace semgb {
   void patch_layout_##n(int* es, int* ts, int* e);                                                        \
   int launch_sensitivity_##n(const float* rec, const int* perm, const float* lam, const float* u_lo,       \
                              const float* u_mid, const float* u_hi, float* g_rho, float* g_kappa,       \
-                             float* g_mu, int nspec, double c_m, double c_k, void* stream);
+                             float* g_mu, int nspec, double c_m, double c_k, void* stream,              \
+                             const DevCtl* idx);
 SEM_DECLARE_ORDER(2)
 SEM_DECLARE_ORDER(3)
 SEM_DECLARE_ORDER(4)
@@ -69,9 +70,9 @@ int launch_forces(int n, const ForceLaunch& L, void* stream) {
 
 int launch_sensitivity(int n, const float* rec, const int* perm, const float* lam, const float* u_lo,
                        const float* u_mid, const float* u_hi, float* g_rho, float* g_kappa, float* g_mu, int nspec,
-                       double c_m, double c_k, void* stream) {
+                       double c_m, double c_k, void* stream, const DevCtl* idx) {
 #define SEM_CALL(k) \
-  launch_sensitivity_##k(rec, perm, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k, stream)
+  launch_sensitivity_##k(rec, perm, lam, u_lo, u_mid, u_hi, g_rho, g_kappa, g_mu, nspec, c_m, c_k, stream, idx)
   SEM_ORDER_SWITCH(n, SEM_CALL)
 #undef SEM_CALL
   return static_cast<int>(cudaErrorInvalidValue);
@@ -197,7 +198,9 @@ int launch_corrector(const DevProblem& p, void* stream) {
 // ---------------------------------------------------------------------------------------
 __global__ void adjoint_inject_kernel(float* __restrict__ F, const float* __restrict__ G,
                                       const int* __restrict__ rnode, const int* __restrict__ roff,
-                                      const int* __restrict__ rlist, int nnodes, float inv_dt2) {
+                                      const int* __restrict__ rlist, int nnodes, float inv_dt2,
+                                      const DevCtl* __restrict__ idx) {
+  if (idx) G = idx->adj_G + static_cast<long long>(idx->adj_j - 1) * idx->adj_gstep;
   // one thread per distinct receiver node; its receivers in ascending order (the order a
   // single thread walking the receivers would add them in)
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nnodes; t += gridDim.x * blockDim.x) {
@@ -219,6 +222,26 @@ __global__ void adjoint_leapfrog_kernel(const float4* __restrict__ lam, float4* 
   }
 }
 
+__global__ void adjoint_index_kernel(DevCtl* ctl, const float* G, const float* u, long long n3, int gstep, int j) {
+  ctl->adj_G = G;
+  ctl->adj_u = u;
+  ctl->adj_n3 = n3;
+  ctl->adj_gstep = gstep;
+  ctl->adj_j = j;
+}
+
+__global__ void adjoint_next_kernel(DevCtl* ctl) { ctl->adj_j -= 1; }
+
+int launch_adjoint_index(DevCtl* ctl, const float* G, const float* u, long long n3, int gstep, int j, void* stream) {
+  adjoint_index_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl, G, u, n3, gstep, j);
+  return static_cast<int>(cudaGetLastError());
+}
+
+int launch_adjoint_next(DevCtl* ctl, void* stream) {
+  adjoint_next_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl);
+  return static_cast<int>(cudaGetLastError());
+}
+
 __global__ void flush_partials_kernel(float* __restrict__ part, double* __restrict__ acc, long long n) {
   for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
        t += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -235,11 +258,11 @@ int launch_flush_partials(float* part, double* acc, long long n, void* stream) {
 
 int launch_adjoint_update(float* F, const float* G_dev, const int* rnode, const int* roff, const int* rlist,
                           int nnodes, const float* lam, float* lam_old, const float* minv, int nglob, double dt,
-                          void* stream) {
+                          void* stream, const DevCtl* idx) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (G_dev && nnodes > 0) {
     adjoint_inject_kernel<<<(nnodes + 127) / 128, 128, 0, s>>>(F, G_dev, rnode, roff, rlist, nnodes,
-                                                             static_cast<float>(1.0 / (dt * dt)));
+                                                             static_cast<float>(1.0 / (dt * dt)), idx);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return static_cast<int>(e);
   }
@@ -443,16 +466,46 @@ __global__ void sources_record_kernel(float* __restrict__ a, const float* __rest
   }
 }
 
-__global__ void set_ctl_kernel(DevCtl* ctl, long long step, int ncols, float* seis) {
+// pack_kernel into the snapshot slot the step counter names (graph-replayable)
+__global__ void snapshot_kernel(const float4* __restrict__ u, const DevCtl* __restrict__ ctl,
+                                const int* __restrict__ perm, long long nglob, int shots) {
+  float* base = ctl->snap;
+  if (!base) return;
+  float* out = base + static_cast<long long>(ctl->col - 1) * ctl->snap_per;
+  const long long n = nglob * shots;
+  for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long g = shots == 1 ? t : t / shots;
+    const long long sh = t - g * shots;
+    const float4 v = u[t];
+    float* o = out + 3 * (sh * nglob + (perm ? perm[g] : g));
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+  }
+}
+
+int launch_snapshot(const float* u, DevCtl* ctl, const int* perm, int nglob, int shots, void* stream) {
+  const long long n = static_cast<long long>(nglob) * shots;
+  if (n == 0) return 0;
+  snapshot_kernel<<<stream_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(reinterpret_cast<const float4*>(u),
+                                                                                 ctl, perm, nglob, shots);
+  return static_cast<int>(cudaGetLastError());
+}
+
+__global__ void set_ctl_kernel(DevCtl* ctl, long long step, int ncols, float* seis, float* snap, long long snap_per) {
   ctl->step = step;
   ctl->col = 0;
   ctl->ncols = ncols;
   ctl->seis = seis;
   ctl->err = 0;
+  ctl->snap = snap;
+  ctl->snap_per = snap_per;
 }
 
-int launch_set_ctl(DevCtl* ctl, long long step, int ncols, float* seis, void* stream) {
-  set_ctl_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl, step, ncols, seis);
+int launch_set_ctl(DevCtl* ctl, long long step, int ncols, float* seis, void* stream, float* snap,
+                   long long snap_per) {
+  set_ctl_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl, step, ncols, seis, snap, snap_per);
   return static_cast<int>(cudaGetLastError());
 }
 

@@ -144,6 +144,22 @@ def test_kept_snapshots_match_checkpoints(oracle, problem, fused):
     assert rel_l2(grads[1][0], r_rho) <= rho_tolerance(oracle, p)
 
 
+def test_fused_adjoint_sweep_equals_separate_passes(problem):
+    """The adjoint step with the residual injection and the leapfrog at each node's last
+    touch in the sweep of lam (SEM_OPT_FUSED_NEWMARK 1) against the sweep followed by the
+    injection and leapfrog passes (0): the same float operations, bitwise equal gradients."""
+    p = problem
+    G = torch.from_numpy(p["G"].astype(np.float32)).cuda()
+    out = []
+    for fused in (0, 1):
+        ctx, sim = make_sim(p, 7, keep_all=True)
+        sem.sem_set_option(ctx, sem.SEM_OPT_FUSED_NEWMARK, fused)
+        sim.forward(*material(p))
+        out.append(sim.gradient(G))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
 def test_segment_equals_single_steps(problem):
     """sem_adjoint_segment (the mass term formed per node by the leapfrog pass) against
     sem_adjoint_step + sem_adjoint_accumulate one step at a time (formed at every local
