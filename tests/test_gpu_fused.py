@@ -156,3 +156,13 @@ def test_shot_pairs_match_one_cta_per_shot(ngll, n):
     for x, y in zip(outs[1], outs[0]):
         y = y.astype(np.float64)
         assert np.linalg.norm(x - y) <= 1e-6 * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("ngll", [2, 4, 6, 8, 9, 10])
+def test_fused_sweep_every_order(ngll):
+    """The remaining orders (the parametrized test above covers 3, 5 and 7): a jittered
+    layered cube of a few bricks, 12 steps split 5 + 7, fused against separate passes."""
+    w = dataclasses.replace(inputs.layered_cube(ngll, n=4, side=800.0, nrec_side=2), t0=0.02)
+    ref = run(w, 0, [12])
+    assert np.abs(ref[0]).max() > 0
+    assert_same(run(w, 1, [5, 7]), ref)
