@@ -31,6 +31,8 @@ struct sem_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t aux = nullptr;      // the adjoint's sensitivity terms run here, one step behind
+  cudaEvent_t ev_sweep[2] = {nullptr, nullptr}, ev_sens[2] = {nullptr, nullptr};
   std::string err;
 
   std::vector<double> xi, w, hprime;
@@ -674,6 +676,11 @@ int sem_destroy(sem_ctx* c) {
   drop_graph(c);
   free_device(c);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->aux) cudaStreamDestroy(c->aux);
+  for (int k = 0; k < 2; ++k) {
+    if (c->ev_sweep[k]) cudaEventDestroy(c->ev_sweep[k]);
+    if (c->ev_sens[k]) cudaEventDestroy(c->ev_sens[k]);
+  }
   delete c;
   return SEM_OK;
 }
@@ -1616,8 +1623,13 @@ int sem_run_record_snapshots(sem_ctx* c, int nsteps, float* seis_dev, float* u_d
     DevProblem q = problem(c);
     q.nsrc = 0;
     SEM_LAUNCH(c, launch_sources_record(q, c->stream));
-    SEM_LAUNCH(c, launch_snapshot(c->d_u, c->d_ctl, perm, c->nglob, c->shots, c->stream));
-    const SweepNewmark nm = sweep_newmark(c, mode);
+    SweepNewmark nm = sweep_newmark(c, mode);
+    if (c->shots == 1) {  // the sweep stores u^{n+1} at each node's last touch
+      nm.snap_ctl = c->d_ctl;
+      nm.snap_perm = perm;
+    } else {
+      SEM_LAUNCH(c, launch_snapshot(c->d_u, c->d_ctl, perm, c->nglob, c->shots, c->stream));
+    }
     return forces_all_colors(c, c->d_u, c->d_a, kNodeStride, c->shots, &nm);
   };
   int left = nsteps - 1;
@@ -1877,14 +1889,34 @@ int sem_adjoint_accumulate(sem_ctx* c, const float* u_lo, const float* u_mid, co
 
 // One adjoint step (sweep of lam, residual injection and leapfrog, sensitivity terms) with
 // its residual and snapshots named by the device's adjoint counter, which it then lowers.
-static int adjoint_indexed_step(sem_ctx* c, bool hasG) {
+// Step k of a run of indexed adjoint steps: the sweep of lam on the context's stream, the
+// sensitivity terms on the auxiliary stream as soon as the sweep is done, so that they overlap
+// the next step's sweep. That sweep only writes the buffer of lam^{m+1}, which these terms do
+// not read; the sweep after it overwrites lam^{m-1}, so it waits for them (ev_sens ring).
+static int adjoint_indexed_step(sem_ctx* c, bool hasG, int k) {
+  if (k >= 2) SEM_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_sens[k & 1], 0));
   // (with the counter the residual comes from it; the pointer only marks that there is one)
   if (int r = adjoint_sweep_step(c, hasG ? c->d_lamF : nullptr, c->d_ctl)) return r;
+  SEM_LAUNCH(c, launch_adjoint_next(c->d_ctl, c->stream));
+  SEM_CUDA(c, cudaEventRecord(c->ev_sweep[k & 1], c->stream));
+  SEM_CUDA(c, cudaStreamWaitEvent(c->aux, c->ev_sweep[k & 1], 0));
   const size_t nloc = static_cast<size_t>(c->nspec) * c->ngll * c->ngll * c->ngll;
   SEM_LAUNCH(c, launch_sensitivity(c->ngll, c->d_rec, c->node_order == 1 ? nullptr : c->d_perm, c->d_lam, nullptr,
                                     nullptr, nullptr, c->d_grad32, c->d_grad32 + nloc, c->d_grad32 + 2 * nloc,
-                                    c->nspec, -1.0, -c->dt * c->dt, c->stream, c->d_ctl));
-  SEM_LAUNCH(c, launch_adjoint_next(c->d_ctl, c->stream));
+                                    c->nspec, -1.0, -c->dt * c->dt, c->aux, c->d_ctl));
+  SEM_LAUNCH(c, launch_adjoint_next(c->d_ctl, c->aux, true));
+  SEM_CUDA(c, cudaEventRecord(c->ev_sens[k & 1], c->aux));
+  return SEM_OK;
+}
+
+// The auxiliary stream and events of the overlapped adjoint steps.
+static int adjoint_aux(sem_ctx* c) {
+  if (c->aux) return SEM_OK;
+  SEM_CUDA(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; ++k) {
+    SEM_CUDA(c, cudaEventCreateWithFlags(&c->ev_sweep[k], cudaEventDisableTiming));
+    SEM_CUDA(c, cudaEventCreateWithFlags(&c->ev_sens[k], cudaEventDisableTiming));
+  }
   return SEM_OK;
 }
 
@@ -1901,6 +1933,7 @@ static int adjoint_segment_steps(sem_ctx* c, int count, const float* G_dev, cons
     // residuals and snapshots named by the device counter; the same kernels and sums as the
     // steps one by one below
     const bool hasG = G_dev != nullptr;
+    if (int r = adjoint_aux(c)) return r;
     SEM_LAUNCH(c, launch_adjoint_index(c->d_ctl, G_dev, u_dev, static_cast<long long>(n3), static_cast<int>(gstep),
                                        count, c->stream));
     if (c->graph_adj && (c->graph_adj_lam != c->d_lam || c->graph_adj_G != hasG)) {
@@ -1913,7 +1946,10 @@ static int adjoint_segment_steps(sem_ctx* c, int count, const float* G_dev, cons
       cudaGraph_t g = nullptr;
       SEM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
       int rc = SEM_OK;
-      for (int s = 0; s < kStepsPerGraph && rc == SEM_OK; ++s) rc = adjoint_indexed_step(c, hasG);
+      for (int s = 0; s < kStepsPerGraph && rc == SEM_OK; ++s) rc = adjoint_indexed_step(c, hasG, s);
+      // join the auxiliary branch (its last terms) before the graph ends
+      if (rc == SEM_OK && cudaStreamWaitEvent(c->stream, c->ev_sens[(kStepsPerGraph - 1) & 1], 0) != cudaSuccess)
+        rc = fail(c, SEM_ECUDA, "adjoint graph join");
       cudaError_t e = cudaStreamEndCapture(c->stream, &g);
       if (rc == SEM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_adj, g, 0);
       if (g) cudaGraphDestroy(g);

@@ -666,7 +666,7 @@ __device__ __forceinline__ void patch_gather_compute(const PatchDesc& d, const f
 #pragma unroll
       for (int r = 0; r < GB; ++r)
         if (w[r] & kPatchLastBit) {
-          prefetch_l2_line(reinterpret_cast<const float4*>(NM == 1 ? nm->v : nm->lam_old) +
+          prefetch_l2_line(reinterpret_cast<const float4*>(NM == 2 ? nm->lam_old : nm->v) +
                            node_slot<MS>(w[r], S, shot));
           prefetch_l2_line(nm->minv + (w[r] & kNodeMask));
         }
@@ -736,12 +736,12 @@ struct NodeState {
   float m;
   float4 v, u;
 };
-template <bool MS>
+template <bool MS, bool WITH_U = false>
 __device__ __forceinline__ void load_node_state(const SweepNewmark& nm, uint32_t w, int S, int shot, NodeState& st) {
   const size_t g = node_slot<MS>(w, S, shot);
   st.m = __ldg(nm.minv + (w & kNodeMask));
   st.v = __ldcg(reinterpret_cast<const float4*>(nm.v) + g);
-  if (nm.mode == 1) st.u = __ldcg(reinterpret_cast<const float4*>(nm.u) + g);
+  if (WITH_U || nm.mode == 1) st.u = __ldcg(reinterpret_cast<const float4*>(nm.u) + g);
 }
 
 // Newmark update of a node whose complete force (fx, fy, fz) is known (mode 1 or 2):
@@ -762,6 +762,17 @@ __device__ __forceinline__ void newmark_node(const SweepNewmark& nm, uint32_t w,
     reinterpret_cast<float4*>(nm.v)[g] = make_float4(vx, vy, vz, 0.f);
     reinterpret_cast<float4*>(nm.a)[g] = make_float4(ax, ay, az, 0.f);
   }
+}
+
+// The snapshot of the node's displacement u^{n+1} (NM 3: a Newmark sweep of a snapshot run).
+__device__ __forceinline__ void snapshot_node(const SweepNewmark& nm, uint32_t w, const NodeState& st) {
+  const DevCtl* ctl = nm.snap_ctl;
+  const uint32_t g = w & kNodeMask;
+  float* o = ctl->snap + static_cast<long long>(ctl->col - 1) * ctl->snap_per +
+             3 * static_cast<size_t>(nm.snap_perm ? __ldg(nm.snap_perm + g) : static_cast<int>(g));
+  o[0] = st.u.x;
+  o[1] = st.u.y;
+  o[2] = st.u.z;
 }
 
 // The adjoint step at a node whose force f = -K lam is complete (NM 2): the receiver
@@ -826,7 +837,7 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
           if constexpr (NM == 2)
             load_adjoint_state(nm, w[r], st[r]);
           else
-            load_node_state<MS>(nm, w[r], S, shot, st[r]);
+            load_node_state<MS, NM == 3>(nm, w[r], S, shot, st[r]);
         }
       }
     }
@@ -842,6 +853,7 @@ __device__ __forceinline__ void patch_write_alone(const PatchDesc& d, float4* __
             if (rr.y) adjoint_receivers(nm, rr, w[r] & kNodeMask, fx, fy, fz);
             adjoint_node(nm, w[r], st[r], fx, fy, fz);
           } else {
+            if constexpr (NM == 3) snapshot_node(nm, w[r], st[r]);
             if (d.nsrc) add_point_sources(d, nm, w[r] & kNodeMask, shot, fx, fy, fz);
             newmark_node<MS>(nm, w[r], S, shot, st[r], fx, fy, fz);
           }
@@ -887,7 +899,7 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
         if constexpr (NM == 2)
           load_adjoint_state(nm, w[r], st[r]);
         else
-          load_node_state<MS>(nm, w[r], S, shot, st[r]);
+          load_node_state<MS, NM == 3>(nm, w[r], S, shot, st[r]);
       }
     }
 #pragma unroll
@@ -921,6 +933,7 @@ __device__ __forceinline__ void patch_write_shared(const PatchDesc& d, const uin
             if (rr.y) adjoint_receivers(nm, rr, w[r] & kNodeMask, fx, fy, fz);
             adjoint_node(nm, w[r], st[r], fx, fy, fz);
           } else {
+            if constexpr (NM == 3) snapshot_node(nm, w[r], st[r]);
             if (d.nsrc) add_point_sources(d, nm, w[r] & kNodeMask, shot, fx, fy, fz);
             newmark_node<MS>(nm, w[r], S, shot, st[r], fx, fy, fz);
           }
@@ -1671,7 +1684,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
                        const DevCtl* __restrict__ idx) {
   using C = ForceCfg<N>;
   if (idx) {  // the snapshots of the step the device's adjoint counter names
-    const float* base = idx->adj_u + static_cast<long long>(idx->adj_j - 1) * idx->adj_n3;
+    const float* base = idx->adj_u + static_cast<long long>(idx->adj_js - 1) * idx->adj_n3;
     u_lo = base;
     u_mid = base + idx->adj_n3;
     u_hi = base + 2 * idx->adj_n3;
@@ -1688,7 +1701,7 @@ __global__ void __launch_bounds__(ForceCfg<N>::T)
   const int ne = min(E, nspec - ebase);
   if (C::KIND != 2 && ne <= 0) return;
   float* ts = reinterpret_cast<float*>(smem4) + team * C::TS;
-  constexpr int GB = 2;  // points per thread whose loads are in flight together
+  constexpr int GB = 4;  // points per thread whose loads are in flight together
   for (int base = tl; base < ne * NP; base += GB * TEAM) {
     size_t g[GB];
 #pragma unroll
@@ -1844,7 +1857,7 @@ int launch_forces_n(const ForceLaunch& L, cudaStream_t s) {
 template <bool LO, bool PAIRS>
 int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
   using C = PatchCfg<SEM_NGLL>;
-  static std::atomic<unsigned long long> attr_done{0}, attr_done_n{0}, attr_done_s{0}, attr_done_sn{0}, attr_done_a{0}, attr_done_p{0};
+  static std::atomic<unsigned long long> attr_done{0}, attr_done_n{0}, attr_done_s{0}, attr_done_sn{0}, attr_done_a{0}, attr_done_ns{0}, attr_done_p{0};
   static std::atomic<int> resident[64];  // CTAs of the persistent kernel per SM, per device
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(C::T);
@@ -1905,6 +1918,12 @@ int launch_patch_lo(const PatchLaunch& L, cudaStream_t s) {
   } else {
     const int S = 1;
     cfg.gridDim = dim3(static_cast<unsigned>(L.p1 - L.p0));
+    if (L.nm.mode && L.nm.mode != 3 && L.nm.snap_ctl) {  // a snapshot run's Newmark sweep
+      if (int r = raise_smem_limit(attr_done_ns, patch_forces_kernel<SEM_NGLL, LO, false, 3>, C::SMEM)) return r;
+      return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, false, 3>, L.rec, L.desc,
+                                                 L.slots, L.words, reinterpret_cast<const float4*>(L.u),
+                                                 reinterpret_cast<float4*>(L.f), L.p0, S, L.nm));
+    }
     if (L.nm.mode == 3) {  // the adjoint leapfrog at each node's last touch
       if (int r = raise_smem_limit(attr_done_a, patch_forces_kernel<SEM_NGLL, LO, false, 2>, C::SMEM)) return r;
       return static_cast<int>(cudaLaunchKernelEx(&cfg, patch_forces_kernel<SEM_NGLL, LO, false, 2>, L.rec, L.desc,

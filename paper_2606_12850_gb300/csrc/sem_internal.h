@@ -125,7 +125,9 @@ struct DevCtl {
   const float* adj_u;
   long long adj_n3;
   int adj_gstep;
-  int adj_j;
+  int adj_j;   // the step the sweep of lam is at (residual injection)
+  int adj_js;  // the step the sensitivity terms are at (they may run one step behind)
+  int pad3;
 };
 
 struct DevProblem {
@@ -214,6 +216,10 @@ struct SweepNewmark {
   // recv_range[2 P + 1] = first, count into recv, ascending receiver within a patch), the
   // residual G [nrec][3]
   // (or, with idx, the one the device's adjoint counter names), 1/dt^2 and dt^2
+  // snapshot run (modes 1, 2): u^{n+1} also stored at each node's last touch into
+  // ctl->snap + (ctl->col - 1) ctl->snap_per, [nglob][3] in the order snap_perm maps to
+  const DevCtl* snap_ctl;
+  const int* snap_perm;
   float* lam_old;
   const int* recv_range;
   const PatchRecv* recv;
@@ -323,7 +329,7 @@ int launch_adjoint_update(float* F, const float* G_dev, const int* rnode, const 
                           int nnodes, const float* lam, float* lam_old, const float* minv, int nglob, double dt,
                           void* stream, const DevCtl* idx = nullptr);
 int launch_adjoint_index(DevCtl* ctl, const float* G, const float* u, long long n3, int gstep, int j, void* stream);
-int launch_adjoint_next(DevCtl* ctl, void* stream);  // j -= 1
+int launch_adjoint_next(DevCtl* ctl, void* stream, bool sensitivity = false);  // adj_j (or adj_js) -= 1
 // acc[t] += part[t] (float64), part[t] = 0, for t < n
 int launch_flush_partials(float* part, double* acc, long long n, void* stream);
 // Material on the device (Sec. II-B moduli, Sec. I diagonal mass). rho, p1, p2: per local

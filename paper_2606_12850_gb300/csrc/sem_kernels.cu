@@ -228,17 +228,23 @@ __global__ void adjoint_index_kernel(DevCtl* ctl, const float* G, const float* u
   ctl->adj_n3 = n3;
   ctl->adj_gstep = gstep;
   ctl->adj_j = j;
+  ctl->adj_js = j;
 }
 
-__global__ void adjoint_next_kernel(DevCtl* ctl) { ctl->adj_j -= 1; }
+__global__ void adjoint_next_kernel(DevCtl* ctl, int sensitivity) {
+  if (sensitivity)
+    ctl->adj_js -= 1;
+  else
+    ctl->adj_j -= 1;
+}
 
 int launch_adjoint_index(DevCtl* ctl, const float* G, const float* u, long long n3, int gstep, int j, void* stream) {
   adjoint_index_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl, G, u, n3, gstep, j);
   return static_cast<int>(cudaGetLastError());
 }
 
-int launch_adjoint_next(DevCtl* ctl, void* stream) {
-  adjoint_next_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl);
+int launch_adjoint_next(DevCtl* ctl, void* stream, bool sensitivity) {
+  adjoint_next_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl, sensitivity ? 1 : 0);
   return static_cast<int>(cudaGetLastError());
 }
 
