@@ -735,19 +735,65 @@ def measure_surrogate(device: int, runs: int, epochs: int, heldout: int = 256, b
     model.forward(xi, yi)
     model.sync()
     infer_s = time.perf_counter() - t
+    products = compare_products(model, spec, xi, yi, batch)
     solver_ms = 1e3 * (tr.seconds + te.seconds) / (runs + heldout)
     net_ms = 1e3 * infer_s / n_inf
     return {"medium": w.name, "train_runs": runs, "heldout_runs": heldout,
             "network": f"MLP 9-512-512, seed [64][125], conv decoder x2 x2 x2 to 1000 samples, "
                        f"6 x 192 channels combined with the moment tensor; {model.nparams} parameters, bf16 "
-                       "weights, fp32 accumulate",
+                       "weights and operands, fp32 accumulate, tcgen05 products (TMEM accumulators)",
             "epochs": epochs, "batch": batch, "train_s": train_s, "final_loss": losses[-1],
             "generation_s": tr.seconds + te.seconds, "solver_ms_per_run": solver_ms,
             "network_ms_per_source_batch4096": net_ms, "speedup_per_source": solver_ms / net_ms,
             "heldout_rel_l2": {"median": float(np.median(err)), "mean": float(err.mean()),
                                "p90": float(np.percentile(err, 90))},
             "nearest_run_rel_l2": {"median": float(np.median(err_nn)), "mean": float(err_nn.mean())},
+            "products": products,
             "timing": "wall clock with device synchronisation"}
+
+
+def product_flops(spec) -> int:
+    """Multiply-add FLOPs (2 per multiply-add) of the network's products for one input: the
+    three dense layers and the decoder's width-3 convolutions."""
+    f = spec.in_dim * spec.hidden + spec.hidden * spec.hidden + spec.hidden * spec.c0 * spec.l0
+    cin, length = spec.c0, spec.l0
+    for co, up in zip(spec.stage_cout, spec.stage_up):
+        length *= up
+        f += co * cin * 3 * length
+        cin = co
+    return 2 * f
+
+
+def compare_products(model, spec, xi, yi, batch: int, reps: int = 5):
+    """The same forward (len(xi) inputs) and loss-gradient step (``batch`` inputs) with each
+    product kernel: tcgen05 with TMEM accumulators (the default) and warp-level mma.sync;
+    median wall clock of ``reps`` synchronised repetitions after one warm-up. The loss step
+    takes the network's own outputs as targets (its gradients are not applied)."""
+    xb = xi[:batch].contiguous()
+    tb = yi[:batch].clone()
+    flops = product_flops(spec)
+    out = {}
+    for kind, name in ((1, "tcgen05"), (0, "mma_sync")):
+        model.product = kind
+        res = {}
+        for what, fn, n, mult in (("forward", lambda: model.forward(xi, yi), len(xi), 1),
+                                  ("loss_grad", lambda: model.loss_grad(xb, tb), batch, 3)):
+            fn()
+            model.sync()
+            times = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                fn()
+                model.sync()
+                times.append(time.perf_counter() - t0)
+            ms = 1e3 * float(np.median(times))
+            res[what] = {"batch": n, "ms": ms, "product_tflops": mult * flops * n / (ms * 1e-3) / 1e12}
+        out[name] = res
+    model.product = 1
+    out["product_gflop_per_input"] = flops / 1e9
+    out["speedup_forward"] = out["mma_sync"]["forward"]["ms"] / out["tcgen05"]["forward"]["ms"]
+    out["speedup_loss_grad"] = out["mma_sync"]["loss_grad"]["ms"] / out["tcgen05"]["loss_grad"]["ms"]
+    return out
 
 
 def run_ours(args):

@@ -79,6 +79,20 @@ int sg_get_grads(sg_model* model, float* grads);
 int sg_adam_step(sg_model* model, float lr, float beta1, float beta2, float eps);
 
 int sg_sync(sg_model* model);
+
+/* Options. SG_OPT_PRODUCT picks the kernel of every product (dense layers, convolutions and
+ * their backward products): 1 (the default) = tcgen05.mma with the float32 accumulator in
+ * tensor memory, 128 x 128 tiles; 0 = warp-level mma.sync, 128/256 x 64 tiles. Both round the
+ * operands to bfloat16 and accumulate in float32, so they agree to float32 rounding order.
+ * Setting an option waits for the model's stream. A tcgen05 product that waits more than 2 s
+ * for its MMAs gives up: sg_loss_grad and sg_sync then return SEM_ETIMEOUT. */
+#define SG_OPT_PRODUCT 1
+/* SG_OPT_STALL_TEST (tests only): 1 makes every tcgen05 product wait for an mbarrier phase
+ * that nothing completes, with a 20 ms limit that runs out; the next sg_loss_grad or sg_sync returns
+ * SEM_ETIMEOUT, no result of the product is written and the model stays usable. */
+#define SG_OPT_STALL_TEST 2
+int sg_set_option(sg_model* model, int option, int value);
+int sg_get_option(sg_model* model, int option, int* value);
 const char* sg_last_error(const sg_model* model);
 
 #ifdef __cplusplus

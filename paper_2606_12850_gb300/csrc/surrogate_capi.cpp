@@ -32,6 +32,8 @@ struct sg_model {
   float* d_y = nullptr;  // network output [max_batch][out_c][out_l] when contract > 0
   float* d_ws = nullptr;
   double* d_partials = nullptr;
+  int* d_err = nullptr;  // set by a tensor-core product whose bounded wait ran out
+  sgk::Products prod;    // product kernel (SG_OPT_PRODUCT) and d_err
   long long step = 0;
   size_t dev_bytes = 0;
   std::vector<void*> allocs;
@@ -75,21 +77,31 @@ int sg_alloc(sg_model* m, T** p, size_t count) {
   return SG_OK;
 }
 
+// After a stream synchronisation: a product kernel that gave up waiting for the tensor cores
+// left d_err set; report it (and clear it for the next call).
+int check_products(sg_model* m, const char* where) {
+  int h = 0;
+  SG_CUDA(m, cudaMemcpy(&h, m->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h == 0) return SG_OK;
+  SG_CUDA(m, cudaMemset(m->d_err, 0, sizeof(int)));
+  return sg_fail(m, SEM_ETIMEOUT, std::string(where) + ": a tensor-core product timed out waiting for its MMAs");
+}
+
 int forward_chunk(sg_model* m, int b, const float* x, float* y_last) {
   cudaStream_t s = m->stream;
   SG_LAUNCH(m, sgk::linear_forward(b, m->in_dim, m->hidden, x, m->d_pb + m->oW1, m->d_p + m->ob1, m->d_a1, m->d_h1,
-                                   true, s));
+                                   true, m->prod, s));
   SG_LAUNCH(m, sgk::linear_forward(b, m->hidden, m->hidden, m->d_h1, m->d_pb + m->oW2, m->d_p + m->ob2, m->d_a2,
-                                   m->d_h2, true, s));
+                                   m->d_h2, true, m->prod, s));
   SG_LAUNCH(m, sgk::linear_forward(b, m->hidden, m->c0 * m->l0, m->d_h2, m->d_pb + m->oW3, m->d_p + m->ob3, m->d_a3,
-                                   m->d_z0, true, s));
+                                   m->d_z0, true, m->prod, s));
   const float* in = m->d_z0;
   const int last = m->nstages - 1;
   for (int st = 0; st < m->nstages; ++st) {
     float* pre = (st == last && y_last && !m->contract) ? y_last : m->d_pre[st];
     float* out = st == last ? nullptr : m->d_out[st];
     SG_LAUNCH(m, sgk::conv_forward(b, m->cin[st], m->cout[st], m->lin[st], m->up[st], in, m->d_pb + m->oC[st],
-                                   m->d_p + m->oc[st], pre, out, s));
+                                   m->d_p + m->oc[st], pre, out, m->prod, s));
     in = out;
   }
   if (m->contract)
@@ -183,6 +195,7 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
       (r = sg_alloc(m, &m->d_a3, B * c0 * l0)) || (r = sg_alloc(m, &m->d_z0, B * c0 * l0)) ||
       (r = sg_alloc(m, &m->d_dA, B * act)) || (r = sg_alloc(m, &m->d_dB, B * act)) ||
       (r = sg_alloc(m, &m->d_ws, ws)) || (r = sg_alloc(m, &m->d_partials, sgk::kLossBlocks)) ||
+      (r = sg_alloc(m, &m->d_err, 1)) ||
       (r = sg_alloc(m, &m->d_y, contract ? B * m->out_c * m->out_l : 0))) {
     std::string msg = m->err;
     sg_destroy(m);
@@ -202,6 +215,7 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
     for (float* q : zero)
       if (z == cudaSuccess) z = cudaMemsetAsync(q, 0, bytes, m->stream);
     if (z == cudaSuccess) z = cudaMemsetAsync(m->d_pb, 0, m->P * sizeof(bf16), m->stream);
+    if (z == cudaSuccess) z = cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream);
     if (z == cudaSuccess) z = cudaStreamSynchronize(m->stream);
     if (z != cudaSuccess) r = sg_fail(m, SEM_ECUDA, std::string("sg_create: ") + cudaGetErrorString(z));
   }
@@ -210,6 +224,7 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
     sg_destroy(m);
     return sg_fail(nullptr, r, msg);
   }
+  m->prod.err = m->d_err;
   *out = m;
   return SG_OK;
 }
@@ -297,26 +312,29 @@ int sg_loss_grad(sg_model* m, int b, const float* x, const float* target, double
       SG_LAUNCH(m, sgk::gelu_backward(static_cast<size_t>(b) * m->cout[st] * m->lout[st], m->d_pre[st], cur, s));
     const float* input = st == 0 ? m->d_z0 : m->d_out[st - 1];
     SG_LAUNCH(m, sgk::conv_backward_weight(b, m->cin[st], m->cout[st], m->lin[st], m->up[st], cur, input,
-                                           m->d_g + m->oC[st], m->d_g + m->oc[st], m->d_ws, s));
+                                           m->d_g + m->oC[st], m->d_g + m->oc[st], m->d_ws, m->prod, s));
     SG_LAUNCH(m, sgk::conv_backward_data(b, m->cin[st], m->cout[st], m->lin[st], m->up[st], cur, m->d_pb + m->oC[st],
-                                         other, s));
+                                         other, m->prod, s));
     std::swap(cur, other);
   }
   const int n3 = m->c0 * m->l0;
   SG_LAUNCH(m, sgk::gelu_backward(static_cast<size_t>(b) * n3, m->d_a3, cur, s));
-  SG_LAUNCH(m, sgk::linear_backward_weight(b, m->hidden, n3, cur, m->d_h2, m->d_g + m->oW3, m->d_g + m->ob3, m->d_ws, s));
-  SG_LAUNCH(m, sgk::linear_backward_data(b, m->hidden, n3, cur, m->d_pb + m->oW3, other, s));
+  SG_LAUNCH(m, sgk::linear_backward_weight(b, m->hidden, n3, cur, m->d_h2, m->d_g + m->oW3, m->d_g + m->ob3, m->d_ws,
+                                           m->prod, s));
+  SG_LAUNCH(m, sgk::linear_backward_data(b, m->hidden, n3, cur, m->d_pb + m->oW3, other, m->prod, s));
   std::swap(cur, other);
   SG_LAUNCH(m, sgk::gelu_backward(static_cast<size_t>(b) * m->hidden, m->d_a2, cur, s));
   SG_LAUNCH(m, sgk::linear_backward_weight(b, m->hidden, m->hidden, cur, m->d_h1, m->d_g + m->oW2, m->d_g + m->ob2,
-                                           m->d_ws, s));
-  SG_LAUNCH(m, sgk::linear_backward_data(b, m->hidden, m->hidden, cur, m->d_pb + m->oW2, other, s));
+                                           m->d_ws, m->prod, s));
+  SG_LAUNCH(m, sgk::linear_backward_data(b, m->hidden, m->hidden, cur, m->d_pb + m->oW2, other, m->prod, s));
   std::swap(cur, other);
   SG_LAUNCH(m, sgk::gelu_backward(static_cast<size_t>(b) * m->hidden, m->d_a1, cur, s));
-  SG_LAUNCH(m, sgk::linear_backward_weight(b, m->in_dim, m->hidden, cur, x, m->d_g + m->oW1, m->d_g + m->ob1, m->d_ws, s));
+  SG_LAUNCH(m, sgk::linear_backward_weight(b, m->in_dim, m->hidden, cur, x, m->d_g + m->oW1, m->d_g + m->ob1, m->d_ws,
+                                           m->prod, s));
   std::vector<double> part(sgk::kLossBlocks);
   SG_CUDA(m, cudaMemcpyAsync(part.data(), m->d_partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   SG_CUDA(m, cudaStreamSynchronize(s));
+  if (int e = check_products(m, "sg_loss_grad")) return e;
   double sum = 0.0;
   for (double v : part) sum += v;
   *loss = sum / static_cast<double>(n);
@@ -340,6 +358,23 @@ int sg_sync(sg_model* m) {
   if (!m) return sg_fail(nullptr, SEM_EINVAL, "null model");
   SG_CUDA(m, cudaSetDevice(m->device));
   SG_CUDA(m, cudaStreamSynchronize(m->stream));
+  return check_products(m, "sg_sync");
+}
+
+int sg_set_option(sg_model* m, int option, int value) {
+  if (!m) return sg_fail(nullptr, SEM_EINVAL, "null model");
+  if ((option != SG_OPT_PRODUCT && option != SG_OPT_STALL_TEST) || (value != 0 && value != 1))
+    return sg_fail(m, SEM_EINVAL, "sg_set_option: unknown option or value");
+  SG_CUDA(m, cudaSetDevice(m->device));
+  SG_CUDA(m, cudaStreamSynchronize(m->stream));
+  (option == SG_OPT_PRODUCT ? m->prod.kind : m->prod.stall_test) = value;
+  return SG_OK;
+}
+
+int sg_get_option(sg_model* m, int option, int* value) {
+  if (!m || !value || (option != SG_OPT_PRODUCT && option != SG_OPT_STALL_TEST))
+    return sg_fail(m, SEM_EINVAL, "sg_get_option: bad arguments");
+  *value = option == SG_OPT_PRODUCT ? m->prod.kind : m->prod.stall_test;
   return SG_OK;
 }
 

@@ -13,29 +13,40 @@ namespace sgk {
 
 using bf16 = __nv_bfloat16;
 
+// How the products run. kind 0: warp-level mma.sync, 128/256 x 64 tiles. kind 1: tcgen05 with
+// the accumulator in tensor memory, 128 x 128 tiles. Both round the operands to bfloat16
+// (nearest even) and accumulate in float32. err: a device word that a kind-1 product sets to 1
+// when one of its bounded waits for the tensor cores runs out (required for kind 1).
+struct Products {
+  int kind = 1;
+  int* err = nullptr;
+  int stall_test = 0;  // 1: every kind-1 product waits for a phase nothing completes (tests the limit)
+};
+
 // Split-K workspace need (floats) of the weight-gradient products for an M x N result.
 size_t splitk_floats(int M, int N, int K);
 
 // Y = act(X W^T + b): X [B][K], W [N][K] (bf16), pre/out [B][N]; out may alias nothing.
 int linear_forward(int B, int K, int N, const float* X, const bf16* W, const float* bias, float* pre, float* out,
-                   bool gelu, cudaStream_t s);
+                   bool gelu, const Products& pr, cudaStream_t s);
 // dX [B][K] = dZ [B][N] W [N][K]
-int linear_backward_data(int B, int K, int N, const float* dZ, const bf16* W, float* dX, cudaStream_t s);
+int linear_backward_data(int B, int K, int N, const float* dZ, const bf16* W, float* dX, const Products& pr,
+                         cudaStream_t s);
 // dW [N][K] = dZ^T X; db [N] = column sums of dZ
 int linear_backward_weight(int B, int K, int N, const float* dZ, const float* X, float* dW, float* db, float* ws,
-                           cudaStream_t s);
+                           const Products& pr, cudaStream_t s);
 
 // Width-3 'same' convolution of the input upsampled by `up` along time:
 // pre[b][o][t] = bias[o] + sum_{c,d} W[o][c][d] X[b][c][(t + d - 1) / up] (zero outside),
 // t < L = Lin * up; out = gelu(pre) when out != nullptr.
 int conv_forward(int B, int Ci, int Co, int Lin, int up, const float* X, const bf16* W, const float* bias,
-                 float* pre, float* out, cudaStream_t s);
+                 float* pre, float* out, const Products& pr, cudaStream_t s);
 // dX [B][Ci][Lin] from dZ [B][Co][L] (the upsampling adjoint sums the repeated samples)
 int conv_backward_data(int B, int Ci, int Co, int Lin, int up, const float* dZ, const bf16* W, float* dX,
-                       cudaStream_t s);
+                       const Products& pr, cudaStream_t s);
 // dW [Co][Ci][3] and db [Co]
 int conv_backward_weight(int B, int Ci, int Co, int Lin, int up, const float* dZ, const float* X, float* dW,
-                         float* db, float* ws, cudaStream_t s);
+                         float* db, float* ws, const Products& pr, cudaStream_t s);
 
 // dz[i] *= gelu'(pre[i])
 int gelu_backward(size_t n, const float* pre, float* dz, cudaStream_t s);

@@ -122,6 +122,229 @@ __global__ void __launch_bounds__(2 * BM) gemm_kernel(int M, int N, int K, int k
       }
 }
 
+// ---- the same product on the fifth-generation tensor cores ------------------------------------
+// C[m][n] = sum_k A(m, k) B(k, n) with tcgen05: a 128 x 128 tile per CTA, the float32
+// accumulator in tensor memory (TMEM lanes = the 128 rows, 128 columns). Eight warps stage the
+// operands: the same loader functors read float32 values, which are rounded to bfloat16
+// (nearest even) and stored in shared memory in the canonical K-major layout of 8-row x
+// 16-byte core matrices without swizzle (core (g, j) of an operand, rows 8g..8g+7 and K
+// elements 8j..8j+7 of the stage, at byte (j * 16 + g) * 128). Each warp writes one whole core
+// matrix per store instruction (8 rows x 4 words: no bank conflict), and lanes follow the
+// operand's contiguous index so the global reads are sector-dense. One thread issues the
+// MMAs (M = 128, N = 128, K = 16 each) and commits them to the stage's mbarrier, which tells
+// the loaders when the stage may be overwritten: four stages of K = 32, so the loads of later
+// stages overlap the MMAs of earlier ones. The epilogue reads TMEM (tcgen05.ld, 32 lanes x 32
+// columns per warp and load), stages the tile in shared memory and calls EP (or stores a
+// split-K partial) with consecutive threads on consecutive n. Every wait is bounded: a stage
+// whose MMAs do not complete within kTcWaitNs sets *err, and the CTA frees its TMEM and
+// returns.
+constexpr int TC_BM = 128;                     // tile rows = MMA M = TMEM lanes
+constexpr int TC_BN = 128;                     // tile columns = MMA N = TMEM columns
+constexpr int TC_BK = 32;                      // K of a stage
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 256;
+constexpr int TC_CORE = 128;                   // bytes of a core matrix
+constexpr int TC_GROUPS = TC_BM / 8;           // 8-row groups of an operand tile (BM == BN)
+constexpr int TC_KCORES = TC_BK / 8;           // core matrices along K in a stage
+constexpr int TC_OPERAND = TC_GROUPS * TC_KCORES * TC_CORE;  // 8 KB
+constexpr int TC_STAGE = 2 * TC_OPERAND;                     // A then B
+constexpr uint32_t TC_LBO = TC_GROUPS * TC_CORE;             // next core along K
+constexpr uint32_t TC_SBO = TC_CORE;                         // next 8-row group
+constexpr int TC_EPI_LD = TC_BN + 1;                         // floats per staged output row
+constexpr int TC_DATA = 100 * 1024;  // >= TC_STAGES * TC_STAGE and TC_BM * TC_EPI_LD * 4
+constexpr int TC_SMEM = TC_DATA + 64;                        // + mbarriers and the TMEM address
+constexpr unsigned long long kTcWaitNs = 2000000000ull;      // 2 s
+static_assert(TC_STAGES * TC_STAGE <= TC_DATA && TC_BM * TC_EPI_LD * 4 <= TC_DATA, "shared memory plan");
+static_assert(TC_GROUPS * TC_KCORES % (TC_THREADS / 32) == 0 && TC_BN / 2 % 32 == 0, "tile plan");
+
+// Instruction descriptor of tcgen05.mma kind::f16: float32 D (bits 4-5 = 1), bfloat16 A and B
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(TC_BN >> 3) << 17) |
+                              (static_cast<uint32_t>(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// Shared-memory matrix descriptor: start, leading (K) and stride (8-row) byte offsets, all
+// >> 4; bit 46 = descriptor version 1; no swizzle, base offset 0.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((TC_LBO >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((TC_SBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of the given parity to complete; false after limit_ns.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns = kTcWaitNs) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_test(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// One core-matrix row word: two consecutive K elements of one row, as packed bfloat16.
+template <bool ALONG_ROWS, class F>
+__device__ __forceinline__ void tc_fill_core(uint8_t* op, int g, int j, int row0, int rows, int k0, int kend,
+                                             int lane, F load) {
+  const int r = ALONG_ROWS ? (lane & 7) : (lane >> 2);
+  const int w = ALONG_ROWS ? (lane >> 3) : (lane & 3);
+  const int row = row0 + g * 8 + r;
+  const int k = k0 + j * 8 + 2 * w;
+  const bool in = row < rows;
+  const float v0 = (in && k < kend) ? load(row, k) : 0.f;
+  const float v1 = (in && k + 1 < kend) ? load(row, k + 1) : 0.f;
+  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(v0));
+  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(v1));
+  *reinterpret_cast<uint32_t*>(op + (j * TC_GROUPS + g) * TC_CORE + r * 16 + w * 4) = lo | (hi << 16);
+}
+
+// B(k, n) read as rows n of a K-major operand
+template <class LB>
+struct RowsOfB {
+  LB lb;
+  __device__ float operator()(int n, int k) const { return lb(k, n); }
+};
+
+template <class LA, class LB, class EP>
+__global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K, int kchunk, LA la, LB lb, EP ep,
+                                                              float* ws, int* err, int stall_test) {
+  extern __shared__ __align__(128) uint8_t tc_smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + TC_DATA);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + TC_STAGES);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int nst = kend > kbeg ? (kend - kbeg + TC_BK - 1) / TC_BK : 0;
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                 "r"(TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const RowsOfB<LB> b_load{lb};
+  int issued = 0;
+  bool late = false;
+  // stall test: wait (20 ms limit) for a phase that no commit completes
+  if (stall_test && !mbar_wait(smem_addr(&bars[0]), 0, 20000000ull)) late = true;
+  if (__syncthreads_or(late)) issued = -1;
+  for (int s = 0; s < nst && issued >= 0; ++s) {
+    const int buf = s % TC_STAGES;
+    if (s >= TC_STAGES && !mbar_wait(smem_addr(&bars[buf]), ((s / TC_STAGES) - 1) & 1)) late = true;
+    uint8_t* a_op = tc_smem + buf * TC_STAGE;
+    uint8_t* b_op = a_op + TC_OPERAND;
+    const int k0 = kbeg + s * TC_BK;
+    if (!late) {
+      constexpr int kCoresPerWarp = TC_GROUPS * TC_KCORES / (TC_THREADS / 32);
+#pragma unroll
+      for (int i = 0; i < kCoresPerWarp; ++i) {
+        const int c = warp + i * (TC_THREADS / 32);
+        tc_fill_core<!LA::kAlongK>(a_op, c % TC_GROUPS, c / TC_GROUPS, m0, M, k0, kend, lane, la);
+      }
+#pragma unroll
+      for (int i = 0; i < kCoresPerWarp; ++i) {
+        const int c = warp + i * (TC_THREADS / 32);
+        tc_fill_core<LB::kAlongN>(b_op, c % TC_GROUPS, c / TC_GROUPS, n0, N, k0, kend, lane, b_load);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(late)) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a_addr = smem_addr(a_op), b_addr = smem_addr(b_op);
+#pragma unroll
+      for (int j = 0; j < TC_KCORES / 2; ++j) {
+        const uint32_t acc = (s | j) != 0;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem), "l"(tc_desc(a_addr + 2 * j * TC_LBO)), "l"(tc_desc(b_addr + 2 * j * TC_LBO)),
+            "r"(kTcIdesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&bars[buf]))
+                   : "memory");
+    }
+    ++issued;
+  }
+  if (issued < 0) issued = 0;
+  if (issued > 0) {
+    const int ls = issued - 1;
+    if (!mbar_wait(smem_addr(&bars[ls % TC_STAGES]), (ls / TC_STAGES) & 1)) late = true;
+  }
+  const bool failed = __syncthreads_or(late) != 0;
+  tc_fence_after();
+  float* tile = reinterpret_cast<float*>(tc_smem);
+  if (!failed) {
+    const int q = warp & 3, h = warp >> 2;
+    float* row = tile + (q * 32 + lane) * TC_EPI_LD + h * (TC_BN / 2);
+#pragma unroll
+    for (int c = 0; c < TC_BN / 2; c += 32) {
+      uint32_t v[32];
+      if (issued > 0) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(h * (TC_BN / 2) + c)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) row[c + i] = __uint_as_float(v[i]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    return;
+  }
+  for (int idx = tid; idx < TC_BM * TC_BN; idx += TC_THREADS) {
+    const int mm = idx / TC_BN, nn = idx - mm * TC_BN;
+    const int m = m0 + mm, n = n0 + nn;
+    if (m < M && n < N) {
+      const float v = tile[mm * TC_EPI_LD + nn];
+      if (ws)
+        ws[(static_cast<size_t>(blockIdx.z) * M + m) * N + n] = v;
+      else
+        ep(m, n, v);
+    }
+  }
+}
+
 template <class EP>
 __global__ void splitk_finalize_kernel(int M, int N, int splits, const float* __restrict__ ws, EP ep) {
   const size_t total = static_cast<size_t>(M) * N;
@@ -140,10 +363,13 @@ int grid_for(size_t n) {
 
 int tile_rows(int M) { return M >= 512 ? 256 : 128; }
 
-int splits_for(int M, int N, int K) {
-  const int BM = tile_rows(M);
-  const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  int s = (608 + tiles - 1) / tiles;
+// CTAs that fill the GPU once: 152 SMs x resident CTAs of the product kernel
+int splits_for(int M, int N, int K, int kind) {
+  const int bm = kind == 1 ? TC_BM : tile_rows(M);
+  const int bn = kind == 1 ? TC_BN : BN;
+  const int fill = kind == 1 ? 152 * 2 : 152 * 4;
+  const int tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+  int s = (fill + tiles - 1) / tiles;
   const int kmax = (K + 255) / 256;
   if (s > kmax) s = kmax;
   if (s > 64) s = 64;
@@ -151,17 +377,27 @@ int splits_for(int M, int N, int K) {
 }
 
 template <class LA, class LB, class EP>
-int run_gemm(int M, int N, int K, LA la, LB lb, EP ep, float* ws, bool allow_split, cudaStream_t s) {
+int run_gemm(int M, int N, int K, LA la, LB lb, EP ep, float* ws, bool allow_split, const Products& pr,
+             cudaStream_t s) {
   if (M <= 0 || N <= 0) return 0;
-  const int splits = (allow_split && ws) ? splits_for(M, N, K) : 1;
+  if (pr.kind != 0 && (pr.kind != 1 || !pr.err)) return static_cast<int>(cudaErrorInvalidValue);
+  const int splits = (allow_split && ws) ? splits_for(M, N, K, pr.kind) : 1;
+  static_assert(BKM == TC_BK, "one K granule for both product kernels");
   int kchunk = (K + splits - 1) / splits;
   kchunk = (kchunk + BKM - 1) / BKM * BKM;
   const int used = K > 0 ? (K + kchunk - 1) / kchunk : 1;
   float* part = used > 1 ? ws : nullptr;
-  if (tile_rows(M) == 256)
+  if (pr.kind == 1) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(tc_gemm_kernel<LA, LB, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    tc_gemm_kernel<LA, LB, EP><<<dim3((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, used), TC_THREADS, TC_SMEM,
+                                 s>>>(M, N, K, kchunk, la, lb, ep, part, pr.err, pr.stall_test);
+  } else if (tile_rows(M) == 256) {
     gemm_kernel<256><<<dim3((N + BN - 1) / BN, (M + 255) / 256, used), 512, 0, s>>>(M, N, K, kchunk, la, lb, ep, part);
-  else
+  } else {
     gemm_kernel<128><<<dim3((N + BN - 1) / BN, (M + 127) / 128, used), 256, 0, s>>>(M, N, K, kchunk, la, lb, ep, part);
+  }
   if (used > 1)
     splitk_finalize_kernel<<<grid_for(static_cast<size_t>(M) * N), 256, 0, s>>>(M, N, used, ws, ep);
   return static_cast<int>(cudaGetLastError());
@@ -408,46 +644,46 @@ __global__ void to_bf16_kernel(size_t n, const float* __restrict__ p, bf16* __re
 }  // namespace
 
 size_t splitk_floats(int M, int N, int K) {
-  const int s = splits_for(M, N, K);
+  const int s = max(splits_for(M, N, K, 0), splits_for(M, N, K, 1));
   return s > 1 ? static_cast<size_t>(s) * M * N : 0;
 }
 
 int linear_forward(int B, int K, int N, const float* X, const bf16* W, const float* bias, float* pre, float* out,
-                   bool act, cudaStream_t s) {
-  return run_gemm(B, N, K, RowMajorA{X, K}, WeightColB{W, K}, LinearEp{pre, out, bias, N, act}, nullptr, false, s);
+                   bool act, const Products& pr, cudaStream_t s) {
+  return run_gemm(B, N, K, RowMajorA{X, K}, WeightColB{W, K}, LinearEp{pre, out, bias, N, act}, nullptr, false, pr, s);
 }
 
-int linear_backward_data(int B, int K, int N, const float* dZ, const bf16* W, float* dX, cudaStream_t s) {
-  return run_gemm(B, K, N, RowMajorA{dZ, N}, WeightRowB{W, K}, StoreEp{dX, K}, nullptr, false, s);
+int linear_backward_data(int B, int K, int N, const float* dZ, const bf16* W, float* dX, const Products& pr, cudaStream_t s) {
+  return run_gemm(B, K, N, RowMajorA{dZ, N}, WeightRowB{W, K}, StoreEp{dX, K}, nullptr, false, pr, s);
 }
 
 int linear_backward_weight(int B, int K, int N, const float* dZ, const float* X, float* dW, float* db, float* ws,
-                           cudaStream_t s) {
-  int r = run_gemm(N, K, B, ColMajorA{dZ, N}, RowMajorB{X, K}, StoreEp{dW, K}, ws, true, s);
+                           const Products& pr, cudaStream_t s) {
+  int r = run_gemm(N, K, B, ColMajorA{dZ, N}, RowMajorB{X, K}, StoreEp{dW, K}, ws, true, pr, s);
   if (r) return r;
   column_sums_kernel<<<grid_for(N), 256, 0, s>>>(B, N, dZ, db);
   return static_cast<int>(cudaGetLastError());
 }
 
 int conv_forward(int B, int Ci, int Co, int Lin, int up, const float* X, const bf16* W, const float* bias,
-                 float* pre, float* out, cudaStream_t s) {
+                 float* pre, float* out, const Products& pr, cudaStream_t s) {
   const int L = Lin * up;
   return run_gemm(Co, B * L, Ci * 3, ConvWeightA{W, Ci * 3}, ConvInputB{X, Ci, Lin, L, up},
-                  ConvEp{pre, out, bias, Co, L}, nullptr, false, s);
+                  ConvEp{pre, out, bias, Co, L}, nullptr, false, pr, s);
 }
 
 int conv_backward_data(int B, int Ci, int Co, int Lin, int up, const float* dZ, const bf16* W, float* dX,
-                       cudaStream_t s) {
+                       const Products& pr, cudaStream_t s) {
   const int L = Lin * up;
   return run_gemm(Ci, B * Lin, Co * 3 * up, ConvWeightTA{W, Ci, up}, ConvGradB{dZ, Co, Lin, L, up},
-                  ConvDataEp{dX, Ci, Lin}, nullptr, false, s);
+                  ConvDataEp{dX, Ci, Lin}, nullptr, false, pr, s);
 }
 
 int conv_backward_weight(int B, int Ci, int Co, int Lin, int up, const float* dZ, const float* X, float* dW,
-                         float* db, float* ws, cudaStream_t s) {
+                         float* db, float* ws, const Products& pr, cudaStream_t s) {
   const int L = Lin * up;
   int r = run_gemm(Co, Ci * 3, B * L, ConvGradA{dZ, Co, L}, ConvInputWB{X, Ci, Lin, L, up}, StoreEp{dW, Ci * 3}, ws,
-                   true, s);
+                   true, pr, s);
   if (r) return r;
   channel_sums_kernel<<<Co, 256, 0, s>>>(B, Co, L, dZ, db);
   return static_cast<int>(cudaGetLastError());

@@ -18,6 +18,8 @@ from . import inputs, sem
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _F = ctypes.c_float
+SG_OPT_PRODUCT = 1  # product kernel: 1 tcgen05 (default), 0 warp mma.sync
+SG_OPT_STALL_TEST = 2  # tests only: tcgen05 products wait until their limit runs out
 
 # name: (restype, argtypes) for every symbol declared in include/surrogate.h
 SIGNATURES = {
@@ -31,6 +33,8 @@ SIGNATURES = {
     "sg_get_grads": (_I, [_P, _P]),
     "sg_adam_step": (_I, [_P, _F, _F, _F, _F]),
     "sg_sync": (_I, [_P]),
+    "sg_set_option": (_I, [_P, _I, _I]),
+    "sg_get_option": (_I, [_P, _I, _P]),
     "sg_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -176,6 +180,20 @@ class Model:
 
     def sync(self):
         _check(lib().sg_sync(self.handle), "sg_sync", self)
+
+    @property
+    def product(self) -> int:
+        """Product kernel: 1 = tcgen05 with TMEM accumulators (default), 0 = warp mma.sync."""
+        out = ctypes.c_int(0)
+        _check(lib().sg_get_option(self.handle, SG_OPT_PRODUCT, ctypes.byref(out)), "sg_get_option", self)
+        return out.value
+
+    @product.setter
+    def product(self, kind: int):
+        _check(lib().sg_set_option(self.handle, SG_OPT_PRODUCT, int(kind)), "sg_set_option", self)
+
+    def set_option(self, option: int, value: int):
+        _check(lib().sg_set_option(self.handle, int(option), int(value)), "sg_set_option", self)
 
 
 # ---- training data, training, fallback ---------------------------------------------------------

@@ -2,8 +2,10 @@
 C ABI: forward outputs, the loss, every parameter gradient and an Adam step. The oracle
 takes the bfloat16-rounded weights the kernels read (biases stay float32).
 
-The kernels run their products on the tensor cores with bfloat16 operands (activations and
-gradients rounded to nearest even, weights stored so) and float32 accumulation; the oracle
+The kernels run their products on the tensor cores (tcgen05 with TMEM accumulators by
+default, warp-level mma.sync as the alternative; both are tested) with bfloat16 operands
+(activations and gradients rounded to nearest even, weights stored so) and float32
+accumulation; the oracle
 rounds the same operands (bf16_operands=True) in float64. Tolerances: relative L2 <= 2e-3
 for outputs and gradients, 1e-3 for the loss: an operand whose float32 and float64 values
 straddle a bfloat16 rounding boundary rounds differently on the two sides (2^-8 relative
@@ -58,11 +60,14 @@ def tiny_contract_spec():
     return surrogate.Spec(in_dim=9, hidden=24, c0=6, l0=7, stage_cout=(10, 8, 12), stage_up=(2, 2, 1), contract=6)
 
 
+@pytest.mark.parametrize("product", [1, 0])
 @pytest.mark.parametrize("contract", [False, True])
-def test_loss_and_gradients_match_oracle(so, contract):
+def test_loss_and_gradients_match_oracle(so, contract, product):
     from paper_2606_12850_gb300 import surrogate
     spec = tiny_contract_spec() if contract else tiny_spec()
     m = surrogate.Model(spec, max_batch=70)
+    m.product = product
+    assert m.product == product
     flat = spec.init_params(5)
     flat += inputs.uniform(6, flat.shape, -0.05, 0.05).astype(np.float32)  # nonzero biases
     m.set_params(flat)
@@ -86,12 +91,14 @@ def test_loss_and_gradients_match_oracle(so, contract):
     assert rel_l2(y.cpu().numpy(), exact_y) <= 3e-2
 
 
-def test_full_size_forward_matches_oracle(so):
+@pytest.mark.parametrize("product", [1, 0])
+def test_full_size_forward_matches_oracle(so, product):
     """The default network (9 -> 512 -> 512 -> [64][125] -> 1000 samples of 6 x 192 channels
     combined with the moment entries) on three inputs, run in chunks smaller than the batch."""
     from paper_2606_12850_gb300 import surrogate
     spec = surrogate.Spec()
     m = surrogate.Model(spec, max_batch=2)
+    m.product = product
     flat = spec.init_params(9)
     m.set_params(flat)
     x = inputs.uniform(10, (3, 9), -1, 1).astype(np.float32)
@@ -188,3 +195,57 @@ def test_trained_surrogate_beats_the_nearest_run_and_the_solver_time():
           f"network {t_net * 1e3:.1f} ms vs solver {te.seconds * 1e3:.1f} ms")
     assert err < err_nn
     assert t_net < te.seconds
+
+
+def test_product_kernels_agree_at_full_size():
+    """tcgen05 (TMEM accumulators, 128 x 128 tiles) against mma.sync (128/256 x 64 tiles) on
+    the default network: loss, every gradient and the output of a ragged batch of 75 runs
+    (several 128-wide tiles and a tail in every product, split-K in the weight gradients). The
+    two round the same operands to bfloat16 and differ only in the order of float32 sums, which
+    can move an activation across a bfloat16 rounding boundary: 2e-3 relative L2 as against
+    the oracle."""
+    from paper_2606_12850_gb300 import surrogate
+    spec = surrogate.Spec()
+    flat = spec.init_params(31)
+    flat += inputs.uniform(32, flat.shape, -0.02, 0.02).astype(np.float32)
+    B = 75
+    x = torch.from_numpy(inputs.uniform(33, (B, 9), -1, 1).astype(np.float32)).cuda()
+    t = torch.from_numpy(inputs.uniform(34, (B, spec.out_c, spec.out_l), -1, 1).astype(np.float32)).cuda()
+    outs = []
+    for product in (0, 1):
+        m = surrogate.Model(spec, max_batch=B)
+        m.product = product
+        m.set_params(flat)
+        loss = m.loss_grad(x, t)
+        y = torch.empty((B, spec.out_c, spec.out_l), device="cuda")
+        m.forward(x, y)
+        m.sync()
+        outs.append((loss, spec.split(m.get_grads()), y.cpu().numpy()))
+    (l0, g0, y0), (l1, g1, y1) = outs
+    assert abs(l1 - l0) <= 1e-4 * l0
+    for name in g0:
+        assert rel_l2(g1[name], g0[name].astype(np.float64)) <= 2e-3, name
+    assert rel_l2(y1, y0.astype(np.float64)) <= 2e-3
+
+
+def test_product_wait_limit_reports_timeout():
+    """A tcgen05 product that waits for an mbarrier phase nothing completes (the stall test)
+    gives up after its limit: the call reports SEM_ETIMEOUT, and with the test switched off
+    the same model computes the same loss and gradients as a fresh one."""
+    from paper_2606_12850_gb300 import surrogate
+    spec = tiny_spec()
+    flat = spec.init_params(41)
+    x = torch.from_numpy(inputs.uniform(42, (16, 9), -1, 1).astype(np.float32)).cuda()
+    t = torch.from_numpy(inputs.uniform(43, (16, spec.out_c, spec.out_l), -1, 1).astype(np.float32)).cuda()
+    m = surrogate.Model(spec, max_batch=16)
+    m.set_params(flat)
+    m.set_option(surrogate.SG_OPT_STALL_TEST, 1)
+    with pytest.raises(sem.SemError) as info:
+        m.loss_grad(x, t)
+    assert info.value.code == -5 and "timed out" in str(info.value)
+    m.set_option(surrogate.SG_OPT_STALL_TEST, 0)
+    loss = m.loss_grad(x, t)
+    fresh = surrogate.Model(spec, max_batch=16)
+    fresh.set_params(flat)
+    assert loss == fresh.loss_grad(x, t)
+    assert np.array_equal(m.get_grads(), fresh.get_grads())
