@@ -51,7 +51,8 @@ typedef struct sg_model sg_model;
 /* Create a model on device `device`, working on `stream` (a cudaStream_t, or NULL for a
  * stream of its own). stage_cout[nstages] and stage_up[nstages] (1 or 2) describe the
  * decoder; max_batch bounds the batch of sg_loss_grad (sg_forward runs larger batches in
- * chunks of max_batch). Parameters start at zero (set them with sg_set_params). */
+ * chunks of max_batch), and max_batch x the output length must be below 2^24. Parameters
+ * start at zero (set them with sg_set_params). */
 int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, int c0, int l0, int nstages,
               const int32_t* stage_cout, const int32_t* stage_up, int contract, int max_batch);
 int sg_destroy(sg_model* model);

@@ -147,6 +147,12 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
     delete m;
     return sg_fail(nullptr, SEM_EINVAL, "sg_create: contract must divide the last stage's channels and be <= in_dim");
   }
+  // the products' index maps divide sample indices (up to max_batch x length) by a float
+  // reciprocal, exact below 2^24
+  if (static_cast<long long>(max_batch) * l >= (1LL << 24)) {
+    delete m;
+    return sg_fail(nullptr, SEM_EINVAL, "sg_create: max_batch x output length must be below 2^24");
+  }
   m->contract = contract;
   m->out_c = contract ? c / contract : c;
   m->out_l = l;

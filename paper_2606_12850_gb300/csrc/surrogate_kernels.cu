@@ -151,11 +151,12 @@ constexpr int TC_STAGE = 2 * TC_OPERAND;                     // A then B
 constexpr uint32_t TC_LBO = TC_GROUPS * TC_CORE;             // next core along K
 constexpr uint32_t TC_SBO = TC_CORE;                         // next 8-row group
 constexpr int TC_EPI_LD = TC_BN + 1;                         // floats per staged output row
-constexpr int TC_DATA = 100 * 1024;  // >= TC_STAGES * TC_STAGE and TC_BM * TC_EPI_LD * 4
+// operand stages, then (reused) the epilogue's output tile; 3 CTAs a SM (3 x 128 TMEM columns)
+constexpr int TC_DATA = (TC_STAGES * TC_STAGE > TC_BM * TC_EPI_LD * 4 ? TC_STAGES * TC_STAGE : TC_BM * TC_EPI_LD * 4);
 constexpr int TC_SMEM = TC_DATA + 64;                        // + mbarriers and the TMEM address
 constexpr unsigned long long kTcWaitNs = 2000000000ull;      // 2 s
 static_assert(TC_STAGES * TC_STAGE <= TC_DATA && TC_BM * TC_EPI_LD * 4 <= TC_DATA, "shared memory plan");
-static_assert(TC_GROUPS * TC_KCORES % (TC_THREADS / 32) == 0 && TC_BN / 2 % 32 == 0, "tile plan");
+static_assert(TC_GROUPS == 2 * (TC_THREADS / 32) && TC_BN / 2 % 32 == 0, "tile plan: two row groups a warp");
 
 // Instruction descriptor of tcgen05.mma kind::f16: float32 D (bits 4-5 = 1), bfloat16 A and B
 // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at
@@ -197,27 +198,36 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limi
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// One core-matrix row word: two consecutive K elements of one row, as packed bfloat16.
+// The part of one operand stage that a lane writes: one word (two consecutive K elements of
+// one row, packed bfloat16) in each core matrix (g, j) with g in {warp, warp + 8} and j < 4.
+// The lane's two rows and their loader state stay fixed for the whole K loop.
 template <bool ALONG_ROWS, class F>
-__device__ __forceinline__ void tc_fill_core(uint8_t* op, int g, int j, int row0, int rows, int k0, int kend,
-                                             int lane, F load) {
-  const int r = ALONG_ROWS ? (lane & 7) : (lane >> 2);
-  const int w = ALONG_ROWS ? (lane >> 3) : (lane & 3);
-  const int row = row0 + g * 8 + r;
-  const int k = k0 + j * 8 + 2 * w;
-  const bool in = row < rows;
-  const float v0 = (in && k < kend) ? load(row, k) : 0.f;
-  const float v1 = (in && k + 1 < kend) ? load(row, k + 1) : 0.f;
-  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(v0));
-  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(v1));
-  *reinterpret_cast<uint32_t*>(op + (j * TC_GROUPS + g) * TC_CORE + r * 16 + w * 4) = lo | (hi << 16);
-}
-
-// B(k, n) read as rows n of a K-major operand
-template <class LB>
-struct RowsOfB {
-  LB lb;
-  __device__ float operator()(int n, int k) const { return lb(k, n); }
+struct CoreFiller {
+  typename F::Row rs[2];
+  bool in[2];
+  int r, w;
+  __device__ void init(const F& f, int row0, int rows, int warp, int lane) {
+    r = ALONG_ROWS ? (lane & 7) : (lane >> 2);
+    w = ALONG_ROWS ? (lane >> 3) : (lane & 3);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = row0 + (warp + 8 * h) * 8 + r;
+      in[h] = i < rows;
+      rs[h] = f.row(in[h] ? i : row0);
+    }
+  }
+  __device__ void fill(const F& f, uint8_t* op, int k0, int kend, int warp) const {
+#pragma unroll
+    for (int i = 0; i < 2 * TC_KCORES; ++i) {
+      const int h = i & 1, j = i >> 1;
+      const int k = k0 + j * 8 + 2 * w;
+      const float v0 = (in[h] && k < kend) ? f.at(rs[h], k) : 0.f;
+      const float v1 = (in[h] && k + 1 < kend) ? f.at(rs[h], k + 1) : 0.f;
+      const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(v0));
+      const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(v1));
+      *reinterpret_cast<uint32_t*>(op + (j * TC_GROUPS + warp + 8 * h) * TC_CORE + r * 16 + w * 4) = lo | (hi << 16);
+    }
+  }
 };
 
 template <class LA, class LB, class EP>
@@ -227,10 +237,16 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
   uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + TC_DATA);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + TC_STAGES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+  // tiles numbered m-fastest, so the row tiles that share a column block run side by side
+  const int mt = (M + TC_BM - 1) / TC_BM;
+  const int m0 = (blockIdx.x % mt) * TC_BM, n0 = (blockIdx.x / mt) * TC_BN;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   const int nst = kend > kbeg ? (kend - kbeg + TC_BK - 1) / TC_BK : 0;
+  CoreFiller<!LA::kAlongK, LA> fa;
+  CoreFiller<LB::kAlongN, LB> fb;
+  fa.init(la, m0, M, warp, lane);
+  fb.init(lb, n0, N, warp, lane);
   if (tid == 0) {
     for (int s = 0; s < TC_STAGES; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[s])) : "memory");
@@ -246,7 +262,6 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const RowsOfB<LB> b_load{lb};
   int issued = 0;
   bool late = false;
   // stall test: wait (20 ms limit) for a phase that no commit completes
@@ -259,17 +274,8 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
     uint8_t* b_op = a_op + TC_OPERAND;
     const int k0 = kbeg + s * TC_BK;
     if (!late) {
-      constexpr int kCoresPerWarp = TC_GROUPS * TC_KCORES / (TC_THREADS / 32);
-#pragma unroll
-      for (int i = 0; i < kCoresPerWarp; ++i) {
-        const int c = warp + i * (TC_THREADS / 32);
-        tc_fill_core<!LA::kAlongK>(a_op, c % TC_GROUPS, c / TC_GROUPS, m0, M, k0, kend, lane, la);
-      }
-#pragma unroll
-      for (int i = 0; i < kCoresPerWarp; ++i) {
-        const int c = warp + i * (TC_THREADS / 32);
-        tc_fill_core<LB::kAlongN>(b_op, c % TC_GROUPS, c / TC_GROUPS, n0, N, k0, kend, lane, b_load);
-      }
+      fa.fill(la, a_op, k0, kend, warp);
+      fb.fill(lb, b_op, k0, kend, warp);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (__syncthreads_or(late)) break;
@@ -367,7 +373,7 @@ int tile_rows(int M) { return M >= 512 ? 256 : 128; }
 int splits_for(int M, int N, int K, int kind) {
   const int bm = kind == 1 ? TC_BM : tile_rows(M);
   const int bn = kind == 1 ? TC_BN : BN;
-  const int fill = kind == 1 ? 152 * 2 : 152 * 4;
+  const int fill = kind == 1 ? 152 * 3 : 152 * 4;
   const int tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
   int s = (fill + tiles - 1) / tiles;
   const int kmax = (K + 255) / 256;
@@ -391,8 +397,10 @@ int run_gemm(int M, int N, int K, LA la, LB lb, EP ep, float* ws, bool allow_spl
     const cudaError_t e =
         cudaFuncSetAttribute(tc_gemm_kernel<LA, LB, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) return static_cast<int>(e);
-    tc_gemm_kernel<LA, LB, EP><<<dim3((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, used), TC_THREADS, TC_SMEM,
-                                 s>>>(M, N, K, kchunk, la, lb, ep, part, pr.err, pr.stall_test);
+    const long long tiles = static_cast<long long>((M + TC_BM - 1) / TC_BM) * ((N + TC_BN - 1) / TC_BN);
+    if (tiles > 0x7FFFFFFFLL) return static_cast<int>(cudaErrorInvalidValue);
+    tc_gemm_kernel<LA, LB, EP><<<dim3(static_cast<unsigned>(tiles), 1, used), TC_THREADS, TC_SMEM, s>>>(
+        M, N, K, kchunk, la, lb, ep, part, pr.err, pr.stall_test);
   } else if (tile_rows(M) == 256) {
     gemm_kernel<256><<<dim3((N + BN - 1) / BN, (M + 255) / 256, used), 512, 0, s>>>(M, N, K, kchunk, la, lb, ep, part);
   } else {
@@ -404,97 +412,169 @@ int run_gemm(int M, int N, int K, LA la, LB lb, EP ep, float* ws, bool allow_spl
 }
 
 // ---- loaders ------------------------------------------------------------------------------
+// Each loader reads one operand as float32: A(m, k) or B(k, n). row(i) gathers what depends on
+// the row alone (i = m for A, n for B) and at(row, k) reads one element, so the tcgen05 kernel,
+// whose lanes keep their rows for the whole K loop, computes the row part once; operator()
+// combines the two for the mma.sync kernel. kAlongK / kAlongN: the index that is contiguous in
+// memory. In the convolutions up is 1 or 2 and ush = up / 2 shifts the upsampling's index map.
+
+// q = k / d for 0 <= k < 2^24, from a float reciprocal and one correction step (the float
+// quotient is within 1 of the exact one there).
+struct DivBy {
+  int d;
+  float inv;
+  __device__ __forceinline__ int operator()(int k) const {
+    int q = __float2int_rz(__int2float_rn(k) * inv);
+    const int r = k - q * d;
+    q += (r >= d) - (r < 0);
+    return q;
+  }
+};
+DivBy div_by(int d) { return DivBy{d, 1.0f / static_cast<float>(d)}; }
+
 struct RowMajorA {  // A(m, k) = P[m * ld + k]
   static constexpr bool kAlongK = true;
   const float* P;
   int ld;
-  __device__ float operator()(int m, int k) const { return P[static_cast<size_t>(m) * ld + k]; }
+  using Row = const float*;
+  __device__ Row row(int m) const { return P + static_cast<size_t>(m) * ld; }
+  __device__ float at(Row p, int k) const { return p[k]; }
+  __device__ float operator()(int m, int k) const { return at(row(m), k); }
 };
 struct ColMajorA {  // A(m, k) = P[k * ld + m]
   static constexpr bool kAlongK = false;
   const float* P;
   int ld;
-  __device__ float operator()(int m, int k) const { return P[static_cast<size_t>(k) * ld + m]; }
+  using Row = const float*;
+  __device__ Row row(int m) const { return P + m; }
+  __device__ float at(Row p, int k) const { return p[static_cast<size_t>(k) * ld]; }
+  __device__ float operator()(int m, int k) const { return at(row(m), k); }
 };
 struct RowMajorB {  // B(k, n) = P[k * ld + n]
   static constexpr bool kAlongN = true;
   const float* P;
   int ld;
-  __device__ float operator()(int k, int n) const { return P[static_cast<size_t>(k) * ld + n]; }
+  using Row = const float*;
+  __device__ Row row(int n) const { return P + n; }
+  __device__ float at(Row p, int k) const { return p[static_cast<size_t>(k) * ld]; }
+  __device__ float operator()(int k, int n) const { return at(row(n), k); }
 };
 struct WeightRowB {  // B(k, n) = W[k * ld + n], bf16
   static constexpr bool kAlongN = true;
   const bf16* W;
   int ld;
-  __device__ float operator()(int k, int n) const { return __bfloat162float(W[static_cast<size_t>(k) * ld + n]); }
+  using Row = const bf16*;
+  __device__ Row row(int n) const { return W + n; }
+  __device__ float at(Row p, int k) const { return __bfloat162float(p[static_cast<size_t>(k) * ld]); }
+  __device__ float operator()(int k, int n) const { return at(row(n), k); }
 };
 struct WeightColB {  // B(k, n) = W[n * ld + k], bf16
   static constexpr bool kAlongN = false;
   const bf16* W;
   int ld;
-  __device__ float operator()(int k, int n) const { return __bfloat162float(W[static_cast<size_t>(n) * ld + k]); }
+  using Row = const bf16*;
+  __device__ Row row(int n) const { return W + static_cast<size_t>(n) * ld; }
+  __device__ float at(Row p, int k) const { return __bfloat162float(p[k]); }
+  __device__ float operator()(int k, int n) const { return at(row(n), k); }
 };
 struct ConvWeightA {  // A(o, k) = W[o][k], k = c * 3 + d
   static constexpr bool kAlongK = true;
   const bf16* W;
   int ld;
-  __device__ float operator()(int m, int k) const { return __bfloat162float(W[static_cast<size_t>(m) * ld + k]); }
+  using Row = const bf16*;
+  __device__ Row row(int m) const { return W + static_cast<size_t>(m) * ld; }
+  __device__ float at(Row p, int k) const { return __bfloat162float(p[k]); }
+  __device__ float operator()(int m, int k) const { return at(row(m), k); }
 };
 struct ConvInputB {  // B(k = c*3+d, n = b*L+t) = X[b][c][(t + d - 1) / up], zero outside [0, L)
   static constexpr bool kAlongN = true;
   const float* X;
-  int Ci, Lin, L, up;
-  __device__ float operator()(int k, int n) const {
-    const int c = k / 3, d = k - 3 * c;
-    const int b = n / L, t = n - b * L;
-    const int sidx = t + d - 1;
-    if (sidx < 0 || sidx >= L) return 0.f;
-    return X[(static_cast<size_t>(b) * Ci + c) * Lin + sidx / up];
+  int Ci, Lin, L, ush;
+  DivBy byL;
+  struct Row {
+    const float* x;  // X[b]
+    int t1;          // t - 1
+  };
+  __device__ Row row(int n) const {
+    const int b = byL(n);
+    return Row{X + static_cast<size_t>(b) * Ci * Lin, n - b * L - 1};
   }
+  __device__ float at(const Row& r, int k) const {
+    const int c = k / 3, d = k - 3 * c;
+    const int s = r.t1 + d;
+    if (static_cast<unsigned>(s) >= static_cast<unsigned>(L)) return 0.f;
+    return r.x[static_cast<size_t>(c) * Lin + (s >> ush)];
+  }
+  __device__ float operator()(int k, int n) const { return at(row(n), k); }
 };
 struct ConvWeightTA {  // A(c, k = (o*3+d)*up + r) = W[o][c][d]
   static constexpr bool kAlongK = false;
   const bf16* W;
-  int Ci, up;
-  __device__ float operator()(int m, int k) const {
-    const int od = k / up;
+  int Ci, ush;
+  using Row = const bf16*;
+  __device__ Row row(int m) const { return W + static_cast<size_t>(m) * 3; }
+  __device__ float at(Row p, int k) const {
+    const int od = k >> ush;
     const int o = od / 3, d = od - 3 * o;
-    return __bfloat162float(W[(static_cast<size_t>(o) * Ci + m) * 3 + d]);
+    return __bfloat162float(p[static_cast<size_t>(o) * Ci * 3 + d]);
   }
+  __device__ float operator()(int m, int k) const { return at(row(m), k); }
 };
 struct ConvGradB {  // B(k = (o*3+d)*up + r, n = b*Lin + t') = dZ[b][o][up t' + r - d + 1]
   static constexpr bool kAlongN = true;
   const float* dZ;
-  int Co, Lin, L, up;
-  __device__ float operator()(int k, int n) const {
-    const int od = k / up, r = k - od * up;
-    const int o = od / 3, d = od - 3 * o;
-    const int b = n / Lin, tp = n - b * Lin;
-    const int t = up * tp + r - d + 1;
-    if (t < 0 || t >= L) return 0.f;
-    return dZ[(static_cast<size_t>(b) * Co + o) * L + t];
+  int Co, Lin, L, ush;
+  DivBy byLin;
+  struct Row {
+    const float* z;  // dZ[b]
+    int t1;          // up t' + 1
+  };
+  __device__ Row row(int n) const {
+    const int b = byLin(n);
+    return Row{dZ + static_cast<size_t>(b) * Co * L, ((n - b * Lin) << ush) + 1};
   }
+  __device__ float at(const Row& rw, int k) const {
+    const int od = k >> ush, r = k - (od << ush);
+    const int o = od / 3, d = od - 3 * o;
+    const int t = rw.t1 + r - d;
+    if (static_cast<unsigned>(t) >= static_cast<unsigned>(L)) return 0.f;
+    return rw.z[static_cast<size_t>(o) * L + t];
+  }
+  __device__ float operator()(int k, int n) const { return at(row(n), k); }
 };
 struct ConvGradA {  // A(o, k = b*L + t) = dZ[b][o][t]
   static constexpr bool kAlongK = true;
   const float* dZ;
   int Co, L;
-  __device__ float operator()(int m, int k) const {
-    const int b = k / L, t = k - b * L;
-    return dZ[(static_cast<size_t>(b) * Co + m) * L + t];
+  DivBy byL;
+  using Row = const float*;
+  __device__ Row row(int m) const { return dZ + static_cast<size_t>(m) * L; }
+  __device__ float at(Row p, int k) const {
+    const int b = byL(k);
+    return p[static_cast<size_t>(b) * Co * L + (k - b * L)];
   }
+  __device__ float operator()(int m, int k) const { return at(row(m), k); }
 };
 struct ConvInputWB {  // B(k = b*L + t, n = c*3 + d) = X[b][c][(t + d - 1) / up]
   static constexpr bool kAlongN = false;
   const float* X;
-  int Ci, Lin, L, up;
-  __device__ float operator()(int k, int n) const {
-    const int b = k / L, t = k - b * L;
-    const int c = n / 3, d = n - 3 * c;
-    const int sidx = t + d - 1;
-    if (sidx < 0 || sidx >= L) return 0.f;
-    return X[(static_cast<size_t>(b) * Ci + c) * Lin + sidx / up];
+  int Ci, Lin, L, ush;
+  DivBy byL;
+  struct Row {
+    const float* x;  // X[0][c]
+    int dm1;         // d - 1
+  };
+  __device__ Row row(int n) const {
+    const int c = n / 3;
+    return Row{X + static_cast<size_t>(c) * Lin, n - 3 * c - 1};
   }
+  __device__ float at(const Row& r, int k) const {
+    const int b = byL(k);
+    const int s = k - b * L + r.dm1;
+    if (static_cast<unsigned>(s) >= static_cast<unsigned>(L)) return 0.f;
+    return r.x[static_cast<size_t>(b) * Ci * Lin + (s >> ush)];
+  }
+  __device__ float operator()(int k, int n) const { return at(row(n), k); }
 };
 
 // ---- epilogues ----------------------------------------------------------------------------
@@ -521,8 +601,9 @@ struct ConvEp {  // (m = o, n = b*L + t)
   float* out;
   const float* bias;
   int Co, L;
+  DivBy byL;
   __device__ void operator()(int m, int n, float v) const {
-    const int b = n / L, t = n - b * L;
+    const int b = byL(n), t = n - b * L;
     const float p = v + bias[m];
     const size_t i = (static_cast<size_t>(b) * Co + m) * L + t;
     pre[i] = p;
@@ -532,8 +613,9 @@ struct ConvEp {  // (m = o, n = b*L + t)
 struct ConvDataEp {  // (m = c, n = b*Lin + t')
   float* dX;
   int Ci, Lin;
+  DivBy byLin;
   __device__ void operator()(int m, int n, float v) const {
-    const int b = n / Lin, tp = n - b * Lin;
+    const int b = byLin(n), tp = n - b * Lin;
     dX[(static_cast<size_t>(b) * Ci + m) * Lin + tp] = v;
   }
 };
@@ -668,21 +750,23 @@ int linear_backward_weight(int B, int K, int N, const float* dZ, const float* X,
 int conv_forward(int B, int Ci, int Co, int Lin, int up, const float* X, const bf16* W, const float* bias,
                  float* pre, float* out, const Products& pr, cudaStream_t s) {
   const int L = Lin * up;
-  return run_gemm(Co, B * L, Ci * 3, ConvWeightA{W, Ci * 3}, ConvInputB{X, Ci, Lin, L, up},
-                  ConvEp{pre, out, bias, Co, L}, nullptr, false, pr, s);
+  return run_gemm(Co, B * L, Ci * 3, ConvWeightA{W, Ci * 3}, ConvInputB{X, Ci, Lin, L, up >> 1, div_by(L)},
+                  ConvEp{pre, out, bias, Co, L, div_by(L)}, nullptr, false, pr, s);
 }
 
 int conv_backward_data(int B, int Ci, int Co, int Lin, int up, const float* dZ, const bf16* W, float* dX,
                        const Products& pr, cudaStream_t s) {
   const int L = Lin * up;
-  return run_gemm(Ci, B * Lin, Co * 3 * up, ConvWeightTA{W, Ci, up}, ConvGradB{dZ, Co, Lin, L, up},
-                  ConvDataEp{dX, Ci, Lin}, nullptr, false, pr, s);
+  return run_gemm(Ci, B * Lin, Co * 3 * up, ConvWeightTA{W, Ci, up >> 1},
+                  ConvGradB{dZ, Co, Lin, L, up >> 1, div_by(Lin)}, ConvDataEp{dX, Ci, Lin, div_by(Lin)}, nullptr,
+                  false, pr, s);
 }
 
 int conv_backward_weight(int B, int Ci, int Co, int Lin, int up, const float* dZ, const float* X, float* dW,
                          float* db, float* ws, const Products& pr, cudaStream_t s) {
   const int L = Lin * up;
-  int r = run_gemm(Co, Ci * 3, B * L, ConvGradA{dZ, Co, L}, ConvInputWB{X, Ci, Lin, L, up}, StoreEp{dW, Ci * 3}, ws,
+  int r = run_gemm(Co, Ci * 3, B * L, ConvGradA{dZ, Co, L, div_by(L)}, ConvInputWB{X, Ci, Lin, L, up >> 1, div_by(L)},
+                   StoreEp{dW, Ci * 3}, ws,
                    true, pr, s);
   if (r) return r;
   channel_sums_kernel<<<Co, 256, 0, s>>>(B, Co, L, dZ, db);
