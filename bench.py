@@ -59,6 +59,8 @@ def parse_args():
     p.add_argument("--no-ablation", action="store_true", help="skip the colouring/atomics assembly ablation")
     p.add_argument("--no-tiles", action="store_true", help="skip the element-tile autotuner measurement")
     p.add_argument("--surrogate-epochs", type=int, default=150)
+    p.add_argument("--products-only", type=int, default=0, metavar="N",
+                   help="only time the surrogate's products (both kernels) on N seeded inputs, print JSON, exit")
     return p.parse_args()
 
 
@@ -980,8 +982,27 @@ def run_ours(args):
     return 0
 
 
+def run_products_only(n: int):
+    """The default surrogate network with seeded weights (init_params(1)) on n seeded inputs:
+    forward and loss-gradient step with each product kernel (compare_products)."""
+    import torch
+
+    from paper_2606_12850_gb300 import build, inputs, surrogate
+
+    build.build()
+    spec = surrogate.Spec()
+    model = surrogate.Model(spec, max_batch=min(n, 256))
+    model.set_params(spec.init_params(1))
+    x = torch.from_numpy(inputs.uniform(3, (n, spec.in_dim), -1, 1).astype(np.float32)).cuda()
+    y = torch.empty((n, spec.out_c, spec.out_l), device="cuda")
+    print(json.dumps(compare_products(model, spec, x, y, min(n, 256))))
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.products_only > 0:
+        return run_products_only(args.products_only)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

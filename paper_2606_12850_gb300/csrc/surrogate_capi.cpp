@@ -33,6 +33,7 @@ struct sg_model {
   float* d_ws = nullptr;
   double* d_partials = nullptr;
   int* d_err = nullptr;  // set by a tensor-core product whose bounded wait ran out
+  bf16* d_pack = nullptr;  // the convolutions' weights packed for the tcgen05 kernel
   sgk::Products prod;    // product kernel (SG_OPT_PRODUCT) and d_err
   long long step = 0;
   size_t dev_bytes = 0;
@@ -193,6 +194,8 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
   ws = std::max(ws, sgk::splitk_floats(c0 * l0, hidden, max_batch));
   for (int st = 0; st < nstages; ++st)
     ws = std::max(ws, sgk::splitk_floats(m->cout[st], m->cin[st] * 3, max_batch * m->lout[st]));
+  size_t pack = 0;
+  for (int st = 0; st < nstages; ++st) pack = std::max(pack, sgk::conv_pack_bytes(m->cin[st], m->cout[st]));
   int r = SG_OK;
   if ((r = sg_alloc(m, &m->d_p, m->P)) || (r = sg_alloc(m, &m->d_g, m->P)) || (r = sg_alloc(m, &m->d_m, m->P)) ||
       (r = sg_alloc(m, &m->d_v, m->P)) || (r = sg_alloc(m, &m->d_pb, m->P)) ||
@@ -201,7 +204,7 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
       (r = sg_alloc(m, &m->d_a3, B * c0 * l0)) || (r = sg_alloc(m, &m->d_z0, B * c0 * l0)) ||
       (r = sg_alloc(m, &m->d_dA, B * act)) || (r = sg_alloc(m, &m->d_dB, B * act)) ||
       (r = sg_alloc(m, &m->d_ws, ws)) || (r = sg_alloc(m, &m->d_partials, sgk::kLossBlocks)) ||
-      (r = sg_alloc(m, &m->d_err, 1)) ||
+      (r = sg_alloc(m, &m->d_err, 1)) || (r = sg_alloc(m, &m->d_pack, pack / sizeof(bf16))) ||
       (r = sg_alloc(m, &m->d_y, contract ? B * m->out_c * m->out_l : 0))) {
     std::string msg = m->err;
     sg_destroy(m);
@@ -231,6 +234,8 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
     return sg_fail(nullptr, r, msg);
   }
   m->prod.err = m->d_err;
+  m->prod.pack = m->d_pack;
+  m->prod.pack_bytes = pack;
   *out = m;
   return SG_OK;
 }

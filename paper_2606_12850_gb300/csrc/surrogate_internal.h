@@ -17,11 +17,17 @@ using bf16 = __nv_bfloat16;
 // the accumulator in tensor memory, 128 x 128 tiles. Both round the operands to bfloat16
 // (nearest even) and accumulate in float32. err: a device word that a kind-1 product sets to 1
 // when one of its bounded waits for the tensor cores runs out (required for kind 1).
+// pack: device scratch of pack_bytes for the convolutions' packed weights (kind 1; at least
+// conv_pack_bytes of every layer).
 struct Products {
   int kind = 1;
   int* err = nullptr;
   int stall_test = 0;  // 1: every kind-1 product waits for a phase nothing completes (tests the limit)
+  bf16* pack = nullptr;
+  size_t pack_bytes = 0;
 };
+// Bytes of the packed weights of a convolution with Ci input and Co output channels.
+size_t conv_pack_bytes(int Ci, int Co);
 
 // Split-K workspace need (floats) of the weight-gradient products for an M x N result.
 size_t splitk_floats(int M, int N, int K);
@@ -38,7 +44,8 @@ int linear_backward_weight(int B, int K, int N, const float* dZ, const float* X,
 
 // Width-3 'same' convolution of the input upsampled by `up` along time:
 // pre[b][o][t] = bias[o] + sum_{c,d} W[o][c][d] X[b][c][(t + d - 1) / up] (zero outside),
-// t < L = Lin * up; out = gelu(pre) when out != nullptr.
+// t < L = Lin * up; out = gelu(pre) when out != nullptr. Kind 1 runs its own tcgen05 kernel
+// (the input window staged once for the three taps), kind 0 the generic product.
 int conv_forward(int B, int Ci, int Co, int Lin, int up, const float* X, const bf16* W, const float* bias,
                  float* pre, float* out, const Products& pr, cudaStream_t s);
 // dX [B][Ci][Lin] from dZ [B][Co][L] (the upsampling adjoint sums the repeated samples)

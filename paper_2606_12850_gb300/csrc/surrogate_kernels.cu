@@ -167,12 +167,6 @@ constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-// Shared-memory matrix descriptor: start, leading (K) and stride (8-row) byte offsets, all
-// >> 4; bit 46 = descriptor version 1; no swizzle, base offset 0.
-__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
-  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((TC_LBO >> 4) & 0x3FFFu) << 16) |
-         (static_cast<uint64_t>((TC_SBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -197,6 +191,89 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limi
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (8-row) byte offsets, all
+// >> 4; bit 46 = descriptor version 1; no swizzle, base offset 0.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo = TC_LBO) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((TC_SBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(kTcIdesc), "r"(accumulate)
+      : "memory");
+}
+// The stage's mbarrier completes its phase when every MMA this thread issued so far is done.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+// Initialises the stages' mbarriers and allocates the CTA's 128 TMEM columns; returns their
+// address. All threads.
+__device__ uint32_t tc_begin(uint64_t* bars, int nbars, uint32_t* slot, int tid, int warp) {
+  if (tid == 0) {
+    for (int s = 0; s < nbars; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *slot;
+}
+// Waits for the MMAs of the last issued stage (the stages complete in order); true, for every
+// thread, when some wait of the CTA gave up.
+__device__ bool tc_finish(uint64_t* bars, int nstages, int issued, bool late) {
+  if (issued > 0) {
+    const int ls = issued - 1;
+    if (!mbar_wait(smem_addr(&bars[ls % nstages]), (ls / nstages) & 1)) late = true;
+  }
+  const bool failed = __syncthreads_or(late) != 0;
+  tc_fence_after();
+  return failed;
+}
+// The accumulator (TMEM lanes = rows, 128 float32 columns) to tile[128][TC_EPI_LD] in shared
+// memory (zeros when no MMA was issued; untouched when the CTA failed), then frees the TMEM.
+// Warp w reads lanes 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63. All threads.
+__device__ void tc_drain_tile(uint32_t tmem, float* tile, bool issued, bool failed, int warp, int lane) {
+  if (!failed) {
+    const int q = warp & 3, h = warp >> 2;
+    float* row = tile + (q * 32 + lane) * TC_EPI_LD + h * (TC_BN / 2);
+#pragma unroll
+    for (int c = 0; c < TC_BN / 2; c += 32) {
+      uint32_t v[32];
+      if (issued) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(h * (TC_BN / 2) + c)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) row[c + i] = __uint_as_float(v[i]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+}
 
 // The part of one operand stage that a lane writes: one word (two consecutive K elements of
 // one row, packed bfloat16) in each core matrix (g, j) with g in {warp, warp + 8} and j < 4.
@@ -247,21 +324,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
   CoreFiller<LB::kAlongN, LB> fb;
   fa.init(la, m0, M, warp, lane);
   fb.init(lb, n0, N, warp, lane);
-  if (tid == 0) {
-    for (int s = 0; s < TC_STAGES; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[s])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                 "r"(TC_BN)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = tc_begin(bars, TC_STAGES, tmem_slot, tid, warp);
   int issued = 0;
   bool late = false;
   // stall test: wait (20 ms limit) for a phase that no commit completes
@@ -283,57 +346,16 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
       tc_fence_after();
       const uint32_t a_addr = smem_addr(a_op), b_addr = smem_addr(b_op);
 #pragma unroll
-      for (int j = 0; j < TC_KCORES / 2; ++j) {
-        const uint32_t acc = (s | j) != 0;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-            ::"r"(tmem), "l"(tc_desc(a_addr + 2 * j * TC_LBO)), "l"(tc_desc(b_addr + 2 * j * TC_LBO)),
-            "r"(kTcIdesc), "r"(acc)
-            : "memory");
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_addr(&bars[buf]))
-                   : "memory");
+      for (int j = 0; j < TC_KCORES / 2; ++j)
+        tc_mma(tmem, tc_desc(a_addr + 2 * j * TC_LBO), tc_desc(b_addr + 2 * j * TC_LBO), (s | j) != 0);
+      tc_commit(&bars[buf]);
     }
     ++issued;
   }
   if (issued < 0) issued = 0;
-  if (issued > 0) {
-    const int ls = issued - 1;
-    if (!mbar_wait(smem_addr(&bars[ls % TC_STAGES]), (ls / TC_STAGES) & 1)) late = true;
-  }
-  const bool failed = __syncthreads_or(late) != 0;
-  tc_fence_after();
+  const bool failed = tc_finish(bars, TC_STAGES, issued, late);
   float* tile = reinterpret_cast<float*>(tc_smem);
-  if (!failed) {
-    const int q = warp & 3, h = warp >> 2;
-    float* row = tile + (q * 32 + lane) * TC_EPI_LD + h * (TC_BN / 2);
-#pragma unroll
-    for (int c = 0; c < TC_BN / 2; c += 32) {
-      uint32_t v[32];
-      if (issued > 0) {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(h * (TC_BN / 2) + c)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      } else {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = 0u;
-      }
-#pragma unroll
-      for (int i = 0; i < 32; ++i) row[c + i] = __uint_as_float(v[i]);
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+  tc_drain_tile(tmem, tile, issued > 0, failed, warp, lane);
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
     return;
@@ -347,6 +369,142 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
         ws[(static_cast<size_t>(blockIdx.z) * M + m) * N + n] = v;
       else
         ep(m, n, v);
+    }
+  }
+}
+
+// ---- the width-3 convolution forward on tcgen05, its input window staged once ---------------
+// pre[b][o][t] = bias[o] + sum_{c,d} W[o][c][d] X[b][c][(t + d - 1) >> ush] (zero outside
+// [0, L)), out = gelu(pre) when out != nullptr. A CTA owns 128 output channels x 128 times
+// t0 .. t0 + 127 of one sample b (tiles numbered channel tile fastest). Per chunk of 32 input
+// channels it stages the upsampled input window s = t0 - 1 .. t0 + 134 as K-major rows (row R
+// holds time t0 - 1 + R, K = channel) and the three taps' 128 x 32 weights, packed beforehand
+// into the core-matrix layout (pack_conv_weights_kernel) so that staging them is 16-byte
+// copies. Tap d multiplies output time t0 + n with window row n + d: the same staged rows
+// through a descriptor that starts d rows (16 bytes) later, so the window serves all three
+// taps. Six MMAs (three taps x two K = 16 halves) a chunk, two chunk stages in flight; the
+// epilogue adds the bias and the activation with consecutive threads on consecutive times.
+constexpr int CV_CK = 32;                               // input channels a chunk
+constexpr int CV_ROWS = 136;                            // window rows: >= 128 + 2, whole groups
+constexpr int CV_WGROUPS = CV_ROWS / 8;
+constexpr int CV_WINDOW = CV_WGROUPS * TC_KCORES * TC_CORE;  // 8704 B
+constexpr int CV_TAP = TC_GROUPS * TC_KCORES * TC_CORE;      // 8192 B: 128 x 32 weights of a tap
+constexpr int CV_STAGE = CV_WINDOW + 3 * CV_TAP;
+constexpr int CV_STAGES = 2;
+constexpr uint32_t CV_LBO = CV_WGROUPS * TC_CORE;            // window: next core along K
+constexpr int CV_DATA = (CV_STAGES * CV_STAGE > TC_BM * TC_EPI_LD * 4 ? CV_STAGES * CV_STAGE : TC_BM * TC_EPI_LD * 4);
+constexpr int CV_SMEM = CV_DATA + 64;
+constexpr int CV_WCORES = CV_WGROUPS * TC_KCORES;            // window core matrices a stage
+constexpr int CV_WITER = (CV_WCORES + TC_THREADS / 32 - 1) / (TC_THREADS / 32);
+static_assert(TC_KCORES * 8 == CV_CK && CV_ROWS % 8 == 0 && CV_ROWS >= TC_BN + 2, "window plan");
+static_assert(CV_STAGE % 16 == 0 && CV_WINDOW % 16 == 0 && (3 * CV_TAP / 16) % TC_THREADS == 0, "16-byte copies");
+
+// Wp[((ot * nq + q) * 3 + d) * 4096 + e]: the weights of output-channel tile ot, input-channel
+// chunk q and tap d in the core-matrix layout: element e = (j * 16 + g) * 64 + r * 8 + i holds
+// W[o][c][d], o = 128 ot + 8 g + r, c = 32 q + 8 j + i (zero outside Co x Ci).
+__global__ void pack_conv_weights_kernel(int Co, int Ci, int nq, size_t total, const bf16* __restrict__ W,
+                                         bf16* __restrict__ Wp) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int e = static_cast<int>(i & 4095);
+    const size_t blk = i >> 12;
+    const int d = static_cast<int>(blk % 3);
+    const size_t oq = blk / 3;
+    const int q = static_cast<int>(oq % nq), ot = static_cast<int>(oq / nq);
+    const int core = e >> 6, g = core & 15, j = core >> 4;
+    const int o = ot * TC_BM + g * 8 + ((e >> 3) & 7), c = q * CV_CK + j * 8 + (e & 7);
+    Wp[i] = (o < Co && c < Ci) ? W[(static_cast<size_t>(o) * Ci + c) * 3 + d] : __float2bfloat16_rn(0.f);
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS) tc_conv_kernel(int Ci, int Co, int Lin, int L, int ush,
+                                                              const float* __restrict__ X, const bf16* __restrict__ Wp,
+                                                              const float* __restrict__ bias, float* __restrict__ pre,
+                                                              float* __restrict__ out, int* err, int stall_test) {
+  extern __shared__ __align__(128) uint8_t cv_smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(cv_smem + CV_DATA);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + CV_STAGES);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_ot = (Co + TC_BM - 1) / TC_BM, n_tt = (L + TC_BN - 1) / TC_BN, nq = (Ci + CV_CK - 1) / CV_CK;
+  const int ot = blockIdx.x % n_ot;
+  const int rest = blockIdx.x / n_ot;
+  const int t0 = (rest % n_tt) * TC_BN, b = rest / n_tt;
+  const float* xb = X + static_cast<size_t>(b) * Ci * Lin;
+  const uint32_t tmem = tc_begin(bars, CV_STAGES, tmem_slot, tid, warp);
+  const int r = lane & 7, w = lane >> 3;  // window row in the group, channel pair in the core
+  int issued = 0;
+  bool late = false;
+  if (stall_test && !mbar_wait(smem_addr(&bars[0]), 0, 20000000ull)) late = true;
+  if (__syncthreads_or(late)) issued = -1;
+  for (int q = 0; q < nq && issued >= 0; ++q) {
+    const int buf = q % CV_STAGES;
+    if (q >= CV_STAGES && !mbar_wait(smem_addr(&bars[buf]), ((q / CV_STAGES) - 1) & 1)) late = true;
+    uint8_t* win = cv_smem + buf * CV_STAGE;
+    uint8_t* taps = win + CV_WINDOW;
+    if (!late) {
+      const uint4* src = reinterpret_cast<const uint4*>(Wp + static_cast<size_t>((ot * nq + q) * 3) * (CV_TAP / 2));
+      uint4 wv[3 * CV_TAP / 16 / TC_THREADS];
+#pragma unroll
+      for (int i = 0; i < 3 * CV_TAP / 16 / TC_THREADS; ++i) wv[i] = src[tid + i * TC_THREADS];
+      float v[CV_WITER][2];
+#pragma unroll
+      for (int i = 0; i < CV_WITER; ++i) {
+        const int cidx = warp + i * (TC_THREADS / 32);
+        const int g = cidx % CV_WGROUPS, j = cidx / CV_WGROUPS;
+        const int s = t0 - 1 + g * 8 + r;
+        const int c = q * CV_CK + j * 8 + 2 * w;
+        v[i][0] = v[i][1] = 0.f;
+        if (cidx < CV_WCORES && static_cast<unsigned>(s) < static_cast<unsigned>(L)) {
+          const float* p = xb + static_cast<size_t>(c) * Lin + (s >> ush);
+          if (c < Ci) v[i][0] = p[0];
+          if (c + 1 < Ci) v[i][1] = p[Lin];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 3 * CV_TAP / 16 / TC_THREADS; ++i) reinterpret_cast<uint4*>(taps)[tid + i * TC_THREADS] = wv[i];
+#pragma unroll
+      for (int i = 0; i < CV_WITER; ++i) {
+        const int cidx = warp + i * (TC_THREADS / 32);
+        if (cidx < CV_WCORES) {
+          const int g = cidx % CV_WGROUPS, j = cidx / CV_WGROUPS;
+          const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(v[i][0]));
+          const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(v[i][1]));
+          *reinterpret_cast<uint32_t*>(win + (j * CV_WGROUPS + g) * TC_CORE + r * 16 + w * 4) = lo | (hi << 16);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(late)) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t w_addr = smem_addr(win), a_addr = smem_addr(taps);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int j = 0; j < TC_KCORES / 2; ++j)
+          tc_mma(tmem, tc_desc(a_addr + d * CV_TAP + 2 * j * TC_LBO), tc_desc(w_addr + d * 16 + 2 * j * CV_LBO, CV_LBO),
+                 (q | d | j) != 0);
+      tc_commit(&bars[buf]);
+    }
+    ++issued;
+  }
+  if (issued < 0) issued = 0;
+  const bool failed = tc_finish(bars, CV_STAGES, issued, late);
+  float* tile = reinterpret_cast<float*>(cv_smem);
+  tc_drain_tile(tmem, tile, issued > 0, failed, warp, lane);
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    return;
+  }
+  const int o0 = ot * TC_BM;
+  for (int idx = tid; idx < TC_BM * TC_BN; idx += TC_THREADS) {
+    const int mm = idx / TC_BN, nn = idx - mm * TC_BN;
+    const int o = o0 + mm, t = t0 + nn;
+    if (o < Co && t < L) {
+      const float p = tile[mm * TC_EPI_LD + nn] + bias[o];
+      const size_t i = (static_cast<size_t>(b) * Co + o) * L + t;
+      pre[i] = p;
+      if (out) out[i] = gelu(p);
     }
   }
 }
@@ -747,9 +905,28 @@ int linear_backward_weight(int B, int K, int N, const float* dZ, const float* X,
   return static_cast<int>(cudaGetLastError());
 }
 
+size_t conv_pack_bytes(int Ci, int Co) {
+  return static_cast<size_t>((Co + TC_BM - 1) / TC_BM) * ((Ci + CV_CK - 1) / CV_CK) * 3 * CV_TAP;
+}
+
 int conv_forward(int B, int Ci, int Co, int Lin, int up, const float* X, const bf16* W, const float* bias,
                  float* pre, float* out, const Products& pr, cudaStream_t s) {
   const int L = Lin * up;
+  if (pr.kind == 1) {
+    if (B <= 0) return 0;
+    if (!pr.err || !pr.pack || conv_pack_bytes(Ci, Co) > pr.pack_bytes) return static_cast<int>(cudaErrorInvalidValue);
+    const int nq = (Ci + CV_CK - 1) / CV_CK;
+    const size_t total = conv_pack_bytes(Ci, Co) / sizeof(bf16);
+    pack_conv_weights_kernel<<<grid_for(total), 256, 0, s>>>(Co, Ci, nq, total, W, pr.pack);
+    const long long tiles =
+        static_cast<long long>((Co + TC_BM - 1) / TC_BM) * ((L + TC_BN - 1) / TC_BN) * static_cast<long long>(B);
+    if (tiles > 0x7FFFFFFFLL) return static_cast<int>(cudaErrorInvalidValue);
+    const cudaError_t e = cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CV_SMEM);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    tc_conv_kernel<<<static_cast<unsigned>(tiles), TC_THREADS, CV_SMEM, s>>>(Ci, Co, Lin, L, up >> 1, X, pr.pack, bias,
+                                                                            pre, out, pr.err, pr.stall_test);
+    return static_cast<int>(cudaGetLastError());
+  }
   return run_gemm(Co, B * L, Ci * 3, ConvWeightA{W, Ci * 3}, ConvInputB{X, Ci, Lin, L, up >> 1, div_by(L)},
                   ConvEp{pre, out, bias, Co, L, div_by(L)}, nullptr, false, pr, s);
 }
