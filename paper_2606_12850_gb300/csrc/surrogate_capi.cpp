@@ -34,6 +34,7 @@ struct sg_model {
   double* d_partials = nullptr;
   int* d_err = nullptr;  // set by a tensor-core product whose bounded wait ran out
   bf16* d_pack = nullptr;  // the convolutions' weights packed for the tcgen05 kernel
+  float* d_red = nullptr;  // per-slice sums of the bias gradients
   sgk::Products prod;    // product kernel (SG_OPT_PRODUCT) and d_err
   long long step = 0;
   size_t dev_bytes = 0;
@@ -44,6 +45,7 @@ struct sg_model {
 namespace {
 
 std::string g_sg_err;
+constexpr size_t kRedFloats = 8192;  // bias-gradient slice sums: up to 8192 / channels slices
 
 int sg_fail(sg_model* m, int code, const std::string& msg) {
   if (m)
@@ -205,6 +207,7 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
       (r = sg_alloc(m, &m->d_dA, B * act)) || (r = sg_alloc(m, &m->d_dB, B * act)) ||
       (r = sg_alloc(m, &m->d_ws, ws)) || (r = sg_alloc(m, &m->d_partials, sgk::kLossBlocks)) ||
       (r = sg_alloc(m, &m->d_err, 1)) || (r = sg_alloc(m, &m->d_pack, pack / sizeof(bf16))) ||
+      (r = sg_alloc(m, &m->d_red, kRedFloats)) ||
       (r = sg_alloc(m, &m->d_y, contract ? B * m->out_c * m->out_l : 0))) {
     std::string msg = m->err;
     sg_destroy(m);
@@ -236,6 +239,8 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
   m->prod.err = m->d_err;
   m->prod.pack = m->d_pack;
   m->prod.pack_bytes = pack;
+  m->prod.red = m->d_red;
+  m->prod.red_floats = kRedFloats;
   *out = m;
   return SG_OK;
 }

@@ -25,6 +25,8 @@ struct Products {
   int stall_test = 0;  // 1: every kind-1 product waits for a phase nothing completes (tests the limit)
   bf16* pack = nullptr;
   size_t pack_bytes = 0;
+  float* red = nullptr;   // scratch of red_floats for the bias gradients' per-slice sums
+  size_t red_floats = 0;
 };
 // Bytes of the packed weights of a convolution with Ci input and Co output channels.
 size_t conv_pack_bytes(int Ci, int Co);

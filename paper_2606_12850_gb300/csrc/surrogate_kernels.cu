@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "surrogate_internal.h"
@@ -509,6 +510,247 @@ __global__ void __launch_bounds__(TC_THREADS) tc_conv_kernel(int Ci, int Co, int
   }
 }
 
+// ---- the convolution's weight gradient on tcgen05 ------------------------------------------
+// dW[o][c][d] = sum_{b,t} dZ[b][o][t] X[b][c][(t + d - 1) >> ush] (zero outside [0, L)). A CTA
+// owns 128 output channels x 128 input channels of one tap d and the samples of split z of S;
+// its K loop runs over those samples' times in chunks of 32, staging dZ (rows o) and the tap's
+// shifted input (rows c) as K-major operands, with no index division. The sums go to
+// dst[z][o][c * 3 + d]: the split-K workspace (added in split order afterwards) or dW itself.
+__global__ void __launch_bounds__(TC_THREADS) tc_conv_wgrad_kernel(int B, int Ci, int Co, int Lin, int L, int ush,
+                                                                    int S, const float* __restrict__ dZ,
+                                                                    const float* __restrict__ X,
+                                                                    float* __restrict__ dst, int* err, int stall_test) {
+  extern __shared__ __align__(128) uint8_t wg_smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wg_smem + TC_DATA);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + TC_STAGES);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_ot = (Co + TC_BM - 1) / TC_BM, n_ct = (Ci + TC_BN - 1) / TC_BN;
+  int id = blockIdx.x;
+  const int ot = id % n_ot;
+  id /= n_ot;
+  const int d = id % 3;
+  id /= 3;
+  const int ct = id % n_ct, z = id / n_ct;
+  const int b0 = static_cast<int>(static_cast<long long>(z) * B / S);
+  const int b1 = static_cast<int>(static_cast<long long>(z + 1) * B / S);
+  const int nchunk = (L + TC_BK - 1) / TC_BK;
+  const int nst = (b1 - b0) * nchunk;
+  const int o0 = ot * TC_BM, c0 = ct * TC_BN;
+  const int r = lane >> 2, w = lane & 3;  // K is contiguous in both operands
+  int orow[2], crow[2];
+  bool oin[2], cin[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    orow[h] = o0 + (warp + 8 * h) * 8 + r;
+    crow[h] = c0 + (warp + 8 * h) * 8 + r;
+    oin[h] = orow[h] < Co;
+    cin[h] = crow[h] < Ci;
+  }
+  const uint32_t tmem = tc_begin(bars, TC_STAGES, tmem_slot, tid, warp);
+  int issued = 0;
+  bool late = false;
+  if (stall_test && !mbar_wait(smem_addr(&bars[0]), 0, 20000000ull)) late = true;
+  if (__syncthreads_or(late)) issued = -1;
+  for (int s = 0; s < nst && issued >= 0; ++s) {
+    const int buf = s % TC_STAGES;
+    if (s >= TC_STAGES && !mbar_wait(smem_addr(&bars[buf]), ((s / TC_STAGES) - 1) & 1)) late = true;
+    uint8_t* a_op = wg_smem + buf * TC_STAGE;
+    uint8_t* b_op = a_op + TC_OPERAND;
+    if (!late) {
+      const int b = b0 + s / nchunk, t0 = (s % nchunk) * TC_BK;
+      const float* zb = dZ + static_cast<size_t>(b) * Co * L;
+      const float* xb = X + static_cast<size_t>(b) * Ci * Lin;
+      float va[2][TC_KCORES][2], vb[2][TC_KCORES][2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < TC_KCORES; ++j)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int t = t0 + j * 8 + 2 * w + e;
+            const int u = t + d - 1;
+            va[h][j][e] = (oin[h] && t < L) ? zb[static_cast<size_t>(orow[h]) * L + t] : 0.f;
+            vb[h][j][e] = (cin[h] && t < L && static_cast<unsigned>(u) < static_cast<unsigned>(L))
+                              ? xb[static_cast<size_t>(crow[h]) * Lin + (u >> ush)]
+                              : 0.f;
+          }
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < TC_KCORES; ++j) {
+          const int off = (j * TC_GROUPS + warp + 8 * h) * TC_CORE + r * 16 + w * 4;
+          *reinterpret_cast<uint32_t*>(a_op + off) =
+              static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(va[h][j][0]))) |
+              (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(va[h][j][1]))) << 16);
+          *reinterpret_cast<uint32_t*>(b_op + off) =
+              static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(vb[h][j][0]))) |
+              (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(vb[h][j][1]))) << 16);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(late)) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a_addr = smem_addr(a_op), b_addr = smem_addr(b_op);
+#pragma unroll
+      for (int j = 0; j < TC_KCORES / 2; ++j)
+        tc_mma(tmem, tc_desc(a_addr + 2 * j * TC_LBO), tc_desc(b_addr + 2 * j * TC_LBO), (s | j) != 0);
+      tc_commit(&bars[buf]);
+    }
+    ++issued;
+  }
+  if (issued < 0) issued = 0;
+  const bool failed = tc_finish(bars, TC_STAGES, issued, late);
+  float* tile = reinterpret_cast<float*>(wg_smem);
+  tc_drain_tile(tmem, tile, issued > 0, failed, warp, lane);
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    return;
+  }
+  float* out = dst + static_cast<size_t>(z) * Co * Ci * 3;
+  for (int idx = tid; idx < TC_BM * TC_BN; idx += TC_THREADS) {
+    const int mm = idx / TC_BN, nn = idx - mm * TC_BN;
+    const int o = o0 + mm, c = c0 + nn;
+    if (o < Co && c < Ci) out[(static_cast<size_t>(o) * Ci + c) * 3 + d] = tile[mm * TC_EPI_LD + nn];
+  }
+}
+
+// Wt[((ct * nq + q) * 3 + d) * 4096 + e]: W[o][c][d] transposed (rows c, K = o) in the
+// core-matrix layout: element e = (j * 16 + g) * 64 + r * 8 + i holds c = 128 ct + 8 g + r,
+// o = 32 q + 8 j + i (zero outside Co x Ci).
+__global__ void pack_conv_weights_t_kernel(int Co, int Ci, int nq, size_t total, const bf16* __restrict__ W,
+                                           bf16* __restrict__ Wt) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int e = static_cast<int>(i & 4095);
+    const size_t blk = i >> 12;
+    const int d = static_cast<int>(blk % 3);
+    const size_t cq = blk / 3;
+    const int q = static_cast<int>(cq % nq), ct = static_cast<int>(cq / nq);
+    const int core = e >> 6, g = core & 15, j = core >> 4;
+    const int c = ct * TC_BM + g * 8 + ((e >> 3) & 7), o = q * CV_CK + j * 8 + (e & 7);
+    Wt[i] = (o < Co && c < Ci) ? W[(static_cast<size_t>(o) * Ci + c) * 3 + d] : __float2bfloat16_rn(0.f);
+  }
+}
+
+// ---- the convolution's data gradient on tcgen05 ---------------------------------------------
+// dX[b][c][t'] = sum_{o,d,r<UP} W[o][c][d] dZ[b][o][UP t' + r - d + 1] (zero outside [0, L)).
+// A CTA owns 128 input channels x 128 times t0' .. t0' + 127 of one sample b. Per chunk of 32
+// output channels it stages dZ around the tile as K-major windows of 136 rows (K = output
+// channel): UP = 1, one window, row R = time t0' - 1 + R; UP = 2, two, row R = time
+// 2 (t0' - 1 + R) + p for parity p. Term (r, d) reads time UP (t0' + n) + e, e = r - d + 1,
+// which is row n + 1 + (e - p) / UP of window p = e mod UP: the staged rows through a
+// descriptor offset by that many rows. The taps' transposed weights are 16-byte copies.
+template <int UP>
+struct Dgrad {
+  static constexpr int kStage = UP * CV_WINDOW + 3 * CV_TAP;
+  static constexpr int kData = (2 * kStage > TC_BM * TC_EPI_LD * 4 ? 2 * kStage : TC_BM * TC_EPI_LD * 4);
+  static constexpr int kSmem = kData + 64;
+  static constexpr int kCores = UP * CV_WCORES;
+  static constexpr int kIter = (kCores + TC_THREADS / 32 - 1) / (TC_THREADS / 32);
+};
+
+template <int UP>
+__global__ void __launch_bounds__(TC_THREADS) tc_conv_dgrad_kernel(int Ci, int Co, int Lin, int L,
+                                                                    const float* __restrict__ dZ,
+                                                                    const bf16* __restrict__ Wt, float* __restrict__ dX,
+                                                                    int* err, int stall_test) {
+  using G = Dgrad<UP>;
+  extern __shared__ __align__(128) uint8_t dg_smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(dg_smem + G::kData);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_ct = (Ci + TC_BM - 1) / TC_BM, n_tt = (Lin + TC_BN - 1) / TC_BN, nq = (Co + CV_CK - 1) / CV_CK;
+  const int ct = blockIdx.x % n_ct;
+  const int rest = blockIdx.x / n_ct;
+  const int t0 = (rest % n_tt) * TC_BN, b = rest / n_tt;
+  const float* zb = dZ + static_cast<size_t>(b) * Co * L;
+  const uint32_t tmem = tc_begin(bars, 2, tmem_slot, tid, warp);
+  const int r = lane & 7, w = lane >> 3;  // window row in the group, output-channel pair
+  int issued = 0;
+  bool late = false;
+  if (stall_test && !mbar_wait(smem_addr(&bars[0]), 0, 20000000ull)) late = true;
+  if (__syncthreads_or(late)) issued = -1;
+  for (int q = 0; q < nq && issued >= 0; ++q) {
+    const int buf = q & 1;
+    if (q >= 2 && !mbar_wait(smem_addr(&bars[buf]), ((q >> 1) - 1) & 1)) late = true;
+    uint8_t* win = dg_smem + buf * G::kStage;
+    uint8_t* taps = win + UP * CV_WINDOW;
+    if (!late) {
+      const uint4* src = reinterpret_cast<const uint4*>(Wt + static_cast<size_t>((ct * nq + q) * 3) * (CV_TAP / 2));
+      uint4 wv[3 * CV_TAP / 16 / TC_THREADS];
+#pragma unroll
+      for (int i = 0; i < 3 * CV_TAP / 16 / TC_THREADS; ++i) wv[i] = src[tid + i * TC_THREADS];
+      float v[G::kIter][2];
+#pragma unroll
+      for (int i = 0; i < G::kIter; ++i) {
+        const int cidx = warp + i * (TC_THREADS / 32);
+        const int p = cidx / CV_WCORES, within = cidx - p * CV_WCORES;
+        const int g = within % CV_WGROUPS, j = within / CV_WGROUPS;
+        const int u = UP * (t0 - 1 + g * 8 + r) + p;
+        const int o = q * CV_CK + j * 8 + 2 * w;
+        v[i][0] = v[i][1] = 0.f;
+        if (cidx < G::kCores && static_cast<unsigned>(u) < static_cast<unsigned>(L)) {
+          const float* pz = zb + static_cast<size_t>(o) * L + u;
+          if (o < Co) v[i][0] = pz[0];
+          if (o + 1 < Co) v[i][1] = pz[L];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 3 * CV_TAP / 16 / TC_THREADS; ++i) reinterpret_cast<uint4*>(taps)[tid + i * TC_THREADS] = wv[i];
+#pragma unroll
+      for (int i = 0; i < G::kIter; ++i) {
+        const int cidx = warp + i * (TC_THREADS / 32);
+        if (cidx < G::kCores) {
+          const int p = cidx / CV_WCORES, within = cidx - p * CV_WCORES;
+          const int g = within % CV_WGROUPS, j = within / CV_WGROUPS;
+          const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(v[i][0]));
+          const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(v[i][1]));
+          *reinterpret_cast<uint32_t*>(win + p * CV_WINDOW + (j * CV_WGROUPS + g) * TC_CORE + r * 16 + w * 4) =
+              lo | (hi << 16);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(late)) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t w_addr = smem_addr(win), a_addr = smem_addr(taps);
+      bool first = q == 0;
+#pragma unroll
+      for (int rr = 0; rr < UP; ++rr)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int e = rr - d + 1;           // -1 .. 2
+          const int p = UP == 2 ? (e & 1) : 0;
+          const int off = 1 + (UP == 2 ? (e - p) / 2 : e);  // window row of output row 0
+#pragma unroll
+          for (int j = 0; j < TC_KCORES / 2; ++j) {
+            tc_mma(tmem, tc_desc(a_addr + d * CV_TAP + 2 * j * TC_LBO),
+                   tc_desc(w_addr + p * CV_WINDOW + off * 16 + 2 * j * CV_LBO, CV_LBO), first ? 0u : 1u);
+            first = false;
+          }
+        }
+      tc_commit(&bars[buf]);
+    }
+    ++issued;
+  }
+  if (issued < 0) issued = 0;
+  const bool failed = tc_finish(bars, 2, issued, late);
+  float* tile = reinterpret_cast<float*>(dg_smem);
+  tc_drain_tile(tmem, tile, issued > 0, failed, warp, lane);
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    return;
+  }
+  const int c0 = ct * TC_BM;
+  for (int idx = tid; idx < TC_BM * TC_BN; idx += TC_THREADS) {
+    const int mm = idx / TC_BN, nn = idx - mm * TC_BN;
+    const int c = c0 + mm, t = t0 + nn;
+    if (c < Ci && t < Lin) dX[(static_cast<size_t>(b) * Ci + c) * Lin + t] = tile[mm * TC_EPI_LD + nn];
+  }
+}
+
 template <class EP>
 __global__ void splitk_finalize_kernel(int M, int N, int splits, const float* __restrict__ ws, EP ep) {
   const size_t total = static_cast<size_t>(M) * N;
@@ -787,14 +1029,19 @@ __global__ void column_sums_kernel(int B, int N, const float* __restrict__ dZ, f
   }
 }
 
-__global__ void channel_sums_kernel(int B, int Co, int L, const float* __restrict__ dZ, float* __restrict__ db) {
+// db[o] = sum_{b,t} dZ[b][o][t] in two fixed-order passes: block (o, p) sums samples
+// [p B / P, (p + 1) B / P) into part[p][o] (a strided sum per thread, then a tree), and
+// channel_finish_kernel adds the P parts in order.
+__global__ void channel_partials_kernel(int B, int Co, int L, int P, const float* __restrict__ dZ,
+                                        float* __restrict__ part) {
   __shared__ float red[256];
-  const int o = blockIdx.x;
+  const int o = blockIdx.x, p = blockIdx.y;
+  const int b0 = static_cast<int>(static_cast<long long>(p) * B / P);
+  const int b1 = static_cast<int>(static_cast<long long>(p + 1) * B / P);
   float s = 0.f;
-  const size_t per = static_cast<size_t>(B) * L;
-  for (size_t i = threadIdx.x; i < per; i += blockDim.x) {
-    const size_t b = i / L, t = i - b * L;
-    s += dZ[(b * Co + o) * L + t];
+  for (int b = b0; b < b1; ++b) {
+    const float* row = dZ + (static_cast<size_t>(b) * Co + o) * L;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) s += row[t];
   }
   red[threadIdx.x] = s;
   __syncthreads();
@@ -802,7 +1049,15 @@ __global__ void channel_sums_kernel(int B, int Co, int L, const float* __restric
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) db[o] = red[0];
+  if (threadIdx.x == 0) part[static_cast<size_t>(p) * Co + o] = red[0];
+}
+
+__global__ void channel_finish_kernel(int Co, int P, const float* __restrict__ part, float* __restrict__ db) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= Co) return;
+  float s = 0.f;
+  for (int p = 0; p < P; ++p) s += part[static_cast<size_t>(p) * Co + o];
+  db[o] = s;
 }
 
 __global__ void gelu_backward_kernel(size_t n, const float* __restrict__ pre, float* __restrict__ dz) {
@@ -848,30 +1103,35 @@ __global__ void adam_kernel(size_t n, float* __restrict__ p, const float* __rest
 }
 
 // y[b][c][t] = sum_k x[b][k0 + k] D[b][k*C + c][t]   (the output is linear in the last K
-// input features: the moment-tensor entries)
+// input features: the moment-tensor entries). Block row y walks samples, x the C*L outputs.
 __global__ void contract_forward_kernel(int B, int K, int C, int L, int in_dim, int k0, const float* __restrict__ x,
                                         const float* __restrict__ D, float* __restrict__ y) {
-  const size_t total = static_cast<size_t>(B) * C * L;
-  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const size_t b = i / (static_cast<size_t>(C) * L);
-    const size_t ct = i - b * C * L;
-    float s = 0.f;
-    for (int k = 0; k < K; ++k) s = fmaf(x[b * in_dim + k0 + k], D[(b * K + k) * C * L + ct], s);
-    y[i] = s;
+  const size_t CL = static_cast<size_t>(C) * L;
+  for (int b = blockIdx.y; b < B; b += gridDim.y) {
+    const float* xb = x + static_cast<size_t>(b) * in_dim + k0;
+    const float* Db = D + static_cast<size_t>(b) * K * CL;
+    float* yb = y + static_cast<size_t>(b) * CL;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < CL;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+      float s = 0.f;
+      for (int k = 0; k < K; ++k) s = fmaf(xb[k], Db[k * CL + i], s);
+      yb[i] = s;
+    }
   }
 }
 
-// dD[b][k*C + c][t] = x[b][k0 + k] dy[b][c][t]
+// dD[b][k*C + c][t] = x[b][k0 + k] dy[b][c][t]; block row y walks the (sample, k) pairs
 __global__ void contract_backward_kernel(int B, int K, int C, int L, int in_dim, int k0, const float* __restrict__ x,
                                          const float* __restrict__ dy, float* __restrict__ dD) {
-  const size_t total = static_cast<size_t>(B) * K * C * L;
-  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const size_t CL = static_cast<size_t>(C) * L;
-    const size_t bk = i / CL, ct = i - bk * CL;
-    const size_t b = bk / K, k = bk - b * K;
-    dD[i] = x[b * in_dim + k0 + k] * dy[b * CL + ct];
+  const size_t CL = static_cast<size_t>(C) * L;
+  for (int bk = blockIdx.y; bk < B * K; bk += gridDim.y) {
+    const int b = bk / K, k = bk - b * K;
+    const float xv = x[static_cast<size_t>(b) * in_dim + k0 + k];
+    const float* src = dy + static_cast<size_t>(b) * CL;
+    float* dst = dD + static_cast<size_t>(bk) * CL;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < CL;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x)
+      dst[i] = xv * src[i];
   }
 }
 
@@ -906,7 +1166,9 @@ int linear_backward_weight(int B, int K, int N, const float* dZ, const float* X,
 }
 
 size_t conv_pack_bytes(int Ci, int Co) {
-  return static_cast<size_t>((Co + TC_BM - 1) / TC_BM) * ((Ci + CV_CK - 1) / CV_CK) * 3 * CV_TAP;
+  const size_t fwd = static_cast<size_t>((Co + TC_BM - 1) / TC_BM) * ((Ci + CV_CK - 1) / CV_CK) * 3 * CV_TAP;
+  const size_t bwd = static_cast<size_t>((Ci + TC_BM - 1) / TC_BM) * ((Co + CV_CK - 1) / CV_CK) * 3 * CV_TAP;
+  return fwd > bwd ? fwd : bwd;
 }
 
 int conv_forward(int B, int Ci, int Co, int Lin, int up, const float* X, const bf16* W, const float* bias,
@@ -916,7 +1178,7 @@ int conv_forward(int B, int Ci, int Co, int Lin, int up, const float* X, const b
     if (B <= 0) return 0;
     if (!pr.err || !pr.pack || conv_pack_bytes(Ci, Co) > pr.pack_bytes) return static_cast<int>(cudaErrorInvalidValue);
     const int nq = (Ci + CV_CK - 1) / CV_CK;
-    const size_t total = conv_pack_bytes(Ci, Co) / sizeof(bf16);
+    const size_t total = static_cast<size_t>((Co + TC_BM - 1) / TC_BM) * nq * 3 * (CV_TAP / 2);
     pack_conv_weights_kernel<<<grid_for(total), 256, 0, s>>>(Co, Ci, nq, total, W, pr.pack);
     const long long tiles =
         static_cast<long long>((Co + TC_BM - 1) / TC_BM) * ((L + TC_BN - 1) / TC_BN) * static_cast<long long>(B);
@@ -931,9 +1193,46 @@ int conv_forward(int B, int Ci, int Co, int Lin, int up, const float* X, const b
                   ConvEp{pre, out, bias, Co, L, div_by(L)}, nullptr, false, pr, s);
 }
 
+// db[o] = sum over samples and times of dZ[b][o][t]: P sample slices a channel (P Co <= the
+// scratch pr.red holds), parts added in slice order
+int channel_sums(int B, int Co, int L, const float* dZ, float* db, const Products& pr, cudaStream_t s) {
+  int P = pr.red ? static_cast<int>(pr.red_floats / static_cast<size_t>(Co)) : 1;
+  if (P > (608 + Co - 1) / Co) P = (608 + Co - 1) / Co;
+  if (P > B) P = B;
+  if (P < 1) P = 1;
+  float* part = pr.red ? pr.red : db;
+  channel_partials_kernel<<<dim3(Co, P), 256, 0, s>>>(B, Co, L, P, dZ, part);
+  if (pr.red) channel_finish_kernel<<<(Co + 255) / 256, 256, 0, s>>>(Co, P, part, db);
+  return static_cast<int>(cudaGetLastError());
+}
+
 int conv_backward_data(int B, int Ci, int Co, int Lin, int up, const float* dZ, const bf16* W, float* dX,
                        const Products& pr, cudaStream_t s) {
   const int L = Lin * up;
+  if (pr.kind == 1) {
+    if (B <= 0) return 0;
+    if (!pr.err || !pr.pack || conv_pack_bytes(Ci, Co) > pr.pack_bytes || (up != 1 && up != 2))
+      return static_cast<int>(cudaErrorInvalidValue);
+    const int nq = (Co + CV_CK - 1) / CV_CK;
+    const size_t total = static_cast<size_t>((Ci + TC_BM - 1) / TC_BM) * nq * 3 * (CV_TAP / 2);
+    pack_conv_weights_t_kernel<<<grid_for(total), 256, 0, s>>>(Co, Ci, nq, total, W, pr.pack);
+    const long long tiles =
+        static_cast<long long>((Ci + TC_BM - 1) / TC_BM) * ((Lin + TC_BN - 1) / TC_BN) * static_cast<long long>(B);
+    if (tiles > 0x7FFFFFFFLL) return static_cast<int>(cudaErrorInvalidValue);
+    cudaError_t e;
+    if (up == 1) {
+      e = cudaFuncSetAttribute(tc_conv_dgrad_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Dgrad<1>::kSmem);
+      if (e != cudaSuccess) return static_cast<int>(e);
+      tc_conv_dgrad_kernel<1><<<static_cast<unsigned>(tiles), TC_THREADS, Dgrad<1>::kSmem, s>>>(
+          Ci, Co, Lin, L, dZ, pr.pack, dX, pr.err, pr.stall_test);
+    } else {
+      e = cudaFuncSetAttribute(tc_conv_dgrad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Dgrad<2>::kSmem);
+      if (e != cudaSuccess) return static_cast<int>(e);
+      tc_conv_dgrad_kernel<2><<<static_cast<unsigned>(tiles), TC_THREADS, Dgrad<2>::kSmem, s>>>(
+          Ci, Co, Lin, L, dZ, pr.pack, dX, pr.err, pr.stall_test);
+    }
+    return static_cast<int>(cudaGetLastError());
+  }
   return run_gemm(Ci, B * Lin, Co * 3 * up, ConvWeightTA{W, Ci, up >> 1},
                   ConvGradB{dZ, Co, Lin, L, up >> 1, div_by(Lin)}, ConvDataEp{dX, Ci, Lin, div_by(Lin)}, nullptr,
                   false, pr, s);
@@ -942,12 +1241,29 @@ int conv_backward_data(int B, int Ci, int Co, int Lin, int up, const float* dZ, 
 int conv_backward_weight(int B, int Ci, int Co, int Lin, int up, const float* dZ, const float* X, float* dW,
                          float* db, float* ws, const Products& pr, cudaStream_t s) {
   const int L = Lin * up;
-  int r = run_gemm(Co, Ci * 3, B * L, ConvGradA{dZ, Co, L, div_by(L)}, ConvInputWB{X, Ci, Lin, L, up >> 1, div_by(L)},
-                   StoreEp{dW, Ci * 3}, ws,
-                   true, pr, s);
+  int r = 0;
+  if (pr.kind == 1 && B > 0) {
+    if (!pr.err) return static_cast<int>(cudaErrorInvalidValue);
+    int S = ws ? splits_for(Co, Ci * 3, B * L, 1) : 1;
+    if (S > B) S = B;
+    const long long tiles =
+        static_cast<long long>((Co + TC_BM - 1) / TC_BM) * 3 * ((Ci + TC_BN - 1) / TC_BN) * static_cast<long long>(S);
+    if (tiles > 0x7FFFFFFFLL) return static_cast<int>(cudaErrorInvalidValue);
+    const cudaError_t e =
+        cudaFuncSetAttribute(tc_conv_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    tc_conv_wgrad_kernel<<<static_cast<unsigned>(tiles), TC_THREADS, TC_SMEM, s>>>(
+        B, Ci, Co, Lin, L, up >> 1, S, dZ, X, S > 1 ? ws : dW, pr.err, pr.stall_test);
+    if (S > 1)
+      splitk_finalize_kernel<<<grid_for(static_cast<size_t>(Co) * Ci * 3), 256, 0, s>>>(Co, Ci * 3, S, ws,
+                                                                                        StoreEp{dW, Ci * 3});
+    r = static_cast<int>(cudaGetLastError());
+  } else {
+    r = run_gemm(Co, Ci * 3, B * L, ConvGradA{dZ, Co, L, div_by(L)}, ConvInputWB{X, Ci, Lin, L, up >> 1, div_by(L)},
+                 StoreEp{dW, Ci * 3}, ws, true, pr, s);
+  }
   if (r) return r;
-  channel_sums_kernel<<<Co, 256, 0, s>>>(B, Co, L, dZ, db);
-  return static_cast<int>(cudaGetLastError());
+  return channel_sums(B, Co, L, dZ, db, pr, s);
 }
 
 int gelu_backward(size_t n, const float* pre, float* dz, cudaStream_t s) {
@@ -967,15 +1283,20 @@ int adam_update(size_t n, float* p, const float* g, float* m, float* v, bf16* pb
 }
 
 int contract_forward(int B, int K, int C, int L, int in_dim, const float* x, const float* D, float* y, cudaStream_t s) {
-  contract_forward_kernel<<<grid_for(static_cast<size_t>(B) * C * L), 256, 0, s>>>(B, K, C, L, in_dim, in_dim - K, x,
-                                                                                  D, y);
+  if (B <= 0) return 0;
+  const size_t CL = static_cast<size_t>(C) * L;
+  const int gx = static_cast<int>(std::min<size_t>((CL + 255) / 256, 64));
+  contract_forward_kernel<<<dim3(gx, std::min(B, 65535)), 256, 0, s>>>(B, K, C, L, in_dim, in_dim - K, x, D, y);
   return static_cast<int>(cudaGetLastError());
 }
 
 int contract_backward(int B, int K, int C, int L, int in_dim, const float* x, const float* dy, float* dD,
                       cudaStream_t s) {
-  contract_backward_kernel<<<grid_for(static_cast<size_t>(B) * K * C * L), 256, 0, s>>>(B, K, C, L, in_dim, in_dim - K,
-                                                                                       x, dy, dD);
+  if (B <= 0) return 0;
+  const size_t CL = static_cast<size_t>(C) * L;
+  const int gx = static_cast<int>(std::min<size_t>((CL + 255) / 256, 64));
+  contract_backward_kernel<<<dim3(gx, std::min(B * K, 65535)), 256, 0, s>>>(B, K, C, L, in_dim, in_dim - K, x, dy,
+                                                                           dD);
   return static_cast<int>(cudaGetLastError());
 }
 
