@@ -194,6 +194,8 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
   ws = std::max(ws, sgk::splitk_floats(hidden, in_dim, max_batch));
   ws = std::max(ws, sgk::splitk_floats(hidden, hidden, max_batch));
   ws = std::max(ws, sgk::splitk_floats(c0 * l0, hidden, max_batch));
+  ws = std::max(ws, sgk::splitk_floats(max_batch, hidden, c0 * l0));  // backward data of the dense layers
+  ws = std::max(ws, sgk::splitk_floats(max_batch, hidden, hidden));
   for (int st = 0; st < nstages; ++st)
     ws = std::max(ws, sgk::splitk_floats(m->cout[st], m->cin[st] * 3, max_batch * m->lout[st]));
   size_t pack = 0;
@@ -241,6 +243,7 @@ int sg_create(sg_model** out, int device, void* stream, int in_dim, int hidden, 
   m->prod.pack_bytes = pack;
   m->prod.red = m->d_red;
   m->prod.red_floats = kRedFloats;
+  m->prod.ws_floats = ws;
   *out = m;
   return SG_OK;
 }
@@ -337,12 +340,12 @@ int sg_loss_grad(sg_model* m, int b, const float* x, const float* target, double
   SG_LAUNCH(m, sgk::gelu_backward(static_cast<size_t>(b) * n3, m->d_a3, cur, s));
   SG_LAUNCH(m, sgk::linear_backward_weight(b, m->hidden, n3, cur, m->d_h2, m->d_g + m->oW3, m->d_g + m->ob3, m->d_ws,
                                            m->prod, s));
-  SG_LAUNCH(m, sgk::linear_backward_data(b, m->hidden, n3, cur, m->d_pb + m->oW3, other, m->prod, s));
+  SG_LAUNCH(m, sgk::linear_backward_data(b, m->hidden, n3, cur, m->d_pb + m->oW3, other, m->d_ws, m->prod, s));
   std::swap(cur, other);
   SG_LAUNCH(m, sgk::gelu_backward(static_cast<size_t>(b) * m->hidden, m->d_a2, cur, s));
   SG_LAUNCH(m, sgk::linear_backward_weight(b, m->hidden, m->hidden, cur, m->d_h1, m->d_g + m->oW2, m->d_g + m->ob2,
                                            m->d_ws, m->prod, s));
-  SG_LAUNCH(m, sgk::linear_backward_data(b, m->hidden, m->hidden, cur, m->d_pb + m->oW2, other, m->prod, s));
+  SG_LAUNCH(m, sgk::linear_backward_data(b, m->hidden, m->hidden, cur, m->d_pb + m->oW2, other, m->d_ws, m->prod, s));
   std::swap(cur, other);
   SG_LAUNCH(m, sgk::gelu_backward(static_cast<size_t>(b) * m->hidden, m->d_a1, cur, s));
   SG_LAUNCH(m, sgk::linear_backward_weight(b, m->in_dim, m->hidden, cur, x, m->d_g + m->oW1, m->d_g + m->ob1, m->d_ws,

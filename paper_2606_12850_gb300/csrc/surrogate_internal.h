@@ -27,6 +27,7 @@ struct Products {
   size_t pack_bytes = 0;
   float* red = nullptr;   // scratch of red_floats for the bias gradients' per-slice sums
   size_t red_floats = 0;
+  size_t ws_floats = 0;   // capacity of the split-K workspace a call receives (splits are clamped to it)
 };
 // Bytes of the packed weights of a convolution with Ci input and Co output channels.
 size_t conv_pack_bytes(int Ci, int Co);
@@ -37,9 +38,9 @@ size_t splitk_floats(int M, int N, int K);
 // Y = act(X W^T + b): X [B][K], W [N][K] (bf16), pre/out [B][N]; out may alias nothing.
 int linear_forward(int B, int K, int N, const float* X, const bf16* W, const float* bias, float* pre, float* out,
                    bool gelu, const Products& pr, cudaStream_t s);
-// dX [B][K] = dZ [B][N] W [N][K]
-int linear_backward_data(int B, int K, int N, const float* dZ, const bf16* W, float* dX, const Products& pr,
-                         cudaStream_t s);
+// dX [B][K] = dZ [B][N] W [N][K]; split over N through ws (splitk_floats(B, K, N)) when given
+int linear_backward_data(int B, int K, int N, const float* dZ, const bf16* W, float* dX, float* ws,
+                         const Products& pr, cudaStream_t s);
 // dW [N][K] = dZ^T X; db [N] = column sums of dZ
 int linear_backward_weight(int B, int K, int N, const float* dZ, const float* X, float* dW, float* db, float* ws,
                            const Products& pr, cudaStream_t s);

@@ -787,7 +787,10 @@ int run_gemm(int M, int N, int K, LA la, LB lb, EP ep, float* ws, bool allow_spl
              cudaStream_t s) {
   if (M <= 0 || N <= 0) return 0;
   if (pr.kind != 0 && (pr.kind != 1 || !pr.err)) return static_cast<int>(cudaErrorInvalidValue);
-  const int splits = (allow_split && ws) ? splits_for(M, N, K, pr.kind) : 1;
+  int splits = (allow_split && ws) ? splits_for(M, N, K, pr.kind) : 1;
+  const size_t mn = static_cast<size_t>(M) * N;
+  if (splits > 1 && static_cast<size_t>(splits) * mn > pr.ws_floats)
+    splits = static_cast<int>(std::max<size_t>(1, pr.ws_floats / mn));
   static_assert(BKM == TC_BK, "one K granule for both product kernels");
   int kchunk = (K + splits - 1) / splits;
   kchunk = (kchunk + BKM - 1) / BKM * BKM;
@@ -1153,8 +1156,9 @@ int linear_forward(int B, int K, int N, const float* X, const bf16* W, const flo
   return run_gemm(B, N, K, RowMajorA{X, K}, WeightColB{W, K}, LinearEp{pre, out, bias, N, act}, nullptr, false, pr, s);
 }
 
-int linear_backward_data(int B, int K, int N, const float* dZ, const bf16* W, float* dX, const Products& pr, cudaStream_t s) {
-  return run_gemm(B, K, N, RowMajorA{dZ, N}, WeightRowB{W, K}, StoreEp{dX, K}, nullptr, false, pr, s);
+int linear_backward_data(int B, int K, int N, const float* dZ, const bf16* W, float* dX, float* ws,
+                         const Products& pr, cudaStream_t s) {
+  return run_gemm(B, K, N, RowMajorA{dZ, N}, WeightRowB{W, K}, StoreEp{dX, K}, ws, true, pr, s);
 }
 
 int linear_backward_weight(int B, int K, int N, const float* dZ, const float* X, float* dW, float* db, float* ws,
@@ -1246,6 +1250,8 @@ int conv_backward_weight(int B, int Ci, int Co, int Lin, int up, const float* dZ
     if (!pr.err) return static_cast<int>(cudaErrorInvalidValue);
     int S = ws ? splits_for(Co, Ci * 3, B * L, 1) : 1;
     if (S > B) S = B;
+    const size_t mn = static_cast<size_t>(Co) * Ci * 3;
+    if (S > 1 && static_cast<size_t>(S) * mn > pr.ws_floats) S = static_cast<int>(std::max<size_t>(1, pr.ws_floats / mn));
     const long long tiles =
         static_cast<long long>((Co + TC_BM - 1) / TC_BM) * 3 * ((Ci + TC_BN - 1) / TC_BN) * static_cast<long long>(S);
     if (tiles > 0x7FFFFFFFLL) return static_cast<int>(cudaErrorInvalidValue);
