@@ -128,6 +128,7 @@ class Model:
                                co.ctypes.data_as(_P), up.ctypes.data_as(_P), int(spec.contract), int(max_batch)),
                "sg_create")
         self.handle = out.value
+        self.device = int(device)
         self.max_batch = int(max_batch)
         info = self.info()
         self.nparams = info["params"]
@@ -163,14 +164,14 @@ class Model:
 
     def forward(self, x_dev, y_dev):
         b = x_dev.shape[0]
-        _check(lib().sg_forward(self.handle, b, sem._dev(x_dev, b * self.spec.in_dim),
-                                sem._dev(y_dev, b * self.spec.out_c * self.spec.out_l)), "sg_forward", self)
+        _check(lib().sg_forward(self.handle, b, sem._dev(x_dev, b * self.spec.in_dim, self),
+                                sem._dev(y_dev, b * self.spec.out_c * self.spec.out_l, self)), "sg_forward", self)
 
     def loss_grad(self, x_dev, t_dev) -> float:
         b = x_dev.shape[0]
         loss = ctypes.c_double(0.0)
-        _check(lib().sg_loss_grad(self.handle, b, sem._dev(x_dev, b * self.spec.in_dim),
-                                  sem._dev(t_dev, b * self.spec.out_c * self.spec.out_l), ctypes.byref(loss)),
+        _check(lib().sg_loss_grad(self.handle, b, sem._dev(x_dev, b * self.spec.in_dim, self),
+                                  sem._dev(t_dev, b * self.spec.out_c * self.spec.out_l, self), ctypes.byref(loss)),
                "sg_loss_grad", self)
         return loss.value
 

@@ -337,3 +337,29 @@ def test_library_geometry_from_points_matches_oracle(ngll):
     bad[0, 0] = bad[0, -1]  # folds the first element
     with pytest.raises(sem.SemError):
         sem.sem_geometry_points(ngll, bad)
+
+
+def test_surrogate_argument_errors_before_any_device_call():
+    """Host-side checks of the surrogate ABI that fail before any CUDA call: options on a null
+    model, an unknown option, and a batch whose sample indices (max_batch x output length)
+    reach 2^24, past which the products' float-reciprocal division is not exact."""
+    import ctypes
+
+    from paper_2606_12850_gb300 import sem, surrogate
+    lib = surrogate.lib()
+    val = ctypes.c_int(7)
+    assert lib.sg_set_option(None, surrogate.SG_OPT_PRODUCT, 1) == -1
+    assert lib.sg_get_option(None, surrogate.SG_OPT_PRODUCT, ctypes.byref(val)) == -1
+    assert val.value == 7
+    spec = surrogate.Spec()
+    co = np.asarray(spec.stage_cout, dtype=np.int32)
+    up = np.asarray(spec.stage_up, dtype=np.int32)
+    out = ctypes.c_void_p()
+    too_big = (1 << 24) // spec.out_l + 1  # max_batch x 1000 samples >= 2^24
+    code = lib.sg_create(ctypes.byref(out), 0, None, spec.in_dim, spec.hidden, spec.c0, spec.l0, len(co),
+                         co.ctypes.data_as(ctypes.c_void_p), up.ctypes.data_as(ctypes.c_void_p), int(spec.contract),
+                         too_big)
+    assert code == -1 and out.value is None
+    assert b"2^24" in lib.sg_last_error(None)
+    with pytest.raises(sem.SemError):
+        surrogate.Model(spec, max_batch=too_big)
