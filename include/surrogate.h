@@ -83,7 +83,8 @@ int sg_sync(sg_model* model);
 
 /* Options. SG_OPT_PRODUCT picks the kernel of every product (dense layers, convolutions and
  * their backward products): 1 (the default) = tcgen05.mma with the float32 accumulator in
- * tensor memory, 128 x 128 tiles; 0 = warp-level mma.sync, 128/256 x 64 tiles. Both round the
+ * tensor memory, 128 x 128 tiles (the convolutions stage their input window once for the
+ * three taps); 0 = warp-level mma.sync, 128/256 x 64 tiles. Both round the
  * operands to bfloat16 and accumulate in float32, so they agree to float32 rounding order.
  * Setting an option waits for the model's stream. A tcgen05 product that waits more than 2 s
  * for its MMAs gives up: sg_loss_grad and sg_sync then return SEM_ETIMEOUT. */

@@ -1,8 +1,11 @@
-// CUDA kernels of the seismogram surrogate (sm_103a): one tiled tensor-core product kernel
-// (bfloat16 operands, float32 accumulation) whose operand loaders express the dense layers,
-// the width-3 convolutions (with nearest upsampling folded into the index map) and their
-// backward products; bias, activation, loss and Adam kernels. Every sum is accumulated in
-// float32 in a fixed order (split-K partial sums are added in split order).
+// CUDA kernels of the seismogram surrogate (sm_103a). Products (bfloat16 operands, float32
+// accumulation) on the fifth-generation tensor cores: tcgen05.mma with the accumulator in
+// tensor memory, for the width-3 convolutions (tc_conv_kernel), their data and weight
+// gradients (tc_conv_dgrad_kernel, tc_conv_wgrad_kernel) and, through operand loaders that
+// express each layer, the dense layers and their backward products (tc_gemm_kernel); the
+// same products on the warp-level mma.sync kernel (gemm_kernel) as the alternative. Bias,
+// activation, loss and Adam kernels. Every sum is accumulated in float32 in a fixed order
+// (split-K partial sums are added in split order).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
