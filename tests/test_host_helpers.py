@@ -126,3 +126,14 @@ def test_predict_or_solve_requires_a_solver():
     sur = surrogate.Surrogate(None, 1.0, 4000.0, amp, solver=None)
     with pytest.raises(ValueError, match="solver"):
         sur.predict_or_solve(np.zeros((2, 3)), np.zeros((2, 6)), tol=0.5)
+
+
+def test_product_flops_of_the_default_network():
+    """The FLOP count behind the surrogate's reported TFLOP/s: 2 per multiply-add of the three
+    dense layers (9x512, 512x512, 512x8000) and the four width-3 convolutions (64->96 at 250
+    samples, 96->96 at 500 and 1000, 96->1152 at 1000)."""
+    import bench
+    from paper_2606_12850_gb300 import surrogate
+    dense = 9 * 512 + 512 * 512 + 512 * 64 * 125
+    conv = 96 * 64 * 3 * 250 + 96 * 96 * 3 * 500 + 96 * 96 * 3 * 1000 + 1152 * 96 * 3 * 1000
+    assert bench.product_flops(surrogate.Spec()) == 2 * (dense + conv) == 764437504
