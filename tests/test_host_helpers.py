@@ -137,3 +137,18 @@ def test_product_flops_of_the_default_network():
     dense = 9 * 512 + 512 * 512 + 512 * 64 * 125
     conv = 96 * 64 * 3 * 250 + 96 * 96 * 3 * 500 + 96 * 96 * 3 * 1000 + 1152 * 96 * 3 * 1000
     assert bench.product_flops(surrogate.Spec()) == 2 * (dense + conv) == 764437504
+
+
+def test_reciprocal_division_is_exact_below_2_pow_24():
+    """The products' index maps divide k (a sample-time index, k < 2^24 as sg_create enforces)
+    by a layer length d with q = trunc(float(k) * float(1/d)) in float32 and one correction
+    step q += (r >= d) - (r < 0), r = k - q d. Checked for every k < 2^24 against integer
+    division, for the lengths of the default and test networks and a spread of others."""
+    ks = np.arange(1 << 24, dtype=np.int64)
+    kf = ks.astype(np.float32)  # exact: every k < 2^24 is a float32
+    for d in (1, 3, 7, 14, 28, 125, 250, 500, 1000, 997, 1024, 4093, 65537):
+        inv = np.float32(1.0) / np.float32(d)
+        q = np.trunc(kf * inv).astype(np.int64)  # float32 product rounded to nearest
+        r = ks - q * d
+        q += (r >= d).astype(np.int64) - (r < 0).astype(np.int64)
+        assert np.array_equal(q, ks // d), d
